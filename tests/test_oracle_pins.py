@@ -1,0 +1,354 @@
+"""Pins of the CPU oracle against facts fixed outside it.
+
+Each test checks the oracle against something other than itself: published
+test vectors, closed forms, brute-force enumeration written independently in
+plain Python loops, invariants the paper fixes, and exact special cases.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import falconn as F
+from oracle import rotations as RG
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- rotations
+
+def test_splitmix64_published_vectors():
+    want = [int(x) for x in open(os.path.join(GOLDEN, "splitmix64_seed1234567.txt"))
+            if x.strip() and not x.startswith("#")]
+    got = [int(v) for v in RG.splitmix64(1234567, 5)]
+    assert got == want
+
+
+def test_splitmix64_counter_offset_matches_sequence():
+    full = RG.splitmix64(99, 40)
+    assert np.array_equal(RG.splitmix64(99, 10, start=30), full[30:])
+
+
+def test_box_muller_closed_forms():
+    # sqrt(-2 ln u1) cos(2 pi u2) at points where it is exact by hand
+    u1 = np.array([math.exp(-0.5), math.exp(-2.0), 1.0, math.exp(-4.5)])
+    u2 = np.array([0.0, 0.5, 0.3, 0.25])
+    z = RG.box_muller(u1, u2)
+    assert z[0] == pytest.approx(1.0, abs=1e-15)
+    assert z[1] == pytest.approx(-2.0, abs=1e-15)
+    assert z[2] == 0.0
+    assert abs(z[3]) < 1e-15
+
+
+def test_rotations_are_standard_normal():
+    from scipy import stats
+    R = O.gaussian_rotations(7, 4, 64, 128).reshape(-1).astype(np.float64)
+    assert abs(R.mean()) < 0.01
+    assert abs(R.var() - 1.0) < 0.01
+    assert stats.kstest(R[:50000], "norm").pvalue > 1e-3
+    # streams of different (table, hash) are uncorrelated
+    a = RG.gaussian_stream(7, 0, 20000).astype(np.float64)
+    b = RG.gaussian_stream(7, 1, 20000).astype(np.float64)
+    assert abs(np.corrcoef(a, b)[0, 1]) < 0.03
+
+
+def test_uniforms_in_range():
+    raw = RG.splitmix64(RG.stream_state(5, 3), 20000)
+    u1, u2 = RG.uniform_pair(raw)
+    assert (u1 > 0).all() and (u1 <= 1).all()
+    assert (u2 >= 0).all() and (u2 < 1).all()
+
+
+# ---------------------------------------------------------------- hashing
+
+def _hash_by_enumeration(p):
+    """Eq. 1 restated as a search over the 2D signed vectors +-r_i: the wedge
+    whose signed projection s * p_i is largest, first wedge on ties."""
+    D = len(p)
+    best_h, best_v = None, -math.inf
+    for i in range(D):           # +r_i wedges first, then ties keep lower i
+        for s, h in ((1.0, i), (-1.0, i + D)):
+            v = s * p[i]
+            if v > best_v:
+                best_h, best_v = h, v
+    return best_h
+
+
+def test_hash_golden_2d():
+    g = json.load(open(os.path.join(GOLDEN, "cross_polytope_2d.json")))
+    X = np.array(g["points"])
+    R1, R2 = np.array(g["R_hash1"]), np.array(g["R_hash2"])
+    h1, _, _ = O.cross_polytope_hash(X @ R1.T)
+    assert h1.tolist() == g["hash1"]
+    h2, _, _ = O.cross_polytope_hash(X @ R2.T)
+    assert int(h2[0]) == g["hash2_point0"]
+    assert int(h1[0]) * 6 + int(h2[0]) == g["bucket_point0"]
+
+
+def test_probe_golden_2d():
+    g = json.load(open(os.path.join(GOLDEN, "cross_polytope_2d.json")))
+    R = np.array([g["R_hash1"], g["R_hash2"]], dtype=np.float64)[None]
+    X = np.array(g["points"])
+    ix = O.build_index(X, L=1, D=3, alpha=1.0, R=R)
+    b, s, flag = O.probe_buckets(ix, np.array(g["query"]), 3)
+    assert b[0].tolist() == g["probes_P3"]
+    assert not flag[0]
+
+
+def test_hash_matches_enumeration():
+    rng = np.random.default_rng(1)
+    for D in (1, 2, 3, 8, 17):
+        p = rng.standard_normal((200, D))
+        h, top, _ = O.cross_polytope_hash(p)
+        for r in range(p.shape[0]):
+            assert h[r] == _hash_by_enumeration(list(p[r]))
+            assert top[r] == max(abs(x) for x in p[r])
+
+
+def test_hash_standard_basis_is_nearest_cross_polytope_vertex():
+    # r_i = e_i: the hash is the nearest vertex +-e_i of the cross-polytope,
+    # i.e. the coordinate of largest magnitude with its sign.
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((500, 6))
+    h, _, _ = O.cross_polytope_hash(x @ np.eye(6).T)
+    verts = np.concatenate([np.eye(6), -np.eye(6)])
+    dist = ((x[:, None, :] / np.linalg.norm(x, axis=1)[:, None, None] - verts[None]) ** 2).sum(-1)
+    assert np.array_equal(h, np.argmin(dist, axis=1))
+
+
+def test_hash_invariances():
+    rng = np.random.default_rng(3)
+    D = 16
+    R = rng.standard_normal((D, 10))
+    x = rng.standard_normal((300, 10))
+    h, _, _ = O.cross_polytope_hash(x @ R.T)
+    h_scaled, _, _ = O.cross_polytope_hash((3.5 * x) @ R.T)
+    h_neg, _, _ = O.cross_polytope_hash((-x) @ R.T)
+    assert np.array_equal(h, h_scaled)
+    assert np.array_equal(h_neg, (h + D) % (2 * D))     # antipodal wedge
+
+
+# ---------------------------------------------------------------- index build
+
+def test_every_point_in_exactly_one_bucket(tiny_data, tiny_index):
+    w, X, _ = tiny_data
+    ix = tiny_index
+    assert (ix.counts.sum(axis=1) == w.n).all()
+    for t in range(ix.L):
+        assert np.array_equal(np.bincount(ix.point_buckets[t], minlength=ix.nbuckets),
+                              ix.counts[t])
+
+
+def test_point_buckets_match_per_point_hash(tiny_data, tiny_index):
+    w, X, _ = tiny_data
+    ix = tiny_index
+    R = O.gaussian_rotations(w.rot_seed, w.L, w.D, w.d).astype(np.float64)
+    rng = np.random.default_rng(4)
+    for pid in rng.choice(w.n, 40, replace=False):
+        for t in (0, w.L - 1):
+            x = X[pid].astype(np.float64)
+            h1 = _hash_by_enumeration(list(R[t, 0] @ x))
+            h2 = _hash_by_enumeration(list(R[t, 1] @ x))
+            assert ix.point_buckets[t, pid] == h1 * 2 * w.D + h2
+
+
+def test_kept_count_is_ceil_alpha_B(tiny_index):
+    ix = tiny_index
+    kept = np.diff(ix.offsets, axis=1)
+    for B, c in zip(ix.counts.reshape(-1), kept.reshape(-1)):
+        assert c == -((-2 * int(B)) // 10)      # ceil(0.2 B) in integers
+
+
+def test_keep_count_matches_rational_ceil():
+    B = np.arange(0, 200001)
+    for a, b in ((1, 10), (1, 5), (1, 20), (1, 100), (3, 10)):
+        want = -((-a * B) // b)
+        assert np.array_equal(O.keep_count(B, a / b), want), (a, b)
+
+
+def test_limit_scaling_keep_count():
+    B = np.arange(0, 500)
+    got = O.keep_count(B, 0.01, iprobes=3, kappa=20)
+    want = np.minimum(B, np.maximum(20, -((-B) // 300)))
+    assert np.array_equal(got, want)
+
+
+def test_alpha_one_keeps_everything(tiny_data):
+    w, X, _ = tiny_data
+    ix = O.build_index(X[:2000], 3, 16, 1.0, seed=11)
+    for t in range(3):
+        assert np.array_equal(np.sort(ix.ids[t]), np.arange(2000))
+
+
+def test_filter_keeps_top_by_projection_magnitude():
+    # brute force per bucket: recompute |x^T r_i1| + |x^T r_i2| in Python
+    X, _ = W.small_mixture(600, 1, 8, 4, 0.2, 5)
+    R = O.gaussian_rotations(12, 2, 4, 8).astype(np.float64)
+    ix = O.build_index(X, 2, 4, 0.3, R=R)
+    for t in range(2):
+        buckets = {}
+        for pid in range(600):
+            x = [float(v) for v in X[pid]]
+            p1 = [sum(a * b for a, b in zip(x, r)) for r in R[t, 0]]
+            p2 = [sum(a * b for a, b in zip(x, r)) for r in R[t, 1]]
+            h1, h2 = _hash_by_enumeration(p1), _hash_by_enumeration(p2)
+            f = max(abs(v) for v in p1) + max(abs(v) for v in p2)
+            buckets.setdefault(h1 * 8 + h2, []).append((-f, pid))
+        for b in range(ix.nbuckets):
+            members = sorted(buckets.get(b, []))
+            c = math.ceil(0.3 * len(members) - 1e-12)
+            assert ix.bucket_ids(t, b).tolist() == [pid for _, pid in members[:c]]
+
+
+def test_multiprobe_indexing_counts():
+    X, _ = W.small_mixture(500, 1, 8, 4, 0.2, 6)
+    ix = O.build_index(X, 2, 4, 0.5, seed=3, iprobes=3, kappa=2)
+    assert (ix.counts.sum(axis=1) == 3 * 500).all()     # Algorithm 1: n*iProbes entries
+    kept = np.diff(ix.offsets, axis=1)
+    assert np.array_equal(kept, O.keep_count(ix.counts, 0.5, 3, 2))
+    for t in range(2):   # a point appears at most once per bucket
+        for b in range(ix.nbuckets):
+            ids = ix.bucket_ids(t, b)
+            assert len(set(ids.tolist())) == len(ids)
+
+
+# ---------------------------------------------------------------- probing
+
+def _pairs_by_enumeration(p1, p2, P):
+    D = len(p1)
+    v1 = list(p1) + [-x for x in p1]
+    v2 = list(p2) + [-x for x in p2]
+    allp = [(-(v1[a] + v2[b]), a * 2 * D + b) for a in range(2 * D) for b in range(2 * D)]
+    allp.sort()
+    return [b for _, b in allp[:P]]
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 5])
+def test_probe_ranking_matches_full_enumeration(D):
+    rng = np.random.default_rng(D)
+    R = rng.standard_normal((1, 2, D, 4))
+    ix = O.build_index(rng.standard_normal((5, 4)), 1, D, 1.0, R=R)
+    for _ in range(20):
+        q = rng.standard_normal(4)
+        p = R[0] @ q
+        for P in sorted({1, 2, 3, D, 2 * D, 4 * D * D - 1, 4 * D * D} - {0}):
+            b, _, _ = O.probe_buckets(ix, q, P)
+            assert b[0].tolist() == _pairs_by_enumeration(p[0], p[1], P)
+
+
+def test_single_probe_is_query_bucket(tiny_data, tiny_index):
+    w, X, Q = tiny_data
+    ix = tiny_index
+    for q in Q[:20]:
+        b, _, _ = O.probe_buckets(ix, q, 1)
+        p = ix.R @ q.astype(np.float64)
+        h1, _, _ = O.cross_polytope_hash(p[:, 0])
+        h2, _, _ = O.cross_polytope_hash(p[:, 1])
+        assert np.array_equal(b[:, 0], h1 * 2 * w.D + h2)
+
+
+def test_probe_sets_nested_and_scores_sorted(tiny_data, tiny_index):
+    w, X, Q = tiny_data
+    for q in Q[:10]:
+        b4, s4, _ = O.probe_buckets(tiny_index, q, 4)
+        b16, s16, _ = O.probe_buckets(tiny_index, q, 16)
+        assert (np.diff(s16, axis=1) <= 0).all()
+        assert np.array_equal(b16[:, :4], b4)
+
+
+# ---------------------------------------------------------------- search
+
+def test_bruteforce_matches_full_sort():
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((300, 5))
+    Q = rng.standard_normal((7, 5))
+    ids, sc, _ = O.brute_force(X, Q, 12)
+    for i in range(7):
+        s = [(-sum(float(a) * float(b) for a, b in zip(X[j], Q[i])), j) for j in range(300)]
+        s.sort()
+        assert ids[i].tolist() == [j for _, j in s[:12]]
+
+
+def test_short_results_are_padded():
+    X = np.eye(4)
+    ids, sc, _ = O.brute_force(X, np.ones((1, 4)), 6)
+    assert ids[0, 4:].tolist() == [-1, -1]
+    assert np.isneginf(sc[0, 4:]).all()
+
+
+def test_unfiltered_full_probe_equals_bruteforce():
+    # alpha = 1 and all 4D^2 buckets probed: every point is a candidate, so
+    # Falconn++ returns the exact top-k.
+    X, Q = W.small_mixture(3000, 20, 16, 32, 0.1, 9)
+    ix = O.build_index(X, 2, 4, 1.0, seed=21)
+    ids, sc, res = O.search_batch(ix, Q, 10, 4 * 4 * 4)
+    bi, bs, _ = O.brute_force(X, Q, 10)
+    assert all(r.cand.size == 3000 for r in res)
+    assert np.array_equal(ids, bi)
+    assert np.allclose(sc, bs)
+
+
+def test_search_topk_is_exact_over_candidates(tiny_data, tiny_index):
+    w, X, Q = tiny_data
+    for q in Q[:10]:
+        r = O.search(tiny_index, q, 10, 4)
+        s = sorted((-float(np.dot(X[c].astype(np.float64), q.astype(np.float64))), int(c))
+                   for c in r.cand)
+        assert r.ids.tolist() == [c for _, c in s[:10]]
+
+
+def test_candidates_are_union_of_probed_buckets(tiny_data, tiny_index):
+    w, X, Q = tiny_data
+    ix = tiny_index
+    r = O.search(ix, Q[0], 10, 4)
+    u = set()
+    for t in range(ix.L):
+        for b in r.buckets[t]:
+            u.update(ix.ids[t][ix.offsets[t, b]: ix.offsets[t, b + 1]].tolist())
+    assert sorted(u) == r.cand.tolist()
+
+
+def test_recall_monotone_in_probes(tiny_data, tiny_index):
+    # probe sets are nested, so candidate sets are nested, so the exact top-k
+    # over them can only gain true neighbours
+    w, X, Q = tiny_data
+    bi, _, _ = O.brute_force(X, Q[:30], 10)
+    prev = -1.0
+    prev_c = None
+    for P in (1, 2, 4, 8, 32):
+        ids, _, res = O.search_batch(tiny_index, Q[:30], 10, P)
+        r = O.recall_at(ids, bi, 10)
+        assert r >= prev
+        prev = r
+        if prev_c is not None:
+            for a, b in zip(prev_c, res):
+                assert set(a.cand.tolist()) <= set(b.cand.tolist())
+        prev_c = res
+    assert prev > 0.9
+
+
+def test_ceos_projection_preserves_inner_product_order():
+    # Lemma 2 (CEOs): on the vector r_1 = argmax |q^T r_i|, x^T r_1 is
+    # centred at sgn(q^T r_1) x^T q sqrt(2 ln D).  Loose statistical check
+    # of the mean over many independent draws.
+    rng = np.random.default_rng(10)
+    d, D, trials = 64, 512, 300
+    q = rng.standard_normal(d); q /= np.linalg.norm(q)
+    z = rng.standard_normal(d); z -= z.dot(q) * q; z /= np.linalg.norm(z)
+    c = 0.6
+    x = c * q + math.sqrt(1 - c * c) * z
+    vals = []
+    for _ in range(trials):
+        R = rng.standard_normal((D, d))
+        p = R @ q
+        i = int(np.argmax(np.abs(p)))
+        vals.append(np.sign(p[i]) * (R[i] @ x))
+    mean = float(np.mean(vals))
+    # asymptotic value c * sqrt(2 ln D) = 2.13; the finite-D mean of the top
+    # order statistic is a little smaller, so a band of +-20%
+    assert 0.8 * c * math.sqrt(2 * math.log(D)) < mean < 1.2 * c * math.sqrt(2 * math.log(D))
