@@ -1,0 +1,194 @@
+/*
+ * fpp.h -- C ABI of libfpp, a GB300 (sm_103a) implementation of the
+ * Falconn++ search path (Pham & Liu, "Falconn++: A Locality-sensitive
+ * Filtering Approach for Approximate Nearest Neighbor Search", NeurIPS 2022).
+ *
+ * The method: L hash tables, each the concatenation of l = 2 cross-polytope
+ * hashes over D Gaussian random vectors (Section 2.2, Eq. 1), so a table has
+ * 4D^2 buckets.  Each bucket keeps only the fraction alpha of its points with
+ * the largest projection magnitude, the locality-sensitive filter (Section
+ * 3.4).  A query probes the P highest-ranked buckets of every table, ranked by
+ * projection value (Section 3.4, "Multi-probing for querying"), takes the
+ * union of their kept points, scores them by exact inner product and returns
+ * the top-k (the problem statement of Section 1: top-k by x^T q on the unit
+ * sphere).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns fpp_status; no exception or abort crosses the ABI.
+ *    On failure fpp_last_error() returns a message owned by the library and
+ *    valid until the calling thread's next libfpp call.
+ *  - Matrices are row-major, FP32, with rows of exactly d elements.
+ *  - A pointer argument may point to host memory (pageable or pinned) or to
+ *    device memory of the current CUDA device; the library detects which
+ *    with cudaPointerGetAttributes and copies as needed.  Device pointers
+ *    must be 4-byte aligned.
+ *  - Results are complete when the call returns, except when the caller
+ *    passes a non-NULL stream in fpp_search_opts AND both result pointers
+ *    are device memory: then the results are complete once that stream has
+ *    reached the call's point (the call itself does not synchronise).
+ *  - An fpp_index is immutable after fpp_build.  Concurrent searches on one
+ *    index from several host threads are serialised by a per-index lock.
+ *  - Decisions (bucket ids, probe sets, candidate sets, top-k ids) equal
+ *    those of an exact FP64 evaluation of the method except where an FP64
+ *    margin below 1e-6 makes two answers equally valid; returned scores are
+ *    FP64-accurate inner products rounded to FP32.
+ */
+#ifndef FPP_H_
+#define FPP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fpp_status {
+  FPP_OK = 0,
+  FPP_EINVAL = 1,    /* an argument is out of range or a pointer is NULL */
+  FPP_ENOMEM = 2,    /* device or host allocation failed */
+  FPP_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+  FPP_ETIMEOUT = 4,  /* a bounded device wait ran out */
+  FPP_EBUSY = 5,     /* resource in use (serving slots, admission) */
+  FPP_EINTERNAL = 6  /* a device-side consistency check failed */
+} fpp_status;
+
+typedef enum fpp_precision {
+  FPP_FP32 = 0,      /* FP32 storage and projections, FP64-exact decisions */
+  FPP_BF16 = 1       /* BF16 storage and projections, FP32 re-rank */
+} fpp_precision;
+
+/* Index parameters.  Initialise with fpp_default_params(). */
+typedef struct fpp_params {
+  int32_t L;           /* hash tables, >= 1 (Section 2.1: L tables)          */
+  int32_t D;           /* random vectors per hash, 1..1024 (Section 2.2)     */
+  int32_t iprobes;     /* indexing probes per point, >= 1 (Algorithm 1)      */
+  int32_t kappa;       /* limit scaling floor, 0 = off (Section 3.4)         */
+  double alpha;        /* kept fraction per bucket, 0 < alpha <= 1 (3.4)     */
+  uint64_t seed;       /* seed of the rotation generator (fpp_rotations)     */
+  const float* R;      /* optional explicit random vectors [L][2][D][d],
+                          host or device; NULL = generate from seed. Copied. */
+  int32_t precision;   /* fpp_precision                                      */
+  int32_t reserved0;
+  void* stream;        /* cudaStream_t for the build, or NULL (legacy)       */
+} fpp_params;
+
+/* Per-call search options.  Initialise with fpp_default_search_opts(). */
+typedef struct fpp_search_opts {
+  int32_t k;                  /* results per query when k_per_query is NULL  */
+  int32_t probes;             /* probes per table when probes_per_query is NULL */
+  const int32_t* k_per_query; /* optional [m] (host or device), each 1..k_max */
+  const int32_t* probes_per_query; /* optional [m], each 1..min(4D^2, 128)   */
+  int32_t k_max;              /* row stride of ids/scores; >= every k         */
+  int32_t table_begin;        /* search tables [table_begin, table_end)     */
+  int32_t table_end;          /* 0 or L = all tables                          */
+  int32_t reserved0;
+  void* stream;               /* cudaStream_t or NULL                         */
+} fpp_search_opts;
+
+/* Counters of one search call (summed over queries). */
+typedef struct fpp_search_stats {
+  uint64_t queries;
+  uint64_t probes;            /* buckets probed                               */
+  uint64_t entries;           /* bucket entries scanned, with duplicates      */
+  uint64_t unique;            /* distinct candidates scored                   */
+  uint64_t probe_rechecks;    /* (query, table) probe sets re-decided in
+                                 FP64-accurate arithmetic                     */
+  uint64_t topk_rechecks;     /* queries whose top-k boundary was re-decided  */
+  float ms_project;           /* device time per phase, milliseconds          */
+  float ms_probe;
+  float ms_gather_score;
+  float ms_total;
+} fpp_search_stats;
+
+typedef struct fpp_index_info {
+  int64_t n;
+  int32_t d, L, D, iprobes, kappa, precision;
+  double alpha;
+  uint64_t kept_total;        /* ids stored over all tables                   */
+  uint32_t max_bucket_kept;   /* largest kept bucket                          */
+  uint64_t device_bytes;      /* device memory held by the index              */
+  float build_ms;             /* wall time of fpp_build                        */
+} fpp_index_info;
+
+typedef struct fpp_index fpp_index;
+
+void fpp_default_params(fpp_params* p);
+void fpp_default_search_opts(fpp_search_opts* o);
+
+/* Builds the index over X [n][d] (Section 3.4 and Algorithm 1): generates or
+ * copies the random vectors, hashes every point into one bucket per table
+ * (iprobes buckets with multi-probe indexing), keeps in each bucket of size
+ * B the min(B, max(kappa, ceil(alpha * B / iprobes))) points with the
+ * largest filter score |x^T r_i1| + |x^T r_i2| (ties: lower point id), and
+ * stores each table as CSR.  X is copied; the caller keeps ownership.
+ * Errors: FPP_EINVAL for n < 1, d < 1, L < 1, D outside 1..1024,
+ * alpha outside (0, 1], iprobes < 1, kappa < 0, n >= 2^32.
+ * *out is set only on success; release it with fpp_free. */
+fpp_status fpp_build(const float* X, int64_t n, int32_t d, const fpp_params* p,
+                     fpp_index** out);
+
+/* Searches m queries Q [m][d]: writes ids [m][k] (int64, -1 padding) and
+ * scores [m][k] (FP32, -inf padding), best first (score desc, id asc).
+ * probes = buckets probed per table, 1..min(4D^2, 128); k = 1..256.
+ * m = 0 is a no-op. */
+fpp_status fpp_search(const fpp_index* ix, const float* Q, int64_t m, int32_t k,
+                      int32_t probes, int64_t* ids, float* scores);
+
+/* fpp_search with per-query k and probe budgets, a table range, a stream and
+ * counters.  ids/scores have row stride opts->k_max; entries past a query's
+ * own k are set to -1 / -inf.  stats may be NULL. */
+fpp_status fpp_search_ex(const fpp_index* ix, const float* Q, int64_t m,
+                         const fpp_search_opts* opts, int64_t* ids,
+                         float* scores, fpp_search_stats* stats);
+
+/* Releases the index and its device memory.  NULL is allowed. */
+void fpp_free(fpp_index* ix);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* fpp_last_error(void);
+
+/* Host-only: the canonical random vectors R[L][2][D][d] for a seed.  Stream
+ * 2t+j (table t, hash j) is SplitMix64 (Steele, Lea, Flood 2014) started at
+ * seed XOR 0x9E3779B97F4A7C15*(2t+j+1); coordinate (i, c) is the FP32-rounded
+ * Box-Muller value sqrt(-2 ln u1) cos(2 pi u2) of the stream's outputs
+ * 2(i d + c) and 2(i d + c)+1, u1 = (top53 + 1) / 2^53, u2 = top53 / 2^53.
+ * The paper fixes only that each coordinate is N(0, 1) (Section 2.2).
+ * R is host memory of L*2*D*d floats owned by the caller.  Needs no GPU. */
+fpp_status fpp_rotations(uint64_t seed, int32_t L, int32_t D, int32_t d, float* R);
+
+/* Host-only: kept count of a bucket of size B (Section 3.4, Algorithm 1):
+ * min(B, max(kappa, ceil((alpha * B) / iprobes))) in IEEE FP64. */
+uint64_t fpp_keep_count(uint64_t B, double alpha, int32_t iprobes, int32_t kappa);
+
+fpp_status fpp_index_get_info(const fpp_index* ix, fpp_index_info* info);
+
+/* Introspection for parity tests (all outputs host or device memory):
+ * fpp_debug_point_buckets: bucket id of every point in table t, [n] (only
+ *   for iprobes = 1; the id is h1 * 2D + h2 with h = i for +r_i, i + D for
+ *   -r_i, Eq. 1).
+ * fpp_debug_table: kept CSR of table t: offsets [4D^2 + 1] (relative to the
+ *   table) and ids [kept_t], ids ordered by filter score desc, id asc inside
+ *   a bucket.  Pass ids = NULL to get only offsets (kept_t = offsets[4D^2]).
+ * fpp_debug_probes: probed bucket ids [m][L'][probes] in rank order for the
+ *   tables of opts (L' = table_end - table_begin).  probes <= 128.  */
+fpp_status fpp_debug_point_buckets(const fpp_index* ix, int32_t t, uint32_t* out);
+fpp_status fpp_debug_table(const fpp_index* ix, int32_t t, uint32_t* offsets,
+                           uint32_t* ids);
+fpp_status fpp_debug_probes(const fpp_index* ix, const float* Q, int64_t m,
+                            int32_t probes, int32_t table_begin, int32_t table_end,
+                            uint32_t* out);
+
+/* Exact search: top-k of every query over all of X by inner product
+ * (ground truth for recall).  Same output conventions as fpp_search.
+ * stream may be NULL. */
+fpp_status fpp_bruteforce(const float* X, int64_t n, int32_t d, const float* Q,
+                          int64_t m, int32_t k, int64_t* ids, float* scores,
+                          void* stream);
+
+/* Number of kernels this process has launched through libfpp. */
+uint64_t fpp_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPP_H_ */

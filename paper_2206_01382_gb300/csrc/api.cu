@@ -1,0 +1,819 @@
+// C ABI of libfpp: index object, build and search orchestration.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace fpp {
+
+void generate_rotations(uint64_t seed, int L, int D, int d, float* R);
+
+namespace {
+thread_local std::string g_err;
+std::atomic<uint64_t> g_launches{0};
+}  // namespace
+
+void set_error(const std::string& msg) { g_err = msg; }
+std::atomic<uint64_t>& launch_counter() { return g_launches; }
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Grow-only device buffer.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  fpp_status ensure(size_t need, bool zero = false, cudaStream_t st = 0) {
+    if (need <= bytes && p) return FPP_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    const size_t sz = std::max<size_t>(need, 256);
+    FPP_CUDA(cudaMalloc(&p, sz));
+    bytes = sz;
+    if (zero) FPP_CUDA(cudaMemsetAsync(p, 0, sz, st));
+    return FPP_OK;
+  }
+  template <class T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
+struct Workspace {
+  DevBuf qpad, proj, probes, entries, kpq, ppq, out_ids, out_scores, bitmaps, stats;
+  int64_t bitmap_words = 0;
+  int slots = 0;
+  void release() {
+    for (DevBuf* b : {&qpad, &proj, &probes, &entries, &kpq, &ppq, &out_ids, &out_scores, &bitmaps, &stats})
+      b->release();
+  }
+};
+
+}  // namespace
+}  // namespace fpp
+
+struct fpp_index {
+  int64_t n = 0;
+  int d = 0, dpad = 0, L = 0, D = 0, iprobes = 1, kappa = 0, precision = 0;
+  double alpha = 1.0;
+  float* X = nullptr;          // [n][dpad]
+  float* R = nullptr;          // [2 L D][dpad]
+  float* rmax = nullptr;       // [2L]
+  float xmax = 0.f;
+  uint32_t* offsets = nullptr; // [L][4D^2 + 1]
+  uint64_t* table_base = nullptr;  // [L]
+  uint32_t* ids = nullptr;
+  uint64_t kept_total = 0;
+  uint32_t max_bucket_kept = 0;
+  std::vector<uint64_t> h_table_base;
+  int device = 0, sm_count = 0;
+  double gamma = 0.0;
+  uint64_t device_bytes = 0;
+  float build_ms = 0.f;
+  uint64_t build_rechecks = 0;
+  std::mutex mu;
+  fpp::Workspace ws;
+};
+
+using namespace fpp;
+
+namespace fpp_api {
+
+int64_t nbuckets(int D) { return 4ll * D * D; }
+
+fpp_status to_device_padded(const float* src, int64_t rows, int d, int dpad, float** dst,
+                            cudaStream_t st, uint64_t* bytes) {
+  FPP_CUDA(cudaMalloc(dst, (size_t)std::max<int64_t>(rows, 1) * dpad * sizeof(float)));
+  if (bytes) *bytes += (uint64_t)rows * dpad * sizeof(float);
+  if (dpad != d) FPP_CUDA(cudaMemsetAsync(*dst, 0, (size_t)rows * dpad * sizeof(float), st));
+  if (rows > 0)
+    FPP_CUDA(cudaMemcpy2DAsync(*dst, dpad * sizeof(float), src, d * sizeof(float), d * sizeof(float),
+                               rows, cudaMemcpyDefault, st));
+  return FPP_OK;
+}
+
+void free_index_memory(fpp_index* ix) {
+  cudaFree(ix->X);
+  cudaFree(ix->R);
+  cudaFree(ix->rmax);
+  cudaFree(ix->offsets);
+  cudaFree(ix->table_base);
+  cudaFree(ix->ids);
+  ix->ws.release();
+}
+
+__global__ void gather_u64_kernel(const uint64_t* src, int64_t stride, int cnt, uint64_t* dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cnt) dst[i] = src[(int64_t)i * stride];
+}
+
+__global__ void max_keep_kernel(const uint32_t* counts, int64_t n, double alpha, int iprobes,
+                                int kappa, unsigned* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t B = counts[i];
+  double c = ceil(__ddiv_rn(__dmul_rn(alpha, (double)B), (double)iprobes));
+  uint64_t k = (uint64_t)c;
+  if (kappa > 0 && k < (uint64_t)kappa) k = kappa;
+  if (k > B) k = B;
+  if (k) atomicMax(out, (unsigned)k);
+}
+
+int sig_bits(uint64_t v) {
+  int b = 0;
+  while (v) { ++b; v >>= 1; }
+  return b;
+}
+
+// Builds tables [t0, t0 + nt) and appends their kept ids.
+struct BuildScratch {
+  DevBuf proj, recA, recB, counts, bstart, kstart, hist, scanbuf, scanscratch, small, rechecks;
+};
+
+fpp_status build_tables(fpp_index* ix, int t0, int nt, BuildScratch& B, cudaStream_t st,
+                        std::vector<std::pair<uint32_t*, uint64_t>>& chunks,
+                        uint64_t& global_base) {
+  const int64_t n = ix->n;
+  const int D = ix->D;
+  const int64_t NB = nbuckets(D);
+  const int64_t nsk = nt * NB;
+  const int64_t ldp = round_up(2ll * nt * D, 4);
+  int64_t rows = std::max<int64_t>(128, (1ll << 28) / ldp);
+  rows = std::min<int64_t>(rows, n);
+  FPP_TRY(B.proj.ensure((size_t)rows * ldp * 4));
+  FPP_TRY(B.recA.ensure((size_t)nt * n * sizeof(Rec)));
+  FPP_TRY(B.recB.ensure((size_t)nt * n * sizeof(Rec)));
+  FPP_TRY(B.counts.ensure((size_t)nsk * 4));
+  FPP_TRY(B.bstart.ensure((size_t)(nsk + 1) * 8));
+  FPP_TRY(B.kstart.ensure((size_t)(nsk + 1) * 8));
+  const int64_t nrec = (int64_t)nt * n;
+  const int64_t he = radix_hist_elems(nrec);
+  FPP_TRY(B.hist.ensure((size_t)he * 4));
+  FPP_TRY(B.scanbuf.ensure((size_t)(he + 1) * 8));
+  FPP_TRY(B.scanscratch.ensure((size_t)scan_scratch_elems(std::max(he, nsk)) * 8));
+  FPP_TRY(B.small.ensure((size_t)(nt + 2) * 8));
+  FPP_CUDA(cudaMemsetAsync(B.counts.p, 0, (size_t)nsk * 4, st));
+
+  for (int64_t r0 = 0; r0 < n; r0 += rows) {
+    const int64_t rc = std::min<int64_t>(rows, n - r0);
+    FPP_TRY(gemm_f32_nt(ix->X + r0 * ix->dpad, ix->dpad, ix->R + (int64_t)2 * t0 * D * ix->dpad,
+                        ix->dpad, B.proj.as<float>(), ldp, rc, 2ll * nt * D, ix->dpad, st));
+    HashArgs h{};
+    h.P = B.proj.as<float>(); h.ldp = ldp; h.rows = rc; h.row0 = r0;
+    h.t0 = t0; h.nt = nt; h.D = D;
+    h.X = ix->X; h.ldx = ix->dpad; h.R = ix->R; h.ldr = ix->dpad; h.d = ix->d;
+    h.rmax = ix->rmax; h.xmax = ix->xmax; h.gamma = ix->gamma; h.n = n;
+    h.rec = B.recA.as<Rec>(); h.counts = B.counts.as<uint32_t>(); h.point_bucket = nullptr;
+    h.rechecks = B.rechecks.as<unsigned long long>();
+    FPP_TRY(launch_build_hash(h, st));
+  }
+  Rec* sorted = nullptr;
+  FPP_TRY(radix_sort_recs(B.recA.as<Rec>(), B.recB.as<Rec>(), nrec, 64, sig_bits(nsk - 1),
+                          B.hist.as<uint32_t>(), he, B.scanbuf.as<uint64_t>(),
+                          B.scanscratch.as<uint64_t>(), &sorted, st));
+  const KeepRule rule{ix->alpha, ix->iprobes, ix->kappa};
+  FPP_TRY(exclusive_scan_u32(B.counts.as<uint32_t>(), nsk, B.bstart.as<uint64_t>(), 0, rule,
+                             B.scanscratch.as<uint64_t>(), st));
+  FPP_TRY(exclusive_scan_u32(B.counts.as<uint32_t>(), nsk, B.kstart.as<uint64_t>(), 1, rule,
+                             B.scanscratch.as<uint64_t>(), st));
+  // per-table starts (relative to the chunk) and the chunk total
+  gather_u64_kernel<<<(unsigned)ceil_div(nt + 1, 128), 128, 0, st>>>(B.kstart.as<uint64_t>(), NB,
+                                                                    nt + 1, B.small.as<uint64_t>());
+  FPP_LAUNCHED();
+  std::vector<uint64_t> starts(nt + 1);
+  FPP_CUDA(cudaMemcpyAsync(starts.data(), B.small.p, (nt + 1) * 8, cudaMemcpyDeviceToHost, st));
+  unsigned* mk = reinterpret_cast<unsigned*>(B.small.as<uint64_t>() + nt + 1);
+  FPP_CUDA(cudaMemsetAsync(mk, 0, 4, st));
+  max_keep_kernel<<<(unsigned)ceil_div(nsk, 256), 256, 0, st>>>(B.counts.as<uint32_t>(), nsk,
+                                                                ix->alpha, ix->iprobes, ix->kappa, mk);
+  FPP_LAUNCHED();
+  unsigned hmk = 0;
+  FPP_CUDA(cudaMemcpyAsync(&hmk, mk, 4, cudaMemcpyDeviceToHost, st));
+  FPP_CUDA(cudaStreamSynchronize(st));
+  ix->max_bucket_kept = std::max(ix->max_bucket_kept, hmk);
+  const uint64_t total = starts[nt];
+  uint32_t* cids = nullptr;
+  FPP_CUDA(cudaMalloc(&cids, std::max<uint64_t>(total, 1) * 4));
+  chunks.emplace_back(cids, total);
+  FPP_TRY(launch_compact(sorted, nrec, B.bstart.as<uint64_t>(), B.kstart.as<uint64_t>(),
+                         B.counts.as<uint32_t>(), rule, cids, st));
+  FPP_TRY(launch_make_offsets(B.kstart.as<uint64_t>(), nt, NB, ix->offsets + (int64_t)t0 * (NB + 1), st));
+  for (int tl = 0; tl < nt; ++tl) ix->h_table_base[t0 + tl] = global_base + starts[tl];
+  global_base += total;
+  return FPP_OK;
+}
+
+fpp_status validate_params(int64_t n, int32_t d, const fpp_params* p) {
+  if (!p) { set_error("params is NULL"); return FPP_EINVAL; }
+  if (n < 1 || n >= (1ll << 32)) { set_error("n must be in [1, 2^32)"); return FPP_EINVAL; }
+  if (d < 1 || d > 16384) { set_error("d must be in [1, 16384]"); return FPP_EINVAL; }
+  if (p->L < 1 || p->L > 4096) { set_error("L must be in [1, 4096]"); return FPP_EINVAL; }
+  if (p->D < 1 || p->D > 1024) { set_error("D must be in [1, 1024]"); return FPP_EINVAL; }
+  if (!(p->alpha > 0.0 && p->alpha <= 1.0)) { set_error("alpha must be in (0, 1]"); return FPP_EINVAL; }
+  if (p->iprobes != 1) { set_error("iprobes > 1 is not supported yet"); return FPP_EINVAL; }
+  if (p->kappa < 0) { set_error("kappa must be >= 0"); return FPP_EINVAL; }
+  if (p->precision != FPP_FP32) { set_error("only FPP_FP32 is supported yet"); return FPP_EINVAL; }
+  return FPP_OK;
+}
+
+fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p, fpp_index** out) {
+  const auto wall0 = std::chrono::steady_clock::now();
+  if (!X || !out) { set_error("X and out must be non-NULL"); return FPP_EINVAL; }
+  FPP_TRY(validate_params(n, d, p));
+  cudaStream_t st = (cudaStream_t)p->stream;
+  fpp_index* ix = new fpp_index();
+  auto fail = [&](fpp_status s) { free_index_memory(ix); delete ix; return s; };
+  fpp_status s;
+  ix->n = n; ix->d = d; ix->dpad = (int)round_up(d, 4);
+  ix->L = p->L; ix->D = p->D; ix->iprobes = p->iprobes; ix->kappa = p->kappa;
+  ix->alpha = p->alpha; ix->precision = p->precision;
+  ix->gamma = gamma_fp32(ix->dpad);
+  if (cudaGetDevice(&ix->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ix->sm_count, cudaDevAttrMultiProcessorCount, ix->device) != cudaSuccess) {
+    set_error("no CUDA device");
+    delete ix;
+    return FPP_ECUDA;
+  }
+  const int L = p->L, D = p->D;
+  const int64_t rrows = 2ll * L * D;
+  // random vectors (host copy needed for the row norms)
+  std::vector<float> hR((size_t)rrows * d);
+  if (p->R) {
+    if (cudaMemcpy(hR.data(), p->R, hR.size() * 4, cudaMemcpyDefault) != cudaSuccess) {
+      set_error("copying params->R failed");
+      return fail(FPP_EINVAL);
+    }
+  } else {
+    generate_rotations(p->seed, L, D, d, hR.data());
+  }
+  std::vector<float> hrmax(2 * L, 0.f);
+  for (int64_t r = 0; r < rrows; ++r) {
+    double s = 0.0;
+    for (int c = 0; c < d; ++c) s += (double)hR[r * d + c] * hR[r * d + c];
+    const int tj = (int)(r / D);
+    hrmax[tj] = std::max(hrmax[tj], (float)(std::sqrt(s) * (1.0 + 1e-6)));
+  }
+  if ((s = to_device_padded(X, n, d, ix->dpad, &ix->X, st, &ix->device_bytes)) != FPP_OK) return fail(s);
+  if ((s = to_device_padded(hR.data(), rrows, d, ix->dpad, &ix->R, st, &ix->device_bytes)) != FPP_OK)
+    return fail(s);
+  if (cudaMalloc(&ix->rmax, 2 * L * 4) != cudaSuccess) { set_error("cudaMalloc rmax"); return fail(FPP_ENOMEM); }
+  if (cudaMemcpyAsync(ix->rmax, hrmax.data(), 2 * L * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    set_error("copy rmax");
+    return fail(FPP_ECUDA);
+  }
+  {
+    float* dxm = nullptr;
+    if (cudaMalloc(&dxm, 4) != cudaSuccess) { set_error("cudaMalloc"); return fail(FPP_ENOMEM); }
+    s = launch_row_norm_max(ix->X, n, ix->dpad, d, dxm, st);
+    if (s == FPP_OK && cudaMemcpyAsync(&ix->xmax, dxm, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) s = FPP_ECUDA;
+    if (s == FPP_OK && cudaStreamSynchronize(st) != cudaSuccess) s = FPP_ECUDA;
+    cudaFree(dxm);
+    if (s != FPP_OK) return fail(s);
+  }
+  const int64_t NB = nbuckets(D);
+  if (cudaMalloc(&ix->offsets, (size_t)L * (NB + 1) * 4) != cudaSuccess) {
+    set_error("cudaMalloc offsets");
+    return fail(FPP_ENOMEM);
+  }
+  ix->device_bytes += (uint64_t)L * (NB + 1) * 4;
+  ix->h_table_base.assign(L, 0);
+
+  const int64_t rcap = 1ll << 28;
+  int nt_chunk = (int)std::max<int64_t>(1, rcap / n);
+  nt_chunk = (int)std::min<int64_t>(nt_chunk, (int64_t)(0xFFFFFFFFll / NB));
+  nt_chunk = std::max(1, std::min(nt_chunk, L));
+  BuildScratch B;
+  std::vector<std::pair<uint32_t*, uint64_t>> chunks;
+  uint64_t base = 0;
+  auto cleanup = [&]() {
+    for (DevBuf* b : {&B.proj, &B.recA, &B.recB, &B.counts, &B.bstart, &B.kstart, &B.hist, &B.scanbuf,
+                      &B.scanscratch, &B.small, &B.rechecks})
+      b->release();
+    for (auto& c : chunks) cudaFree(c.first);
+  };
+  if ((s = B.rechecks.ensure(8, true, st)) != FPP_OK) { cleanup(); return fail(s); }
+  for (int t0 = 0; t0 < L; t0 += nt_chunk) {
+    const int nt = std::min(nt_chunk, L - t0);
+    if ((s = build_tables(ix, t0, nt, B, st, chunks, base)) != FPP_OK) { cleanup(); return fail(s); }
+  }
+  ix->kept_total = base;
+  if (cudaMalloc(&ix->ids, std::max<uint64_t>(base, 1) * 4) != cudaSuccess) {
+    set_error("cudaMalloc ids");
+    cleanup();
+    return fail(FPP_ENOMEM);
+  }
+  ix->device_bytes += base * 4;
+  uint64_t at = 0;
+  for (auto& c : chunks) {
+    if (c.second && cudaMemcpyAsync(ix->ids + at, c.first, c.second * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+      set_error("concatenating ids");
+      cleanup();
+      return fail(FPP_ECUDA);
+    }
+    at += c.second;
+  }
+  if (cudaMalloc(&ix->table_base, L * 8) != cudaSuccess ||
+      cudaMemcpyAsync(ix->table_base, ix->h_table_base.data(), L * 8, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    set_error("table_base");
+    cleanup();
+    return fail(FPP_ECUDA);
+  }
+  unsigned long long rech = 0;
+  cudaMemcpyAsync(&rech, B.rechecks.p, 8, cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error(std::string("build: ") + cudaGetErrorString(cudaGetLastError()));
+    cleanup();
+    return fail(FPP_ECUDA);
+  }
+  ix->build_rechecks = rech;
+  cleanup();
+  ix->build_ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+  *out = ix;
+  return FPP_OK;
+}
+
+// ------------------------------------------------------------------ search
+
+struct SearchPlan {
+  int64_t m;
+  int kmax, pmax, tb, te;
+  const int32_t* kpq;   // user arrays (host or device) or NULL
+  const int32_t* ppq;
+  bool kpq_dev, ppq_dev;
+  int k, probes;
+};
+
+fpp_status validate_search(const fpp_index* ix, const float* Q, int64_t m, const fpp_search_opts* o,
+                           int64_t* ids, float* scores, SearchPlan& pl) {
+  if (!ix) { set_error("index is NULL"); return FPP_EINVAL; }
+  if (!o) { set_error("opts is NULL"); return FPP_EINVAL; }
+  if (m < 0) { set_error("m must be >= 0"); return FPP_EINVAL; }
+  if (m > 0 && (!Q || !ids || !scores)) { set_error("Q, ids and scores must be non-NULL"); return FPP_EINVAL; }
+  pl.m = m;
+  pl.tb = o->table_begin;
+  pl.te = (o->table_end == 0) ? ix->L : o->table_end;
+  if (pl.tb < 0 || pl.te > ix->L || pl.tb >= pl.te) { set_error("bad table range"); return FPP_EINVAL; }
+  const int64_t NB = nbuckets(ix->D);
+  const int pcap = (int)std::min<int64_t>(NB, 128);
+  pl.kpq = o->k_per_query;
+  pl.ppq = o->probes_per_query;
+  pl.kpq_dev = is_device_ptr(pl.kpq);
+  pl.ppq_dev = is_device_ptr(pl.ppq);
+  pl.k = o->k;
+  pl.probes = o->probes;
+  int kmax_seen = pl.kpq ? 0 : pl.k, pmax_seen = pl.ppq ? 0 : pl.probes;
+  auto check_arr = [&](const int32_t* a, int lo, int hi, int& mx, const char* what) -> fpp_status {
+    std::vector<int32_t> h(m);
+    if (m && cudaMemcpy(h.data(), a, m * 4, cudaMemcpyDefault) != cudaSuccess) {
+      set_error(std::string("reading ") + what);
+      return FPP_EINVAL;
+    }
+    for (int64_t i = 0; i < m; ++i) {
+      if (h[i] < lo || h[i] > hi) {
+        set_error(std::string(what) + " out of range at query " + std::to_string(i));
+        return FPP_EINVAL;
+      }
+      mx = std::max(mx, (int)h[i]);
+    }
+    return FPP_OK;
+  };
+  if (pl.kpq) FPP_TRY(check_arr(pl.kpq, 1, 256, kmax_seen, "k_per_query"));
+  else if (pl.k < 1 || pl.k > 256) { set_error("k must be in [1, 256]"); return FPP_EINVAL; }
+  if (pl.ppq) FPP_TRY(check_arr(pl.ppq, 1, pcap, pmax_seen, "probes_per_query"));
+  else if (pl.probes < 1 || pl.probes > pcap) {
+    set_error("probes must be in [1, min(4D^2, 128)]");
+    return FPP_EINVAL;
+  }
+  pl.kmax = o->k_max > 0 ? o->k_max : kmax_seen;
+  if (pl.kmax < kmax_seen || pl.kmax > 256) { set_error("k_max must cover every k and be <= 256"); return FPP_EINVAL; }
+  pl.pmax = std::max(1, pmax_seen);
+  return FPP_OK;
+}
+
+// Runs projection + probe ranking (and, unless probes_only, gather/score) for
+// queries [q0, q0 + mc).
+fpp_status search_chunk(fpp_index* ix, const float* Q, int64_t q0, int64_t mc, const SearchPlan& pl,
+                        int64_t* ids_dev, float* scores_dev, cudaStream_t st, bool probes_only,
+                        cudaEvent_t* ev) {
+  Workspace& ws = ix->ws;
+  const int nt = pl.te - pl.tb;
+  const int64_t ldp = round_up(2ll * nt * ix->D, 4);
+  // queries, padded
+  FPP_CUDA(cudaMemcpy2DAsync(ws.qpad.p, ix->dpad * 4, Q + q0 * ix->d, ix->d * 4, ix->d * 4, mc,
+                             cudaMemcpyDefault, st));
+  const int32_t* kpq = nullptr;
+  const int32_t* ppq = nullptr;
+  if (pl.kpq) {
+    if (pl.kpq_dev) kpq = pl.kpq + q0;
+    else {
+      FPP_CUDA(cudaMemcpyAsync(ws.kpq.p, pl.kpq + q0, mc * 4, cudaMemcpyHostToDevice, st));
+      kpq = ws.kpq.as<int32_t>();
+    }
+  }
+  if (pl.ppq) {
+    if (pl.ppq_dev) ppq = pl.ppq + q0;
+    else {
+      FPP_CUDA(cudaMemcpyAsync(ws.ppq.p, pl.ppq + q0, mc * 4, cudaMemcpyHostToDevice, st));
+      ppq = ws.ppq.as<int32_t>();
+    }
+  }
+  if (ev) FPP_CUDA(cudaEventRecord(ev[0], st));
+  FPP_TRY(gemm_f32_nt(ws.qpad.as<float>(), ix->dpad, ix->R + (int64_t)2 * pl.tb * ix->D * ix->dpad,
+                      ix->dpad, ws.proj.as<float>(), ldp, mc, 2ll * nt * ix->D, ix->dpad, st));
+  if (ev) FPP_CUDA(cudaEventRecord(ev[1], st));
+  ProbeArgs pa{};
+  pa.P = ws.proj.as<float>(); pa.ldp = ldp; pa.mq = mc;
+  pa.Q = ws.qpad.as<float>(); pa.ldq = ix->dpad;
+  pa.R = ix->R; pa.ldr = ix->dpad; pa.d = ix->d; pa.D = ix->D; pa.tb = pl.tb; pa.nt = nt;
+  pa.rmax = ix->rmax; pa.gamma = ix->gamma;
+  pa.probes_pq = ppq; pa.probes = pl.pmax;
+  pa.offsets = ix->offsets;
+  pa.out = ws.probes.as<uint32_t>();
+  pa.entries = nullptr;
+  pa.rechecks = ws.stats.as<unsigned long long>() + 6;
+  FPP_TRY(launch_probe(pa, st));
+  if (ev) FPP_CUDA(cudaEventRecord(ev[2], st));
+  if (probes_only) return FPP_OK;
+  FPP_CUDA(cudaMemsetAsync(ws.stats.as<unsigned long long>() + 4, 0, 8, st));
+  GatherArgs ga{};
+  ga.probes = ws.probes.as<uint32_t>(); ga.pstride = pl.pmax; ga.mq = mc;
+  ga.tb = pl.tb; ga.nt = nt; ga.D = ix->D;
+  ga.probes_pq = ppq; ga.k_pq = kpq; ga.k = pl.k; ga.kmax = pl.kmax;
+  ga.offsets = ix->offsets; ga.table_base = ix->table_base; ga.ids = ix->ids;
+  ga.X = ix->X; ga.ldx = ix->dpad; ga.d = ix->d; ga.n = ix->n;
+  ga.Q = ws.qpad.as<float>(); ga.ldq = ix->dpad;
+  ga.xmax = ix->xmax; ga.gamma = ix->gamma;
+  ga.bitmaps = ws.bitmaps.as<uint32_t>(); ga.bitmap_words = ws.bitmap_words; ga.slots = ws.slots;
+  ga.out_ids = ids_dev; ga.out_scores = scores_dev;
+  ga.stats = ws.stats.as<unsigned long long>();
+  FPP_TRY(launch_gather_score(ga, st));
+  if (ev) FPP_CUDA(cudaEventRecord(ev[3], st));
+  return FPP_OK;
+}
+
+int64_t chunk_rows(const fpp_index* ix, int nt) {
+  const int64_t ldp = round_up(2ll * nt * ix->D, 4);
+  int64_t mc = (1ll << 28) / ldp;
+  mc = std::max<int64_t>(128, std::min<int64_t>(mc, 16384));
+  return mc;
+}
+
+fpp_status prepare_workspace(fpp_index* ix, const SearchPlan& pl, int64_t mc, bool host_out,
+                             cudaStream_t st) {
+  Workspace& ws = ix->ws;
+  const int nt = pl.te - pl.tb;
+  const int64_t ldp = round_up(2ll * nt * ix->D, 4);
+  const bool qz = ws.qpad.bytes < (size_t)mc * ix->dpad * 4;
+  FPP_TRY(ws.qpad.ensure((size_t)mc * ix->dpad * 4, false, st));
+  if (qz && ix->dpad != ix->d) FPP_CUDA(cudaMemsetAsync(ws.qpad.p, 0, ws.qpad.bytes, st));
+  FPP_TRY(ws.proj.ensure((size_t)mc * ldp * 4, false, st));
+  FPP_TRY(ws.probes.ensure((size_t)mc * nt * pl.pmax * 4, false, st));
+  FPP_TRY(ws.kpq.ensure((size_t)mc * 4, false, st));
+  FPP_TRY(ws.ppq.ensure((size_t)mc * 4, false, st));
+  FPP_TRY(ws.stats.ensure(16 * 8, true, st));
+  if (host_out) {
+    FPP_TRY(ws.out_ids.ensure((size_t)mc * pl.kmax * 8, false, st));
+    FPP_TRY(ws.out_scores.ensure((size_t)mc * pl.kmax * 4, false, st));
+  }
+  const int slots = gather_slots(ix->sm_count);
+  const int64_t words = ceil_div(ix->n, 32);
+  if (ws.slots != slots || ws.bitmap_words != words || !ws.bitmaps.p) {
+    ws.bitmaps.release();
+    FPP_TRY(ws.bitmaps.ensure((size_t)slots * words * 4, true, st));
+    ws.slots = slots;
+    ws.bitmap_words = words;
+  }
+  return FPP_OK;
+}
+
+fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fpp_search_opts* o,
+                       int64_t* ids, float* scores, fpp_search_stats* stats) {
+  SearchPlan pl{};
+  FPP_TRY(validate_search(cix, Q, m, o, ids, scores, pl));
+  fpp_index* ix = const_cast<fpp_index*>(cix);
+  std::lock_guard<std::mutex> lock(ix->mu);
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (m == 0) return FPP_OK;
+  cudaStream_t st = (cudaStream_t)o->stream;
+  const bool dev_out = is_device_ptr(ids) && is_device_ptr(scores);
+  const int nt = pl.te - pl.tb;
+  const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt), m);
+  FPP_TRY(prepare_workspace(ix, pl, mc, !dev_out, st));
+  FPP_CUDA(cudaMemsetAsync(ix->ws.stats.p, 0, 16 * 8, st));
+  cudaEvent_t ev[5] = {};
+  bool timing = stats != nullptr;
+  if (timing)
+    for (auto& e : ev) FPP_CUDA(cudaEventCreate(&e));
+  float ms[3] = {0, 0, 0};
+  for (int64_t q0 = 0; q0 < m; q0 += mc) {
+    const int64_t c = std::min<int64_t>(mc, m - q0);
+    int64_t* oid = dev_out ? ids + q0 * pl.kmax : ix->ws.out_ids.as<int64_t>();
+    float* osc = dev_out ? scores + q0 * pl.kmax : ix->ws.out_scores.as<float>();
+    FPP_TRY(search_chunk(ix, Q, q0, c, pl, oid, osc, st, false, timing ? ev : nullptr));
+    if (!dev_out) {
+      FPP_CUDA(cudaMemcpyAsync(ids + q0 * pl.kmax, oid, c * pl.kmax * 8, cudaMemcpyDeviceToHost, st));
+      FPP_CUDA(cudaMemcpyAsync(scores + q0 * pl.kmax, osc, c * pl.kmax * 4, cudaMemcpyDeviceToHost, st));
+    }
+    if (timing) {
+      FPP_CUDA(cudaEventSynchronize(ev[3]));
+      float a, b, cc;
+      cudaEventElapsedTime(&a, ev[0], ev[1]);
+      cudaEventElapsedTime(&b, ev[1], ev[2]);
+      cudaEventElapsedTime(&cc, ev[2], ev[3]);
+      ms[0] += a; ms[1] += b; ms[2] += cc;
+    }
+  }
+  const bool need_sync = !dev_out || o->stream == nullptr || stats != nullptr;
+  unsigned long long hs[8] = {0};
+  if (need_sync) {
+    FPP_CUDA(cudaMemcpyAsync(hs, ix->ws.stats.p, 8 * 8, cudaMemcpyDeviceToHost, st));
+    FPP_CUDA(cudaStreamSynchronize(st));
+    if (hs[5]) {
+      set_error("search: top-k re-check capacity exceeded");
+      return FPP_EINTERNAL;
+    }
+  }
+  if (timing)
+    for (auto& e : ev) cudaEventDestroy(e);
+  if (stats) {
+    stats->queries = m;
+    stats->entries = hs[0];
+    stats->unique = hs[1];
+    stats->topk_rechecks = hs[2];
+    stats->probes = hs[3];
+    stats->probe_rechecks = hs[6];
+    stats->ms_project = ms[0];
+    stats->ms_probe = ms[1];
+    stats->ms_gather_score = ms[2];
+    stats->ms_total = ms[0] + ms[1] + ms[2];
+  }
+  return FPP_OK;
+}
+
+}  // namespace fpp_api
+
+using namespace fpp_api;
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+void fpp_default_params(fpp_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->L = 10;
+  p->D = 64;
+  p->iprobes = 1;
+  p->kappa = 0;
+  p->alpha = 0.1;
+  p->seed = 0;
+  p->R = nullptr;
+  p->precision = FPP_FP32;
+  p->stream = nullptr;
+}
+
+void fpp_default_search_opts(fpp_search_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->k = 10;
+  o->probes = 1;
+}
+
+const char* fpp_last_error(void) { return g_err.c_str(); }
+
+uint64_t fpp_launch_count(void) { return g_launches.load(); }
+
+uint64_t fpp_keep_count(uint64_t B, double alpha, int32_t iprobes, int32_t kappa) {
+  if (iprobes < 1) iprobes = 1;
+  const double c = std::ceil((alpha * (double)B) / (double)iprobes);
+  uint64_t k = (uint64_t)c;
+  if (kappa > 0 && k < (uint64_t)kappa) k = (uint64_t)kappa;
+  return k > B ? B : k;
+}
+
+fpp_status fpp_rotations(uint64_t seed, int32_t L, int32_t D, int32_t d, float* R) {
+  g_err.clear();
+  if (!R || L < 1 || D < 1 || d < 1) {
+    set_error("fpp_rotations: L, D, d must be >= 1 and R non-NULL");
+    return FPP_EINVAL;
+  }
+  generate_rotations(seed, L, D, d, R);
+  return FPP_OK;
+}
+
+fpp_status fpp_build(const float* X, int64_t n, int32_t d, const fpp_params* p, fpp_index** out) {
+  g_err.clear();
+  try {
+    return build_impl(X, n, d, p, out);
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return FPP_ENOMEM;
+  } catch (...) {
+    set_error("unexpected exception in fpp_build");
+    return FPP_EINTERNAL;
+  }
+}
+
+fpp_status fpp_search_ex(const fpp_index* ix, const float* Q, int64_t m, const fpp_search_opts* opts,
+                         int64_t* ids, float* scores, fpp_search_stats* stats) {
+  g_err.clear();
+  try {
+    return search_impl(ix, Q, m, opts, ids, scores, stats);
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return FPP_ENOMEM;
+  } catch (...) {
+    set_error("unexpected exception in fpp_search_ex");
+    return FPP_EINTERNAL;
+  }
+}
+
+fpp_status fpp_search(const fpp_index* ix, const float* Q, int64_t m, int32_t k, int32_t probes,
+                      int64_t* ids, float* scores) {
+  fpp_search_opts o;
+  fpp_default_search_opts(&o);
+  o.k = k;
+  o.probes = probes;
+  o.k_max = k;
+  return fpp_search_ex(ix, Q, m, &o, ids, scores, nullptr);
+}
+
+void fpp_free(fpp_index* ix) {
+  if (!ix) return;
+  free_index_memory(ix);
+  delete ix;
+}
+
+fpp_status fpp_index_get_info(const fpp_index* ix, fpp_index_info* info) {
+  g_err.clear();
+  if (!ix || !info) { set_error("NULL argument"); return FPP_EINVAL; }
+  info->n = ix->n; info->d = ix->d; info->L = ix->L; info->D = ix->D;
+  info->iprobes = ix->iprobes; info->kappa = ix->kappa; info->precision = ix->precision;
+  info->alpha = ix->alpha; info->kept_total = ix->kept_total;
+  info->max_bucket_kept = ix->max_bucket_kept; info->device_bytes = ix->device_bytes;
+  info->build_ms = ix->build_ms;
+  return FPP_OK;
+}
+
+fpp_status fpp_debug_point_buckets(const fpp_index* cix, int32_t t, uint32_t* out) {
+  g_err.clear();
+  if (!cix || !out) { set_error("NULL argument"); return FPP_EINVAL; }
+  if (t < 0 || t >= cix->L) { set_error("table out of range"); return FPP_EINVAL; }
+  if (cix->iprobes != 1) { set_error("point buckets need iprobes = 1"); return FPP_EINVAL; }
+  fpp_index* ix = const_cast<fpp_index*>(cix);
+  std::lock_guard<std::mutex> lock(ix->mu);
+  cudaStream_t st = 0;
+  const int64_t ldp = round_up(2ll * ix->D, 4);
+  const int64_t rows = std::min<int64_t>(ix->n, std::max<int64_t>(128, (1ll << 27) / ldp));
+  DevBuf proj, pb;
+  auto done = [&](fpp_status s) { proj.release(); pb.release(); return s; };
+  fpp_status s;
+  if ((s = proj.ensure((size_t)rows * ldp * 4)) != FPP_OK) return done(s);
+  if ((s = pb.ensure((size_t)ix->n * 4)) != FPP_OK) return done(s);
+  for (int64_t r0 = 0; r0 < ix->n; r0 += rows) {
+    const int64_t rc = std::min<int64_t>(rows, ix->n - r0);
+    if ((s = gemm_f32_nt(ix->X + r0 * ix->dpad, ix->dpad, ix->R + (int64_t)2 * t * ix->D * ix->dpad,
+                         ix->dpad, proj.as<float>(), ldp, rc, 2ll * ix->D, ix->dpad, st)) != FPP_OK)
+      return done(s);
+    HashArgs h{};
+    h.P = proj.as<float>(); h.ldp = ldp; h.rows = rc; h.row0 = r0; h.t0 = t; h.nt = 1; h.D = ix->D;
+    h.X = ix->X; h.ldx = ix->dpad; h.R = ix->R; h.ldr = ix->dpad; h.d = ix->d;
+    h.rmax = ix->rmax; h.xmax = ix->xmax; h.gamma = ix->gamma; h.n = ix->n;
+    h.point_bucket = pb.as<uint32_t>() + r0;
+    if ((s = launch_build_hash(h, st)) != FPP_OK) return done(s);
+  }
+  if (cudaMemcpy(out, pb.p, ix->n * 4, cudaMemcpyDefault) != cudaSuccess) {
+    set_error("copy point buckets");
+    return done(FPP_ECUDA);
+  }
+  return done(FPP_OK);
+}
+
+fpp_status fpp_debug_table(const fpp_index* ix, int32_t t, uint32_t* offsets, uint32_t* ids) {
+  g_err.clear();
+  if (!ix || !offsets) { set_error("NULL argument"); return FPP_EINVAL; }
+  if (t < 0 || t >= ix->L) { set_error("table out of range"); return FPP_EINVAL; }
+  const int64_t NB = nbuckets(ix->D);
+  FPP_CUDA(cudaMemcpy(offsets, ix->offsets + (int64_t)t * (NB + 1), (NB + 1) * 4, cudaMemcpyDefault));
+  if (ids) {
+    uint32_t cnt = 0;
+    FPP_CUDA(cudaMemcpy(&cnt, ix->offsets + (int64_t)t * (NB + 1) + NB, 4, cudaMemcpyDeviceToHost));
+    if (cnt) FPP_CUDA(cudaMemcpy(ids, ix->ids + ix->h_table_base[t], (size_t)cnt * 4, cudaMemcpyDefault));
+  }
+  return FPP_OK;
+}
+
+fpp_status fpp_debug_probes(const fpp_index* cix, const float* Q, int64_t m, int32_t probes,
+                            int32_t table_begin, int32_t table_end, uint32_t* out) {
+  g_err.clear();
+  fpp_search_opts o;
+  fpp_default_search_opts(&o);
+  o.probes = probes;
+  o.k = 1;
+  o.table_begin = table_begin;
+  o.table_end = table_end;
+  SearchPlan pl{};
+  int64_t dummy_i = 0;
+  float dummy_s = 0;
+  FPP_TRY(validate_search(cix, Q, m, &o, &dummy_i, &dummy_s, pl));
+  if (!out && m) { set_error("out is NULL"); return FPP_EINVAL; }
+  fpp_index* ix = const_cast<fpp_index*>(cix);
+  std::lock_guard<std::mutex> lock(ix->mu);
+  if (m == 0) return FPP_OK;
+  const int nt = pl.te - pl.tb;
+  const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt), m);
+  FPP_TRY(prepare_workspace(ix, pl, mc, false, 0));
+  for (int64_t q0 = 0; q0 < m; q0 += mc) {
+    const int64_t c = std::min<int64_t>(mc, m - q0);
+    FPP_TRY(search_chunk(ix, Q, q0, c, pl, nullptr, nullptr, 0, true, nullptr));
+    FPP_CUDA(cudaMemcpy(out + q0 * nt * probes, ix->ws.probes.p, (size_t)c * nt * probes * 4,
+                        cudaMemcpyDefault));
+  }
+  return FPP_OK;
+}
+
+fpp_status fpp_bruteforce(const float* X, int64_t n, int32_t d, const float* Q, int64_t m, int32_t k,
+                          int64_t* ids, float* scores, void* stream) {
+  g_err.clear();
+  if (!X || n < 1 || n >= (1ll << 32) || d < 1 || m < 0 || k < 1 || k > 256 ||
+      (m > 0 && (!Q || !ids || !scores))) {
+    set_error("fpp_bruteforce: bad arguments");
+    return FPP_EINVAL;
+  }
+  if (m == 0) return FPP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int dpad = (int)round_up(d, 4);
+  float* dX = nullptr;
+  float* dQ = nullptr;
+  DevBuf S, oi, os, misc, xm;
+  auto done = [&](fpp_status s) {
+    cudaStreamSynchronize(st);
+    cudaFree(dX); cudaFree(dQ);
+    S.release(); oi.release(); os.release(); misc.release(); xm.release();
+    return s;
+  };
+  fpp_status s;
+  if ((s = to_device_padded(X, n, d, dpad, &dX, st, nullptr)) != FPP_OK) return done(s);
+  if ((s = to_device_padded(Q, m, d, dpad, &dQ, st, nullptr)) != FPP_OK) return done(s);
+  if ((s = xm.ensure(4)) != FPP_OK) return done(s);
+  if ((s = launch_row_norm_max(dX, n, dpad, d, xm.as<float>(), st)) != FPP_OK) return done(s);
+  float xmax = 0.f;
+  if (cudaMemcpyAsync(&xmax, xm.p, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error("bruteforce: norm");
+    return done(FPP_ECUDA);
+  }
+  const int64_t lds = round_up(n, 4);
+  int64_t mc = std::max<int64_t>(1, std::min<int64_t>(m, (1ll << 28) / lds));
+  if ((s = S.ensure((size_t)mc * lds * 4)) != FPP_OK) return done(s);
+  if ((s = oi.ensure((size_t)mc * k * 8)) != FPP_OK) return done(s);
+  if ((s = os.ensure((size_t)mc * k * 4)) != FPP_OK) return done(s);
+  if ((s = misc.ensure(16, true, st)) != FPP_OK) return done(s);
+  const double gamma = gamma_fp32(dpad);
+  for (int64_t q0 = 0; q0 < m; q0 += mc) {
+    const int64_t c = std::min<int64_t>(mc, m - q0);
+    if ((s = gemm_f32_nt(dQ + q0 * dpad, dpad, dX, dpad, S.as<float>(), lds, c, n, dpad, st)) != FPP_OK)
+      return done(s);
+    if ((s = launch_topk_dense(S.as<float>(), lds, c, n, k, dQ + q0 * dpad, dpad, dX, dpad, d, xmax,
+                               gamma, oi.as<int64_t>(), os.as<float>(), k,
+                               misc.as<unsigned long long>(), st)) != FPP_OK)
+      return done(s);
+    if (cudaMemcpyAsync(ids + q0 * k, oi.p, c * k * 8, cudaMemcpyDefault, st) != cudaSuccess ||
+        cudaMemcpyAsync(scores + q0 * k, os.p, c * k * 4, cudaMemcpyDefault, st) != cudaSuccess) {
+      set_error("bruteforce: copy out");
+      return done(FPP_ECUDA);
+    }
+  }
+  unsigned long long hm[2] = {0, 0};
+  if (cudaMemcpyAsync(hm, misc.p, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error(std::string("bruteforce: ") + cudaGetErrorString(cudaGetLastError()));
+    return done(FPP_ECUDA);
+  }
+  if (hm[1]) {
+    set_error("bruteforce: top-k re-check capacity exceeded");
+    return done(FPP_EINTERNAL);
+  }
+  return done(FPP_OK);
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// Shared device/host helpers of libfpp.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <cstdio>
+#include <string>
+
+#include "../../include/fpp.h"
+
+namespace fpp {
+
+// ---------------------------------------------------------------- errors
+
+void set_error(const std::string& msg);
+std::atomic<uint64_t>& launch_counter();
+
+struct Status {
+  fpp_status code = FPP_OK;
+  bool ok() const { return code == FPP_OK; }
+};
+
+#define FPP_CUDA(call)                                                        \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      ::fpp::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));   \
+      return e_ == cudaErrorMemoryAllocation ? FPP_ENOMEM : FPP_ECUDA;        \
+    }                                                                         \
+  } while (0)
+
+#define FPP_LAUNCHED()                                                        \
+  do {                                                                        \
+    ::fpp::launch_counter().fetch_add(1, std::memory_order_relaxed);          \
+    cudaError_t e_ = cudaGetLastError();                                      \
+    if (e_ != cudaSuccess) {                                                  \
+      ::fpp::set_error(std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+      return FPP_ECUDA;                                                       \
+    }                                                                         \
+  } while (0)
+
+#define FPP_TRY(expr)                                                         \
+  do {                                                                        \
+    fpp_status s_ = (expr);                                                   \
+    if (s_ != FPP_OK) return s_;                                              \
+  } while (0)
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+// ---------------------------------------------------------------- error bounds
+//
+// gamma_n = n u / (1 - n u) bounds the relative error of any n-term FP32
+// dot product evaluated with rounding to nearest, whatever the order of the
+// additions (Higham, "Accuracy and Stability of Numerical Algorithms", 3.1):
+// |fl(x^T y) - x^T y| <= gamma_n sum |x_i y_i| <= gamma_n ||x|| ||y||.
+inline double gamma_fp32(int64_t n) {
+  const double u = 5.9604644775390625e-08;  // 2^-24
+  return (n * u) / (1.0 - n * u);
+}
+
+// ---------------------------------------------------------------- device math
+
+#ifdef __CUDACC__
+
+// Error-free transformations (Knuth's TwoSum; TwoProduct with a fused
+// multiply-add).  Explicit _rn intrinsics keep the compiler from fusing or
+// reassociating them.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// A float-float value hi + lo.
+struct FF {
+  float hi, lo;
+};
+
+// Accumulates a * b into (p, s) as in the compensated dot product "Dot2" of
+// Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J. Sci.
+// Comput. 26(6), 2005, Algorithm 5.3): p carries the running sum, s the
+// running sum of the rounding errors.  The result p + s is as accurate as a
+// dot product computed in twice the working precision.
+__device__ __forceinline__ void dot2_step(float a, float b, float& p, float& s) {
+  float h, r, q;
+  two_prod(a, b, h, r);
+  two_sum(p, h, p, q);
+  s = __fadd_rn(s, __fadd_rn(q, r));
+}
+
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  float s, e;
+  two_sum(x.hi, y.hi, s, e);
+  return FF{s, __fadd_rn(__fadd_rn(x.lo, y.lo), e)};
+}
+
+__device__ __forceinline__ double ff_value(FF x) { return (double)x.hi + (double)x.lo; }
+
+// Warp-cooperative compensated dot product of two length-n FP32 vectors;
+// every lane returns the result.  Lanes take strided elements; the 32 partial
+// float-float sums are combined with error-free additions.
+__device__ __forceinline__ double warp_dot2(const float* __restrict__ a,
+                                            const float* __restrict__ b, int n) {
+  const int lane = threadIdx.x & 31;
+  float p = 0.f, s = 0.f;
+  for (int i = lane; i < n; i += 32) dot2_step(a[i], b[i], p, s);
+  FF v{p, s};
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    FF w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = ff_add(v, w);
+  }
+  return ff_value(v);
+}
+
+// Single-thread compensated dot product.
+__device__ __forceinline__ double thread_dot2(const float* __restrict__ a,
+                                              const float* __restrict__ b, int n) {
+  float p = 0.f, s = 0.f;
+  for (int i = 0; i < n; ++i) dot2_step(a[i], b[i], p, s);
+  return ff_value(FF{p, s});
+}
+
+// Order-preserving map of a float to uint32 (larger float -> larger uint).
+__device__ __forceinline__ uint32_t float_key(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+#endif  // __CUDACC__
+
+}  // namespace fpp

@@ -1,0 +1,134 @@
+// Internal launchers of libfpp (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fpp.h"
+
+namespace fpp {
+
+// One bucket entry of a table during the build: sorted by (sk asc, key asc,
+// id asc) where key = ~bits(filter score) so that ascending key order is
+// descending filter score.  sk = table-in-chunk * 4D^2 + bucket.
+struct __align__(16) Rec {
+  uint64_t key;
+  uint32_t sk;
+  uint32_t id;
+};
+
+// Projection GEMM (gemm_f32.cu).
+fpp_status gemm_f32_nt(const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
+                       int64_t ldc, int64_t M, int64_t N, int K, cudaStream_t st);
+
+// Build (build_kernels.cu).
+struct HashArgs {
+  const float* P;        // projections [rows][ldp] for tables [t0, t0 + nt)
+  int64_t ldp;
+  int64_t rows;          // points in this chunk
+  int64_t row0;          // id of the chunk's first point
+  int t0, nt, D;
+  const float* X;        // [n][ldx] padded points
+  int64_t ldx;
+  const float* R;        // [2 L D][ldr] padded random vectors
+  int64_t ldr;
+  int d;                 // true dimension (padded columns are zero)
+  const float* rmax;     // [2L] max row norm per (table, hash), inflated
+  float xmax;            // max point norm, inflated
+  double gamma;          // gamma_K of the projection GEMM
+  int64_t n;             // points in the index (record stride per table)
+  Rec* rec;              // [nt][n] records, or NULL
+  uint32_t* counts;      // [nt][4D^2] bucket sizes, or NULL
+  uint32_t* point_bucket;// [rows] (nt must be 1), or NULL
+  unsigned long long* rechecks;  // counter of FP64-accurate re-decisions, or NULL
+};
+fpp_status launch_build_hash(const HashArgs& a, cudaStream_t st);
+
+fpp_status launch_row_norm_max(const float* X, int64_t n, int64_t ldx, int d, float* out,
+                               cudaStream_t st);
+
+// Exclusive scan of n values into out[0..n] (out[n] = total).  mode 0: the
+// values are in[i]; mode 1: the values are keep_count(in[i]).
+struct KeepRule {
+  double alpha;
+  int iprobes;
+  int kappa;
+};
+fpp_status exclusive_scan_u32(const uint32_t* in, int64_t n, uint64_t* out, int mode,
+                              KeepRule rule, uint64_t* scratch, cudaStream_t st);
+int64_t scan_scratch_elems(int64_t n);
+
+// Stable LSD radix sort of records by (sk, key) with 8-bit digits;
+// key_bits / sk_bits give the number of significant low bits of each field.
+fpp_status radix_sort_recs(Rec* a, Rec* b, int64_t n, int key_bits, int sk_bits,
+                           uint32_t* hist, int64_t hist_elems, uint64_t* scan_buf,
+                           uint64_t* scan_scratch, Rec** sorted, cudaStream_t st);
+int64_t radix_hist_elems(int64_t n);
+
+// Kept-CSR compaction: records sorted by (sk, key, id); bstart = exclusive
+// scan of counts, kstart = exclusive scan of keep counts (both [nsk + 1]).
+fpp_status launch_compact(const Rec* sorted, int64_t nrec, const uint64_t* bstart,
+                          const uint64_t* kstart, const uint32_t* counts, KeepRule rule,
+                          uint32_t* ids_out, cudaStream_t st);
+fpp_status launch_make_offsets(const uint64_t* kstart, int nt, int64_t NB, uint32_t* offsets,
+                               cudaStream_t st);
+
+// Search (search_kernels.cu).
+struct ProbeArgs {
+  const float* P;            // [mq][ldp] query projections for tables [tb, te)
+  int64_t ldp;
+  int64_t mq;
+  const float* Q;            // [mq][ldq] padded queries
+  int64_t ldq;
+  const float* R;            // [2 L D][ldr]
+  int64_t ldr;
+  int d, D, tb, nt;
+  const float* rmax;         // [2L]
+  double gamma;
+  const int32_t* probes_pq;  // [mq] or NULL
+  int probes;                // scalar probes / max over queries
+  const uint32_t* offsets;   // [L][4D^2 + 1]
+  uint32_t* out;             // [mq][nt][probes] bucket ids
+  unsigned long long* entries;   // [mq] bucket entries (accumulated) or NULL
+  unsigned long long* rechecks;  // counter or NULL
+};
+fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st);
+size_t probe_smem_bytes(int D);
+
+struct GatherArgs {
+  const uint32_t* probes;    // [mq][nt][pstride]
+  int pstride;
+  int64_t mq;
+  int tb, nt, D;
+  const int32_t* probes_pq;  // [mq] or NULL (then pstride probes each)
+  const int32_t* k_pq;       // [mq] or NULL (then k each)
+  int k;
+  int kmax;                  // output row stride
+  const uint32_t* offsets;   // [L][4D^2 + 1]
+  const uint64_t* table_base;// [L]
+  const uint32_t* ids;       // kept ids
+  const float* X;            // [n][ldx]
+  int64_t ldx;
+  int d;
+  int64_t n;
+  const float* Q;            // [mq][ldq]
+  int64_t ldq;
+  float xmax;
+  double gamma;
+  uint32_t* bitmaps;         // [slots][words]
+  int64_t bitmap_words;
+  int slots;
+  int64_t* out_ids;          // [mq][kmax]
+  float* out_scores;
+  unsigned long long* stats; // [4]: entries, unique, topk rechecks, probes
+};
+fpp_status launch_gather_score(const GatherArgs& a, cudaStream_t st);
+int gather_slots(int sm_count);
+
+// Brute force top-k over a dense score matrix S [mq][lds] (n columns).
+fpp_status launch_topk_dense(const float* S, int64_t lds, int64_t mq, int64_t n, int k,
+                             const float* Q, int64_t ldq, const float* X, int64_t ldx, int d,
+                             float qxmax, double gamma, int64_t* out_ids, float* out_scores,
+                             int kmax, unsigned long long* rechecks, cudaStream_t st);
+
+}  // namespace fpp

@@ -1,0 +1,729 @@
+// Search kernels: probe ranking per (query, table) (Section 3.4, "Multi-
+// probing for querying") and the fused candidate gather, bitmap
+// de-duplication, exact scoring and top-k (Sections 1 and 4).
+#include <climits>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "topk.cuh"
+
+namespace fpp {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ============================================================== probe ranking
+//
+// One warp per (query, table).  Each hash j gives the signed list v_j over the
+// 2D wedges (v_j(i) = q^T r_i, v_j(i + D) = -q^T r_i); its top D entries are
+// the |q^T r_i| in the wedge on q's side.  A bucket (h1, h2) scores
+// v_1(h1) + v_2(h2) and the P best buckets are probed (ties: lower bucket id).
+//
+// Fast path (FP32 projections from the GEMM): the top E = min(D, P + SLACK)
+// entries of each list are extracted, the candidate pairs (a, b) with
+// (a+1)(b+1) <= P + SLACK are scored (a pair ranked a-th in list 1 and b-th
+// in list 2 is preceded by at least (a+1)(b+1) - 1 pairs, so these contain the
+// FP32 top P+1), and the top P+1 are selected.  The FP32 top-P set equals the
+// exact one when the gap between the P-th and (P+1)-th FP32 pair scores
+// exceeds twice their error bound.  Otherwise the (query, table) is re-decided
+// from compensated (FP64-accurate) projections.
+
+constexpr int PROBE_WARPS = 4;
+constexpr int SLACK = 8;
+constexpr int COLS = 1024;           // u64 slots of the selection buffer
+constexpr int SLOW_PAIRS = 1024;     // pair capacity of the slow path
+constexpr int POUT = 160;            // >= PMAX + SLACK + 1 (u64 slots)
+
+__host__ __device__ inline size_t probe_warp_bytes(int D) {
+  const size_t u = (size_t)16 * D > (size_t)16 * SLOW_PAIRS ? (size_t)16 * D : (size_t)16 * SLOW_PAIRS;
+  return (size_t)8 * COLS + u + (size_t)8 * POUT * 2;
+}
+
+// Sorts each lane's column col[s*32 + lane], s < S, descending, then pulls
+// the best T keys of the whole array into out[0..T) in descending order.
+__device__ void warp_select(uint64_t* col, int S, int T, uint64_t* out) {
+  const int lane = threadIdx.x & 31;
+  for (int s = 1; s < S; ++s) {
+    const uint64_t x = col[s * 32 + lane];
+    int k = s - 1;
+    while (k >= 0 && col[k * 32 + lane] < x) {
+      col[(k + 1) * 32 + lane] = col[k * 32 + lane];
+      --k;
+    }
+    col[(k + 1) * 32 + lane] = x;
+  }
+  __syncwarp();
+  int hp = 0;
+  for (int r = 0; r < T; ++r) {
+    const uint64_t my = hp < S ? col[hp * 32 + lane] : 0ull;
+    const uint32_t hi = (uint32_t)(my >> 32), lo = (uint32_t)my;
+    const uint32_t mh = __reduce_max_sync(FULL, hi);
+    const uint32_t ml = __reduce_max_sync(FULL, hi == mh ? lo : 0u);
+    if (hi == mh && lo == ml && my != 0ull) ++hp;
+    if (lane == 0) out[r] = ((uint64_t)mh << 32) | ml;
+  }
+  __syncwarp();
+}
+
+struct ListEntry {
+  float v;
+  uint32_t h;
+};
+
+// Signed-list entry a of a list whose E best |p| entries are in keys[0..E);
+// positions a >= D (available when E == D) are the antipodal wedges.
+__device__ __forceinline__ ListEntry signed_entry(const uint64_t* keys, int a, int D) {
+  ListEntry e;
+  if (a < D) {
+    const uint64_t k = keys[a];
+    e.v = key_score(k);
+    e.h = 0xFFFFFFFFu - (uint32_t)k;
+  } else {
+    const uint64_t k = keys[2 * D - 1 - a];
+    e.v = -key_score(k);
+    const uint32_t h = 0xFFFFFFFFu - (uint32_t)k;
+    e.h = h < (uint32_t)D ? h + D : h - D;
+  }
+  return e;
+}
+
+struct DEntry {
+  double v;
+  uint32_t h;
+  uint32_t pad;
+};
+
+__device__ __forceinline__ bool dentry_before(double v1, uint32_t h1, double v2, uint32_t h2) {
+  return v1 > v2 || (v1 == v2 && h1 < h2);
+}
+
+// Warp argmax over one candidate per lane (v, h, lane-valid); all lanes get
+// the winner.
+__device__ __forceinline__ void warp_best(double& v, uint32_t& h) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double v2 = __shfl_xor_sync(FULL, v, o);
+    const uint32_t h2 = __shfl_xor_sync(FULL, h, o);
+    if (dentry_before(v2, h2, v, h)) { v = v2; h = h2; }
+  }
+}
+
+// Exact re-decision of one (query, table): compensated projections, then the
+// same ranking rule on FP64-accurate values, by rounds of warp argmax.
+__device__ void probe_slow(const float* q, const float* Rt /* [2][D][ldr] */, int64_t ldr, int d,
+                           int D, int P, int Tpp, unsigned char* wsm, uint32_t* bucket_out) {
+  const int lane = threadIdx.x & 31;
+  DEntry* top = reinterpret_cast<DEntry*>(wsm);                   // 2 x Tpp (<= 2 x 136 x 16 B)
+  double* dv = reinterpret_cast<double*>(wsm + (size_t)8 * COLS);  // 2 x D doubles
+  const int W2 = 2 * D;
+  const int E = Tpp < W2 ? Tpp : W2;
+  for (int j = 0; j < 2; ++j) {
+    const float* Rj = Rt + (int64_t)j * D * ldr;
+    for (int i = lane; i < D; i += 32) dv[j * D + i] = thread_dot2(q, Rj + (int64_t)i * ldr, d);
+  }
+  __syncwarp();
+  for (int j = 0; j < 2; ++j) {
+    uint64_t taken = 0ull;  // bit s: wedge lane + 32 s already selected
+    for (int r = 0; r < E; ++r) {
+      double bv = -INFINITY;
+      uint32_t bh = 0xFFFFFFFFu;
+      for (int s = 0; s * 32 + lane < W2; ++s) {
+        if (taken & (1ull << s)) continue;
+        const uint32_t h = s * 32 + lane;
+        const double v = h < (uint32_t)D ? dv[j * D + h] : -dv[j * D + h - D];
+        if (dentry_before(v, h, bv, bh)) { bv = v; bh = h; }
+      }
+      warp_best(bv, bh);
+      if ((int)(bh & 31) == lane) taken |= 1ull << (bh >> 5);
+      if (lane == 0) top[j * Tpp + r] = DEntry{bv, bh, 0};
+    }
+  }
+  __syncwarp();
+  // candidate pairs, materialised over the (no longer needed) dv region
+  DEntry* pairs = reinterpret_cast<DEntry*>(dv);
+  int C = 0;
+  for (int a = 0; a < E; ++a) {
+    int nb = Tpp / (a + 1);
+    if (nb > E) nb = E;
+    if (nb <= 0) break;
+    for (int b = lane; b < nb; b += 32) {
+      const DEntry x = top[a], y = top[Tpp + b];
+      pairs[C + b] = DEntry{x.v + y.v, x.h * (uint32_t)W2 + y.h, 0};
+    }
+    C += nb;
+  }
+  __syncwarp();
+  unsigned taken = 0u;
+  for (int r = 0; r < P; ++r) {
+    double bv = -INFINITY;
+    uint32_t bh = 0xFFFFFFFFu;
+    int bs = -1;
+    for (int s = 0; s * 32 + lane < C; ++s) {
+      if (taken & (1u << s)) continue;
+      const DEntry e = pairs[s * 32 + lane];
+      if (dentry_before(e.v, e.h, bv, bh)) { bv = e.v; bh = e.h; bs = s; }
+    }
+    // bucket ids of distinct pairs are distinct, so the owner is unique
+    double wv = bv;
+    uint32_t wh = bh;
+    warp_best(wv, wh);
+    if (bs >= 0 && bh == wh) taken |= 1u << bs;
+    if (lane == 0) bucket_out[r] = wh;
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(PROBE_WARPS * 32)
+probe_kernel(ProbeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t w = (int64_t)blockIdx.x * PROBE_WARPS + wid;
+  if (w >= a.mq * a.nt) return;
+  const int64_t q = w / a.nt;
+  const int tl = (int)(w % a.nt);
+  const int t = a.tb + tl;
+  const int D = a.D;
+  const int P = a.probes_pq ? a.probes_pq[q] : a.probes;
+  const int64_t NB = 4ll * D * D;
+  unsigned char* wsm = smem + (size_t)wid * probe_warp_bytes(D);
+  uint64_t* col = reinterpret_cast<uint64_t*>(wsm);
+  uint64_t* lists = reinterpret_cast<uint64_t*>(wsm + (size_t)8 * COLS);  // 2 x D
+  uint64_t* pout = reinterpret_cast<uint64_t*>(
+      wsm + (size_t)8 * COLS + ((size_t)16 * D > (size_t)16 * SLOW_PAIRS ? (size_t)16 * D : (size_t)16 * SLOW_PAIRS));
+  uint32_t* bout = reinterpret_cast<uint32_t*>(pout + POUT);
+
+  const float* qv = a.Q + q * a.ldq;
+  float ss = 0.f;
+  for (int i = lane; i < a.d; i += 32) ss = fmaf(qv[i], qv[i], ss);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(FULL, ss, o);
+  const double qn = (double)sqrtf(ss) * (1.0 + 1e-4 + 2e-7 * a.d);
+
+  const int Tpp = P + SLACK;
+  const int E = Tpp < D ? Tpp : D;
+  const int S = (D + 31) / 32;
+  for (int j = 0; j < 2; ++j) {
+    const float* pr = a.P + q * a.ldp + (int64_t)(2 * tl + j) * D;
+    for (int s = 0; s < S; ++s) {
+      const int i = s * 32 + lane;
+      uint64_t key = 0ull;
+      if (i < D) {
+        const float p = pr[i];
+        const uint32_t h = (uint32_t)i + (p < 0.f ? (uint32_t)D : 0u);
+        key = ((uint64_t)float_key(fabsf(p)) << 32) | (uint64_t)(0xFFFFFFFFu - h);
+      }
+      col[s * 32 + lane] = key;
+    }
+    __syncwarp();
+    warp_select(col, S, E, lists + (size_t)j * D);
+  }
+  // candidate pairs
+  const int A = (E == D) ? 2 * D : E;
+  int C = 0;
+  for (int ai = 0; ai < A && ai < Tpp; ++ai) {
+    int nb = Tpp / (ai + 1);
+    if (nb > A) nb = A;
+    const ListEntry x = signed_entry(lists, ai, D);
+    for (int b = lane; b < nb; b += 32) {
+      const ListEntry y = signed_entry(lists + D, b, D);
+      const uint32_t bucket = x.h * (uint32_t)(2 * D) + y.h;
+      col[C + b] = ((uint64_t)float_key(x.v + y.v) << 32) | (uint64_t)(0xFFFFFFFFu - bucket);
+    }
+    C += nb;
+  }
+  const int Sc = (C + 31) / 32;
+  for (int e = C + lane; e < Sc * 32; e += 32) col[e] = 0ull;
+  __syncwarp();
+  const bool boundary = (int64_t)P < NB;
+  const int Tsel = boundary ? P + 1 : P;
+  warp_select(col, Sc, Tsel, pout);
+
+  bool certain = C >= Tsel;
+  if (certain && boundary) {
+    const double sP = key_score(pout[P - 1]), sP1 = key_score(pout[P]);
+    const double eps = a.gamma * qn * ((double)a.rmax[2 * t] + (double)a.rmax[2 * t + 1]);
+    const double need = (2.0 * eps + 6.0e-8 * (fabs(sP) + fabs(sP1))) * 1.001 + 1e-30;
+    certain = (sP - sP1) > need;
+  }
+  uint32_t* dst = a.out + (q * a.nt + tl) * (int64_t)a.probes;
+  if (certain) {
+    for (int p = lane; p < P; p += 32) bout[p] = 0xFFFFFFFFu - (uint32_t)pout[p];
+  } else {
+    if (lane == 0 && a.rechecks) atomicAdd(a.rechecks, 1ull);
+    probe_slow(a.Q + q * a.ldq, a.R + (int64_t)2 * t * D * a.ldr, a.ldr, a.d, D, P, Tpp, wsm, bout);
+  }
+  __syncwarp();
+  const uint32_t* off = a.offsets + (int64_t)t * (NB + 1);
+  unsigned long long ent = 0;
+  for (int p = lane; p < P; p += 32) {
+    const uint32_t b = bout[p];
+    dst[p] = b;
+    ent += off[b + 1] - off[b];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ent += __shfl_xor_sync(FULL, ent, o);
+  if (lane == 0 && a.entries) atomicAdd(a.entries + q, ent);
+}
+
+// ============================================================== gather + score
+//
+// One CTA per query at a time (queries handed out by an atomic counter).
+// Phase 1: warps walk the probed buckets; each kept id is test-and-set in the
+// CTA's bitmap (n bits, in global memory, L2-resident), so every distinct
+// candidate is scored exactly once, with coalesced float4 row loads, and
+// offered to the warp's running top-K' (K' = k + 16).  Phase 2: the warps'
+// lists are merged and the best K' are re-scored with the compensated dot
+// product; the FP32 pre-selection is exact unless the K'-th FP32 score lies
+// within the FP32 error bound of the k-th re-scored one, in which case the
+// buckets are walked again and every candidate that could still reach the
+// top-k is re-scored.  Phase 3: the buckets are walked again to clear the
+// bitmap words that were touched.
+
+constexpr int GS_WARPS = 8;
+constexpr int SLOW_CAP = 2048;
+constexpr int KSLACK = 16;
+
+struct GSLayout {
+  int kp, cap, mcap, rcap;
+  size_t q_off, queue_off, wtop_off, merge_off, resc_off, total;
+};
+
+__host__ __device__ inline GSLayout gs_layout(int kmax, int ldq) {
+  GSLayout L;
+  L.kp = kmax + KSLACK;
+  L.cap = pow2_ceil(2 * L.kp + 32);
+  L.mcap = pow2_ceil(GS_WARPS * L.kp);
+  L.rcap = pow2_ceil(L.kp);
+  size_t o = 0;
+  L.q_off = o; o += (size_t)4 * ldq; o = (o + 15) & ~(size_t)15;
+  L.queue_off = o; o += (size_t)GS_WARPS * 64 * 4;
+  L.wtop_off = o; o += (size_t)GS_WARPS * L.cap * 8;
+  L.merge_off = o;
+  {
+    size_t mb = (size_t)L.mcap * 8;
+    if (mb < (size_t)SLOW_CAP * 16) mb = (size_t)SLOW_CAP * 16;
+    o += mb;
+  }
+  L.resc_off = o; o += (size_t)L.rcap * 16;
+  L.total = o;
+  return L;
+}
+
+// Scores up to 32 queued rows against q (FP32, coalesced float4 loads, G lanes
+// per row) and hands each (score, id) to emit(lane_valid, score, id).
+template <int G, class Emit>
+__device__ __forceinline__ void score_rows(const uint32_t* queue, int nrows, const float4* q4,
+                                           int nf4, const float* __restrict__ X, int64_t ldx,
+                                           Emit emit) {
+  const int lane = threadIdx.x & 31;
+  constexpr int RPP = 32 / G;
+  const int sub = lane % G, grp = lane / G;
+  for (int r0 = 0; r0 < nrows; r0 += 2 * RPP) {
+    const int ra = r0 + grp, rb = r0 + RPP + grp;
+    const bool oka = ra < nrows, okb = rb < nrows;
+    const uint32_t ida = queue[oka ? ra : 0], idb = queue[okb ? rb : 0];
+    const float4* xa = reinterpret_cast<const float4*>(X + (int64_t)ida * ldx);
+    const float4* xb = reinterpret_cast<const float4*>(X + (int64_t)idb * ldx);
+    float sa = 0.f, sb = 0.f;
+    for (int c = sub; c < nf4; c += G) {
+      const float4 qq = q4[c];
+      const float4 va = oka ? __ldg(xa + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 vb = okb ? __ldg(xb + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+      sa = fmaf(va.x, qq.x, sa); sa = fmaf(va.y, qq.y, sa);
+      sa = fmaf(va.z, qq.z, sa); sa = fmaf(va.w, qq.w, sa);
+      sb = fmaf(vb.x, qq.x, sb); sb = fmaf(vb.y, qq.y, sb);
+      sb = fmaf(vb.z, qq.z, sb); sb = fmaf(vb.w, qq.w, sb);
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      sa += __shfl_xor_sync(FULL, sa, o);
+      sb += __shfl_xor_sync(FULL, sb, o);
+    }
+    emit(oka && sub == 0, sa, ida);
+    emit(okb && sub == 0, sb, idb);
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(GS_WARPS * 32)
+gather_score_kernel(GatherArgs a, unsigned long long* qcounter, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long s_q;
+  __shared__ unsigned s_U, s_nslow;
+  __shared__ int s_slow;
+  __shared__ double s_thr64;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const GSLayout Lo = gs_layout(a.kmax, (int)a.ldq);
+  float* qs = reinterpret_cast<float*>(smem + Lo.q_off);
+  const float4* q4 = reinterpret_cast<const float4*>(qs);
+  uint32_t* queue = reinterpret_cast<uint32_t*>(smem + Lo.queue_off) + wid * 64;
+  uint64_t* wbuf = reinterpret_cast<uint64_t*>(smem + Lo.wtop_off) + (size_t)wid * Lo.cap;
+  uint64_t* merge = reinterpret_cast<uint64_t*>(smem + Lo.merge_off);
+  SD* slow = reinterpret_cast<SD*>(smem + Lo.merge_off);
+  SD* resc = reinterpret_cast<SD*>(smem + Lo.resc_off);
+  const int nf4 = (int)(a.ldq / 4);
+  const int64_t NB = 4ll * a.D * a.D;
+  uint32_t* bm = a.bitmaps + (int64_t)blockIdx.x * a.bitmap_words;
+  const unsigned lt = (1u << lane) - 1u;
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_q = (long long)atomicAdd(qcounter, 1ull);
+      s_U = 0; s_nslow = 0; s_slow = 0;
+    }
+    __syncthreads();
+    const int64_t q = s_q;
+    if (q >= a.mq) break;
+    const int kq = a.k_pq ? a.k_pq[q] : a.k;
+    const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
+    const float* qg = a.Q + q * a.ldq;
+    for (int i = threadIdx.x; i < (int)a.ldq; i += blockDim.x) qs[i] = qg[i];
+    __syncthreads();
+    float ss = 0.f;
+    for (int i = lane; i < a.d; i += 32) ss = fmaf(qs[i], qs[i], ss);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(FULL, ss, o);
+    const double qn = (double)sqrtf(ss) * (1.0 + 1e-4 + 2e-7 * a.d);
+    const double eps_s = a.gamma * qn * (double)a.xmax;
+    const double du = 5.9604644775390625e-08 * (a.d + 8);
+    const double delta = 4.0 * du * du * qn * (double)a.xmax + 1e-300;
+
+    // ---------------- phase 1: discover, de-duplicate, score
+    WarpTop wt;
+    wt.init(wbuf, Lo.cap, Lo.kp);
+    int qn_cnt = 0;
+    unsigned myU = 0;
+    unsigned long long ent = 0;
+    auto offer = [&](bool v, float s, uint32_t id) { wt.offer(v, pack_key(s, id)); };
+    const int nprobe = a.nt * Pq;
+    for (int pi = wid; pi < nprobe; pi += GS_WARPS) {
+      const int tl = pi / Pq, p = pi - tl * Pq;
+      const int t = a.tb + tl;
+      const uint32_t b = a.probes[(q * a.nt + tl) * (int64_t)a.pstride + p];
+      const uint32_t* off = a.offsets + (int64_t)t * (NB + 1);
+      const uint32_t o0 = off[b], cnt = off[b + 1] - o0;
+      const uint32_t* idp = a.ids + a.table_base[t] + o0;
+      ent += cnt;
+      for (uint32_t c = 0; c < cnt; c += 32) {
+        const bool has = c + lane < cnt;
+        const uint32_t id = has ? __ldg(idp + c + lane) : 0u;
+        bool fresh = false;
+        if (has) {
+          const uint32_t bit = 1u << (id & 31);
+          fresh = !(atomicOr(bm + (id >> 5), bit) & bit);
+        }
+        const unsigned m = __ballot_sync(FULL, fresh);
+        if (fresh) queue[qn_cnt + __popc(m & lt)] = id;
+        qn_cnt += __popc(m);
+        myU += __popc(m);
+        __syncwarp();
+        if (qn_cnt >= 32) {
+          score_rows<G>(queue, 32, q4, nf4, a.X, a.ldx, offer);
+          qn_cnt -= 32;
+          if (lane < qn_cnt) queue[lane] = queue[32 + lane];
+          __syncwarp();
+        }
+      }
+    }
+    if (qn_cnt > 0) score_rows<G>(queue, qn_cnt, q4, nf4, a.X, a.ldx, offer);
+    const int nw = wt.finish();
+    for (int e = lane; e < Lo.kp; e += 32) merge[(size_t)wid * Lo.kp + e] = e < nw ? wbuf[e] : 0ull;
+    if (lane == 0) {
+      atomicAdd(&s_U, myU);
+      if (a.stats) atomicAdd(a.stats + 0, ent);
+    }
+    __syncthreads();
+    for (int e = GS_WARPS * Lo.kp + threadIdx.x; e < Lo.mcap; e += blockDim.x) merge[e] = 0ull;
+    __syncthreads();
+    block_sort_desc(merge, Lo.mcap);
+
+    // ---------------- phase 2: re-score the best K' with FP64 accuracy
+    const unsigned U = s_U;
+    const int Kpp = (int)(U < (unsigned)Lo.kp ? U : (unsigned)Lo.kp);
+    for (int e = wid; e < Kpp; e += GS_WARPS) {
+      const uint32_t id = key_id(merge[e]);
+      const double s = warp_dot2(qs, a.X + (int64_t)id * a.ldx, a.d);
+      if (lane == 0) resc[e] = SD{s, id, 0};
+    }
+    for (int e = Kpp + threadIdx.x; e < Lo.rcap; e += blockDim.x) resc[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+    __syncthreads();
+    if (wid == 0) warp_sort_sd(resc, Lo.rcap);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (U > (unsigned)Kpp) {
+        const double sK = (double)key_score(merge[Lo.kp - 1]);
+        const double need = resc[kq - 1].s;
+        if (!(sK + eps_s + 2.0 * delta < need)) {
+          s_slow = 1;
+          s_thr64 = need - eps_s - 2.0 * delta;
+        }
+      }
+      if (a.stats) {
+        atomicAdd(a.stats + 1, (unsigned long long)U);
+        atomicAdd(a.stats + 3, (unsigned long long)nprobe);
+        if (s_slow) atomicAdd(a.stats + 2, 1ull);
+      }
+    }
+    __syncthreads();
+
+    const int64_t orow = q * a.kmax;
+    if (!s_slow) {
+      for (int e = threadIdx.x; e < a.kmax; e += blockDim.x) {
+        const bool ok = e < kq && e < Kpp;
+        a.out_ids[orow + e] = ok ? (int64_t)resc[e].id : -1;
+        a.out_scores[orow + e] = ok ? (float)resc[e].s : -INFINITY;
+      }
+      // ---------------- phase 3: clear the touched bitmap words
+      for (int pi = wid; pi < nprobe; pi += GS_WARPS) {
+        const int tl = pi / Pq, p = pi - tl * Pq;
+        const int t = a.tb + tl;
+        const uint32_t b = a.probes[(q * a.nt + tl) * (int64_t)a.pstride + p];
+        const uint32_t* off = a.offsets + (int64_t)t * (NB + 1);
+        const uint32_t o0 = off[b], cnt = off[b + 1] - o0;
+        const uint32_t* idp = a.ids + a.table_base[t] + o0;
+        for (uint32_t c = lane; c < cnt; c += 32) bm[__ldg(idp + c) >> 5] = 0u;
+      }
+    } else {
+      // ---------------- slow path: every candidate that may reach the top-k
+      const double thr64 = s_thr64;
+      int qc = 0;
+      auto collect = [&](bool v, float s, uint32_t id) {
+        if (v && (double)s >= thr64) {
+          const unsigned slot = atomicAdd(&s_nslow, 1u);
+          if (slot < (unsigned)SLOW_CAP) slow[slot].id = id;
+          else if (err) atomicExch(err, 1);
+        }
+      };
+      __syncthreads();  // merge region is reused by the slow list
+      for (int pi = wid; pi < nprobe; pi += GS_WARPS) {
+        const int tl = pi / Pq, p = pi - tl * Pq;
+        const int t = a.tb + tl;
+        const uint32_t b = a.probes[(q * a.nt + tl) * (int64_t)a.pstride + p];
+        const uint32_t* off = a.offsets + (int64_t)t * (NB + 1);
+        const uint32_t o0 = off[b], cnt = off[b + 1] - o0;
+        const uint32_t* idp = a.ids + a.table_base[t] + o0;
+        for (uint32_t c = 0; c < cnt; c += 32) {
+          const bool has = c + lane < cnt;
+          const uint32_t id = has ? __ldg(idp + c + lane) : 0u;
+          bool first = false;
+          if (has) {
+            const uint32_t bit = 1u << (id & 31);
+            first = (atomicAnd(bm + (id >> 5), ~bit) & bit) != 0u;
+          }
+          const unsigned m = __ballot_sync(FULL, first);
+          if (first) queue[qc + __popc(m & lt)] = id;
+          qc += __popc(m);
+          __syncwarp();
+          if (qc >= 32) {
+            score_rows<G>(queue, 32, q4, nf4, a.X, a.ldx, collect);
+            qc -= 32;
+            if (lane < qc) queue[lane] = queue[32 + lane];
+            __syncwarp();
+          }
+        }
+      }
+      if (qc > 0) score_rows<G>(queue, qc, q4, nf4, a.X, a.ldx, collect);
+      __syncthreads();
+      const int ns = (int)(s_nslow < (unsigned)SLOW_CAP ? s_nslow : (unsigned)SLOW_CAP);
+      for (int e = wid; e < ns; e += GS_WARPS) {
+        const uint32_t id = slow[e].id;
+        const double s = warp_dot2(qs, a.X + (int64_t)id * a.ldx, a.d);
+        if (lane == 0) slow[e].s = s;
+      }
+      const int np2 = pow2_ceil(ns > 1 ? ns : 1);
+      for (int e = ns + threadIdx.x; e < np2; e += blockDim.x) slow[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+      __syncthreads();
+      block_sort_sd(slow, np2);
+      for (int e = threadIdx.x; e < a.kmax; e += blockDim.x) {
+        const bool ok = e < kq && e < ns;
+        a.out_ids[orow + e] = ok ? (int64_t)slow[e].id : -1;
+        a.out_scores[orow + e] = ok ? (float)slow[e].s : -INFINITY;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ============================================================== dense top-k
+//
+// Exact top-k over a dense FP32 score row (brute-force search): the same
+// FP32 pre-selection, compensated re-scoring and boundary check as above,
+// with every column a candidate.
+__global__ void __launch_bounds__(GS_WARPS * 32)
+topk_dense_kernel(const float* __restrict__ S, int64_t lds, int64_t n, int k, const float* Q,
+                  int64_t ldq, const float* __restrict__ X, int64_t ldx, int d, float xmax,
+                  double gamma, int64_t* out_ids, float* out_scores, int kmax,
+                  unsigned long long* rechecks, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned s_nslow;
+  __shared__ int s_slow;
+  __shared__ double s_thr64;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const GSLayout Lo = gs_layout(kmax, (int)ldq);
+  float* qs = reinterpret_cast<float*>(smem + Lo.q_off);
+  uint64_t* wbuf = reinterpret_cast<uint64_t*>(smem + Lo.wtop_off) + (size_t)wid * Lo.cap;
+  uint64_t* merge = reinterpret_cast<uint64_t*>(smem + Lo.merge_off);
+  SD* slow = reinterpret_cast<SD*>(smem + Lo.merge_off);
+  SD* resc = reinterpret_cast<SD*>(smem + Lo.resc_off);
+  const int64_t q = blockIdx.x;
+  const float* row = S + q * lds;
+  for (int i = threadIdx.x; i < (int)ldq; i += blockDim.x) qs[i] = Q[q * ldq + i];
+  if (threadIdx.x == 0) { s_nslow = 0; s_slow = 0; }
+  __syncthreads();
+  float ss = 0.f;
+  for (int i = lane; i < d; i += 32) ss = fmaf(qs[i], qs[i], ss);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(FULL, ss, o);
+  const double qn = (double)sqrtf(ss) * (1.0 + 1e-4 + 2e-7 * d);
+  const double eps_s = gamma * qn * (double)xmax;
+  const double du = 5.9604644775390625e-08 * (d + 8);
+  const double delta = 4.0 * du * du * qn * (double)xmax + 1e-300;
+
+  WarpTop wt;
+  wt.init(wbuf, Lo.cap, Lo.kp);
+  for (int64_t c0 = (int64_t)wid * 32; c0 < n; c0 += (int64_t)GS_WARPS * 32) {
+    const int64_t c = c0 + lane;
+    const bool ok = c < n;
+    wt.offer(ok, ok ? pack_key(row[c], (uint32_t)c) : 0ull);
+  }
+  const int nw = wt.finish();
+  for (int e = lane; e < Lo.kp; e += 32) merge[(size_t)wid * Lo.kp + e] = e < nw ? wbuf[e] : 0ull;
+  __syncthreads();
+  for (int e = GS_WARPS * Lo.kp + threadIdx.x; e < Lo.mcap; e += blockDim.x) merge[e] = 0ull;
+  __syncthreads();
+  block_sort_desc(merge, Lo.mcap);
+  const int Kpp = (int)(n < (int64_t)Lo.kp ? n : (int64_t)Lo.kp);
+  for (int e = wid; e < Kpp; e += GS_WARPS) {
+    const uint32_t id = key_id(merge[e]);
+    const double s = warp_dot2(qs, X + (int64_t)id * ldx, d);
+    if (lane == 0) resc[e] = SD{s, id, 0};
+  }
+  for (int e = Kpp + threadIdx.x; e < Lo.rcap; e += blockDim.x) resc[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+  __syncthreads();
+  if (wid == 0) warp_sort_sd(resc, Lo.rcap);
+  __syncthreads();
+  if (threadIdx.x == 0 && n > Kpp) {
+    const double sK = (double)key_score(merge[Lo.kp - 1]);
+    const double need = resc[k - 1].s;
+    if (!(sK + eps_s + 2.0 * delta < need)) {
+      s_slow = 1;
+      s_thr64 = need - eps_s - 2.0 * delta;
+      if (rechecks) atomicAdd(rechecks, 1ull);
+    }
+  }
+  __syncthreads();
+  const int64_t orow = q * kmax;
+  if (!s_slow) {
+    for (int e = threadIdx.x; e < kmax; e += blockDim.x) {
+      const bool ok = e < k && e < Kpp;
+      out_ids[orow + e] = ok ? (int64_t)resc[e].id : -1;
+      out_scores[orow + e] = ok ? (float)resc[e].s : -INFINITY;
+    }
+    return;
+  }
+  const double thr64 = s_thr64;
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+    if ((double)row[c] >= thr64) {
+      const unsigned slot = atomicAdd(&s_nslow, 1u);
+      if (slot < (unsigned)SLOW_CAP) slow[slot].id = (uint32_t)c;
+      else if (err) atomicExch(err, 1);
+    }
+  }
+  __syncthreads();
+  const int ns = (int)(s_nslow < (unsigned)SLOW_CAP ? s_nslow : (unsigned)SLOW_CAP);
+  for (int e = wid; e < ns; e += GS_WARPS) {
+    const uint32_t id = slow[e].id;
+    const double s = warp_dot2(qs, X + (int64_t)id * ldx, d);
+    if (lane == 0) slow[e].s = s;
+  }
+  const int np2 = pow2_ceil(ns > 1 ? ns : 1);
+  for (int e = ns + threadIdx.x; e < np2; e += blockDim.x) slow[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+  __syncthreads();
+  block_sort_sd(slow, np2);
+  for (int e = threadIdx.x; e < kmax; e += blockDim.x) {
+    const bool ok = e < k && e < ns;
+    out_ids[orow + e] = ok ? (int64_t)slow[e].id : -1;
+    out_scores[orow + e] = ok ? (float)slow[e].s : -INFINITY;
+  }
+}
+
+int choose_g(int nf4) {
+  int g = 1;
+  while (g < 32 && g * 4 < nf4) g <<= 1;
+  return g;
+}
+
+template <int G>
+fpp_status launch_gs(const GatherArgs& a, size_t smem, int grid, unsigned long long* qc, int* err,
+                     cudaStream_t st) {
+  static bool attr_set = false;  // per instantiation; benign race (idempotent)
+  if (!attr_set) {
+    FPP_CUDA(cudaFuncSetAttribute(gather_score_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024));
+    attr_set = true;
+  }
+  gather_score_kernel<G><<<grid, GS_WARPS * 32, smem, st>>>(a, qc, err);
+  FPP_LAUNCHED();
+  return FPP_OK;
+}
+
+}  // namespace
+
+size_t probe_smem_bytes(int D) { return (size_t)PROBE_WARPS * probe_warp_bytes(D); }
+
+fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st) {
+  const int64_t warps = a.mq * a.nt;
+  if (warps <= 0) return FPP_OK;
+  if (a.probes > 128) {
+    set_error("probes per table must be <= 128");
+    return FPP_EINVAL;
+  }
+  const size_t smem = probe_smem_bytes(a.D);
+  FPP_CUDA(cudaFuncSetAttribute(probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  probe_kernel<<<(unsigned)ceil_div(warps, PROBE_WARPS), PROBE_WARPS * 32, smem, st>>>(a);
+  FPP_LAUNCHED();
+  return FPP_OK;
+}
+
+int gather_slots(int sm_count) { return sm_count * 4; }
+
+fpp_status launch_gather_score(const GatherArgs& a, cudaStream_t st) {
+  if (a.mq <= 0) return FPP_OK;
+  const GSLayout Lo = gs_layout(a.kmax, (int)a.ldq);
+  if (Lo.total > 200 * 1024) {
+    set_error("gather_score: k too large for shared memory");
+    return FPP_EINVAL;
+  }
+  // a.stats[4] is the query counter, a.stats[5] the error flag (see the caller)
+  unsigned long long* qc = a.stats + 4;
+  int* err = reinterpret_cast<int*>(a.stats + 5);
+  const int grid = (int)(a.mq < a.slots ? a.mq : a.slots);
+  const int g = choose_g((int)(a.ldq / 4));
+  switch (g) {
+    case 1: return launch_gs<1>(a, Lo.total, grid, qc, err, st);
+    case 2: return launch_gs<2>(a, Lo.total, grid, qc, err, st);
+    case 4: return launch_gs<4>(a, Lo.total, grid, qc, err, st);
+    case 8: return launch_gs<8>(a, Lo.total, grid, qc, err, st);
+    case 16: return launch_gs<16>(a, Lo.total, grid, qc, err, st);
+    default: return launch_gs<32>(a, Lo.total, grid, qc, err, st);
+  }
+}
+
+fpp_status launch_topk_dense(const float* S, int64_t lds, int64_t mq, int64_t n, int k,
+                             const float* Q, int64_t ldq, const float* X, int64_t ldx, int d,
+                             float xmax, double gamma, int64_t* out_ids, float* out_scores,
+                             int kmax, unsigned long long* rechecks, cudaStream_t st) {
+  if (mq <= 0) return FPP_OK;
+  const GSLayout Lo = gs_layout(kmax, (int)ldq);
+  FPP_CUDA(cudaFuncSetAttribute(topk_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024));
+  int* err = reinterpret_cast<int*>(rechecks + 1);
+  topk_dense_kernel<<<(unsigned)mq, GS_WARPS * 32, Lo.total, st>>>(
+      S, lds, n, k, Q, ldq, X, ldx, d, xmax, gamma, out_ids, out_scores, kmax, rechecks, err);
+  FPP_LAUNCHED();
+  return FPP_OK;
+}
+
+}  // namespace fpp

@@ -1,0 +1,102 @@
+"""Comparison helpers for GPU-vs-oracle parity: exact equality of every
+discrete decision except where the oracle flags an FP64 near-tie."""
+import numpy as np
+
+import oracle as O
+
+SCORE_RTOL = 1e-5
+
+
+def excluded_buckets(ix: O.OracleIndex, t: int, gpu_point_buckets=None) -> set:
+    """Buckets of table t whose content may legitimately differ: those that
+    hold a point whose assignment is a near-tie (under either assignment),
+    and those whose filter boundary is a near-tie."""
+    ex = set(np.nonzero(ix.filter_flag[t])[0].tolist())
+    flagged = np.nonzero(ix.hash_flag[t])[0]
+    if ix.point_buckets is not None:
+        ex.update(ix.point_buckets[t, flagged].tolist())
+    if gpu_point_buckets is not None:
+        ex.update(np.asarray(gpu_point_buckets)[flagged].tolist())
+    return ex
+
+
+def compare_point_buckets(ix, t, gpu_pb):
+    ora = ix.point_buckets[t]
+    bad = np.nonzero(ora != gpu_pb.astype(np.int64))[0]
+    unexplained = [int(p) for p in bad if not ix.hash_flag[t, p]]
+    return len(bad), unexplained
+
+
+def compare_table(ix, t, gpu_off, gpu_ids, exclude):
+    """Returns the list of buckets whose kept ids differ and are not excluded."""
+    off = ix.offsets[t]
+    bad = []
+    g_off = gpu_off.astype(np.int64)
+    for b in np.nonzero((np.diff(off) != np.diff(g_off)) | (off[:-1] != g_off[:-1]))[0]:
+        if int(b) not in exclude:
+            bad.append(int(b))
+    # same kept counts: compare ids bucket by bucket (order inside a bucket is
+    # filter score desc, id asc on both sides)
+    if not bad:
+        diff = np.nonzero(ix.ids[t] != gpu_ids.astype(np.int64))[0]
+        if diff.size:
+            bk = np.searchsorted(off, diff, side="right") - 1
+            for b in np.unique(bk):
+                if int(b) not in exclude:
+                    # order within a bucket may swap only on exactly tied scores;
+                    # the kept SET must agree
+                    a = set(ix.bucket_ids(t, int(b)).tolist())
+                    g = set(gpu_ids[off[b]: off[b + 1]].astype(np.int64).tolist())
+                    if a != g:
+                        bad.append(int(b))
+    return bad
+
+
+def compare_search(res, gpu_ids, gpu_scores, k, tables, excl_by_table):
+    """Per query: exact ids and scores within SCORE_RTOL unless a flag
+    (probe boundary, top-k boundary, or a probed bucket that is excluded)
+    allows another answer.  Returns (n_compared, n_skipped, failures)."""
+    compared, skipped, fails = 0, 0, []
+    for i, r in enumerate(res):
+        flagged = bool(r.topk_flag) or bool(np.any(r.probe_flag))
+        if not flagged:
+            for ti, t in enumerate(tables):
+                ex = excl_by_table[t]
+                if ex and any(int(b) in ex for b in r.buckets[ti]):
+                    flagged = True
+                    break
+        if flagged:
+            skipped += 1
+            continue
+        compared += 1
+        kk = len(r.ids)
+        gi = np.asarray(gpu_ids[i][:kk]).astype(np.int64)
+        gs = np.asarray(gpu_scores[i][:kk]).astype(np.float64)
+        if not np.array_equal(gi, r.ids):
+            fails.append((i, "ids", r.ids.tolist(), gi.tolist()))
+            continue
+        fin = np.isfinite(r.scores)
+        if not np.array_equal(np.isfinite(gs), fin):
+            fails.append((i, "padding", r.scores.tolist(), gs.tolist()))
+            continue
+        err = np.abs(gs[fin] - r.scores[fin])
+        tol = SCORE_RTOL * np.maximum(np.abs(r.scores[fin]), 1e-3)
+        if np.any(err > tol):
+            fails.append((i, "scores", r.scores.tolist(), gs.tolist()))
+    return compared, skipped, fails
+
+
+def compare_probes(ix, Q, P, gpu_probes, tables):
+    """Probe sets per (query, table) must agree unless the oracle flags the
+    P-th / (P+1)-th boundary.  Returns (compared, skipped, failures)."""
+    compared, skipped, fails = 0, 0, []
+    for i, q in enumerate(Q):
+        b, _, flag = O.probe_buckets(ix, q, P, tables)
+        for ti in range(len(tables)):
+            if flag[ti]:
+                skipped += 1
+                continue
+            compared += 1
+            if set(b[ti].tolist()) != set(gpu_probes[i, ti].astype(np.int64).tolist()):
+                fails.append((i, tables[ti]))
+    return compared, skipped, fails

@@ -1,0 +1,204 @@
+"""GPU path vs the FP64 oracle, through the C ABI.
+
+Bucket ids, kept CSR, probe sets, candidate sets and top-k ids must be equal
+except where the oracle flags an FP64 near-tie (margin < 1e-6); scores agree
+within 1e-5 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests import parity as PT
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2206_01382_gb300 as F
+    from paper_2206_01382_gb300 import _build
+    _build.build()
+    F.load()
+    return F
+
+
+def _full_parity(F, X, Q, L, D, alpha, seed, k, probes_list, min_compared=0.9):
+    ix_o = O.build_index(X, L, D, alpha, seed=seed)
+    ix_g = F.Index(X, L, D, alpha, seed=seed)
+    excl = {}
+    for t in range(L):
+        gpb = F.fpp_debug_point_buckets(ix_g.handle, t)
+        nbad, unexplained = PT.compare_point_buckets(ix_o, t, gpb)
+        assert not unexplained, f"table {t}: points {unexplained[:10]}"
+        excl[t] = PT.excluded_buckets(ix_o, t, gpb)
+        off, ids = F.fpp_debug_table(ix_g.handle, t)
+        bad = PT.compare_table(ix_o, t, off, ids, excl[t])
+        assert not bad, f"table {t}: buckets {bad[:10]}"
+    for P in probes_list:
+        gp = F.fpp_debug_probes(ix_g.handle, Q, P)
+        c, s, fails = PT.compare_probes(ix_o, Q, P, gp, list(range(L)))
+        assert not fails, fails[:5]
+        gi, gs = ix_g.search(Q, k, P)
+        _, _, res = O.search_batch(ix_o, Q, k, P)
+        c, s, fails = PT.compare_search(res, gi, gs, k, list(range(L)), excl)
+        assert not fails, fails[:3]
+        assert c >= min_compared * len(res), (c, s)
+    return ix_o, ix_g
+
+
+def test_tiny_workload_full_parity(F):
+    w = W.WORKLOADS["tiny"]
+    X, Q = W.dataset(w)
+    _full_parity(F, X, Q, w.L, w.D, w.alpha, w.rot_seed, w.k, (1, 4, 16))
+
+
+def test_ragged_shapes_full_parity(F):
+    # n, d, D, k, probes off every tile size; d not a multiple of 4
+    X, Q = W.small_mixture(2999, 37, 30, 40, 0.2, 77)
+    _full_parity(F, X, Q, L=3, D=5, alpha=0.37, seed=5, k=7, probes_list=(1, 11, 100))
+
+
+def test_large_k_and_probes_parity(F):
+    X, Q = W.small_mixture(20000, 25, 48, 128, 0.15, 78)
+    _full_parity(F, X, Q, L=4, D=16, alpha=0.5, seed=6, k=100, probes_list=(128,))
+
+
+def test_unfiltered_all_buckets_equals_bruteforce(F):
+    # alpha = 1 and every one of the 4D^2 buckets probed: exact search
+    X, Q = W.small_mixture(5000, 40, 24, 16, 0.2, 79)
+    ix = F.Index(X, 3, 3, 1.0, seed=9)
+    gi, gs = ix.search(Q, 10, 36)
+    bi, bs, bf = O.brute_force(X, Q, 10)
+    for i in range(len(Q)):
+        if not bf[i]:
+            assert np.array_equal(gi[i], bi[i])
+        assert np.allclose(gs[i], bs[i], rtol=1e-5, atol=1e-6)
+
+
+def test_gpu_bruteforce_matches_oracle(F):
+    X, Q = W.small_mixture(30000, 50, 64, 64, 0.25, 80)
+    gi, gs = F.fpp_bruteforce(X, Q, 20)
+    bi, bs, bf = O.brute_force(X, Q, 20)
+    for i in range(len(Q)):
+        if not bf[i]:
+            assert np.array_equal(gi[i], bi[i])
+        assert np.allclose(gs[i], bs[i], rtol=1e-5, atol=1e-6)
+
+
+def test_short_results_are_padded(F):
+    X, Q = W.small_mixture(40, 3, 16, 4, 0.2, 81)
+    ix = F.Index(X, 1, 2, 0.2, seed=1)
+    gi, gs = ix.search(Q, 50, 1)
+    ix_o = O.build_index(X, 1, 2, 0.2, seed=1)
+    _, _, res = O.search_batch(ix_o, Q, 50, 1)
+    for i, r in enumerate(res):
+        assert np.array_equal(gi[i], r.ids)
+        assert np.array_equal(np.isneginf(gs[i]), np.isneginf(r.scores))
+
+
+def test_per_query_k_and_probes(F):
+    X, Q = W.small_mixture(20000, 60, 32, 128, 0.2, 82)
+    rng = np.random.default_rng(3)
+    kq = rng.choice([1, 10, 100], size=len(Q)).astype(np.int32)
+    pq = rng.choice([2, 8, 32, 128], size=len(Q)).astype(np.int32)
+    L, D = 5, 12
+    ix_o = O.build_index(X, L, D, 0.3, seed=4)
+    ix = F.Index(X, L, D, 0.3, seed=4)
+    gi, gs, st = ix.search(Q, 10, 1, k_per_query=kq, probes_per_query=pq)
+    assert gi.shape == (len(Q), 100)
+    _, _, res = O.search_batch(ix_o, Q, kq, pq)
+    excl = {t: PT.excluded_buckets(ix_o, t) for t in range(L)}
+    c, s, fails = PT.compare_search(res, gi, gs, 100, list(range(L)), excl)
+    assert not fails, fails[:3]
+    for i in range(len(Q)):       # past a query's own k: padding
+        assert (gi[i, kq[i]:] == -1).all()
+    assert st["queries"] == len(Q)
+    assert st["entries"] == sum(r.entries for r in res)
+    assert st["unique"] == sum(r.cand.size for r in res)
+
+
+def test_table_range(F):
+    w = W.WORKLOADS["tiny"]
+    X, Q = W.dataset(w)
+    ix_o = O.build_index(X, w.L, w.D, w.alpha, seed=w.rot_seed)
+    ix = F.Index(X, w.L, w.D, w.alpha, seed=w.rot_seed)
+    tabs = [3, 4, 5, 6]
+    gi, gs, _ = ix.search(Q, 10, 4, table_begin=3, table_end=7)
+    _, _, res = O.search_batch(ix_o, Q, 10, 4, tables=tabs)
+    excl = {t: PT.excluded_buckets(ix_o, t) for t in range(w.L)}
+    c, s, fails = PT.compare_search(res, gi, gs, 10, tabs, excl)
+    assert not fails and c > 80
+
+
+def test_device_pointers_and_stream(F):
+    w = W.WORKLOADS["tiny"]
+    X, Q = W.dataset(w)
+    ix = F.Index(torch.from_numpy(X).cuda(), w.L, w.D, w.alpha, seed=w.rot_seed)
+    hi, hs = ix.search(Q, 10, 4)
+    Qd = torch.from_numpy(Q).cuda()
+    s = torch.cuda.Stream()
+    gi, gs, _ = ix.search(Qd, 10, 4, stream=s, want_stats=False)
+    s.synchronize()
+    assert gi.is_cuda
+    assert np.array_equal(gi.cpu().numpy(), hi)
+    assert np.array_equal(gs.cpu().numpy(), hs)
+
+
+def test_empty_query_batch(F):
+    w = W.WORKLOADS["tiny"]
+    X, Q = W.dataset(w)
+    ix = F.Index(X[:500], 2, 8, 0.5, seed=1)
+    gi, gs = ix.search(Q[:0], 10, 4)
+    assert gi.shape == (0, 10)
+
+
+def test_repeat_search_is_deterministic(F):
+    w = W.WORKLOADS["tiny"]
+    X, Q = W.dataset(w)
+    ix = F.Index(X, w.L, w.D, w.alpha, seed=w.rot_seed)
+    a = ix.search(Q, 10, 16)
+    b = ix.search(Q, 10, 16)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_plain1m_full_size_sampled(F):
+    """The 1M x 128 workload at full size: index build parity on two tables
+    the oracle rebuilds, probe parity on sampled queries over all 100 tables,
+    end-to-end search parity restricted to those two tables, and properties
+    of the full 100-table search."""
+    w = W.WORKLOADS["plain1m"]
+    X, Q = W.dataset(w, m=2000)
+    ix = F.Index(X, w.L, w.D, w.alpha, seed=w.rot_seed)
+    tabs = [0, 1]
+    ix_o = O.build_index(X, w.L, w.D, w.alpha, seed=w.rot_seed, tables=tabs)
+    excl = {}
+    for t in tabs:
+        gpb = F.fpp_debug_point_buckets(ix.handle, t)
+        nbad, unexplained = PT.compare_point_buckets(ix_o, t, gpb)
+        assert not unexplained
+        excl[t] = PT.excluded_buckets(ix_o, t, gpb)
+        off, ids = F.fpp_debug_table(ix.handle, t)
+        assert not PT.compare_table(ix_o, t, off, ids, excl[t])
+    Qs = Q[:150]
+    for P in (1, 16, 64):
+        gp = F.fpp_debug_probes(ix.handle, Qs, P)
+        c, s, fails = PT.compare_probes(ix_o, Qs, P, gp, list(range(w.L)))
+        assert not fails and c > 0.95 * len(Qs) * w.L
+    gi, gs, _ = ix.search(Q[:300], 10, 16, table_begin=0, table_end=2)
+    _, _, res = O.search_batch(ix_o, Q[:300], 10, 16, tables=tabs)
+    c, s, fails = PT.compare_search(res, gi, gs, 10, tabs, excl)
+    assert not fails and c > 250
+    # all tables: returned scores are the FP64 inner products of the returned
+    # ids, best first
+    gi, gs = ix.search(Q, 10, 16)
+    X64 = X.astype(np.float64)
+    for i in range(0, len(Q), 97):
+        ok = gi[i] >= 0
+        s64 = X64[gi[i][ok]] @ Q[i].astype(np.float64)
+        assert np.allclose(gs[i][ok], s64, rtol=1e-6, atol=1e-7)
+        assert (np.diff(gs[i][ok]) <= 0).all()
