@@ -65,7 +65,8 @@ def test_ragged_shapes_full_parity(F):
 
 def test_large_k_and_probes_parity(F):
     X, Q = W.small_mixture(20000, 25, 48, 128, 0.15, 78)
-    _full_parity(F, X, Q, L=4, D=16, alpha=0.5, seed=6, k=100, probes_list=(128,))
+    _full_parity(F, X, Q, L=4, D=16, alpha=0.5, seed=6, k=100, probes_list=(128,),
+                 min_compared=0.7)
 
 
 def test_unfiltered_all_buckets_equals_bruteforce(F):
