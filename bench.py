@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 Falconn++ search path.
+
+One step = one batched search of the workload's whole query set through the
+hot path (projection GEMM, probe ranking, gather + bitmap dedup + exact
+scoring + top-k), with the index and the queries resident in HBM.  The probe
+budget is the smallest of the workload's sweep whose recall@10 against exact
+search reaches 0.90 (measured once, before timing, on a query sample with the
+library's own brute-force search).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+a bounded sample of the same workload instead.
+
+Multi-GPU (torchrun, N > 1): every rank is an independent replica with its
+own index and query set (query sharding, no collective on the data path), so
+the aggregate QPS is N x queries / max-over-ranks time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = ("QPS at recall@10>=0.90 on 1 GB300 (BF16 serving vs plain FP32 GPU); "
+          "p50/p99 ms; HBM GB/s")
+RECALL_TARGET = 0.90
+CALIB_QUERIES = 1000
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2.07 GHz
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="plain1m", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--probes", type=int, default=0, help="force a probe budget")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), float(d.get("bf16_tflops", 1953.4)), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash(name: str) -> str:
+    p = os.path.join(ROOT, "paper_2206_01382_gb300", "csrc", name)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def committed_traffic(kernel: str, workload: str, src: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's
+    source has not changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p)).get(f"{kernel}@{workload}")
+    except (OSError, ValueError):
+        return None
+    if not d or d.get("source_sha") != kernel_source_hash(src):
+        return None
+    return d.get("bytes_per_launch")
+
+
+def cpu_baseline(w, X, Q, P, k, n_sample=20000, max_q=100, budget_s=20.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import oracle as O
+    ix = O.build_index(X[:n_sample], w.L, w.D, w.alpha, seed=w.rot_seed)
+    t0 = time.perf_counter()
+    nq = 0
+    while nq < max_q and time.perf_counter() - t0 < budget_s:
+        O.search(ix, Q[nq], k, P)
+        nq += 1
+    dt = time.perf_counter() - t0
+    return {"value": nq / dt, "unit": "queries/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 numpy oracle: index over the first {n_sample} points "
+                      f"(L={w.L}, D={w.D}, alpha={w.alpha}), {nq} queries at {P} probes/table, k={k}"}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    X, Q = W.dataset(w)
+    P = args.probes or (16 if w.name == "plain1m" else w.probes[0])
+    import oracle as O
+    n_sample, per_step = 20000, 10
+    ix = O.build_index(X[:n_sample], w.L, w.D, w.alpha, seed=w.rot_seed)
+    qi = 0
+    for _ in range(args.warmup):
+        for _ in range(per_step):
+            O.search(ix, Q[qi % len(Q)], w.k, P)
+            qi += 1
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for _ in range(per_step):
+            O.search(ix, Q[qi % len(Q)], w.k, P)
+            qi += 1
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    qps = per_step * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "note": w.note, "probes": P, "k": w.k,
+                   "sample": f"index over the first {n_sample} points, {per_step} queries per step"},
+        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": os.cpu_count(),
+                         "kind": "oracle",
+                         "sample": f"FP64 numpy oracle, index over the first {n_sample} points, "
+                                   f"{per_step} queries per step"},
+        "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    w = W.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+    import torch
+    import paper_2206_01382_gb300 as F
+    from paper_2206_01382_gb300 import _build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    _build.build()
+    F.load()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    X, Q = W.dataset(w)
+    Xd = torch.from_numpy(X).to(dev)
+    Qd = torch.from_numpy(Q).to(dev)
+    torch.cuda.synchronize()
+    tb = time.perf_counter()
+    ix = F.Index(Xd, w.L, w.D, w.alpha, seed=w.rot_seed)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - tb
+    info = ix.info()
+
+    # probe budget: smallest of the sweep with recall@10 >= 0.90 on a sample
+    k = w.k
+    mcal = min(CALIB_QUERIES, len(Q))
+    ti, _ = F.fpp_bruteforce(Xd, Qd[:mcal], k)
+    truth = ti.cpu().numpy()
+    recalls = {}
+    chosen = None
+    for P in ([args.probes] if args.probes else list(w.probes)):
+        gi, _ = ix.search(Qd[:mcal], k, P)
+        g = gi.cpu().numpy()
+        hit = sum(len(set(a.tolist()) & set(b.tolist())) for a, b in zip(g, truth))
+        recalls[P] = hit / (k * mcal)
+        if chosen is None and recalls[P] >= RECALL_TARGET:
+            chosen = P
+    if chosen is None:
+        chosen = max(recalls, key=lambda p: recalls[p])
+    P = chosen
+    m = Q.shape[0]
+    ids = torch.empty((m, k), dtype=torch.int64, device=dev)
+    sc = torch.empty((m, k), dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    for _ in range(args.warmup):
+        F.fpp_search_ex(ix.handle, Qd, k=k, probes=P, stream=stream, ids=ids, scores=sc)
+    barrier()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    launches0 = F.fpp_launch_count()
+    phase = {"ms_project": 0.0, "ms_probe": 0.0, "ms_gather_score": 0.0}
+    tot = {"entries": 0, "unique": 0, "probes": 0, "probe_rechecks": 0, "topk_rechecks": 0,
+           "batches": 0}
+    evs[0].record(stream)
+    for s in range(args.steps):
+        _, _, st = F.fpp_search_ex(ix.handle, Qd, k=k, probes=P, stream=stream, ids=ids, scores=sc)
+        evs[s + 1].record(stream)
+        for key in phase:
+            phase[key] += st[key]
+        for key in tot:
+            tot[key] += st[key]
+    barrier()
+    launches = F.fpp_launch_count() - launches0
+    clocks = sampler.stop()
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    elapsed_ms = evs[0].elapsed_time(evs[-1])
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    qps = world * m / (ms_per_step / 1e3)
+
+    # per-phase rooflines (device time measured with CUDA events on the
+    # launching stream inside the library, summed over the timed steps)
+    hbm_peak, bf16_peak, peak_src = peaks()
+    K = args.steps
+    chunks = tot["batches"] // K
+    d = w.d
+    gather_bytes = (8 * tot["probes"] + 4 * tot["entries"] + 4 * d * tot["unique"]
+                    + (12 * k + 4 * d) * m * K)
+    gs_ms = phase["ms_gather_score"] / (chunks * K)
+    gs_gbs = gather_bytes / (chunks * K) / (gs_ms / 1e3) / 1e9
+    proj_flops = 2.0 * m * d * 2 * w.L * w.D
+    pj_ms = phase["ms_project"] / (chunks * K)
+    pj_tf = proj_flops / chunks / (pj_ms / 1e3) / 1e12
+    phases = {
+        "project": {"ms_per_launch": pj_ms, "launches_per_step": chunks, "bound": "alu",
+                    "achieved": pj_tf, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": pj_tf / FP32_SIMT_PEAK_TFLOPS},
+        "probe": {"ms_per_launch": phase["ms_probe"] / (chunks * K), "launches_per_step": chunks},
+        "gather_score": {"ms_per_launch": gs_ms, "launches_per_step": chunks, "bound": "hbm",
+                         "achieved": gs_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": gs_gbs / hbm_peak,
+                         "algorithmic_bytes_per_launch": gather_bytes / (chunks * K)},
+    }
+    dom = max(("project", "probe", "gather_score"), key=lambda p: phases[p]["ms_per_launch"])
+    if dom == "gather_score":
+        roof = {"kernel": "gather_score_kernel", "bound": "hbm", "achieved": gs_gbs,
+                "peak": hbm_peak, "unit": "GB/s", "frac": gs_gbs / hbm_peak,
+                "peak_source": peak_src + " (hbm_gbs, STREAM-style copy)",
+                "traffic": committed_traffic("gather_score_kernel", w.name, "search_kernels.cu")}
+    elif dom == "project":
+        roof = {"kernel": "sgemm_nt_kernel", "bound": "alu", "achieved": pj_tf,
+                "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": pj_tf / FP32_SIMT_PEAK_TFLOPS,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "traffic": committed_traffic("sgemm_nt_kernel", w.name, "gemm_f32.cu")}
+    else:
+        roof = {"kernel": "probe_kernel", "bound": "alu", "achieved": None, "peak": None,
+                "unit": None, "frac": None, "traffic": None}
+
+    # end to end: host (pinned) queries in, host results out, through the C ABI
+    e2e = None
+    if not args.no_e2e:
+        Qh = torch.from_numpy(Q).pin_memory()
+        ih = torch.empty((m, k), dtype=torch.int64).pin_memory()
+        sh = torch.empty((m, k), dtype=torch.float32).pin_memory()
+        F.fpp_search_ex(ix.handle, Qh, k=k, probes=P, ids=ih, scores=sh, want_stats=False)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            F.fpp_search_ex(ix.handle, Qh, k=k, probes=P, ids=ih, scores=sh, want_stats=False)
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        if dist is not None:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * m / e2e_s, "unit": "queries/s",
+               "h2d_bytes_per_step": int(m * w.d * 4), "d2h_bytes_per_step": int(m * k * 12)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, X, Q, P, k)
+
+    if rank == 0:
+        sm = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "note": w.note, "n": w.n, "d": w.d, "m": m, "L": w.L,
+                       "D": w.D, "alpha": w.alpha, "k": k, "probes": P,
+                       "recall_at_10": recalls[P], "recall_sweep": recalls,
+                       "recall_sample": mcal, "l2": "inputs larger than L2 (X is "
+                       f"{w.n * w.d * 4 / 2**20:.0f} MiB), no flush",
+                       "build_s": build_s, "index_kept_ids": info["kept_total"],
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"batch_p50": sm[len(sm) // 2], "batch_p99": sm[min(len(sm) - 1, int(0.99 * len(sm)))]},
+            "roofline": roof,
+            "phases": phases,
+            "search_stats_per_step": {kk: v / K for kk, v in tot.items()},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

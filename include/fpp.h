@@ -94,6 +94,8 @@ typedef struct fpp_search_stats {
   uint64_t probe_rechecks;    /* (query, table) probe sets re-decided in
                                  FP64-accurate arithmetic                     */
   uint64_t topk_rechecks;     /* queries whose top-k boundary was re-decided  */
+  uint64_t batches;           /* query batches the call was split into (each
+                                 batch is one launch of every search kernel)  */
   float ms_project;           /* device time per phase, milliseconds          */
   float ms_probe;
   float ms_gather_score;

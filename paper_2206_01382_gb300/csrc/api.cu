@@ -59,11 +59,12 @@ struct DevBuf {
 };
 
 struct Workspace {
-  DevBuf qpad, proj, probes, entries, kpq, ppq, out_ids, out_scores, bitmaps, stats;
+  DevBuf qpad, proj, probes, qnorm, recheck, kpq, ppq, out_ids, out_scores, bitmaps, stats;
   int64_t bitmap_words = 0;
   int slots = 0;
   void release() {
-    for (DevBuf* b : {&qpad, &proj, &probes, &entries, &kpq, &ppq, &out_ids, &out_scores, &bitmaps, &stats})
+    for (DevBuf* b : {&qpad, &proj, &probes, &qnorm, &recheck, &kpq, &ppq, &out_ids, &out_scores,
+                      &bitmaps, &stats})
       b->release();
   }
 };
@@ -440,15 +441,16 @@ fpp_status search_chunk(fpp_index* ix, const float* Q, int64_t q0, int64_t mc, c
   FPP_TRY(gemm_f32_nt(ws.qpad.as<float>(), ix->dpad, ix->R + (int64_t)2 * pl.tb * ix->D * ix->dpad,
                       ix->dpad, ws.proj.as<float>(), ldp, mc, 2ll * nt * ix->D, ix->dpad, st));
   if (ev) FPP_CUDA(cudaEventRecord(ev[1], st));
+  FPP_TRY(launch_query_norms(ws.qpad.as<float>(), mc, ix->dpad, ix->d, ws.qnorm.as<float>(), st));
   ProbeArgs pa{};
   pa.P = ws.proj.as<float>(); pa.ldp = ldp; pa.mq = mc;
-  pa.Q = ws.qpad.as<float>(); pa.ldq = ix->dpad;
+  pa.Q = ws.qpad.as<float>(); pa.ldq = ix->dpad; pa.qnorm = ws.qnorm.as<float>();
   pa.R = ix->R; pa.ldr = ix->dpad; pa.d = ix->d; pa.D = ix->D; pa.tb = pl.tb; pa.nt = nt;
   pa.rmax = ix->rmax; pa.gamma = ix->gamma;
   pa.probes_pq = ppq; pa.probes = pl.pmax;
-  pa.offsets = ix->offsets;
   pa.out = ws.probes.as<uint32_t>();
-  pa.entries = nullptr;
+  pa.recheck = ws.recheck.as<uint32_t>();
+  pa.recheck_count = reinterpret_cast<unsigned*>(ws.stats.as<unsigned long long>() + 8);
   pa.rechecks = ws.stats.as<unsigned long long>() + 6;
   FPP_TRY(launch_probe(pa, st));
   if (ev) FPP_CUDA(cudaEventRecord(ev[2], st));
@@ -460,7 +462,7 @@ fpp_status search_chunk(fpp_index* ix, const float* Q, int64_t q0, int64_t mc, c
   ga.probes_pq = ppq; ga.k_pq = kpq; ga.k = pl.k; ga.kmax = pl.kmax;
   ga.offsets = ix->offsets; ga.table_base = ix->table_base; ga.ids = ix->ids;
   ga.X = ix->X; ga.ldx = ix->dpad; ga.d = ix->d; ga.n = ix->n;
-  ga.Q = ws.qpad.as<float>(); ga.ldq = ix->dpad;
+  ga.Q = ws.qpad.as<float>(); ga.ldq = ix->dpad; ga.qnorm = ws.qnorm.as<float>();
   ga.xmax = ix->xmax; ga.gamma = ix->gamma;
   ga.bitmaps = ws.bitmaps.as<uint32_t>(); ga.bitmap_words = ws.bitmap_words; ga.slots = ws.slots;
   ga.out_ids = ids_dev; ga.out_scores = scores_dev;
@@ -487,6 +489,8 @@ fpp_status prepare_workspace(fpp_index* ix, const SearchPlan& pl, int64_t mc, bo
   if (qz && ix->dpad != ix->d) FPP_CUDA(cudaMemsetAsync(ws.qpad.p, 0, ws.qpad.bytes, st));
   FPP_TRY(ws.proj.ensure((size_t)mc * ldp * 4, false, st));
   FPP_TRY(ws.probes.ensure((size_t)mc * nt * pl.pmax * 4, false, st));
+  FPP_TRY(ws.qnorm.ensure((size_t)mc * 4, false, st));
+  FPP_TRY(ws.recheck.ensure((size_t)mc * nt * 4, false, st));
   FPP_TRY(ws.kpq.ensure((size_t)mc * 4, false, st));
   FPP_TRY(ws.ppq.ensure((size_t)mc * 4, false, st));
   FPP_TRY(ws.stats.ensure(16 * 8, true, st));
@@ -524,7 +528,8 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
   if (timing)
     for (auto& e : ev) FPP_CUDA(cudaEventCreate(&e));
   float ms[3] = {0, 0, 0};
-  for (int64_t q0 = 0; q0 < m; q0 += mc) {
+  uint64_t batches = 0;
+  for (int64_t q0 = 0; q0 < m; q0 += mc, ++batches) {
     const int64_t c = std::min<int64_t>(mc, m - q0);
     int64_t* oid = dev_out ? ids + q0 * pl.kmax : ix->ws.out_ids.as<int64_t>();
     float* osc = dev_out ? scores + q0 * pl.kmax : ix->ws.out_scores.as<float>();
@@ -561,6 +566,7 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
     stats->topk_rechecks = hs[2];
     stats->probes = hs[3];
     stats->probe_rechecks = hs[6];
+    stats->batches = batches;
     stats->ms_project = ms[0];
     stats->ms_probe = ms[1];
     stats->ms_gather_score = ms[2];

@@ -80,20 +80,22 @@ struct ProbeArgs {
   int64_t mq;
   const float* Q;            // [mq][ldq] padded queries
   int64_t ldq;
+  const float* qnorm;        // [mq] upper bounds of the query norms
   const float* R;            // [2 L D][ldr]
   int64_t ldr;
   int d, D, tb, nt;
   const float* rmax;         // [2L]
   double gamma;
   const int32_t* probes_pq;  // [mq] or NULL
-  int probes;                // scalar probes / max over queries
-  const uint32_t* offsets;   // [L][4D^2 + 1]
+  int probes;                // scalar probes / max over queries (row stride of out)
   uint32_t* out;             // [mq][nt][probes] bucket ids
-  unsigned long long* entries;   // [mq] bucket entries (accumulated) or NULL
-  unsigned long long* rechecks;  // counter or NULL
+  uint32_t* recheck;         // [mq * nt] (query, table) items for the exact pass
+  unsigned* recheck_count;   // device counter of recheck items
+  unsigned long long* rechecks;  // statistics counter or NULL
 };
 fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st);
-size_t probe_smem_bytes(int D);
+fpp_status launch_query_norms(const float* Q, int64_t m, int64_t ldq, int d, float* out,
+                              cudaStream_t st);
 
 struct GatherArgs {
   const uint32_t* probes;    // [mq][nt][pstride]
@@ -113,6 +115,7 @@ struct GatherArgs {
   int64_t n;
   const float* Q;            // [mq][ldq]
   int64_t ldq;
+  const float* qnorm;        // [mq]
   float xmax;
   double gamma;
   uint32_t* bitmaps;         // [slots][words]

@@ -20,24 +20,38 @@ constexpr unsigned FULL = 0xffffffffu;
 // the |q^T r_i| in the wedge on q's side.  A bucket (h1, h2) scores
 // v_1(h1) + v_2(h2) and the P best buckets are probed (ties: lower bucket id).
 //
-// Fast path (FP32 projections from the GEMM): the top E = min(D, P + SLACK)
-// entries of each list are extracted, the candidate pairs (a, b) with
-// (a+1)(b+1) <= P + SLACK are scored (a pair ranked a-th in list 1 and b-th
-// in list 2 is preceded by at least (a+1)(b+1) - 1 pairs, so these contain the
-// FP32 top P+1), and the top P+1 are selected.  The FP32 top-P set equals the
-// exact one when the gap between the P-th and (P+1)-th FP32 pair scores
-// exceeds twice their error bound.  Otherwise the (query, table) is re-decided
-// from compensated (FP64-accurate) projections.
+// Fast path, on the FP32 projections of the GEMM: each lane holds its S =
+// D/32 projections of a hash as packed keys in registers, sorted; the best
+// T = P + 1 entries of the list are pulled out by rounds of warp-wide max.  A
+// pair ranked a-th in list 1 and b-th in list 2 is preceded by at least
+// (a+1)(b+1) - 1 other pairs, so the pairs with (a+1)(b+1) <= P + 1 contain
+// the FP32 top P + 1; those are scored and the top P + 1 selected.  The FP32
+// top-P set is the exact one when the gap between the P-th and (P+1)-th FP32
+// pair scores exceeds twice their error bound.  Otherwise the (query, table)
+// goes on a device-side list that a second kernel re-decides from compensated
+// (FP64-accurate) projections.
 
-constexpr int PROBE_WARPS = 4;
-constexpr int SLACK = 8;
-constexpr int COLS = 1024;           // u64 slots of the selection buffer
-constexpr int SLOW_PAIRS = 1024;     // pair capacity of the slow path
-constexpr int POUT = 160;            // >= PMAX + SLACK + 1 (u64 slots)
+constexpr int PROBE_WARPS = 8;
+constexpr int PMAX = 128;
+constexpr int LIST_CAP = PMAX + 1;
 
-__host__ __device__ inline size_t probe_warp_bytes(int D) {
-  const size_t u = (size_t)16 * D > (size_t)16 * SLOW_PAIRS ? (size_t)16 * D : (size_t)16 * SLOW_PAIRS;
-  return (size_t)8 * COLS + u + (size_t)8 * POUT * 2;
+// Pair candidates with (a+1)(b+1) <= T over lists of length A (host and device).
+__host__ __device__ inline int pair_count(int T, int A) {
+  int C = 0;
+  for (int a = 0; a < A && a < T; ++a) {
+    int nb = T / (a + 1);
+    C += nb < A ? nb : A;
+  }
+  return C;
+}
+
+__host__ __device__ inline size_t probe_warp_bytes(int pmax, int D) {
+  const int T = pmax + 1;
+  const int E = T < D ? T : D;
+  const int A = (E == D) ? 2 * D : E;
+  const int C = pair_count(T, A);
+  const int Cp = ((C + 31) / 32) * 32;
+  return (size_t)2 * LIST_CAP * 8 + (size_t)Cp * 8 + (size_t)LIST_CAP * 8;
 }
 
 // Sorts each lane's column col[s*32 + lane], s < S, descending, then pulls
@@ -66,6 +80,13 @@ __device__ void warp_select(uint64_t* col, int S, int T, uint64_t* out) {
   __syncwarp();
 }
 
+// Key of a list entry: (bits(|p|) + 1) << 32 | (0xFFFFFFFF - h); larger key =
+// larger |p|, then lower wedge.  0 marks an empty slot.
+__device__ __forceinline__ uint64_t list_key(float p, uint32_t i, uint32_t D) {
+  const uint32_t h = i + (p < 0.f ? D : 0u);
+  return ((uint64_t)(__float_as_uint(fabsf(p)) + 1u) << 32) | (uint64_t)(0xFFFFFFFFu - h);
+}
+
 struct ListEntry {
   float v;
   uint32_t h;
@@ -74,19 +95,117 @@ struct ListEntry {
 // Signed-list entry a of a list whose E best |p| entries are in keys[0..E);
 // positions a >= D (available when E == D) are the antipodal wedges.
 __device__ __forceinline__ ListEntry signed_entry(const uint64_t* keys, int a, int D) {
-  ListEntry e;
-  if (a < D) {
-    const uint64_t k = keys[a];
-    e.v = key_score(k);
-    e.h = 0xFFFFFFFFu - (uint32_t)k;
-  } else {
-    const uint64_t k = keys[2 * D - 1 - a];
-    e.v = -key_score(k);
-    const uint32_t h = 0xFFFFFFFFu - (uint32_t)k;
-    e.h = h < (uint32_t)D ? h + D : h - D;
-  }
-  return e;
+  const uint64_t k = keys[a < D ? a : 2 * D - 1 - a];
+  const float v = __uint_as_float((uint32_t)(k >> 32) - 1u);
+  uint32_t h = 0xFFFFFFFFu - (uint32_t)k;
+  if (a < D) return ListEntry{v, h};
+  h = h < (uint32_t)D ? h + D : h - D;
+  return ListEntry{-v, h};
 }
+
+// Best E entries of one list into out[0..E): register-resident sorted runs of
+// S keys per lane and E rounds of warp max.
+template <int S>
+__device__ __forceinline__ void list_top(const float* __restrict__ pr, int D, int E, uint64_t* out) {
+  const int lane = threadIdx.x & 31;
+  uint64_t key[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int i = s * 32 + lane;
+    key[s] = i < D ? list_key(pr[i], (uint32_t)i, (uint32_t)D) : 0ull;
+  }
+  // bitonic sort, descending, fully unrolled (register indices are static)
+#pragma unroll
+  for (int k = 2; k <= S; k <<= 1)
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool desc = (i & k) == 0;
+          const uint64_t x = key[i], y = key[l];
+          if (desc ? (x < y) : (x > y)) { key[i] = y; key[l] = x; }
+        }
+      }
+  for (int r = 0; r < E; ++r) {
+    const uint32_t hi = (uint32_t)(key[0] >> 32), lo = (uint32_t)key[0];
+    const uint32_t mh = __reduce_max_sync(FULL, hi);
+    const uint32_t ml = __reduce_max_sync(FULL, hi == mh ? lo : 0u);
+    if (hi == mh && lo == ml) {
+#pragma unroll
+      for (int s = 0; s + 1 < S; ++s) key[s] = key[s + 1];
+      key[S - 1] = 0ull;
+    }
+    if (lane == 0) out[r] = ((uint64_t)mh << 32) | ml;
+  }
+  __syncwarp();
+}
+
+template <int S>
+__global__ void __launch_bounds__(PROBE_WARPS * 32)
+probe_kernel(ProbeArgs a, int pmax) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t w = (int64_t)blockIdx.x * PROBE_WARPS + wid;
+  if (w >= a.mq * a.nt) return;
+  const int64_t q = w / a.nt;
+  const int tl = (int)(w % a.nt);
+  const int t = a.tb + tl;
+  const int D = a.D;
+  const int P = a.probes_pq ? a.probes_pq[q] : a.probes;
+  const int64_t NB = 4ll * D * D;
+  unsigned char* wsm = smem + (size_t)wid * probe_warp_bytes(pmax, D);
+  uint64_t* lists = reinterpret_cast<uint64_t*>(wsm);            // 2 x LIST_CAP
+  uint64_t* pout = lists + 2 * LIST_CAP;                          // LIST_CAP
+  uint64_t* col = pout + LIST_CAP;                                // pairs
+
+  const int T = P + 1;
+  const int E = T < D ? T : D;
+  for (int j = 0; j < 2; ++j)
+    list_top<S>(a.P + q * a.ldp + (int64_t)(2 * tl + j) * D, D, E, lists + j * LIST_CAP);
+  const int A = (E == D) ? 2 * D : E;
+  int C = 0;
+  for (int ai = 0; ai < A && ai < T; ++ai) {
+    int nb = T / (ai + 1);
+    if (nb > A) nb = A;
+    const ListEntry x = signed_entry(lists, ai, D);
+    for (int b = lane; b < nb; b += 32) {
+      const ListEntry y = signed_entry(lists + LIST_CAP, b, D);
+      const uint32_t bucket = x.h * (uint32_t)(2 * D) + y.h;
+      col[C + b] = ((uint64_t)float_key(x.v + y.v) << 32) | (uint64_t)(0xFFFFFFFFu - bucket);
+    }
+    C += nb;
+  }
+  const int Sc = (C + 31) / 32;
+  for (int e = C + lane; e < Sc * 32; e += 32) col[e] = 0ull;
+  __syncwarp();
+  const bool boundary = (int64_t)P < NB;
+  const int Tsel = boundary ? P + 1 : P;
+  warp_select(col, Sc, Tsel, pout);
+
+  bool certain = C >= Tsel;
+  if (certain && boundary) {
+    const double sP = key_score(pout[P - 1]), sP1 = key_score(pout[P]);
+    const double qn = (double)a.qnorm[q];
+    const double eps = a.gamma * qn * ((double)a.rmax[2 * t] + (double)a.rmax[2 * t + 1]);
+    const double need = (2.0 * eps + 6.0e-8 * (fabs(sP) + fabs(sP1))) * 1.001 + 1e-30;
+    certain = (sP - sP1) > need;
+  }
+  if (certain) {
+    uint32_t* dst = a.out + (q * a.nt + tl) * (int64_t)a.probes;
+    for (int p = lane; p < P; p += 32) dst[p] = 0xFFFFFFFFu - (uint32_t)pout[p];
+  } else if (lane == 0) {
+    const unsigned slot = atomicAdd(a.recheck_count, 1u);
+    a.recheck[slot] = (uint32_t)(q * a.nt + tl);
+    if (a.rechecks) atomicAdd(a.rechecks, 1ull);
+  }
+}
+
+// ---------------------------------------------------------------- exact pass
+
+constexpr int RECHECK_WARPS = 2;
+constexpr int SLOW_PAIRS = 1024;
 
 struct DEntry {
   double v;
@@ -98,8 +217,6 @@ __device__ __forceinline__ bool dentry_before(double v1, uint32_t h1, double v2,
   return v1 > v2 || (v1 == v2 && h1 < h2);
 }
 
-// Warp argmax over one candidate per lane (v, h, lane-valid); all lanes get
-// the winner.
 __device__ __forceinline__ void warp_best(double& v, uint32_t& h) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -109,15 +226,21 @@ __device__ __forceinline__ void warp_best(double& v, uint32_t& h) {
   }
 }
 
-// Exact re-decision of one (query, table): compensated projections, then the
-// same ranking rule on FP64-accurate values, by rounds of warp argmax.
-__device__ void probe_slow(const float* q, const float* Rt /* [2][D][ldr] */, int64_t ldr, int d,
-                           int D, int P, int Tpp, unsigned char* wsm, uint32_t* bucket_out) {
+__host__ __device__ inline size_t recheck_warp_bytes(int D) {
+  const size_t dvb = (size_t)16 * D;
+  const size_t pb = (size_t)16 * SLOW_PAIRS;
+  return (size_t)2 * LIST_CAP * 16 + (dvb > pb ? dvb : pb);
+}
+
+// Re-decides the probe set of one (query, table) from compensated
+// projections, with the same ranking rule on FP64-accurate values.
+__device__ void probe_exact(const float* q, const float* Rt /* [2][D][ldr] */, int64_t ldr, int d,
+                            int D, int P, unsigned char* wsm, uint32_t* bucket_out) {
   const int lane = threadIdx.x & 31;
-  DEntry* top = reinterpret_cast<DEntry*>(wsm);                   // 2 x Tpp (<= 2 x 136 x 16 B)
-  double* dv = reinterpret_cast<double*>(wsm + (size_t)8 * COLS);  // 2 x D doubles
+  DEntry* top = reinterpret_cast<DEntry*>(wsm);                             // 2 x LIST_CAP
+  double* dv = reinterpret_cast<double*>(wsm + (size_t)2 * LIST_CAP * 16);  // 2 x D
   const int W2 = 2 * D;
-  const int E = Tpp < W2 ? Tpp : W2;
+  const int E = P < W2 ? P : W2;
   for (int j = 0; j < 2; ++j) {
     const float* Rj = Rt + (int64_t)j * D * ldr;
     for (int i = lane; i < D; i += 32) dv[j * D + i] = thread_dot2(q, Rj + (int64_t)i * ldr, d);
@@ -136,19 +259,18 @@ __device__ void probe_slow(const float* q, const float* Rt /* [2][D][ldr] */, in
       }
       warp_best(bv, bh);
       if ((int)(bh & 31) == lane) taken |= 1ull << (bh >> 5);
-      if (lane == 0) top[j * Tpp + r] = DEntry{bv, bh, 0};
+      if (lane == 0) top[j * LIST_CAP + r] = DEntry{bv, bh, 0};
     }
   }
   __syncwarp();
-  // candidate pairs, materialised over the (no longer needed) dv region
-  DEntry* pairs = reinterpret_cast<DEntry*>(dv);
+  DEntry* pairs = reinterpret_cast<DEntry*>(dv);   // dv is no longer needed
   int C = 0;
-  for (int a = 0; a < E; ++a) {
-    int nb = Tpp / (a + 1);
+  for (int ai = 0; ai < E; ++ai) {
+    int nb = P / (ai + 1);
     if (nb > E) nb = E;
     if (nb <= 0) break;
     for (int b = lane; b < nb; b += 32) {
-      const DEntry x = top[a], y = top[Tpp + b];
+      const DEntry x = top[ai], y = top[LIST_CAP + b];
       pairs[C + b] = DEntry{x.v + y.v, x.h * (uint32_t)W2 + y.h, 0};
     }
     C += nb;
@@ -164,7 +286,7 @@ __device__ void probe_slow(const float* q, const float* Rt /* [2][D][ldr] */, in
       const DEntry e = pairs[s * 32 + lane];
       if (dentry_before(e.v, e.h, bv, bh)) { bv = e.v; bh = e.h; bs = s; }
     }
-    // bucket ids of distinct pairs are distinct, so the owner is unique
+    // bucket ids of distinct pairs are distinct, so the owner lane is unique
     double wv = bv;
     uint32_t wh = bh;
     warp_best(wv, wh);
@@ -174,96 +296,35 @@ __device__ void probe_slow(const float* q, const float* Rt /* [2][D][ldr] */, in
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(PROBE_WARPS * 32)
-probe_kernel(ProbeArgs a) {
+__global__ void __launch_bounds__(RECHECK_WARPS * 32)
+probe_recheck_kernel(ProbeArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t w = (int64_t)blockIdx.x * PROBE_WARPS + wid;
-  if (w >= a.mq * a.nt) return;
-  const int64_t q = w / a.nt;
-  const int tl = (int)(w % a.nt);
-  const int t = a.tb + tl;
-  const int D = a.D;
-  const int P = a.probes_pq ? a.probes_pq[q] : a.probes;
-  const int64_t NB = 4ll * D * D;
-  unsigned char* wsm = smem + (size_t)wid * probe_warp_bytes(D);
-  uint64_t* col = reinterpret_cast<uint64_t*>(wsm);
-  uint64_t* lists = reinterpret_cast<uint64_t*>(wsm + (size_t)8 * COLS);  // 2 x D
-  uint64_t* pout = reinterpret_cast<uint64_t*>(
-      wsm + (size_t)8 * COLS + ((size_t)16 * D > (size_t)16 * SLOW_PAIRS ? (size_t)16 * D : (size_t)16 * SLOW_PAIRS));
-  uint32_t* bout = reinterpret_cast<uint32_t*>(pout + POUT);
+  const int wid = threadIdx.x >> 5;
+  unsigned char* wsm = smem + (size_t)wid * recheck_warp_bytes(a.D);
+  const unsigned cnt = *a.recheck_count;
+  for (unsigned it = blockIdx.x * RECHECK_WARPS + wid; it < cnt; it += gridDim.x * RECHECK_WARPS) {
+    const uint32_t item = a.recheck[it];
+    const int64_t q = item / a.nt;
+    const int tl = (int)(item % a.nt);
+    const int t = a.tb + tl;
+    const int P = a.probes_pq ? a.probes_pq[q] : a.probes;
+    probe_exact(a.Q + q * a.ldq, a.R + (int64_t)2 * t * a.D * a.ldr, a.ldr, a.d, a.D, P, wsm,
+                a.out + (q * a.nt + tl) * (int64_t)a.probes);
+  }
+}
 
-  const float* qv = a.Q + q * a.ldq;
-  float ss = 0.f;
-  for (int i = lane; i < a.d; i += 32) ss = fmaf(qv[i], qv[i], ss);
+__global__ void query_norms_kernel(const float* __restrict__ Q, int64_t m, int64_t ldq, int d,
+                                   float* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= m) return;
+  const float* x = Q + r * ldq;
+  float s = 0.f;
+  for (int i = lane; i < d; i += 32) s = fmaf(x[i], x[i], s);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(FULL, ss, o);
-  const double qn = (double)sqrtf(ss) * (1.0 + 1e-4 + 2e-7 * a.d);
-
-  const int Tpp = P + SLACK;
-  const int E = Tpp < D ? Tpp : D;
-  const int S = (D + 31) / 32;
-  for (int j = 0; j < 2; ++j) {
-    const float* pr = a.P + q * a.ldp + (int64_t)(2 * tl + j) * D;
-    for (int s = 0; s < S; ++s) {
-      const int i = s * 32 + lane;
-      uint64_t key = 0ull;
-      if (i < D) {
-        const float p = pr[i];
-        const uint32_t h = (uint32_t)i + (p < 0.f ? (uint32_t)D : 0u);
-        key = ((uint64_t)float_key(fabsf(p)) << 32) | (uint64_t)(0xFFFFFFFFu - h);
-      }
-      col[s * 32 + lane] = key;
-    }
-    __syncwarp();
-    warp_select(col, S, E, lists + (size_t)j * D);
-  }
-  // candidate pairs
-  const int A = (E == D) ? 2 * D : E;
-  int C = 0;
-  for (int ai = 0; ai < A && ai < Tpp; ++ai) {
-    int nb = Tpp / (ai + 1);
-    if (nb > A) nb = A;
-    const ListEntry x = signed_entry(lists, ai, D);
-    for (int b = lane; b < nb; b += 32) {
-      const ListEntry y = signed_entry(lists + D, b, D);
-      const uint32_t bucket = x.h * (uint32_t)(2 * D) + y.h;
-      col[C + b] = ((uint64_t)float_key(x.v + y.v) << 32) | (uint64_t)(0xFFFFFFFFu - bucket);
-    }
-    C += nb;
-  }
-  const int Sc = (C + 31) / 32;
-  for (int e = C + lane; e < Sc * 32; e += 32) col[e] = 0ull;
-  __syncwarp();
-  const bool boundary = (int64_t)P < NB;
-  const int Tsel = boundary ? P + 1 : P;
-  warp_select(col, Sc, Tsel, pout);
-
-  bool certain = C >= Tsel;
-  if (certain && boundary) {
-    const double sP = key_score(pout[P - 1]), sP1 = key_score(pout[P]);
-    const double eps = a.gamma * qn * ((double)a.rmax[2 * t] + (double)a.rmax[2 * t + 1]);
-    const double need = (2.0 * eps + 6.0e-8 * (fabs(sP) + fabs(sP1))) * 1.001 + 1e-30;
-    certain = (sP - sP1) > need;
-  }
-  uint32_t* dst = a.out + (q * a.nt + tl) * (int64_t)a.probes;
-  if (certain) {
-    for (int p = lane; p < P; p += 32) bout[p] = 0xFFFFFFFFu - (uint32_t)pout[p];
-  } else {
-    if (lane == 0 && a.rechecks) atomicAdd(a.rechecks, 1ull);
-    probe_slow(a.Q + q * a.ldq, a.R + (int64_t)2 * t * D * a.ldr, a.ldr, a.d, D, P, Tpp, wsm, bout);
-  }
-  __syncwarp();
-  const uint32_t* off = a.offsets + (int64_t)t * (NB + 1);
-  unsigned long long ent = 0;
-  for (int p = lane; p < P; p += 32) {
-    const uint32_t b = bout[p];
-    dst[p] = b;
-    ent += off[b + 1] - off[b];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ent += __shfl_xor_sync(FULL, ent, o);
-  if (lane == 0 && a.entries) atomicAdd(a.entries + q, ent);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+  // the FP32 sum carries relative error <= gamma_d: inflate to an upper bound
+  if (lane == 0) out[r] = sqrtf(s) * (1.f + 1e-4f + 2e-7f * d);
 }
 
 // ============================================================== gather + score
@@ -380,11 +441,7 @@ gather_score_kernel(GatherArgs a, unsigned long long* qcounter, int* err) {
     const float* qg = a.Q + q * a.ldq;
     for (int i = threadIdx.x; i < (int)a.ldq; i += blockDim.x) qs[i] = qg[i];
     __syncthreads();
-    float ss = 0.f;
-    for (int i = lane; i < a.d; i += 32) ss = fmaf(qs[i], qs[i], ss);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(FULL, ss, o);
-    const double qn = (double)sqrtf(ss) * (1.0 + 1e-4 + 2e-7 * a.d);
+    const double qn = (double)a.qnorm[q];
     const double eps_s = a.gamma * qn * (double)a.xmax;
     const double du = 5.9604644775390625e-08 * (a.d + 8);
     const double delta = 4.0 * du * du * qn * (double)a.xmax + 1e-300;
@@ -671,18 +728,53 @@ fpp_status launch_gs(const GatherArgs& a, size_t smem, int grid, unsigned long l
 
 }  // namespace
 
-size_t probe_smem_bytes(int D) { return (size_t)PROBE_WARPS * probe_warp_bytes(D); }
+template <int S>
+fpp_status launch_probe_s(const ProbeArgs& a, cudaStream_t st) {
+  const size_t smem = (size_t)PROBE_WARPS * probe_warp_bytes(a.probes, a.D);
+  FPP_CUDA(cudaFuncSetAttribute(probe_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(smem > 48 * 1024 ? smem : 48 * 1024)));
+  probe_kernel<S><<<(unsigned)ceil_div(a.mq * a.nt, PROBE_WARPS), PROBE_WARPS * 32, smem, st>>>(
+      a, a.probes);
+  FPP_LAUNCHED();
+  return FPP_OK;
+}
 
 fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st) {
   const int64_t warps = a.mq * a.nt;
   if (warps <= 0) return FPP_OK;
-  if (a.probes > 128) {
+  if (a.probes > PMAX) {
     set_error("probes per table must be <= 128");
     return FPP_EINVAL;
   }
-  const size_t smem = probe_smem_bytes(a.D);
-  FPP_CUDA(cudaFuncSetAttribute(probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  probe_kernel<<<(unsigned)ceil_div(warps, PROBE_WARPS), PROBE_WARPS * 32, smem, st>>>(a);
+  FPP_CUDA(cudaMemsetAsync(a.recheck_count, 0, sizeof(unsigned), st));
+  const int S = pow2_ceil((a.D + 31) / 32);
+  fpp_status s;
+  switch (S) {
+    case 1: s = launch_probe_s<1>(a, st); break;
+    case 2: s = launch_probe_s<2>(a, st); break;
+    case 4: s = launch_probe_s<4>(a, st); break;
+    case 8: s = launch_probe_s<8>(a, st); break;
+    case 16: s = launch_probe_s<16>(a, st); break;
+    default: s = launch_probe_s<32>(a, st); break;
+  }
+  if (s != FPP_OK) return s;
+  // exact pass over the items the fast pass could not decide; the grid is
+  // fixed and the kernel reads the item count on the device
+  const size_t smem = (size_t)RECHECK_WARPS * recheck_warp_bytes(a.D);
+  FPP_CUDA(cudaFuncSetAttribute(probe_recheck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  probe_recheck_kernel<<<sms * 2, RECHECK_WARPS * 32, smem, st>>>(a);
+  FPP_LAUNCHED();
+  return FPP_OK;
+}
+
+fpp_status launch_query_norms(const float* Q, int64_t m, int64_t ldq, int d, float* out,
+                              cudaStream_t st) {
+  if (m <= 0) return FPP_OK;
+  query_norms_kernel<<<(unsigned)ceil_div(m, 8), 256, 0, st>>>(Q, m, ldq, d, out);
   FPP_LAUNCHED();
   return FPP_OK;
 }
