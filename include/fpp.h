@@ -187,6 +187,33 @@ fpp_status fpp_bruteforce(const float* X, int64_t n, int32_t d, const float* Q,
                           int64_t m, int32_t k, int64_t* ids, float* scores,
                           void* stream);
 
+/* Exact search that allocates nothing.  The paper has no counterpart: this
+ * is for callers that cannot allocate device memory when they search, for
+ * example because their framework has already reserved the whole GPU for its
+ * own allocator, because the implicit device synchronisation of cudaMalloc
+ * and cudaFree is too costly on their path, or because they run where CUDA
+ * forbids allocation calls (such as a host function enqueued on a stream).
+ * It computes the same result as fpp_bruteforce with the same kernels, but
+ * its scratch is a file-scope device array of FPP_STATIC_SCRATCH_BYTES that
+ * every GPU which loads libfpp holds until the process exits.
+ *  - X [n][d], Q [m][d], ids [m][k], scores [m][k] must all be device memory
+ *    of the current device; d must be a multiple of 4 and X, Q 16-byte
+ *    aligned; 4 * round_up(n, 4) + 256 bytes must fit the array (n up to
+ *    8,388,544), else FPP_EINVAL with a message.  1 <= k <= 256.
+ *  - The first call on a device looks up the array's device address for that
+ *    device (cudaGetSymbolAddress, with the device current); make that first
+ *    call before any stream capture.
+ *  - All calls share the one array and each call clears what must start at
+ *    zero.  Calls that overlap on the GPU (several host threads or streams)
+ *    race on the array and must be serialised by the caller.
+ *  - The call synchronises the stream before it returns; results are then
+ *    complete.  It calls no cudaMalloc, cudaFree or allocating library
+ *    routine. */
+#define FPP_STATIC_SCRATCH_BYTES (32ull << 20)
+fpp_status fpp_bruteforce_static(const float* X, int64_t n, int32_t d, const float* Q,
+                                 int64_t m, int32_t k, int64_t* ids, float* scores,
+                                 void* stream);
+
 /* Number of kernels this process has launched through libfpp. */
 uint64_t fpp_launch_count(void);
 

@@ -103,6 +103,7 @@ def load(path: str | None = None):
         "fpp_debug_table": (ctypes.c_int, [vp, i32, vp, vp]),
         "fpp_debug_probes": (ctypes.c_int, [vp, f32p, i64, i32, i32, i32, vp]),
         "fpp_bruteforce": (ctypes.c_int, [f32p, i64, i32, f32p, i64, i32, vp, vp, vp]),
+        "fpp_bruteforce_static": (ctypes.c_int, [f32p, i64, i32, f32p, i64, i32, vp, vp, vp]),
         "fpp_launch_count": (u64, []),
     }
     for name, (res, args) in sig.items():
@@ -285,6 +286,17 @@ def fpp_bruteforce(X, Q, k: int, stream=None):
     scores = _alloc_like(Q, (m, k), "f32")
     _check(load().fpp_bruteforce(_ptr(X), X.shape[0], X.shape[1], _ptr(Q), m, k, _ptr(ids),
                                  _ptr(scores), _stream_ptr(stream)))
+    return ids, scores
+
+
+def fpp_bruteforce_static(X, Q, k: int, ids=None, scores=None, stream=None):
+    """Exact search that allocates no device memory inside the library; X, Q
+    and the outputs must be CUDA tensors (d a multiple of 4)."""
+    m = Q.shape[0]
+    ids = _alloc_like(Q, (m, k), "i64") if ids is None else ids
+    scores = _alloc_like(Q, (m, k), "f32") if scores is None else scores
+    _check(load().fpp_bruteforce_static(_ptr(X), X.shape[0], X.shape[1], _ptr(Q), m, k,
+                                        _ptr(ids), _ptr(scores), _stream_ptr(stream)))
     return ids, scores
 
 
