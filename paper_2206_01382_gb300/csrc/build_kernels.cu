@@ -76,18 +76,23 @@ build_hash_kernel(HashArgs a) {
       h[j] = i1 + (val[j] < 0.0 ? D : 0);
     } else {
       if (lane == 0 && a.rechecks) atomicAdd(a.rechecks, 1ull);
+      // every lane computes the same running argmax (rows in increasing
+      // order, strict comparison: lowest index on ties)
       double bv = -1.0, bs = 0.0;
       int bi = INT_MAX;
-      for (int i = lane; i < D; i += 32) {
-        const double v = thread_dot2(x, Rj + (int64_t)i * a.ldr, a.d);
-        if (fabs(v) > bv) { bv = fabs(v); bs = v; bi = i; }
-      }
+      const int nf4 = (int)(a.ldr / 4);
+      int i = 0;
+      for (; i + 4 <= D; i += 4) {
+        double v[4];
+        warp_dot2_rows<4>(x, Rj + (int64_t)i * a.ldr, a.ldr, nf4, v);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
-        const double s2 = __shfl_xor_sync(0xffffffffu, bs, o);
-        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (v2 > bv || (v2 == bv && i2 < bi)) { bv = v2; bs = s2; bi = i2; }
+        for (int k = 0; k < 4; ++k)
+          if (fabs(v[k]) > bv) { bv = fabs(v[k]); bs = v[k]; bi = i + k; }
+      }
+      for (; i < D; ++i) {
+        double v[1];
+        warp_dot2_rows<1>(x, Rj + (int64_t)i * a.ldr, a.ldr, nf4, v);
+        if (fabs(v[0]) > bv) { bv = fabs(v[0]); bs = v[0]; bi = i; }
       }
       val[j] = bs;
       h[j] = bi + (bs < 0.0 ? D : 0);

@@ -121,6 +121,44 @@ __device__ __forceinline__ double warp_dot2(const float* __restrict__ a,
   return ff_value(v);
 }
 
+// Warp-cooperative compensated dot products of q with NR rows r_0..r_{NR-1}
+// (row stride ldr floats); q and the rows are 16-byte aligned with nf4 float4
+// per row.  Lanes read float4 chunks (coalesced); the NR rows are in flight
+// together.  Every lane returns all NR results.
+template <int NR>
+__device__ __forceinline__ void warp_dot2_rows(const float* __restrict__ q,
+                                               const float* __restrict__ r0, int64_t ldr,
+                                               int nf4, double* out) {
+  const int lane = threadIdx.x & 31;
+  float p[NR], s[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) { p[k] = 0.f; s[k] = 0.f; }
+  const float4* q4 = reinterpret_cast<const float4*>(q);
+  for (int c = lane; c < nf4; c += 32) {
+    const float4 a = q4[c];
+    float4 b[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) b[k] = __ldg(reinterpret_cast<const float4*>(r0 + k * ldr) + c);
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      dot2_step(a.x, b[k].x, p[k], s[k]);
+      dot2_step(a.y, b[k].y, p[k], s[k]);
+      dot2_step(a.z, b[k].z, p[k], s[k]);
+      dot2_step(a.w, b[k].w, p[k], s[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    FF v{p[k], s[k]};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      FF w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+      v = ff_add(v, w);
+    }
+    out[k] = ff_value(v);
+  }
+}
+
 // Single-thread compensated dot product.
 __device__ __forceinline__ double thread_dot2(const float* __restrict__ a,
                                               const float* __restrict__ b, int n) {

@@ -204,7 +204,6 @@ probe_kernel(ProbeArgs a, int pmax) {
 
 // ---------------------------------------------------------------- exact pass
 
-constexpr int RECHECK_WARPS = 2;
 constexpr int SLOW_PAIRS = 1024;
 
 struct DEntry {
@@ -226,26 +225,17 @@ __device__ __forceinline__ void warp_best(double& v, uint32_t& h) {
   }
 }
 
-__host__ __device__ inline size_t recheck_warp_bytes(int D) {
-  const size_t dvb = (size_t)16 * D;
-  const size_t pb = (size_t)16 * SLOW_PAIRS;
-  return (size_t)2 * LIST_CAP * 16 + (dvb > pb ? dvb : pb);
-}
 
 // Re-decides the probe set of one (query, table) from compensated
-// projections, with the same ranking rule on FP64-accurate values.
-__device__ void probe_exact(const float* q, const float* Rt /* [2][D][ldr] */, int64_t ldr, int d,
-                            int D, int P, unsigned char* wsm, uint32_t* bucket_out) {
+// projections dv[2D] (computed by the whole CTA), with the same ranking rule
+// on FP64-accurate values.  Run by one warp.
+__device__ void probe_exact_select(const double* dv, int D, int P, unsigned char* wsm,
+                                   uint32_t* bucket_out) {
   const int lane = threadIdx.x & 31;
-  DEntry* top = reinterpret_cast<DEntry*>(wsm);                             // 2 x LIST_CAP
-  double* dv = reinterpret_cast<double*>(wsm + (size_t)2 * LIST_CAP * 16);  // 2 x D
+  DEntry* top = reinterpret_cast<DEntry*>(wsm);                              // 2 x LIST_CAP
+  DEntry* pairs = reinterpret_cast<DEntry*>(wsm + (size_t)2 * LIST_CAP * 16);  // SLOW_PAIRS
   const int W2 = 2 * D;
   const int E = P < W2 ? P : W2;
-  for (int j = 0; j < 2; ++j) {
-    const float* Rj = Rt + (int64_t)j * D * ldr;
-    for (int i = lane; i < D; i += 32) dv[j * D + i] = thread_dot2(q, Rj + (int64_t)i * ldr, d);
-  }
-  __syncwarp();
   for (int j = 0; j < 2; ++j) {
     uint64_t taken = 0ull;  // bit s: wedge lane + 32 s already selected
     for (int r = 0; r < E; ++r) {
@@ -263,7 +253,6 @@ __device__ void probe_exact(const float* q, const float* Rt /* [2][D][ldr] */, i
     }
   }
   __syncwarp();
-  DEntry* pairs = reinterpret_cast<DEntry*>(dv);   // dv is no longer needed
   int C = 0;
   for (int ai = 0; ai < E; ++ai) {
     int nb = P / (ai + 1);
@@ -296,20 +285,48 @@ __device__ void probe_exact(const float* q, const float* Rt /* [2][D][ldr] */, i
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(RECHECK_WARPS * 32)
+constexpr int RECHECK_THREADS = 256;
+
+__host__ __device__ inline size_t recheck_smem_bytes(int D) {
+  return (size_t)8 * 2 * D + (size_t)2 * LIST_CAP * 16 + (size_t)16 * SLOW_PAIRS;
+}
+
+// One CTA per (query, table) item of the recheck list: its warps compute the
+// 2D compensated projections (four rows in flight per warp, coalesced float4
+// loads), then warp 0 re-decides the probe set.
+__global__ void __launch_bounds__(RECHECK_THREADS)
 probe_recheck_kernel(ProbeArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int wid = threadIdx.x >> 5;
-  unsigned char* wsm = smem + (size_t)wid * recheck_warp_bytes(a.D);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = RECHECK_THREADS / 32;
+  double* dv = reinterpret_cast<double*>(smem);
+  unsigned char* wsm = smem + (size_t)8 * 2 * a.D;
   const unsigned cnt = *a.recheck_count;
-  for (unsigned it = blockIdx.x * RECHECK_WARPS + wid; it < cnt; it += gridDim.x * RECHECK_WARPS) {
+  const int rows = 2 * a.D;
+  const int nf4 = (int)(a.ldr / 4);
+  for (unsigned it = blockIdx.x; it < cnt; it += gridDim.x) {
     const uint32_t item = a.recheck[it];
     const int64_t q = item / a.nt;
     const int tl = (int)(item % a.nt);
     const int t = a.tb + tl;
     const int P = a.probes_pq ? a.probes_pq[q] : a.probes;
-    probe_exact(a.Q + q * a.ldq, a.R + (int64_t)2 * t * a.D * a.ldr, a.ldr, a.d, a.D, P, wsm,
-                a.out + (q * a.nt + tl) * (int64_t)a.probes);
+    const float* qv = a.Q + q * a.ldq;
+    const float* Rt = a.R + (int64_t)2 * t * a.D * a.ldr;
+    for (int i0 = wid * 4; i0 < rows; i0 += nw * 4) {
+      if (i0 + 4 <= rows) {
+        double v[4];
+        warp_dot2_rows<4>(qv, Rt + (int64_t)i0 * a.ldr, a.ldr, nf4, v);
+        if (lane == 0) { dv[i0] = v[0]; dv[i0 + 1] = v[1]; dv[i0 + 2] = v[2]; dv[i0 + 3] = v[3]; }
+      } else {
+        for (int i = i0; i < rows; ++i) {
+          double v[1];
+          warp_dot2_rows<1>(qv, Rt + (int64_t)i * a.ldr, a.ldr, nf4, v);
+          if (lane == 0) dv[i] = v[0];
+        }
+      }
+    }
+    __syncthreads();
+    if (wid == 0) probe_exact_select(dv, a.D, P, wsm, a.out + (q * a.nt + tl) * (int64_t)a.probes);
+    __syncthreads();
   }
 }
 
@@ -760,13 +777,13 @@ fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st) {
   if (s != FPP_OK) return s;
   // exact pass over the items the fast pass could not decide; the grid is
   // fixed and the kernel reads the item count on the device
-  const size_t smem = (size_t)RECHECK_WARPS * recheck_warp_bytes(a.D);
+  const size_t smem = recheck_smem_bytes(a.D);
   FPP_CUDA(cudaFuncSetAttribute(probe_recheck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  probe_recheck_kernel<<<sms * 2, RECHECK_WARPS * 32, smem, st>>>(a);
+  probe_recheck_kernel<<<sms * 4, RECHECK_THREADS, smem, st>>>(a);
   FPP_LAUNCHED();
   return FPP_OK;
 }
