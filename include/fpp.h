@@ -180,6 +180,17 @@ fpp_status fpp_debug_probes(const fpp_index* ix, const float* Q, int64_t m,
                             int32_t probes, int32_t table_begin, int32_t table_end,
                             uint32_t* out);
 
+/* fpp_debug_projections: the projections q^T r [m][2 L' D] of the queries
+ *   onto the random vectors of tables [table_begin, table_end) (0, 0 = all),
+ *   column (2 t' + j) D + i for table t' of the range, hash j, vector i, as
+ *   the search computes them (tensor cores, exact three-piece BF16 split).
+ * fpp_projection_error_bound: the factor c such that every such projection
+ *   is within c ||q|| ||r_i|| of the exact inner product; the search's
+ *   decisions rely on it (Section 2.2's projections, evaluated in pieces). */
+fpp_status fpp_debug_projections(const fpp_index* ix, const float* Q, int64_t m,
+                                 int32_t table_begin, int32_t table_end, float* out);
+fpp_status fpp_projection_error_bound(const fpp_index* ix, double* factor);
+
 /* Exact search: top-k of every query over all of X by inner product
  * (ground truth for recall).  Same output conventions as fpp_search.
  * stream may be NULL. */

@@ -103,6 +103,8 @@ def load(path: str | None = None):
         "fpp_debug_table": (ctypes.c_int, [vp, i32, vp, vp]),
         "fpp_debug_probes": (ctypes.c_int, [vp, f32p, i64, i32, i32, i32, vp]),
         "fpp_bruteforce": (ctypes.c_int, [f32p, i64, i32, f32p, i64, i32, vp, vp, vp]),
+        "fpp_debug_projections": (ctypes.c_int, [vp, f32p, i64, i32, i32, vp]),
+        "fpp_projection_error_bound": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
         "fpp_bruteforce_static": (ctypes.c_int, [f32p, i64, i32, f32p, i64, i32, vp, vp, vp]),
         "fpp_launch_count": (u64, []),
     }
@@ -276,6 +278,22 @@ def fpp_debug_probes(ix, Q, probes: int, table_begin: int = 0, table_end: int = 
     out = np.empty((m, te - table_begin, probes), dtype=np.uint32)
     _check(load().fpp_debug_probes(ix, _ptr(Q), m, probes, table_begin, table_end, out.ctypes.data))
     return out
+
+
+def fpp_debug_projections(ix, Q, table_begin: int = 0, table_end: int = 0) -> np.ndarray:
+    info = fpp_index_get_info(ix)
+    te = table_end or info["L"]
+    Q = _f32(Q)
+    m = Q.shape[0]
+    out = np.empty((m, 2 * (te - table_begin) * info["D"]), dtype=np.float32)
+    _check(load().fpp_debug_projections(ix, _ptr(Q), m, table_begin, table_end, out.ctypes.data))
+    return out
+
+
+def fpp_projection_error_bound(ix) -> float:
+    f = ctypes.c_double()
+    _check(load().fpp_projection_error_bound(ix, ctypes.byref(f)))
+    return f.value
 
 
 def fpp_bruteforce(X, Q, k: int, stream=None):

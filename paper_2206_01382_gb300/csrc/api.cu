@@ -59,12 +59,12 @@ struct DevBuf {
 };
 
 struct Workspace {
-  DevBuf qpad, proj, probes, qnorm, recheck, kpq, ppq, out_ids, out_scores, bitmaps, stats;
+  DevBuf qpad, qsplit, proj, probes, qnorm, recheck, kpq, ppq, out_ids, out_scores, bitmaps, stats;
   int64_t bitmap_words = 0;
   int slots = 0;
   void release() {
-    for (DevBuf* b : {&qpad, &proj, &probes, &qnorm, &recheck, &kpq, &ppq, &out_ids, &out_scores,
-                      &bitmaps, &stats})
+    for (DevBuf* b : {&qpad, &qsplit, &proj, &probes, &qnorm, &recheck, &kpq, &ppq, &out_ids,
+                      &out_scores, &bitmaps, &stats})
       b->release();
   }
 };
@@ -78,6 +78,8 @@ struct fpp_index {
   double alpha = 1.0;
   float* X = nullptr;          // [n][dpad]
   float* R = nullptr;          // [2 L D][dpad]
+  void* Rs = nullptr;          // [2 L D][3 Kp] BF16 pieces of R (tensor-core operand)
+  int Kp = 0;
   float* rmax = nullptr;       // [2L]
   float xmax = 0.f;
   uint32_t* offsets = nullptr; // [L][4D^2 + 1]
@@ -115,6 +117,7 @@ fpp_status to_device_padded(const float* src, int64_t rows, int d, int dpad, flo
 void free_index_memory(fpp_index* ix) {
   cudaFree(ix->X);
   cudaFree(ix->R);
+  cudaFree(ix->Rs);
   cudaFree(ix->rmax);
   cudaFree(ix->offsets);
   cudaFree(ix->table_base);
@@ -147,8 +150,20 @@ int sig_bits(uint64_t v) {
 
 // Builds tables [t0, t0 + nt) and appends their kept ids.
 struct BuildScratch {
-  DevBuf proj, recA, recB, counts, bstart, kstart, hist, scanbuf, scanscratch, small, rechecks;
+  DevBuf proj, xsplit, recA, recB, counts, bstart, kstart, hist, scanbuf, scanscratch, small, rechecks;
 };
+
+constexpr int kPieces = 3;   // exact three-piece BF16 split for the FP32 path
+
+// Projection of rows [r0, r0 + rc) of a padded FP32 matrix onto the random
+// vectors of tables [t0, t0 + nt): split into BF16 pieces, tensor-core GEMM.
+fpp_status project_rows(const fpp_index* ix, const float* src, int64_t rc, DevBuf& split, int t0,
+                        int nt, float* out, int64_t ldp, int* err, cudaStream_t st) {
+  FPP_TRY(split.ensure((size_t)rc * kPieces * ix->Kp * 2));
+  FPP_TRY(split_to_bf16(src, rc, ix->dpad, ix->d, kPieces, split.p, st));
+  const char* rb = static_cast<const char*>(ix->Rs) + (size_t)2 * t0 * ix->D * kPieces * ix->Kp * 2;
+  return gemm_tc(split.p, rc, rb, 2ll * nt * ix->D, ix->Kp, kPieces, out, ldp, err, st);
+}
 
 fpp_status build_tables(fpp_index* ix, int t0, int nt, BuildScratch& B, cudaStream_t st,
                         std::vector<std::pair<uint32_t*, uint64_t>>& chunks,
@@ -176,8 +191,8 @@ fpp_status build_tables(fpp_index* ix, int t0, int nt, BuildScratch& B, cudaStre
 
   for (int64_t r0 = 0; r0 < n; r0 += rows) {
     const int64_t rc = std::min<int64_t>(rows, n - r0);
-    FPP_TRY(gemm_f32_nt(ix->X + r0 * ix->dpad, ix->dpad, ix->R + (int64_t)2 * t0 * D * ix->dpad,
-                        ix->dpad, B.proj.as<float>(), ldp, rc, 2ll * nt * D, ix->dpad, st));
+    FPP_TRY(project_rows(ix, ix->X + r0 * ix->dpad, rc, B.xsplit, t0, nt, B.proj.as<float>(), ldp,
+                         reinterpret_cast<int*>(B.rechecks.as<unsigned long long>() + 1), st));
     HashArgs h{};
     h.P = B.proj.as<float>(); h.ldp = ldp; h.rows = rc; h.row0 = r0;
     h.t0 = t0; h.nt = nt; h.D = D;
@@ -247,7 +262,8 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
   ix->n = n; ix->d = d; ix->dpad = (int)round_up(d, 4);
   ix->L = p->L; ix->D = p->D; ix->iprobes = p->iprobes; ix->kappa = p->kappa;
   ix->alpha = p->alpha; ix->precision = p->precision;
-  ix->gamma = gamma_fp32(ix->dpad);
+  ix->Kp = tc_kpad(d);
+  ix->gamma = tc_error_bound_factor(ix->Kp, kPieces);
   if (cudaGetDevice(&ix->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&ix->sm_count, cudaDevAttrMultiProcessorCount, ix->device) != cudaSuccess) {
     set_error("no CUDA device");
@@ -276,6 +292,12 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
   if ((s = to_device_padded(X, n, d, ix->dpad, &ix->X, st, &ix->device_bytes)) != FPP_OK) return fail(s);
   if ((s = to_device_padded(hR.data(), rrows, d, ix->dpad, &ix->R, st, &ix->device_bytes)) != FPP_OK)
     return fail(s);
+  if (cudaMalloc(&ix->Rs, (size_t)rrows * kPieces * ix->Kp * 2) != cudaSuccess) {
+    set_error("cudaMalloc Rs");
+    return fail(FPP_ENOMEM);
+  }
+  ix->device_bytes += (uint64_t)rrows * kPieces * ix->Kp * 2;
+  if ((s = split_to_bf16(ix->R, rrows, ix->dpad, d, kPieces, ix->Rs, st)) != FPP_OK) return fail(s);
   if (cudaMalloc(&ix->rmax, 2 * L * 4) != cudaSuccess) { set_error("cudaMalloc rmax"); return fail(FPP_ENOMEM); }
   if (cudaMemcpyAsync(ix->rmax, hrmax.data(), 2 * L * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) {
     set_error("copy rmax");
@@ -306,12 +328,12 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
   std::vector<std::pair<uint32_t*, uint64_t>> chunks;
   uint64_t base = 0;
   auto cleanup = [&]() {
-    for (DevBuf* b : {&B.proj, &B.recA, &B.recB, &B.counts, &B.bstart, &B.kstart, &B.hist, &B.scanbuf,
-                      &B.scanscratch, &B.small, &B.rechecks})
+    for (DevBuf* b : {&B.proj, &B.xsplit, &B.recA, &B.recB, &B.counts, &B.bstart, &B.kstart, &B.hist,
+                      &B.scanbuf, &B.scanscratch, &B.small, &B.rechecks})
       b->release();
     for (auto& c : chunks) cudaFree(c.first);
   };
-  if ((s = B.rechecks.ensure(8, true, st)) != FPP_OK) { cleanup(); return fail(s); }
+  if ((s = B.rechecks.ensure(16, true, st)) != FPP_OK) { cleanup(); return fail(s); }
   for (int t0 = 0; t0 < L; t0 += nt_chunk) {
     const int nt = std::min(nt_chunk, L - t0);
     if ((s = build_tables(ix, t0, nt, B, st, chunks, base)) != FPP_OK) { cleanup(); return fail(s); }
@@ -338,14 +360,19 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
     cleanup();
     return fail(FPP_ECUDA);
   }
-  unsigned long long rech = 0;
-  cudaMemcpyAsync(&rech, B.rechecks.p, 8, cudaMemcpyDeviceToHost, st);
+  unsigned long long rech[2] = {0, 0};
+  cudaMemcpyAsync(rech, B.rechecks.p, 16, cudaMemcpyDeviceToHost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) {
     set_error(std::string("build: ") + cudaGetErrorString(cudaGetLastError()));
     cleanup();
     return fail(FPP_ECUDA);
   }
-  ix->build_rechecks = rech;
+  if (rech[1]) {
+    set_error("build: a bounded wait in the projection kernel ran out");
+    cleanup();
+    return fail(FPP_ETIMEOUT);
+  }
+  ix->build_rechecks = rech[0];
   cleanup();
   ix->build_ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - wall0).count();
   *out = ix;
@@ -438,8 +465,8 @@ fpp_status search_chunk(fpp_index* ix, const float* Q, int64_t q0, int64_t mc, c
     }
   }
   if (ev) FPP_CUDA(cudaEventRecord(ev[0], st));
-  FPP_TRY(gemm_f32_nt(ws.qpad.as<float>(), ix->dpad, ix->R + (int64_t)2 * pl.tb * ix->D * ix->dpad,
-                      ix->dpad, ws.proj.as<float>(), ldp, mc, 2ll * nt * ix->D, ix->dpad, st));
+  FPP_TRY(project_rows(ix, ws.qpad.as<float>(), mc, ws.qsplit, pl.tb, nt, ws.proj.as<float>(), ldp,
+                       reinterpret_cast<int*>(ws.stats.as<unsigned long long>() + 9), st));
   if (ev) FPP_CUDA(cudaEventRecord(ev[1], st));
   FPP_TRY(launch_query_norms(ws.qpad.as<float>(), mc, ix->dpad, ix->d, ws.qnorm.as<float>(), st));
   ProbeArgs pa{};
@@ -556,6 +583,14 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
       set_error("search: top-k re-check capacity exceeded");
       return FPP_EINTERNAL;
     }
+    FPP_CUDA(cudaMemcpyAsync(hs, ix->ws.stats.as<unsigned long long>() + 9, 8, cudaMemcpyDeviceToHost, st));
+    FPP_CUDA(cudaStreamSynchronize(st));
+    if (hs[0]) {
+      set_error("search: a bounded wait in the projection kernel ran out");
+      return FPP_ETIMEOUT;
+    }
+    FPP_CUDA(cudaMemcpyAsync(hs, ix->ws.stats.p, 8 * 8, cudaMemcpyDeviceToHost, st));
+    FPP_CUDA(cudaStreamSynchronize(st));
   }
   if (timing)
     for (auto& e : ev) cudaEventDestroy(e);
@@ -690,15 +725,16 @@ fpp_status fpp_debug_point_buckets(const fpp_index* cix, int32_t t, uint32_t* ou
   cudaStream_t st = 0;
   const int64_t ldp = round_up(2ll * ix->D, 4);
   const int64_t rows = std::min<int64_t>(ix->n, std::max<int64_t>(128, (1ll << 27) / ldp));
-  DevBuf proj, pb;
-  auto done = [&](fpp_status s) { proj.release(); pb.release(); return s; };
+  DevBuf proj, pb, split, err;
+  auto done = [&](fpp_status s) { proj.release(); pb.release(); split.release(); err.release(); return s; };
   fpp_status s;
+  if ((s = err.ensure(8, true, st)) != FPP_OK) return done(s);
   if ((s = proj.ensure((size_t)rows * ldp * 4)) != FPP_OK) return done(s);
   if ((s = pb.ensure((size_t)ix->n * 4)) != FPP_OK) return done(s);
   for (int64_t r0 = 0; r0 < ix->n; r0 += rows) {
     const int64_t rc = std::min<int64_t>(rows, ix->n - r0);
-    if ((s = gemm_f32_nt(ix->X + r0 * ix->dpad, ix->dpad, ix->R + (int64_t)2 * t * ix->D * ix->dpad,
-                         ix->dpad, proj.as<float>(), ldp, rc, 2ll * ix->D, ix->dpad, st)) != FPP_OK)
+    if ((s = project_rows(ix, ix->X + r0 * ix->dpad, rc, split, t, 1, proj.as<float>(), ldp,
+                          err.as<int>(), st)) != FPP_OK)
       return done(s);
     HashArgs h{};
     h.P = proj.as<float>(); h.ldp = ldp; h.rows = rc; h.row0 = r0; h.t0 = t; h.nt = 1; h.D = ix->D;
@@ -754,6 +790,46 @@ fpp_status fpp_debug_probes(const fpp_index* cix, const float* Q, int64_t m, int
     FPP_CUDA(cudaMemcpy(out + q0 * nt * probes, ix->ws.probes.p, (size_t)c * nt * probes * 4,
                         cudaMemcpyDefault));
   }
+  return FPP_OK;
+}
+
+fpp_status fpp_debug_projections(const fpp_index* cix, const float* Q, int64_t m, int32_t table_begin,
+                                 int32_t table_end, float* out) {
+  g_err.clear();
+  fpp_search_opts o;
+  fpp_default_search_opts(&o);
+  o.table_begin = table_begin;
+  o.table_end = table_end;
+  SearchPlan pl{};
+  int64_t dummy_i = 0;
+  float dummy_s = 0;
+  FPP_TRY(validate_search(cix, Q, m, &o, &dummy_i, &dummy_s, pl));
+  if (!out && m) { set_error("out is NULL"); return FPP_EINVAL; }
+  fpp_index* ix = const_cast<fpp_index*>(cix);
+  std::lock_guard<std::mutex> lock(ix->mu);
+  if (m == 0) return FPP_OK;
+  const int nt = pl.te - pl.tb;
+  const int64_t N = 2ll * nt * ix->D;
+  const int64_t ldp = round_up(N, 4);
+  const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt), m);
+  FPP_TRY(prepare_workspace(ix, pl, mc, false, 0));
+  FPP_CUDA(cudaMemset(ix->ws.stats.p, 0, 16 * 8));
+  for (int64_t q0 = 0; q0 < m; q0 += mc) {
+    const int64_t c = std::min<int64_t>(mc, m - q0);
+    FPP_CUDA(cudaMemcpy2D(ix->ws.qpad.p, ix->dpad * 4, Q + q0 * ix->d, ix->d * 4, ix->d * 4, c,
+                          cudaMemcpyDefault));
+    FPP_TRY(project_rows(ix, ix->ws.qpad.as<float>(), c, ix->ws.qsplit, pl.tb, nt,
+                         ix->ws.proj.as<float>(), ldp,
+                         reinterpret_cast<int*>(ix->ws.stats.as<unsigned long long>() + 9), 0));
+    FPP_CUDA(cudaMemcpy2D(out + q0 * N, N * 4, ix->ws.proj.p, ldp * 4, N * 4, c, cudaMemcpyDefault));
+  }
+  return FPP_OK;
+}
+
+fpp_status fpp_projection_error_bound(const fpp_index* ix, double* factor) {
+  g_err.clear();
+  if (!ix || !factor) { set_error("NULL argument"); return FPP_EINVAL; }
+  *factor = ix->gamma;
   return FPP_OK;
 }
 

@@ -21,6 +21,15 @@ struct __align__(16) Rec {
 fpp_status gemm_f32_nt(const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
                        int64_t ldc, int64_t M, int64_t N, int K, cudaStream_t st);
 
+// Tensor-core projection GEMM (gemm_tc.cu).  Operands are BF16 piece
+// arrays [rows][pieces * Kp] made by split_to_bf16; C is FP32 [M][ldc].
+int tc_kpad(int d);
+double tc_error_bound_factor(int Kp, int pieces);
+fpp_status split_to_bf16(const float* src, int64_t rows, int64_t lds, int d, int pieces,
+                         void* dst, cudaStream_t st);
+fpp_status gemm_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, int pieces,
+                   float* C, int64_t ldc, int* err, cudaStream_t st);
+
 // Build (build_kernels.cu).
 struct HashArgs {
   const float* P;        // projections [rows][ldp] for tables [t0, t0 + nt)

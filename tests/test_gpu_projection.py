@@ -1,0 +1,47 @@
+"""The tensor-core projections the search decides on stay inside the error
+bound the decisions assume, with margin: |p - q^T r| <= c ||q|| ||r||."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2206_01382_gb300 as F
+    from paper_2206_01382_gb300 import _build
+    _build.build()
+    F.load()
+    return F
+
+
+@pytest.mark.parametrize("d,D,L", [(128, 256, 3), (64, 64, 4), (30, 5, 3), (960, 64, 2), (96, 128, 2)])
+def test_projection_error_within_bound(F, d, D, L):
+    X, Q = W.small_mixture(600, 300, d, 32, 0.25, 95 + d)
+    ix = F.Index(X, L, D, 0.5, seed=40 + d)
+    P = F.fpp_debug_projections(ix.handle, Q).astype(np.float64)
+    R = O.gaussian_rotations(40 + d, L, D, d).astype(np.float64).reshape(-1, d)
+    Q64 = Q.astype(np.float64)
+    exact = Q64 @ R.T
+    c = F.fpp_projection_error_bound(ix.handle)
+    bound = c * np.linalg.norm(Q64, axis=1)[:, None] * np.linalg.norm(R, axis=1)[None, :]
+    err = np.abs(P - exact)
+    ratio = float((err / bound).max())
+    assert ratio < 0.25, f"max error / bound = {ratio}"
+    # and the split path is far more accurate than plain BF16 would be
+    assert float(err.max()) < 1e-4 * np.abs(exact).max()
+
+
+def test_projection_table_range(F):
+    X, Q = W.small_mixture(500, 20, 64, 16, 0.25, 99)
+    ix = F.Index(X, 6, 32, 0.5, seed=3)
+    full = F.fpp_debug_projections(ix.handle, Q)
+    part = F.fpp_debug_projections(ix.handle, Q, 2, 5)
+    assert np.array_equal(part, full[:, 2 * 2 * 32: 5 * 2 * 32])
