@@ -158,11 +158,21 @@ constexpr int kPieces = 3;   // exact three-piece BF16 split for the FP32 path
 // Projection of rows [r0, r0 + rc) of a padded FP32 matrix onto the random
 // vectors of tables [t0, t0 + nt): split into BF16 pieces, tensor-core GEMM.
 fpp_status project_rows(const fpp_index* ix, const float* src, int64_t rc, DevBuf& split, int t0,
-                        int nt, float* out, int64_t ldp, int* err, cudaStream_t st) {
+                        int nt, float* out, int64_t ldp, int* err, cudaStream_t st,
+                        uint64_t* lists = nullptr, int EL = 0) {
   FPP_TRY(split.ensure((size_t)rc * kPieces * ix->Kp * 2));
   FPP_TRY(split_to_bf16(src, rc, ix->dpad, ix->d, kPieces, split.p, st));
   const char* rb = static_cast<const char*>(ix->Rs) + (size_t)2 * t0 * ix->D * kPieces * ix->Kp * 2;
-  return gemm_tc(split.p, rc, rb, 2ll * nt * ix->D, ix->Kp, kPieces, out, ldp, err, st);
+  return project_tc(split.p, rc, rb, 2ll * nt * ix->D, ix->Kp, kPieces, ix->D, EL, out, ldp, lists,
+                    err, st);
+}
+
+// List length of the fused projection epilogue for a probe budget, or 0
+// when the projections must be stored (D must divide 256, and the P + 1
+// best entries of a list must lie on q's side of every hash).
+int fused_list_len(const fpp_index* ix, int pmax) {
+  if (256 % ix->D != 0 || pmax + 1 > ix->D) return 0;
+  return tc_list_len(pmax + 1);
 }
 
 fpp_status build_tables(fpp_index* ix, int t0, int nt, BuildScratch& B, cudaStream_t st,
@@ -175,7 +185,8 @@ fpp_status build_tables(fpp_index* ix, int t0, int nt, BuildScratch& B, cudaStre
   const int64_t ldp = round_up(2ll * nt * D, 4);
   int64_t rows = std::max<int64_t>(128, (1ll << 28) / ldp);
   rows = std::min<int64_t>(rows, n);
-  FPP_TRY(B.proj.ensure((size_t)rows * ldp * 4));
+  // projections (4 B per column) or the two best keys per hash (2 x 8 B per D columns)
+  FPP_TRY(B.proj.ensure(std::max((size_t)rows * ldp * 4, (size_t)rows * 2 * nt * 2 * 8)));
   FPP_TRY(B.recA.ensure((size_t)nt * n * sizeof(Rec)));
   FPP_TRY(B.recB.ensure((size_t)nt * n * sizeof(Rec)));
   FPP_TRY(B.counts.ensure((size_t)nsk * 4));
@@ -191,10 +202,13 @@ fpp_status build_tables(fpp_index* ix, int t0, int nt, BuildScratch& B, cudaStre
 
   for (int64_t r0 = 0; r0 < n; r0 += rows) {
     const int64_t rc = std::min<int64_t>(rows, n - r0);
+    const int EL = (256 % D == 0) ? 2 : 0;
     FPP_TRY(project_rows(ix, ix->X + r0 * ix->dpad, rc, B.xsplit, t0, nt, B.proj.as<float>(), ldp,
-                         reinterpret_cast<int*>(B.rechecks.as<unsigned long long>() + 1), st));
+                         reinterpret_cast<int*>(B.rechecks.as<unsigned long long>() + 1), st,
+                         EL ? B.proj.as<uint64_t>() : nullptr, EL));
     HashArgs h{};
-    h.P = B.proj.as<float>(); h.ldp = ldp; h.rows = rc; h.row0 = r0;
+    h.P = EL ? nullptr : B.proj.as<float>(); h.ldp = ldp; h.rows = rc; h.row0 = r0;
+    h.lists = EL ? B.proj.as<uint64_t>() : nullptr; h.EL = EL;
     h.t0 = t0; h.nt = nt; h.D = D;
     h.X = ix->X; h.ldx = ix->dpad; h.R = ix->R; h.ldr = ix->dpad; h.d = ix->d;
     h.rmax = ix->rmax; h.xmax = ix->xmax; h.gamma = ix->gamma; h.n = n;
@@ -465,12 +479,15 @@ fpp_status search_chunk(fpp_index* ix, const float* Q, int64_t q0, int64_t mc, c
     }
   }
   if (ev) FPP_CUDA(cudaEventRecord(ev[0], st));
+  const int EL = fused_list_len(ix, pl.pmax);
   FPP_TRY(project_rows(ix, ws.qpad.as<float>(), mc, ws.qsplit, pl.tb, nt, ws.proj.as<float>(), ldp,
-                       reinterpret_cast<int*>(ws.stats.as<unsigned long long>() + 9), st));
+                       reinterpret_cast<int*>(ws.stats.as<unsigned long long>() + 9), st,
+                       EL ? ws.proj.as<uint64_t>() : nullptr, EL));
   if (ev) FPP_CUDA(cudaEventRecord(ev[1], st));
   FPP_TRY(launch_query_norms(ws.qpad.as<float>(), mc, ix->dpad, ix->d, ws.qnorm.as<float>(), st));
   ProbeArgs pa{};
-  pa.P = ws.proj.as<float>(); pa.ldp = ldp; pa.mq = mc;
+  pa.P = EL ? nullptr : ws.proj.as<float>(); pa.ldp = ldp; pa.mq = mc;
+  pa.lists = EL ? ws.proj.as<uint64_t>() : nullptr; pa.EL = EL;
   pa.Q = ws.qpad.as<float>(); pa.ldq = ix->dpad; pa.qnorm = ws.qnorm.as<float>();
   pa.R = ix->R; pa.ldr = ix->dpad; pa.d = ix->d; pa.D = ix->D; pa.tb = pl.tb; pa.nt = nt;
   pa.rmax = ix->rmax; pa.gamma = ix->gamma;
@@ -514,7 +531,7 @@ fpp_status prepare_workspace(fpp_index* ix, const SearchPlan& pl, int64_t mc, bo
   const bool qz = ws.qpad.bytes < (size_t)mc * ix->dpad * 4;
   FPP_TRY(ws.qpad.ensure((size_t)mc * ix->dpad * 4, false, st));
   if (qz && ix->dpad != ix->d) FPP_CUDA(cudaMemsetAsync(ws.qpad.p, 0, ws.qpad.bytes, st));
-  FPP_TRY(ws.proj.ensure((size_t)mc * ldp * 4, false, st));
+  FPP_TRY(ws.proj.ensure(std::max((size_t)mc * ldp * 4, (size_t)mc * 2 * nt * 8 * 8), false, st));
   FPP_TRY(ws.probes.ensure((size_t)mc * nt * pl.pmax * 4, false, st));
   FPP_TRY(ws.qnorm.ensure((size_t)mc * 4, false, st));
   FPP_TRY(ws.recheck.ensure((size_t)mc * nt * 4, false, st));

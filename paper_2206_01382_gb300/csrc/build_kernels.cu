@@ -46,27 +46,37 @@ build_hash_kernel(HashArgs a) {
   int h[2];
   double val[2];
   for (int j = 0; j < 2; ++j) {
-    const float* pr = a.P + r * a.ldp + (int64_t)(2 * tl + j) * D;
     float b1 = -1.f, s1 = -1.f;
     int i1 = INT_MAX;
-    for (int i = lane; i < D; i += 32) {
-      const float v = fabsf(pr[i]);
-      if (v > b1) {
-        s1 = b1; b1 = v; i1 = i;
-      } else if (v > s1) {
-        s1 = v;
+    if (a.P) {
+      const float* pr = a.P + r * a.ldp + (int64_t)(2 * tl + j) * D;
+      for (int i = lane; i < D; i += 32) {
+        const float v = fabsf(pr[i]);
+        if (v > b1) {
+          s1 = b1; b1 = v; i1 = i;
+        } else if (v > s1) {
+          s1 = v;
+        }
       }
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float b2 = __shfl_xor_sync(0xffffffffu, b1, o);
-      const float s2 = __shfl_xor_sync(0xffffffffu, s1, o);
-      const int i2 = __shfl_xor_sync(0xffffffffu, i1, o);
-      if (b2 > b1 || (b2 == b1 && i2 < i1)) {
-        s1 = fmaxf(b1, s2); b1 = b2; i1 = i2;
-      } else {
-        s1 = fmaxf(s1, b2);
+      for (int o = 16; o > 0; o >>= 1) {
+        const float b2 = __shfl_xor_sync(0xffffffffu, b1, o);
+        const float s2 = __shfl_xor_sync(0xffffffffu, s1, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, i1, o);
+        if (b2 > b1 || (b2 == b1 && i2 < i1)) {
+          s1 = fmaxf(b1, s2); b1 = b2; i1 = i2;
+        } else {
+          s1 = fmaxf(s1, b2);
+        }
       }
+    } else {
+      // best two keys of the hash, kept by the projection epilogue:
+      // key = (bits(|p|) + 1) << 32 | (0xFFFFFFFF - h)
+      const uint64_t* kk = a.lists + ((r * a.nt + tl) * 2 + j) * (int64_t)a.EL;
+      const uint64_t k0 = kk[0], k1 = kk[1];
+      b1 = __uint_as_float((uint32_t)(k0 >> 32) - 1u);
+      i1 = (int)((0xFFFFFFFFu - (uint32_t)k0) % (uint32_t)D);
+      s1 = D > 1 ? __uint_as_float((uint32_t)(k1 >> 32) - 1u) : -1.f;
     }
     const float eps = (float)(a.gamma * (double)a.xmax * (double)a.rmax[2 * t + j] * (1.0 + 1e-6));
     const bool certain = (b1 - s1 > 2.f * eps) && (b1 > eps);

@@ -35,16 +35,19 @@ namespace fpp {
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64;   // BK: 64 BF16 = one 128-byte row
-constexpr int TC_STAGES = 3;
+constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 64;   // BK: 64 BF16 = one 128-byte row
+constexpr int TC_STAGES = 4;
 constexpr int TC_THREADS = 192;
-constexpr uint32_t TILE_BYTES = TC_BM * TC_BK * 2;     // 16 KB (A and B tiles alike)
+constexpr uint32_t A_TILE = TC_BM * TC_BK * 2;         // 16 KB
+constexpr uint32_t B_TILE = TC_BN * TC_BK * 2;         // 32 KB
+constexpr uint32_t STAGE_BYTES = A_TILE + B_TILE;
 constexpr long long WAIT_CYCLES = 4000000000ll;        // ~2 s at 2 GHz
 
 struct __align__(8) TcShared {
   uint64_t full[TC_STAGES];
   uint64_t empty[TC_STAGES];
-  uint64_t acc_ready;
+  uint64_t tfull[2];
+  uint64_t tempty[2];
   uint32_t tmem_base;
   int abort;
 };
@@ -112,7 +115,7 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = 128.
+// Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = 256.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
                            ((uint32_t)(TC_BM >> 4) << 24);
 
@@ -132,6 +135,10 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
   asm volatile(
@@ -149,48 +156,61 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Chunk c of the K loop: which A piece, which B piece, which 64-wide K block,
-// and which accumulator.  Exact-split order: hi.hi first (accumulator 0),
-// then hi.mid, mid.hi, hi.lo, mid.mid, lo.hi (accumulator 1).
+// Chunk c of a tile's K loop: A piece, B piece and 64-wide K block.  In the
+// exact-split mode the five next-order products (hi.mid, mid.hi, hi.lo,
+// mid.mid, lo.hi) are accumulated first and hi.hi last, into one
+// accumulator: while the small products accumulate, the partial sums (and so
+// the rounding errors) stay 2^-7 smaller than the final value, which keeps
+// the error bound of the whole sum close to that of hi.hi alone.
 __device__ __forceinline__ void chunk_pieces(int c, int nkb, int pieces, int& pa, int& pb,
-                                             int& kb, int& acc, bool& first) {
+                                             int& kb) {
   const int pair = c / nkb;
   kb = c - pair * nkb;
-  if (pieces == 1) {
-    pa = pb = 0; acc = 0; first = (kb == 0);
-    return;
+  if (pieces == 1) { pa = pb = 0; return; }
+  switch (pair) {
+    case 0: pa = 0; pb = 1; break;
+    case 1: pa = 1; pb = 0; break;
+    case 2: pa = 0; pb = 2; break;
+    case 3: pa = 1; pb = 1; break;
+    case 4: pa = 2; pb = 0; break;
+    default: pa = 0; pb = 0; break;
   }
-  const int PA[6] = {0, 0, 1, 0, 1, 2};
-  const int PB[6] = {0, 1, 0, 2, 1, 0};
-  pa = PA[pair];
-  pb = PB[pair];
-  acc = pair == 0 ? 0 : 1;
-  first = (kb == 0) && (pair <= 1);
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 2)
-tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-               float* __restrict__ C, int64_t ldc, int M, int N, int Kp, int pieces, int* err) {
+// A hash list entry is stored as the key (bits(|p|) + 1) << 32 | (0xFFFFFFFF - h)
+// with h = i for p >= 0 and i + D otherwise: a larger key is a larger |p|,
+// 0 marks an empty slot.
+
+// Persistent projection kernel.  Tiles of 128 rows x 256 columns are handed
+// out round-robin; the TMEM accumulator is double-buffered so the epilogue of
+// one tile overlaps the MMAs of the next.  EL = 0: the epilogue stores the
+// FP32 projections.  EL > 0: for every (row, hash) it keeps the EL largest
+// keys of the hash's D columns (D divides 256) and stores only those.
+template <int EL>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+               float* __restrict__ C, int64_t ldc, uint64_t* __restrict__ lists, int M, int N,
+               int Kp, int pieces, int D, int* err) {
   extern __shared__ __align__(1024) unsigned char dsm[];
-  // 1024-byte alignment of the tile ring (required by the 128-byte swizzle)
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
-  unsigned char* tilesA = base;
-  unsigned char* tilesB = base + TC_STAGES * TILE_BYTES;
-  TcShared* sh = reinterpret_cast<TcShared*>(base + 2 * TC_STAGES * TILE_BYTES);
+  TcShared* sh = reinterpret_cast<TcShared*>(base + TC_STAGES * STAGE_BYTES);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * TC_BN, m0 = blockIdx.y * TC_BM;
   const int nkb = Kp / TC_BK;
   const int nchunks = (pieces == 1 ? 1 : 6) * nkb;
-  const uint32_t ncols = pieces == 1 ? 128u : 256u;
+  const int ntn = (N + TC_BN - 1) / TC_BN, ntm = (M + TC_BM - 1) / TC_BM;
+  const int ntiles = ntn * ntm;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&sh->full[s], 1);
       mbar_init(&sh->empty[s], 1);
     }
-    mbar_init(&sh->acc_ready, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh->tfull[b], 1);
+      mbar_init(&sh->tempty[b], 4);
+    }
     sh->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -198,7 +218,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&sh->tmem_base)),
-                 "r"(ncols)
+                 "r"(512u)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -209,75 +229,136 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
-    for (int c = 0; c < nchunks; ++c) {
-      const int s = c % TC_STAGES;
-      const uint32_t round = (uint32_t)(c / TC_STAGES);
-      if (c >= TC_STAGES && !mbar_wait(&sh->empty[s], (round - 1) & 1, sh, err, 1)) break;
-      int pa, pb, kb, acc;
-      bool first;
-      chunk_pieces(c, nkb, pieces, pa, pb, kb, acc, first);
-      mbar_expect_tx(&sh->full[s], 2 * TILE_BYTES);
-      tma_load_2d(tilesA + s * TILE_BYTES, &mapA, pa * Kp + kb * TC_BK, m0, &sh->full[s]);
-      tma_load_2d(tilesB + s * TILE_BYTES, &mapB, pb * Kp + kb * TC_BK, n0, &sh->full[s]);
+    uint32_t g = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const int m0 = (t / ntn) * TC_BM, n0 = (t % ntn) * TC_BN;
+      bool ok = true;
+      for (int c = 0; c < nchunks; ++c, ++g) {
+        const uint32_t s = g % TC_STAGES;
+        if (g >= TC_STAGES && !mbar_wait(&sh->empty[s], ((g / TC_STAGES) - 1) & 1, sh, err, 1)) {
+          ok = false;
+          break;
+        }
+        int pa, pb, kb;
+        chunk_pieces(c, nkb, pieces, pa, pb, kb);
+        unsigned char* st = base + s * STAGE_BYTES;
+        mbar_expect_tx(&sh->full[s], STAGE_BYTES);
+        tma_load_2d(st, &mapA, pa * Kp + kb * TC_BK, m0, &sh->full[s]);
+        tma_load_2d(st + A_TILE, &mapB, pb * Kp + kb * TC_BK, n0, &sh->full[s]);
+      }
+      if (!ok) break;
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    for (int c = 0; c < nchunks; ++c) {
-      const int s = c % TC_STAGES;
-      const uint32_t round = (uint32_t)(c / TC_STAGES);
-      if (!mbar_wait(&sh->full[s], round & 1, sh, err, 2)) break;
+    uint32_t g = 0;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int b = i & 1;
+      if (i >= 2 && !mbar_wait(&sh->tempty[b], ((i >> 1) - 1) & 1, sh, err, 4)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      int pa, pb, kb, acc;
-      bool first;
-      chunk_pieces(c, nkb, pieces, pa, pb, kb, acc, first);
-      const uint32_t a_addr = smem_u32(tilesA + s * TILE_BYTES);
-      const uint32_t b_addr = smem_u32(tilesB + s * TILE_BYTES);
-      const uint32_t d = tmem + (uint32_t)(acc * TC_BN);
+      const uint32_t d = tmem + (uint32_t)(b * TC_BN);
+      bool ok = true;
+      for (int c = 0; c < nchunks; ++c, ++g) {
+        const uint32_t s = g % TC_STAGES;
+        if (!mbar_wait(&sh->full[s], (g / TC_STAGES) & 1, sh, err, 2)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a_addr = smem_u32(base + s * STAGE_BYTES);
+        const uint32_t b_addr = a_addr + A_TILE;
 #pragma unroll
-      for (int kk = 0; kk < TC_BK / 16; ++kk) {
-        // K step of 16 BF16 = 32 bytes inside the swizzled 128-byte row
-        mma_bf16(d, smem_desc_sw128(a_addr + kk * 32), smem_desc_sw128(b_addr + kk * 32),
-                 (first && kk == 0) ? 0u : 1u);
+        for (int kk = 0; kk < TC_BK / 16; ++kk)
+          mma_bf16(d, smem_desc_sw128(a_addr + kk * 32), smem_desc_sw128(b_addr + kk * 32),
+                   (c == 0 && kk == 0) ? 0u : 1u);
+        mma_commit(&sh->empty[s]);
       }
-      mma_commit(&sh->empty[s]);
+      mma_commit(&sh->tfull[b]);
+      if (!ok) break;
     }
-    mma_commit(&sh->acc_ready);
   } else if (warp >= 2) {
-    // ---------------- epilogue: TMEM -> registers -> global
+    // ---------------- epilogue: warp w owns TMEM lanes (rows) 32 (w mod 4) .. +31
     const int quarter = warp & 3;
-    const bool ok = mbar_wait(&sh->acc_ready, 0, sh, err, 3);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
+    const int NH = N / D;   // hashes per row (list mode)
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int b = i & 1;
+      const int m0 = (t / ntn) * TC_BM, n0 = (t % ntn) * TC_BN;
+      if (!mbar_wait(&sh->tfull[b], (i >> 1) & 1, sh, err, 3)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int row = m0 + quarter * 32 + lane;
-      const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
-      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-        float v[32];
-        tmem_ld32(lane_addr + (uint32_t)c0, v);
-        if (pieces != 1) {
-          float w[32];
-          tmem_ld32(lane_addr + (uint32_t)(TC_BN + c0), w);
+      const uint32_t taddr = tmem + (uint32_t)(b * TC_BN) + ((uint32_t)(quarter * 32) << 16);
+      if (EL == 0) {
+        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+          float v[32];
+          tmem_ld32(taddr + (uint32_t)c0, v);
+          if (row < M) {
+            float* dst = C + (int64_t)row * ldc + n0 + c0;
+            if (n0 + c0 + 32 <= N) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = __fadd_rn(v[i], w[i]);
-        }
-        if (row < M) {
-          float* dst = C + (int64_t)row * ldc + n0 + c0;
-          if (n0 + c0 + 32 <= N) {
-#pragma unroll
-            for (int i = 0; i < 32; i += 4)
-              *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-          } else {
-            for (int i = 0; i < 32; ++i)
-              if (n0 + c0 + i < N) dst[i] = v[i];
+              for (int k = 0; k < 32; k += 4)
+                *reinterpret_cast<float4*>(dst + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+            } else {
+              for (int k = 0; k < 32; ++k)
+                if (n0 + c0 + k < N) dst[k] = v[k];
+            }
           }
         }
+      } else {
+        // running top-EL of the current hash: |p| descending (earlier column
+        // first on ties) and its wedge h; a value enters only if it beats
+        // the EL-th, so almost every value costs one comparison
+        const uint32_t dmask = (uint32_t)D - 1u;   // D is a power of two dividing 256
+        float ta[EL > 0 ? EL : 1];
+        uint32_t th[EL > 0 ? EL : 1];
+#pragma unroll
+        for (int e = 0; e < EL; ++e) { ta[e] = -1.f; th[e] = 0u; }
+        auto emit = [&](int col_last) {
+          const int hg = (n0 + col_last) / D;
+          if (row < M && hg < NH) {
+            uint64_t* dst = lists + ((int64_t)row * NH + hg) * EL;
+#pragma unroll
+            for (int e = 0; e < EL; ++e)
+              dst[e] = ta[e] < 0.f ? 0ull
+                                   : (((uint64_t)(__float_as_uint(ta[e]) + 1u) << 32) |
+                                      (uint64_t)(0xFFFFFFFFu - th[e]));
+          }
+#pragma unroll
+          for (int e = 0; e < EL; ++e) ta[e] = -1.f;
+        };
+        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+          float v[32];
+          tmem_ld32(taddr + (uint32_t)c0, v);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const float av = fabsf(v[k]);
+            if (av > ta[EL - 1]) {
+              const uint32_t i_in = (uint32_t)(n0 + c0 + k) & dmask;
+              float x = av;
+              uint32_t xh = i_in + (v[k] < 0.f ? (uint32_t)D : 0u);
+#pragma unroll
+              for (int e = 0; e < EL; ++e) {
+                const bool sw = x > ta[e];
+                const float t = ta[e];
+                const uint32_t u = th[e];
+                ta[e] = sw ? x : t;
+                th[e] = sw ? xh : u;
+                x = sw ? t : x;
+                xh = sw ? u : xh;
+              }
+            }
+            if (D < 32 && (((uint32_t)(n0 + c0 + k) & dmask) == dmask)) emit(c0 + k);
+          }
+          if (D >= 32 && (((uint32_t)(n0 + c0 + 31) & dmask) == dmask)) emit(c0 + 31);
+        }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh->tempty[b]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
                  : "memory");
   }
 }
@@ -339,12 +420,15 @@ fpp_status make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t co
 int tc_kpad(int d) { return (int)round_up(d, TC_BK); }
 
 double tc_error_bound_factor(int Kp, int pieces) {
-  // Relative bound (times ||a|| ||b||) of one exact-split tensor-core
-  // projection: main accumulator 2 gamma_Kp (a factor 2 allows truncating
-  // accumulation), correction accumulator 2 gamma_{5 Kp} 2^-7, dropped
-  // products 2^-23, final addition 2^-24; plain BF16 adds the input rounding.
-  if (pieces == 1) return 2.0 * 3.90625e-3 + 2.0 * gamma_fp32(Kp) + 1.5e-5;
-  return 2.0 * gamma_fp32(Kp) * 1.01 + 2.0 * gamma_fp32(5ll * Kp) * 7.8125e-3 + 1.2e-7 + 6.0e-8;
+  // Relative bound (times ||a|| ||b||) of one tensor-core projection.
+  // Exact split: the accumulation error is at most u * (sum of partial-sum
+  // magnitudes); the 5 Kp small products keep partial sums below
+  // 2^-7 sum|a b|, the Kp main products below (1 + 2^-7) sum|a b|, so the
+  // bound is gamma_Kp (1 + 5 2^-7 + 2^-7) doubled to allow truncating
+  // accumulation, plus the dropped products (< 2^-23 |a||b|) and the BF16
+  // piece residuals.  Plain BF16: the input rounding 2 * 2^-8 dominates.
+  if (pieces == 1) return 2.0 * 3.90625e-3 + 2.0 * gamma_fp32(Kp) + 1.6e-5;
+  return 2.0 * gamma_fp32(Kp) * 1.05 + 2.0e-7;
 }
 
 fpp_status split_to_bf16(const float* src, int64_t rows, int64_t lds, int d, int pieces,
@@ -358,32 +442,72 @@ fpp_status split_to_bf16(const float* src, int64_t rows, int64_t lds, int d, int
   return FPP_OK;
 }
 
+namespace {
+
+template <int EL>
+fpp_status launch_proj(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int64_t ldc,
+                       uint64_t* lists, int64_t M, int64_t N, int Kp, int pieces, int D, int* err,
+                       cudaStream_t st) {
+  const size_t smem = 1024 + TC_STAGES * STAGE_BYTES + sizeof(TcShared);
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&]() {
+    attr_err = cudaFuncSetAttribute(tc_proj_kernel<EL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+  });
+  FPP_CUDA(attr_err);
+  int dev = 0, sms = 0;
+  FPP_CUDA(cudaGetDevice(&dev));
+  FPP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t ntiles = ceil_div(M, TC_BM) * ceil_div(N, TC_BN);
+  const int grid = (int)std::min<int64_t>(ntiles, sms);
+  tc_proj_kernel<EL><<<grid, TC_THREADS, smem, st>>>(ma, mb, C, ldc, lists, (int)M, (int)N, Kp,
+                                                     pieces, D, err);
+  FPP_LAUNCHED();
+  return FPP_OK;
+}
+
+}  // namespace
+
+int tc_list_len(int want) {
+  if (want <= 2) return 2;
+  if (want <= 4) return 4;
+  if (want <= 8) return 8;
+  return 0;
+}
+
 fpp_status gemm_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, int pieces, float* C,
                    int64_t ldc, int* err, cudaStream_t st) {
+  return project_tc(A, M, B, N, Kp, pieces, 0, 0, C, ldc, nullptr, err, st);
+}
+
+fpp_status project_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, int pieces, int D,
+                      int EL, float* C, int64_t ldc, uint64_t* lists, int* err, cudaStream_t st) {
   if (M <= 0 || N <= 0) return FPP_OK;
-  if (Kp % TC_BK || (ldc & 3) || ((uintptr_t)C & 15) || (pieces != 1 && pieces != 3)) {
-    set_error("gemm_tc: bad shape");
+  if (Kp % TC_BK || (pieces != 1 && pieces != 3) || M >= (1ll << 31) || N >= (1ll << 31)) {
+    set_error("project_tc: bad shape");
     return FPP_EINTERNAL;
   }
-  if (ceil_div(M, TC_BM) > 65535) {
-    set_error("gemm_tc: M too large for one launch");
+  if (EL == 0 && ((ldc & 3) || ((uintptr_t)C & 15))) {
+    set_error("project_tc: C must be 16-byte aligned with ldc a multiple of 4");
+    return FPP_EINTERNAL;
+  }
+  if (EL != 0 && (D < 1 || TC_BN % D != 0 || N % D != 0 || !lists)) {
+    set_error("project_tc: list mode needs D dividing 256");
     return FPP_EINTERNAL;
   }
   CUtensorMap ma, mb;
   FPP_TRY(make_map(&ma, A, M, (int64_t)pieces * Kp, TC_BM));
   FPP_TRY(make_map(&mb, B, N, (int64_t)pieces * Kp, TC_BN));
-  const size_t smem = 1024 + 2 * TC_STAGES * TILE_BYTES + sizeof(TcShared);
-  static std::once_flag attr;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr, [&]() {
-    attr_err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem);
-  });
-  FPP_CUDA(attr_err);
-  dim3 grid((unsigned)ceil_div(N, TC_BN), (unsigned)ceil_div(M, TC_BM));
-  tc_gemm_kernel<<<grid, TC_THREADS, smem, st>>>(ma, mb, C, ldc, (int)M, (int)N, Kp, pieces, err);
-  FPP_LAUNCHED();
-  return FPP_OK;
+  switch (EL) {
+    case 0: return launch_proj<0>(ma, mb, C, ldc, lists, M, N, Kp, pieces, D, err, st);
+    case 2: return launch_proj<2>(ma, mb, C, ldc, lists, M, N, Kp, pieces, D, err, st);
+    case 4: return launch_proj<4>(ma, mb, C, ldc, lists, M, N, Kp, pieces, D, err, st);
+    case 8: return launch_proj<8>(ma, mb, C, ldc, lists, M, N, Kp, pieces, D, err, st);
+    default:
+      set_error("project_tc: list length must be 0, 2, 4 or 8");
+      return FPP_EINTERNAL;
+  }
 }
 
 }  // namespace fpp

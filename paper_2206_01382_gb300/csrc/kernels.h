@@ -29,11 +29,18 @@ fpp_status split_to_bf16(const float* src, int64_t rows, int64_t lds, int d, int
                          void* dst, cudaStream_t st);
 fpp_status gemm_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, int pieces,
                    float* C, int64_t ldc, int* err, cudaStream_t st);
+// Projection with the per-(row, hash) top-EL list epilogue (EL in {2, 4, 8};
+// D must divide 256); EL = 0 stores the projections like gemm_tc.
+int tc_list_len(int want);
+fpp_status project_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, int pieces, int D,
+                      int EL, float* C, int64_t ldc, uint64_t* lists, int* err, cudaStream_t st);
 
 // Build (build_kernels.cu).
 struct HashArgs {
-  const float* P;        // projections [rows][ldp] for tables [t0, t0 + nt)
+  const float* P;        // projections [rows][ldp] for tables [t0, t0 + nt), or NULL
   int64_t ldp;
+  const uint64_t* lists; // [rows][2 nt][EL] per-hash top-EL keys (EL >= 2) when P is NULL
+  int EL;
   int64_t rows;          // points in this chunk
   int64_t row0;          // id of the chunk's first point
   int t0, nt, D;
@@ -84,8 +91,10 @@ fpp_status launch_make_offsets(const uint64_t* kstart, int nt, int64_t NB, uint3
 
 // Search (search_kernels.cu).
 struct ProbeArgs {
-  const float* P;            // [mq][ldp] query projections for tables [tb, te)
+  const float* P;            // [mq][ldp] query projections for tables [tb, te), or NULL
   int64_t ldp;
+  const uint64_t* lists;     // [mq][2 nt][EL] per-hash top-EL keys (when P is NULL)
+  int EL;
   int64_t mq;
   const float* Q;            // [mq][ldq] padded queries
   int64_t ldq;

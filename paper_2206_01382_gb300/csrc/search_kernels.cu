@@ -162,8 +162,17 @@ probe_kernel(ProbeArgs a, int pmax) {
 
   const int T = P + 1;
   const int E = T < D ? T : D;
-  for (int j = 0; j < 2; ++j)
-    list_top<S>(a.P + q * a.ldp + (int64_t)(2 * tl + j) * D, D, E, lists + j * LIST_CAP);
+  if (a.P) {
+    for (int j = 0; j < 2; ++j)
+      list_top<S>(a.P + q * a.ldp + (int64_t)(2 * tl + j) * D, D, E, lists + j * LIST_CAP);
+  } else {
+    // the projection epilogue already kept the EL >= E best keys per hash
+    for (int j = 0; j < 2; ++j) {
+      const uint64_t* src = a.lists + ((q * a.nt + tl) * 2 + j) * (int64_t)a.EL;
+      for (int e = lane; e < E; e += 32) lists[j * LIST_CAP + e] = src[e];
+    }
+    __syncwarp();
+  }
   const int A = (E == D) ? 2 * D : E;
   int C = 0;
   for (int ai = 0; ai < A && ai < T; ++ai) {
