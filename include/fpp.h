@@ -97,7 +97,8 @@ typedef struct fpp_search_stats {
   uint64_t batches;           /* query batches the call was split into (each
                                  batch is one launch of every search kernel)  */
   float ms_project;           /* device time per phase, milliseconds          */
-  float ms_probe;
+  float ms_probe;             /* fast probe ranking                            */
+  float ms_probe_exact;       /* exact re-decision of near-tie probe sets      */
   float ms_gather_score;
   float ms_total;
 } fpp_search_stats;

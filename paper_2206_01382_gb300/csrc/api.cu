@@ -59,12 +59,13 @@ struct DevBuf {
 };
 
 struct Workspace {
-  DevBuf qpad, qsplit, proj, probes, qnorm, recheck, kpq, ppq, out_ids, out_scores, bitmaps, stats;
+  DevBuf qpad, qsplit, proj, probes, qnorm, recheck, recheck2, kpq, ppq, out_ids, out_scores,
+      bitmaps, slow, stats;
   int64_t bitmap_words = 0;
   int slots = 0;
   void release() {
-    for (DevBuf* b : {&qpad, &qsplit, &proj, &probes, &qnorm, &recheck, &kpq, &ppq, &out_ids,
-                      &out_scores, &bitmaps, &stats})
+    for (DevBuf* b : {&qpad, &qsplit, &proj, &probes, &qnorm, &recheck, &recheck2, &kpq, &ppq,
+                      &out_ids, &out_scores, &bitmaps, &slow, &stats})
       b->release();
   }
 };
@@ -186,7 +187,7 @@ fpp_status build_tables(fpp_index* ix, int t0, int nt, BuildScratch& B, cudaStre
   int64_t rows = std::max<int64_t>(128, (1ll << 28) / ldp);
   rows = std::min<int64_t>(rows, n);
   // projections (4 B per column) or the two best keys per hash (2 x 8 B per D columns)
-  FPP_TRY(B.proj.ensure(std::max((size_t)rows * ldp * 4, (size_t)rows * 2 * nt * 2 * 8)));
+  FPP_TRY(B.proj.ensure(std::max((size_t)rows * ldp * 4, (size_t)rows * 2 * nt * 3 * 8)));
   FPP_TRY(B.recA.ensure((size_t)nt * n * sizeof(Rec)));
   FPP_TRY(B.recB.ensure((size_t)nt * n * sizeof(Rec)));
   FPP_TRY(B.counts.ensure((size_t)nsk * 4));
@@ -212,6 +213,7 @@ fpp_status build_tables(fpp_index* ix, int t0, int nt, BuildScratch& B, cudaStre
     h.t0 = t0; h.nt = nt; h.D = D;
     h.X = ix->X; h.ldx = ix->dpad; h.R = ix->R; h.ldr = ix->dpad; h.d = ix->d;
     h.rmax = ix->rmax; h.xmax = ix->xmax; h.gamma = ix->gamma; h.n = n;
+    h.eps_xf = (float)(ix->gamma * (double)ix->xmax * 1.0001);
     h.rec = B.recA.as<Rec>(); h.counts = B.counts.as<uint32_t>(); h.point_bucket = nullptr;
     h.rechecks = B.rechecks.as<unsigned long long>();
     FPP_TRY(launch_build_hash(h, st));
@@ -490,13 +492,15 @@ fpp_status search_chunk(fpp_index* ix, const float* Q, int64_t q0, int64_t mc, c
   pa.lists = EL ? ws.proj.as<uint64_t>() : nullptr; pa.EL = EL;
   pa.Q = ws.qpad.as<float>(); pa.ldq = ix->dpad; pa.qnorm = ws.qnorm.as<float>();
   pa.R = ix->R; pa.ldr = ix->dpad; pa.d = ix->d; pa.D = ix->D; pa.tb = pl.tb; pa.nt = nt;
-  pa.rmax = ix->rmax; pa.gamma = ix->gamma;
+  pa.rmax = ix->rmax; pa.gamma = ix->gamma; pa.gammaf = (float)(ix->gamma * 1.0001);
   pa.probes_pq = ppq; pa.probes = pl.pmax;
   pa.out = ws.probes.as<uint32_t>();
   pa.recheck = ws.recheck.as<uint32_t>();
   pa.recheck_count = reinterpret_cast<unsigned*>(ws.stats.as<unsigned long long>() + 8);
+  pa.recheck2 = ws.recheck2.as<uint32_t>();
+  pa.recheck2_count = reinterpret_cast<unsigned*>(ws.stats.as<unsigned long long>() + 8) + 1;
   pa.rechecks = ws.stats.as<unsigned long long>() + 6;
-  FPP_TRY(launch_probe(pa, st));
+  FPP_TRY(launch_probe(pa, st, ev ? ev[4] : nullptr));
   if (ev) FPP_CUDA(cudaEventRecord(ev[2], st));
   if (probes_only) return FPP_OK;
   FPP_CUDA(cudaMemsetAsync(ws.stats.as<unsigned long long>() + 4, 0, 8, st));
@@ -509,6 +513,7 @@ fpp_status search_chunk(fpp_index* ix, const float* Q, int64_t q0, int64_t mc, c
   ga.Q = ws.qpad.as<float>(); ga.ldq = ix->dpad; ga.qnorm = ws.qnorm.as<float>();
   ga.xmax = ix->xmax; ga.gamma = ix->gamma;
   ga.bitmaps = ws.bitmaps.as<uint32_t>(); ga.bitmap_words = ws.bitmap_words; ga.slots = ws.slots;
+  ga.slow_scratch = ws.slow.p;
   ga.out_ids = ids_dev; ga.out_scores = scores_dev;
   ga.stats = ws.stats.as<unsigned long long>();
   FPP_TRY(launch_gather_score(ga, st));
@@ -516,25 +521,31 @@ fpp_status search_chunk(fpp_index* ix, const float* Q, int64_t q0, int64_t mc, c
   return FPP_OK;
 }
 
-int64_t chunk_rows(const fpp_index* ix, int nt) {
-  const int64_t ldp = round_up(2ll * nt * ix->D, 4);
-  int64_t mc = (1ll << 28) / ldp;
-  mc = std::max<int64_t>(128, std::min<int64_t>(mc, 16384));
+// Queries per batch: bounded by the projection workspace (the FP32 tile, or
+// the per-hash lists in fused mode) of about 1 GB.
+int64_t chunk_rows(const fpp_index* ix, int nt, int pmax, bool allow_fused = true) {
+  const int EL = allow_fused ? fused_list_len(ix, pmax) : 0;
+  const int64_t per_query = EL ? 2ll * nt * (EL + 1) * 8 : round_up(2ll * nt * ix->D, 4) * 4;
+  int64_t mc = (1ll << 30) / per_query;
+  mc = std::max<int64_t>(128, std::min<int64_t>(mc, 65536));
   return mc;
 }
 
 fpp_status prepare_workspace(fpp_index* ix, const SearchPlan& pl, int64_t mc, bool host_out,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool allow_fused = true) {
   Workspace& ws = ix->ws;
   const int nt = pl.te - pl.tb;
   const int64_t ldp = round_up(2ll * nt * ix->D, 4);
   const bool qz = ws.qpad.bytes < (size_t)mc * ix->dpad * 4;
   FPP_TRY(ws.qpad.ensure((size_t)mc * ix->dpad * 4, false, st));
   if (qz && ix->dpad != ix->d) FPP_CUDA(cudaMemsetAsync(ws.qpad.p, 0, ws.qpad.bytes, st));
-  FPP_TRY(ws.proj.ensure(std::max((size_t)mc * ldp * 4, (size_t)mc * 2 * nt * 8 * 8), false, st));
+  const int EL = allow_fused ? fused_list_len(ix, pl.pmax) : 0;
+  const size_t tile = EL ? (size_t)mc * 2 * nt * (EL + 1) * 8 : (size_t)mc * ldp * 4;
+  FPP_TRY(ws.proj.ensure(tile, false, st));
   FPP_TRY(ws.probes.ensure((size_t)mc * nt * pl.pmax * 4, false, st));
   FPP_TRY(ws.qnorm.ensure((size_t)mc * 4, false, st));
   FPP_TRY(ws.recheck.ensure((size_t)mc * nt * 4, false, st));
+  FPP_TRY(ws.recheck2.ensure((size_t)mc * nt * 4, false, st));
   FPP_TRY(ws.kpq.ensure((size_t)mc * 4, false, st));
   FPP_TRY(ws.ppq.ensure((size_t)mc * 4, false, st));
   FPP_TRY(ws.stats.ensure(16 * 8, true, st));
@@ -547,6 +558,8 @@ fpp_status prepare_workspace(fpp_index* ix, const SearchPlan& pl, int64_t mc, bo
   if (ws.slots != slots || ws.bitmap_words != words || !ws.bitmaps.p) {
     ws.bitmaps.release();
     FPP_TRY(ws.bitmaps.ensure((size_t)slots * words * 4, true, st));
+    ws.slow.release();
+    FPP_TRY(ws.slow.ensure((size_t)slots * gather_slow_cap() * 16, false, st));
     ws.slots = slots;
     ws.bitmap_words = words;
   }
@@ -564,14 +577,14 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
   cudaStream_t st = (cudaStream_t)o->stream;
   const bool dev_out = is_device_ptr(ids) && is_device_ptr(scores);
   const int nt = pl.te - pl.tb;
-  const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt), m);
+  const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt, pl.pmax), m);
   FPP_TRY(prepare_workspace(ix, pl, mc, !dev_out, st));
   FPP_CUDA(cudaMemsetAsync(ix->ws.stats.p, 0, 16 * 8, st));
   cudaEvent_t ev[5] = {};
   bool timing = stats != nullptr;
   if (timing)
     for (auto& e : ev) FPP_CUDA(cudaEventCreate(&e));
-  float ms[3] = {0, 0, 0};
+  float ms[4] = {0, 0, 0, 0};
   uint64_t batches = 0;
   for (int64_t q0 = 0; q0 < m; q0 += mc, ++batches) {
     const int64_t c = std::min<int64_t>(mc, m - q0);
@@ -584,11 +597,12 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
     }
     if (timing) {
       FPP_CUDA(cudaEventSynchronize(ev[3]));
-      float a, b, cc;
-      cudaEventElapsedTime(&a, ev[0], ev[1]);
-      cudaEventElapsedTime(&b, ev[1], ev[2]);
-      cudaEventElapsedTime(&cc, ev[2], ev[3]);
-      ms[0] += a; ms[1] += b; ms[2] += cc;
+      float t[4];
+      cudaEventElapsedTime(&t[0], ev[0], ev[1]);
+      cudaEventElapsedTime(&t[1], ev[1], ev[4]);
+      cudaEventElapsedTime(&t[2], ev[4], ev[2]);
+      cudaEventElapsedTime(&t[3], ev[2], ev[3]);
+      for (int i = 0; i < 4; ++i) ms[i] += t[i];
     }
   }
   const bool need_sync = !dev_out || o->stream == nullptr || stats != nullptr;
@@ -621,8 +635,9 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
     stats->batches = batches;
     stats->ms_project = ms[0];
     stats->ms_probe = ms[1];
-    stats->ms_gather_score = ms[2];
-    stats->ms_total = ms[0] + ms[1] + ms[2];
+    stats->ms_probe_exact = ms[2];
+    stats->ms_gather_score = ms[3];
+    stats->ms_total = ms[0] + ms[1] + ms[2] + ms[3];
   }
   return FPP_OK;
 }
@@ -757,6 +772,7 @@ fpp_status fpp_debug_point_buckets(const fpp_index* cix, int32_t t, uint32_t* ou
     h.P = proj.as<float>(); h.ldp = ldp; h.rows = rc; h.row0 = r0; h.t0 = t; h.nt = 1; h.D = ix->D;
     h.X = ix->X; h.ldx = ix->dpad; h.R = ix->R; h.ldr = ix->dpad; h.d = ix->d;
     h.rmax = ix->rmax; h.xmax = ix->xmax; h.gamma = ix->gamma; h.n = ix->n;
+    h.eps_xf = (float)(ix->gamma * (double)ix->xmax * 1.0001);
     h.point_bucket = pb.as<uint32_t>() + r0;
     if ((s = launch_build_hash(h, st)) != FPP_OK) return done(s);
   }
@@ -799,7 +815,7 @@ fpp_status fpp_debug_probes(const fpp_index* cix, const float* Q, int64_t m, int
   std::lock_guard<std::mutex> lock(ix->mu);
   if (m == 0) return FPP_OK;
   const int nt = pl.te - pl.tb;
-  const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt), m);
+  const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt, pl.pmax), m);
   FPP_TRY(prepare_workspace(ix, pl, mc, false, 0));
   for (int64_t q0 = 0; q0 < m; q0 += mc) {
     const int64_t c = std::min<int64_t>(mc, m - q0);
@@ -828,8 +844,8 @@ fpp_status fpp_debug_projections(const fpp_index* cix, const float* Q, int64_t m
   const int nt = pl.te - pl.tb;
   const int64_t N = 2ll * nt * ix->D;
   const int64_t ldp = round_up(N, 4);
-  const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt), m);
-  FPP_TRY(prepare_workspace(ix, pl, mc, false, 0));
+  const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt, pl.pmax, false), m);
+  FPP_TRY(prepare_workspace(ix, pl, mc, false, 0, false));
   FPP_CUDA(cudaMemset(ix->ws.stats.p, 0, 16 * 8));
   for (int64_t q0 = 0; q0 < m; q0 += mc) {
     const int64_t c = std::min<int64_t>(mc, m - q0);

@@ -72,13 +72,13 @@ build_hash_kernel(HashArgs a) {
     } else {
       // best two keys of the hash, kept by the projection epilogue:
       // key = (bits(|p|) + 1) << 32 | (0xFFFFFFFF - h)
-      const uint64_t* kk = a.lists + ((r * a.nt + tl) * 2 + j) * (int64_t)a.EL;
+      const uint64_t* kk = a.lists + ((r * a.nt + tl) * 2 + j) * (int64_t)(a.EL + 1);
       const uint64_t k0 = kk[0], k1 = kk[1];
       b1 = __uint_as_float((uint32_t)(k0 >> 32) - 1u);
       i1 = (int)((0xFFFFFFFFu - (uint32_t)k0) % (uint32_t)D);
       s1 = D > 1 ? __uint_as_float((uint32_t)(k1 >> 32) - 1u) : -1.f;
     }
-    const float eps = (float)(a.gamma * (double)a.xmax * (double)a.rmax[2 * t + j] * (1.0 + 1e-6));
+    const float eps = a.eps_xf * a.rmax[2 * t + j] * 1.0001f;
     const bool certain = (b1 - s1 > 2.f * eps) && (b1 > eps);
     const float* Rj = a.R + (int64_t)(2 * t + j) * D * a.ldr;
     if (certain) {

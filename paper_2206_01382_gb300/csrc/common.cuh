@@ -159,6 +159,40 @@ __device__ __forceinline__ void warp_dot2_rows(const float* __restrict__ q,
   }
 }
 
+// Same, for NR rows at arbitrary addresses (16-byte aligned).
+template <int NR>
+__device__ __forceinline__ void warp_dot2_gather(const float* __restrict__ q,
+                                                 const float* const* rows, int nf4, double* out) {
+  const int lane = threadIdx.x & 31;
+  float p[NR], s[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) { p[k] = 0.f; s[k] = 0.f; }
+  const float4* q4 = reinterpret_cast<const float4*>(q);
+  for (int c = lane; c < nf4; c += 32) {
+    const float4 a = q4[c];
+    float4 b[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) b[k] = __ldg(reinterpret_cast<const float4*>(rows[k]) + c);
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      dot2_step(a.x, b[k].x, p[k], s[k]);
+      dot2_step(a.y, b[k].y, p[k], s[k]);
+      dot2_step(a.z, b[k].z, p[k], s[k]);
+      dot2_step(a.w, b[k].w, p[k], s[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    FF v{p[k], s[k]};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      FF w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+      v = ff_add(v, w);
+    }
+    out[k] = ff_value(v);
+  }
+}
+
 // Single-thread compensated dot product.
 __device__ __forceinline__ double thread_dot2(const float* __restrict__ a,
                                               const float* __restrict__ b, int n) {

@@ -37,7 +37,8 @@ namespace {
 
 constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 64;   // BK: 64 BF16 = one 128-byte row
 constexpr int TC_STAGES = 4;
-constexpr int TC_THREADS = 192;
+constexpr int TC_THREADS = 320;                     // 2 + 8 epilogue warps
+constexpr int EPI_WARPS = 8;
 constexpr uint32_t A_TILE = TC_BM * TC_BK * 2;         // 16 KB
 constexpr uint32_t B_TILE = TC_BN * TC_BK * 2;         // 32 KB
 constexpr uint32_t STAGE_BYTES = A_TILE + B_TILE;
@@ -50,6 +51,10 @@ struct __align__(8) TcShared {
   uint64_t tempty[2];
   uint32_t tmem_base;
   int abort;
+  // list mode with D = 256: the second column half of every row hands its
+  // partial top list (up to 8 entries and the cut) to the first half
+  float xa[4][32][9];
+  uint32_t xh[4][32][8];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -185,7 +190,8 @@ __device__ __forceinline__ void chunk_pieces(int c, int nkb, int pieces, int& pa
 // out round-robin; the TMEM accumulator is double-buffered so the epilogue of
 // one tile overlaps the MMAs of the next.  EL = 0: the epilogue stores the
 // FP32 projections.  EL > 0: for every (row, hash) it keeps the EL largest
-// keys of the hash's D columns (D divides 256) and stores only those.
+// keys of the hash's D columns (D divides 256) followed by a "cut" key whose
+// value is the largest |p| left out, and stores only those EL + 1 keys.
 template <int EL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
@@ -209,7 +215,7 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sh->tfull[b], 1);
-      mbar_init(&sh->tempty[b], 4);
+      mbar_init(&sh->tempty[b], EPI_WARPS);
     }
     sh->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -275,8 +281,11 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     }
   } else if (warp >= 2) {
     // ---------------- epilogue: warp w owns TMEM lanes (rows) 32 (w mod 4) .. +31
+    // and column half (w - 2) / 4 of every tile
     const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int NH = N / D;   // hashes per row (list mode)
+    const int LS = EL + 1;  // list stride: EL keys and the cut
     int i = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
       const int b = i & 1;
@@ -285,8 +294,9 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int row = m0 + quarter * 32 + lane;
       const uint32_t taddr = tmem + (uint32_t)(b * TC_BN) + ((uint32_t)(quarter * 32) << 16);
+      const int cbeg = half * (TC_BN / 2), cend = cbeg + TC_BN / 2;
       if (EL == 0) {
-        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+        for (int c0 = cbeg; c0 < cend; c0 += 32) {
           float v[32];
           tmem_ld32(taddr + (uint32_t)c0, v);
           if (row < M) {
@@ -304,26 +314,29 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       } else {
         // running top-EL of the current hash: |p| descending (earlier column
         // first on ties) and its wedge h; a value enters only if it beats
-        // the EL-th, so almost every value costs one comparison
+        // the EL-th; `cut` is the largest |p| that did not stay in the list
         const uint32_t dmask = (uint32_t)D - 1u;   // D is a power of two dividing 256
         float ta[EL > 0 ? EL : 1];
         uint32_t th[EL > 0 ? EL : 1];
+        float cut = -1.f;
 #pragma unroll
         for (int e = 0; e < EL; ++e) { ta[e] = -1.f; th[e] = 0u; }
         auto emit = [&](int col_last) {
           const int hg = (n0 + col_last) / D;
           if (row < M && hg < NH) {
-            uint64_t* dst = lists + ((int64_t)row * NH + hg) * EL;
+            uint64_t* dst = lists + ((int64_t)row * NH + hg) * LS;
 #pragma unroll
             for (int e = 0; e < EL; ++e)
               dst[e] = ta[e] < 0.f ? 0ull
                                    : (((uint64_t)(__float_as_uint(ta[e]) + 1u) << 32) |
                                       (uint64_t)(0xFFFFFFFFu - th[e]));
+            dst[EL] = cut < 0.f ? 0ull : ((uint64_t)(__float_as_uint(cut) + 1u) << 32);
           }
 #pragma unroll
           for (int e = 0; e < EL; ++e) ta[e] = -1.f;
+          cut = -1.f;
         };
-        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+        for (int c0 = cbeg; c0 < cend; c0 += 32) {
           float v[32];
           tmem_ld32(taddr + (uint32_t)c0, v);
 #pragma unroll
@@ -336,17 +349,53 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 #pragma unroll
               for (int e = 0; e < EL; ++e) {
                 const bool sw = x > ta[e];
-                const float t = ta[e];
+                const float tv = ta[e];
                 const uint32_t u = th[e];
-                ta[e] = sw ? x : t;
+                ta[e] = sw ? x : tv;
                 th[e] = sw ? xh : u;
-                x = sw ? t : x;
+                x = sw ? tv : x;
                 xh = sw ? u : xh;
               }
+              cut = fmaxf(cut, x);     // the entry pushed out of the list
+            } else {
+              cut = fmaxf(cut, av);
             }
             if (D < 32 && (((uint32_t)(n0 + c0 + k) & dmask) == dmask)) emit(c0 + k);
           }
-          if (D >= 32 && (((uint32_t)(n0 + c0 + 31) & dmask) == dmask)) emit(c0 + 31);
+          if (D >= 32 && D <= TC_BN / 2 && (((uint32_t)(n0 + c0 + 31) & dmask) == dmask)) emit(c0 + 31);
+        }
+        if (D == TC_BN) {
+          // the hash spans both column halves: merge the second half into the first
+          const int bA = 1 + quarter, bB = 5 + quarter;
+          if (half == 1) {
+#pragma unroll
+            for (int e = 0; e < EL; ++e) { sh->xa[quarter][lane][e] = ta[e]; sh->xh[quarter][lane][e] = th[e]; }
+            sh->xa[quarter][lane][EL] = cut;
+            asm volatile("bar.sync %0, 64;" ::"r"(bA) : "memory");
+            asm volatile("bar.sync %0, 64;" ::"r"(bB) : "memory");
+          } else {
+            asm volatile("bar.sync %0, 64;" ::"r"(bA) : "memory");
+            cut = fmaxf(cut, sh->xa[quarter][lane][EL]);
+#pragma unroll
+            for (int f = 0; f < EL; ++f) {
+              float x = sh->xa[quarter][lane][f];
+              uint32_t xh = sh->xh[quarter][lane][f];
+              if (x < 0.f) continue;
+#pragma unroll
+              for (int e = 0; e < EL; ++e) {   // strictly greater: first-half entries win ties
+                const bool sw = x > ta[e];
+                const float tv = ta[e];
+                const uint32_t u = th[e];
+                ta[e] = sw ? x : tv;
+                th[e] = sw ? xh : u;
+                x = sw ? tv : x;
+                xh = sw ? u : xh;
+              }
+              cut = fmaxf(cut, x);
+            }
+            asm volatile("bar.sync %0, 64;" ::"r"(bB) : "memory");
+            emit(TC_BN - 1);
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -39,7 +39,7 @@ fpp_status project_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp
 struct HashArgs {
   const float* P;        // projections [rows][ldp] for tables [t0, t0 + nt), or NULL
   int64_t ldp;
-  const uint64_t* lists; // [rows][2 nt][EL] per-hash top-EL keys (EL >= 2) when P is NULL
+  const uint64_t* lists; // [rows][2 nt][EL + 1] per-hash top-EL keys + cut when P is NULL
   int EL;
   int64_t rows;          // points in this chunk
   int64_t row0;          // id of the chunk's first point
@@ -51,7 +51,8 @@ struct HashArgs {
   int d;                 // true dimension (padded columns are zero)
   const float* rmax;     // [2L] max row norm per (table, hash), inflated
   float xmax;            // max point norm, inflated
-  double gamma;          // gamma_K of the projection GEMM
+  double gamma;          // error factor of the projection
+  float eps_xf;          // gamma * xmax, rounded up to FP32 with margin
   int64_t n;             // points in the index (record stride per table)
   Rec* rec;              // [nt][n] records, or NULL
   uint32_t* counts;      // [nt][4D^2] bucket sizes, or NULL
@@ -93,7 +94,7 @@ fpp_status launch_make_offsets(const uint64_t* kstart, int nt, int64_t NB, uint3
 struct ProbeArgs {
   const float* P;            // [mq][ldp] query projections for tables [tb, te), or NULL
   int64_t ldp;
-  const uint64_t* lists;     // [mq][2 nt][EL] per-hash top-EL keys (when P is NULL)
+  const uint64_t* lists;     // [mq][2 nt][EL + 1] per-hash top-EL keys and cut (P NULL)
   int EL;
   int64_t mq;
   const float* Q;            // [mq][ldq] padded queries
@@ -104,14 +105,17 @@ struct ProbeArgs {
   int d, D, tb, nt;
   const float* rmax;         // [2L]
   double gamma;
+  float gammaf;              // gamma, rounded up to FP32 with margin
   const int32_t* probes_pq;  // [mq] or NULL
   int probes;                // scalar probes / max over queries (row stride of out)
   uint32_t* out;             // [mq][nt][probes] bucket ids
   uint32_t* recheck;         // [mq * nt] (query, table) items for the exact pass
   unsigned* recheck_count;   // device counter of recheck items
+  uint32_t* recheck2;        // [mq * nt] items the window pass could not settle
+  unsigned* recheck2_count;
   unsigned long long* rechecks;  // statistics counter or NULL
 };
-fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st);
+fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_begin = nullptr);
 fpp_status launch_query_norms(const float* Q, int64_t m, int64_t ldq, int d, float* out,
                               cudaStream_t st);
 
@@ -137,6 +141,7 @@ struct GatherArgs {
   float xmax;
   double gamma;
   uint32_t* bitmaps;         // [slots][words]
+  void* slow_scratch;        // [slots][gather_slow_cap()] 16-byte entries
   int64_t bitmap_words;
   int slots;
   int64_t* out_ids;          // [mq][kmax]
@@ -145,6 +150,7 @@ struct GatherArgs {
 };
 fpp_status launch_gather_score(const GatherArgs& a, cudaStream_t st);
 int gather_slots(int sm_count);
+int gather_slow_cap();
 
 // Brute force top-k over a dense score matrix S [mq][lds] (n columns).
 fpp_status launch_topk_dense(const float* S, int64_t lds, int64_t mq, int64_t n, int k,

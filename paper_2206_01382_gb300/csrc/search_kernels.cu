@@ -168,7 +168,7 @@ probe_kernel(ProbeArgs a, int pmax) {
   } else {
     // the projection epilogue already kept the EL >= E best keys per hash
     for (int j = 0; j < 2; ++j) {
-      const uint64_t* src = a.lists + ((q * a.nt + tl) * 2 + j) * (int64_t)a.EL;
+      const uint64_t* src = a.lists + ((q * a.nt + tl) * 2 + j) * (int64_t)(a.EL + 1);
       for (int e = lane; e < E; e += 32) lists[j * LIST_CAP + e] = src[e];
     }
     __syncwarp();
@@ -195,10 +195,11 @@ probe_kernel(ProbeArgs a, int pmax) {
 
   bool certain = C >= Tsel;
   if (certain && boundary) {
-    const double sP = key_score(pout[P - 1]), sP1 = key_score(pout[P]);
-    const double qn = (double)a.qnorm[q];
-    const double eps = a.gamma * qn * ((double)a.rmax[2 * t] + (double)a.rmax[2 * t + 1]);
-    const double need = (2.0 * eps + 6.0e-8 * (fabs(sP) + fabs(sP1))) * 1.001 + 1e-30;
+    // FP32 arithmetic (the FP64 pipe is slow); every factor is positive and
+    // the 1.001 margin covers the few roundings of this expression
+    const float sP = key_score(pout[P - 1]), sP1 = key_score(pout[P]);
+    const float eps = a.gammaf * a.qnorm[q] * (a.rmax[2 * t] + a.rmax[2 * t + 1]);
+    const float need = (2.f * eps + 6.0e-8f * (fabsf(sP) + fabsf(sP1))) * 1.001f + 1e-30f;
     certain = (sP - sP1) > need;
   }
   if (certain) {
@@ -309,11 +310,12 @@ probe_recheck_kernel(ProbeArgs a) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = RECHECK_THREADS / 32;
   double* dv = reinterpret_cast<double*>(smem);
   unsigned char* wsm = smem + (size_t)8 * 2 * a.D;
-  const unsigned cnt = *a.recheck_count;
+  const unsigned cnt = a.lists ? *a.recheck2_count : *a.recheck_count;
+  const uint32_t* items = a.lists ? a.recheck2 : a.recheck;
   const int rows = 2 * a.D;
   const int nf4 = (int)(a.ldr / 4);
   for (unsigned it = blockIdx.x; it < cnt; it += gridDim.x) {
-    const uint32_t item = a.recheck[it];
+    const uint32_t item = items[it];
     const int64_t q = item / a.nt;
     const int tl = (int)(item % a.nt);
     const int t = a.tb + tl;
@@ -339,6 +341,99 @@ probe_recheck_kernel(ProbeArgs a) {
   }
 }
 
+// Window pass (list mode): a (query, table) whose FP32 probe boundary was
+// inside the error bound is usually settled by recomputing only the list
+// entries that can still be among the P best of their hash.  For hash j with
+// FP32 list values v_0 >= v_1 >= ..., every entry whose exact |q^T r| could
+// reach the exact P-th largest has v >= v_{P-1} - 2 eps_j; if the largest
+// value left out of the list (its cut) is already below that, all
+// candidates are in the list.  Their
+// compensated projections then decide the P best entries of each hash and
+// the P best pairs exactly; otherwise the item goes to the full pass.
+constexpr int WIN_MAX = 8;
+
+__global__ void __launch_bounds__(256)
+probe_window_kernel(ProbeArgs a) {
+  const int lane = threadIdx.x & 31;
+  const unsigned cnt = *a.recheck_count;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int nf4 = (int)(a.ldr / 4);
+  for (unsigned it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < cnt; it += nwarps) {
+    const uint32_t item = a.recheck[it];
+    const int64_t q = item / a.nt;
+    const int tl = (int)(item % a.nt);
+    const int t = a.tb + tl;
+    const int P = a.probes_pq ? a.probes_pq[q] : a.probes;
+    const int D = a.D;
+    const double qn = (double)a.qnorm[q];
+    bool ok = P <= a.EL;
+    int ncand[2] = {0, 0};
+    uint32_t hh[2][WIN_MAX];
+    for (int j = 0; j < 2 && ok; ++j) {
+      const uint64_t* L = a.lists + ((q * a.nt + tl) * 2 + j) * (int64_t)(a.EL + 1);
+      const double eps = a.gamma * qn * (double)a.rmax[2 * t + j] * (1.0 + 1e-6);
+      auto val = [&](uint64_t k) { return k ? (double)__uint_as_float((uint32_t)(k >> 32) - 1u) : -1.0; };
+      const double lim = val(L[P - 1]) - 2.0 * eps;
+      if (!(val(L[a.EL]) < lim)) { ok = false; break; }   // L[EL]: largest |p| left out
+      for (int e = 0; e < a.EL && e < WIN_MAX; ++e)
+        if (L[e] && val(L[e]) >= lim) hh[j][ncand[j]++] = 0xFFFFFFFFu - (uint32_t)L[e];
+    }
+    if (!ok) {
+      if (lane == 0) a.recheck2[atomicAdd(a.recheck2_count, 1u)] = item;
+      continue;
+    }
+    // exact projections of the candidates
+    double ev[2][WIN_MAX];
+    const float* qv = a.Q + q * a.ldq;
+    for (int j = 0; j < 2; ++j) {
+      const float* rows[WIN_MAX];
+#pragma unroll
+      for (int e = 0; e < WIN_MAX; ++e) {
+        const uint32_t i = hh[j][e < ncand[j] ? e : 0] % (uint32_t)D;
+        rows[e] = a.R + ((int64_t)(2 * t + j) * D + i) * a.ldr;
+      }
+      warp_dot2_gather<WIN_MAX>(qv, rows, nf4, ev[j]);
+    }
+    if (lane == 0) {
+      // exact lists: (|v|, wedge) of the candidates, best first
+      double av[2][WIN_MAX];
+      uint32_t wh[2][WIN_MAX];
+      for (int j = 0; j < 2; ++j) {
+        for (int e = 0; e < ncand[j]; ++e) {
+          const uint32_t i = hh[j][e] % (uint32_t)D;
+          av[j][e] = fabs(ev[j][e]);
+          wh[j][e] = i + (ev[j][e] < 0.0 ? (uint32_t)D : 0u);
+        }
+        for (int x = 1; x < ncand[j]; ++x)   // insertion sort (at most 8 entries)
+          for (int y = x; y > 0 && dentry_before(av[j][y], wh[j][y], av[j][y - 1], wh[j][y - 1]); --y) {
+            const double tv = av[j][y]; av[j][y] = av[j][y - 1]; av[j][y - 1] = tv;
+            const uint32_t tw = wh[j][y]; wh[j][y] = wh[j][y - 1]; wh[j][y - 1] = tw;
+          }
+      }
+      // the P best pairs: candidates (a+1)(b+1) <= P, P < 8
+      double ps[WIN_MAX * 4];
+      uint32_t pb[WIN_MAX * 4];
+      int C = 0;
+      for (int x = 0; x < P && x < ncand[0]; ++x)
+        for (int y = 0; (x + 1) * (y + 1) <= P && y < ncand[1]; ++y) {
+          ps[C] = av[0][x] + av[1][y];
+          pb[C] = wh[0][x] * (uint32_t)(2 * D) + wh[1][y];
+          ++C;
+        }
+      uint32_t* dst = a.out + (q * a.nt + tl) * (int64_t)a.probes;
+      for (int r = 0; r < P; ++r) {
+        int best = r;
+        for (int c = r + 1; c < C; ++c)
+          if (dentry_before(ps[c], pb[c], ps[best], pb[best])) best = c;
+        const double tv = ps[r]; ps[r] = ps[best]; ps[best] = tv;
+        const uint32_t tb = pb[r]; pb[r] = pb[best]; pb[best] = tb;
+        dst[r] = pb[r];
+      }
+    }
+    __syncwarp();
+  }
+}
+
 __global__ void query_norms_kernel(const float* __restrict__ Q, int64_t m, int64_t ldq, int d,
                                    float* __restrict__ out) {
   const int lane = threadIdx.x & 31;
@@ -355,276 +450,421 @@ __global__ void query_norms_kernel(const float* __restrict__ Q, int64_t m, int64
 
 // ============================================================== gather + score
 //
-// One CTA per query at a time (queries handed out by an atomic counter).
-// Phase 1: warps walk the probed buckets; each kept id is test-and-set in the
-// CTA's bitmap (n bits, in global memory, L2-resident), so every distinct
-// candidate is scored exactly once, with coalesced float4 row loads, and
-// offered to the warp's running top-K' (K' = k + 16).  Phase 2: the warps'
-// lists are merged and the best K' are re-scored with the compensated dot
-// product; the FP32 pre-selection is exact unless the K'-th FP32 score lies
-// within the FP32 error bound of the k-th re-scored one, in which case the
-// buckets are walked again and every candidate that could still reach the
-// top-k is re-scored.  Phase 3: the buckets are walked again to clear the
-// bitmap words that were touched.
+// A CTA runs NG independent queries at a time, one per group of GW warps
+// (queries are handed out by an atomic counter; groups synchronise with their
+// own named barrier, never with the whole CTA).  For its query a group:
+//  1. resolves the probed buckets together: their (start, size) pairs are
+//     read in parallel and prefix-summed, so the flattened bucket entries can
+//     be spread over the group's threads (binary search per entry);
+//  2. test-and-sets every kept id in the group's bitmap (n bits in global
+//     memory, L2-resident; one bitmap per group slot), collects the ids seen
+//     for the first time and scores them in batches, each warp taking up to
+//     32 rows at a time with coalesced float4 loads (G lanes per row), each
+//     warp keeping a running top-K' (K' = k + 16);
+//  3. merges the warps' lists and re-scores the best K' with the
+//     compensated dot product; the FP32 pre-selection is exact unless the
+//     K'-th FP32 score lies within the FP32 error bound of the k-th re-scored
+//     one, in which case the buckets are walked again and every candidate
+//     that could still reach the top-k is re-scored;
+//  4. walks the buckets once more to clear the bitmap words it touched.
 
-constexpr int GS_WARPS = 8;
-constexpr int SLOW_CAP = 2048;
+constexpr int GW = 1;                          // warps per query group
+constexpr int NG = 8;                          // query groups per CTA
+constexpr int GT = GW * 32;                    // threads per group
+constexpr int GS_THREADS = NG * GT;
+constexpr int SLOW_CAP = 2048;                 // slow-path list (global scratch, per slot)
 constexpr int KSLACK = 16;
+constexpr int PCHUNK = 128;                    // probed buckets resolved per pass
+constexpr int PPT = PCHUNK / GT;               // buckets per thread per pass
+constexpr int EPT = 8;                         // entries per thread per round
+constexpr int ROUND = GT * EPT;                // entries examined per round
+constexpr int CAND_CAP = 2 * ROUND;            // candidate ids buffered before scoring
 
 struct GSLayout {
   int kp, cap, mcap, rcap;
-  size_t q_off, queue_off, wtop_off, merge_off, resc_off, total;
+  size_t q_off, pbase_off, pstart_off, cand_off, wtop_off, merge_off, resc_off, group;
+  size_t total;
 };
 
 __host__ __device__ inline GSLayout gs_layout(int kmax, int ldq) {
   GSLayout L;
   L.kp = kmax + KSLACK;
   L.cap = pow2_ceil(2 * L.kp + 32);
-  L.mcap = pow2_ceil(GS_WARPS * L.kp);
+  L.mcap = pow2_ceil(GW * L.kp);
   L.rcap = pow2_ceil(L.kp);
   size_t o = 0;
   L.q_off = o; o += (size_t)4 * ldq; o = (o + 15) & ~(size_t)15;
-  L.queue_off = o; o += (size_t)GS_WARPS * 64 * 4;
-  L.wtop_off = o; o += (size_t)GS_WARPS * L.cap * 8;
-  L.merge_off = o;
-  {
-    size_t mb = (size_t)L.mcap * 8;
-    if (mb < (size_t)SLOW_CAP * 16) mb = (size_t)SLOW_CAP * 16;
-    o += mb;
-  }
+  L.pbase_off = o; o += (size_t)8 * PCHUNK;
+  L.pstart_off = o; o += (size_t)4 * (PCHUNK + 1); o = (o + 15) & ~(size_t)15;
+  L.cand_off = o; o += (size_t)4 * CAND_CAP;
+  L.wtop_off = o; o += (size_t)GW * L.cap * 8;
+  L.merge_off = o; o += (size_t)L.mcap * 8;
   L.resc_off = o; o += (size_t)L.rcap * 16;
-  L.total = o;
+  o = (o + 15) & ~(size_t)15;
+  L.group = o;
+  L.total = o * NG;
   return L;
 }
 
-// Scores up to 32 queued rows against q (FP32, coalesced float4 loads, G lanes
-// per row) and hands each (score, id) to emit(lane_valid, score, id).
+__device__ __forceinline__ void group_sync(int g) {
+  if (GW == 1) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(GT) : "memory");
+  }
+}
+
+// Scores up to 32 rows ids[0..nrows) against q (FP32, coalesced float4 loads,
+// G lanes per row, four row groups in flight) and hands each (score, id) to
+// emit(lane_valid, score, id).  Warp-collective.
 template <int G, class Emit>
-__device__ __forceinline__ void score_rows(const uint32_t* queue, int nrows, const float4* q4,
+__device__ __forceinline__ void score_rows(const uint32_t* ids, int nrows, const float4* q4,
                                            int nf4, const float* __restrict__ X, int64_t ldx,
                                            Emit emit) {
   const int lane = threadIdx.x & 31;
   constexpr int RPP = 32 / G;
+  constexpr int U = 4;
   const int sub = lane % G, grp = lane / G;
-  for (int r0 = 0; r0 < nrows; r0 += 2 * RPP) {
-    const int ra = r0 + grp, rb = r0 + RPP + grp;
-    const bool oka = ra < nrows, okb = rb < nrows;
-    const uint32_t ida = queue[oka ? ra : 0], idb = queue[okb ? rb : 0];
-    const float4* xa = reinterpret_cast<const float4*>(X + (int64_t)ida * ldx);
-    const float4* xb = reinterpret_cast<const float4*>(X + (int64_t)idb * ldx);
-    float sa = 0.f, sb = 0.f;
+  for (int r0 = 0; r0 < nrows; r0 += U * RPP) {
+    uint32_t id[U];
+    bool ok[U];
+    float s[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 + u * RPP + grp;
+      ok[u] = r < nrows;
+      id[u] = ids[ok[u] ? r : 0];
+      s[u] = 0.f;
+    }
     for (int c = sub; c < nf4; c += G) {
       const float4 qq = q4[c];
-      const float4 va = oka ? __ldg(xa + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 vb = okb ? __ldg(xb + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-      sa = fmaf(va.x, qq.x, sa); sa = fmaf(va.y, qq.y, sa);
-      sa = fmaf(va.z, qq.z, sa); sa = fmaf(va.w, qq.w, sa);
-      sb = fmaf(vb.x, qq.x, sb); sb = fmaf(vb.y, qq.y, sb);
-      sb = fmaf(vb.z, qq.z, sb); sb = fmaf(vb.w, qq.w, sb);
+      float4 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        v[u] = ok[u] ? __ldg(reinterpret_cast<const float4*>(X + (int64_t)id[u] * ldx) + c)
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        s[u] = fmaf(v[u].x, qq.x, s[u]); s[u] = fmaf(v[u].y, qq.y, s[u]);
+        s[u] = fmaf(v[u].z, qq.z, s[u]); s[u] = fmaf(v[u].w, qq.w, s[u]);
+      }
     }
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-      sa += __shfl_xor_sync(FULL, sa, o);
-      sb += __shfl_xor_sync(FULL, sb, o);
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) s[u] += __shfl_xor_sync(FULL, s[u], o);
+      emit(ok[u] && sub == 0, s[u], id[u]);
     }
-    emit(oka && sub == 0, sa, ida);
-    emit(okb && sub == 0, sb, idb);
   }
 }
 
+struct GroupCtx {
+  const GatherArgs* a;
+  int g;            // group index in the CTA
+  int gt;           // thread index in the group
+  int64_t q;
+  int Pq, nprobe;
+  int64_t NB;
+  uint64_t* pbase;
+  uint32_t* pstart;
+  uint32_t* wsum;   // [GW] warp sums of the group scan
+};
+
+// Walks the kept ids of every probed bucket of the group's query; visit(ids,
+// valid) runs on all group threads with EPT entries per thread per round,
+// then round_end().  Returns the number of entries walked.
+template <class Visit>
+__device__ __forceinline__ uint64_t walk_entries(const GroupCtx& w, Visit& visit) {
+  const GatherArgs& a = *w.a;
+  const int lane = threadIdx.x & 31, gw = w.gt >> 5;
+  uint64_t walked = 0;
+  for (int pc0 = 0; pc0 < w.nprobe; pc0 += PCHUNK) {
+    const int nc = min(PCHUNK, w.nprobe - pc0);
+    uint32_t cnt[PPT];
+    uint32_t tsum = 0;
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+      const int i = w.gt * PPT + r;
+      uint32_t c = 0;
+      if (i < nc) {
+        const int pi = pc0 + i;
+        const int tl = pi / w.Pq, p = pi - tl * w.Pq;
+        const int t = a.tb + tl;
+        const uint32_t b = a.probes[(w.q * a.nt + tl) * (int64_t)a.pstride + p];
+        const uint32_t* off = a.offsets + (int64_t)t * (w.NB + 1);
+        const uint32_t o0 = off[b];
+        c = off[b + 1] - o0;
+        w.pbase[i] = a.table_base[t] + o0;
+      }
+      cnt[r] = c;
+      tsum += c;
+    }
+    uint32_t inc = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t2 = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += t2;
+    }
+    if (lane == 31) w.wsum[gw] = inc;
+    group_sync(w.g);
+    uint32_t wbase = 0, total = 0;
+#pragma unroll
+    for (int k = 0; k < GW; ++k) {
+      const uint32_t v = w.wsum[k];
+      wbase += k < gw ? v : 0u;
+      total += v;
+    }
+    uint32_t run = wbase + inc - tsum;
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+      w.pstart[w.gt * PPT + r] = run;
+      run += cnt[r];
+    }
+    if (w.gt == 0) w.pstart[PCHUNK] = total;
+    group_sync(w.g);
+    walked += total;
+    for (uint32_t e0 = 0; e0 < total; e0 += ROUND) {
+      uint32_t id[EPT];
+      bool has[EPT];
+#pragma unroll
+      for (int r = 0; r < EPT; ++r) {
+        const uint32_t e = e0 + r * GT + w.gt;
+        has[r] = e < total;
+        id[r] = 0u;
+        if (has[r]) {
+          int lo = 0, hi = nc;   // last bucket whose start <= e (it is non-empty)
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (w.pstart[mid] <= e) lo = mid; else hi = mid;
+          }
+          id[r] = __ldg(a.ids + w.pbase[lo] + (e - w.pstart[lo]));
+        }
+      }
+      visit(id, has);
+      visit.round_end();
+    }
+    group_sync(w.g);
+  }
+  return walked;
+}
+
+// Appends the lanes' flagged ids to the group's candidate buffer.
+__device__ __forceinline__ void append_ids(bool flag, uint32_t id, uint32_t* cand, unsigned* nc) {
+  const unsigned m = __ballot_sync(FULL, flag);
+  if (!m) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  unsigned base = 0;
+  if (lane == leader) base = atomicAdd(nc, (unsigned)__popc(m));
+  base = __shfl_sync(FULL, base, leader);
+  if (flag) cand[base + __popc(m & ((1u << lane) - 1u))] = id;
+}
+
 template <int G>
-__global__ void __launch_bounds__(GS_WARPS * 32)
+__global__ void __launch_bounds__(GS_THREADS, 4)
 gather_score_kernel(GatherArgs a, unsigned long long* qcounter, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ long long s_q;
-  __shared__ unsigned s_U, s_nslow;
-  __shared__ int s_slow;
-  __shared__ double s_thr64;
+  __shared__ long long s_q[NG];
+  __shared__ unsigned s_U[NG], s_nslow[NG], s_nc[NG];
+  __shared__ int s_slow[NG];
+  __shared__ double s_thr64[NG];
+  __shared__ uint32_t s_wsum[NG][GW];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int g = wid / GW, gw = wid % GW, gt = threadIdx.x - g * GT;
   const GSLayout Lo = gs_layout(a.kmax, (int)a.ldq);
-  float* qs = reinterpret_cast<float*>(smem + Lo.q_off);
+  unsigned char* gsm = smem + (size_t)g * Lo.group;
+  float* qs = reinterpret_cast<float*>(gsm + Lo.q_off);
   const float4* q4 = reinterpret_cast<const float4*>(qs);
-  uint32_t* queue = reinterpret_cast<uint32_t*>(smem + Lo.queue_off) + wid * 64;
-  uint64_t* wbuf = reinterpret_cast<uint64_t*>(smem + Lo.wtop_off) + (size_t)wid * Lo.cap;
-  uint64_t* merge = reinterpret_cast<uint64_t*>(smem + Lo.merge_off);
-  SD* slow = reinterpret_cast<SD*>(smem + Lo.merge_off);
-  SD* resc = reinterpret_cast<SD*>(smem + Lo.resc_off);
+  uint64_t* pbase = reinterpret_cast<uint64_t*>(gsm + Lo.pbase_off);
+  uint32_t* pstart = reinterpret_cast<uint32_t*>(gsm + Lo.pstart_off);
+  uint32_t* cand = reinterpret_cast<uint32_t*>(gsm + Lo.cand_off);
+  uint64_t* wbuf = reinterpret_cast<uint64_t*>(gsm + Lo.wtop_off) + (size_t)gw * Lo.cap;
+  uint64_t* merge = reinterpret_cast<uint64_t*>(gsm + Lo.merge_off);
+  SD* resc = reinterpret_cast<SD*>(gsm + Lo.resc_off);
   const int nf4 = (int)(a.ldq / 4);
   const int64_t NB = 4ll * a.D * a.D;
-  uint32_t* bm = a.bitmaps + (int64_t)blockIdx.x * a.bitmap_words;
-  const unsigned lt = (1u << lane) - 1u;
+  const int slot = blockIdx.x * NG + g;
+  SD* slow = reinterpret_cast<SD*>(a.slow_scratch) + (int64_t)slot * SLOW_CAP;
+  uint32_t* bm = a.bitmaps + (int64_t)slot * a.bitmap_words;
+  unsigned* nc = &s_nc[g];
 
   for (;;) {
-    if (threadIdx.x == 0) {
-      s_q = (long long)atomicAdd(qcounter, 1ull);
-      s_U = 0; s_nslow = 0; s_slow = 0;
+    if (gt == 0) {
+      s_q[g] = (long long)atomicAdd(qcounter, 1ull);
+      s_U[g] = 0; s_nslow[g] = 0; s_slow[g] = 0; s_nc[g] = 0;
     }
-    __syncthreads();
-    const int64_t q = s_q;
+    group_sync(g);
+    const int64_t q = s_q[g];
     if (q >= a.mq) break;
     const int kq = a.k_pq ? a.k_pq[q] : a.k;
     const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
     const float* qg = a.Q + q * a.ldq;
-    for (int i = threadIdx.x; i < (int)a.ldq; i += blockDim.x) qs[i] = qg[i];
-    __syncthreads();
+    for (int i = gt; i < (int)a.ldq; i += GT) qs[i] = qg[i];
     const double qn = (double)a.qnorm[q];
     const double eps_s = a.gamma * qn * (double)a.xmax;
     const double du = 5.9604644775390625e-08 * (a.d + 8);
     const double delta = 4.0 * du * du * qn * (double)a.xmax + 1e-300;
+    const int nprobe = a.nt * Pq;
+    GroupCtx wc{&a, g, gt, q, Pq, nprobe, NB, pbase, pstart, s_wsum[g]};
 
-    // ---------------- phase 1: discover, de-duplicate, score
+    // ---------------- discover, de-duplicate, score
     WarpTop wt;
     wt.init(wbuf, Lo.cap, Lo.kp);
-    int qn_cnt = 0;
-    unsigned myU = 0;
-    unsigned long long ent = 0;
     auto offer = [&](bool v, float s, uint32_t id) { wt.offer(v, pack_key(s, id)); };
-    const int nprobe = a.nt * Pq;
-    for (int pi = wid; pi < nprobe; pi += GS_WARPS) {
-      const int tl = pi / Pq, p = pi - tl * Pq;
-      const int t = a.tb + tl;
-      const uint32_t b = a.probes[(q * a.nt + tl) * (int64_t)a.pstride + p];
-      const uint32_t* off = a.offsets + (int64_t)t * (NB + 1);
-      const uint32_t o0 = off[b], cnt = off[b + 1] - o0;
-      const uint32_t* idp = a.ids + a.table_base[t] + o0;
-      ent += cnt;
-      for (uint32_t c = 0; c < cnt; c += 32) {
-        const bool has = c + lane < cnt;
-        const uint32_t id = has ? __ldg(idp + c + lane) : 0u;
-        bool fresh = false;
-        if (has) {
-          const uint32_t bit = 1u << (id & 31);
-          fresh = !(atomicOr(bm + (id >> 5), bit) & bit);
-        }
-        const unsigned m = __ballot_sync(FULL, fresh);
-        if (fresh) queue[qn_cnt + __popc(m & lt)] = id;
-        qn_cnt += __popc(m);
-        myU += __popc(m);
-        __syncwarp();
-        if (qn_cnt >= 32) {
-          score_rows<G>(queue, 32, q4, nf4, a.X, a.ldx, offer);
-          qn_cnt -= 32;
-          if (lane < qn_cnt) queue[lane] = queue[32 + lane];
-          __syncwarp();
-        }
+    auto drain = [&]() {   // group-uniform: score the buffered candidates
+      group_sync(g);
+      const unsigned n = *nc;
+      for (unsigned r0 = (unsigned)gw * 32; r0 < n; r0 += GW * 32)
+        score_rows<G>(cand + r0, (int)min(32u, n - r0), q4, nf4, a.X, a.ldx, offer);
+      group_sync(g);
+      if (gt == 0) { s_U[g] += n; *nc = 0; }
+      group_sync(g);
+    };
+    struct Discover {
+      uint32_t* bm; uint32_t* cand; unsigned* nc; int g; decltype(drain)* dr;
+      __device__ void operator()(const uint32_t (&id)[EPT], const bool (&has)[EPT]) {
+        uint32_t old[EPT];
+#pragma unroll
+        for (int r = 0; r < EPT; ++r)   // all atomics in flight before any result is used
+          old[r] = has[r] ? atomicOr(bm + (id[r] >> 5), 1u << (id[r] & 31)) : 0xFFFFFFFFu;
+#pragma unroll
+        for (int r = 0; r < EPT; ++r)
+          append_ids(!(old[r] & (1u << (id[r] & 31))), id[r], cand, nc);
       }
-    }
-    if (qn_cnt > 0) score_rows<G>(queue, qn_cnt, q4, nf4, a.X, a.ldx, offer);
+      __device__ void round_end() {
+        group_sync(g);
+        if (*(volatile unsigned*)nc > (unsigned)(CAND_CAP - ROUND)) (*dr)();
+      }
+    } disc{bm, cand, nc, g, &drain};
+    const uint64_t entries = walk_entries(wc, disc);
+    drain();
     const int nw = wt.finish();
-    for (int e = lane; e < Lo.kp; e += 32) merge[(size_t)wid * Lo.kp + e] = e < nw ? wbuf[e] : 0ull;
-    if (lane == 0) {
-      atomicAdd(&s_U, myU);
-      if (a.stats) atomicAdd(a.stats + 0, ent);
+    for (int e = lane; e < Lo.kp; e += 32) merge[(size_t)gw * Lo.kp + e] = e < nw ? wbuf[e] : 0ull;
+    group_sync(g);
+    if (GW > 1 && gw == 0) {
+      for (int e = GW * Lo.kp + lane; e < Lo.mcap; e += 32) merge[e] = 0ull;
+      __syncwarp();
+      warp_sort_desc(merge, Lo.mcap);
     }
-    __syncthreads();
-    for (int e = GS_WARPS * Lo.kp + threadIdx.x; e < Lo.mcap; e += blockDim.x) merge[e] = 0ull;
-    __syncthreads();
-    block_sort_desc(merge, Lo.mcap);
+    group_sync(g);
 
-    // ---------------- phase 2: re-score the best K' with FP64 accuracy
-    const unsigned U = s_U;
+    // ---------------- re-score the best K' with FP64 accuracy
+    const unsigned U = s_U[g];
     const int Kpp = (int)(U < (unsigned)Lo.kp ? U : (unsigned)Lo.kp);
-    for (int e = wid; e < Kpp; e += GS_WARPS) {
-      const uint32_t id = key_id(merge[e]);
-      const double s = warp_dot2(qs, a.X + (int64_t)id * a.ldx, a.d);
-      if (lane == 0) resc[e] = SD{s, id, 0};
+    for (int e0 = gw * 8; e0 < Kpp; e0 += GW * 8) {
+      double sv[8];
+      uint32_t idv[8];
+      const float* rows[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        idv[u] = key_id(merge[min(e0 + u, Kpp - 1)]);
+        rows[u] = a.X + (int64_t)idv[u] * a.ldx;
+      }
+      warp_dot2_gather<8>(qs, rows, nf4, sv);
+      if (lane == 0)
+        for (int u = 0; u < 8 && e0 + u < Kpp; ++u) resc[e0 + u] = SD{sv[u], idv[u], 0};
     }
-    for (int e = Kpp + threadIdx.x; e < Lo.rcap; e += blockDim.x) resc[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
-    __syncthreads();
-    if (wid == 0) warp_sort_sd(resc, Lo.rcap);
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    for (int e = Kpp + gt; e < Lo.rcap; e += GT) resc[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+    group_sync(g);
+    if (gw == 0) warp_sort_sd(resc, Lo.rcap);
+    group_sync(g);
+    if (gt == 0) {
       if (U > (unsigned)Kpp) {
         const double sK = (double)key_score(merge[Lo.kp - 1]);
         const double need = resc[kq - 1].s;
         if (!(sK + eps_s + 2.0 * delta < need)) {
-          s_slow = 1;
-          s_thr64 = need - eps_s - 2.0 * delta;
+          s_slow[g] = 1;
+          s_thr64[g] = need - eps_s - 2.0 * delta;
         }
       }
       if (a.stats) {
+        atomicAdd(a.stats + 0, (unsigned long long)entries);
         atomicAdd(a.stats + 1, (unsigned long long)U);
         atomicAdd(a.stats + 3, (unsigned long long)nprobe);
-        if (s_slow) atomicAdd(a.stats + 2, 1ull);
+        if (s_slow[g]) atomicAdd(a.stats + 2, 1ull);
       }
     }
-    __syncthreads();
+    group_sync(g);
 
     const int64_t orow = q * a.kmax;
-    if (!s_slow) {
-      for (int e = threadIdx.x; e < a.kmax; e += blockDim.x) {
+    if (!s_slow[g]) {
+      for (int e = gt; e < a.kmax; e += GT) {
         const bool ok = e < kq && e < Kpp;
         a.out_ids[orow + e] = ok ? (int64_t)resc[e].id : -1;
         a.out_scores[orow + e] = ok ? (float)resc[e].s : -INFINITY;
       }
-      // ---------------- phase 3: clear the touched bitmap words
-      for (int pi = wid; pi < nprobe; pi += GS_WARPS) {
-        const int tl = pi / Pq, p = pi - tl * Pq;
-        const int t = a.tb + tl;
-        const uint32_t b = a.probes[(q * a.nt + tl) * (int64_t)a.pstride + p];
-        const uint32_t* off = a.offsets + (int64_t)t * (NB + 1);
-        const uint32_t o0 = off[b], cnt = off[b + 1] - o0;
-        const uint32_t* idp = a.ids + a.table_base[t] + o0;
-        for (uint32_t c = lane; c < cnt; c += 32) bm[__ldg(idp + c) >> 5] = 0u;
-      }
+      // ---------------- clear the touched bitmap words
+      struct Clear {
+        uint32_t* bm;
+        __device__ void operator()(const uint32_t (&id)[EPT], const bool (&has)[EPT]) {
+#pragma unroll
+          for (int r = 0; r < EPT; ++r)
+            if (has[r]) bm[id[r] >> 5] = 0u;
+        }
+        __device__ void round_end() {}
+      } clr{bm};
+      walk_entries(wc, clr);
     } else {
       // ---------------- slow path: every candidate that may reach the top-k
-      const double thr64 = s_thr64;
-      int qc = 0;
+      const double thr64 = s_thr64[g];
+      unsigned* nslow = &s_nslow[g];
       auto collect = [&](bool v, float s, uint32_t id) {
         if (v && (double)s >= thr64) {
-          const unsigned slot = atomicAdd(&s_nslow, 1u);
-          if (slot < (unsigned)SLOW_CAP) slow[slot].id = id;
+          const unsigned k = atomicAdd(nslow, 1u);
+          if (k < (unsigned)SLOW_CAP) slow[k].id = id;
           else if (err) atomicExch(err, 1);
         }
       };
-      __syncthreads();  // merge region is reused by the slow list
-      for (int pi = wid; pi < nprobe; pi += GS_WARPS) {
-        const int tl = pi / Pq, p = pi - tl * Pq;
-        const int t = a.tb + tl;
-        const uint32_t b = a.probes[(q * a.nt + tl) * (int64_t)a.pstride + p];
-        const uint32_t* off = a.offsets + (int64_t)t * (NB + 1);
-        const uint32_t o0 = off[b], cnt = off[b + 1] - o0;
-        const uint32_t* idp = a.ids + a.table_base[t] + o0;
-        for (uint32_t c = 0; c < cnt; c += 32) {
-          const bool has = c + lane < cnt;
-          const uint32_t id = has ? __ldg(idp + c + lane) : 0u;
-          bool first = false;
-          if (has) {
-            const uint32_t bit = 1u << (id & 31);
-            first = (atomicAnd(bm + (id >> 5), ~bit) & bit) != 0u;
-          }
-          const unsigned m = __ballot_sync(FULL, first);
-          if (first) queue[qc + __popc(m & lt)] = id;
-          qc += __popc(m);
-          __syncwarp();
-          if (qc >= 32) {
-            score_rows<G>(queue, 32, q4, nf4, a.X, a.ldx, collect);
-            qc -= 32;
-            if (lane < qc) queue[lane] = queue[32 + lane];
-            __syncwarp();
-          }
+      auto drain2 = [&]() {
+        group_sync(g);
+        const unsigned n = *nc;
+        for (unsigned r0 = (unsigned)gw * 32; r0 < n; r0 += GW * 32)
+          score_rows<G>(cand + r0, (int)min(32u, n - r0), q4, nf4, a.X, a.ldx, collect);
+        group_sync(g);
+        if (gt == 0) *nc = 0;
+        group_sync(g);
+      };
+      struct Revisit {
+        uint32_t* bm; uint32_t* cand; unsigned* nc; int g; decltype(drain2)* dr;
+        __device__ void operator()(const uint32_t (&id)[EPT], const bool (&has)[EPT]) {
+          uint32_t old[EPT];
+#pragma unroll
+          for (int r = 0; r < EPT; ++r)
+            old[r] = has[r] ? atomicAnd(bm + (id[r] >> 5), ~(1u << (id[r] & 31))) : 0u;
+#pragma unroll
+          for (int r = 0; r < EPT; ++r)
+            append_ids((old[r] & (1u << (id[r] & 31))) != 0u, id[r], cand, nc);
         }
+        __device__ void round_end() {
+          group_sync(g);
+          if (*(volatile unsigned*)nc > (unsigned)(CAND_CAP - ROUND)) (*dr)();
+        }
+      } rev{bm, cand, nc, g, &drain2};
+      walk_entries(wc, rev);
+      drain2();
+      const int ns = (int)(*nslow < (unsigned)SLOW_CAP ? *nslow : (unsigned)SLOW_CAP);
+      __syncwarp();
+      for (int e0 = gw * 4; e0 < ns; e0 += GW * 4) {
+        double sv[4];
+        const float* rows[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) rows[u] = a.X + (int64_t)slow[min(e0 + u, ns - 1)].id * a.ldx;
+        warp_dot2_gather<4>(qs, rows, nf4, sv);
+        if (lane == 0)
+          for (int u = 0; u < 4 && e0 + u < ns; ++u) slow[e0 + u].s = sv[u];
       }
-      if (qc > 0) score_rows<G>(queue, qc, q4, nf4, a.X, a.ldx, collect);
-      __syncthreads();
-      const int ns = (int)(s_nslow < (unsigned)SLOW_CAP ? s_nslow : (unsigned)SLOW_CAP);
-      for (int e = wid; e < ns; e += GS_WARPS) {
-        const uint32_t id = slow[e].id;
-        const double s = warp_dot2(qs, a.X + (int64_t)id * a.ldx, a.d);
-        if (lane == 0) slow[e].s = s;
-      }
+      __syncwarp();
       const int np2 = pow2_ceil(ns > 1 ? ns : 1);
-      for (int e = ns + threadIdx.x; e < np2; e += blockDim.x) slow[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
-      __syncthreads();
-      block_sort_sd(slow, np2);
-      for (int e = threadIdx.x; e < a.kmax; e += blockDim.x) {
+      for (int e = ns + gt; e < np2; e += GT) slow[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+      group_sync(g);
+      if (gw == 0) warp_sort_sd(slow, np2);
+      group_sync(g);
+      for (int e = gt; e < a.kmax; e += GT) {
         const bool ok = e < kq && e < ns;
         a.out_ids[orow + e] = ok ? (int64_t)slow[e].id : -1;
         a.out_scores[orow + e] = ok ? (float)slow[e].s : -INFINITY;
       }
     }
-    __syncthreads();
+    group_sync(g);
   }
 }
 
@@ -633,7 +873,35 @@ gather_score_kernel(GatherArgs a, unsigned long long* qcounter, int* err) {
 // Exact top-k over a dense FP32 score row (brute-force search): the same
 // FP32 pre-selection, compensated re-scoring and boundary check as above,
 // with every column a candidate.
-__global__ void __launch_bounds__(GS_WARPS * 32)
+constexpr int TD_WARPS = 8;
+constexpr int TD_SLOW = 2048;
+
+struct DenseLayout {
+  int kp, cap, mcap, rcap;
+  size_t q_off, wtop_off, merge_off, resc_off, total;
+};
+
+__host__ __device__ inline DenseLayout dense_layout(int kmax, int ldq) {
+  DenseLayout L;
+  L.kp = kmax + KSLACK;
+  L.cap = pow2_ceil(2 * L.kp + 32);
+  L.mcap = pow2_ceil(TD_WARPS * L.kp);
+  L.rcap = pow2_ceil(L.kp);
+  size_t o = 0;
+  L.q_off = o; o += (size_t)4 * ldq; o = (o + 15) & ~(size_t)15;
+  L.wtop_off = o; o += (size_t)TD_WARPS * L.cap * 8;
+  L.merge_off = o;
+  {
+    size_t mb = (size_t)L.mcap * 8;
+    if (mb < (size_t)TD_SLOW * 16) mb = (size_t)TD_SLOW * 16;
+    o += mb;
+  }
+  L.resc_off = o; o += (size_t)L.rcap * 16;
+  L.total = o;
+  return L;
+}
+
+__global__ void __launch_bounds__(TD_WARPS * 32)
 topk_dense_kernel(const float* __restrict__ S, int64_t lds, int64_t n, int k, const float* Q,
                   int64_t ldq, const float* __restrict__ X, int64_t ldx, int d, float xmax,
                   double gamma, int64_t* out_ids, float* out_scores, int kmax,
@@ -643,7 +911,7 @@ topk_dense_kernel(const float* __restrict__ S, int64_t lds, int64_t n, int k, co
   __shared__ int s_slow;
   __shared__ double s_thr64;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const GSLayout Lo = gs_layout(kmax, (int)ldq);
+  const DenseLayout Lo = dense_layout(kmax, (int)ldq);
   float* qs = reinterpret_cast<float*>(smem + Lo.q_off);
   uint64_t* wbuf = reinterpret_cast<uint64_t*>(smem + Lo.wtop_off) + (size_t)wid * Lo.cap;
   uint64_t* merge = reinterpret_cast<uint64_t*>(smem + Lo.merge_off);
@@ -665,7 +933,7 @@ topk_dense_kernel(const float* __restrict__ S, int64_t lds, int64_t n, int k, co
 
   WarpTop wt;
   wt.init(wbuf, Lo.cap, Lo.kp);
-  for (int64_t c0 = (int64_t)wid * 32; c0 < n; c0 += (int64_t)GS_WARPS * 32) {
+  for (int64_t c0 = (int64_t)wid * 32; c0 < n; c0 += (int64_t)TD_WARPS * 32) {
     const int64_t c = c0 + lane;
     const bool ok = c < n;
     wt.offer(ok, ok ? pack_key(row[c], (uint32_t)c) : 0ull);
@@ -673,11 +941,11 @@ topk_dense_kernel(const float* __restrict__ S, int64_t lds, int64_t n, int k, co
   const int nw = wt.finish();
   for (int e = lane; e < Lo.kp; e += 32) merge[(size_t)wid * Lo.kp + e] = e < nw ? wbuf[e] : 0ull;
   __syncthreads();
-  for (int e = GS_WARPS * Lo.kp + threadIdx.x; e < Lo.mcap; e += blockDim.x) merge[e] = 0ull;
+  for (int e = TD_WARPS * Lo.kp + threadIdx.x; e < Lo.mcap; e += blockDim.x) merge[e] = 0ull;
   __syncthreads();
   block_sort_desc(merge, Lo.mcap);
   const int Kpp = (int)(n < (int64_t)Lo.kp ? n : (int64_t)Lo.kp);
-  for (int e = wid; e < Kpp; e += GS_WARPS) {
+  for (int e = wid; e < Kpp; e += TD_WARPS) {
     const uint32_t id = key_id(merge[e]);
     const double s = warp_dot2(qs, X + (int64_t)id * ldx, d);
     if (lane == 0) resc[e] = SD{s, id, 0};
@@ -710,13 +978,13 @@ topk_dense_kernel(const float* __restrict__ S, int64_t lds, int64_t n, int k, co
   for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
     if ((double)row[c] >= thr64) {
       const unsigned slot = atomicAdd(&s_nslow, 1u);
-      if (slot < (unsigned)SLOW_CAP) slow[slot].id = (uint32_t)c;
+      if (slot < (unsigned)TD_SLOW) slow[slot].id = (uint32_t)c;
       else if (err) atomicExch(err, 1);
     }
   }
   __syncthreads();
-  const int ns = (int)(s_nslow < (unsigned)SLOW_CAP ? s_nslow : (unsigned)SLOW_CAP);
-  for (int e = wid; e < ns; e += GS_WARPS) {
+  const int ns = (int)(s_nslow < (unsigned)TD_SLOW ? s_nslow : (unsigned)TD_SLOW);
+  for (int e = wid; e < ns; e += TD_WARPS) {
     const uint32_t id = slow[e].id;
     const double s = warp_dot2(qs, X + (int64_t)id * ldx, d);
     if (lane == 0) slow[e].s = s;
@@ -747,7 +1015,7 @@ fpp_status launch_gs(const GatherArgs& a, size_t smem, int grid, unsigned long l
                                   200 * 1024));
     attr_set = true;
   }
-  gather_score_kernel<G><<<grid, GS_WARPS * 32, smem, st>>>(a, qc, err);
+  gather_score_kernel<G><<<grid, GS_THREADS, smem, st>>>(a, qc, err);
   FPP_LAUNCHED();
   return FPP_OK;
 }
@@ -765,7 +1033,7 @@ fpp_status launch_probe_s(const ProbeArgs& a, cudaStream_t st) {
   return FPP_OK;
 }
 
-fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st) {
+fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_begin) {
   const int64_t warps = a.mq * a.nt;
   if (warps <= 0) return FPP_OK;
   if (a.probes > PMAX) {
@@ -773,6 +1041,7 @@ fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st) {
     return FPP_EINVAL;
   }
   FPP_CUDA(cudaMemsetAsync(a.recheck_count, 0, sizeof(unsigned), st));
+  if (a.lists) FPP_CUDA(cudaMemsetAsync(a.recheck2_count, 0, sizeof(unsigned), st));
   const int S = pow2_ceil((a.D + 31) / 32);
   fpp_status s;
   switch (S) {
@@ -784,6 +1053,14 @@ fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st) {
     default: s = launch_probe_s<32>(a, st); break;
   }
   if (s != FPP_OK) return s;
+  if (exact_begin) FPP_CUDA(cudaEventRecord(exact_begin, st));
+  int dev0 = 0, sms0 = 0;
+  cudaGetDevice(&dev0);
+  cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, dev0);
+  if (a.lists) {
+    probe_window_kernel<<<sms0 * 2, 256, 0, st>>>(a);
+    FPP_LAUNCHED();
+  }
   // exact pass over the items the fast pass could not decide; the grid is
   // fixed and the kernel reads the item count on the device
   const size_t smem = recheck_smem_bytes(a.D);
@@ -805,7 +1082,9 @@ fpp_status launch_query_norms(const float* Q, int64_t m, int64_t ldq, int d, flo
   return FPP_OK;
 }
 
-int gather_slots(int sm_count) { return sm_count * 4; }
+int gather_slots(int sm_count) { return sm_count * 4 * NG; }
+
+int gather_slow_cap() { return SLOW_CAP; }
 
 fpp_status launch_gather_score(const GatherArgs& a, cudaStream_t st) {
   if (a.mq <= 0) return FPP_OK;
@@ -817,7 +1096,8 @@ fpp_status launch_gather_score(const GatherArgs& a, cudaStream_t st) {
   // a.stats[4] is the query counter, a.stats[5] the error flag (see the caller)
   unsigned long long* qc = a.stats + 4;
   int* err = reinterpret_cast<int*>(a.stats + 5);
-  const int grid = (int)(a.mq < a.slots ? a.mq : a.slots);
+  const int64_t ctas = ceil_div(a.mq, NG);
+  const int grid = (int)(ctas < a.slots / NG ? ctas : a.slots / NG);
   const int g = choose_g((int)(a.ldq / 4));
   switch (g) {
     case 1: return launch_gs<1>(a, Lo.total, grid, qc, err, st);
@@ -834,11 +1114,11 @@ fpp_status launch_topk_dense(const float* S, int64_t lds, int64_t mq, int64_t n,
                              float xmax, double gamma, int64_t* out_ids, float* out_scores,
                              int kmax, unsigned long long* rechecks, cudaStream_t st) {
   if (mq <= 0) return FPP_OK;
-  const GSLayout Lo = gs_layout(kmax, (int)ldq);
+  const DenseLayout Lo = dense_layout(kmax, (int)ldq);
   FPP_CUDA(cudaFuncSetAttribute(topk_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 200 * 1024));
   int* err = reinterpret_cast<int*>(rechecks + 1);
-  topk_dense_kernel<<<(unsigned)mq, GS_WARPS * 32, Lo.total, st>>>(
+  topk_dense_kernel<<<(unsigned)mq, TD_WARPS * 32, Lo.total, st>>>(
       S, lds, n, k, Q, ldq, X, ldx, d, xmax, gamma, out_ids, out_scores, kmax, rechecks, err);
   FPP_LAUNCHED();
   return FPP_OK;
