@@ -253,7 +253,8 @@ def main():
     time.sleep(0.3)
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     launches0 = F.fpp_launch_count()
-    phase = {"ms_project": 0.0, "ms_probe": 0.0, "ms_probe_exact": 0.0, "ms_gather_score": 0.0}
+    phase = {"ms_project": 0.0, "ms_probe": 0.0, "ms_probe_exact": 0.0, "ms_gather_score": 0.0,
+             "ms_dedup": 0.0, "ms_score": 0.0, "ms_topk": 0.0}
     tot = {"entries": 0, "unique": 0, "probes": 0, "probe_rechecks": 0, "topk_rechecks": 0,
            "batches": 0}
     evs[0].record(stream)
@@ -297,6 +298,9 @@ def main():
         "probe_exact": {"ms_per_launch": phase["ms_probe_exact"] / (chunks * K),
                         "launches_per_step": chunks},
         "gather_score": {"ms_per_launch": gs_ms, "launches_per_step": chunks, "bound": "hbm",
+                         "ms_dedup": phase["ms_dedup"] / (chunks * K),
+                         "ms_score": phase["ms_score"] / (chunks * K),
+                         "ms_topk": phase["ms_topk"] / (chunks * K),
                          "achieved": gs_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": gs_gbs / hbm_peak,
                          "algorithmic_bytes_per_launch": gather_bytes / (chunks * K)},

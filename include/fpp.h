@@ -99,7 +99,10 @@ typedef struct fpp_search_stats {
   float ms_project;           /* device time per phase, milliseconds          */
   float ms_probe;             /* fast probe ranking                            */
   float ms_probe_exact;       /* exact re-decision of near-tie probe sets      */
-  float ms_gather_score;
+  float ms_gather_score;      /* candidate gather, scoring and top-k, of which: */
+  float ms_dedup;             /*   bucket walk and bitmap de-duplication       */
+  float ms_score;             /*   candidate scoring                            */
+  float ms_topk;              /*   per-query top-k                              */
   float ms_total;
 } fpp_search_stats;
 

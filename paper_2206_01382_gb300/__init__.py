@@ -54,7 +54,8 @@ class fpp_search_stats(ctypes.Structure):
                 ("probe_rechecks", ctypes.c_uint64), ("topk_rechecks", ctypes.c_uint64),
                 ("batches", ctypes.c_uint64), ("ms_project", ctypes.c_float), ("ms_probe", ctypes.c_float),
                 ("ms_probe_exact", ctypes.c_float), ("ms_gather_score", ctypes.c_float),
-                ("ms_total", ctypes.c_float)]
+                ("ms_dedup", ctypes.c_float), ("ms_score", ctypes.c_float),
+                ("ms_topk", ctypes.c_float), ("ms_total", ctypes.c_float)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

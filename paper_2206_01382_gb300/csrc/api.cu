@@ -60,12 +60,14 @@ struct DevBuf {
 
 struct Workspace {
   DevBuf qpad, qsplit, proj, probes, qnorm, recheck, recheck2, kpq, ppq, out_ids, out_scores,
-      bitmaps, slow, stats;
+      bitmaps, ecount, eoff, scan, cand, cscores, items, tkslow, stats;
   int64_t bitmap_words = 0;
+  uint64_t cand_cap = 0;    // candidate slots in cand / cscores
   int slots = 0;
   void release() {
     for (DevBuf* b : {&qpad, &qsplit, &proj, &probes, &qnorm, &recheck, &recheck2, &kpq, &ppq,
-                      &out_ids, &out_scores, &bitmaps, &slow, &stats})
+                      &out_ids, &out_scores, &bitmaps, &ecount, &eoff, &scan, &cand, &cscores,
+                      &items, &tkslow, &stats})
       b->release();
   }
 };
@@ -503,20 +505,60 @@ fpp_status search_chunk(fpp_index* ix, const float* Q, int64_t q0, int64_t mc, c
   FPP_TRY(launch_probe(pa, st, ev ? ev[4] : nullptr));
   if (ev) FPP_CUDA(cudaEventRecord(ev[2], st));
   if (probes_only) return FPP_OK;
-  FPP_CUDA(cudaMemsetAsync(ws.stats.as<unsigned long long>() + 4, 0, 8, st));
-  GatherArgs ga{};
-  ga.probes = ws.probes.as<uint32_t>(); ga.pstride = pl.pmax; ga.mq = mc;
-  ga.tb = pl.tb; ga.nt = nt; ga.D = ix->D;
-  ga.probes_pq = ppq; ga.k_pq = kpq; ga.k = pl.k; ga.kmax = pl.kmax;
-  ga.offsets = ix->offsets; ga.table_base = ix->table_base; ga.ids = ix->ids;
-  ga.X = ix->X; ga.ldx = ix->dpad; ga.d = ix->d; ga.n = ix->n;
-  ga.Q = ws.qpad.as<float>(); ga.ldq = ix->dpad; ga.qnorm = ws.qnorm.as<float>();
-  ga.xmax = ix->xmax; ga.gamma = ix->gamma;
-  ga.bitmaps = ws.bitmaps.as<uint32_t>(); ga.bitmap_words = ws.bitmap_words; ga.slots = ws.slots;
-  ga.slow_scratch = ws.slow.p;
-  ga.out_ids = ids_dev; ga.out_scores = scores_dev;
-  ga.stats = ws.stats.as<unsigned long long>();
-  FPP_TRY(launch_gather_score(ga, st));
+  // ---- candidates: count bucket entries, give each query a region, dedup,
+  // score, top-k
+  unsigned long long* stv = ws.stats.as<unsigned long long>();
+  DedupArgs da{};
+  da.probes = ws.probes.as<uint32_t>(); da.pstride = pl.pmax; da.mq = mc;
+  da.tb = pl.tb; da.nt = nt; da.D = ix->D; da.probes_pq = ppq;
+  da.offsets = ix->offsets; da.table_base = ix->table_base; da.ids = ix->ids;
+  da.bitmaps = ws.bitmaps.as<uint32_t>(); da.bitmap_words = ws.bitmap_words;
+  da.ecount = ws.ecount.as<uint32_t>(); da.eoff = ws.eoff.as<uint64_t>();
+  da.ucount = ws.ecount.as<uint32_t>() + mc;
+  da.stats = stv;
+  FPP_TRY(launch_count_entries(da, st));
+  FPP_TRY(exclusive_scan_u32(ws.ecount.as<uint32_t>(), mc, ws.eoff.as<uint64_t>(), 0,
+                             KeepRule{1.0, 1, 0}, ws.scan.as<uint64_t>(), st));
+  // candidate slots: a bound from the largest kept bucket when it is small
+  // enough, otherwise the exact total (read back)
+  const uint64_t bound = (uint64_t)mc * nt * pl.pmax * std::max<uint32_t>(ix->max_bucket_kept, 1);
+  uint64_t need = bound;
+  if (bound > (1ull << 28)) {
+    FPP_CUDA(cudaMemcpyAsync(&need, ws.eoff.as<uint64_t>() + mc, 8, cudaMemcpyDeviceToHost, st));
+    FPP_CUDA(cudaStreamSynchronize(st));
+  }
+  if (need > ws.cand_cap) {
+    ws.cand.release(); ws.cscores.release(); ws.items.release();
+    const uint64_t cap = need + need / 4 + 1024;
+    FPP_TRY(ws.cand.ensure((size_t)cap * 4));
+    FPP_TRY(ws.cscores.ensure((size_t)cap * 4));
+    ws.cand_cap = cap;
+  }
+  {
+    const size_t ib = (size_t)score_item_slots(ws.cand_cap, mc) * sizeof(ScoreItem);
+    FPP_TRY(ws.items.ensure(ib));
+    FPP_CUDA(cudaMemsetAsync(ws.items.p, 0, ib, st));
+  }
+  da.cand = ws.cand.as<uint32_t>();
+  da.items = ws.items.as<ScoreItem>();
+  FPP_TRY(launch_dedup(da, ws.slots, st));
+  if (ev) FPP_CUDA(cudaEventRecord(ev[5], st));
+  ScoreArgs sa{};
+  sa.items = ws.items.as<ScoreItem>(); sa.eoff = ws.eoff.as<uint64_t>(); sa.mq = mc;
+  sa.cand = ws.cand.as<uint32_t>();
+  sa.X = ix->X; sa.ldx = ix->dpad; sa.Q = ws.qpad.as<float>(); sa.ldq = ix->dpad;
+  sa.scores = ws.cscores.as<float>();
+  FPP_TRY(launch_score(sa, ix->sm_count, st));
+  if (ev) FPP_CUDA(cudaEventRecord(ev[6], st));
+  TopkArgs ta{};
+  ta.mq = mc; ta.eoff = ws.eoff.as<uint64_t>(); ta.ucount = da.ucount; ta.cand = ws.cand.as<uint32_t>();
+  ta.scores = ws.cscores.as<float>(); ta.k_pq = kpq; ta.k = pl.k; ta.kmax = pl.kmax;
+  ta.X = ix->X; ta.ldx = ix->dpad; ta.Q = ws.qpad.as<float>(); ta.ldq = ix->dpad; ta.d = ix->d;
+  ta.qnorm = ws.qnorm.as<float>(); ta.xmax = ix->xmax; ta.gamma = gamma_fp32(ix->dpad);
+  ta.cap = topk_cap(pl.kmax); ta.rcap = topk_rcap(pl.kmax);
+  ta.slow = ws.tkslow.p; ta.err = reinterpret_cast<int*>(stv + 5); ta.stats = stv;
+  ta.out_ids = ids_dev; ta.out_scores = scores_dev;
+  FPP_TRY(launch_topk(ta, st));
   if (ev) FPP_CUDA(cudaEventRecord(ev[3], st));
   return FPP_OK;
 }
@@ -553,16 +595,18 @@ fpp_status prepare_workspace(fpp_index* ix, const SearchPlan& pl, int64_t mc, bo
     FPP_TRY(ws.out_ids.ensure((size_t)mc * pl.kmax * 8, false, st));
     FPP_TRY(ws.out_scores.ensure((size_t)mc * pl.kmax * 4, false, st));
   }
-  const int slots = gather_slots(ix->sm_count);
+  const int slots = dedup_slots(ix->sm_count);
   const int64_t words = ceil_div(ix->n, 32);
   if (ws.slots != slots || ws.bitmap_words != words || !ws.bitmaps.p) {
     ws.bitmaps.release();
     FPP_TRY(ws.bitmaps.ensure((size_t)slots * words * 4, true, st));
-    ws.slow.release();
-    FPP_TRY(ws.slow.ensure((size_t)slots * gather_slow_cap() * 16, false, st));
     ws.slots = slots;
     ws.bitmap_words = words;
   }
+  FPP_TRY(ws.ecount.ensure((size_t)2 * mc * 4, false, st));
+  FPP_TRY(ws.eoff.ensure((size_t)(mc + 1) * 8, false, st));
+  FPP_TRY(ws.scan.ensure((size_t)scan_scratch_elems(mc) * 8, false, st));
+  FPP_TRY(ws.tkslow.ensure((size_t)(ceil_div(mc, 8) * 8) * topk_slow_cap() * 16, false, st));
   return FPP_OK;
 }
 
@@ -580,11 +624,11 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
   const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt, pl.pmax), m);
   FPP_TRY(prepare_workspace(ix, pl, mc, !dev_out, st));
   FPP_CUDA(cudaMemsetAsync(ix->ws.stats.p, 0, 16 * 8, st));
-  cudaEvent_t ev[5] = {};
+  cudaEvent_t ev[7] = {};
   bool timing = stats != nullptr;
   if (timing)
     for (auto& e : ev) FPP_CUDA(cudaEventCreate(&e));
-  float ms[4] = {0, 0, 0, 0};
+  float ms[7] = {0, 0, 0, 0, 0, 0, 0};
   uint64_t batches = 0;
   for (int64_t q0 = 0; q0 < m; q0 += mc, ++batches) {
     const int64_t c = std::min<int64_t>(mc, m - q0);
@@ -597,12 +641,15 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
     }
     if (timing) {
       FPP_CUDA(cudaEventSynchronize(ev[3]));
-      float t[4];
+      float t[7];
       cudaEventElapsedTime(&t[0], ev[0], ev[1]);
       cudaEventElapsedTime(&t[1], ev[1], ev[4]);
       cudaEventElapsedTime(&t[2], ev[4], ev[2]);
       cudaEventElapsedTime(&t[3], ev[2], ev[3]);
-      for (int i = 0; i < 4; ++i) ms[i] += t[i];
+      cudaEventElapsedTime(&t[4], ev[2], ev[5]);
+      cudaEventElapsedTime(&t[5], ev[5], ev[6]);
+      cudaEventElapsedTime(&t[6], ev[6], ev[3]);
+      for (int i = 0; i < 7; ++i) ms[i] += t[i];
     }
   }
   const bool need_sync = !dev_out || o->stream == nullptr || stats != nullptr;
@@ -637,6 +684,9 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
     stats->ms_probe = ms[1];
     stats->ms_probe_exact = ms[2];
     stats->ms_gather_score = ms[3];
+    stats->ms_dedup = ms[4];
+    stats->ms_score = ms[5];
+    stats->ms_topk = ms[6];
     stats->ms_total = ms[0] + ms[1] + ms[2] + ms[3];
   }
   return FPP_OK;

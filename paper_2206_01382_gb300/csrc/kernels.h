@@ -119,38 +119,77 @@ fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_b
 fpp_status launch_query_norms(const float* Q, int64_t m, int64_t ldq, int d, float* out,
                               cudaStream_t st);
 
-struct GatherArgs {
-  const uint32_t* probes;    // [mq][nt][pstride]
+// Candidate gather / de-duplication / scoring / top-k (search_kernels.cu).
+struct ScoreItem {
+  uint32_t q;        // query in the batch
+  uint32_t len;      // candidates in this item
+  uint64_t start;    // first candidate slot
+};
+
+struct DedupArgs {
+  const uint32_t* probes;    // [mq][nt][pstride] probed bucket ids
   int pstride;
   int64_t mq;
   int tb, nt, D;
   const int32_t* probes_pq;  // [mq] or NULL (then pstride probes each)
-  const int32_t* k_pq;       // [mq] or NULL (then k each)
-  int k;
-  int kmax;                  // output row stride
   const uint32_t* offsets;   // [L][4D^2 + 1]
   const uint64_t* table_base;// [L]
   const uint32_t* ids;       // kept ids
+  uint32_t* bitmaps;         // [slots][bitmap_words]
+  int64_t bitmap_words;
+  uint32_t* ecount;          // [mq] bucket entries per query
+  const uint64_t* eoff;      // [mq + 1] exclusive scan of ecount
+  uint32_t* cand;            // candidate ids, query q at eoff[q] ..
+  uint32_t* ucount;          // [mq] distinct candidates per query
+  ScoreItem* items;          // per-query slots from eoff[q] / ITEM + q (pre-zeroed)
+  unsigned long long* stats; // entries, unique, -, probes
+};
+
+struct ScoreArgs {
+  const ScoreItem* items;    // slots [0, eoff[mq] / ITEM + mq + 1), zero-length = unused
+  const uint64_t* eoff;
+  int64_t mq;
+  const uint32_t* cand;
   const float* X;            // [n][ldx]
   int64_t ldx;
-  int d;
-  int64_t n;
+  const float* Q;            // [mq][ldq] (ldq == ldx)
+  int64_t ldq;
+  float* scores;             // FP32 scores, parallel to cand
+};
+
+struct TopkArgs {
+  int64_t mq;
+  const uint64_t* eoff;
+  const uint32_t* ucount;
+  const uint32_t* cand;
+  const float* scores;
+  const float* X;            // [n][ldx] for the compensated re-scoring
+  int64_t ldx;
   const float* Q;            // [mq][ldq]
   int64_t ldq;
+  int d;
   const float* qnorm;        // [mq]
   float xmax;
-  double gamma;
-  uint32_t* bitmaps;         // [slots][words]
-  void* slow_scratch;        // [slots][gather_slow_cap()] 16-byte entries
-  int64_t bitmap_words;
-  int slots;
+  double gamma;              // FP32 score error factor gamma_d
+  const int32_t* k_pq;       // [mq] or NULL
+  int k, kmax, cap, rcap;
+  void* slow;                // [ceil(mq / 8) * 8][topk_slow_cap()] 16-byte entries
+  int* err;
+  unsigned long long* stats; // stats[2] counts slow-path queries
   int64_t* out_ids;          // [mq][kmax]
   float* out_scores;
-  unsigned long long* stats; // [4]: entries, unique, topk rechecks, probes
 };
-fpp_status launch_gather_score(const GatherArgs& a, cudaStream_t st);
-int gather_slots(int sm_count);
-int gather_slow_cap();
+
+int dedup_slots(int sm_count);
+int score_item_len();
+int64_t score_item_slots(uint64_t entries_total, int64_t mq);
+int topk_cap(int kmax);
+int topk_rcap(int kmax);
+int topk_slow_cap();
+fpp_status launch_count_entries(const DedupArgs& a, cudaStream_t st);
+fpp_status launch_dedup(const DedupArgs& a, int slots, cudaStream_t st);
+fpp_status launch_score(const ScoreArgs& a, int sm_count, cudaStream_t st);
+fpp_status launch_topk(const TopkArgs& a, cudaStream_t st);
 
 // Brute force top-k over a dense score matrix S [mq][lds] (n columns).
 fpp_status launch_topk_dense(const float* S, int64_t lds, int64_t mq, int64_t n, int k,

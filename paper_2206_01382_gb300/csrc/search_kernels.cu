@@ -212,6 +212,85 @@ probe_kernel(ProbeArgs a, int pmax) {
   }
 }
 
+// Thread-per-(query, table) variant of the fast pass for small budgets in
+// list mode (P + 1 <= EL <= 8): the same candidate pairs, selection and
+// margin test on at most 8 list entries per hash, held in registers.
+constexpr int SMALL_E = 8;
+
+__global__ void __launch_bounds__(256)
+probe_small_kernel(ProbeArgs a) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= a.mq * a.nt) return;
+  const int64_t q = idx / a.nt;
+  const int tl = (int)(idx % a.nt);
+  const int t = a.tb + tl;
+  const int D = a.D;
+  const int P = a.probes_pq ? a.probes_pq[q] : a.probes;
+  const int T = P + 1;
+  const int E = T < D ? T : D;
+  const int64_t NB = 4ll * D * D;
+  float va[2][SMALL_E];
+  uint32_t ha[2][SMALL_E];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const uint64_t* L = a.lists + (idx * 2 + j) * (int64_t)(a.EL + 1);
+#pragma unroll
+    for (int e = 0; e < SMALL_E; ++e) {
+      const uint64_t k = e < E ? L[e] : 0ull;
+      va[j][e] = __uint_as_float((uint32_t)(k >> 32) - 1u);
+      ha[j][e] = 0xFFFFFFFFu - (uint32_t)k;
+    }
+  }
+  // the best T pairs among (a+1)(b+1) <= T, kept sorted in registers
+  uint64_t best[SMALL_E + 1];
+#pragma unroll
+  for (int e = 0; e <= SMALL_E; ++e) best[e] = 0ull;
+  int C = 0;
+#pragma unroll
+  for (int x = 0; x < SMALL_E; ++x) {
+#pragma unroll
+    for (int y = 0; y < SMALL_E; ++y) {
+      if (x < E && y < E && (x + 1) * (y + 1) <= T) {
+        const uint32_t bucket = ha[0][x] * (uint32_t)(2 * D) + ha[1][y];
+        uint64_t key = ((uint64_t)float_key(va[0][x] + va[1][y]) << 32) |
+                       (uint64_t)(0xFFFFFFFFu - bucket);
+        ++C;
+#pragma unroll
+        for (int e = 0; e <= SMALL_E; ++e) {
+          const bool sw = key > best[e];
+          const uint64_t tv = best[e];
+          best[e] = sw ? key : tv;
+          key = sw ? tv : key;
+        }
+      }
+    }
+  }
+  const bool boundary = (int64_t)P < NB;
+  bool certain = C >= (boundary ? P + 1 : P);
+  if (certain && boundary) {
+    uint64_t kP = 0, kP1 = 0;
+#pragma unroll
+    for (int e = 0; e <= SMALL_E; ++e) {
+      if (e == P - 1) kP = best[e];
+      if (e == P) kP1 = best[e];
+    }
+    const float sP = key_score(kP), sP1 = key_score(kP1);
+    const float eps = a.gammaf * a.qnorm[q] * (a.rmax[2 * t] + a.rmax[2 * t + 1]);
+    const float need = (2.f * eps + 6.0e-8f * (fabsf(sP) + fabsf(sP1))) * 1.001f + 1e-30f;
+    certain = (sP - sP1) > need;
+  }
+  if (certain) {
+    uint32_t* dst = a.out + idx * (int64_t)a.probes;
+#pragma unroll
+    for (int e = 0; e < SMALL_E; ++e)
+      if (e < P) dst[e] = 0xFFFFFFFFu - (uint32_t)best[e];
+  } else {
+    const unsigned slot = atomicAdd(a.recheck_count, 1u);
+    a.recheck[slot] = (uint32_t)idx;
+    if (a.rechecks) atomicAdd(a.rechecks, 1ull);
+  }
+}
+
 // ---------------------------------------------------------------- exact pass
 
 constexpr int SLOW_PAIRS = 1024;
@@ -450,141 +529,54 @@ __global__ void query_norms_kernel(const float* __restrict__ Q, int64_t m, int64
 
 // ============================================================== gather + score
 //
-// A CTA runs NG independent queries at a time, one per group of GW warps
-// (queries are handed out by an atomic counter; groups synchronise with their
-// own named barrier, never with the whole CTA).  For its query a group:
-//  1. resolves the probed buckets together: their (start, size) pairs are
-//     read in parallel and prefix-summed, so the flattened bucket entries can
-//     be spread over the group's threads (binary search per entry);
-//  2. test-and-sets every kept id in the group's bitmap (n bits in global
-//     memory, L2-resident; one bitmap per group slot), collects the ids seen
-//     for the first time and scores them in batches, each warp taking up to
-//     32 rows at a time with coalesced float4 loads (G lanes per row), each
-//     warp keeping a running top-K' (K' = k + 16);
-//  3. merges the warps' lists and re-scores the best K' with the
-//     compensated dot product; the FP32 pre-selection is exact unless the
-//     K'-th FP32 score lies within the FP32 error bound of the k-th re-scored
-//     one, in which case the buckets are walked again and every candidate
-//     that could still reach the top-k is re-scored;
-//  4. walks the buckets once more to clear the bitmap words it touched.
+// Candidate gather, de-duplication and scoring run as four kernels per query
+// batch, so that the latency-bound part (walking buckets, bitmap
+// test-and-set) and the bandwidth-bound part (streaming candidate rows) each
+// get a launch shaped for them:
+//  count_entries  warp per query: bucket entries E_q of its probed buckets;
+//                 an exclusive scan gives each query a region of E_q slots;
+//  dedup          warp per query: walks the kept ids of its buckets (all
+//                 buckets resolved together, entries spread over the lanes),
+//                 test-and-sets each id in the warp's bitmap (n bits in
+//                 global memory, one bitmap per resident warp, L2-resident),
+//                 writes the ids seen first to the front of its region,
+//                 cuts them into work items of <= ITEM ids, and clears the
+//                 bitmap words it touched;
+//  score          flat over work items: every candidate row is read once
+//                 with coalesced float4 loads, 8 lanes per row and 16 rows in
+//                 flight per warp, and scored with the compensated dot
+//                 product, so scores are FP64-accurate;
+//  topk           warp per query: best k of its candidates by (score desc,
+//                 id asc).
 
-constexpr int GW = 1;                          // warps per query group
-constexpr int NG = 8;                          // query groups per CTA
-constexpr int GT = GW * 32;                    // threads per group
-constexpr int GS_THREADS = NG * GT;
-constexpr int SLOW_CAP = 2048;                 // slow-path list (global scratch, per slot)
-constexpr int KSLACK = 16;
-constexpr int PCHUNK = 128;                    // probed buckets resolved per pass
-constexpr int PPT = PCHUNK / GT;               // buckets per thread per pass
-constexpr int EPT = 8;                         // entries per thread per round
-constexpr int ROUND = GT * EPT;                // entries examined per round
-constexpr int CAND_CAP = 2 * ROUND;            // candidate ids buffered before scoring
+constexpr int DW = 8;                           // warps per dedup CTA
+constexpr int PCHUNK = 128;                     // probed buckets resolved per pass
+constexpr int PPT = PCHUNK / 32;                // buckets per lane per pass
+constexpr int EPT = 8;                          // entries per lane per round
+constexpr int ITEM = 128;                       // candidates per score work item
 
-struct GSLayout {
-  int kp, cap, mcap, rcap;
-  size_t q_off, pbase_off, pstart_off, cand_off, wtop_off, merge_off, resc_off, group;
-  size_t total;
-};
-
-__host__ __device__ inline GSLayout gs_layout(int kmax, int ldq) {
-  GSLayout L;
-  L.kp = kmax + KSLACK;
-  L.cap = pow2_ceil(2 * L.kp + 32);
-  L.mcap = pow2_ceil(GW * L.kp);
-  L.rcap = pow2_ceil(L.kp);
-  size_t o = 0;
-  L.q_off = o; o += (size_t)4 * ldq; o = (o + 15) & ~(size_t)15;
-  L.pbase_off = o; o += (size_t)8 * PCHUNK;
-  L.pstart_off = o; o += (size_t)4 * (PCHUNK + 1); o = (o + 15) & ~(size_t)15;
-  L.cand_off = o; o += (size_t)4 * CAND_CAP;
-  L.wtop_off = o; o += (size_t)GW * L.cap * 8;
-  L.merge_off = o; o += (size_t)L.mcap * 8;
-  L.resc_off = o; o += (size_t)L.rcap * 16;
-  o = (o + 15) & ~(size_t)15;
-  L.group = o;
-  L.total = o * NG;
-  return L;
-}
-
-__device__ __forceinline__ void group_sync(int g) {
-  if (GW == 1) {
-    __syncwarp();
-  } else {
-    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(GT) : "memory");
-  }
-}
-
-// Scores up to 32 rows ids[0..nrows) against q (FP32, coalesced float4 loads,
-// G lanes per row, four row groups in flight) and hands each (score, id) to
-// emit(lane_valid, score, id).  Warp-collective.
-template <int G, class Emit>
-__device__ __forceinline__ void score_rows(const uint32_t* ids, int nrows, const float4* q4,
-                                           int nf4, const float* __restrict__ X, int64_t ldx,
-                                           Emit emit) {
-  const int lane = threadIdx.x & 31;
-  constexpr int RPP = 32 / G;
-  constexpr int U = 4;
-  const int sub = lane % G, grp = lane / G;
-  for (int r0 = 0; r0 < nrows; r0 += U * RPP) {
-    uint32_t id[U];
-    bool ok[U];
-    float s[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int r = r0 + u * RPP + grp;
-      ok[u] = r < nrows;
-      id[u] = ids[ok[u] ? r : 0];
-      s[u] = 0.f;
-    }
-    for (int c = sub; c < nf4; c += G) {
-      const float4 qq = q4[c];
-      float4 v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        v[u] = ok[u] ? __ldg(reinterpret_cast<const float4*>(X + (int64_t)id[u] * ldx) + c)
-                     : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        s[u] = fmaf(v[u].x, qq.x, s[u]); s[u] = fmaf(v[u].y, qq.y, s[u]);
-        s[u] = fmaf(v[u].z, qq.z, s[u]); s[u] = fmaf(v[u].w, qq.w, s[u]);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-#pragma unroll
-      for (int o = G / 2; o > 0; o >>= 1) s[u] += __shfl_xor_sync(FULL, s[u], o);
-      emit(ok[u] && sub == 0, s[u], id[u]);
-    }
-  }
-}
-
-struct GroupCtx {
-  const GatherArgs* a;
-  int g;            // group index in the CTA
-  int gt;           // thread index in the group
+struct WarpWalk {
+  const DedupArgs* a;
   int64_t q;
   int Pq, nprobe;
   int64_t NB;
-  uint64_t* pbase;
-  uint32_t* pstart;
-  uint32_t* wsum;   // [GW] warp sums of the group scan
+  uint64_t* pbase;   // [PCHUNK] shared
+  uint32_t* pstart;  // [PCHUNK + 1] shared
 };
 
-// Walks the kept ids of every probed bucket of the group's query; visit(ids,
-// valid) runs on all group threads with EPT entries per thread per round,
-// then round_end().  Returns the number of entries walked.
+// Calls visit(id[EPT], has[EPT]) for every kept id of every probed bucket of
+// the warp's query, EPT ids per lane per round (warp-collective).
 template <class Visit>
-__device__ __forceinline__ uint64_t walk_entries(const GroupCtx& w, Visit& visit) {
-  const GatherArgs& a = *w.a;
-  const int lane = threadIdx.x & 31, gw = w.gt >> 5;
-  uint64_t walked = 0;
+__device__ __forceinline__ void warp_walk(const WarpWalk& w, Visit& visit) {
+  const DedupArgs& a = *w.a;
+  const int lane = threadIdx.x & 31;
   for (int pc0 = 0; pc0 < w.nprobe; pc0 += PCHUNK) {
     const int nc = min(PCHUNK, w.nprobe - pc0);
     uint32_t cnt[PPT];
     uint32_t tsum = 0;
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
-      const int i = w.gt * PPT + r;
+      const int i = lane * PPT + r;
       uint32_t c = 0;
       if (i < nc) {
         const int pi = pc0 + i;
@@ -605,30 +597,20 @@ __device__ __forceinline__ uint64_t walk_entries(const GroupCtx& w, Visit& visit
       const uint32_t t2 = __shfl_up_sync(FULL, inc, o);
       if (lane >= o) inc += t2;
     }
-    if (lane == 31) w.wsum[gw] = inc;
-    group_sync(w.g);
-    uint32_t wbase = 0, total = 0;
-#pragma unroll
-    for (int k = 0; k < GW; ++k) {
-      const uint32_t v = w.wsum[k];
-      wbase += k < gw ? v : 0u;
-      total += v;
-    }
-    uint32_t run = wbase + inc - tsum;
+    const uint32_t total = __shfl_sync(FULL, inc, 31);
+    uint32_t run = inc - tsum;
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
-      w.pstart[w.gt * PPT + r] = run;
+      w.pstart[lane * PPT + r] = run;
       run += cnt[r];
     }
-    if (w.gt == 0) w.pstart[PCHUNK] = total;
-    group_sync(w.g);
-    walked += total;
-    for (uint32_t e0 = 0; e0 < total; e0 += ROUND) {
+    __syncwarp();
+    for (uint32_t e0 = 0; e0 < total; e0 += 32 * EPT) {
       uint32_t id[EPT];
       bool has[EPT];
 #pragma unroll
       for (int r = 0; r < EPT; ++r) {
-        const uint32_t e = e0 + r * GT + w.gt;
+        const uint32_t e = e0 + r * 32 + lane;
         has[r] = e < total;
         id[r] = 0u;
         if (has[r]) {
@@ -641,230 +623,280 @@ __device__ __forceinline__ uint64_t walk_entries(const GroupCtx& w, Visit& visit
         }
       }
       visit(id, has);
-      visit.round_end();
     }
-    group_sync(w.g);
+    __syncwarp();
   }
-  return walked;
 }
 
-// Appends the lanes' flagged ids to the group's candidate buffer.
-__device__ __forceinline__ void append_ids(bool flag, uint32_t id, uint32_t* cand, unsigned* nc) {
-  const unsigned m = __ballot_sync(FULL, flag);
-  if (!m) return;
-  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-  unsigned base = 0;
-  if (lane == leader) base = atomicAdd(nc, (unsigned)__popc(m));
-  base = __shfl_sync(FULL, base, leader);
-  if (flag) cand[base + __popc(m & ((1u << lane) - 1u))] = id;
-}
-
-template <int G>
-__global__ void __launch_bounds__(GS_THREADS, 4)
-gather_score_kernel(GatherArgs a, unsigned long long* qcounter, int* err) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ long long s_q[NG];
-  __shared__ unsigned s_U[NG], s_nslow[NG], s_nc[NG];
-  __shared__ int s_slow[NG];
-  __shared__ double s_thr64[NG];
-  __shared__ uint32_t s_wsum[NG][GW];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int g = wid / GW, gw = wid % GW, gt = threadIdx.x - g * GT;
-  const GSLayout Lo = gs_layout(a.kmax, (int)a.ldq);
-  unsigned char* gsm = smem + (size_t)g * Lo.group;
-  float* qs = reinterpret_cast<float*>(gsm + Lo.q_off);
-  const float4* q4 = reinterpret_cast<const float4*>(qs);
-  uint64_t* pbase = reinterpret_cast<uint64_t*>(gsm + Lo.pbase_off);
-  uint32_t* pstart = reinterpret_cast<uint32_t*>(gsm + Lo.pstart_off);
-  uint32_t* cand = reinterpret_cast<uint32_t*>(gsm + Lo.cand_off);
-  uint64_t* wbuf = reinterpret_cast<uint64_t*>(gsm + Lo.wtop_off) + (size_t)gw * Lo.cap;
-  uint64_t* merge = reinterpret_cast<uint64_t*>(gsm + Lo.merge_off);
-  SD* resc = reinterpret_cast<SD*>(gsm + Lo.resc_off);
-  const int nf4 = (int)(a.ldq / 4);
+__global__ void __launch_bounds__(256)
+count_entries_kernel(DedupArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (q >= a.mq) return;
+  const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
   const int64_t NB = 4ll * a.D * a.D;
-  const int slot = blockIdx.x * NG + g;
-  SD* slow = reinterpret_cast<SD*>(a.slow_scratch) + (int64_t)slot * SLOW_CAP;
+  const int nprobe = a.nt * Pq;
+  uint32_t s = 0;
+  for (int pi = lane; pi < nprobe; pi += 32) {
+    const int tl = pi / Pq, p = pi - tl * Pq;
+    const uint32_t b = a.probes[(q * a.nt + tl) * (int64_t)a.pstride + p];
+    const uint32_t* off = a.offsets + (int64_t)(a.tb + tl) * (NB + 1);
+    s += off[b + 1] - off[b];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+  if (lane == 0) a.ecount[q] = s;
+}
+
+__global__ void __launch_bounds__(DW * 32, 4)
+dedup_kernel(DedupArgs a) {
+  __shared__ uint64_t s_pbase[DW][PCHUNK];
+  __shared__ uint32_t s_pstart[DW][PCHUNK + 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int slot = blockIdx.x * DW + wid;
   uint32_t* bm = a.bitmaps + (int64_t)slot * a.bitmap_words;
-  unsigned* nc = &s_nc[g];
-
-  for (;;) {
-    if (gt == 0) {
-      s_q[g] = (long long)atomicAdd(qcounter, 1ull);
-      s_U[g] = 0; s_nslow[g] = 0; s_slow[g] = 0; s_nc[g] = 0;
-    }
-    group_sync(g);
-    const int64_t q = s_q[g];
-    if (q >= a.mq) break;
-    const int kq = a.k_pq ? a.k_pq[q] : a.k;
+  const int64_t NB = 4ll * a.D * a.D;
+  unsigned long long ent = 0, uni = 0, prb = 0;
+  const int64_t nwarps = (int64_t)gridDim.x * DW;
+  for (int64_t q = (int64_t)blockIdx.x * DW + wid; q < a.mq; q += nwarps) {
     const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
-    const float* qg = a.Q + q * a.ldq;
-    for (int i = gt; i < (int)a.ldq; i += GT) qs[i] = qg[i];
-    const double qn = (double)a.qnorm[q];
-    const double eps_s = a.gamma * qn * (double)a.xmax;
-    const double du = 5.9604644775390625e-08 * (a.d + 8);
-    const double delta = 4.0 * du * du * qn * (double)a.xmax + 1e-300;
-    const int nprobe = a.nt * Pq;
-    GroupCtx wc{&a, g, gt, q, Pq, nprobe, NB, pbase, pstart, s_wsum[g]};
-
-    // ---------------- discover, de-duplicate, score
-    WarpTop wt;
-    wt.init(wbuf, Lo.cap, Lo.kp);
-    auto offer = [&](bool v, float s, uint32_t id) { wt.offer(v, pack_key(s, id)); };
-    auto drain = [&]() {   // group-uniform: score the buffered candidates
-      group_sync(g);
-      const unsigned n = *nc;
-      for (unsigned r0 = (unsigned)gw * 32; r0 < n; r0 += GW * 32)
-        score_rows<G>(cand + r0, (int)min(32u, n - r0), q4, nf4, a.X, a.ldx, offer);
-      group_sync(g);
-      if (gt == 0) { s_U[g] += n; *nc = 0; }
-      group_sync(g);
-    };
+    WarpWalk w{&a, q, Pq, a.nt * Pq, NB, s_pbase[wid], s_pstart[wid]};
+    uint32_t* out = a.cand + a.eoff[q];
     struct Discover {
-      uint32_t* bm; uint32_t* cand; unsigned* nc; int g; decltype(drain)* dr;
+      uint32_t* bm; uint32_t* out; uint32_t n;
       __device__ void operator()(const uint32_t (&id)[EPT], const bool (&has)[EPT]) {
         uint32_t old[EPT];
 #pragma unroll
         for (int r = 0; r < EPT; ++r)   // all atomics in flight before any result is used
           old[r] = has[r] ? atomicOr(bm + (id[r] >> 5), 1u << (id[r] & 31)) : 0xFFFFFFFFu;
+        const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
 #pragma unroll
-        for (int r = 0; r < EPT; ++r)
-          append_ids(!(old[r] & (1u << (id[r] & 31))), id[r], cand, nc);
+        for (int r = 0; r < EPT; ++r) {
+          const bool fresh = !(old[r] & (1u << (id[r] & 31)));
+          const unsigned m = __ballot_sync(FULL, fresh);
+          if (fresh) out[n + __popc(m & lt)] = id[r];
+          n += __popc(m);
+        }
       }
-      __device__ void round_end() {
-        group_sync(g);
-        if (*(volatile unsigned*)nc > (unsigned)(CAND_CAP - ROUND)) (*dr)();
-      }
-    } disc{bm, cand, nc, g, &drain};
-    const uint64_t entries = walk_entries(wc, disc);
-    drain();
-    const int nw = wt.finish();
-    for (int e = lane; e < Lo.kp; e += 32) merge[(size_t)gw * Lo.kp + e] = e < nw ? wbuf[e] : 0ull;
-    group_sync(g);
-    if (GW > 1 && gw == 0) {
-      for (int e = GW * Lo.kp + lane; e < Lo.mcap; e += 32) merge[e] = 0ull;
-      __syncwarp();
-      warp_sort_desc(merge, Lo.mcap);
+    } disc{bm, out, 0u};
+    warp_walk(w, disc);
+    const uint32_t U = disc.n;
+    if (lane == 0) {   // per-warp totals, summed over the warp below
+      ent += a.eoff[q + 1] - a.eoff[q];
+      uni += U;
+      prb += (unsigned long long)w.nprobe;
     }
-    group_sync(g);
+    if (lane == 0) a.ucount[q] = U;
+    // work items of at most ITEM candidates, in the query's own item slots
+    // [eoff[q] / ITEM + q, ...): ceil(E_q / ITEM) of them, never overlapping
+    // the next query's (unused slots stay zero-length)
+    const uint32_t nit = (U + ITEM - 1) / ITEM;
+    const uint64_t base = a.eoff[q] / ITEM + (uint64_t)q;
+    for (uint32_t k = lane; k < nit; k += 32) {
+      ScoreItem it;
+      it.q = (uint32_t)q;
+      it.len = min((uint32_t)ITEM, U - k * ITEM);
+      it.start = a.eoff[q] + (uint64_t)k * ITEM;
+      a.items[base + k] = it;
+    }
+    __syncwarp();
+    // clear the bitmap words of the ids just written (this warp wrote them)
+    for (uint32_t k = lane; k < U; k += 32) bm[out[k] >> 5] = 0u;
+    __syncwarp();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ent += __shfl_xor_sync(FULL, ent, o);
+    uni += __shfl_xor_sync(FULL, uni, o);
+    prb += __shfl_xor_sync(FULL, prb, o);
+  }
+  if (lane == 0 && a.stats) {
+    atomicAdd(a.stats + 0, ent);
+    atomicAdd(a.stats + 1, uni);
+    atomicAdd(a.stats + 3, prb);
+  }
+}
 
-    // ---------------- re-score the best K' with FP64 accuracy
-    const unsigned U = s_U[g];
-    const int Kpp = (int)(U < (unsigned)Lo.kp ? U : (unsigned)Lo.kp);
-    for (int e0 = gw * 8; e0 < Kpp; e0 += GW * 8) {
-      double sv[8];
-      uint32_t idv[8];
-      const float* rows[8];
+// FP32 scores of the candidates of a work item: G lanes per row, each lane
+// CPL float4 chunks of a row, U rows per lane group in flight (all U * CPL
+// row loads of a step issued before any is used; ids are read per step).
+// Every score is within gamma_d ||q|| ||x|| of the exact inner product.
+// EXACT: G * CPL float4 chunks cover a row exactly (no chunk loop).
+template <int G, int CPL, bool EXACT>
+__global__ void __launch_bounds__(256)
+score_kernel(ScoreArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t nslots = (int64_t)(a.eoff[a.mq] / ITEM) + a.mq + 1;
+  constexpr int RPP = 32 / G;
+  constexpr int U = 4;
+  const int sub = lane % G, grp = lane / G;
+  const int nf4 = (int)(a.ldx / 4);
+  for (int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < nslots; it += nw) {
+    const ScoreItem item = a.items[it];
+    if (item.len == 0) continue;
+    const float4* q4 = reinterpret_cast<const float4*>(a.Q + (int64_t)item.q * a.ldq);
+    const uint32_t* ids = a.cand + item.start;
+    float* out = a.scores + item.start;
+    for (int r0 = 0; r0 < (int)item.len; r0 += U * RPP) {
+      uint32_t id[U];
+      bool ok[U];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        idv[u] = key_id(merge[min(e0 + u, Kpp - 1)]);
-        rows[u] = a.X + (int64_t)idv[u] * a.ldx;
+      for (int u = 0; u < U; ++u) {
+        const int r = r0 + u * RPP + grp;
+        ok[u] = (uint32_t)r < item.len;
+        id[u] = ok[u] ? __ldg(ids + r) : 0u;
       }
-      warp_dot2_gather<8>(qs, rows, nf4, sv);
-      if (lane == 0)
-        for (int u = 0; u < 8 && e0 + u < Kpp; ++u) resc[e0 + u] = SD{sv[u], idv[u], 0};
-    }
-    for (int e = Kpp + gt; e < Lo.rcap; e += GT) resc[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
-    group_sync(g);
-    if (gw == 0) warp_sort_sd(resc, Lo.rcap);
-    group_sync(g);
-    if (gt == 0) {
-      if (U > (unsigned)Kpp) {
-        const double sK = (double)key_score(merge[Lo.kp - 1]);
-        const double need = resc[kq - 1].s;
-        if (!(sK + eps_s + 2.0 * delta < need)) {
-          s_slow[g] = 1;
-          s_thr64[g] = need - eps_s - 2.0 * delta;
+      float p[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) p[u] = 0.f;
+      for (int cb = 0; cb < nf4; cb += CPL * G) {   // a single pass when EXACT
+        float4 x[U][CPL];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            const int ch = cb + sub + c * G;
+            x[u][c] = (ok[u] && (EXACT || ch < nf4))
+                          ? __ldg(reinterpret_cast<const float4*>(a.X + (int64_t)id[u] * a.ldx) + ch)
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        float4 qq[CPL];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          const int ch = cb + sub + c * G;
+          qq[c] = (EXACT || ch < nf4) ? __ldg(q4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            p[u] = fmaf(x[u][c].x, qq[c].x, p[u]);
+            p[u] = fmaf(x[u][c].y, qq[c].y, p[u]);
+            p[u] = fmaf(x[u][c].z, qq[c].z, p[u]);
+            p[u] = fmaf(x[u][c].w, qq[c].w, p[u]);
+          }
+        if (EXACT) break;
       }
-      if (a.stats) {
-        atomicAdd(a.stats + 0, (unsigned long long)entries);
-        atomicAdd(a.stats + 1, (unsigned long long)U);
-        atomicAdd(a.stats + 3, (unsigned long long)nprobe);
-        if (s_slow[g]) atomicAdd(a.stats + 2, 1ull);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        float f = p[u];
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) f += __shfl_xor_sync(FULL, f, o);
+        if (ok[u] && sub == 0) out[r0 + u * RPP + grp] = f;
       }
     }
-    group_sync(g);
+  }
+}
 
-    const int64_t orow = q * a.kmax;
-    if (!s_slow[g]) {
-      for (int e = gt; e < a.kmax; e += GT) {
-        const bool ok = e < kq && e < Kpp;
-        a.out_ids[orow + e] = ok ? (int64_t)resc[e].id : -1;
-        a.out_scores[orow + e] = ok ? (float)resc[e].s : -INFINITY;
-      }
-      // ---------------- clear the touched bitmap words
-      struct Clear {
-        uint32_t* bm;
-        __device__ void operator()(const uint32_t (&id)[EPT], const bool (&has)[EPT]) {
+// Best k candidates of each query by (score desc, id asc).  The FP32 scores
+// pre-select the best K' = k + 16; those are re-scored with the compensated
+// dot product and sorted.  The selection is exact unless the K'-th FP32
+// score lies within the FP32 error bound of the k-th re-scored one; then
+// every candidate whose stored FP32 score could still reach the top-k is
+// re-scored (the slow path, rare).
+constexpr int TK_SLOW = 2048;
+
+__global__ void __launch_bounds__(256)
+topk_kernel(TopkArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * 8 + wid;
+  uint64_t* buf = reinterpret_cast<uint64_t*>(smem) + (size_t)wid * a.cap;
+  SD* resc = reinterpret_cast<SD*>(smem + (size_t)8 * a.cap * 8) + (size_t)wid * a.rcap;
+  if (q >= a.mq) return;
+  const int kq = a.k_pq ? a.k_pq[q] : a.k;
+  const int kp = kq + 16;
+  const uint64_t start = a.eoff[q];
+  const uint32_t U = a.ucount[q];
+  const float* sc = a.scores + start;
+  const uint32_t* cid = a.cand + start;
+  const float* qv = a.Q + q * a.ldq;
+  const int nf4 = (int)(a.ldq / 4);
+  WarpTop wt;
+  wt.init(buf, a.cap, kp);
+  for (uint32_t i0 = 0; i0 < U; i0 += 32) {
+    const uint32_t i = i0 + lane;
+    const bool ok = i < U;
+    wt.offer(ok, ok ? pack_key(sc[i], cid[i]) : 0ull);
+  }
+  const int nk = wt.finish();
+  // exact re-scoring of the pre-selected entries, 8 rows at a time
+  for (int e0 = 0; e0 < nk; e0 += 8) {
+    double sv[8];
+    uint32_t idv[8];
+    const float* rows[8];
 #pragma unroll
-          for (int r = 0; r < EPT; ++r)
-            if (has[r]) bm[id[r] >> 5] = 0u;
-        }
-        __device__ void round_end() {}
-      } clr{bm};
-      walk_entries(wc, clr);
-    } else {
-      // ---------------- slow path: every candidate that may reach the top-k
-      const double thr64 = s_thr64[g];
-      unsigned* nslow = &s_nslow[g];
-      auto collect = [&](bool v, float s, uint32_t id) {
-        if (v && (double)s >= thr64) {
-          const unsigned k = atomicAdd(nslow, 1u);
-          if (k < (unsigned)SLOW_CAP) slow[k].id = id;
-          else if (err) atomicExch(err, 1);
-        }
-      };
-      auto drain2 = [&]() {
-        group_sync(g);
-        const unsigned n = *nc;
-        for (unsigned r0 = (unsigned)gw * 32; r0 < n; r0 += GW * 32)
-          score_rows<G>(cand + r0, (int)min(32u, n - r0), q4, nf4, a.X, a.ldx, collect);
-        group_sync(g);
-        if (gt == 0) *nc = 0;
-        group_sync(g);
-      };
-      struct Revisit {
-        uint32_t* bm; uint32_t* cand; unsigned* nc; int g; decltype(drain2)* dr;
-        __device__ void operator()(const uint32_t (&id)[EPT], const bool (&has)[EPT]) {
-          uint32_t old[EPT];
-#pragma unroll
-          for (int r = 0; r < EPT; ++r)
-            old[r] = has[r] ? atomicAnd(bm + (id[r] >> 5), ~(1u << (id[r] & 31))) : 0u;
-#pragma unroll
-          for (int r = 0; r < EPT; ++r)
-            append_ids((old[r] & (1u << (id[r] & 31))) != 0u, id[r], cand, nc);
-        }
-        __device__ void round_end() {
-          group_sync(g);
-          if (*(volatile unsigned*)nc > (unsigned)(CAND_CAP - ROUND)) (*dr)();
-        }
-      } rev{bm, cand, nc, g, &drain2};
-      walk_entries(wc, rev);
-      drain2();
-      const int ns = (int)(*nslow < (unsigned)SLOW_CAP ? *nslow : (unsigned)SLOW_CAP);
-      __syncwarp();
-      for (int e0 = gw * 4; e0 < ns; e0 += GW * 4) {
-        double sv[4];
-        const float* rows[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) rows[u] = a.X + (int64_t)slow[min(e0 + u, ns - 1)].id * a.ldx;
-        warp_dot2_gather<4>(qs, rows, nf4, sv);
-        if (lane == 0)
-          for (int u = 0; u < 4 && e0 + u < ns; ++u) slow[e0 + u].s = sv[u];
-      }
-      __syncwarp();
-      const int np2 = pow2_ceil(ns > 1 ? ns : 1);
-      for (int e = ns + gt; e < np2; e += GT) slow[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
-      group_sync(g);
-      if (gw == 0) warp_sort_sd(slow, np2);
-      group_sync(g);
-      for (int e = gt; e < a.kmax; e += GT) {
-        const bool ok = e < kq && e < ns;
-        a.out_ids[orow + e] = ok ? (int64_t)slow[e].id : -1;
-        a.out_scores[orow + e] = ok ? (float)slow[e].s : -INFINITY;
-      }
+    for (int u = 0; u < 8; ++u) {
+      idv[u] = key_id(buf[min(e0 + u, nk - 1)]);
+      rows[u] = a.X + (int64_t)idv[u] * a.ldx;
     }
-    group_sync(g);
+    warp_dot2_gather<8>(qv, rows, nf4, sv);
+    if (lane == 0)
+      for (int u = 0; u < 8 && e0 + u < nk; ++u) resc[e0 + u] = SD{sv[u], idv[u], 0};
+  }
+  for (int e = nk + lane; e < a.rcap; e += 32) resc[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+  __syncwarp();
+  warp_sort_sd(resc, a.rcap);
+  bool slow = false;
+  double thr64 = 0.0;
+  if (U > (uint32_t)nk) {
+    const double qn = (double)a.qnorm[q];
+    const double eps_s = a.gamma * qn * (double)a.xmax;
+    const double du = 5.9604644775390625e-08 * (a.d + 8);
+    const double delta = 4.0 * du * du * qn * (double)a.xmax + 1e-300;
+    const double sK = (double)key_score(buf[nk - 1]);
+    const double need = resc[kq - 1].s;
+    if (!(sK + eps_s + 2.0 * delta < need)) {
+      slow = true;
+      thr64 = need - eps_s - 2.0 * delta;
+    }
+  }
+  const int64_t orow = q * a.kmax;
+  if (!slow) {
+    for (int e = lane; e < a.kmax; e += 32) {
+      const bool ok = e < kq && e < nk;
+      a.out_ids[orow + e] = ok ? (int64_t)resc[e].id : -1;
+      a.out_scores[orow + e] = ok ? (float)resc[e].s : -INFINITY;
+    }
+    return;
+  }
+  // slow path: every candidate whose FP32 score may still reach the top-k
+  if (lane == 0 && a.stats) atomicAdd(a.stats + 2, 1ull);
+  SD* list = reinterpret_cast<SD*>(a.slow) + (int64_t)(blockIdx.x * 8 + wid) * TK_SLOW;
+  unsigned ns = 0;
+  for (uint32_t i0 = 0; i0 < U; i0 += 32) {
+    const uint32_t i = i0 + lane;
+    const bool take = i < U && (double)sc[i] >= thr64;
+    const unsigned m = __ballot_sync(FULL, take);
+    if (take) {
+      const unsigned slot = ns + __popc(m & ((1u << lane) - 1u));
+      if (slot < (unsigned)TK_SLOW) list[slot].id = cid[i];
+    }
+    ns += __popc(m);
+  }
+  if (ns > (unsigned)TK_SLOW) {
+    if (lane == 0 && a.err) atomicExch(a.err, 1);
+    ns = TK_SLOW;
+  }
+  __syncwarp();
+  for (unsigned e0 = 0; e0 < ns; e0 += 8) {
+    double sv[8];
+    const float* rows[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) rows[u] = a.X + (int64_t)list[min(e0 + u, ns - 1)].id * a.ldx;
+    warp_dot2_gather<8>(qv, rows, nf4, sv);
+    if (lane == 0)
+      for (unsigned u = 0; u < 8 && e0 + u < ns; ++u) list[e0 + u].s = sv[u];
+  }
+  const int np2 = pow2_ceil(ns > 1 ? (int)ns : 1);
+  for (int e = (int)ns + lane; e < np2; e += 32) list[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+  __syncwarp();
+  warp_sort_sd(list, np2);
+  for (int e = lane; e < a.kmax; e += 32) {
+    const bool ok = e < kq && e < (int)ns;
+    a.out_ids[orow + e] = ok ? (int64_t)list[e].id : -1;
+    a.out_scores[orow + e] = ok ? (float)list[e].s : -INFINITY;
   }
 }
 
@@ -875,6 +907,7 @@ gather_score_kernel(GatherArgs a, unsigned long long* qcounter, int* err) {
 // with every column a candidate.
 constexpr int TD_WARPS = 8;
 constexpr int TD_SLOW = 2048;
+constexpr int KSLACK = 16;
 
 struct DenseLayout {
   int kp, cap, mcap, rcap;
@@ -1007,15 +1040,18 @@ int choose_g(int nf4) {
 }
 
 template <int G>
-fpp_status launch_gs(const GatherArgs& a, size_t smem, int grid, unsigned long long* qc, int* err,
-                     cudaStream_t st) {
-  static bool attr_set = false;  // per instantiation; benign race (idempotent)
-  if (!attr_set) {
-    FPP_CUDA(cudaFuncSetAttribute(gather_score_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  200 * 1024));
-    attr_set = true;
-  }
-  gather_score_kernel<G><<<grid, GS_THREADS, smem, st>>>(a, qc, err);
+fpp_status launch_score_g(const ScoreArgs& a, int grid, cudaStream_t st) {
+  // chunks per lane: ceil(nf4 / G) <= 4 by the choice of G, except G = 32
+  // (large d), which loops over chunk groups of 8
+  const int nf4 = (int)(a.ldx / 4);
+  const int cpl = (nf4 + G - 1) / G;
+  if (cpl == 1 && nf4 == G) score_kernel<G, 1, true><<<grid, 256, 0, st>>>(a);
+  else if (cpl == 2 && nf4 == 2 * G) score_kernel<G, 2, true><<<grid, 256, 0, st>>>(a);
+  else if (cpl == 4 && nf4 == 4 * G) score_kernel<G, 4, true><<<grid, 256, 0, st>>>(a);
+  else if (cpl <= 1) score_kernel<G, 1, false><<<grid, 256, 0, st>>>(a);
+  else if (cpl <= 2) score_kernel<G, 2, false><<<grid, 256, 0, st>>>(a);
+  else if (cpl <= 4) score_kernel<G, 4, false><<<grid, 256, 0, st>>>(a);
+  else score_kernel<G, 8, false><<<grid, 256, 0, st>>>(a);
   FPP_LAUNCHED();
   return FPP_OK;
 }
@@ -1044,7 +1080,11 @@ fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_b
   if (a.lists) FPP_CUDA(cudaMemsetAsync(a.recheck2_count, 0, sizeof(unsigned), st));
   const int S = pow2_ceil((a.D + 31) / 32);
   fpp_status s;
-  switch (S) {
+  if (a.lists && a.probes + 1 <= a.EL && a.EL <= SMALL_E) {
+    probe_small_kernel<<<(unsigned)ceil_div(warps, 256), 256, 0, st>>>(a);
+    FPP_LAUNCHED();
+    s = FPP_OK;
+  } else switch (S) {
     case 1: s = launch_probe_s<1>(a, st); break;
     case 2: s = launch_probe_s<2>(a, st); break;
     case 4: s = launch_probe_s<4>(a, st); break;
@@ -1082,32 +1122,56 @@ fpp_status launch_query_norms(const float* Q, int64_t m, int64_t ldq, int d, flo
   return FPP_OK;
 }
 
-int gather_slots(int sm_count) { return sm_count * 4 * NG; }
+int dedup_slots(int sm_count) { return sm_count * 4 * DW; }
+int score_item_len() { return ITEM; }
+int64_t score_item_slots(uint64_t entries_total, int64_t mq) {
+  return (int64_t)(entries_total / ITEM) + mq + 1;
+}
 
-int gather_slow_cap() { return SLOW_CAP; }
-
-fpp_status launch_gather_score(const GatherArgs& a, cudaStream_t st) {
+fpp_status launch_count_entries(const DedupArgs& a, cudaStream_t st) {
   if (a.mq <= 0) return FPP_OK;
-  const GSLayout Lo = gs_layout(a.kmax, (int)a.ldq);
-  if (Lo.total > 200 * 1024) {
-    set_error("gather_score: k too large for shared memory");
-    return FPP_EINVAL;
-  }
-  // a.stats[4] is the query counter, a.stats[5] the error flag (see the caller)
-  unsigned long long* qc = a.stats + 4;
-  int* err = reinterpret_cast<int*>(a.stats + 5);
-  const int64_t ctas = ceil_div(a.mq, NG);
-  const int grid = (int)(ctas < a.slots / NG ? ctas : a.slots / NG);
-  const int g = choose_g((int)(a.ldq / 4));
-  switch (g) {
-    case 1: return launch_gs<1>(a, Lo.total, grid, qc, err, st);
-    case 2: return launch_gs<2>(a, Lo.total, grid, qc, err, st);
-    case 4: return launch_gs<4>(a, Lo.total, grid, qc, err, st);
-    case 8: return launch_gs<8>(a, Lo.total, grid, qc, err, st);
-    case 16: return launch_gs<16>(a, Lo.total, grid, qc, err, st);
-    default: return launch_gs<32>(a, Lo.total, grid, qc, err, st);
+  count_entries_kernel<<<(unsigned)ceil_div(a.mq, 8), 256, 0, st>>>(a);
+  FPP_LAUNCHED();
+  return FPP_OK;
+}
+
+fpp_status launch_dedup(const DedupArgs& a, int slots, cudaStream_t st) {
+  if (a.mq <= 0) return FPP_OK;
+  const int64_t ctas = ceil_div(a.mq, DW);
+  const int grid = (int)std::min<int64_t>(ctas, slots / DW);
+  dedup_kernel<<<grid, DW * 32, 0, st>>>(a);
+  FPP_LAUNCHED();
+  return FPP_OK;
+}
+
+fpp_status launch_score(const ScoreArgs& a, int sm_count, cudaStream_t st) {
+  const int grid = sm_count * 8;
+  switch (choose_g((int)(a.ldx / 4))) {
+    case 1: return launch_score_g<1>(a, grid, st);
+    case 2: return launch_score_g<2>(a, grid, st);
+    case 4: return launch_score_g<4>(a, grid, st);
+    case 8: return launch_score_g<8>(a, grid, st);
+    case 16: return launch_score_g<16>(a, grid, st);
+    default: return launch_score_g<32>(a, grid, st);
   }
 }
+
+fpp_status launch_topk(const TopkArgs& a, cudaStream_t st) {
+  if (a.mq <= 0) return FPP_OK;
+  const size_t smem = (size_t)8 * a.cap * 8 + (size_t)8 * a.rcap * sizeof(SD);
+  static bool attr = false;
+  if (!attr) {
+    FPP_CUDA(cudaFuncSetAttribute(topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    attr = true;
+  }
+  topk_kernel<<<(unsigned)ceil_div(a.mq, 8), 256, smem, st>>>(a);
+  FPP_LAUNCHED();
+  return FPP_OK;
+}
+
+int topk_cap(int kmax) { return pow2_ceil(2 * (kmax + 16) + 32); }
+int topk_rcap(int kmax) { return pow2_ceil(kmax + 16); }
+int topk_slow_cap() { return TK_SLOW; }
 
 fpp_status launch_topk_dense(const float* S, int64_t lds, int64_t mq, int64_t n, int k,
                              const float* Q, int64_t ldq, const float* X, int64_t ldx, int d,

@@ -145,6 +145,75 @@ struct WarpTop {
   }
 };
 
+// An exact-score entry: order key of an FP64 score (larger = better) and id.
+struct SK {
+  uint64_t k;
+  uint32_t id;
+  uint32_t pad;
+};
+__device__ __forceinline__ bool sk_before(const SK& x, const SK& y) {
+  return x.k > y.k || (x.k == y.k && x.id < y.id);
+}
+__device__ __forceinline__ uint64_t double_key(double x) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double key_double(uint64_t k) {
+  const uint64_t u = (k & 0x8000000000000000ull) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+  return __longlong_as_double((long long)u);
+}
+
+__device__ __forceinline__ void warp_sort_sk(SK* a, int N) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 2; k <= N; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < N; i += 32) {
+        const int l = i ^ j;
+        if (l > i) {
+          const SK x = a[i], y = a[l];
+          const bool first = (i & k) == 0;
+          if (first ? sk_before(y, x) : sk_before(x, y)) { a[i] = y; a[l] = x; }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Per-warp running top-k of exact entries (same scheme as WarpTop).
+struct WarpTopSK {
+  SK* buf;
+  int cap, kp, cnt;
+  SK thr;
+  bool full;
+  __device__ __forceinline__ void init(SK* b, int c, int k) {
+    buf = b; cap = c; kp = k; cnt = 0; full = false; thr = SK{0ull, 0xFFFFFFFFu, 0u};
+  }
+  __device__ __forceinline__ void compact() {
+    const int lane = threadIdx.x & 31;
+    for (int i = cnt + lane; i < cap; i += 32) buf[i] = SK{0ull, 0xFFFFFFFFu, 0u};
+    __syncwarp();
+    warp_sort_sk(buf, cap);
+    cnt = cnt < kp ? cnt : kp;
+    if (cnt == kp) { thr = buf[kp - 1]; full = true; }
+    __syncwarp();
+  }
+  __device__ __forceinline__ void offer(bool valid, const SK& e) {
+    const int lane = threadIdx.x & 31;
+    const bool take = valid && (!full || sk_before(e, thr));
+    const unsigned m = __ballot_sync(0xffffffffu, take);
+    if (m == 0) return;
+    if (cnt + 32 > cap) compact();
+    if (take) buf[cnt + __popc(m & ((1u << lane) - 1u))] = e;
+    cnt += __popc(m);
+    __syncwarp();
+  }
+  __device__ __forceinline__ int finish() {
+    compact();
+    return cnt;
+  }
+};
+
 #endif  // __CUDACC__
 
 }  // namespace fpp

@@ -33,7 +33,7 @@ def test_struct_sizes_match_header(lib):
     assert (o.k, o.probes, o.k_max, o.table_begin, o.table_end) == (10, 1, 0, 0, 0)
     assert ctypes.sizeof(F.fpp_params) == 56
     assert ctypes.sizeof(F.fpp_search_opts) == 48
-    assert ctypes.sizeof(F.fpp_search_stats) == 80
+    assert ctypes.sizeof(F.fpp_search_stats) == 88
 
 
 @pytest.mark.parametrize("seed,L,D,d", [(2000, 10, 64, 64), (7, 3, 5, 13), (2001, 4, 256, 128)])
