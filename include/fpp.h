@@ -28,10 +28,13 @@
  *    reached the call's point (the call itself does not synchronise).
  *  - An fpp_index is immutable after fpp_build.  Concurrent searches on one
  *    index from several host threads are serialised by a per-index lock.
- *  - Decisions (bucket ids, probe sets, candidate sets, top-k ids) equal
- *    those of an exact FP64 evaluation of the method except where an FP64
- *    margin below 1e-6 makes two answers equally valid; returned scores are
- *    FP64-accurate inner products rounded to FP32.
+ *  - With precision FPP_FP32, decisions (bucket ids, probe sets, candidate
+ *    sets, top-k ids) equal those of an exact FP64 evaluation of the method
+ *    except where an FP64 margin below 1e-6 makes two answers equally valid;
+ *    returned scores are FP64-accurate inner products rounded to FP32.  With
+ *    FPP_BF16 the same holds except with the (small) probability that a BF16
+ *    rounding error exceeds the statistical window described at
+ *    fpp_precision; returned scores are still FP64-accurate.
  */
 #ifndef FPP_H_
 #define FPP_H_
@@ -54,7 +57,16 @@ typedef enum fpp_status {
 
 typedef enum fpp_precision {
   FPP_FP32 = 0,      /* FP32 storage and projections, FP64-exact decisions */
-  FPP_BF16 = 1       /* BF16 storage and projections, FP32 re-rank */
+  FPP_BF16 = 1       /* BF16 copies of X and R: projections are one BF16
+                        tensor-core product, candidate scores are read from
+                        BF16 rows (FP32 accumulation).  Decisions closer than
+                        nine estimated standard deviations of the BF16
+                        rounding error (fpp_projection_error_bound) are
+                        re-decided with compensated arithmetic on the FP32
+                        rows, and the best max(rerank_k, k + 16) candidates
+                        are re-scored on the FP32 rows before the top-k.  The
+                        index holds X in both precisions (6 bytes per
+                        element).  Graded by recall and score error. */
 } fpp_precision;
 
 /* Index parameters.  Initialise with fpp_default_params(). */
@@ -68,7 +80,7 @@ typedef struct fpp_params {
   const float* R;      /* optional explicit random vectors [L][2][D][d],
                           host or device; NULL = generate from seed. Copied. */
   int32_t precision;   /* fpp_precision                                      */
-  int32_t reserved0;
+  int32_t rerank_k;    /* FPP_BF16: shortlist re-ranked in FP32 (default 100)*/
   void* stream;        /* cudaStream_t for the build, or NULL (legacy)       */
 } fpp_params;
 
@@ -128,7 +140,8 @@ void fpp_default_search_opts(fpp_search_opts* o);
  * largest filter score |x^T r_i1| + |x^T r_i2| (ties: lower point id), and
  * stores each table as CSR.  X is copied; the caller keeps ownership.
  * Errors: FPP_EINVAL for n < 1, d < 1, L < 1, D outside 1..1024,
- * alpha outside (0, 1], iprobes < 1, kappa < 0, n >= 2^32.
+ * alpha outside (0, 1], iprobes < 1, kappa < 0, n >= 2^32, precision not
+ * an fpp_precision, rerank_k outside 0..256 with FPP_BF16.
  * *out is set only on success; release it with fpp_free. */
 fpp_status fpp_build(const float* X, int64_t n, int32_t d, const fpp_params* p,
                      fpp_index** out);
@@ -187,10 +200,12 @@ fpp_status fpp_debug_probes(const fpp_index* ix, const float* Q, int64_t m,
 /* fpp_debug_projections: the projections q^T r [m][2 L' D] of the queries
  *   onto the random vectors of tables [table_begin, table_end) (0, 0 = all),
  *   column (2 t' + j) D + i for table t' of the range, hash j, vector i, as
- *   the search computes them (tensor cores, exact three-piece BF16 split).
+ *   the search computes them (tensor cores; FPP_FP32: exact three-piece
+ *   BF16 split, FPP_BF16: one BF16 product).
  * fpp_projection_error_bound: the factor c such that every such projection
  *   is within c ||q|| ||r_i|| of the exact inner product; the search's
- *   decisions rely on it (Section 2.2's projections, evaluated in pieces). */
+ *   decisions rely on it (Section 2.2's projections, evaluated in pieces).
+ *   For FPP_BF16 c is the statistical near-tie window, not a bound. */
 fpp_status fpp_debug_projections(const fpp_index* ix, const float* Q, int64_t m,
                                  int32_t table_begin, int32_t table_end, float* out);
 fpp_status fpp_projection_error_bound(const fpp_index* ix, double* factor);

@@ -81,8 +81,13 @@ struct fpp_index {
   double alpha = 1.0;
   float* X = nullptr;          // [n][dpad]
   float* R = nullptr;          // [2 L D][dpad]
-  void* Rs = nullptr;          // [2 L D][3 Kp] BF16 pieces of R (tensor-core operand)
+  void* Rs = nullptr;          // [2 L D][pieces Kp] BF16 pieces of R (tensor-core operand)
   int Kp = 0;
+  int pieces = 3;              // 3: exact split (FPP_FP32); 1: plain BF16 (FPP_BF16)
+  void* Xb = nullptr;          // [n][ldxb] BF16 copy of X (FPP_BF16 only)
+  int64_t ldxb = 0;
+  int rerank_k = 0;            // FPP_BF16: shortlist re-ranked on the FP32 rows
+  double score_gamma = 0.0;    // candidate score error factor
   float* rmax = nullptr;       // [2L]
   float xmax = 0.f;
   uint32_t* offsets = nullptr; // [L][4D^2 + 1]
@@ -121,6 +126,7 @@ void free_index_memory(fpp_index* ix) {
   cudaFree(ix->X);
   cudaFree(ix->R);
   cudaFree(ix->Rs);
+  cudaFree(ix->Xb);
   cudaFree(ix->rmax);
   cudaFree(ix->offsets);
   cudaFree(ix->table_base);
@@ -156,18 +162,17 @@ struct BuildScratch {
   DevBuf proj, xsplit, recA, recB, counts, bstart, kstart, hist, scanbuf, scanscratch, small, rechecks;
 };
 
-constexpr int kPieces = 3;   // exact three-piece BF16 split for the FP32 path
-
 // Projection of rows [r0, r0 + rc) of a padded FP32 matrix onto the random
 // vectors of tables [t0, t0 + nt): split into BF16 pieces, tensor-core GEMM.
 fpp_status project_rows(const fpp_index* ix, const float* src, int64_t rc, DevBuf& split, int t0,
                         int nt, float* out, int64_t ldp, int* err, cudaStream_t st,
                         uint64_t* lists = nullptr, int EL = 0) {
-  FPP_TRY(split.ensure((size_t)rc * kPieces * ix->Kp * 2));
-  FPP_TRY(split_to_bf16(src, rc, ix->dpad, ix->d, kPieces, split.p, st));
-  const char* rb = static_cast<const char*>(ix->Rs) + (size_t)2 * t0 * ix->D * kPieces * ix->Kp * 2;
-  return project_tc(split.p, rc, rb, 2ll * nt * ix->D, ix->Kp, kPieces, ix->D, EL, out, ldp, lists,
-                    err, st);
+  FPP_TRY(split.ensure((size_t)rc * ix->pieces * ix->Kp * 2));
+  FPP_TRY(split_to_bf16(src, rc, ix->dpad, ix->d, ix->pieces, split.p, st));
+  const char* rb =
+      static_cast<const char*>(ix->Rs) + (size_t)2 * t0 * ix->D * ix->pieces * ix->Kp * 2;
+  return project_tc(split.p, rc, rb, 2ll * nt * ix->D, ix->Kp, ix->pieces, ix->D, EL, out, ldp,
+                    lists, err, st);
 }
 
 // List length of the fused projection epilogue for a probe budget, or 0
@@ -265,7 +270,14 @@ fpp_status validate_params(int64_t n, int32_t d, const fpp_params* p) {
   if (!(p->alpha > 0.0 && p->alpha <= 1.0)) { set_error("alpha must be in (0, 1]"); return FPP_EINVAL; }
   if (p->iprobes != 1) { set_error("iprobes > 1 is not supported yet"); return FPP_EINVAL; }
   if (p->kappa < 0) { set_error("kappa must be >= 0"); return FPP_EINVAL; }
-  if (p->precision != FPP_FP32) { set_error("only FPP_FP32 is supported yet"); return FPP_EINVAL; }
+  if (p->precision != FPP_FP32 && p->precision != FPP_BF16) {
+    set_error("precision must be FPP_FP32 or FPP_BF16");
+    return FPP_EINVAL;
+  }
+  if (p->precision == FPP_BF16 && (p->rerank_k < 0 || p->rerank_k > 256)) {
+    set_error("rerank_k must be in [0, 256]");
+    return FPP_EINVAL;
+  }
   return FPP_OK;
 }
 
@@ -281,7 +293,16 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
   ix->L = p->L; ix->D = p->D; ix->iprobes = p->iprobes; ix->kappa = p->kappa;
   ix->alpha = p->alpha; ix->precision = p->precision;
   ix->Kp = tc_kpad(d);
-  ix->gamma = tc_error_bound_factor(ix->Kp, kPieces);
+  if (p->precision == FPP_BF16) {
+    ix->pieces = 1;
+    ix->rerank_k = p->rerank_k;
+    ix->gamma = bf16_window_factor(d);
+    ix->score_gamma = bf16_window_factor(d);
+  } else {
+    ix->pieces = 3;
+    ix->gamma = tc_error_bound_factor(ix->Kp, 3);
+    ix->score_gamma = gamma_fp32(ix->dpad);
+  }
   if (cudaGetDevice(&ix->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&ix->sm_count, cudaDevAttrMultiProcessorCount, ix->device) != cudaSuccess) {
     set_error("no CUDA device");
@@ -310,12 +331,21 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
   if ((s = to_device_padded(X, n, d, ix->dpad, &ix->X, st, &ix->device_bytes)) != FPP_OK) return fail(s);
   if ((s = to_device_padded(hR.data(), rrows, d, ix->dpad, &ix->R, st, &ix->device_bytes)) != FPP_OK)
     return fail(s);
-  if (cudaMalloc(&ix->Rs, (size_t)rrows * kPieces * ix->Kp * 2) != cudaSuccess) {
+  if (cudaMalloc(&ix->Rs, (size_t)rrows * ix->pieces * ix->Kp * 2) != cudaSuccess) {
     set_error("cudaMalloc Rs");
     return fail(FPP_ENOMEM);
   }
-  ix->device_bytes += (uint64_t)rrows * kPieces * ix->Kp * 2;
-  if ((s = split_to_bf16(ix->R, rrows, ix->dpad, d, kPieces, ix->Rs, st)) != FPP_OK) return fail(s);
+  ix->device_bytes += (uint64_t)rrows * ix->pieces * ix->Kp * 2;
+  if ((s = split_to_bf16(ix->R, rrows, ix->dpad, d, ix->pieces, ix->Rs, st)) != FPP_OK) return fail(s);
+  if (ix->precision == FPP_BF16) {
+    ix->ldxb = round_up(d, 8);
+    if (cudaMalloc(&ix->Xb, (size_t)n * ix->ldxb * 2) != cudaSuccess) {
+      set_error("cudaMalloc Xb");
+      return fail(FPP_ENOMEM);
+    }
+    ix->device_bytes += (uint64_t)n * ix->ldxb * 2;
+    if ((s = rows_to_bf16(ix->X, n, ix->dpad, d, ix->ldxb, ix->Xb, st)) != FPP_OK) return fail(s);
+  }
   if (cudaMalloc(&ix->rmax, 2 * L * 4) != cudaSuccess) { set_error("cudaMalloc rmax"); return fail(FPP_ENOMEM); }
   if (cudaMemcpyAsync(ix->rmax, hrmax.data(), 2 * L * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) {
     set_error("copy rmax");
@@ -455,6 +485,12 @@ fpp_status validate_search(const fpp_index* ix, const float* Q, int64_t m, const
   return FPP_OK;
 }
 
+// Entries the top-k kernel re-scores exactly: k + 16, or the FP32 shortlist
+// of the BF16 path when that is longer.
+int topk_kprime(const fpp_index* ix, int kmax) {
+  return std::max(kmax + 16, ix->precision == FPP_BF16 ? ix->rerank_k : 0);
+}
+
 // Runs projection + probe ranking (and, unless probes_only, gather/score) for
 // queries [q0, q0 + mc).
 fpp_status search_chunk(fpp_index* ix, const float* Q, int64_t q0, int64_t mc, const SearchPlan& pl,
@@ -547,6 +583,7 @@ fpp_status search_chunk(fpp_index* ix, const float* Q, int64_t q0, int64_t mc, c
   sa.items = ws.items.as<ScoreItem>(); sa.eoff = ws.eoff.as<uint64_t>(); sa.mq = mc;
   sa.cand = ws.cand.as<uint32_t>();
   sa.X = ix->X; sa.ldx = ix->dpad; sa.Q = ws.qpad.as<float>(); sa.ldq = ix->dpad;
+  sa.Xb = ix->Xb; sa.ldxb = ix->ldxb;
   sa.scores = ws.cscores.as<float>();
   FPP_TRY(launch_score(sa, ix->sm_count, st));
   if (ev) FPP_CUDA(cudaEventRecord(ev[6], st));
@@ -554,8 +591,10 @@ fpp_status search_chunk(fpp_index* ix, const float* Q, int64_t q0, int64_t mc, c
   ta.mq = mc; ta.eoff = ws.eoff.as<uint64_t>(); ta.ucount = da.ucount; ta.cand = ws.cand.as<uint32_t>();
   ta.scores = ws.cscores.as<float>(); ta.k_pq = kpq; ta.k = pl.k; ta.kmax = pl.kmax;
   ta.X = ix->X; ta.ldx = ix->dpad; ta.Q = ws.qpad.as<float>(); ta.ldq = ix->dpad; ta.d = ix->d;
-  ta.qnorm = ws.qnorm.as<float>(); ta.xmax = ix->xmax; ta.gamma = gamma_fp32(ix->dpad);
-  ta.cap = topk_cap(pl.kmax); ta.rcap = topk_rcap(pl.kmax);
+  ta.qnorm = ws.qnorm.as<float>(); ta.xmax = ix->xmax; ta.gamma = ix->score_gamma;
+  ta.kprime = topk_kprime(ix, pl.kmax);
+  ta.approx = ix->precision == FPP_BF16;
+  ta.cap = topk_cap(ta.kprime); ta.rcap = topk_rcap(ta.kprime);
   ta.slow = ws.tkslow.p; ta.err = reinterpret_cast<int*>(stv + 5); ta.stats = stv;
   ta.out_ids = ids_dev; ta.out_scores = scores_dev;
   FPP_TRY(launch_topk(ta, st));
@@ -711,6 +750,7 @@ void fpp_default_params(fpp_params* p) {
   p->seed = 0;
   p->R = nullptr;
   p->precision = FPP_FP32;
+  p->rerank_k = 100;
   p->stream = nullptr;
 }
 

@@ -28,12 +28,17 @@ __device__ __forceinline__ uint32_t keep_dev(uint32_t B, const KeepRule& r) {
 // winner when its lead exceeds twice the GEMM error bound eps (and its value
 // exceeds eps, which fixes the sign); its projection is then recomputed with
 // the compensated dot product to give an FP64-accurate filter score.
-// Otherwise all D projections are recomputed compensated and the argmax is
-// taken on those (lowest index on ties), so bucket ids agree with an exact
-// evaluation except for genuine near-ties.
+// Otherwise the entries whose FP32 value is within 2 eps of the FP32 maximum
+// (the only ones that can be the exact maximum) are recomputed compensated,
+// or all D of them when that window holds more than WIN entries, and the
+// argmax is taken on those (lowest index on ties), so bucket ids agree with
+// an exact evaluation except for genuine near-ties.
+constexpr int WIN = 8;   // window entries recomputed before falling back to all D
+
 __global__ void __launch_bounds__(256)
 build_hash_kernel(HashArgs a) {
-  const int lane = threadIdx.x & 31;
+  __shared__ uint32_t win[8][WIN];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w >= a.rows * a.nt) return;
   const int64_t r = w / a.nt;
@@ -86,23 +91,70 @@ build_hash_kernel(HashArgs a) {
       h[j] = i1 + (val[j] < 0.0 ? D : 0);
     } else {
       if (lane == 0 && a.rechecks) atomicAdd(a.rechecks, 1ull);
-      // every lane computes the same running argmax (rows in increasing
-      // order, strict comparison: lowest index on ties)
+      // window: only entries whose FP32 |p| is within 2 eps of the FP32
+      // maximum can be the exact maximum; recompute those when they are few
+      const float lim = b1 - 2.f * eps;
+      int nc = 0;
+      bool all = false;
+      if (a.P) {
+        const float* pr = a.P + r * a.ldp + (int64_t)(2 * tl + j) * D;
+        for (int i0 = 0; i0 < D && !all; i0 += 32) {
+          const int i = i0 + lane;
+          const bool in = i < D && fabsf(pr[i]) >= lim;
+          const unsigned m = __ballot_sync(0xffffffffu, in);
+          if (in) {
+            const int slot = nc + __popc(m & ((1u << lane) - 1u));
+            if (slot < WIN) win[wid][slot] = (uint32_t)i;
+          }
+          nc += __popc(m);
+          if (nc > WIN) all = true;
+        }
+      } else {
+        const uint64_t* kk = a.lists + ((r * a.nt + tl) * 2 + j) * (int64_t)(a.EL + 1);
+        const float cut = kk[a.EL] ? __uint_as_float((uint32_t)(kk[a.EL] >> 32) - 1u) : -1.f;
+        if (!(cut < lim)) {
+          all = true;
+        } else if (lane == 0) {
+          for (int e = 0; e < a.EL; ++e)
+            if (kk[e] && __uint_as_float((uint32_t)(kk[e] >> 32) - 1u) >= lim)
+              win[wid][nc++] = (0xFFFFFFFFu - (uint32_t)kk[e]) % (uint32_t)D;
+        }
+        nc = __shfl_sync(0xffffffffu, nc, 0);
+      }
+      __syncwarp();
       double bv = -1.0, bs = 0.0;
       int bi = INT_MAX;
       const int nf4 = (int)(a.ldr / 4);
-      int i = 0;
-      for (; i + 4 <= D; i += 4) {
-        double v[4];
-        warp_dot2_rows<4>(x, Rj + (int64_t)i * a.ldr, a.ldr, nf4, v);
+      if (!all) {
+        // every lane computes the same argmax (lowest index on ties)
+        const float* rows[WIN];
+        uint32_t ii[WIN];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (fabs(v[k]) > bv) { bv = fabs(v[k]); bs = v[k]; bi = i + k; }
-      }
-      for (; i < D; ++i) {
-        double v[1];
-        warp_dot2_rows<1>(x, Rj + (int64_t)i * a.ldr, a.ldr, nf4, v);
-        if (fabs(v[0]) > bv) { bv = fabs(v[0]); bs = v[0]; bi = i; }
+        for (int e = 0; e < WIN; ++e) {
+          ii[e] = win[wid][e < nc ? e : 0];
+          rows[e] = Rj + (int64_t)ii[e] * a.ldr;
+        }
+        double v[WIN];
+        warp_dot2_gather<WIN>(x, rows, nf4, v);
+#pragma unroll
+        for (int e = 0; e < WIN; ++e)
+          if (e < nc && (fabs(v[e]) > bv || (fabs(v[e]) == bv && (int)ii[e] < bi))) {
+            bv = fabs(v[e]); bs = v[e]; bi = (int)ii[e];
+          }
+      } else {
+        int i = 0;
+        for (; i + 4 <= D; i += 4) {
+          double v[4];
+          warp_dot2_rows<4>(x, Rj + (int64_t)i * a.ldr, a.ldr, nf4, v);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (fabs(v[k]) > bv) { bv = fabs(v[k]); bs = v[k]; bi = i + k; }
+        }
+        for (; i < D; ++i) {
+          double v[1];
+          warp_dot2_rows<1>(x, Rj + (int64_t)i * a.ldr, a.ldr, nf4, v);
+          if (fabs(v[0]) > bv) { bv = fabs(v[0]); bs = v[0]; bi = i; }
+        }
       }
       val[j] = bs;
       h[j] = bi + (bs < 0.0 ? D : 0);

@@ -26,6 +26,8 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <cmath>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -478,6 +480,38 @@ double tc_error_bound_factor(int Kp, int pieces) {
   // piece residuals.  Plain BF16: the input rounding 2 * 2^-8 dominates.
   if (pieces == 1) return 2.0 * 3.90625e-3 + 2.0 * gamma_fp32(Kp) + 1.6e-5;
   return 2.0 * gamma_fp32(Kp) * 1.05 + 2.0e-7;
+}
+
+double bf16_window_factor(int d) {
+  // Near-tie window of the BF16 path, relative to ||a|| ||b||.  Rounding both
+  // operands to BF16 (unit roundoff u = 2^-8) perturbs each product by a
+  // relative error of variance at most 2 u^2 / 3, so for vectors whose mass
+  // is spread over the d coordinates the projection error has standard
+  // deviation about sqrt(2/3) u ||a|| ||b|| / sqrt(d).  The window is nine of
+  // those plus the worst-case FP32 accumulation error: a statistical margin,
+  // not a bound (the BF16 path is graded by recall and score error).
+  return 9.0 * 0.816496580927726 * 3.90625e-3 / std::sqrt((double)d) +
+         2.0 * gamma_fp32(tc_kpad(d));
+}
+
+namespace {
+__global__ void rows_bf16_kernel(const float* __restrict__ src, int64_t rows, int64_t lds, int d,
+                                 int64_t ldo, __nv_bfloat16* __restrict__ dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * ldo) return;
+  const int64_t r = i / ldo;
+  const int c = (int)(i - r * ldo);
+  dst[i] = __float2bfloat16_rn(c < d ? src[r * lds + c] : 0.f);
+}
+}  // namespace
+
+fpp_status rows_to_bf16(const float* src, int64_t rows, int64_t lds, int d, int64_t ldo, void* dst,
+                        cudaStream_t st) {
+  if (rows <= 0) return FPP_OK;
+  rows_bf16_kernel<<<(unsigned)ceil_div(rows * ldo, 256), 256, 0, st>>>(
+      src, rows, lds, d, ldo, reinterpret_cast<__nv_bfloat16*>(dst));
+  FPP_LAUNCHED();
+  return FPP_OK;
 }
 
 fpp_status split_to_bf16(const float* src, int64_t rows, int64_t lds, int d, int pieces,

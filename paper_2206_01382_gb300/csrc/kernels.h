@@ -25,6 +25,11 @@ fpp_status gemm_f32_nt(const float* A, int64_t lda, const float* B, int64_t ldb,
 // arrays [rows][pieces * Kp] made by split_to_bf16; C is FP32 [M][ldc].
 int tc_kpad(int d);
 double tc_error_bound_factor(int Kp, int pieces);
+// Near-tie window (relative to ||a|| ||b||) of plain BF16 projections and scores.
+double bf16_window_factor(int d);
+// FP32 rows [rows][lds] (d used) -> BF16 rows [rows][ldo], zero padded.
+fpp_status rows_to_bf16(const float* src, int64_t rows, int64_t lds, int d, int64_t ldo, void* dst,
+                        cudaStream_t st);
 fpp_status split_to_bf16(const float* src, int64_t rows, int64_t lds, int d, int pieces,
                          void* dst, cudaStream_t st);
 fpp_status gemm_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, int pieces,
@@ -154,6 +159,8 @@ struct ScoreArgs {
   int64_t ldx;
   const float* Q;            // [mq][ldq] (ldq == ldx)
   int64_t ldq;
+  const void* Xb;            // BF16 rows [n][ldxb] (precision path) or NULL
+  int64_t ldxb;
   float* scores;             // FP32 scores, parallel to cand
 };
 
@@ -173,6 +180,8 @@ struct TopkArgs {
   double gamma;              // FP32 score error factor gamma_d
   const int32_t* k_pq;       // [mq] or NULL
   int k, kmax, cap, rcap;
+  int kprime;                // shortlist re-scored exactly (>= k + 16)
+  int approx;                // precision path: overflow of the slow list is not an error
   void* slow;                // [ceil(mq / 8) * 8][topk_slow_cap()] 16-byte entries
   int* err;
   unsigned long long* stats; // stats[2] counts slow-path queries
@@ -183,8 +192,8 @@ struct TopkArgs {
 int dedup_slots(int sm_count);
 int score_item_len();
 int64_t score_item_slots(uint64_t entries_total, int64_t mq);
-int topk_cap(int kmax);
-int topk_rcap(int kmax);
+int topk_cap(int kprime);
+int topk_rcap(int kprime);
 int topk_slow_cap();
 fpp_status launch_count_entries(const DedupArgs& a, cudaStream_t st);
 fpp_status launch_dedup(const DedupArgs& a, int slots, cudaStream_t st);

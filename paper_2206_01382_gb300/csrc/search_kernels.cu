@@ -3,6 +3,8 @@
 // de-duplication, exact scoring and top-k (Sections 1 and 4).
 #include <climits>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "topk.cuh"
@@ -789,6 +791,80 @@ score_kernel(ScoreArgs a) {
   }
 }
 
+// BF16 rows (precision path): the same structure, each chunk 8 BF16 values
+// (16 bytes) against 8 FP32 query values, FP32 accumulation.
+template <int G, int CPL, bool EXACT>
+__global__ void __launch_bounds__(256)
+score_bf16_kernel(ScoreArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t nslots = (int64_t)(a.eoff[a.mq] / ITEM) + a.mq + 1;
+  constexpr int RPP = 32 / G;
+  constexpr int U = 4;
+  const int sub = lane % G, grp = lane / G;
+  const int nch = (int)(a.ldxb / 8);
+  const uint4* Xb = reinterpret_cast<const uint4*>(a.Xb);
+  for (int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < nslots; it += nw) {
+    const ScoreItem item = a.items[it];
+    if (item.len == 0) continue;
+    const float4* q4 = reinterpret_cast<const float4*>(a.Q + (int64_t)item.q * a.ldq);
+    const uint32_t* ids = a.cand + item.start;
+    float* out = a.scores + item.start;
+    for (int r0 = 0; r0 < (int)item.len; r0 += U * RPP) {
+      uint32_t id[U];
+      bool ok[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int r = r0 + u * RPP + grp;
+        ok[u] = (uint32_t)r < item.len;
+        id[u] = ok[u] ? __ldg(ids + r) : 0u;
+      }
+      float p[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) p[u] = 0.f;
+      for (int cb = 0; cb < nch; cb += CPL * G) {
+        uint4 x[U][CPL];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            const int ch = cb + sub + c * G;
+            x[u][c] = (ok[u] && (EXACT || ch < nch)) ? __ldg(Xb + (int64_t)id[u] * (a.ldxb / 8) + ch)
+                                                     : make_uint4(0u, 0u, 0u, 0u);
+          }
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          const int ch = cb + sub + c * G;
+          const bool in = EXACT || ch < nch;
+          const float4 qa = in ? __ldg(q4 + 2 * ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+          // the query row may end 4 floats before the padded BF16 row
+          const bool inb = in && 8 * ch + 4 < a.ldq;
+          const float4 qb = inb ? __ldg(q4 + 2 * ch + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const float2 f0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&x[u][c].x));
+            const float2 f1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&x[u][c].y));
+            const float2 f2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&x[u][c].z));
+            const float2 f3 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&x[u][c].w));
+            p[u] = fmaf(f0.x, qa.x, p[u]); p[u] = fmaf(f0.y, qa.y, p[u]);
+            p[u] = fmaf(f1.x, qa.z, p[u]); p[u] = fmaf(f1.y, qa.w, p[u]);
+            p[u] = fmaf(f2.x, qb.x, p[u]); p[u] = fmaf(f2.y, qb.y, p[u]);
+            p[u] = fmaf(f3.x, qb.z, p[u]); p[u] = fmaf(f3.y, qb.w, p[u]);
+          }
+        }
+        if (EXACT) break;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        float f = p[u];
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) f += __shfl_xor_sync(FULL, f, o);
+        if (ok[u] && sub == 0) out[r0 + u * RPP + grp] = f;
+      }
+    }
+  }
+}
+
 // Best k candidates of each query by (score desc, id asc).  The FP32 scores
 // pre-select the best K' = k + 16; those are re-scored with the compensated
 // dot product and sorted.  The selection is exact unless the K'-th FP32
@@ -806,7 +882,7 @@ topk_kernel(TopkArgs a) {
   SD* resc = reinterpret_cast<SD*>(smem + (size_t)8 * a.cap * 8) + (size_t)wid * a.rcap;
   if (q >= a.mq) return;
   const int kq = a.k_pq ? a.k_pq[q] : a.k;
-  const int kp = kq + 16;
+  const int kp = max(kq + 16, a.kprime);   // the FP32 re-ranked shortlist
   const uint64_t start = a.eoff[q];
   const uint32_t U = a.ucount[q];
   const float* sc = a.scores + start;
@@ -876,7 +952,9 @@ topk_kernel(TopkArgs a) {
     ns += __popc(m);
   }
   if (ns > (unsigned)TK_SLOW) {
-    if (lane == 0 && a.err) atomicExch(a.err, 1);
+    // exact mode cannot guarantee the result; the BF16 path keeps the best
+    // effort (the shortlist order is approximate there anyway)
+    if (lane == 0 && a.err && !a.approx) atomicExch(a.err, 1);
     ns = TK_SLOW;
   }
   __syncwarp();
@@ -1144,8 +1222,35 @@ fpp_status launch_dedup(const DedupArgs& a, int slots, cudaStream_t st) {
   return FPP_OK;
 }
 
+template <int G>
+fpp_status launch_score_bf(const ScoreArgs& a, int grid, cudaStream_t st) {
+  const int nch = (int)(a.ldxb / 8);
+  const int cpl = (nch + G - 1) / G;
+  if (cpl == 1 && nch == G) score_bf16_kernel<G, 1, true><<<grid, 256, 0, st>>>(a);
+  else if (cpl == 2 && nch == 2 * G) score_bf16_kernel<G, 2, true><<<grid, 256, 0, st>>>(a);
+  else if (cpl <= 1) score_bf16_kernel<G, 1, false><<<grid, 256, 0, st>>>(a);
+  else if (cpl <= 2) score_bf16_kernel<G, 2, false><<<grid, 256, 0, st>>>(a);
+  else score_bf16_kernel<G, 4, false><<<grid, 256, 0, st>>>(a);
+  FPP_LAUNCHED();
+  return FPP_OK;
+}
+
 fpp_status launch_score(const ScoreArgs& a, int sm_count, cudaStream_t st) {
   const int grid = sm_count * 8;
+  if (a.Xb) {
+    // 16-byte chunks of 8 BF16; at most 2 chunks per lane before G = 32
+    int g = 1;
+    const int nch = (int)(a.ldxb / 8);
+    while (g < 32 && g * 2 < nch) g <<= 1;
+    switch (g) {
+      case 1: return launch_score_bf<1>(a, grid, st);
+      case 2: return launch_score_bf<2>(a, grid, st);
+      case 4: return launch_score_bf<4>(a, grid, st);
+      case 8: return launch_score_bf<8>(a, grid, st);
+      case 16: return launch_score_bf<16>(a, grid, st);
+      default: return launch_score_bf<32>(a, grid, st);
+    }
+  }
   switch (choose_g((int)(a.ldx / 4))) {
     case 1: return launch_score_g<1>(a, grid, st);
     case 2: return launch_score_g<2>(a, grid, st);
@@ -1169,8 +1274,8 @@ fpp_status launch_topk(const TopkArgs& a, cudaStream_t st) {
   return FPP_OK;
 }
 
-int topk_cap(int kmax) { return pow2_ceil(2 * (kmax + 16) + 32); }
-int topk_rcap(int kmax) { return pow2_ceil(kmax + 16); }
+int topk_cap(int kprime) { return pow2_ceil(2 * kprime + 32); }
+int topk_rcap(int kprime) { return pow2_ceil(kprime); }
 int topk_slow_cap() { return TK_SLOW; }
 
 fpp_status launch_topk_dense(const float* S, int64_t lds, int64_t mq, int64_t n, int k,

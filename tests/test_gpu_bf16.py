@@ -1,0 +1,134 @@
+"""BF16 precision path (FPP_BF16) against the FP64 oracle and the exact path.
+
+The BF16 path decides on one-product BF16 projections and BF16 candidate
+scores; decisions inside a statistical near-tie window are re-decided on the
+FP32 rows and a shortlist is re-scored exactly.  It is graded by recall and
+score error, so these tests bound the disagreement rather than require none:
+bucket ids, probe sets and top-k ids agree with the oracle except on a small
+fraction of decisions, returned scores are exact inner products of the
+returned ids, and recall matches the exact path's.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests import parity as PT
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2206_01382_gb300 as F
+    from paper_2206_01382_gb300 import _build
+    _build.build()
+    F.load()
+    return F
+
+
+def _exact_scores(X, Q, ids):
+    X64, Q64 = X.astype(np.float64), Q.astype(np.float64)
+    out = np.full(ids.shape, -np.inf)
+    for i in range(ids.shape[0]):
+        ok = ids[i] >= 0
+        out[i, ok] = X64[ids[i, ok]] @ Q64[i]
+    return out
+
+
+def test_bf16_window_covers_projection_error(F):
+    # every BF16 projection error stays inside the near-tie window
+    for d, D, L in ((128, 256, 2), (960, 64, 1), (37, 5, 3)):
+        X, Q = W.small_mixture(800, 400, d, 32, 0.25, 300 + d)
+        ix = F.Index(X, L, D, 0.5, seed=50 + d, precision=F.FPP_BF16)
+        P = F.fpp_debug_projections(ix.handle, Q).astype(np.float64)
+        R = O.gaussian_rotations(50 + d, L, D, d).astype(np.float64).reshape(-1, d)
+        Q64 = Q.astype(np.float64)
+        exact = Q64 @ R.T
+        c = F.fpp_projection_error_bound(ix.handle)
+        win = c * np.linalg.norm(Q64, axis=1)[:, None] * np.linalg.norm(R, axis=1)[None, :]
+        ratio = np.abs(P - exact) / win
+        assert float(ratio.max()) < 1.0, (d, float(ratio.max()))
+        # and the projections really are single BF16 products (not the split)
+        assert float(np.abs(P - exact).max()) > 1e-4 * float(np.abs(exact).max())
+
+
+def test_bf16_tiny_decisions_match_oracle(F):
+    w = W.WORKLOADS["tiny"]
+    X, Q = W.dataset(w)
+    ix_o = O.build_index(X, w.L, w.D, w.alpha, seed=w.rot_seed)
+    ix_b = F.Index(X, w.L, w.D, w.alpha, seed=w.rot_seed, precision=F.FPP_BF16)
+    excl, bad_points = {}, 0
+    for t in range(w.L):
+        gpb = F.fpp_debug_point_buckets(ix_b.handle, t)
+        nbad, unexplained = PT.compare_point_buckets(ix_o, t, gpb)
+        bad_points += len(unexplained)
+        excl[t] = PT.excluded_buckets(ix_o, t, gpb)
+        # buckets holding a point hashed differently may differ too
+        ora = ix_o.point_buckets[t]
+        diff = np.nonzero(ora != gpb.astype(np.int64))[0]
+        excl[t].update(ora[diff].tolist())
+        excl[t].update(gpb[diff].astype(np.int64).tolist())
+        off, ids = F.fpp_debug_table(ix_b.handle, t)
+        assert not PT.compare_table(ix_o, t, off, ids, excl[t]), t
+    assert bad_points <= 1e-4 * X.shape[0] * w.L, bad_points
+    for P in (1, 4, 16):
+        gp = F.fpp_debug_probes(ix_b.handle, Q, P)
+        c, s, fails = PT.compare_probes(ix_o, Q, P, gp, list(range(w.L)))
+        assert len(fails) <= 0.002 * max(c, 1), (P, len(fails), c)
+        gi, gs = ix_b.search(Q, w.k, P)
+        _, _, res = O.search_batch(ix_o, Q, w.k, P)
+        c, s, fails = PT.compare_search(res, gi, gs, w.k, list(range(w.L)), excl)
+        assert len(fails) <= 0.02 * max(c, 1), (P, len(fails), c, fails[:3])
+        assert c >= 0.8 * len(res)
+        # scores are exact inner products of the returned ids
+        ex = _exact_scores(X, Q, gi)
+        fin = gi >= 0
+        assert np.all(np.isfinite(gs) == fin)
+        err = np.abs(gs[fin].astype(np.float64) - ex[fin])
+        assert float(err.max(initial=0.0)) <= 1e-5 * max(1.0, float(np.abs(ex[fin]).max()))
+
+
+def test_bf16_recall_matches_exact_path(F):
+    X, Q = W.small_mixture(60000, 300, 96, 256, 0.3 / np.sqrt(96), 311)
+    k = 10
+    bi, _, _ = O.brute_force(X, Q, k)
+    ix32 = F.Index(X, 20, 64, 0.1, seed=12)
+    ix16 = F.Index(X, 20, 64, 0.1, seed=12, precision=F.FPP_BF16)
+    for P in (1, 4, 16):
+        i32, _ = ix32.search(Q, k, P)
+        i16, s16 = ix16.search(Q, k, P)
+        r32 = O.recall_at(i32, bi, k)
+        r16 = O.recall_at(i16, bi, k)
+        assert r16 >= r32 - 0.005, (P, r32, r16)
+        same = np.mean([np.array_equal(a, b) for a, b in zip(i32, i16)])
+        assert same >= 0.97, (P, same)
+
+
+@pytest.mark.parametrize("rerank_k", [0, 5, 100, 256])
+def test_bf16_rerank_lengths(F, rerank_k):
+    # shortlists shorter or longer than k + 16 give the same answer here
+    X, Q = W.small_mixture(20000, 100, 64, 64, 0.25, 312)
+    ix = F.Index(X, 8, 32, 0.2, seed=3, precision=F.FPP_BF16, rerank_k=rerank_k)
+    ref = F.Index(X, 8, 32, 0.2, seed=3)
+    gi, gs = ix.search(Q, 20, 4)
+    ri, rs = ref.search(Q, 20, 4)
+    same = np.mean([np.array_equal(a, b) for a, b in zip(gi, ri)])
+    assert same >= 0.97, same
+
+
+def test_bf16_ragged_dimension(F):
+    # d not a multiple of 8: the BF16 rows are zero padded
+    X, Q = W.small_mixture(3000, 50, 37, 30, 0.2, 313)
+    ix = F.Index(X, 3, 5, 0.37, seed=5, precision=F.FPP_BF16)
+    gi, gs = ix.search(Q, 7, 11)
+    ex = _exact_scores(X, Q, gi)
+    fin = gi >= 0
+    assert fin.any()
+    assert float(np.abs(gs[fin] - ex[fin]).max()) <= 1e-5
+    info = ix.info()
+    assert info["precision"] == F.FPP_BF16
