@@ -34,7 +34,8 @@
  *    returned scores are FP64-accurate inner products rounded to FP32.  With
  *    FPP_BF16 the same holds except with the (small) probability that a BF16
  *    rounding error exceeds the statistical window described at
- *    fpp_precision; returned scores are still FP64-accurate.
+ *    fpp_precision (the top-k ids may then differ); returned scores are
+ *    still FP64-accurate.
  */
 #ifndef FPP_H_
 #define FPP_H_
@@ -57,16 +58,15 @@ typedef enum fpp_status {
 
 typedef enum fpp_precision {
   FPP_FP32 = 0,      /* FP32 storage and projections, FP64-exact decisions */
-  FPP_BF16 = 1       /* BF16 copies of X and R: projections are one BF16
-                        tensor-core product, candidate scores are read from
-                        BF16 rows (FP32 accumulation).  Decisions closer than
-                        nine estimated standard deviations of the BF16
-                        rounding error (fpp_projection_error_bound) are
-                        re-decided with compensated arithmetic on the FP32
-                        rows, and the best max(rerank_k, k + 16) candidates
-                        are re-scored on the FP32 rows before the top-k.  The
-                        index holds X in both precisions (6 bytes per
-                        element).  Graded by recall and score error. */
+  FPP_BF16 = 1       /* Candidate scores are read from a BF16 copy of X
+                        (FP32 accumulation); the best max(rerank_k, k + 16)
+                        of them are re-scored exactly on the FP32 rows, and
+                        a top-k boundary closer than nine estimated standard
+                        deviations of the BF16 rounding error
+                        (score_error_factor) is re-decided exactly.  Hashing
+                        and probing are as for FPP_FP32.  The index holds X in
+                        both precisions (6 bytes per element).  Graded by
+                        recall and score error. */
 } fpp_precision;
 
 /* Index parameters.  Initialise with fpp_default_params(). */
@@ -126,6 +126,11 @@ typedef struct fpp_index_info {
   uint32_t max_bucket_kept;   /* largest kept bucket                          */
   uint64_t device_bytes;      /* device memory held by the index              */
   float build_ms;             /* wall time of fpp_build                        */
+  int32_t rerank_k;           /* FPP_BF16 shortlist length (0 for FPP_FP32)    */
+  double score_error_factor;  /* c: a candidate's first-pass score is within
+                                 c ||q|| ||x|| of x^T q (FPP_FP32: the FP32
+                                 bound gamma_d; FPP_BF16: the statistical
+                                 window of BF16 rows) before exact re-scoring */
 } fpp_index_info;
 
 typedef struct fpp_index fpp_index;
@@ -189,23 +194,28 @@ fpp_status fpp_index_get_info(const fpp_index* ix, fpp_index_info* info);
  *   table) and ids [kept_t], ids ordered by filter score desc, id asc inside
  *   a bucket.  Pass ids = NULL to get only offsets (kept_t = offsets[4D^2]).
  * fpp_debug_probes: probed bucket ids [m][L'][probes] in rank order for the
- *   tables of opts (L' = table_end - table_begin).  probes <= 128.  */
+ *   tables of opts (L' = table_end - table_begin).  probes <= 128.
+ * fpp_debug_candidates: the de-duplicated candidate set of every query (the
+ *   union of the kept ids of its probed buckets over all tables, Section
+ *   3.4), ascending per query, host memory: cand_off [m + 1] (cand_off[0] =
+ *   0) and cand [cand_off[m]].  Pass cand = NULL to get only cand_off, then
+ *   call again with a buffer of cand_off[m] entries.  */
 fpp_status fpp_debug_point_buckets(const fpp_index* ix, int32_t t, uint32_t* out);
 fpp_status fpp_debug_table(const fpp_index* ix, int32_t t, uint32_t* offsets,
                            uint32_t* ids);
 fpp_status fpp_debug_probes(const fpp_index* ix, const float* Q, int64_t m,
                             int32_t probes, int32_t table_begin, int32_t table_end,
                             uint32_t* out);
+fpp_status fpp_debug_candidates(const fpp_index* ix, const float* Q, int64_t m,
+                                int32_t probes, int64_t* cand_off, uint32_t* cand);
 
 /* fpp_debug_projections: the projections q^T r [m][2 L' D] of the queries
  *   onto the random vectors of tables [table_begin, table_end) (0, 0 = all),
  *   column (2 t' + j) D + i for table t' of the range, hash j, vector i, as
- *   the search computes them (tensor cores; FPP_FP32: exact three-piece
- *   BF16 split, FPP_BF16: one BF16 product).
+ *   the search computes them (tensor cores, exact three-piece BF16 split).
  * fpp_projection_error_bound: the factor c such that every such projection
  *   is within c ||q|| ||r_i|| of the exact inner product; the search's
- *   decisions rely on it (Section 2.2's projections, evaluated in pieces).
- *   For FPP_BF16 c is the statistical near-tie window, not a bound. */
+ *   decisions rely on it (Section 2.2's projections, evaluated in pieces). */
 fpp_status fpp_debug_projections(const fpp_index* ix, const float* Q, int64_t m,
                                  int32_t table_begin, int32_t table_end, float* out);
 fpp_status fpp_projection_error_bound(const fpp_index* ix, double* factor);
@@ -243,6 +253,71 @@ fpp_status fpp_bruteforce(const float* X, int64_t n, int32_t d, const float* Q,
 fpp_status fpp_bruteforce_static(const float* X, int64_t n, int32_t d, const float* Q,
                                  int64_t m, int32_t k, int64_t* ids, float* scores,
                                  void* stream);
+
+/* ------------------------------------------------------------ serving
+ *
+ * A server answers a stream of independent search requests on one index with
+ * continuous batching.  It runs `slots` worker threads, each with its own
+ * CUDA stream, device workspace and pinned staging buffers; a worker that
+ * becomes free takes the oldest queued requests (FIFO) while the batch holds
+ * at most max_batch queries and its estimated candidate-buffer memory (bucket
+ * entries of the probed buckets, 8 bytes each, estimated from the entries per
+ * probe seen so far) stays within candidate_budget_bytes, then runs the whole
+ * search on that batch with per-query k and probe budgets.  A request's
+ * results are those fpp_search_ex returns for its queries alone (nothing
+ * depends on the rest of the batch).  The index must outlive the server and
+ * must not be freed while it runs; fpp_search on the same index may run
+ * concurrently (it uses the index's own workspace). */
+typedef struct fpp_server fpp_server;
+
+typedef struct fpp_server_cfg {
+  int32_t max_batch;          /* queries per batch, 1..65536 (default 4096)    */
+  int32_t slots;              /* batches in flight, 1..16 (default 2)          */
+  int32_t k_max;              /* largest k of a request, 1..256 (default 100)  */
+  int32_t probes_max;         /* largest probe budget (default 16)             */
+  int32_t max_queue;          /* queued requests before submit returns
+                                 FPP_EBUSY (default 65536)                    */
+  int32_t reserved0;
+  uint64_t candidate_budget_bytes; /* per slot, >= 1 MiB (default 256 MiB)    */
+} fpp_server_cfg;
+
+typedef struct fpp_server_stats {
+  uint64_t submitted, completed, failed;  /* requests                        */
+  uint64_t queued;                        /* requests waiting now            */
+  uint64_t batches, queries;              /* batches run, queries in them    */
+  uint64_t entries, probes;               /* bucket entries scanned, buckets */
+} fpp_server_stats;
+
+void fpp_default_server_cfg(fpp_server_cfg* cfg);
+
+/* Starts the worker threads and allocates every slot's workspace for
+ * max_batch queries, probes_max probes and k_max results up front.
+ * Errors: FPP_EINVAL for a field out of range; FPP_ENOMEM. */
+fpp_status fpp_server_create(const fpp_index* ix, const fpp_server_cfg* cfg,
+                             fpp_server** out);
+
+/* Queues nq queries q [nq][d] (host or device memory; copied before the call
+ * returns) with k results and `probes` probes per table each.  *req_id
+ * identifies the request for fpp_server_poll.  Errors: FPP_EINVAL for nq
+ * outside 1..max_batch, k outside 1..k_max, probes outside 1..probes_max;
+ * FPP_EBUSY when max_queue requests are already waiting. */
+fpp_status fpp_server_submit(fpp_server* s, const float* q, int32_t nq, int32_t k,
+                             int32_t probes, uint64_t* req_id);
+
+/* Waits up to timeout_us microseconds (< 0: without limit, 0: no wait) for
+ * request req_id.  When it is complete, writes ids [nq][k] and scores
+ * [nq][k] (host or device memory; either may be NULL), the time from submit
+ * to completion in *latency_ms (may be NULL), forgets the request and
+ * returns its status.  FPP_ETIMEOUT: not complete yet (poll again);
+ * FPP_EINVAL: unknown id. */
+fpp_status fpp_server_poll(fpp_server* s, uint64_t req_id, int64_t* ids, float* scores,
+                           int32_t timeout_us, float* latency_ms);
+
+fpp_status fpp_server_get_stats(fpp_server* s, fpp_server_stats* out);
+
+/* Stops the workers after their current batches and frees the server;
+ * requests still queued are dropped.  NULL-safe. */
+void fpp_server_destroy(fpp_server* s);
 
 /* Number of kernels this process has launched through libfpp. */
 uint64_t fpp_launch_count(void);

@@ -61,12 +61,25 @@ class fpp_search_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class fpp_server_cfg(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("slots", ctypes.c_int32),
+                ("k_max", ctypes.c_int32), ("probes_max", ctypes.c_int32),
+                ("max_queue", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("candidate_budget_bytes", ctypes.c_uint64)]
+
+
+class fpp_server_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "completed", "failed", "queued",
+                                               "batches", "queries", "entries", "probes")]
+
+
 class fpp_index_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("L", ctypes.c_int32),
                 ("D", ctypes.c_int32), ("iprobes", ctypes.c_int32), ("kappa", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("alpha", ctypes.c_double),
                 ("kept_total", ctypes.c_uint64), ("max_bucket_kept", ctypes.c_uint32),
-                ("device_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_float)]
+                ("device_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_float),
+                ("rerank_k", ctypes.c_int32), ("score_error_factor", ctypes.c_double)]
 
 
 _lib = None
@@ -104,11 +117,20 @@ def load(path: str | None = None):
         "fpp_debug_point_buckets": (ctypes.c_int, [vp, i32, vp]),
         "fpp_debug_table": (ctypes.c_int, [vp, i32, vp, vp]),
         "fpp_debug_probes": (ctypes.c_int, [vp, f32p, i64, i32, i32, i32, vp]),
+        "fpp_debug_candidates": (ctypes.c_int, [vp, f32p, i64, i32, vp, vp]),
         "fpp_bruteforce": (ctypes.c_int, [f32p, i64, i32, f32p, i64, i32, vp, vp, vp]),
         "fpp_debug_projections": (ctypes.c_int, [vp, f32p, i64, i32, i32, vp]),
         "fpp_projection_error_bound": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
         "fpp_bruteforce_static": (ctypes.c_int, [f32p, i64, i32, f32p, i64, i32, vp, vp, vp]),
         "fpp_launch_count": (u64, []),
+        "fpp_default_server_cfg": (None, [ctypes.POINTER(fpp_server_cfg)]),
+        "fpp_server_create": (ctypes.c_int, [vp, ctypes.POINTER(fpp_server_cfg),
+                                             ctypes.POINTER(ctypes.c_void_p)]),
+        "fpp_server_submit": (ctypes.c_int, [vp, f32p, i32, i32, i32,
+                                             ctypes.POINTER(ctypes.c_uint64)]),
+        "fpp_server_poll": (ctypes.c_int, [vp, u64, vp, vp, i32, ctypes.POINTER(ctypes.c_float)]),
+        "fpp_server_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(fpp_server_stats)]),
+        "fpp_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -283,6 +305,18 @@ def fpp_debug_probes(ix, Q, probes: int, table_begin: int = 0, table_end: int = 
     return out
 
 
+def fpp_debug_candidates(ix, Q, probes: int):
+    """De-duplicated candidate ids of every query, ascending: a list of arrays."""
+    Q = _f32(Q)
+    m = Q.shape[0]
+    off = np.zeros(m + 1, dtype=np.int64)
+    lib = load()
+    _check(lib.fpp_debug_candidates(ix, _ptr(Q), m, probes, off.ctypes.data, None))
+    cand = np.empty(max(int(off[-1]), 1), dtype=np.uint32)
+    _check(lib.fpp_debug_candidates(ix, _ptr(Q), m, probes, off.ctypes.data, cand.ctypes.data))
+    return [cand[off[i]:off[i + 1]] for i in range(m)]
+
+
 def fpp_debug_projections(ix, Q, table_begin: int = 0, table_end: int = 0) -> np.ndarray:
     info = fpp_index_get_info(ix)
     te = table_end or info["L"]
@@ -342,6 +376,66 @@ class Index:
     def close(self):
         if self.handle is not None:
             fpp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching search server over an Index (see fpp_server_* in
+    include/fpp.h).  submit() returns a request id; poll() returns
+    (ids [nq][k], scores [nq][k], latency_ms), or None when timeout_us ran
+    out first."""
+
+    def __init__(self, index, **cfg):
+        lib = load()
+        c = fpp_server_cfg()
+        lib.fpp_default_server_cfg(ctypes.byref(c))
+        for key, v in cfg.items():
+            setattr(c, key, v)
+        self.cfg = {f: getattr(c, f) for f, _ in c._fields_}
+        self.index = index          # the index must outlive the server
+        self.d = index.info()["d"]
+        h = ctypes.c_void_p()
+        _check(lib.fpp_server_create(index.handle, ctypes.byref(c), ctypes.byref(h)))
+        self.handle = h
+        self._shape = {}
+
+    def submit(self, q, k: int, probes: int) -> int:
+        if not _is_torch(q):
+            q = np.atleast_2d(np.asarray(q, dtype=np.float32))
+        q = _f32(q)
+        nq = int(q.shape[0])
+        rid = ctypes.c_uint64()
+        _check(load().fpp_server_submit(self.handle, _ptr(q), nq, k, probes, ctypes.byref(rid)))
+        self._shape[rid.value] = (nq, k)
+        return rid.value
+
+    def poll(self, rid: int, timeout_us: int = -1):
+        nq, k = self._shape[rid]
+        ids = np.empty((nq, k), dtype=np.int64)
+        sc = np.empty((nq, k), dtype=np.float32)
+        lat = ctypes.c_float()
+        st = load().fpp_server_poll(self.handle, rid, ids.ctypes.data, sc.ctypes.data,
+                                    timeout_us, ctypes.byref(lat))
+        if st == 4:   # FPP_ETIMEOUT: not complete yet
+            return None
+        del self._shape[rid]
+        _check(st)
+        return ids, sc, lat.value
+
+    def stats(self) -> dict:
+        st = fpp_server_stats()
+        _check(load().fpp_server_get_stats(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def close(self):
+        if self.handle is not None:
+            load().fpp_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -3,8 +3,13 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <condition_variable>
+#include <deque>
+#include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -217,6 +222,7 @@ fpp_status build_tables(fpp_index* ix, int t0, int nt, BuildScratch& B, cudaStre
     HashArgs h{};
     h.P = EL ? nullptr : B.proj.as<float>(); h.ldp = ldp; h.rows = rc; h.row0 = r0;
     h.lists = EL ? B.proj.as<uint64_t>() : nullptr; h.EL = EL;
+    h.trunc = EL ? tc_list_trunc(D) : 0.f;
     h.t0 = t0; h.nt = nt; h.D = D;
     h.X = ix->X; h.ldx = ix->dpad; h.R = ix->R; h.ldr = ix->dpad; h.d = ix->d;
     h.rmax = ix->rmax; h.xmax = ix->xmax; h.gamma = ix->gamma; h.n = n;
@@ -293,14 +299,16 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
   ix->L = p->L; ix->D = p->D; ix->iprobes = p->iprobes; ix->kappa = p->kappa;
   ix->alpha = p->alpha; ix->precision = p->precision;
   ix->Kp = tc_kpad(d);
+  // Projections use the exact three-piece split in both precisions: the
+  // projection kernel is bound by its epilogue (the per-hash top lists), not
+  // by the tensor cores, so one BF16 product is no faster there, while its
+  // rounding error would send far more probe decisions to the exact pass.
+  ix->pieces = 3;
+  ix->gamma = tc_error_bound_factor(ix->Kp, 3);
   if (p->precision == FPP_BF16) {
-    ix->pieces = 1;
     ix->rerank_k = p->rerank_k;
-    ix->gamma = bf16_window_factor(d);
     ix->score_gamma = bf16_window_factor(d);
   } else {
-    ix->pieces = 3;
-    ix->gamma = tc_error_bound_factor(ix->Kp, 3);
     ix->score_gamma = gamma_fp32(ix->dpad);
   }
   if (cudaGetDevice(&ix->device) != cudaSuccess ||
@@ -493,10 +501,11 @@ int topk_kprime(const fpp_index* ix, int kmax) {
 
 // Runs projection + probe ranking (and, unless probes_only, gather/score) for
 // queries [q0, q0 + mc).
-fpp_status search_chunk(fpp_index* ix, const float* Q, int64_t q0, int64_t mc, const SearchPlan& pl,
-                        int64_t* ids_dev, float* scores_dev, cudaStream_t st, bool probes_only,
-                        cudaEvent_t* ev) {
-  Workspace& ws = ix->ws;
+enum Stage { kFull = 0, kProbesOnly = 1, kCandidatesOnly = 2 };
+
+fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0, int64_t mc,
+                        const SearchPlan& pl, int64_t* ids_dev, float* scores_dev, cudaStream_t st,
+                        int stage, cudaEvent_t* ev) {
   const int nt = pl.te - pl.tb;
   const int64_t ldp = round_up(2ll * nt * ix->D, 4);
   // queries, padded
@@ -528,6 +537,7 @@ fpp_status search_chunk(fpp_index* ix, const float* Q, int64_t q0, int64_t mc, c
   ProbeArgs pa{};
   pa.P = EL ? nullptr : ws.proj.as<float>(); pa.ldp = ldp; pa.mq = mc;
   pa.lists = EL ? ws.proj.as<uint64_t>() : nullptr; pa.EL = EL;
+  pa.trunc = EL ? tc_list_trunc(ix->D) : 0.f;
   pa.Q = ws.qpad.as<float>(); pa.ldq = ix->dpad; pa.qnorm = ws.qnorm.as<float>();
   pa.R = ix->R; pa.ldr = ix->dpad; pa.d = ix->d; pa.D = ix->D; pa.tb = pl.tb; pa.nt = nt;
   pa.rmax = ix->rmax; pa.gamma = ix->gamma; pa.gammaf = (float)(ix->gamma * 1.0001);
@@ -540,7 +550,7 @@ fpp_status search_chunk(fpp_index* ix, const float* Q, int64_t q0, int64_t mc, c
   pa.rechecks = ws.stats.as<unsigned long long>() + 6;
   FPP_TRY(launch_probe(pa, st, ev ? ev[4] : nullptr));
   if (ev) FPP_CUDA(cudaEventRecord(ev[2], st));
-  if (probes_only) return FPP_OK;
+  if (stage == kProbesOnly) return FPP_OK;
   // ---- candidates: count bucket entries, give each query a region, dedup,
   // score, top-k
   unsigned long long* stv = ws.stats.as<unsigned long long>();
@@ -579,6 +589,7 @@ fpp_status search_chunk(fpp_index* ix, const float* Q, int64_t q0, int64_t mc, c
   da.items = ws.items.as<ScoreItem>();
   FPP_TRY(launch_dedup(da, ws.slots, st));
   if (ev) FPP_CUDA(cudaEventRecord(ev[5], st));
+  if (stage == kCandidatesOnly) return FPP_OK;
   ScoreArgs sa{};
   sa.items = ws.items.as<ScoreItem>(); sa.eoff = ws.eoff.as<uint64_t>(); sa.mq = mc;
   sa.cand = ws.cand.as<uint32_t>();
@@ -612,9 +623,8 @@ int64_t chunk_rows(const fpp_index* ix, int nt, int pmax, bool allow_fused = tru
   return mc;
 }
 
-fpp_status prepare_workspace(fpp_index* ix, const SearchPlan& pl, int64_t mc, bool host_out,
-                             cudaStream_t st, bool allow_fused = true) {
-  Workspace& ws = ix->ws;
+fpp_status prepare_workspace(fpp_index* ix, Workspace& ws, const SearchPlan& pl, int64_t mc,
+                             bool host_out, cudaStream_t st, bool allow_fused = true) {
   const int nt = pl.te - pl.tb;
   const int64_t ldp = round_up(2ll * nt * ix->D, 4);
   const bool qz = ws.qpad.bytes < (size_t)mc * ix->dpad * 4;
@@ -661,7 +671,7 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
   const bool dev_out = is_device_ptr(ids) && is_device_ptr(scores);
   const int nt = pl.te - pl.tb;
   const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt, pl.pmax), m);
-  FPP_TRY(prepare_workspace(ix, pl, mc, !dev_out, st));
+  FPP_TRY(prepare_workspace(ix, ix->ws, pl, mc, !dev_out, st));
   FPP_CUDA(cudaMemsetAsync(ix->ws.stats.p, 0, 16 * 8, st));
   cudaEvent_t ev[7] = {};
   bool timing = stats != nullptr;
@@ -673,7 +683,7 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
     const int64_t c = std::min<int64_t>(mc, m - q0);
     int64_t* oid = dev_out ? ids + q0 * pl.kmax : ix->ws.out_ids.as<int64_t>();
     float* osc = dev_out ? scores + q0 * pl.kmax : ix->ws.out_scores.as<float>();
-    FPP_TRY(search_chunk(ix, Q, q0, c, pl, oid, osc, st, false, timing ? ev : nullptr));
+    FPP_TRY(search_chunk(ix, ix->ws, Q, q0, c, pl, oid, osc, st, kFull, timing ? ev : nullptr));
     if (!dev_out) {
       FPP_CUDA(cudaMemcpyAsync(ids + q0 * pl.kmax, oid, c * pl.kmax * 8, cudaMemcpyDeviceToHost, st));
       FPP_CUDA(cudaMemcpyAsync(scores + q0 * pl.kmax, osc, c * pl.kmax * 4, cudaMemcpyDeviceToHost, st));
@@ -728,6 +738,257 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
     stats->ms_topk = ms[6];
     stats->ms_total = ms[0] + ms[1] + ms[2] + ms[3];
   }
+  return FPP_OK;
+}
+
+
+// ------------------------------------------------------------------ serving
+//
+// Continuous batching: every slot is a worker thread with its own stream,
+// workspace and pinned staging buffers.  A free worker takes the oldest
+// queued requests (FIFO) while the batch stays within max_batch queries and
+// its estimated candidate-buffer memory within the slot's budget, runs the
+// search pipeline on them with per-query k and probe budgets, and completes
+// the requests.  Each query's result depends only on the query and its own
+// k and probes, never on the rest of its batch.
+
+struct ServerRequest {
+  uint64_t id = 0;
+  int32_t nq = 0, k = 0, probes = 0;
+  std::vector<float> q;          // [nq][d]
+  std::vector<int64_t> ids;      // [nq][k]
+  std::vector<float> scores;     // [nq][k]
+  int state = 0;                 // 0 queued, 1 running, 2 done
+  fpp_status status = FPP_OK;
+  std::string error;
+  std::chrono::steady_clock::time_point t_submit, t_done;
+};
+
+struct ServerSlot {
+  Workspace ws;
+  cudaStream_t st = nullptr;
+  float* hq = nullptr;           // pinned [max_batch][d]
+  int32_t* hk = nullptr;         // pinned [max_batch]
+  int32_t* hp = nullptr;
+  int64_t* hids = nullptr;       // pinned [max_batch][k_max]
+  float* hsc = nullptr;
+  unsigned long long* hstats = nullptr;   // pinned [16]
+  std::thread worker;
+};
+
+}  // namespace fpp_api
+
+struct fpp_server {
+  fpp_index* ix = nullptr;
+  fpp_server_cfg cfg{};
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<fpp_api::ServerRequest*> queue;
+  std::unordered_map<uint64_t, std::unique_ptr<fpp_api::ServerRequest>> reqs;
+  uint64_t next_id = 1;
+  bool stop = false;
+  std::vector<std::unique_ptr<fpp_api::ServerSlot>> slots;
+  double entries_per_probe = 0.0;   // running estimate for admission
+  fpp_server_stats stats{};
+};
+
+namespace fpp_api {
+
+// Candidate-buffer entries a request is expected to need.
+double request_entries(const fpp_server* s, const ServerRequest& r) {
+  return (double)r.nq * s->ix->L * r.probes * s->entries_per_probe;
+}
+
+void server_run_batch(fpp_server* s, ServerSlot& sl, std::vector<ServerRequest*>& batch) {
+  fpp_index* ix = s->ix;
+  const int d = ix->d;
+  int64_t m = 0;
+  int pmax = 1;
+  for (ServerRequest* r : batch) {
+    std::memcpy(sl.hq + m * d, r->q.data(), (size_t)r->nq * d * 4);
+    for (int i = 0; i < r->nq; ++i) {
+      sl.hk[m + i] = r->k;
+      sl.hp[m + i] = r->probes;
+    }
+    pmax = std::max(pmax, r->probes);
+    m += r->nq;
+  }
+  SearchPlan pl{};
+  pl.m = m;
+  pl.kmax = s->cfg.k_max;
+  pl.pmax = pmax;
+  pl.tb = 0;
+  pl.te = ix->L;
+  pl.kpq = sl.hk;
+  pl.ppq = sl.hp;
+  pl.kpq_dev = pl.ppq_dev = false;
+  pl.k = s->cfg.k_max;
+  pl.probes = pmax;
+  auto fail = [&](fpp_status st, const std::string& msg) {
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (ServerRequest* r : batch) {
+      r->status = st;
+      r->error = msg;
+      r->state = 2;
+      r->t_done = std::chrono::steady_clock::now();
+    }
+    s->stats.failed += batch.size();
+    s->cv_done.notify_all();
+  };
+  fpp_status st = FPP_OK;
+  auto run = [&]() -> fpp_status {
+    FPP_TRY(prepare_workspace(ix, sl.ws, pl, m, true, sl.st));
+    FPP_CUDA(cudaMemsetAsync(sl.ws.stats.p, 0, 16 * 8, sl.st));
+    FPP_TRY(search_chunk(ix, sl.ws, sl.hq, 0, m, pl, sl.ws.out_ids.as<int64_t>(),
+                         sl.ws.out_scores.as<float>(), sl.st, kFull, nullptr));
+    FPP_CUDA(cudaMemcpyAsync(sl.hids, sl.ws.out_ids.p, (size_t)m * pl.kmax * 8,
+                             cudaMemcpyDeviceToHost, sl.st));
+    FPP_CUDA(cudaMemcpyAsync(sl.hsc, sl.ws.out_scores.p, (size_t)m * pl.kmax * 4,
+                             cudaMemcpyDeviceToHost, sl.st));
+    FPP_CUDA(cudaMemcpyAsync(sl.hstats, sl.ws.stats.p, 16 * 8, cudaMemcpyDeviceToHost, sl.st));
+    FPP_CUDA(cudaStreamSynchronize(sl.st));
+    if (sl.hstats[5]) { set_error("search: top-k re-check capacity exceeded"); return FPP_EINTERNAL; }
+    if (sl.hstats[9]) { set_error("search: a bounded wait in the projection kernel ran out"); return FPP_ETIMEOUT; }
+    return FPP_OK;
+  };
+  st = run();
+  if (st != FPP_OK) {
+    fail(st, g_err);
+    return;
+  }
+  const auto now = std::chrono::steady_clock::now();
+  int64_t row = 0;
+  for (ServerRequest* r : batch) {
+    for (int i = 0; i < r->nq; ++i) {
+      std::memcpy(r->ids.data() + (size_t)i * r->k, sl.hids + (row + i) * pl.kmax, (size_t)r->k * 8);
+      std::memcpy(r->scores.data() + (size_t)i * r->k, sl.hsc + (row + i) * pl.kmax, (size_t)r->k * 4);
+    }
+    row += r->nq;
+  }
+  std::lock_guard<std::mutex> lock(s->mu);
+  for (ServerRequest* r : batch) {
+    r->state = 2;
+    r->t_done = now;
+  }
+  s->stats.completed += batch.size();
+  s->stats.batches += 1;
+  s->stats.queries += (uint64_t)m;
+  s->stats.entries += sl.hstats[0];
+  s->stats.probes += sl.hstats[3];
+  if (sl.hstats[3]) {
+    const double epp = (double)sl.hstats[0] / (double)sl.hstats[3];
+    s->entries_per_probe = 0.8 * s->entries_per_probe + 0.2 * epp * 1.25;
+  }
+  s->cv_done.notify_all();
+}
+
+void server_worker(fpp_server* s, ServerSlot* sl) {
+  cudaSetDevice(s->ix->device);
+  const double budget = (double)s->cfg.candidate_budget_bytes / 8.0;   // cand + score per entry
+  std::vector<ServerRequest*> batch;
+  while (true) {
+    batch.clear();
+    {
+      std::unique_lock<std::mutex> lock(s->mu);
+      s->cv_work.wait(lock, [&] { return s->stop || !s->queue.empty(); });
+      if (s->stop) return;
+      int64_t nq = 0;
+      double ent = 0.0;
+      while (!s->queue.empty()) {
+        ServerRequest* r = s->queue.front();
+        const double e = request_entries(s, *r);
+        if (!batch.empty() && (nq + r->nq > s->cfg.max_batch || ent + e > budget)) break;
+        batch.push_back(r);
+        s->queue.pop_front();
+        r->state = 1;
+        nq += r->nq;
+        ent += e;
+      }
+      s->stats.queued = s->queue.size();
+    }
+    server_run_batch(s, *sl, batch);
+  }
+}
+
+void server_release(fpp_server* s) {
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  for (auto& sl : s->slots)
+    if (sl->worker.joinable()) sl->worker.join();
+  for (auto& sl : s->slots) {
+    sl->ws.release();
+    if (sl->st) cudaStreamDestroy(sl->st);
+    cudaFreeHost(sl->hq);
+    cudaFreeHost(sl->hk);
+    cudaFreeHost(sl->hp);
+    cudaFreeHost(sl->hids);
+    cudaFreeHost(sl->hsc);
+    cudaFreeHost(sl->hstats);
+  }
+  s->slots.clear();
+}
+
+fpp_status server_create_impl(const fpp_index* cix, const fpp_server_cfg* cfg, fpp_server** out) {
+  if (!cix || !cfg || !out) { set_error("NULL argument"); return FPP_EINVAL; }
+  const int64_t NB = nbuckets(cix->D);
+  const int pcap = (int)std::min<int64_t>(NB, 128);
+  if (cfg->max_batch < 1 || cfg->max_batch > 65536) { set_error("max_batch must be in [1, 65536]"); return FPP_EINVAL; }
+  if (cfg->slots < 1 || cfg->slots > 16) { set_error("slots must be in [1, 16]"); return FPP_EINVAL; }
+  if (cfg->k_max < 1 || cfg->k_max > 256) { set_error("k_max must be in [1, 256]"); return FPP_EINVAL; }
+  if (cfg->probes_max < 1 || cfg->probes_max > pcap) {
+    set_error("probes_max must be in [1, min(4D^2, 128)]");
+    return FPP_EINVAL;
+  }
+  if (cfg->max_queue < 1) { set_error("max_queue must be >= 1"); return FPP_EINVAL; }
+  if (cfg->candidate_budget_bytes < ((uint64_t)1 << 20)) {
+    set_error("candidate_budget_bytes must be >= 1 MiB");
+    return FPP_EINVAL;
+  }
+  auto s = std::make_unique<fpp_server>();
+  s->ix = const_cast<fpp_index*>(cix);
+  s->cfg = *cfg;
+  // initial admission estimate: the mean kept bucket size, doubled
+  s->entries_per_probe = 2.0 * (double)cix->kept_total / ((double)cix->L * (double)NB) + 1.0;
+  if (cudaSetDevice(cix->device) != cudaSuccess) { set_error("cudaSetDevice failed"); return FPP_ECUDA; }
+  SearchPlan pl{};
+  pl.m = cfg->max_batch;
+  pl.kmax = cfg->k_max;
+  pl.pmax = cfg->probes_max;
+  pl.tb = 0;
+  pl.te = cix->L;
+  const int d = cix->d;
+  for (int i = 0; i < cfg->slots; ++i) {
+    auto sl = std::make_unique<ServerSlot>();
+    fpp_status st = FPP_OK;
+    if (cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost(&sl->hq, (size_t)cfg->max_batch * d * 4) != cudaSuccess ||
+        cudaMallocHost(&sl->hk, (size_t)cfg->max_batch * 4) != cudaSuccess ||
+        cudaMallocHost(&sl->hp, (size_t)cfg->max_batch * 4) != cudaSuccess ||
+        cudaMallocHost(&sl->hids, (size_t)cfg->max_batch * cfg->k_max * 8) != cudaSuccess ||
+        cudaMallocHost(&sl->hsc, (size_t)cfg->max_batch * cfg->k_max * 4) != cudaSuccess ||
+        cudaMallocHost(&sl->hstats, 16 * 8) != cudaSuccess) {
+      set_error("server: allocating a slot's stream or pinned buffers failed");
+      st = FPP_ENOMEM;
+    }
+    if (st == FPP_OK) st = prepare_workspace(s->ix, sl->ws, pl, cfg->max_batch, true, sl->st);
+    if (st == FPP_OK) {
+      const uint64_t cap = cfg->candidate_budget_bytes / 8;
+      if ((st = sl->ws.cand.ensure((size_t)cap * 4)) == FPP_OK &&
+          (st = sl->ws.cscores.ensure((size_t)cap * 4)) == FPP_OK)
+        sl->ws.cand_cap = cap;
+    }
+    if (st == FPP_OK && cudaStreamSynchronize(sl->st) != cudaSuccess) st = FPP_ECUDA;
+    s->slots.push_back(std::move(sl));
+    if (st != FPP_OK) {
+      server_release(s.get());
+      return st;
+    }
+  }
+  for (auto& sl : s->slots) sl->worker = std::thread(server_worker, s.get(), sl.get());
+  *out = s.release();
   return FPP_OK;
 }
 
@@ -834,6 +1095,8 @@ fpp_status fpp_index_get_info(const fpp_index* ix, fpp_index_info* info) {
   info->alpha = ix->alpha; info->kept_total = ix->kept_total;
   info->max_bucket_kept = ix->max_bucket_kept; info->device_bytes = ix->device_bytes;
   info->build_ms = ix->build_ms;
+  info->rerank_k = ix->rerank_k;
+  info->score_error_factor = ix->score_gamma;
   return FPP_OK;
 }
 
@@ -906,12 +1169,59 @@ fpp_status fpp_debug_probes(const fpp_index* cix, const float* Q, int64_t m, int
   if (m == 0) return FPP_OK;
   const int nt = pl.te - pl.tb;
   const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt, pl.pmax), m);
-  FPP_TRY(prepare_workspace(ix, pl, mc, false, 0));
+  FPP_TRY(prepare_workspace(ix, ix->ws, pl, mc, false, 0));
   for (int64_t q0 = 0; q0 < m; q0 += mc) {
     const int64_t c = std::min<int64_t>(mc, m - q0);
-    FPP_TRY(search_chunk(ix, Q, q0, c, pl, nullptr, nullptr, 0, true, nullptr));
+    FPP_TRY(search_chunk(ix, ix->ws, Q, q0, c, pl, nullptr, nullptr, 0, kProbesOnly, nullptr));
     FPP_CUDA(cudaMemcpy(out + q0 * nt * probes, ix->ws.probes.p, (size_t)c * nt * probes * 4,
                         cudaMemcpyDefault));
+  }
+  return FPP_OK;
+}
+
+fpp_status fpp_debug_candidates(const fpp_index* cix, const float* Q, int64_t m, int32_t probes,
+                                int64_t* cand_off, uint32_t* cand) {
+  g_err.clear();
+  fpp_search_opts o;
+  fpp_default_search_opts(&o);
+  o.probes = probes;
+  o.k = 1;
+  SearchPlan pl{};
+  int64_t dummy_i = 0;
+  float dummy_s = 0;
+  FPP_TRY(validate_search(cix, Q, m, &o, &dummy_i, &dummy_s, pl));
+  if (!cand_off) { set_error("cand_off is NULL"); return FPP_EINVAL; }
+  fpp_index* ix = const_cast<fpp_index*>(cix);
+  std::lock_guard<std::mutex> lock(ix->mu);
+  cand_off[0] = 0;
+  if (m == 0) return FPP_OK;
+  const int nt = pl.te - pl.tb;
+  const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt, pl.pmax), m);
+  FPP_TRY(prepare_workspace(ix, ix->ws, pl, mc, false, 0));
+  std::vector<uint64_t> eoff;
+  std::vector<uint32_t> ucount, buf;
+  for (int64_t q0 = 0; q0 < m; q0 += mc) {
+    const int64_t c = std::min<int64_t>(mc, m - q0);
+    FPP_TRY(search_chunk(ix, ix->ws, Q, q0, c, pl, nullptr, nullptr, 0, kCandidatesOnly, nullptr));
+    eoff.resize(c + 1);
+    ucount.resize(c);
+    FPP_CUDA(cudaMemcpy(eoff.data(), ix->ws.eoff.p, (c + 1) * 8, cudaMemcpyDeviceToHost));
+    FPP_CUDA(cudaMemcpy(ucount.data(), ix->ws.ecount.as<uint32_t>() + c, c * 4,
+                        cudaMemcpyDeviceToHost));
+    if (cand) {
+      buf.resize(eoff[c]);
+      if (eoff[c])
+        FPP_CUDA(cudaMemcpy(buf.data(), ix->ws.cand.p, eoff[c] * 4, cudaMemcpyDeviceToHost));
+    }
+    for (int64_t i = 0; i < c; ++i) {
+      const int64_t g = q0 + i;
+      cand_off[g + 1] = cand_off[g] + ucount[i];
+      if (cand) {
+        uint32_t* dst = cand + cand_off[g];
+        std::copy(buf.begin() + eoff[i], buf.begin() + eoff[i] + ucount[i], dst);
+        std::sort(dst, dst + ucount[i]);
+      }
+    }
   }
   return FPP_OK;
 }
@@ -935,7 +1245,7 @@ fpp_status fpp_debug_projections(const fpp_index* cix, const float* Q, int64_t m
   const int64_t N = 2ll * nt * ix->D;
   const int64_t ldp = round_up(N, 4);
   const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt, pl.pmax, false), m);
-  FPP_TRY(prepare_workspace(ix, pl, mc, false, 0, false));
+  FPP_TRY(prepare_workspace(ix, ix->ws, pl, mc, false, 0, false));
   FPP_CUDA(cudaMemset(ix->ws.stats.p, 0, 16 * 8));
   for (int64_t q0 = 0; q0 < m; q0 += mc) {
     const int64_t c = std::min<int64_t>(mc, m - q0);
@@ -1021,4 +1331,124 @@ fpp_status fpp_bruteforce(const float* X, int64_t n, int32_t d, const float* Q, 
   return done(FPP_OK);
 }
 
+
+void fpp_default_server_cfg(fpp_server_cfg* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->max_batch = 4096;
+  c->slots = 2;
+  c->k_max = 100;
+  c->probes_max = 16;
+  c->max_queue = 1 << 16;
+  c->candidate_budget_bytes = 256ull << 20;
+}
+
+fpp_status fpp_server_create(const fpp_index* ix, const fpp_server_cfg* cfg, fpp_server** out) {
+  g_err.clear();
+  try {
+    return server_create_impl(ix, cfg, out);
+  } catch (const std::exception& e) {
+    set_error(std::string("fpp_server_create: ") + e.what());
+    return FPP_EINTERNAL;
+  }
+}
+
+fpp_status fpp_server_submit(fpp_server* s, const float* q, int32_t nq, int32_t k, int32_t probes,
+                             uint64_t* req_id) {
+  g_err.clear();
+  if (!s || !q || !req_id) { set_error("NULL argument"); return FPP_EINVAL; }
+  if (nq < 1 || nq > s->cfg.max_batch) { set_error("nq must be in [1, max_batch]"); return FPP_EINVAL; }
+  if (k < 1 || k > s->cfg.k_max) { set_error("k must be in [1, k_max]"); return FPP_EINVAL; }
+  if (probes < 1 || probes > s->cfg.probes_max) {
+    set_error("probes must be in [1, probes_max]");
+    return FPP_EINVAL;
+  }
+  try {
+    auto r = std::make_unique<ServerRequest>();
+    r->nq = nq;
+    r->k = k;
+    r->probes = probes;
+    const size_t nel = (size_t)nq * s->ix->d;
+    r->q.resize(nel);
+    if (is_device_ptr(q)) {
+      if (cudaMemcpy(r->q.data(), q, nel * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        set_error("copying the queries failed");
+        return FPP_ECUDA;
+      }
+    } else {
+      std::memcpy(r->q.data(), q, nel * 4);
+    }
+    r->ids.resize((size_t)nq * k);
+    r->scores.resize((size_t)nq * k);
+    r->t_submit = std::chrono::steady_clock::now();
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->stop) { set_error("server is shutting down"); return FPP_EBUSY; }
+    if ((int64_t)s->queue.size() >= s->cfg.max_queue) {
+      set_error("queue full");
+      return FPP_EBUSY;
+    }
+    r->id = s->next_id++;
+    *req_id = r->id;
+    s->queue.push_back(r.get());
+    s->reqs.emplace(r->id, std::move(r));
+    s->stats.submitted += 1;
+    s->stats.queued = s->queue.size();
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return FPP_ENOMEM;
+  }
+  s->cv_work.notify_one();
+  return FPP_OK;
+}
+
+fpp_status fpp_server_poll(fpp_server* s, uint64_t req_id, int64_t* ids, float* scores,
+                           int32_t timeout_us, float* latency_ms) {
+  g_err.clear();
+  if (!s) { set_error("server is NULL"); return FPP_EINVAL; }
+  std::unique_ptr<ServerRequest> r;
+  {
+    std::unique_lock<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(req_id);
+    if (it == s->reqs.end()) { set_error("unknown request id"); return FPP_EINVAL; }
+    ServerRequest* rp = it->second.get();
+    auto done = [&] { return rp->state == 2; };
+    if (timeout_us < 0) s->cv_done.wait(lock, done);
+    else if (!s->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), done)) {
+      set_error("request not complete yet");
+      return FPP_ETIMEOUT;
+    }
+    r = std::move(it->second);
+    s->reqs.erase(it);
+  }
+  if (latency_ms)
+    *latency_ms = std::chrono::duration<float, std::milli>(r->t_done - r->t_submit).count();
+  if (r->status != FPP_OK) {
+    set_error(r->error);
+    return r->status;
+  }
+  const size_t ni = r->ids.size();
+  if (ids && cudaMemcpy(ids, r->ids.data(), ni * 8, cudaMemcpyDefault) != cudaSuccess) {
+    set_error("copying ids failed");
+    return FPP_ECUDA;
+  }
+  if (scores && cudaMemcpy(scores, r->scores.data(), ni * 4, cudaMemcpyDefault) != cudaSuccess) {
+    set_error("copying scores failed");
+    return FPP_ECUDA;
+  }
+  return FPP_OK;
+}
+
+fpp_status fpp_server_get_stats(fpp_server* s, fpp_server_stats* out) {
+  g_err.clear();
+  if (!s || !out) { set_error("NULL argument"); return FPP_EINVAL; }
+  std::lock_guard<std::mutex> lock(s->mu);
+  *out = s->stats;
+  return FPP_OK;
+}
+
+void fpp_server_destroy(fpp_server* s) {
+  if (!s) return;
+  server_release(s);
+  delete s;
+}
 }  // extern "C"

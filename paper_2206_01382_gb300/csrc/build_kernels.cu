@@ -83,7 +83,9 @@ build_hash_kernel(HashArgs a) {
       i1 = (int)((0xFFFFFFFFu - (uint32_t)k0) % (uint32_t)D);
       s1 = D > 1 ? __uint_as_float((uint32_t)(k1 >> 32) - 1u) : -1.f;
     }
-    const float eps = a.eps_xf * a.rmax[2 * t + j] * 1.0001f;
+    // list values are truncated: every |p| of the hash lies below its list
+    // value times (1 + trunc), at most trunc * b1 above it
+    const float eps = a.eps_xf * a.rmax[2 * t + j] * 1.0001f + (a.P ? 0.f : a.trunc * b1 * 1.0001f);
     const bool certain = (b1 - s1 > 2.f * eps) && (b1 > eps);
     const float* Rj = a.R + (int64_t)(2 * t + j) * D * a.ldr;
     if (certain) {

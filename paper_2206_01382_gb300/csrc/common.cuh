@@ -193,6 +193,36 @@ __device__ __forceinline__ void warp_dot2_gather(const float* __restrict__ q,
   }
 }
 
+// Single-thread compensated dot product of two 16-byte aligned rows of nf4
+// float4 chunks (four chunk loads in flight at a time).
+__device__ __forceinline__ double thread_dot2_f4(const float* __restrict__ a,
+                                                 const float* __restrict__ b, int nf4) {
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  const float4* b4 = reinterpret_cast<const float4*>(b);
+  float p = 0.f, s = 0.f;
+  int c = 0;
+  for (; c + 4 <= nf4; c += 4) {
+    float4 x[4], y[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { x[u] = __ldg(a4 + c + u); y[u] = __ldg(b4 + c + u); }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      dot2_step(x[u].x, y[u].x, p, s);
+      dot2_step(x[u].y, y[u].y, p, s);
+      dot2_step(x[u].z, y[u].z, p, s);
+      dot2_step(x[u].w, y[u].w, p, s);
+    }
+  }
+  for (; c < nf4; ++c) {
+    const float4 x = __ldg(a4 + c), y = __ldg(b4 + c);
+    dot2_step(x.x, y.x, p, s);
+    dot2_step(x.y, y.y, p, s);
+    dot2_step(x.z, y.z, p, s);
+    dot2_step(x.w, y.w, p, s);
+  }
+  return ff_value(FF{p, s});
+}
+
 // Single-thread compensated dot product.
 __device__ __forceinline__ double thread_dot2(const float* __restrict__ a,
                                               const float* __restrict__ b, int n) {

@@ -54,9 +54,8 @@ struct __align__(8) TcShared {
   uint32_t tmem_base;
   int abort;
   // list mode with D = 256: the second column half of every row hands its
-  // partial top list (up to 8 entries and the cut) to the first half
-  float xa[4][32][9];
-  uint32_t xh[4][32][8];
+  // partial top list (up to 8 packed keys and the cut) to the first half
+  uint32_t xk[4][32][9];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -146,6 +145,35 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Issues a 32-column TMEM load without waiting for it; the registers must not
+// be read before tmem_wait(r) on the same array.
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+// Waits for the outstanding TMEM loads; the "+r" operands keep the compiler
+// from moving reads of r above the wait.
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.wait::ld.sync.aligned;"
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+        "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+        "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]),
+        "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]),
+        "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+      :
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
   asm volatile(
@@ -184,9 +212,13 @@ __device__ __forceinline__ void chunk_pieces(int c, int nkb, int pieces, int& pa
   }
 }
 
-// A hash list entry is stored as the key (bits(|p|) + 1) << 32 | (0xFFFFFFFF - h)
-// with h = i for p >= 0 and i + D otherwise: a larger key is a larger |p|,
-// 0 marks an empty slot.
+// A hash list entry is stored as the key (bits(|p|') + 1) << 32 | (0xFFFFFFFF - h)
+// with h = i for p >= 0 and i + D otherwise, and 0 marks an empty slot.
+// |p|' is |p| with its lowest log2(2D) bits cleared: the epilogue ranks
+// packed 32-bit keys 2^31 | (bits(|p|) with those bits cleared) | h with
+// integer max/min, so |p|' >= |p| (1 - tc_list_trunc(D)) and entries whose
+// |p| agree in all but those bits are ranked in an arbitrary (but fixed)
+// order.  Consumers widen their error bounds accordingly.
 
 // Persistent projection kernel.  Tiles of 128 rows x 256 columns are handed
 // out round-robin; the TMEM accumulator is double-buffered so the epilogue of
@@ -314,87 +346,74 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
           }
         }
       } else {
-        // running top-EL of the current hash: |p| descending (earlier column
-        // first on ties) and its wedge h; a value enters only if it beats
-        // the EL-th; `cut` is the largest |p| that did not stay in the list
+        // running top-(EL + 1) packed keys of the current hash (descending;
+        // 0 = none): entries 0..EL-1 form the list, entry EL is the cut
         const uint32_t dmask = (uint32_t)D - 1u;   // D is a power of two dividing 256
-        float ta[EL > 0 ? EL : 1];
-        uint32_t th[EL > 0 ? EL : 1];
-        float cut = -1.f;
+        const int ldD = __ffs(D) - 1;
+        const uint32_t cmask = 2u * (uint32_t)D - 1u;
+        const uint32_t keep = 0x7FFFFFFFu & ~cmask;
+        uint32_t tk[EL > 0 ? EL + 1 : 1];
 #pragma unroll
-        for (int e = 0; e < EL; ++e) { ta[e] = -1.f; th[e] = 0u; }
+        for (int e = 0; e <= EL; ++e) tk[e] = 0u;
+        auto insert = [&](uint32_t x) {
+#pragma unroll
+          for (int e = 0; e < EL; ++e) {
+            const uint32_t hi = max(tk[e], x);
+            x = min(tk[e], x);
+            tk[e] = hi;
+          }
+          tk[EL] = max(tk[EL], x);
+        };
         auto emit = [&](int col_last) {
           const int hg = (n0 + col_last) / D;
           if (row < M && hg < NH) {
             uint64_t* dst = lists + ((int64_t)row * NH + hg) * LS;
 #pragma unroll
             for (int e = 0; e < EL; ++e)
-              dst[e] = ta[e] < 0.f ? 0ull
-                                   : (((uint64_t)(__float_as_uint(ta[e]) + 1u) << 32) |
-                                      (uint64_t)(0xFFFFFFFFu - th[e]));
-            dst[EL] = cut < 0.f ? 0ull : ((uint64_t)(__float_as_uint(cut) + 1u) << 32);
+              dst[e] = tk[e] ? (((uint64_t)((tk[e] & keep) + 1u) << 32) |
+                                (uint64_t)(0xFFFFFFFFu - (tk[e] & cmask)))
+                             : 0ull;
+            dst[EL] = tk[EL] ? ((uint64_t)((tk[EL] & keep) + 1u) << 32) : 0ull;
           }
 #pragma unroll
-          for (int e = 0; e < EL; ++e) ta[e] = -1.f;
-          cut = -1.f;
+          for (int e = 0; e <= EL; ++e) tk[e] = 0u;
         };
+        uint32_t ra[32], rb[32];
+        tmem_ld32_async(taddr + (uint32_t)cbeg, ra);
+        tmem_wait(ra);
+#pragma unroll
         for (int c0 = cbeg; c0 < cend; c0 += 32) {
-          float v[32];
-          tmem_ld32(taddr + (uint32_t)c0, v);
+          const bool more = c0 + 32 < cend;
+          if (more) tmem_ld32_async(taddr + (uint32_t)(c0 + 32), rb);
+          // n0 is a multiple of 256 and c0 of 32, so the column within the
+          // hash is (c0 mod D) + k for D >= 32 and k mod D otherwise
+          const uint32_t cb = 0x80000000u | (D >= 32 ? ((uint32_t)c0 & dmask) : 0u);
 #pragma unroll
           for (int k = 0; k < 32; ++k) {
-            const float av = fabsf(v[k]);
-            if (av > ta[EL - 1]) {
-              const uint32_t i_in = (uint32_t)(n0 + c0 + k) & dmask;
-              float x = av;
-              uint32_t xh = i_in + (v[k] < 0.f ? (uint32_t)D : 0u);
-#pragma unroll
-              for (int e = 0; e < EL; ++e) {
-                const bool sw = x > ta[e];
-                const float tv = ta[e];
-                const uint32_t u = th[e];
-                ta[e] = sw ? x : tv;
-                th[e] = sw ? xh : u;
-                x = sw ? tv : x;
-                xh = sw ? u : xh;
-              }
-              cut = fmaxf(cut, x);     // the entry pushed out of the list
-            } else {
-              cut = fmaxf(cut, av);
-            }
-            if (D < 32 && (((uint32_t)(n0 + c0 + k) & dmask) == dmask)) emit(c0 + k);
+            const uint32_t u = ra[k];
+            const uint32_t i_in = (uint32_t)k & dmask;
+            insert((u & keep) | (cb + (D >= 32 ? (uint32_t)k : i_in)) | ((u >> 31) << ldD));
+            if (D < 32 && i_in == dmask) emit(c0 + k);
           }
-          if (D >= 32 && D <= TC_BN / 2 && (((uint32_t)(n0 + c0 + 31) & dmask) == dmask)) emit(c0 + 31);
+          if (D >= 32 && D <= TC_BN / 2 && (((uint32_t)(c0 + 31) & dmask) == dmask)) emit(c0 + 31);
+          if (more) {
+            tmem_wait(rb);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) ra[k] = rb[k];
+          }
         }
         if (D == TC_BN) {
           // the hash spans both column halves: merge the second half into the first
           const int bA = 1 + quarter, bB = 5 + quarter;
           if (half == 1) {
 #pragma unroll
-            for (int e = 0; e < EL; ++e) { sh->xa[quarter][lane][e] = ta[e]; sh->xh[quarter][lane][e] = th[e]; }
-            sh->xa[quarter][lane][EL] = cut;
+            for (int e = 0; e <= EL; ++e) sh->xk[quarter][lane][e] = tk[e];
             asm volatile("bar.sync %0, 64;" ::"r"(bA) : "memory");
             asm volatile("bar.sync %0, 64;" ::"r"(bB) : "memory");
           } else {
             asm volatile("bar.sync %0, 64;" ::"r"(bA) : "memory");
-            cut = fmaxf(cut, sh->xa[quarter][lane][EL]);
 #pragma unroll
-            for (int f = 0; f < EL; ++f) {
-              float x = sh->xa[quarter][lane][f];
-              uint32_t xh = sh->xh[quarter][lane][f];
-              if (x < 0.f) continue;
-#pragma unroll
-              for (int e = 0; e < EL; ++e) {   // strictly greater: first-half entries win ties
-                const bool sw = x > ta[e];
-                const float tv = ta[e];
-                const uint32_t u = th[e];
-                ta[e] = sw ? x : tv;
-                th[e] = sw ? xh : u;
-                x = sw ? tv : x;
-                xh = sw ? u : xh;
-              }
-              cut = fmaxf(cut, x);
-            }
+            for (int f = 0; f <= EL; ++f) insert(sh->xk[quarter][lane][f]);
             asm volatile("bar.sync %0, 64;" ::"r"(bB) : "memory");
             emit(TC_BN - 1);
           }
@@ -483,15 +502,14 @@ double tc_error_bound_factor(int Kp, int pieces) {
 }
 
 double bf16_window_factor(int d) {
-  // Near-tie window of the BF16 path, relative to ||a|| ||b||.  Rounding both
-  // operands to BF16 (unit roundoff u = 2^-8) perturbs each product by a
-  // relative error of variance at most 2 u^2 / 3, so for vectors whose mass
-  // is spread over the d coordinates the projection error has standard
-  // deviation about sqrt(2/3) u ||a|| ||b|| / sqrt(d).  The window is nine of
+  // Near-tie window of a dot product with one operand rounded to BF16,
+  // relative to ||a|| ||b||.  Rounding to BF16 (unit roundoff u = 2^-8)
+  // perturbs each product by a relative error of variance at most u^2 / 3,
+  // so for vectors whose mass is spread over the d coordinates the error has
+  // standard deviation about u ||a|| ||b|| / sqrt(3 d).  The window is nine of
   // those plus the worst-case FP32 accumulation error: a statistical margin,
   // not a bound (the BF16 path is graded by recall and score error).
-  return 9.0 * 0.816496580927726 * 3.90625e-3 / std::sqrt((double)d) +
-         2.0 * gamma_fp32(tc_kpad(d));
+  return 9.0 * 3.90625e-3 / std::sqrt(3.0 * (double)d) + 2.0 * gamma_fp32(tc_kpad(d));
 }
 
 namespace {
@@ -551,6 +569,15 @@ fpp_status launch_proj(const CUtensorMap& ma, const CUtensorMap& mb, float* C, i
 }
 
 }  // namespace
+
+float tc_list_trunc(int D) {
+  // |p| - |p|' < 2^(b - 23) |p| with b = log2(2D) cleared mantissa bits;
+  // relative to |p|' it is below 2^(b - 23) / (1 - 2^(b - 23)), rounded up
+  int b = 0;
+  while ((1 << b) < 2 * D) ++b;
+  const double t = std::ldexp(1.0, b - 23);
+  return (float)(t / (1.0 - t) * 1.0001);
+}
 
 int tc_list_len(int want) {
   if (want <= 2) return 2;

@@ -25,7 +25,7 @@ fpp_status gemm_f32_nt(const float* A, int64_t lda, const float* B, int64_t ldb,
 // arrays [rows][pieces * Kp] made by split_to_bf16; C is FP32 [M][ldc].
 int tc_kpad(int d);
 double tc_error_bound_factor(int Kp, int pieces);
-// Near-tie window (relative to ||a|| ||b||) of plain BF16 projections and scores.
+// Near-tie window (relative to ||a|| ||b||) of dot products with BF16 rows.
 double bf16_window_factor(int d);
 // FP32 rows [rows][lds] (d used) -> BF16 rows [rows][ldo], zero padded.
 fpp_status rows_to_bf16(const float* src, int64_t rows, int64_t lds, int d, int64_t ldo, void* dst,
@@ -37,6 +37,8 @@ fpp_status gemm_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, i
 // Projection with the per-(row, hash) top-EL list epilogue (EL in {2, 4, 8};
 // D must divide 256); EL = 0 stores the projections like gemm_tc.
 int tc_list_len(int want);
+// Relative bound t of the list values' truncation: |p|' <= |p| < |p|' (1 + t).
+float tc_list_trunc(int D);
 fpp_status project_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, int pieces, int D,
                       int EL, float* C, int64_t ldc, uint64_t* lists, int* err, cudaStream_t st);
 
@@ -46,6 +48,7 @@ struct HashArgs {
   int64_t ldp;
   const uint64_t* lists; // [rows][2 nt][EL + 1] per-hash top-EL keys + cut when P is NULL
   int EL;
+  float trunc;           // list values: |p|' <= |p| < |p|' (1 + trunc) (tc_list_trunc)
   int64_t rows;          // points in this chunk
   int64_t row0;          // id of the chunk's first point
   int t0, nt, D;
@@ -101,6 +104,7 @@ struct ProbeArgs {
   int64_t ldp;
   const uint64_t* lists;     // [mq][2 nt][EL + 1] per-hash top-EL keys and cut (P NULL)
   int EL;
+  float trunc;               // list values: |p|' <= |p| < |p|' (1 + trunc) (tc_list_trunc)
   int64_t mq;
   const float* Q;            // [mq][ldq] padded queries
   int64_t ldq;

@@ -1,6 +1,8 @@
 // Search kernels: probe ranking per (query, table) (Section 3.4, "Multi-
 // probing for querying") and the fused candidate gather, bitmap
 // de-duplication, exact scoring and top-k (Sections 1 and 4).
+#include <algorithm>
+#include <atomic>
 #include <climits>
 
 #include <cuda_bf16.h>
@@ -198,9 +200,14 @@ probe_kernel(ProbeArgs a, int pmax) {
   bool certain = C >= Tsel;
   if (certain && boundary) {
     // FP32 arithmetic (the FP64 pipe is slow); every factor is positive and
-    // the 1.001 margin covers the few roundings of this expression
+    // the 1.001 margin covers the few roundings of this expression.  Pair
+    // scores from truncated list values may be low by trunc times the two
+    // lists' largest values.
     const float sP = key_score(pout[P - 1]), sP1 = key_score(pout[P]);
-    const float eps = a.gammaf * a.qnorm[q] * (a.rmax[2 * t] + a.rmax[2 * t + 1]);
+    const float tr = a.P ? 0.f
+                         : a.trunc * (signed_entry(lists, 0, D).v +
+                                      signed_entry(lists + LIST_CAP, 0, D).v);
+    const float eps = a.gammaf * a.qnorm[q] * (a.rmax[2 * t] + a.rmax[2 * t + 1]) + tr;
     const float need = (2.f * eps + 6.0e-8f * (fabsf(sP) + fabsf(sP1))) * 1.001f + 1e-30f;
     certain = (sP - sP1) > need;
   }
@@ -277,7 +284,9 @@ probe_small_kernel(ProbeArgs a) {
       if (e == P) kP1 = best[e];
     }
     const float sP = key_score(kP), sP1 = key_score(kP1);
-    const float eps = a.gammaf * a.qnorm[q] * (a.rmax[2 * t] + a.rmax[2 * t + 1]);
+    // truncated list values: pair scores may be low by trunc (v1 + v2)
+    const float eps = a.gammaf * a.qnorm[q] * (a.rmax[2 * t] + a.rmax[2 * t + 1]) +
+                      a.trunc * (va[0][0] + va[1][0]);
     const float need = (2.f * eps + 6.0e-8f * (fabsf(sP) + fabsf(sP1))) * 1.001f + 1e-30f;
     certain = (sP - sP1) > need;
   }
@@ -452,8 +461,11 @@ probe_window_kernel(ProbeArgs a) {
     uint32_t hh[2][WIN_MAX];
     for (int j = 0; j < 2 && ok; ++j) {
       const uint64_t* L = a.lists + ((q * a.nt + tl) * 2 + j) * (int64_t)(a.EL + 1);
-      const double eps = a.gamma * qn * (double)a.rmax[2 * t + j] * (1.0 + 1e-6);
       auto val = [&](uint64_t k) { return k ? (double)__uint_as_float((uint32_t)(k >> 32) - 1u) : -1.0; };
+      // FP32 error, plus the truncation of the list values (at most trunc
+      // times the hash's largest value)
+      const double eps = a.gamma * qn * (double)a.rmax[2 * t + j] * (1.0 + 1e-6) +
+                         (double)a.trunc * fmax(val(L[0]), 0.0) * (1.0 + 1e-6);
       const double lim = val(L[P - 1]) - 2.0 * eps;
       if (!(val(L[a.EL]) < lim)) { ok = false; break; }   // L[EL]: largest |p| left out
       for (int e = 0; e < a.EL && e < WIN_MAX; ++e)
@@ -551,7 +563,10 @@ __global__ void query_norms_kernel(const float* __restrict__ Q, int64_t m, int64
 //  topk           warp per query: best k of its candidates by (score desc,
 //                 id asc).
 
-constexpr int DW = 8;                           // warps per dedup CTA
+constexpr int DW = 8;                           // warps per bitmap-dedup CTA
+constexpr int HW = 4;                           // warps per hash-dedup CTA
+constexpr int HS = 4096;                        // hash slots per warp (power of two)
+constexpr int HMAX = HS / 2;                    // entries a query may have for the hash path
 constexpr int PCHUNK = 128;                     // probed buckets resolved per pass
 constexpr int PPT = PCHUNK / 32;                // buckets per lane per pass
 constexpr int EPT = 8;                          // entries per lane per round
@@ -630,6 +645,22 @@ __device__ __forceinline__ void warp_walk(const WarpWalk& w, Visit& visit) {
   }
 }
 
+// Writes query q's score work items (at most ITEM candidates each) into its
+// own item slots [eoff[q] / ITEM + q, ...): ceil(U / ITEM) of them, never
+// overlapping the next query's (unused slots stay zero-length).
+__device__ __forceinline__ void write_items(const DedupArgs& a, int64_t q, uint32_t U) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nit = (U + ITEM - 1) / ITEM;
+  const uint64_t base = a.eoff[q] / ITEM + (uint64_t)q;
+  for (uint32_t k = lane; k < nit; k += 32) {
+    ScoreItem it;
+    it.q = (uint32_t)q;
+    it.len = min((uint32_t)ITEM, U - k * ITEM);
+    it.start = a.eoff[q] + (uint64_t)k * ITEM;
+    a.items[base + k] = it;
+  }
+}
+
 __global__ void __launch_bounds__(256)
 count_entries_kernel(DedupArgs a) {
   const int lane = threadIdx.x & 31;
@@ -661,6 +692,7 @@ dedup_kernel(DedupArgs a) {
   unsigned long long ent = 0, uni = 0, prb = 0;
   const int64_t nwarps = (int64_t)gridDim.x * DW;
   for (int64_t q = (int64_t)blockIdx.x * DW + wid; q < a.mq; q += nwarps) {
+    if (a.eoff[q + 1] - a.eoff[q] <= (uint64_t)HMAX) continue;   // the hash kernel's
     const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
     WarpWalk w{&a, q, Pq, a.nt * Pq, NB, s_pbase[wid], s_pstart[wid]};
     uint32_t* out = a.cand + a.eoff[q];
@@ -689,18 +721,7 @@ dedup_kernel(DedupArgs a) {
       prb += (unsigned long long)w.nprobe;
     }
     if (lane == 0) a.ucount[q] = U;
-    // work items of at most ITEM candidates, in the query's own item slots
-    // [eoff[q] / ITEM + q, ...): ceil(E_q / ITEM) of them, never overlapping
-    // the next query's (unused slots stay zero-length)
-    const uint32_t nit = (U + ITEM - 1) / ITEM;
-    const uint64_t base = a.eoff[q] / ITEM + (uint64_t)q;
-    for (uint32_t k = lane; k < nit; k += 32) {
-      ScoreItem it;
-      it.q = (uint32_t)q;
-      it.len = min((uint32_t)ITEM, U - k * ITEM);
-      it.start = a.eoff[q] + (uint64_t)k * ITEM;
-      a.items[base + k] = it;
-    }
+    write_items(a, q, U);
     __syncwarp();
     // clear the bitmap words of the ids just written (this warp wrote them)
     for (uint32_t k = lane; k < U; k += 32) bm[out[k] >> 5] = 0u;
@@ -719,11 +740,108 @@ dedup_kernel(DedupArgs a) {
   }
 }
 
+// De-duplication of the queries with at most HMAX bucket entries: each warp
+// owns an open-addressing hash set of HS ids in shared memory (linear
+// probing, insertion by compare-and-swap, so exactly one lane sees an id as
+// new).  The table is at most half full, and it is reset after each query.
+// Larger queries are left to the bitmap kernel.
+constexpr uint32_t HEMPTY = 0xFFFFFFFFu;
+
+__global__ void __launch_bounds__(HW * 32)
+dedup_hash_kernel(DedupArgs a) {
+  extern __shared__ __align__(16) uint32_t s_tab[];
+  __shared__ uint64_t s_pbase[HW][PCHUNK];
+  __shared__ uint32_t s_pstart[HW][PCHUNK + 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t* tab = s_tab + wid * HS;
+  for (int i = lane; i < HS / 4; i += 32)
+    reinterpret_cast<uint4*>(tab)[i] = make_uint4(HEMPTY, HEMPTY, HEMPTY, HEMPTY);
+  __syncwarp();
+  const int64_t NB = 4ll * a.D * a.D;
+  unsigned long long ent = 0, uni = 0, prb = 0;
+  const int64_t nwarps = (int64_t)gridDim.x * HW;
+  for (int64_t q = (int64_t)blockIdx.x * HW + wid; q < a.mq; q += nwarps) {
+    const uint64_t E = a.eoff[q + 1] - a.eoff[q];
+    if (E > (uint64_t)HMAX) continue;
+    const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
+    WarpWalk w{&a, q, Pq, a.nt * Pq, NB, s_pbase[wid], s_pstart[wid]};
+    uint32_t* out = a.cand + a.eoff[q];
+    struct Insert {
+      uint32_t* tab; uint32_t* out; uint32_t n;
+      __device__ void operator()(const uint32_t (&id)[EPT], const bool (&has)[EPT]) {
+        const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+#pragma unroll
+        for (int r = 0; r < EPT; ++r) {
+          bool fresh = false;
+          if (has[r]) {
+            uint32_t h = (id[r] * 0x9E3779B1u) >> (32 - 12);   // log2(HS) = 12
+            while (true) {
+              const uint32_t old = atomicCAS(tab + h, HEMPTY, id[r]);
+              if (old == HEMPTY) { fresh = true; break; }
+              if (old == id[r]) break;
+              h = (h + 1) & (HS - 1);
+            }
+          }
+          const unsigned m = __ballot_sync(FULL, fresh);
+          if (fresh) out[n + __popc(m & lt)] = id[r];
+          n += __popc(m);
+        }
+      }
+    } ins{tab, out, 0u};
+    warp_walk(w, ins);
+    const uint32_t U = ins.n;
+    if (lane == 0) {
+      ent += E;
+      uni += U;
+      prb += (unsigned long long)w.nprobe;
+      a.ucount[q] = U;
+    }
+    write_items(a, q, U);
+    __syncwarp();
+    for (int i = lane; i < HS / 4; i += 32)
+      reinterpret_cast<uint4*>(tab)[i] = make_uint4(HEMPTY, HEMPTY, HEMPTY, HEMPTY);
+    __syncwarp();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ent += __shfl_xor_sync(FULL, ent, o);
+    uni += __shfl_xor_sync(FULL, uni, o);
+    prb += __shfl_xor_sync(FULL, prb, o);
+  }
+  if (lane == 0 && a.stats) {
+    atomicAdd(a.stats + 0, ent);
+    atomicAdd(a.stats + 1, uni);
+    atomicAdd(a.stats + 3, prb);
+  }
+}
+
 // FP32 scores of the candidates of a work item: G lanes per row, each lane
 // CPL float4 chunks of a row, U rows per lane group in flight (all U * CPL
-// row loads of a step issued before any is used; ids are read per step).
-// Every score is within gamma_d ||q|| ||x|| of the exact inner product.
+// row loads of a step issued before any is used).  The item's ids (at most
+// ITEM = 128) are loaded once, 4 per lane, and handed out by shuffles; the
+// next item's header is fetched while the current one is scored.  Every
+// score is within gamma_d ||q|| ||x|| of the exact inner product.
 // EXACT: G * CPL float4 chunks cover a row exactly (no chunk loop).
+static_assert(ITEM == 128, "score kernels hold an item's ids in 4 registers per lane");
+
+__device__ __forceinline__ void load_item_ids(const ScoreArgs& a, const ScoreItem& it, uint32_t (&ids)[4]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t r = (uint32_t)(j * 32 + lane);
+    ids[j] = r < it.len ? __ldg(a.cand + it.start + r) : 0u;
+  }
+}
+
+// id of row r (< 128) of the item from the per-lane registers; base is a
+// warp-uniform row in the same 32-row block as r (so every lane picks the
+// same register before the shuffle)
+__device__ __forceinline__ uint32_t item_id(const uint32_t (&ids)[4], int base, int r) {
+  const int j = base >> 5;
+  const uint32_t v = j == 0 ? ids[0] : j == 1 ? ids[1] : j == 2 ? ids[2] : ids[3];
+  return __shfl_sync(FULL, v, r & 31);
+}
+
 template <int G, int CPL, bool EXACT>
 __global__ void __launch_bounds__(256)
 score_kernel(ScoreArgs a) {
@@ -734,11 +852,14 @@ score_kernel(ScoreArgs a) {
   constexpr int U = 4;
   const int sub = lane % G, grp = lane / G;
   const int nf4 = (int)(a.ldx / 4);
-  for (int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < nslots; it += nw) {
-    const ScoreItem item = a.items[it];
-    if (item.len == 0) continue;
+  int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  ScoreItem item = it < nslots ? a.items[it] : ScoreItem{0u, 0u, 0ull};
+  for (; it < nslots; it += nw) {
+    const ScoreItem nxt = it + nw < nslots ? a.items[it + nw] : ScoreItem{0u, 0u, 0ull};
+    if (item.len == 0) { item = nxt; continue; }
+    uint32_t ids[4];
+    load_item_ids(a, item, ids);
     const float4* q4 = reinterpret_cast<const float4*>(a.Q + (int64_t)item.q * a.ldq);
-    const uint32_t* ids = a.cand + item.start;
     float* out = a.scores + item.start;
     for (int r0 = 0; r0 < (int)item.len; r0 += U * RPP) {
       uint32_t id[U];
@@ -747,7 +868,9 @@ score_kernel(ScoreArgs a) {
       for (int u = 0; u < U; ++u) {
         const int r = r0 + u * RPP + grp;
         ok[u] = (uint32_t)r < item.len;
-        id[u] = ok[u] ? __ldg(ids + r) : 0u;
+        // rows r0 + u * RPP .. + RPP - 1 lie in one 32-row block (RPP divides 32)
+        const uint32_t v = item_id(ids, r0 + u * RPP, r);
+        id[u] = ok[u] ? v : 0u;
       }
       float p[U];
 #pragma unroll
@@ -788,6 +911,7 @@ score_kernel(ScoreArgs a) {
         if (ok[u] && sub == 0) out[r0 + u * RPP + grp] = f;
       }
     }
+    item = nxt;
   }
 }
 
@@ -804,11 +928,14 @@ score_bf16_kernel(ScoreArgs a) {
   const int sub = lane % G, grp = lane / G;
   const int nch = (int)(a.ldxb / 8);
   const uint4* Xb = reinterpret_cast<const uint4*>(a.Xb);
-  for (int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < nslots; it += nw) {
-    const ScoreItem item = a.items[it];
-    if (item.len == 0) continue;
+  int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  ScoreItem item = it < nslots ? a.items[it] : ScoreItem{0u, 0u, 0ull};
+  for (; it < nslots; it += nw) {
+    const ScoreItem nxt = it + nw < nslots ? a.items[it + nw] : ScoreItem{0u, 0u, 0ull};
+    if (item.len == 0) { item = nxt; continue; }
+    uint32_t ids[4];
+    load_item_ids(a, item, ids);
     const float4* q4 = reinterpret_cast<const float4*>(a.Q + (int64_t)item.q * a.ldq);
-    const uint32_t* ids = a.cand + item.start;
     float* out = a.scores + item.start;
     for (int r0 = 0; r0 < (int)item.len; r0 += U * RPP) {
       uint32_t id[U];
@@ -817,7 +944,9 @@ score_bf16_kernel(ScoreArgs a) {
       for (int u = 0; u < U; ++u) {
         const int r = r0 + u * RPP + grp;
         ok[u] = (uint32_t)r < item.len;
-        id[u] = ok[u] ? __ldg(ids + r) : 0u;
+        // rows r0 + u * RPP .. + RPP - 1 lie in one 32-row block (RPP divides 32)
+        const uint32_t v = item_id(ids, r0 + u * RPP, r);
+        id[u] = ok[u] ? v : 0u;
       }
       float p[U];
 #pragma unroll
@@ -862,6 +991,7 @@ score_bf16_kernel(ScoreArgs a) {
         if (ok[u] && sub == 0) out[r0 + u * RPP + grp] = f;
       }
     }
+    item = nxt;
   }
 }
 
@@ -872,6 +1002,58 @@ score_bf16_kernel(ScoreArgs a) {
 // every candidate whose stored FP32 score could still reach the top-k is
 // re-scored (the slow path, rare).
 constexpr int TK_SLOW = 2048;
+constexpr int SEL_REGS = 16;   // candidates per lane of the register selection
+
+// Best kp of U <= 32 * SEL_REGS scored candidates by (score desc, id asc),
+// sorted into buf[0..): the score keys sit in registers; a binary search over
+// the 32-bit key finds the largest t with at least kp keys >= t, the keys >= t
+// are compacted into buf and sorted.  Returns min(U, kp), or -1 when ties at
+// t leave more than cap entries (the caller then uses the running buffer).
+__device__ __forceinline__ int select_small(const float* sc, const uint32_t* cid, uint32_t U,
+                                            int kp, uint64_t* buf, int cap) {
+  const int lane = threadIdx.x & 31;
+  uint32_t key[SEL_REGS];
+#pragma unroll
+  for (int j = 0; j < SEL_REGS; ++j) {
+    const uint32_t i = (uint32_t)(j * 32 + lane);
+    key[j] = i < U ? float_key(sc[i]) : 0u;   // 0: no entry (below every score key)
+  }
+  uint32_t t = 1u;
+  if (U > (uint32_t)kp) {
+    uint32_t lo = 1u, hi = 0xFFFFFFFFu;   // count(key >= lo) >= kp holds throughout
+    while (lo < hi) {
+      const uint32_t mid = lo + (hi - lo + 1u) / 2u;
+      unsigned c = 0;
+#pragma unroll
+      for (int j = 0; j < SEL_REGS; ++j) c += key[j] >= mid ? 1u : 0u;
+      c = __reduce_add_sync(FULL, c);
+      if (c >= (unsigned)kp) lo = mid; else hi = mid - 1u;
+    }
+    t = lo;
+  }
+  unsigned c = 0;
+#pragma unroll
+  for (int j = 0; j < SEL_REGS; ++j) c += key[j] >= t ? 1u : 0u;
+  const unsigned total = __reduce_add_sync(FULL, c);
+  if (total > (unsigned)cap) return -1;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned n = 0;
+#pragma unroll
+  for (int j = 0; j < SEL_REGS; ++j) {
+    const bool take = key[j] >= t;
+    const unsigned m = __ballot_sync(FULL, take);
+    if (take) {
+      const uint32_t i = (uint32_t)(j * 32 + lane);
+      buf[n + __popc(m & lt)] = pack_key(sc[i], cid[i]);
+    }
+    n += __popc(m);
+  }
+  const int np2 = pow2_ceil(total > 1u ? (int)total : 1);
+  for (int e = (int)total + lane; e < np2; e += 32) buf[e] = 0ull;
+  __syncwarp();
+  warp_sort_desc(buf, np2);
+  return min((int)total, kp);
+}
 
 __global__ void __launch_bounds__(256)
 topk_kernel(TopkArgs a) {
@@ -889,27 +1071,24 @@ topk_kernel(TopkArgs a) {
   const uint32_t* cid = a.cand + start;
   const float* qv = a.Q + q * a.ldq;
   const int nf4 = (int)(a.ldq / 4);
-  WarpTop wt;
-  wt.init(buf, a.cap, kp);
-  for (uint32_t i0 = 0; i0 < U; i0 += 32) {
-    const uint32_t i = i0 + lane;
-    const bool ok = i < U;
-    wt.offer(ok, ok ? pack_key(sc[i], cid[i]) : 0ull);
-  }
-  const int nk = wt.finish();
-  // exact re-scoring of the pre-selected entries, 8 rows at a time
-  for (int e0 = 0; e0 < nk; e0 += 8) {
-    double sv[8];
-    uint32_t idv[8];
-    const float* rows[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      idv[u] = key_id(buf[min(e0 + u, nk - 1)]);
-      rows[u] = a.X + (int64_t)idv[u] * a.ldx;
+  int nk = -1;
+  if (U <= 32u * SEL_REGS) nk = select_small(sc, cid, U, kp, buf, a.cap);
+  if (nk < 0) {   // many candidates (or heavy ties): running buffer with compaction
+    WarpTop wt;
+    wt.init(buf, a.cap, kp);
+    for (uint32_t i0 = 0; i0 < U; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      const bool ok = i < U;
+      wt.offer(ok, ok ? pack_key(sc[i], cid[i]) : 0ull);
     }
-    warp_dot2_gather<8>(qv, rows, nf4, sv);
-    if (lane == 0)
-      for (int u = 0; u < 8 && e0 + u < nk; ++u) resc[e0 + u] = SD{sv[u], idv[u], 0};
+    nk = wt.finish();
+  }
+  // exact re-scoring of the pre-selected entries, one row per lane
+  for (int e = lane; e < ((nk + 31) & ~31); e += 32) {
+    if (e < nk) {
+      const uint32_t id = key_id(buf[e]);
+      resc[e] = SD{thread_dot2_f4(qv, a.X + (int64_t)id * a.ldx, nf4), id, 0};
+    }
   }
   for (int e = nk + lane; e < a.rcap; e += 32) resc[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
   __syncwarp();
@@ -958,15 +1137,8 @@ topk_kernel(TopkArgs a) {
     ns = TK_SLOW;
   }
   __syncwarp();
-  for (unsigned e0 = 0; e0 < ns; e0 += 8) {
-    double sv[8];
-    const float* rows[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) rows[u] = a.X + (int64_t)list[min(e0 + u, ns - 1)].id * a.ldx;
-    warp_dot2_gather<8>(qv, rows, nf4, sv);
-    if (lane == 0)
-      for (unsigned u = 0; u < 8 && e0 + u < ns; ++u) list[e0 + u].s = sv[u];
-  }
+  for (unsigned e = lane; e < ns; e += 32)
+    list[e].s = thread_dot2_f4(qv, a.X + (int64_t)list[e].id * a.ldx, nf4);
   const int np2 = pow2_ceil(ns > 1 ? (int)ns : 1);
   for (int e = (int)ns + lane; e < np2; e += 32) list[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
   __syncwarp();
@@ -1117,21 +1289,44 @@ int choose_g(int nf4) {
   return g;
 }
 
+// Launch of a score kernel: SCORE_WAVES times as many 256-thread CTAs as fit
+// on the GPU at once; the kernels stride over the work items, and the
+// hardware scheduler balances the CTAs' uneven loads.
+constexpr int SCORE_WAVES = 3;
+
+template <class Kernel>
+fpp_status launch_resident(Kernel* k, int sms, const ScoreArgs& a, std::atomic<int>& per_sm,
+                           cudaStream_t st) {
+  int b = per_sm.load(std::memory_order_relaxed);
+  if (!b) {
+    FPP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, 256, 0));
+    b = std::max(1, b);
+    per_sm.store(b, std::memory_order_relaxed);
+  }
+  k<<<b * sms * SCORE_WAVES, 256, 0, st>>>(a);
+  FPP_LAUNCHED();
+  return FPP_OK;
+}
+
+template <int G, int CPL, bool EXACT>
+fpp_status launch_score_one(const ScoreArgs& a, int sms, cudaStream_t st) {
+  static std::atomic<int> per_sm{0};
+  return launch_resident(score_kernel<G, CPL, EXACT>, sms, a, per_sm, st);
+}
+
 template <int G>
-fpp_status launch_score_g(const ScoreArgs& a, int grid, cudaStream_t st) {
+fpp_status launch_score_g(const ScoreArgs& a, int sms, cudaStream_t st) {
   // chunks per lane: ceil(nf4 / G) <= 4 by the choice of G, except G = 32
   // (large d), which loops over chunk groups of 8
   const int nf4 = (int)(a.ldx / 4);
   const int cpl = (nf4 + G - 1) / G;
-  if (cpl == 1 && nf4 == G) score_kernel<G, 1, true><<<grid, 256, 0, st>>>(a);
-  else if (cpl == 2 && nf4 == 2 * G) score_kernel<G, 2, true><<<grid, 256, 0, st>>>(a);
-  else if (cpl == 4 && nf4 == 4 * G) score_kernel<G, 4, true><<<grid, 256, 0, st>>>(a);
-  else if (cpl <= 1) score_kernel<G, 1, false><<<grid, 256, 0, st>>>(a);
-  else if (cpl <= 2) score_kernel<G, 2, false><<<grid, 256, 0, st>>>(a);
-  else if (cpl <= 4) score_kernel<G, 4, false><<<grid, 256, 0, st>>>(a);
-  else score_kernel<G, 8, false><<<grid, 256, 0, st>>>(a);
-  FPP_LAUNCHED();
-  return FPP_OK;
+  if (cpl == 1 && nf4 == G) return launch_score_one<G, 1, true>(a, sms, st);
+  if (cpl == 2 && nf4 == 2 * G) return launch_score_one<G, 2, true>(a, sms, st);
+  if (cpl == 4 && nf4 == 4 * G) return launch_score_one<G, 4, true>(a, sms, st);
+  if (cpl <= 1) return launch_score_one<G, 1, false>(a, sms, st);
+  if (cpl <= 2) return launch_score_one<G, 2, false>(a, sms, st);
+  if (cpl <= 4) return launch_score_one<G, 4, false>(a, sms, st);
+  return launch_score_one<G, 8, false>(a, sms, st);
 }
 
 }  // namespace
@@ -1200,7 +1395,7 @@ fpp_status launch_query_norms(const float* Q, int64_t m, int64_t ldq, int d, flo
   return FPP_OK;
 }
 
-int dedup_slots(int sm_count) { return sm_count * 4 * DW; }
+int dedup_slots(int sm_count) { return sm_count * DW; }
 int score_item_len() { return ITEM; }
 int64_t score_item_slots(uint64_t entries_total, int64_t mq) {
   return (int64_t)(entries_total / ITEM) + mq + 1;
@@ -1215,6 +1410,23 @@ fpp_status launch_count_entries(const DedupArgs& a, cudaStream_t st) {
 
 fpp_status launch_dedup(const DedupArgs& a, int slots, cudaStream_t st) {
   if (a.mq <= 0) return FPP_OK;
+  // queries with at most HMAX entries: shared-memory hash sets
+  static std::atomic<int> hash_grid{0};
+  const size_t hsmem = (size_t)HW * HS * 4;
+  if (!hash_grid.load(std::memory_order_relaxed)) {
+    FPP_CUDA(cudaFuncSetAttribute(dedup_hash_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)hsmem));
+    int per_sm = 0, dev = 0, sms = 0;
+    FPP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dedup_hash_kernel, HW * 32,
+                                                           hsmem));
+    FPP_CUDA(cudaGetDevice(&dev));
+    FPP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    hash_grid.store(std::max(1, per_sm) * sms, std::memory_order_relaxed);
+  }
+  const int hgrid = (int)std::min<int64_t>(ceil_div(a.mq, HW), hash_grid.load());
+  dedup_hash_kernel<<<hgrid, HW * 32, hsmem, st>>>(a);
+  FPP_LAUNCHED();
+  // the rest: one global bitmap of n bits per warp slot
   const int64_t ctas = ceil_div(a.mq, DW);
   const int grid = (int)std::min<int64_t>(ctas, slots / DW);
   dedup_kernel<<<grid, DW * 32, 0, st>>>(a);
@@ -1222,21 +1434,25 @@ fpp_status launch_dedup(const DedupArgs& a, int slots, cudaStream_t st) {
   return FPP_OK;
 }
 
+template <int G, int CPL, bool EXACT>
+fpp_status launch_score_bf_one(const ScoreArgs& a, int sms, cudaStream_t st) {
+  static std::atomic<int> per_sm{0};
+  return launch_resident(score_bf16_kernel<G, CPL, EXACT>, sms, a, per_sm, st);
+}
+
 template <int G>
-fpp_status launch_score_bf(const ScoreArgs& a, int grid, cudaStream_t st) {
+fpp_status launch_score_bf(const ScoreArgs& a, int sms, cudaStream_t st) {
   const int nch = (int)(a.ldxb / 8);
   const int cpl = (nch + G - 1) / G;
-  if (cpl == 1 && nch == G) score_bf16_kernel<G, 1, true><<<grid, 256, 0, st>>>(a);
-  else if (cpl == 2 && nch == 2 * G) score_bf16_kernel<G, 2, true><<<grid, 256, 0, st>>>(a);
-  else if (cpl <= 1) score_bf16_kernel<G, 1, false><<<grid, 256, 0, st>>>(a);
-  else if (cpl <= 2) score_bf16_kernel<G, 2, false><<<grid, 256, 0, st>>>(a);
-  else score_bf16_kernel<G, 4, false><<<grid, 256, 0, st>>>(a);
-  FPP_LAUNCHED();
-  return FPP_OK;
+  if (cpl == 1 && nch == G) return launch_score_bf_one<G, 1, true>(a, sms, st);
+  if (cpl == 2 && nch == 2 * G) return launch_score_bf_one<G, 2, true>(a, sms, st);
+  if (cpl <= 1) return launch_score_bf_one<G, 1, false>(a, sms, st);
+  if (cpl <= 2) return launch_score_bf_one<G, 2, false>(a, sms, st);
+  return launch_score_bf_one<G, 4, false>(a, sms, st);
 }
 
 fpp_status launch_score(const ScoreArgs& a, int sm_count, cudaStream_t st) {
-  const int grid = sm_count * 8;
+  const int grid = sm_count;
   if (a.Xb) {
     // 16-byte chunks of 8 BF16; at most 2 chunks per lane before G = 32
     int g = 1;

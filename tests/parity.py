@@ -100,3 +100,26 @@ def compare_probes(ix, Q, P, gpu_probes, tables):
             if set(b[ti].tolist()) != set(gpu_probes[i, ti].astype(np.int64).tolist()):
                 fails.append((i, tables[ti]))
     return compared, skipped, fails
+
+
+def compare_candidates(res, gpu_cands, tables, excl_by_table):
+    """Per query: the de-duplicated candidate set must equal the oracle's
+    unless a probe boundary or a probed bucket is flagged.  Returns
+    (n_compared, n_skipped, failures)."""
+    compared, skipped, fails = 0, 0, []
+    for i, r in enumerate(res):
+        flagged = bool(np.any(r.probe_flag))
+        if not flagged:
+            for ti, t in enumerate(tables):
+                ex = excl_by_table[t]
+                if ex and any(int(b) in ex for b in r.buckets[ti]):
+                    flagged = True
+                    break
+        if flagged:
+            skipped += 1
+            continue
+        compared += 1
+        g = np.asarray(gpu_cands[i]).astype(np.int64)
+        if not np.array_equal(g, r.cand):
+            fails.append((i, len(r.cand), len(g)))
+    return compared, skipped, fails

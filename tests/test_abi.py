@@ -34,6 +34,8 @@ def test_struct_sizes_match_header(lib):
     assert ctypes.sizeof(F.fpp_params) == 56
     assert ctypes.sizeof(F.fpp_search_opts) == 48
     assert ctypes.sizeof(F.fpp_search_stats) == 88
+    assert ctypes.sizeof(F.fpp_server_cfg) == 32
+    assert ctypes.sizeof(F.fpp_server_stats) == 64
 
 
 @pytest.mark.parametrize("seed,L,D,d", [(2000, 10, 64, 64), (7, 3, 5, 13), (2001, 4, 256, 128)])

@@ -1,12 +1,12 @@
 """BF16 precision path (FPP_BF16) against the FP64 oracle and the exact path.
 
-The BF16 path decides on one-product BF16 projections and BF16 candidate
-scores; decisions inside a statistical near-tie window are re-decided on the
-FP32 rows and a shortlist is re-scored exactly.  It is graded by recall and
-score error, so these tests bound the disagreement rather than require none:
-bucket ids, probe sets and top-k ids agree with the oracle except on a small
-fraction of decisions, returned scores are exact inner products of the
-returned ids, and recall matches the exact path's.
+The BF16 path hashes and probes exactly as the FP32 path does and scores
+candidates from BF16 rows; a shortlist is re-scored exactly and a top-k
+boundary inside the statistical BF16 window is re-decided.  It is graded by
+recall and score error: bucket ids and probe sets equal the exact path's,
+top-k ids agree with the oracle except on a small fraction of queries,
+returned scores are exact inner products of the returned ids, and recall
+matches the exact path's.
 """
 import numpy as np
 import pytest
@@ -40,21 +40,29 @@ def _exact_scores(X, Q, ids):
     return out
 
 
-def test_bf16_window_covers_projection_error(F):
-    # every BF16 projection error stays inside the near-tie window
+def _round_bf16(x):
+    """Round-to-nearest-even of FP32 values to BF16, returned as FP32."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16
+    return u.astype(np.uint32).view(np.float32)
+
+
+def test_bf16_hashing_equals_exact_path_and_window_covers_bf16_scores(F):
     for d, D, L in ((128, 256, 2), (960, 64, 1), (37, 5, 3)):
         X, Q = W.small_mixture(800, 400, d, 32, 0.25, 300 + d)
-        ix = F.Index(X, L, D, 0.5, seed=50 + d, precision=F.FPP_BF16)
-        P = F.fpp_debug_projections(ix.handle, Q).astype(np.float64)
-        R = O.gaussian_rotations(50 + d, L, D, d).astype(np.float64).reshape(-1, d)
-        Q64 = Q.astype(np.float64)
-        exact = Q64 @ R.T
-        c = F.fpp_projection_error_bound(ix.handle)
-        win = c * np.linalg.norm(Q64, axis=1)[:, None] * np.linalg.norm(R, axis=1)[None, :]
-        ratio = np.abs(P - exact) / win
-        assert float(ratio.max()) < 1.0, (d, float(ratio.max()))
-        # and the projections really are single BF16 products (not the split)
-        assert float(np.abs(P - exact).max()) > 1e-4 * float(np.abs(exact).max())
+        ix16 = F.Index(X, L, D, 0.5, seed=50 + d, precision=F.FPP_BF16)
+        ix32 = F.Index(X, L, D, 0.5, seed=50 + d)
+        # hashing and probing run on the same exact-split projections
+        assert np.array_equal(F.fpp_debug_projections(ix16.handle, Q),
+                              F.fpp_debug_projections(ix32.handle, Q))
+        # first-pass scores from BF16 rows stay inside the statistical window
+        c = ix16.info()["score_error_factor"]
+        Xb = _round_bf16(X).astype(np.float64)
+        X64, Q64 = X.astype(np.float64), Q.astype(np.float64)
+        err = np.abs(Q64 @ Xb.T - Q64 @ X64.T)
+        win = c * np.linalg.norm(Q64, axis=1)[:, None] * np.linalg.norm(X64, axis=1)[None, :]
+        assert float((err / win).max()) < 1.0, d
+        assert ix32.info()["score_error_factor"] < 0.1 * c   # FP32 bound gamma_d
 
 
 def test_bf16_tiny_decisions_match_oracle(F):
@@ -62,11 +70,11 @@ def test_bf16_tiny_decisions_match_oracle(F):
     X, Q = W.dataset(w)
     ix_o = O.build_index(X, w.L, w.D, w.alpha, seed=w.rot_seed)
     ix_b = F.Index(X, w.L, w.D, w.alpha, seed=w.rot_seed, precision=F.FPP_BF16)
-    excl, bad_points = {}, 0
+    excl = {}
     for t in range(w.L):
         gpb = F.fpp_debug_point_buckets(ix_b.handle, t)
         nbad, unexplained = PT.compare_point_buckets(ix_o, t, gpb)
-        bad_points += len(unexplained)
+        assert not unexplained, (t, unexplained[:10])
         excl[t] = PT.excluded_buckets(ix_o, t, gpb)
         # buckets holding a point hashed differently may differ too
         ora = ix_o.point_buckets[t]
@@ -75,15 +83,14 @@ def test_bf16_tiny_decisions_match_oracle(F):
         excl[t].update(gpb[diff].astype(np.int64).tolist())
         off, ids = F.fpp_debug_table(ix_b.handle, t)
         assert not PT.compare_table(ix_o, t, off, ids, excl[t]), t
-    assert bad_points <= 1e-4 * X.shape[0] * w.L, bad_points
     for P in (1, 4, 16):
         gp = F.fpp_debug_probes(ix_b.handle, Q, P)
         c, s, fails = PT.compare_probes(ix_o, Q, P, gp, list(range(w.L)))
-        assert len(fails) <= 0.002 * max(c, 1), (P, len(fails), c)
+        assert not fails, (P, fails[:5])
         gi, gs = ix_b.search(Q, w.k, P)
         _, _, res = O.search_batch(ix_o, Q, w.k, P)
         c, s, fails = PT.compare_search(res, gi, gs, w.k, list(range(w.L)), excl)
-        assert len(fails) <= 0.02 * max(c, 1), (P, len(fails), c, fails[:3])
+        assert len(fails) <= 0.01 * max(c, 1), (P, len(fails), c, fails[:3])
         assert c >= 0.8 * len(res)
         # scores are exact inner products of the returned ids
         ex = _exact_scores(X, Q, gi)
@@ -106,7 +113,7 @@ def test_bf16_recall_matches_exact_path(F):
         r16 = O.recall_at(i16, bi, k)
         assert r16 >= r32 - 0.005, (P, r32, r16)
         same = np.mean([np.array_equal(a, b) for a, b in zip(i32, i16)])
-        assert same >= 0.97, (P, same)
+        assert same >= 0.99, (P, same)
 
 
 @pytest.mark.parametrize("rerank_k", [0, 5, 100, 256])
@@ -118,7 +125,7 @@ def test_bf16_rerank_lengths(F, rerank_k):
     gi, gs = ix.search(Q, 20, 4)
     ri, rs = ref.search(Q, 20, 4)
     same = np.mean([np.array_equal(a, b) for a, b in zip(gi, ri)])
-    assert same >= 0.97, same
+    assert same >= 0.99, same
 
 
 def test_bf16_ragged_dimension(F):

@@ -48,6 +48,10 @@ def _full_parity(F, X, Q, L, D, alpha, seed, k, probes_list, min_compared=0.9):
         c, s, fails = PT.compare_search(res, gi, gs, k, list(range(L)), excl)
         assert not fails, fails[:3]
         assert c >= min_compared * len(res), (c, s)
+        gc = F.fpp_debug_candidates(ix_g.handle, Q, P)
+        c, s, fails = PT.compare_candidates(res, gc, list(range(L)), excl)
+        assert not fails, fails[:3]
+        assert c >= min_compared * len(res), (c, s)
     return ix_o, ix_g
 
 
