@@ -51,6 +51,9 @@ def parse():
                     help="fp32: exact decisions; bf16: BF16 projections and scores with an "
                          "FP32 re-ranked shortlist")
     ap.add_argument("--rerank-k", type=int, default=100)
+    ap.add_argument("--serve-seconds", type=float, default=3.0,
+                    help="serving workload: seconds of arrivals per offered rate")
+    ap.add_argument("--slots", type=int, default=3, help="serving workload: batches in flight")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -188,11 +191,131 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def calibrate_probes(F, ix, Xd, Qd, k, sweep):
+    """Smallest probe budget of the sweep whose recall@k against the
+    library's brute-force search reaches RECALL_TARGET on a query sample."""
+    mcal = min(CALIB_QUERIES, Qd.shape[0])
+    ti, _ = F.fpp_bruteforce(Xd, Qd[:mcal], k)
+    truth = ti.cpu().numpy()
+    recalls, chosen = {}, None
+    for P in sweep:
+        gi, _ = ix.search(Qd[:mcal], k, P)
+        g = gi.cpu().numpy()
+        hit = sum(len(set(a.tolist()) & set(b.tolist())) for a, b in zip(g, truth))
+        recalls[P] = hit / (k * mcal)
+        if chosen is None and recalls[P] >= RECALL_TARGET:
+            chosen = P
+    if chosen is None:
+        chosen = max(recalls, key=lambda p: recalls[p])
+    return chosen, recalls, mcal
+
+
+def run_serve(args, w):
+    """Serving workload: requests arrive as a Poisson process at each offered
+    query rate (sizes log-uniform in 1..4096, k in {10, 100}), go through the
+    library's continuous-batching server and are timed from submit to
+    completion (host queries in, host results out).  Then a saturation run
+    submits the same request mix without pacing; its throughput is `value`."""
+    import threading
+
+    import torch
+    import paper_2206_01382_gb300 as F
+    from paper_2206_01382_gb300 import _build
+
+    torch.cuda.set_device(0)
+    _build.build()
+    F.load()
+    X, Q = W.dataset(w)
+    Xd = torch.from_numpy(X).cuda()
+    Qd = torch.from_numpy(Q[:CALIB_QUERIES]).cuda()
+    prec = F.FPP_BF16 if args.precision == "bf16" else F.FPP_FP32
+    tb = time.perf_counter()
+    ix = F.Index(Xd, w.L, w.D, w.alpha, seed=w.rot_seed, precision=prec, rerank_k=args.rerank_k)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - tb
+    P, recalls, mcal = calibrate_probes(F, ix, Xd, Qd, w.k, [args.probes] if args.probes else w.probes)
+    del Xd
+    srv = F.Server(ix, k_max=100, probes_max=P, slots=args.slots, max_batch=4096)
+    m = Q.shape[0]
+
+    def drive(t, sizes, ks, paced):
+        rids = [None] * len(t)
+        lat = np.zeros(len(t))
+        start = time.perf_counter()
+
+        def submitter():
+            qi = 0
+            for i in range(len(t)):
+                if paced:
+                    wait = t[i] - (time.perf_counter() - start)
+                    if wait > 0:
+                        time.sleep(wait)
+                nq = int(sizes[i])
+                if qi + nq > m:
+                    qi = 0
+                rids[i] = srv.submit(Q[qi:qi + nq], int(ks[i]), P)
+                qi += nq
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        for i in range(len(t)):
+            while rids[i] is None:
+                time.sleep(5e-5)
+            lat[i] = srv.poll(rids[i])[2]
+        th.join()
+        wall = time.perf_counter() - start
+        return {"requests": int(len(t)), "queries": int(sizes.sum()),
+                "qps": float(sizes.sum() / wall),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_request": float(sizes.mean())}
+
+    # warm-up (allocations, first launches)
+    t, sizes, ks = W.serve_arrivals(99, 100_000, 0.2)
+    drive(t, sizes, ks, paced=False)
+    s0 = srv.stats()
+    rates = {}
+    for ri, rate in enumerate(W.SERVE_RATES):
+        t, sizes, ks = W.serve_arrivals(ri, rate, args.serve_seconds)
+        r = drive(t, sizes, ks, paced=True)
+        r["offered_qps"] = rate
+        rates[str(rate)] = r
+    t, sizes, ks = W.serve_arrivals(len(W.SERVE_RATES), W.SERVE_RATES[-1], args.serve_seconds)
+    sat = drive(t, sizes, ks, paced=False)
+    s1 = srv.stats()
+    srv.close()
+    batches = s1["batches"] - s0["batches"]
+    line = {
+        "metric": METRIC, "value": sat["qps"], "unit": "queries/s", "n_gpus": 1,
+        "steps": len(W.SERVE_RATES) + 1, "warmup": 1, "ms_per_step": None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if prec == F.FPP_BF16 else "f32", "data": "synthetic",
+        "config": {"workload": w.name, "note": w.note, "precision": args.precision,
+                   "rerank_k": args.rerank_k if prec == F.FPP_BF16 else None,
+                   "n": w.n, "d": w.d, "L": w.L, "D": w.D, "alpha": w.alpha, "probes": P,
+                   "recall_at_10": recalls[P], "recall_sweep": recalls, "recall_sample": mcal,
+                   "slots": args.slots, "max_batch": 4096, "build_s": build_s,
+                   "l2": "inputs larger than L2 (X is "
+                         f"{w.n * w.d * 4 / 2**20:.0f} MiB FP32), no flush"},
+        "serving": {"offered": rates, "saturation": sat,
+                    "mean_batch_queries": (s1["queries"] - s0["queries"]) / max(batches, 1)},
+        "latency_ms": {"p50": sat["p50_ms"], "p99": sat["p99_ms"]},
+        "roofline": None,
+        "e2e": {"value": sat["qps"], "unit": "queries/s",
+                "h2d_bytes_per_step": int(sat["queries"] * w.d * 4),
+                "d2h_bytes_per_step": None},
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     w = W.WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, w)
+        return
+    if w.name == "serve2m":
+        run_serve(args, w)
         return
     import torch
     import paper_2206_01382_gb300 as F
@@ -230,21 +353,8 @@ def main():
 
     # probe budget: smallest of the sweep with recall@10 >= 0.90 on a sample
     k = w.k
-    mcal = min(CALIB_QUERIES, len(Q))
-    ti, _ = F.fpp_bruteforce(Xd, Qd[:mcal], k)
-    truth = ti.cpu().numpy()
-    recalls = {}
-    chosen = None
-    for P in ([args.probes] if args.probes else list(w.probes)):
-        gi, _ = ix.search(Qd[:mcal], k, P)
-        g = gi.cpu().numpy()
-        hit = sum(len(set(a.tolist()) & set(b.tolist())) for a, b in zip(g, truth))
-        recalls[P] = hit / (k * mcal)
-        if chosen is None and recalls[P] >= RECALL_TARGET:
-            chosen = P
-    if chosen is None:
-        chosen = max(recalls, key=lambda p: recalls[p])
-    P = chosen
+    P, recalls, mcal = calibrate_probes(F, ix, Xd, Qd, k,
+                                        [args.probes] if args.probes else list(w.probes))
     m = Q.shape[0]
     ids = torch.empty((m, k), dtype=torch.int64, device=dev)
     sc = torch.empty((m, k), dtype=torch.float32, device=dev)

@@ -561,6 +561,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   da.bitmaps = ws.bitmaps.as<uint32_t>(); da.bitmap_words = ws.bitmap_words;
   da.ecount = ws.ecount.as<uint32_t>(); da.eoff = ws.eoff.as<uint64_t>();
   da.ucount = ws.ecount.as<uint32_t>() + mc;
+  da.nitems = reinterpret_cast<unsigned*>(stv + 10);
   da.stats = stv;
   FPP_TRY(launch_count_entries(da, st));
   FPP_TRY(exclusive_scan_u32(ws.ecount.as<uint32_t>(), mc, ws.eoff.as<uint64_t>(), 0,
@@ -580,18 +581,15 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
     FPP_TRY(ws.cscores.ensure((size_t)cap * 4));
     ws.cand_cap = cap;
   }
-  {
-    const size_t ib = (size_t)score_item_slots(ws.cand_cap, mc) * sizeof(ScoreItem);
-    FPP_TRY(ws.items.ensure(ib));
-    FPP_CUDA(cudaMemsetAsync(ws.items.p, 0, ib, st));
-  }
+  FPP_TRY(ws.items.ensure((size_t)score_item_slots(ws.cand_cap, mc) * sizeof(ScoreItem)));
   da.cand = ws.cand.as<uint32_t>();
   da.items = ws.items.as<ScoreItem>();
   FPP_TRY(launch_dedup(da, ws.slots, st));
   if (ev) FPP_CUDA(cudaEventRecord(ev[5], st));
   if (stage == kCandidatesOnly) return FPP_OK;
   ScoreArgs sa{};
-  sa.items = ws.items.as<ScoreItem>(); sa.eoff = ws.eoff.as<uint64_t>(); sa.mq = mc;
+  sa.items = ws.items.as<ScoreItem>(); sa.nitems = da.nitems;
+  sa.eoff = ws.eoff.as<uint64_t>(); sa.mq = mc;
   sa.cand = ws.cand.as<uint32_t>();
   sa.X = ix->X; sa.ldx = ix->dpad; sa.Q = ws.qpad.as<float>(); sa.ldq = ix->dpad;
   sa.Xb = ix->Xb; sa.ldxb = ix->ldxb;

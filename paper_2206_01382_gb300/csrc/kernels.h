@@ -150,12 +150,14 @@ struct DedupArgs {
   const uint64_t* eoff;      // [mq + 1] exclusive scan of ecount
   uint32_t* cand;            // candidate ids, query q at eoff[q] ..
   uint32_t* ucount;          // [mq] distinct candidates per query
-  ScoreItem* items;          // per-query slots from eoff[q] / ITEM + q (pre-zeroed)
+  ScoreItem* items;          // score work items, appended (any order)
+  unsigned* nitems;          // items appended (zeroed by count_entries)
   unsigned long long* stats; // entries, unique, -, probes
 };
 
 struct ScoreArgs {
-  const ScoreItem* items;    // slots [0, eoff[mq] / ITEM + mq + 1), zero-length = unused
+  const ScoreItem* items;    // [*nitems] work items
+  const unsigned* nitems;
   const uint64_t* eoff;
   int64_t mq;
   const uint32_t* cand;

@@ -645,13 +645,14 @@ __device__ __forceinline__ void warp_walk(const WarpWalk& w, Visit& visit) {
   }
 }
 
-// Writes query q's score work items (at most ITEM candidates each) into its
-// own item slots [eoff[q] / ITEM + q, ...): ceil(U / ITEM) of them, never
-// overlapping the next query's (unused slots stay zero-length).
+// Appends query q's ceil(U / ITEM) score work items (at most ITEM candidates
+// each) to the item list (one counter atomic per query, warp-collective).
 __device__ __forceinline__ void write_items(const DedupArgs& a, int64_t q, uint32_t U) {
   const int lane = threadIdx.x & 31;
   const uint32_t nit = (U + ITEM - 1) / ITEM;
-  const uint64_t base = a.eoff[q] / ITEM + (uint64_t)q;
+  unsigned base = 0;
+  if (lane == 0 && nit) base = atomicAdd(a.nitems, nit);
+  base = __shfl_sync(FULL, base, 0);
   for (uint32_t k = lane; k < nit; k += 32) {
     ScoreItem it;
     it.q = (uint32_t)q;
@@ -664,6 +665,7 @@ __device__ __forceinline__ void write_items(const DedupArgs& a, int64_t q, uint3
 __global__ void __launch_bounds__(256)
 count_entries_kernel(DedupArgs a) {
   const int lane = threadIdx.x & 31;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.nitems = 0u;   // the dedup kernels append
   const int64_t q = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (q >= a.mq) return;
   const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
@@ -817,37 +819,18 @@ dedup_hash_kernel(DedupArgs a) {
 
 // FP32 scores of the candidates of a work item: G lanes per row, each lane
 // CPL float4 chunks of a row, U rows per lane group in flight (all U * CPL
-// row loads of a step issued before any is used).  The item's ids (at most
-// ITEM = 128) are loaded once, 4 per lane, and handed out by shuffles; the
-// next item's header is fetched while the current one is scored.  Every
-// score is within gamma_d ||q|| ||x|| of the exact inner product.
-// EXACT: G * CPL float4 chunks cover a row exactly (no chunk loop).
-static_assert(ITEM == 128, "score kernels hold an item's ids in 4 registers per lane");
-
-__device__ __forceinline__ void load_item_ids(const ScoreArgs& a, const ScoreItem& it, uint32_t (&ids)[4]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const uint32_t r = (uint32_t)(j * 32 + lane);
-    ids[j] = r < it.len ? __ldg(a.cand + it.start + r) : 0u;
-  }
-}
-
-// id of row r (< 128) of the item from the per-lane registers; base is a
-// warp-uniform row in the same 32-row block as r (so every lane picks the
-// same register before the shuffle)
-__device__ __forceinline__ uint32_t item_id(const uint32_t (&ids)[4], int base, int r) {
-  const int j = base >> 5;
-  const uint32_t v = j == 0 ? ids[0] : j == 1 ? ids[1] : j == 2 ? ids[2] : ids[3];
-  return __shfl_sync(FULL, v, r & 31);
-}
+// row loads of a step issued before any is used; ids are read per step,
+// which measured faster than holding an item's ids in registers and
+// shuffling them out).  The next item's header is fetched while the current
+// one is scored.  Every score is within gamma_d ||q|| ||x|| of the exact
+// inner product.  EXACT: G * CPL float4 chunks cover a row exactly.
 
 template <int G, int CPL, bool EXACT>
 __global__ void __launch_bounds__(256)
 score_kernel(ScoreArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t nslots = (int64_t)(a.eoff[a.mq] / ITEM) + a.mq + 1;
+  const int64_t nslots = (int64_t)*a.nitems;
   constexpr int RPP = 32 / G;
   constexpr int U = 4;
   const int sub = lane % G, grp = lane / G;
@@ -857,8 +840,7 @@ score_kernel(ScoreArgs a) {
   for (; it < nslots; it += nw) {
     const ScoreItem nxt = it + nw < nslots ? a.items[it + nw] : ScoreItem{0u, 0u, 0ull};
     if (item.len == 0) { item = nxt; continue; }
-    uint32_t ids[4];
-    load_item_ids(a, item, ids);
+    const uint32_t* ids = a.cand + item.start;
     const float4* q4 = reinterpret_cast<const float4*>(a.Q + (int64_t)item.q * a.ldq);
     float* out = a.scores + item.start;
     for (int r0 = 0; r0 < (int)item.len; r0 += U * RPP) {
@@ -868,9 +850,7 @@ score_kernel(ScoreArgs a) {
       for (int u = 0; u < U; ++u) {
         const int r = r0 + u * RPP + grp;
         ok[u] = (uint32_t)r < item.len;
-        // rows r0 + u * RPP .. + RPP - 1 lie in one 32-row block (RPP divides 32)
-        const uint32_t v = item_id(ids, r0 + u * RPP, r);
-        id[u] = ok[u] ? v : 0u;
+        id[u] = ok[u] ? __ldg(ids + r) : 0u;
       }
       float p[U];
 #pragma unroll
@@ -922,7 +902,7 @@ __global__ void __launch_bounds__(256)
 score_bf16_kernel(ScoreArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t nslots = (int64_t)(a.eoff[a.mq] / ITEM) + a.mq + 1;
+  const int64_t nslots = (int64_t)*a.nitems;
   constexpr int RPP = 32 / G;
   constexpr int U = 4;
   const int sub = lane % G, grp = lane / G;
@@ -933,8 +913,7 @@ score_bf16_kernel(ScoreArgs a) {
   for (; it < nslots; it += nw) {
     const ScoreItem nxt = it + nw < nslots ? a.items[it + nw] : ScoreItem{0u, 0u, 0ull};
     if (item.len == 0) { item = nxt; continue; }
-    uint32_t ids[4];
-    load_item_ids(a, item, ids);
+    const uint32_t* ids = a.cand + item.start;
     const float4* q4 = reinterpret_cast<const float4*>(a.Q + (int64_t)item.q * a.ldq);
     float* out = a.scores + item.start;
     for (int r0 = 0; r0 < (int)item.len; r0 += U * RPP) {
@@ -944,9 +923,7 @@ score_bf16_kernel(ScoreArgs a) {
       for (int u = 0; u < U; ++u) {
         const int r = r0 + u * RPP + grp;
         ok[u] = (uint32_t)r < item.len;
-        // rows r0 + u * RPP .. + RPP - 1 lie in one 32-row block (RPP divides 32)
-        const uint32_t v = item_id(ids, r0 + u * RPP, r);
-        id[u] = ok[u] ? v : 0u;
+        id[u] = ok[u] ? __ldg(ids + r) : 0u;
       }
       float p[U];
 #pragma unroll
@@ -1397,8 +1374,8 @@ fpp_status launch_query_norms(const float* Q, int64_t m, int64_t ldq, int d, flo
 
 int dedup_slots(int sm_count) { return sm_count * DW; }
 int score_item_len() { return ITEM; }
-int64_t score_item_slots(uint64_t entries_total, int64_t mq) {
-  return (int64_t)(entries_total / ITEM) + mq + 1;
+int64_t score_item_slots(uint64_t cand_total, int64_t mq) {
+  return (int64_t)(cand_total / ITEM) + mq + 1;
 }
 
 fpp_status launch_count_entries(const DedupArgs& a, cudaStream_t st) {

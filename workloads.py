@@ -131,3 +131,26 @@ def per_query_draws(w: Workload, m: int, ks=(1, 10, 100), probes=(2, 8, 32, 128)
     k = rng.choice(np.asarray(ks, dtype=np.int32), size=m)
     p = rng.choice(np.asarray(probes, dtype=np.int32), size=m)
     return k.astype(np.int32), p.astype(np.int32)
+
+
+SERVE_RATES = (10_000, 100_000, 1_000_000)   # offered queries per second
+
+
+def serve_arrivals(rate_index: int, rate: float, duration_s: float, max_size: int = 4096,
+                   ks=(10, 100)):
+    """Poisson request arrivals for the serving workload: arrival times (s),
+    request sizes (log-uniform integers in [1, max_size]) and k per request,
+    seeded with 4000 + rate_index.  The request rate is the offered query
+    rate divided by the mean request size."""
+    rng = np.random.Generator(np.random.PCG64(4000 + rate_index))
+    mean_size = (max_size - 1) / math.log(max_size)      # mean of the log-uniform law
+    req_rate = rate / mean_size
+    n = max(1, int(math.ceil(req_rate * duration_s * 1.2)) + 16)
+    t = np.cumsum(rng.exponential(1.0 / req_rate, size=n))
+    t = t[t < duration_s]
+    if t.size == 0:
+        t = np.zeros(1)
+    sizes = np.floor(np.exp(rng.uniform(0.0, math.log(max_size + 1), size=t.size))).astype(np.int64)
+    sizes = np.clip(sizes, 1, max_size)
+    k = rng.choice(np.asarray(ks, dtype=np.int32), size=t.size)
+    return t, sizes, k
