@@ -60,13 +60,13 @@ def parse():
 
 
 def peaks():
+    """HBM GB/s and dense BF16 TFLOP/s: the measured copy bandwidth and the
+    cuBLAS burst figure (each kernel runs well under a second per step)."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        # the projection runs inside a long step: the sustained GEMM figure
-        return (float(d["hbm_gbs"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
-                "measured")
-    return 6800.0, 1700.0, "fallback"
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, "fallback"
 
 
 class ClockSampler:
@@ -392,61 +392,75 @@ def main():
     ms_per_step = elapsed_ms / args.steps
     qps = world * m / (ms_per_step / 1e3)
 
-    # per-phase rooflines (device time measured with CUDA events on the
-    # launching stream inside the library, summed over the timed steps)
+    # per-kernel rooflines (device time measured with CUDA events on the
+    # launching stream inside the library, summed over the timed steps;
+    # "per launch" = one query batch)
     hbm_peak, bf16_peak, peak_src = peaks()
     K = args.steps
     chunks = tot["batches"] // K
+    per = chunks * K
+    qpl = m / chunks
     d = w.d
     bf16 = args.precision == "bf16"
     row_bytes = 2 * (-(-d // 8) * 8) if bf16 else 4 * d
     kprime = max(k + 16, args.rerank_k if bf16 else 0)
-    # probe ids, bucket entries, candidate rows, query rows, the exactly
-    # re-scored shortlist (FP32 rows) and the results
-    gather_bytes = (8 * tot["probes"] + 4 * tot["entries"] + row_bytes * tot["unique"]
-                    + (12 * k + 4 * d + 4 * d * kprime) * m * K)
-    gs_ms = phase["ms_gather_score"] / (chunks * K)
-    gs_gbs = gather_bytes / (chunks * K) / (gs_ms / 1e3) / 1e9
-    # projection: BF16 tensor-core products over the K dimension padded to
-    # 64; the FP32 path runs 6 of them (exact three-piece split), BF16 one
+    probes_pl, entries_pl, unique_pl = (tot["probes"] / per, tot["entries"] / per,
+                                        tot["unique"] / per)
+    # algorithmic bytes per launch: offset pairs of the probed buckets and the
+    # kept ids scanned, written candidates (dedup); candidate rows, their ids,
+    # the scores and the query rows (score); scores and ids read, the exactly
+    # re-scored FP32 rows and the results (top-k)
+    dedup_b = 8 * probes_pl + 4 * entries_pl + 4 * unique_pl
+    score_b = (row_bytes + 8) * unique_pl + 4 * d * qpl
+    topk_b = 8 * unique_pl + 4 * d * kprime * qpl + 12 * k * qpl
+    # projection: BF16 tensor-core products over K padded to 64; the FP32
+    # contraction runs 6 of them (exact three-piece split)
     kpad = -(-d // 64) * 64
-    products = 1 if bf16 else 6
-    proj_flops = 2.0 * m * kpad * 2 * w.L * w.D * products
-    pj_ms = phase["ms_project"] / (chunks * K)
-    pj_tf = proj_flops / chunks / (pj_ms / 1e3) / 1e12
-    pj_alg = 2.0 * m * d * 2 * w.L * w.D / chunks / (pj_ms / 1e3) / 1e12
-    phases = {
-        "project": {"ms_per_launch": pj_ms, "launches_per_step": chunks, "bound": "tensor",
-                    "achieved": pj_tf, "peak": bf16_peak, "unit": "TFLOP/s",
-                    "frac": pj_tf / bf16_peak, "bf16_products": products,
-                    "fp32_equivalent_tflops": pj_alg},
-        "probe": {"ms_per_launch": phase["ms_probe"] / (chunks * K), "launches_per_step": chunks},
-        "probe_exact": {"ms_per_launch": phase["ms_probe_exact"] / (chunks * K),
-                        "launches_per_step": chunks},
-        "gather_score": {"ms_per_launch": gs_ms, "launches_per_step": chunks, "bound": "hbm",
-                         "ms_dedup": phase["ms_dedup"] / (chunks * K),
-                         "ms_score": phase["ms_score"] / (chunks * K),
-                         "ms_topk": phase["ms_topk"] / (chunks * K),
-                         "achieved": gs_gbs, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": gs_gbs / hbm_peak,
-                         "algorithmic_bytes_per_launch": gather_bytes / (chunks * K)},
-    }
-    dom = max(("project", "probe", "probe_exact", "gather_score"),
-              key=lambda p: phases[p]["ms_per_launch"])
-    if dom == "gather_score":
-        roof = {"kernel": "gather_score_kernel", "bound": "hbm", "achieved": gs_gbs,
-                "peak": hbm_peak, "unit": "GB/s", "frac": gs_gbs / hbm_peak,
+    products = 6
+    proj_flops = 2.0 * qpl * kpad * 2 * w.L * w.D * products
+    ms_of = {key: phase[key] / per for key in phase}
+
+    def hbm(name, src, ms, nbytes, note):
+        gbs = nbytes / (ms / 1e3) / 1e9
+        return {"kernel": name, "ms_per_launch": ms, "launches_per_step": chunks, "bound": "hbm",
+                "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "algorithmic_bytes_per_launch": nbytes, "note": note,
                 "peak_source": peak_src + " (hbm_gbs, STREAM-style copy)",
-                "traffic": committed_traffic("gather_score_kernel", w.name, "search_kernels.cu")}
-    elif dom == "project":
-        roof = {"kernel": "tc_proj_kernel", "bound": "tensor", "achieved": pj_tf,
-                "peak": bf16_peak, "unit": "TFLOP/s", "frac": pj_tf / bf16_peak,
-                "peak_source": peak_src + " (bf16_tflops_sustained, cuBLAS loop)",
-                "traffic": committed_traffic("tc_proj_kernel", w.name, "gemm_tc.cu")}
-    else:
-        roof = {"kernel": "probe_kernel" if dom == "probe" else "probe_recheck_kernel",
-                "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": None}
+                "traffic": committed_traffic(name, w.name, src)}
+
+    pj_tf = proj_flops / (ms_of["ms_project"] / 1e3) / 1e12
+    kernels = {
+        "project": {"kernel": "tc_proj_kernel", "ms_per_launch": ms_of["ms_project"],
+                    "launches_per_step": chunks, "bound": "tensor", "achieved": pj_tf,
+                    "peak": bf16_peak, "unit": "TFLOP/s", "frac": pj_tf / bf16_peak,
+                    "bf16_products_per_fp32_product": products,
+                    "fp32_equivalent_tflops": pj_tf / products * d / kpad,
+                    "peak_source": peak_src + " (bf16_tflops, cuBLAS burst)",
+                    "traffic": committed_traffic("tc_proj_kernel", w.name, "gemm_tc.cu")},
+        "probe": {"kernel": "probe_small_kernel", "ms_per_launch": ms_of["ms_probe"],
+                  "launches_per_step": chunks, "bound": "alu"},
+        "probe_exact": {"kernel": "probe_window_kernel + probe_recheck_kernel",
+                        "ms_per_launch": ms_of["ms_probe_exact"], "launches_per_step": chunks,
+                        "bound": "alu"},
+        "dedup": hbm("dedup_hash_kernel", "search_kernels.cu", ms_of["ms_dedup"], dedup_b,
+                     "count_entries + scan + dedup_hash + dedup (bitmap) kernels; "
+                     "latency-bound bucket walk"),
+        "score": hbm("score_bf16_kernel" if bf16 else "score_kernel", "search_kernels.cu",
+                     ms_of["ms_score"], score_b, "candidate rows streamed once"),
+        "topk": hbm("topk_kernel", "search_kernels.cu", ms_of["ms_topk"], topk_b,
+                    "selection, exact re-scoring of the shortlist"),
+    }
+    gs_ms = ms_of["ms_gather_score"]
+    gs_gbs = (dedup_b + score_b + topk_b) / (gs_ms / 1e3) / 1e9
+    kernels["gather_score"] = {"kernel": "dedup + score + topk", "ms_per_launch": gs_ms,
+                               "bound": "hbm", "achieved": gs_gbs, "peak": hbm_peak,
+                               "unit": "GB/s", "frac": gs_gbs / hbm_peak,
+                               "algorithmic_bytes_per_launch": dedup_b + score_b + topk_b}
+    # the roofline line is the single kernel with the largest device time
+    dom = max(("project", "dedup", "score", "topk"), key=lambda p: kernels[p]["ms_per_launch"])
+    roof = {kk: kernels[dom][kk] for kk in ("kernel", "bound", "achieved", "peak", "unit", "frac",
+                                            "traffic", "peak_source")}
+    phases = kernels
 
     # end to end: host (pinned) queries in, host results out, through the C ABI
     e2e = None
