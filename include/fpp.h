@@ -60,13 +60,14 @@ typedef enum fpp_precision {
   FPP_FP32 = 0,      /* FP32 storage and projections, FP64-exact decisions */
   FPP_BF16 = 1       /* Candidate scores are read from a BF16 copy of X
                         (FP32 accumulation); the best max(rerank_k, k + 16)
-                        of them are re-scored exactly on the FP32 rows, and
-                        a top-k boundary closer than nine estimated standard
-                        deviations of the BF16 rounding error
-                        (score_error_factor) is re-decided exactly.  Hashing
-                        and probing are as for FPP_FP32.  The index holds X in
-                        both precisions (6 bytes per element).  Graded by
-                        recall and score error. */
+                        of them form the shortlist, and every shortlisted
+                        candidate within twice the BF16 error window
+                        (nine estimated standard deviations of the rounding
+                        error, score_error_factor) of the k-th is re-scored
+                        exactly on the FP32 rows before the final top-k.
+                        Hashing and probing are as for FPP_FP32.  The index
+                        holds X in both precisions (6 bytes per element).
+                        Graded by recall and score error. */
 } fpp_precision;
 
 /* Index parameters.  Initialise with fpp_default_params(). */
@@ -80,7 +81,7 @@ typedef struct fpp_params {
   const float* R;      /* optional explicit random vectors [L][2][D][d],
                           host or device; NULL = generate from seed. Copied. */
   int32_t precision;   /* fpp_precision                                      */
-  int32_t rerank_k;    /* FPP_BF16: shortlist re-ranked in FP32 (default 100)*/
+  int32_t rerank_k;    /* FPP_BF16: shortlist length (default 100), 0..256  */
   void* stream;        /* cudaStream_t for the build, or NULL (legacy)       */
 } fpp_params;
 
@@ -318,6 +319,19 @@ fpp_status fpp_server_get_stats(fpp_server* s, fpp_server_stats* out);
 /* Stops the workers after their current batches and frees the server;
  * requests still queued are dropped.  NULL-safe. */
 void fpp_server_destroy(fpp_server* s);
+
+/* Table-sharded search (one index per GPU over a slice of the tables, built
+ * from the same seed, searched with fpp_search_ex's table range): merges the
+ * parts' top-k lists of every query into the global top-k.  ids, scores:
+ * host memory [parts][m][k] (rows padded with -1 / -inf); out_ids,
+ * out_scores: host memory [m][k].  Entries are ordered by (score desc, id
+ * asc); an id in several parts is kept once.  The exact top-k over the union
+ * of the tables' candidates is contained in the union of the parts' top-k
+ * lists, so this equals the unsharded search.  Host code only (parts x k
+ * entries per query); no device needed.  Errors: FPP_EINVAL for NULL
+ * pointers, parts < 1, m < 0, k < 1. */
+fpp_status fpp_merge_topk(const int64_t* ids, const float* scores, int32_t parts, int64_t m,
+                          int32_t k, int64_t* out_ids, float* out_scores);
 
 /* Number of kernels this process has launched through libfpp. */
 uint64_t fpp_launch_count(void);

@@ -123,6 +123,7 @@ def load(path: str | None = None):
         "fpp_projection_error_bound": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
         "fpp_bruteforce_static": (ctypes.c_int, [f32p, i64, i32, f32p, i64, i32, vp, vp, vp]),
         "fpp_launch_count": (u64, []),
+        "fpp_merge_topk": (ctypes.c_int, [vp, vp, i32, i64, i32, vp, vp]),
         "fpp_default_server_cfg": (None, [ctypes.POINTER(fpp_server_cfg)]),
         "fpp_server_create": (ctypes.c_int, [vp, ctypes.POINTER(fpp_server_cfg),
                                              ctypes.POINTER(ctypes.c_void_p)]),
@@ -383,6 +384,19 @@ class Index:
             self.close()
         except Exception:
             pass
+
+
+def fpp_merge_topk(ids, scores):
+    """Merges per-part top-k lists ids/scores [parts][m][k] (host arrays) into
+    the global top-k [m][k] (score desc, id asc, each id once)."""
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    scores = np.ascontiguousarray(scores, dtype=np.float32)
+    parts, m, k = ids.shape
+    oi = np.empty((m, k), dtype=np.int64)
+    osc = np.empty((m, k), dtype=np.float32)
+    _check(load().fpp_merge_topk(ids.ctypes.data, scores.ctypes.data, parts, m, k,
+                                 oi.ctypes.data, osc.ctypes.data))
+    return oi, osc
 
 
 class Server:

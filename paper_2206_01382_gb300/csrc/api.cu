@@ -1330,6 +1330,43 @@ fpp_status fpp_bruteforce(const float* X, int64_t n, int32_t d, const float* Q, 
 }
 
 
+fpp_status fpp_merge_topk(const int64_t* ids, const float* scores, int32_t parts, int64_t m,
+                          int32_t k, int64_t* out_ids, float* out_scores) {
+  g_err.clear();
+  if (!ids || !scores || !out_ids || !out_scores || parts < 1 || m < 0 || k < 1) {
+    set_error("fpp_merge_topk: bad arguments");
+    return FPP_EINVAL;
+  }
+  std::vector<std::pair<float, int64_t>> e;
+  e.reserve((size_t)parts * k);
+  for (int64_t q = 0; q < m; ++q) {
+    e.clear();
+    for (int p = 0; p < parts; ++p) {
+      const size_t row = ((size_t)p * m + q) * k;
+      for (int j = 0; j < k; ++j)
+        if (ids[row + j] >= 0) e.emplace_back(scores[row + j], ids[row + j]);
+    }
+    std::sort(e.begin(), e.end(), [](const std::pair<float, int64_t>& x,
+                                     const std::pair<float, int64_t>& y) {
+      return x.first > y.first || (x.first == y.first && x.second < y.second);
+    });
+    int n = 0;
+    for (size_t i = 0; i < e.size() && n < k; ++i) {
+      bool dup = false;
+      for (int j = 0; j < n && !dup; ++j) dup = out_ids[q * k + j] == e[i].second;
+      if (dup) continue;
+      out_ids[q * k + n] = e[i].second;
+      out_scores[q * k + n] = e[i].first;
+      ++n;
+    }
+    for (; n < k; ++n) {
+      out_ids[q * k + n] = -1;
+      out_scores[q * k + n] = -INFINITY;
+    }
+  }
+  return FPP_OK;
+}
+
 void fpp_default_server_cfg(fpp_server_cfg* c) {
   if (!c) return;
   std::memset(c, 0, sizeof(*c));

@@ -564,9 +564,9 @@ __global__ void query_norms_kernel(const float* __restrict__ Q, int64_t m, int64
 //                 id asc).
 
 constexpr int DW = 8;                           // warps per bitmap-dedup CTA
-constexpr int HW = 4;                           // warps per hash-dedup CTA
 constexpr int HS = 4096;                        // hash slots per warp (power of two)
 constexpr int HMAX = HS / 2;                    // entries a query may have for the hash path
+constexpr int HU = 8;                           // entry loads in flight per lane
 constexpr int PCHUNK = 128;                     // probed buckets resolved per pass
 constexpr int PPT = PCHUNK / 32;                // buckets per lane per pass
 constexpr int EPT = 8;                          // entries per lane per round
@@ -742,75 +742,147 @@ dedup_kernel(DedupArgs a) {
   }
 }
 
-// De-duplication of the queries with at most HMAX bucket entries: each warp
-// owns an open-addressing hash set of HS ids in shared memory (linear
-// probing, insertion by compare-and-swap, so exactly one lane sees an id as
-// new).  The table is at most half full, and it is reset after each query.
-// Larger queries are left to the bitmap kernel.
+// De-duplication of the queries with at most HMAX bucket entries, one CTA
+// (HT threads) per query: an open-addressing hash set of HS ids in shared
+// memory (linear probing, insertion by compare-and-swap, so exactly one
+// thread sees an id as new), at most half full and reset after each query.
+// The probed buckets are resolved HT at a time; each thread then walks a
+// contiguous run of the entries, so the bucket of its next entry is found by
+// stepping instead of searching.  Larger queries are left to the bitmap
+// kernel.
 constexpr uint32_t HEMPTY = 0xFFFFFFFFu;
+constexpr int HT = 256;                         // threads per hash-dedup CTA
 
-__global__ void __launch_bounds__(HW * 32)
+__global__ void __launch_bounds__(HT, 4)
 dedup_hash_kernel(DedupArgs a) {
-  extern __shared__ __align__(16) uint32_t s_tab[];
-  __shared__ uint64_t s_pbase[HW][PCHUNK];
-  __shared__ uint32_t s_pstart[HW][PCHUNK + 1];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t* tab = s_tab + wid * HS;
-  for (int i = lane; i < HS / 4; i += 32)
+  __shared__ __align__(16) uint32_t tab[HS];
+  __shared__ uint64_t pbase[HT];
+  __shared__ uint32_t pstart[HT + 1];
+  __shared__ uint32_t wsum[HT / 32];
+  __shared__ uint32_t s_n, s_base;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int i = tid; i < HS / 4; i += HT)
     reinterpret_cast<uint4*>(tab)[i] = make_uint4(HEMPTY, HEMPTY, HEMPTY, HEMPTY);
-  __syncwarp();
+  if (tid == 0) s_n = 0;
+  __syncthreads();
   const int64_t NB = 4ll * a.D * a.D;
   unsigned long long ent = 0, uni = 0, prb = 0;
-  const int64_t nwarps = (int64_t)gridDim.x * HW;
-  for (int64_t q = (int64_t)blockIdx.x * HW + wid; q < a.mq; q += nwarps) {
+  for (int64_t q = blockIdx.x; q < a.mq; q += gridDim.x) {
     const uint64_t E = a.eoff[q + 1] - a.eoff[q];
-    if (E > (uint64_t)HMAX) continue;
+    if (E > (uint64_t)HMAX) continue;   // uniform over the CTA
     const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
-    WarpWalk w{&a, q, Pq, a.nt * Pq, NB, s_pbase[wid], s_pstart[wid]};
+    const int nprobe = a.nt * Pq;
     uint32_t* out = a.cand + a.eoff[q];
-    struct Insert {
-      uint32_t* tab; uint32_t* out; uint32_t n;
-      __device__ void operator()(const uint32_t (&id)[EPT], const bool (&has)[EPT]) {
-        const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+    for (int pc0 = 0; pc0 < nprobe; pc0 += HT) {
+      const int nc = min(HT, nprobe - pc0);
+      uint32_t c = 0;
+      if (tid < nc) {
+        const int pi = pc0 + tid;
+        const int tl = pi / Pq, p = pi - tl * Pq;
+        const int t = a.tb + tl;
+        const uint32_t bk = a.probes[(q * a.nt + tl) * (int64_t)a.pstride + p];
+        const uint32_t* off = a.offsets + (int64_t)t * (NB + 1);
+        const uint32_t o0 = off[bk];
+        c = off[bk + 1] - o0;
+        pbase[tid] = a.table_base[t] + o0;
+      }
+      // exclusive prefix sum of the bucket sizes over the CTA
+      uint32_t inc = c;
 #pragma unroll
-        for (int r = 0; r < EPT; ++r) {
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t2 = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += t2;
+      }
+      if (lane == 31) wsum[wid] = inc;
+      __syncthreads();
+      uint32_t woff = 0, total = 0;
+#pragma unroll
+      for (int w = 0; w < HT / 32; ++w) {
+        const uint32_t v = wsum[w];
+        woff += w < wid ? v : 0u;
+        total += v;
+      }
+      if (tid < nc) pstart[tid] = woff + inc - c;
+      if (tid == 0) pstart[nc] = total;   // nc <= HT; entries past nc are never read
+      __syncthreads();
+      const uint32_t per = (total + HT - 1) / HT;
+      uint32_t e = tid * per;
+      const uint32_t eend = min(e + per, total);
+      int bk = 0;
+      if (e < eend) {
+        int lo = 0, hi = nc;   // last bucket whose start is <= e
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (pstart[mid] <= e) lo = mid; else hi = mid;
+        }
+        bk = lo;
+      }
+      uint32_t bstart = pstart[bk], bnext = pstart[bk + 1];
+      uint64_t bbase = pbase[bk];
+      for (uint32_t it = 0; it < per; it += HU) {
+        uint32_t id[HU];
+        bool has[HU];
+#pragma unroll
+        for (int u = 0; u < HU; ++u) {
+          has[u] = e < eend;
+          id[u] = 0u;
+          if (has[u]) {
+            while (e >= bnext) {   // step over finished (or empty) buckets
+              ++bk;
+              bstart = bnext;
+              bnext = pstart[bk + 1];
+              bbase = pbase[bk];
+            }
+            id[u] = __ldg(a.ids + bbase + (e - bstart));
+            ++e;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < HU; ++u) {
           bool fresh = false;
-          if (has[r]) {
-            uint32_t h = (id[r] * 0x9E3779B1u) >> (32 - 12);   // log2(HS) = 12
+          if (has[u]) {
+            uint32_t h = (id[u] * 0x9E3779B1u) >> (32 - 12);   // log2(HS) = 12
             while (true) {
-              const uint32_t old = atomicCAS(tab + h, HEMPTY, id[r]);
+              const uint32_t old = atomicCAS(tab + h, HEMPTY, id[u]);
               if (old == HEMPTY) { fresh = true; break; }
-              if (old == id[r]) break;
+              if (old == id[u]) break;
               h = (h + 1) & (HS - 1);
             }
           }
           const unsigned m = __ballot_sync(FULL, fresh);
-          if (fresh) out[n + __popc(m & lt)] = id[r];
-          n += __popc(m);
+          if (m) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(&s_n, (uint32_t)__popc(m));
+            base = __shfl_sync(FULL, base, 0);
+            if (fresh) out[base + __popc(m & ((1u << lane) - 1u))] = id[u];
+          }
         }
       }
-    } ins{tab, out, 0u};
-    warp_walk(w, ins);
-    const uint32_t U = ins.n;
-    if (lane == 0) {
+      __syncthreads();   // pbase / pstart are rewritten by the next chunk
+    }
+    const uint32_t U = s_n;
+    const uint32_t nit = (U + ITEM - 1) / ITEM;
+    if (tid == 0) {
       ent += E;
       uni += U;
-      prb += (unsigned long long)w.nprobe;
+      prb += (unsigned long long)nprobe;
       a.ucount[q] = U;
+      s_base = nit ? atomicAdd(a.nitems, nit) : 0u;
     }
-    write_items(a, q, U);
-    __syncwarp();
-    for (int i = lane; i < HS / 4; i += 32)
+    __syncthreads();
+    for (uint32_t k = tid; k < nit; k += HT) {
+      ScoreItem itm;
+      itm.q = (uint32_t)q;
+      itm.len = min((uint32_t)ITEM, U - k * ITEM);
+      itm.start = a.eoff[q] + (uint64_t)k * ITEM;
+      a.items[s_base + k] = itm;
+    }
+    for (int i = tid; i < HS / 4; i += HT)
       reinterpret_cast<uint4*>(tab)[i] = make_uint4(HEMPTY, HEMPTY, HEMPTY, HEMPTY);
-    __syncwarp();
+    if (tid == 0) s_n = 0;
+    __syncthreads();
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    ent += __shfl_xor_sync(FULL, ent, o);
-    uni += __shfl_xor_sync(FULL, uni, o);
-    prb += __shfl_xor_sync(FULL, prb, o);
-  }
-  if (lane == 0 && a.stats) {
+  if (tid == 0 && a.stats) {
     atomicAdd(a.stats + 0, ent);
     atomicAdd(a.stats + 1, uni);
     atomicAdd(a.stats + 3, prb);
@@ -972,14 +1044,15 @@ score_bf16_kernel(ScoreArgs a) {
   }
 }
 
-// Best k candidates of each query by (score desc, id asc).  The FP32 scores
-// pre-select the best K' = k + 16; those are re-scored with the compensated
-// dot product and sorted.  The selection is exact unless the K'-th FP32
-// score lies within the FP32 error bound of the k-th re-scored one; then
-// every candidate whose stored FP32 score could still reach the top-k is
-// re-scored (the slow path, rare).
+// Best k candidates of each query by (score desc, id asc).  The first-pass
+// scores pre-select the best K' = max(k + 16, kprime); the entries among them
+// within twice the score error of the k-th are re-scored with the
+// compensated dot product and sorted.  When that window reaches past the
+// K'-th entry, every candidate in the window is re-scored (the slow path,
+// rare).
 constexpr int TK_SLOW = 2048;
 constexpr int SEL_REGS = 16;   // candidates per lane of the register selection
+constexpr int SEL_SLACK = 16;  // extra keys the selection threshold may keep
 
 // Best kp of U <= 32 * SEL_REGS scored candidates by (score desc, id asc),
 // sorted into buf[0..): the score keys sit in registers; a binary search over
@@ -997,14 +1070,27 @@ __device__ __forceinline__ int select_small(const float* sc, const uint32_t* cid
   }
   uint32_t t = 1u;
   if (U > (uint32_t)kp) {
-    uint32_t lo = 1u, hi = 0xFFFFFFFFu;   // count(key >= lo) >= kp holds throughout
+    // count(key >= lo) >= kp holds throughout; stop early once a threshold
+    // keeps at most kp + SEL_SLACK keys (the sort below orders them anyway)
+    uint32_t kmin = 0xFFFFFFFFu, kmax = 0u;
+#pragma unroll
+    for (int j = 0; j < SEL_REGS; ++j) {
+      if (key[j]) kmin = min(kmin, key[j]);
+      kmax = max(kmax, key[j]);
+    }
+    uint32_t lo = __reduce_min_sync(FULL, kmin), hi = __reduce_max_sync(FULL, kmax);
     while (lo < hi) {
       const uint32_t mid = lo + (hi - lo + 1u) / 2u;
       unsigned c = 0;
 #pragma unroll
       for (int j = 0; j < SEL_REGS; ++j) c += key[j] >= mid ? 1u : 0u;
       c = __reduce_add_sync(FULL, c);
-      if (c >= (unsigned)kp) lo = mid; else hi = mid - 1u;
+      if (c >= (unsigned)kp) {
+        lo = mid;
+        if (c <= (unsigned)(kp + SEL_SLACK)) break;
+      } else {
+        hi = mid - 1u;
+      }
     }
     t = lo;
   }
@@ -1060,34 +1146,57 @@ topk_kernel(TopkArgs a) {
     }
     nk = wt.finish();
   }
-  // exact re-scoring of the pre-selected entries, one row per lane
-  for (int e = lane; e < ((nk + 31) & ~31); e += 32) {
-    if (e < nk) {
-      const uint32_t id = key_id(buf[e]);
-      resc[e] = SD{thread_dot2_f4(qv, a.X + (int64_t)id * a.ldx, nf4), id, 0};
-    }
+  // Only entries whose first-pass score is within twice the score error of
+  // the k-th first-pass score can be in the exact top-k (every entry below
+  // that window is exactly below the k entries above it); the pre-selection
+  // is sorted, so those entries are a prefix S of it.  If the window reaches
+  // the end of the pre-selection while more candidates exist, the slow path
+  // re-scores every candidate in the window.
+  const double qn = (double)a.qnorm[q];
+  const double eps_s = a.gamma * qn * (double)a.xmax;
+  const double du = 5.9604644775390625e-08 * (a.d + 8);
+  const double delta = 4.0 * du * du * qn * (double)a.xmax + 1e-300;
+  const int kk = min(kq, nk);
+  const double thr64 = nk > 0 ? (double)key_score(buf[kk - 1]) - 2.0 * eps_s - 2.0 * delta : 0.0;
+  int ns = 0;   // |S|
+  for (int e0 = 0; e0 < nk; e0 += 32) {
+    const int e = e0 + lane;
+    ns += __popc(__ballot_sync(FULL, e < nk && (double)key_score(buf[e]) >= thr64));
   }
-  for (int e = nk + lane; e < a.rcap; e += 32) resc[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
-  __syncwarp();
-  warp_sort_sd(resc, a.rcap);
-  bool slow = false;
-  double thr64 = 0.0;
-  if (U > (uint32_t)nk) {
-    const double qn = (double)a.qnorm[q];
-    const double eps_s = a.gamma * qn * (double)a.xmax;
-    const double du = 5.9604644775390625e-08 * (a.d + 8);
-    const double delta = 4.0 * du * du * qn * (double)a.xmax + 1e-300;
-    const double sK = (double)key_score(buf[nk - 1]);
-    const double need = resc[kq - 1].s;
-    if (!(sK + eps_s + 2.0 * delta < need)) {
-      slow = true;
-      thr64 = need - eps_s - 2.0 * delta;
-    }
-  }
+  const bool slow = U > (uint32_t)nk && ns == nk;
   const int64_t orow = q * a.kmax;
   if (!slow) {
+    // exact re-scoring of S: G lanes per row (a power of two, 32 / G rows per round)
+    const int G = ns >= 32 ? 1 : 32 / pow2_ceil(ns > 1 ? ns : 1);
+    const int rows_per_round = 32 / G;
+    const int sub = lane % G;
+    for (int r0 = 0; r0 < ns; r0 += rows_per_round) {
+      const int r = r0 + lane / G;
+      const bool ok = r < ns;
+      const uint32_t id = ok ? key_id(buf[r]) : key_id(buf[0]);
+      const float4* x4 = reinterpret_cast<const float4*>(a.X + (int64_t)id * a.ldx);
+      const float4* q4 = reinterpret_cast<const float4*>(qv);
+      float p = 0.f, sacc = 0.f;
+      for (int c = sub; c < nf4; c += G) {
+        const float4 x = __ldg(x4 + c), y = __ldg(q4 + c);
+        dot2_step(x.x, y.x, p, sacc);
+        dot2_step(x.y, y.y, p, sacc);
+        dot2_step(x.z, y.z, p, sacc);
+        dot2_step(x.w, y.w, p, sacc);
+      }
+      FF v{p, sacc};
+      for (int o = G / 2; o > 0; o >>= 1) {
+        FF w{__shfl_xor_sync(FULL, v.hi, o), __shfl_xor_sync(FULL, v.lo, o)};
+        v = ff_add(v, w);
+      }
+      if (ok && sub == 0) resc[r] = SD{ff_value(v), id, 0};
+    }
+    const int np2 = pow2_ceil(ns > 1 ? ns : 1);
+    for (int e = ns + lane; e < np2; e += 32) resc[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+    __syncwarp();
+    warp_sort_sd(resc, np2);
     for (int e = lane; e < a.kmax; e += 32) {
-      const bool ok = e < kq && e < nk;
+      const bool ok = e < kq && e < ns;
       a.out_ids[orow + e] = ok ? (int64_t)resc[e].id : -1;
       a.out_scores[orow + e] = ok ? (float)resc[e].s : -INFINITY;
     }
@@ -1096,32 +1205,32 @@ topk_kernel(TopkArgs a) {
   // slow path: every candidate whose FP32 score may still reach the top-k
   if (lane == 0 && a.stats) atomicAdd(a.stats + 2, 1ull);
   SD* list = reinterpret_cast<SD*>(a.slow) + (int64_t)(blockIdx.x * 8 + wid) * TK_SLOW;
-  unsigned ns = 0;
+  unsigned nsl = 0;
   for (uint32_t i0 = 0; i0 < U; i0 += 32) {
     const uint32_t i = i0 + lane;
     const bool take = i < U && (double)sc[i] >= thr64;
     const unsigned m = __ballot_sync(FULL, take);
     if (take) {
-      const unsigned slot = ns + __popc(m & ((1u << lane) - 1u));
+      const unsigned slot = nsl + __popc(m & ((1u << lane) - 1u));
       if (slot < (unsigned)TK_SLOW) list[slot].id = cid[i];
     }
-    ns += __popc(m);
+    nsl += __popc(m);
   }
-  if (ns > (unsigned)TK_SLOW) {
+  if (nsl > (unsigned)TK_SLOW) {
     // exact mode cannot guarantee the result; the BF16 path keeps the best
     // effort (the shortlist order is approximate there anyway)
     if (lane == 0 && a.err && !a.approx) atomicExch(a.err, 1);
-    ns = TK_SLOW;
+    nsl = TK_SLOW;
   }
   __syncwarp();
-  for (unsigned e = lane; e < ns; e += 32)
+  for (unsigned e = lane; e < nsl; e += 32)
     list[e].s = thread_dot2_f4(qv, a.X + (int64_t)list[e].id * a.ldx, nf4);
-  const int np2 = pow2_ceil(ns > 1 ? (int)ns : 1);
-  for (int e = (int)ns + lane; e < np2; e += 32) list[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+  const int np2 = pow2_ceil(nsl > 1 ? (int)nsl : 1);
+  for (int e = (int)nsl + lane; e < np2; e += 32) list[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
   __syncwarp();
   warp_sort_sd(list, np2);
   for (int e = lane; e < a.kmax; e += 32) {
-    const bool ok = e < kq && e < (int)ns;
+    const bool ok = e < kq && e < (int)nsl;
     a.out_ids[orow + e] = ok ? (int64_t)list[e].id : -1;
     a.out_scores[orow + e] = ok ? (float)list[e].s : -INFINITY;
   }
@@ -1387,21 +1496,17 @@ fpp_status launch_count_entries(const DedupArgs& a, cudaStream_t st) {
 
 fpp_status launch_dedup(const DedupArgs& a, int slots, cudaStream_t st) {
   if (a.mq <= 0) return FPP_OK;
-  // queries with at most HMAX entries: shared-memory hash sets
+  // queries with at most HMAX entries: shared-memory hash sets, one CTA each
   static std::atomic<int> hash_grid{0};
-  const size_t hsmem = (size_t)HW * HS * 4;
   if (!hash_grid.load(std::memory_order_relaxed)) {
-    FPP_CUDA(cudaFuncSetAttribute(dedup_hash_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)hsmem));
     int per_sm = 0, dev = 0, sms = 0;
-    FPP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dedup_hash_kernel, HW * 32,
-                                                           hsmem));
+    FPP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dedup_hash_kernel, HT, 0));
     FPP_CUDA(cudaGetDevice(&dev));
     FPP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     hash_grid.store(std::max(1, per_sm) * sms, std::memory_order_relaxed);
   }
-  const int hgrid = (int)std::min<int64_t>(ceil_div(a.mq, HW), hash_grid.load());
-  dedup_hash_kernel<<<hgrid, HW * 32, hsmem, st>>>(a);
+  const int hgrid = (int)std::min<int64_t>(a.mq, hash_grid.load());
+  dedup_hash_kernel<<<hgrid, HT, 0, st>>>(a);
   FPP_LAUNCHED();
   // the rest: one global bitmap of n bits per warp slot
   const int64_t ctas = ceil_div(a.mq, DW);

@@ -207,3 +207,23 @@ def test_plain1m_full_size_sampled(F):
         s64 = X64[gi[i][ok]] @ Q[i].astype(np.float64)
         assert np.allclose(gs[i][ok], s64, rtol=1e-6, atol=1e-7)
         assert (np.diff(gs[i][ok]) <= 0).all()
+
+
+def test_table_slices_merged_equal_full_search(F):
+    # the table-sharded plan on one GPU: every slice searched through
+    # fpp_search_ex's table range, merged by fpp_merge_topk
+    from paper_2206_01382_gb300 import sharded
+    X, Q = W.small_mixture(20000, 200, 48, 64, 0.25, 90)
+    ix = F.Index(X, 10, 16, 0.3, seed=21)
+    for P in (1, 3):
+        fi, fs = ix.search(Q, 10, P)
+        parts_i, parts_s = [], []
+        for r in range(3):
+            tb, te = sharded.table_range(r, 3, 10)
+            gi, gs, _ = F.fpp_search_ex(ix.handle, Q, k=10, probes=P, table_begin=tb,
+                                        table_end=te, want_stats=False)
+            parts_i.append(gi)
+            parts_s.append(gs)
+        mi, ms = F.fpp_merge_topk(np.stack(parts_i), np.stack(parts_s))
+        assert np.array_equal(mi, fi)
+        assert np.array_equal(ms, fs)
