@@ -143,13 +143,17 @@ def cpu_baseline(w, X, Q, P, k, n_sample=20000, max_q=100, budget_s=20.0):
     ix = O.build_index(X[:n_sample], w.L, w.D, w.alpha, seed=w.rot_seed)
     t0 = time.perf_counter()
     nq = 0
+    kk = np.broadcast_to(np.asarray(k), (len(Q),))
+    pp = np.broadcast_to(np.asarray(P), (len(Q),))
     while nq < max_q and time.perf_counter() - t0 < budget_s:
-        O.search(ix, Q[nq], k, P)
+        O.search(ix, Q[nq], int(kk[nq]), int(pp[nq]))
         nq += 1
     dt = time.perf_counter() - t0
     return {"value": nq / dt, "unit": "queries/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"FP64 numpy oracle: index over the first {n_sample} points "
-                      f"(L={w.L}, D={w.D}, alpha={w.alpha}), {nq} queries at {P} probes/table, k={k}"}
+                      f"(L={w.L}, D={w.D}, alpha={w.alpha}), {nq} queries at "
+                      f"{'per-query' if np.ndim(P) else P} probes/table, "
+                      f"k={'per-query' if np.ndim(k) else k}"}
 
 
 def run_reference(args, w):
@@ -351,17 +355,30 @@ def main():
     build_s = time.perf_counter() - tb
     info = ix.info()
 
-    # probe budget: smallest of the sweep with recall@10 >= 0.90 on a sample
-    k = w.k
-    P, recalls, mcal = calibrate_probes(F, ix, Xd, Qd, k,
-                                        [args.probes] if args.probes else list(w.probes))
     m = Q.shape[0]
+    per_query = w.name == "batch10m"
+    if per_query:
+        # uneven work: per-query k in {1, 10, 100} and probes in {2, 8, 32, 128}
+        kpq, ppq = W.per_query_draws(w, m)
+        k = int(kpq.max())
+        P = "per-query"
+        kpq_d = torch.from_numpy(kpq).to(dev)
+        ppq_d = torch.from_numpy(ppq).to(dev)
+        search_kw = dict(k=k, probes=1, k_per_query=kpq_d, probes_per_query=ppq_d, k_max=k)
+        recalls, mcal = {}, min(CALIB_QUERIES, m)
+    else:
+        # probe budget: smallest of the sweep with recall@10 >= 0.90 on a sample
+        k = w.k
+        P, recalls, mcal = calibrate_probes(F, ix, Xd, Qd, k,
+                                            [args.probes] if args.probes else list(w.probes))
+        kpq = ppq = None
+        search_kw = dict(k=k, probes=P)
     ids = torch.empty((m, k), dtype=torch.int64, device=dev)
     sc = torch.empty((m, k), dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
 
     for _ in range(args.warmup):
-        F.fpp_search_ex(ix.handle, Qd, k=k, probes=P, stream=stream, ids=ids, scores=sc)
+        F.fpp_search_ex(ix.handle, Qd, stream=stream, ids=ids, scores=sc, **search_kw)
     barrier()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
@@ -372,17 +389,24 @@ def main():
              "ms_dedup": 0.0, "ms_score": 0.0, "ms_topk": 0.0}
     tot = {"entries": 0, "unique": 0, "probes": 0, "probe_rechecks": 0, "topk_rechecks": 0,
            "batches": 0}
+    # timed steps: asynchronous on one stream, no host round trip per step
     evs[0].record(stream)
     for s in range(args.steps):
-        _, _, st = F.fpp_search_ex(ix.handle, Qd, k=k, probes=P, stream=stream, ids=ids, scores=sc)
+        F.fpp_search_ex(ix.handle, Qd, stream=stream, ids=ids, scores=sc, want_stats=False,
+                        **search_kw)
         evs[s + 1].record(stream)
+    barrier()
+    launches = F.fpp_launch_count() - launches0
+    clocks = sampler.stop()
+    # per-kernel breakdown: a few more steps with the library's phase events
+    # (these synchronise at the end of every call, so they are not timed)
+    PK = min(args.steps, 5)
+    for s in range(PK):
+        _, _, st = F.fpp_search_ex(ix.handle, Qd, stream=stream, ids=ids, scores=sc, **search_kw)
         for key in phase:
             phase[key] += st[key]
         for key in tot:
             tot[key] += st[key]
-    barrier()
-    launches = F.fpp_launch_count() - launches0
-    clocks = sampler.stop()
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     elapsed_ms = evs[0].elapsed_time(evs[-1])
     if dist is not None:
@@ -396,7 +420,7 @@ def main():
     # launching stream inside the library, summed over the timed steps;
     # "per launch" = one query batch)
     hbm_peak, bf16_peak, peak_src = peaks()
-    K = args.steps
+    K = PK
     chunks = tot["batches"] // K
     per = chunks * K
     qpl = m / chunks
@@ -468,11 +492,15 @@ def main():
         Qh = torch.from_numpy(Q).pin_memory()
         ih = torch.empty((m, k), dtype=torch.int64).pin_memory()
         sh = torch.empty((m, k), dtype=torch.float32).pin_memory()
-        F.fpp_search_ex(ix.handle, Qh, k=k, probes=P, ids=ih, scores=sh, want_stats=False)
+        host_kw = dict(search_kw)
+        if per_query:   # the per-query budgets come from the host too
+            host_kw.update(k_per_query=torch.from_numpy(kpq).pin_memory(),
+                           probes_per_query=torch.from_numpy(ppq).pin_memory())
+        F.fpp_search_ex(ix.handle, Qh, ids=ih, scores=sh, want_stats=False, **host_kw)
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            F.fpp_search_ex(ix.handle, Qh, k=k, probes=P, ids=ih, scores=sh, want_stats=False)
+            F.fpp_search_ex(ix.handle, Qh, ids=ih, scores=sh, want_stats=False, **host_kw)
         barrier()
         e2e_s = (time.perf_counter() - t0) / args.steps
         if dist is not None:
@@ -480,11 +508,32 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
         e2e = {"value": world * m / e2e_s, "unit": "queries/s",
-               "h2d_bytes_per_step": int(m * w.d * 4), "d2h_bytes_per_step": int(m * k * 12)}
+               "h2d_bytes_per_step": int(m * w.d * 4 + (8 * m if per_query else 0)),
+               "d2h_bytes_per_step": int(m * k * 12)}
+
+    # recall (per-query k) and score error of the returned results on the
+    # calibration sample: returned ids against the library's exact search,
+    # returned scores against FP64 inner products of the returned ids
+    gi = ids[:mcal].cpu().numpy()
+    gs = sc[:mcal].cpu().numpy().astype(np.float64)
+    ti, _ = F.fpp_bruteforce(Xd, Qd[:mcal], k)
+    truth = ti.cpu().numpy()
+    kq = kpq[:mcal] if per_query else np.full(mcal, k)
+    hit = sum(len(set(gi[i, :kq[i]].tolist()) & set(truth[i, :kq[i]].tolist())) / kq[i]
+              for i in range(mcal))
+    recall_k = hit / mcal
+    okm = gi >= 0
+    ex = np.zeros_like(gs)
+    for i in range(mcal):
+        sel = gi[i][okm[i]]
+        ex[i, okm[i]] = X[sel].astype(np.float64) @ Q[i].astype(np.float64)
+    max_score_err = float(np.abs(gs[okm] - ex[okm]).max()) if okm.any() else 0.0
+    if per_query:
+        recalls = {"per-query": recall_k}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, X, Q, P, k)
+        cpu = cpu_baseline(w, X, Q, ppq if per_query else P, kpq if per_query else k)
 
     if rank == 0:
         sm = sorted(step_ms)
@@ -499,6 +548,7 @@ def main():
                        "n": w.n, "d": w.d, "m": m, "L": w.L,
                        "D": w.D, "alpha": w.alpha, "k": k, "probes": P,
                        "recall_at_10": recalls[P], "recall_sweep": recalls,
+                       "recall_at_k_timed": recall_k, "max_abs_score_error": max_score_err,
                        "recall_sample": mcal, "l2": "inputs larger than L2 (X is "
                        f"{w.n * w.d * 4 / 2**20:.0f} MiB), no flush",
                        "build_s": build_s, "index_kept_ids": info["kept_total"],

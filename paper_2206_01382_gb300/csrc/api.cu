@@ -93,6 +93,7 @@ struct fpp_index {
   int64_t ldxb = 0;
   int rerank_k = 0;            // FPP_BF16: shortlist re-ranked on the FP32 rows
   double score_gamma = 0.0;    // candidate score error factor
+  uint64_t cand_budget_entries = 0;  // candidate slots a batch may provision without a read-back
   float* rmax = nullptr;       // [2L]
   float xmax = 0.f;
   uint32_t* offsets = nullptr; // [L][4D^2 + 1]
@@ -299,6 +300,14 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
   ix->L = p->L; ix->D = p->D; ix->iprobes = p->iprobes; ix->kappa = p->kappa;
   ix->alpha = p->alpha; ix->precision = p->precision;
   ix->Kp = tc_kpad(d);
+  {
+    // candidate buffers (8 bytes per slot) up to min(8 GiB, 1/16 of the
+    // device) are provisioned from the worst-case bound without a read-back
+    size_t fr = 0, tot = 0;
+    const uint64_t lim = cudaMemGetInfo(&fr, &tot) == cudaSuccess ? std::min<uint64_t>(8ull << 30, tot / 16)
+                                                                 : (1ull << 31);
+    ix->cand_budget_entries = lim / 8;
+  }
   // Projections use the exact three-piece split in both precisions: the
   // projection kernel is bound by its epilogue (the per-hash top lists), not
   // by the tensor cores, so one BF16 product is no faster there, while its
@@ -566,17 +575,21 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   FPP_TRY(launch_count_entries(da, st));
   FPP_TRY(exclusive_scan_u32(ws.ecount.as<uint32_t>(), mc, ws.eoff.as<uint64_t>(), 0,
                              KeepRule{1.0, 1, 0}, ws.scan.as<uint64_t>(), st));
-  // candidate slots: a bound from the largest kept bucket when it is small
-  // enough, otherwise the exact total (read back)
+  // candidate slots: the bound from the largest kept bucket when the
+  // workspace holds it or can be grown to it within the sync-free budget
+  // (no host round trip, so the batch can be captured in a graph);
+  // otherwise the exact total, read back
   const uint64_t bound = (uint64_t)mc * nt * pl.pmax * std::max<uint32_t>(ix->max_bucket_kept, 1);
   uint64_t need = bound;
-  if (bound > (1ull << 28)) {
+  bool exact = false;
+  if (bound > ws.cand_cap && bound > ix->cand_budget_entries) {
     FPP_CUDA(cudaMemcpyAsync(&need, ws.eoff.as<uint64_t>() + mc, 8, cudaMemcpyDeviceToHost, st));
     FPP_CUDA(cudaStreamSynchronize(st));
+    exact = true;
   }
   if (need > ws.cand_cap) {
     ws.cand.release(); ws.cscores.release(); ws.items.release();
-    const uint64_t cap = need + need / 4 + 1024;
+    const uint64_t cap = exact ? need + need / 4 + 1024 : need;
     FPP_TRY(ws.cand.ensure((size_t)cap * 4));
     FPP_TRY(ws.cscores.ensure((size_t)cap * 4));
     ws.cand_cap = cap;
