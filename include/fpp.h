@@ -146,7 +146,8 @@ void fpp_default_search_opts(fpp_search_opts* o);
  * largest filter score |x^T r_i1| + |x^T r_i2| (ties: lower point id), and
  * stores each table as CSR.  X is copied; the caller keeps ownership.
  * Errors: FPP_EINVAL for n < 1, d < 1, L < 1, D outside 1..1024,
- * alpha outside (0, 1], iprobes < 1, kappa < 0, n >= 2^32, precision not
+ * alpha outside (0, 1], iprobes outside 1..min(4D^2, 16), kappa < 0,
+ * n >= 2^32, precision not
  * an fpp_precision, rerank_k outside 0..256 with FPP_BF16.
  * *out is set only on success; release it with fpp_free. */
 fpp_status fpp_build(const float* X, int64_t n, int32_t d, const fpp_params* p,
@@ -188,9 +189,10 @@ uint64_t fpp_keep_count(uint64_t B, double alpha, int32_t iprobes, int32_t kappa
 fpp_status fpp_index_get_info(const fpp_index* ix, fpp_index_info* info);
 
 /* Introspection for parity tests (all outputs host or device memory):
- * fpp_debug_point_buckets: bucket id of every point in table t, [n] (only
- *   for iprobes = 1; the id is h1 * 2D + h2 with h = i for +r_i, i + D for
- *   -r_i, Eq. 1).
+ * fpp_debug_point_buckets: bucket ids of every point in table t before
+ *   filtering, [n][iprobes]: for iprobes = 1 the point's hash bucket
+ *   h1 * 2D + h2 (h = i for +r_i, i + D for -r_i, Eq. 1); for iprobes > 1
+ *   its iprobes best buckets in rank order (Algorithm 1).
  * fpp_debug_table: kept CSR of table t: offsets [4D^2 + 1] (relative to the
  *   table) and ids [kept_t], ids ordered by filter score desc, id asc inside
  *   a bucket.  Pass ids = NULL to get only offsets (kept_t = offsets[4D^2]).

@@ -281,8 +281,10 @@ def fpp_index_get_info(ix) -> dict:
 
 
 def fpp_debug_point_buckets(ix, t: int) -> np.ndarray:
-    n = fpp_index_get_info(ix)["n"]
-    out = np.empty(n, dtype=np.uint32)
+    """[n] bucket ids (iprobes = 1) or [n][iprobes] ranked bucket ids."""
+    info = fpp_index_get_info(ix)
+    n, ip = info["n"], info["iprobes"]
+    out = np.empty((n, ip) if ip > 1 else n, dtype=np.uint32)
     _check(load().fpp_debug_point_buckets(ix, t, out.ctypes.data))
     return out
 

@@ -166,6 +166,7 @@ int sig_bits(uint64_t v) {
 // Builds tables [t0, t0 + nt) and appends their kept ids.
 struct BuildScratch {
   DevBuf proj, xsplit, recA, recB, counts, bstart, kstart, hist, scanbuf, scanscratch, small, rechecks;
+  DevBuf norms, pout, rc1, rc2, pcount;   // multi-probe indexing: the points' probe sets
 };
 
 // Projection of rows [r0, r0 + rc) of a padded FP32 matrix onto the random
@@ -197,16 +198,28 @@ fpp_status build_tables(fpp_index* ix, int t0, int nt, BuildScratch& B, cudaStre
   const int64_t NB = nbuckets(D);
   const int64_t nsk = nt * NB;
   const int64_t ldp = round_up(2ll * nt * D, 4);
+  const int ip = ix->iprobes;
+  // list length of the projection epilogue: the best two keys (and the cut)
+  // per hash for iProbes = 1; the best iProbes + 1 for multi-probe indexing
+  // (0: store the projections)
+  const int EL = (256 % D != 0) ? 0 : (ip == 1 ? 2 : (ip + 1 <= D ? tc_list_len(ip + 1) : 0));
   int64_t rows = std::max<int64_t>(128, (1ll << 28) / ldp);
   rows = std::min<int64_t>(rows, n);
-  // projections (4 B per column) or the two best keys per hash (2 x 8 B per D columns)
-  FPP_TRY(B.proj.ensure(std::max((size_t)rows * ldp * 4, (size_t)rows * 2 * nt * 3 * 8)));
-  FPP_TRY(B.recA.ensure((size_t)nt * n * sizeof(Rec)));
-  FPP_TRY(B.recB.ensure((size_t)nt * n * sizeof(Rec)));
+  // projections (4 B per column) or the EL + 1 best keys per hash (8 B each)
+  FPP_TRY(B.proj.ensure(std::max((size_t)rows * ldp * 4, (size_t)rows * 2 * nt * (EL + 1) * 8)));
+  const int64_t nrec = (int64_t)nt * n * ip;
+  FPP_TRY(B.recA.ensure((size_t)nrec * sizeof(Rec)));
+  FPP_TRY(B.recB.ensure((size_t)nrec * sizeof(Rec)));
   FPP_TRY(B.counts.ensure((size_t)nsk * 4));
   FPP_TRY(B.bstart.ensure((size_t)(nsk + 1) * 8));
   FPP_TRY(B.kstart.ensure((size_t)(nsk + 1) * 8));
-  const int64_t nrec = (int64_t)nt * n;
+  if (ip > 1) {
+    FPP_TRY(B.norms.ensure((size_t)rows * 4));
+    FPP_TRY(B.pout.ensure((size_t)rows * nt * ip * 4));
+    FPP_TRY(B.rc1.ensure((size_t)rows * nt * 4));
+    FPP_TRY(B.rc2.ensure((size_t)rows * nt * 4));
+    FPP_TRY(B.pcount.ensure(16, true, st));
+  }
   const int64_t he = radix_hist_elems(nrec);
   FPP_TRY(B.hist.ensure((size_t)he * 4));
   FPP_TRY(B.scanbuf.ensure((size_t)(he + 1) * 8));
@@ -216,10 +229,37 @@ fpp_status build_tables(fpp_index* ix, int t0, int nt, BuildScratch& B, cudaStre
 
   for (int64_t r0 = 0; r0 < n; r0 += rows) {
     const int64_t rc = std::min<int64_t>(rows, n - r0);
-    const int EL = (256 % D == 0) ? 2 : 0;
     FPP_TRY(project_rows(ix, ix->X + r0 * ix->dpad, rc, B.xsplit, t0, nt, B.proj.as<float>(), ldp,
                          reinterpret_cast<int*>(B.rechecks.as<unsigned long long>() + 1), st,
                          EL ? B.proj.as<uint64_t>() : nullptr, EL));
+    if (ip > 1) {
+      // Algorithm 1 with iProbes > 1: each point goes into the iProbes
+      // buckets it ranks highest, by the same exact ranking as a query
+      const float* xr = ix->X + r0 * ix->dpad;
+      FPP_TRY(launch_query_norms(xr, rc, ix->dpad, ix->d, B.norms.as<float>(), st));
+      ProbeArgs pa{};
+      pa.P = EL ? nullptr : B.proj.as<float>(); pa.ldp = ldp; pa.mq = rc;
+      pa.lists = EL ? B.proj.as<uint64_t>() : nullptr; pa.EL = EL;
+      pa.trunc = EL ? tc_list_trunc(D) : 0.f;
+      pa.Q = xr; pa.ldq = ix->dpad; pa.qnorm = B.norms.as<float>();
+      pa.R = ix->R; pa.ldr = ix->dpad; pa.d = ix->d; pa.D = D; pa.tb = t0; pa.nt = nt;
+      pa.rmax = ix->rmax; pa.gamma = ix->gamma; pa.gammaf = (float)(ix->gamma * 1.0001);
+      pa.probes_pq = nullptr; pa.probes = ip;
+      pa.out = B.pout.as<uint32_t>();
+      pa.recheck = B.rc1.as<uint32_t>();
+      pa.recheck_count = B.pcount.as<unsigned>();
+      pa.recheck2 = B.rc2.as<uint32_t>();
+      pa.recheck2_count = B.pcount.as<unsigned>() + 1;
+      pa.rechecks = B.rechecks.as<unsigned long long>();
+      FPP_TRY(launch_probe(pa, st));
+      PairArgs pr{};
+      pr.probes = B.pout.as<uint32_t>(); pr.iprobes = ip; pr.rows = rc; pr.row0 = r0;
+      pr.t0 = t0; pr.nt = nt; pr.D = D; pr.X = ix->X; pr.ldx = ix->dpad;
+      pr.R = ix->R; pr.ldr = ix->dpad; pr.n = n;
+      pr.rec = B.recA.as<Rec>(); pr.counts = B.counts.as<uint32_t>();
+      FPP_TRY(launch_pair_records(pr, st));
+      continue;
+    }
     HashArgs h{};
     h.P = EL ? nullptr : B.proj.as<float>(); h.ldp = ldp; h.rows = rc; h.row0 = r0;
     h.lists = EL ? B.proj.as<uint64_t>() : nullptr; h.EL = EL;
@@ -275,7 +315,10 @@ fpp_status validate_params(int64_t n, int32_t d, const fpp_params* p) {
   if (p->L < 1 || p->L > 4096) { set_error("L must be in [1, 4096]"); return FPP_EINVAL; }
   if (p->D < 1 || p->D > 1024) { set_error("D must be in [1, 1024]"); return FPP_EINVAL; }
   if (!(p->alpha > 0.0 && p->alpha <= 1.0)) { set_error("alpha must be in (0, 1]"); return FPP_EINVAL; }
-  if (p->iprobes != 1) { set_error("iprobes > 1 is not supported yet"); return FPP_EINVAL; }
+  if (p->iprobes < 1 || p->iprobes > 16 || p->iprobes > 4ll * p->D * p->D) {
+    set_error("iprobes must be in [1, min(4D^2, 16)]");
+    return FPP_EINVAL;
+  }
   if (p->kappa < 0) { set_error("kappa must be >= 0"); return FPP_EINVAL; }
   if (p->precision != FPP_FP32 && p->precision != FPP_BF16) {
     set_error("precision must be FPP_FP32 or FPP_BF16");
@@ -385,8 +428,8 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
   ix->device_bytes += (uint64_t)L * (NB + 1) * 4;
   ix->h_table_base.assign(L, 0);
 
-  const int64_t rcap = 1ll << 28;
-  int nt_chunk = (int)std::max<int64_t>(1, rcap / n);
+  const int64_t rcap = 1ll << 28;   // records per table chunk
+  int nt_chunk = (int)std::max<int64_t>(1, rcap / (n * p->iprobes));
   nt_chunk = (int)std::min<int64_t>(nt_chunk, (int64_t)(0xFFFFFFFFll / NB));
   nt_chunk = std::max(1, std::min(nt_chunk, L));
   BuildScratch B;
@@ -394,7 +437,8 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
   uint64_t base = 0;
   auto cleanup = [&]() {
     for (DevBuf* b : {&B.proj, &B.xsplit, &B.recA, &B.recB, &B.counts, &B.bstart, &B.kstart, &B.hist,
-                      &B.scanbuf, &B.scanscratch, &B.small, &B.rechecks})
+                      &B.scanbuf, &B.scanscratch, &B.small, &B.rechecks, &B.norms, &B.pout, &B.rc1,
+                      &B.rc2, &B.pcount})
       b->release();
     for (auto& c : chunks) cudaFree(c.first);
   };
@@ -1115,23 +1159,46 @@ fpp_status fpp_debug_point_buckets(const fpp_index* cix, int32_t t, uint32_t* ou
   g_err.clear();
   if (!cix || !out) { set_error("NULL argument"); return FPP_EINVAL; }
   if (t < 0 || t >= cix->L) { set_error("table out of range"); return FPP_EINVAL; }
-  if (cix->iprobes != 1) { set_error("point buckets need iprobes = 1"); return FPP_EINVAL; }
   fpp_index* ix = const_cast<fpp_index*>(cix);
   std::lock_guard<std::mutex> lock(ix->mu);
   cudaStream_t st = 0;
+  const int ip = ix->iprobes;
   const int64_t ldp = round_up(2ll * ix->D, 4);
   const int64_t rows = std::min<int64_t>(ix->n, std::max<int64_t>(128, (1ll << 27) / ldp));
-  DevBuf proj, pb, split, err;
-  auto done = [&](fpp_status s) { proj.release(); pb.release(); split.release(); err.release(); return s; };
+  DevBuf proj, pb, split, err, norms, rc1, rc2;
+  auto done = [&](fpp_status s) {
+    for (DevBuf* b : {&proj, &pb, &split, &err, &norms, &rc1, &rc2}) b->release();
+    return s;
+  };
   fpp_status s;
-  if ((s = err.ensure(8, true, st)) != FPP_OK) return done(s);
+  if ((s = err.ensure(16, true, st)) != FPP_OK) return done(s);
   if ((s = proj.ensure((size_t)rows * ldp * 4)) != FPP_OK) return done(s);
-  if ((s = pb.ensure((size_t)ix->n * 4)) != FPP_OK) return done(s);
+  if ((s = pb.ensure((size_t)ix->n * ip * 4)) != FPP_OK) return done(s);
+  if (ip > 1 && ((s = norms.ensure((size_t)rows * 4)) != FPP_OK ||
+                 (s = rc1.ensure((size_t)rows * 4)) != FPP_OK ||
+                 (s = rc2.ensure((size_t)rows * 4)) != FPP_OK))
+    return done(s);
   for (int64_t r0 = 0; r0 < ix->n; r0 += rows) {
     const int64_t rc = std::min<int64_t>(rows, ix->n - r0);
     if ((s = project_rows(ix, ix->X + r0 * ix->dpad, rc, split, t, 1, proj.as<float>(), ldp,
                           err.as<int>(), st)) != FPP_OK)
       return done(s);
+    if (ip > 1) {
+      // the point's iProbes best buckets, ranked as for a query
+      const float* xr = ix->X + r0 * ix->dpad;
+      if ((s = launch_query_norms(xr, rc, ix->dpad, ix->d, norms.as<float>(), st)) != FPP_OK)
+        return done(s);
+      ProbeArgs pa{};
+      pa.P = proj.as<float>(); pa.ldp = ldp; pa.mq = rc;
+      pa.Q = xr; pa.ldq = ix->dpad; pa.qnorm = norms.as<float>();
+      pa.R = ix->R; pa.ldr = ix->dpad; pa.d = ix->d; pa.D = ix->D; pa.tb = t; pa.nt = 1;
+      pa.rmax = ix->rmax; pa.gamma = ix->gamma; pa.gammaf = (float)(ix->gamma * 1.0001);
+      pa.probes = ip; pa.out = pb.as<uint32_t>() + r0 * ip;
+      pa.recheck = rc1.as<uint32_t>(); pa.recheck_count = err.as<unsigned>() + 2;
+      pa.recheck2 = rc2.as<uint32_t>(); pa.recheck2_count = err.as<unsigned>() + 3;
+      if ((s = launch_probe(pa, st)) != FPP_OK) return done(s);
+      continue;
+    }
     HashArgs h{};
     h.P = proj.as<float>(); h.ldp = ldp; h.rows = rc; h.row0 = r0; h.t0 = t; h.nt = 1; h.D = ix->D;
     h.X = ix->X; h.ldx = ix->dpad; h.R = ix->R; h.ldr = ix->dpad; h.d = ix->d;
@@ -1140,7 +1207,7 @@ fpp_status fpp_debug_point_buckets(const fpp_index* cix, int32_t t, uint32_t* ou
     h.point_bucket = pb.as<uint32_t>() + r0;
     if ((s = launch_build_hash(h, st)) != FPP_OK) return done(s);
   }
-  if (cudaMemcpy(out, pb.p, ix->n * 4, cudaMemcpyDefault) != cudaSuccess) {
+  if (cudaMemcpy(out, pb.p, (size_t)ix->n * ip * 4, cudaMemcpyDefault) != cudaSuccess) {
     set_error("copy point buckets");
     return done(FPP_ECUDA);
   }

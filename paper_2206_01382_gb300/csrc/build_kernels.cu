@@ -378,6 +378,55 @@ __global__ void make_offsets_kernel(const uint64_t* __restrict__ kstart, int nt,
 
 }  // namespace
 
+// One warp per (point, table): for each of the point's probed buckets
+// (h1, h2), the filter score v1(h1) + v2(h2) from compensated projections
+// (v(h) = x^T r_i for h = i, -x^T r_i for h = i + D), and its record.
+__global__ void __launch_bounds__(256)
+pair_records_kernel(PairArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= a.rows * a.nt) return;
+  const int64_t r = w / a.nt;
+  const int tl = (int)(w % a.nt);
+  const int t = a.t0 + tl;
+  const int D = a.D;
+  const int64_t pid = a.row0 + r;
+  const float* x = a.X + pid * a.ldx;
+  const int nf4 = (int)(a.ldx / 4);
+  const int64_t NB = 4ll * D * D;
+  for (int e = 0; e < a.iprobes; ++e) {
+    const uint32_t bucket = a.probes[(r * a.nt + tl) * (int64_t)a.iprobes + e];
+    const uint32_t h1 = bucket / (uint32_t)(2 * D), h2 = bucket % (uint32_t)(2 * D);
+    const float* rows[2] = {
+        a.R + ((int64_t)(2 * t) * D + (h1 % (uint32_t)D)) * a.ldr,
+        a.R + ((int64_t)(2 * t + 1) * D + (h2 % (uint32_t)D)) * a.ldr};
+    double v[2];
+    warp_dot2_gather<2>(x, rows, nf4, v);
+    if (lane == 0) {
+      const double f = (h1 < (uint32_t)D ? v[0] : -v[0]) + (h2 < (uint32_t)D ? v[1] : -v[1]);
+      // order-preserving key of the (possibly negative, for tiny D) score,
+      // complemented so that ascending keys are descending scores
+      const uint64_t u = (uint64_t)__double_as_longlong(f);
+      const uint64_t okey = (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+      const uint32_t sk = (uint32_t)(tl * NB + bucket);
+      Rec rc;
+      rc.key = ~okey;
+      rc.sk = sk;
+      rc.id = (uint32_t)pid;
+      a.rec[(int64_t)tl * a.n * a.iprobes + pid * a.iprobes + e] = rc;
+      atomicAdd(a.counts + sk, 1u);
+    }
+  }
+}
+
+fpp_status launch_pair_records(const PairArgs& a, cudaStream_t st) {
+  const int64_t warps = a.rows * a.nt;
+  if (warps <= 0) return FPP_OK;
+  pair_records_kernel<<<(unsigned)ceil_div(warps, 8), 256, 0, st>>>(a);
+  FPP_LAUNCHED();
+  return FPP_OK;
+}
+
 fpp_status launch_build_hash(const HashArgs& a, cudaStream_t st) {
   const int64_t warps = a.rows * a.nt;
   if (warps <= 0) return FPP_OK;

@@ -69,6 +69,24 @@ struct HashArgs {
 };
 fpp_status launch_build_hash(const HashArgs& a, cudaStream_t st);
 
+// Multi-probe indexing (Algorithm 1, iProbes > 1): the records of the
+// iProbes buckets each point was ranked into (probe kernels run on the
+// points), with the exact pair score v1(h1) + v2(h2) as filter score.
+struct PairArgs {
+  const uint32_t* probes;    // [rows][nt][iprobes] bucket ids in rank order
+  int iprobes;
+  int64_t rows, row0;
+  int t0, nt, D;
+  const float* X;            // [n][ldx] padded points
+  int64_t ldx;
+  const float* R;            // [2 L D][ldr]
+  int64_t ldr;
+  int64_t n;
+  Rec* rec;                  // [nt][n * iprobes]
+  uint32_t* counts;          // [nt][4D^2]
+};
+fpp_status launch_pair_records(const PairArgs& a, cudaStream_t st);
+
 fpp_status launch_row_norm_max(const float* X, int64_t n, int64_t ldx, int d, float* out,
                                cudaStream_t st);
 

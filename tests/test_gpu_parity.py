@@ -227,3 +227,42 @@ def test_table_slices_merged_equal_full_search(F):
         mi, ms = F.fpp_merge_topk(np.stack(parts_i), np.stack(parts_s))
         assert np.array_equal(mi, fi)
         assert np.array_equal(ms, fs)
+
+
+def _oracle_point_probes(ix_o, t, ip):
+    """Each point's ip best buckets in table t (Algorithm 1) and a near-tie
+    flag per point (hash ties or the ip-th / (ip+1)-th pair boundary)."""
+    p1 = ix_o.X @ ix_o.R[t, 0].T
+    p2 = ix_o.X @ ix_o.R[t, 1].T
+    b, _, margin = O._top_pairs(O._signed_lists(p1), O._signed_lists(p2), ip)
+    _, _, f1 = O.cross_polytope_hash(p1)
+    _, _, f2 = O.cross_polytope_hash(p2)
+    return b, (margin < O.NEAR_TIE) | f1 | f2
+
+
+@pytest.mark.parametrize("ip,kappa,D", [(3, 0, 8), (2, 3, 16), (5, 2, 4)])
+def test_multiprobe_indexing_and_limit_scaling_parity(F, ip, kappa, D):
+    # Algorithm 1 with iProbes > 1 and the limit-scaling floor kappa
+    X, Q = W.small_mixture(6000, 80, 32, 48, 0.25, 91 + ip)
+    L, alpha = 4, 0.3
+    ix_o = O.build_index(X, L, D, alpha, seed=33, iprobes=ip, kappa=kappa)
+    ix_g = F.Index(X, L, D, alpha, seed=33, iprobes=ip, kappa=kappa)
+    excl = {}
+    for t in range(L):
+        ob, flag = _oracle_point_probes(ix_o, t, ip)
+        gb = F.fpp_debug_point_buckets(ix_g.handle, t).astype(np.int64)
+        bad = np.nonzero(np.any(ob != gb, axis=1) & ~flag)[0]
+        assert bad.size == 0, (t, bad[:5], ob[bad[:2]], gb[bad[:2]])
+        ex = set(np.nonzero(ix_o.filter_flag[t])[0].tolist())
+        fl = np.nonzero(flag)[0]
+        ex.update(ob[fl].reshape(-1).tolist())
+        ex.update(gb[fl].reshape(-1).tolist())
+        excl[t] = ex
+        off, ids = F.fpp_debug_table(ix_g.handle, t)
+        assert not PT.compare_table(ix_o, t, off, ids, ex), t
+    for P in (1, 4):
+        gi, gs = ix_g.search(Q, 10, P)
+        _, _, res = O.search_batch(ix_o, Q, 10, P)
+        c, s, fails = PT.compare_search(res, gi, gs, 10, list(range(L)), excl)
+        assert not fails, fails[:3]
+        assert c >= 0.7 * len(res), (c, s)
