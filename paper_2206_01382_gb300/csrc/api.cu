@@ -65,13 +65,11 @@ struct DevBuf {
 
 struct Workspace {
   DevBuf qpad, qsplit, proj, probes, qnorm, recheck, recheck2, kpq, ppq, out_ids, out_scores,
-      bitmaps, ecount, eoff, scan, cand, cscores, items, tkslow, stats;
-  int64_t bitmap_words = 0;
+      ecount, eoff, scan, cand, cscores, items, tkslow, stats;
   uint64_t cand_cap = 0;    // candidate slots in cand / cscores
-  int slots = 0;
   void release() {
     for (DevBuf* b : {&qpad, &qsplit, &proj, &probes, &qnorm, &recheck, &recheck2, &kpq, &ppq,
-                      &out_ids, &out_scores, &bitmaps, &ecount, &eoff, &scan, &cand, &cscores,
+                      &out_ids, &out_scores, &ecount, &eoff, &scan, &cand, &cscores,
                       &items, &tkslow, &stats})
       b->release();
   }
@@ -611,7 +609,6 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   da.probes = ws.probes.as<uint32_t>(); da.pstride = pl.pmax; da.mq = mc;
   da.tb = pl.tb; da.nt = nt; da.D = ix->D; da.probes_pq = ppq;
   da.offsets = ix->offsets; da.table_base = ix->table_base; da.ids = ix->ids;
-  da.bitmaps = ws.bitmaps.as<uint32_t>(); da.bitmap_words = ws.bitmap_words;
   da.ecount = ws.ecount.as<uint32_t>(); da.eoff = ws.eoff.as<uint64_t>();
   da.ucount = ws.ecount.as<uint32_t>() + mc;
   da.nitems = reinterpret_cast<unsigned*>(stv + 10);
@@ -641,7 +638,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   FPP_TRY(ws.items.ensure((size_t)score_item_slots(ws.cand_cap, mc) * sizeof(ScoreItem)));
   da.cand = ws.cand.as<uint32_t>();
   da.items = ws.items.as<ScoreItem>();
-  FPP_TRY(launch_dedup(da, ws.slots, st));
+  FPP_TRY(launch_dedup(da, st));
   if (ev) FPP_CUDA(cudaEventRecord(ev[5], st));
   if (stage == kCandidatesOnly) return FPP_OK;
   ScoreArgs sa{};
@@ -698,14 +695,6 @@ fpp_status prepare_workspace(fpp_index* ix, Workspace& ws, const SearchPlan& pl,
   if (host_out) {
     FPP_TRY(ws.out_ids.ensure((size_t)mc * pl.kmax * 8, false, st));
     FPP_TRY(ws.out_scores.ensure((size_t)mc * pl.kmax * 4, false, st));
-  }
-  const int slots = dedup_slots(ix->sm_count);
-  const int64_t words = ceil_div(ix->n, 32);
-  if (ws.slots != slots || ws.bitmap_words != words || !ws.bitmaps.p) {
-    ws.bitmaps.release();
-    FPP_TRY(ws.bitmaps.ensure((size_t)slots * words * 4, true, st));
-    ws.slots = slots;
-    ws.bitmap_words = words;
   }
   FPP_TRY(ws.ecount.ensure((size_t)2 * mc * 4, false, st));
   FPP_TRY(ws.eoff.ensure((size_t)(mc + 1) * 8, false, st));

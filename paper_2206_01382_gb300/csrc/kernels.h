@@ -162,8 +162,6 @@ struct DedupArgs {
   const uint32_t* offsets;   // [L][4D^2 + 1]
   const uint64_t* table_base;// [L]
   const uint32_t* ids;       // kept ids
-  uint32_t* bitmaps;         // [slots][bitmap_words]
-  int64_t bitmap_words;
   uint32_t* ecount;          // [mq] bucket entries per query
   const uint64_t* eoff;      // [mq + 1] exclusive scan of ecount
   uint32_t* cand;            // candidate ids, query q at eoff[q] ..
@@ -213,14 +211,13 @@ struct TopkArgs {
   float* out_scores;
 };
 
-int dedup_slots(int sm_count);
 int score_item_len();
 int64_t score_item_slots(uint64_t entries_total, int64_t mq);
 int topk_cap(int kprime);
 int topk_rcap(int kprime);
 int topk_slow_cap();
 fpp_status launch_count_entries(const DedupArgs& a, cudaStream_t st);
-fpp_status launch_dedup(const DedupArgs& a, int slots, cudaStream_t st);
+fpp_status launch_dedup(const DedupArgs& a, cudaStream_t st);
 fpp_status launch_score(const ScoreArgs& a, int sm_count, cudaStream_t st);
 fpp_status launch_topk(const TopkArgs& a, cudaStream_t st);
 

@@ -1,6 +1,6 @@
 // Search kernels: probe ranking per (query, table) (Section 3.4, "Multi-
-// probing for querying") and the fused candidate gather, bitmap
-// de-duplication, exact scoring and top-k (Sections 1 and 4).
+// probing for querying"), candidate gather and de-duplication, scoring and
+// top-k (Sections 1 and 4).
 #include <algorithm>
 #include <atomic>
 #include <climits>
@@ -327,68 +327,59 @@ __device__ __forceinline__ void warp_best(double& v, uint32_t& h) {
 
 
 // Re-decides the probe set of one (query, table) from compensated
-// projections dv[2D] (computed by the whole CTA), with the same ranking rule
-// on FP64-accurate values.  Run by one warp.
-__device__ void probe_exact_select(const double* dv, int D, int P, unsigned char* wsm,
+// projections dv[2D] (FP64-accurate), with the same ranking rule: the whole
+// CTA sorts each hash's signed list (v desc, wedge asc), forms the pairs of
+// the best E = min(P, 2D) entries of each list with (a+1)(b+1) <= P, and
+// sorts them (score desc, bucket asc).  wsm holds 2 lists of pow2(2D) and
+// the pairs, pow2(pair_count) entries.
+__device__ void probe_exact_select(const double* dv, int D, int P, SD* lists, SD* pairs,
                                    uint32_t* bucket_out) {
-  const int lane = threadIdx.x & 31;
-  DEntry* top = reinterpret_cast<DEntry*>(wsm);                              // 2 x LIST_CAP
-  DEntry* pairs = reinterpret_cast<DEntry*>(wsm + (size_t)2 * LIST_CAP * 16);  // SLOW_PAIRS
   const int W2 = 2 * D;
+  const int NL = pow2_ceil(W2);
   const int E = P < W2 ? P : W2;
   for (int j = 0; j < 2; ++j) {
-    uint64_t taken = 0ull;  // bit s: wedge lane + 32 s already selected
-    for (int r = 0; r < E; ++r) {
-      double bv = -INFINITY;
-      uint32_t bh = 0xFFFFFFFFu;
-      for (int s = 0; s * 32 + lane < W2; ++s) {
-        if (taken & (1ull << s)) continue;
-        const uint32_t h = s * 32 + lane;
-        const double v = h < (uint32_t)D ? dv[j * D + h] : -dv[j * D + h - D];
-        if (dentry_before(v, h, bv, bh)) { bv = v; bh = h; }
+    SD* L = lists + j * NL;
+    for (int h = threadIdx.x; h < NL; h += blockDim.x) {
+      if (h < W2) {
+        const double v = h < D ? dv[j * D + h] : -dv[j * D + h - D];
+        L[h] = SD{v, (uint32_t)h, 0};
+      } else {
+        L[h] = SD{-INFINITY, 0xFFFFFFFFu, 0};
       }
-      warp_best(bv, bh);
-      if ((int)(bh & 31) == lane) taken |= 1ull << (bh >> 5);
-      if (lane == 0) top[j * LIST_CAP + r] = DEntry{bv, bh, 0};
     }
   }
-  __syncwarp();
+  __syncthreads();
+  block_sort_sd(lists, NL);
+  block_sort_sd(lists + NL, NL);
+  // pairs (a, b) with (a+1)(b+1) <= P: row a holds min(P / (a+1), E) of them
   int C = 0;
-  for (int ai = 0; ai < E; ++ai) {
-    int nb = P / (ai + 1);
-    if (nb > E) nb = E;
-    if (nb <= 0) break;
-    for (int b = lane; b < nb; b += 32) {
-      const DEntry x = top[ai], y = top[LIST_CAP + b];
-      pairs[C + b] = DEntry{x.v + y.v, x.h * (uint32_t)W2 + y.h, 0};
+  for (int ai = 0; ai < E; ++ai) C += min(P / (ai + 1), E);
+  const int NC = pow2_ceil(C > 1 ? C : 1);
+  for (int idx = threadIdx.x; idx < NC; idx += blockDim.x) {
+    if (idx < C) {
+      int ai = 0, base = 0;
+      while (base + min(P / (ai + 1), E) <= idx) { base += min(P / (ai + 1), E); ++ai; }
+      const int bi = idx - base;
+      const SD x = lists[ai], y = lists[NL + bi];
+      pairs[idx] = SD{x.s + y.s, x.id * (uint32_t)W2 + y.id, 0};
+    } else {
+      pairs[idx] = SD{-INFINITY, 0xFFFFFFFFu, 0};
     }
-    C += nb;
   }
-  __syncwarp();
-  unsigned taken = 0u;
-  for (int r = 0; r < P; ++r) {
-    double bv = -INFINITY;
-    uint32_t bh = 0xFFFFFFFFu;
-    int bs = -1;
-    for (int s = 0; s * 32 + lane < C; ++s) {
-      if (taken & (1u << s)) continue;
-      const DEntry e = pairs[s * 32 + lane];
-      if (dentry_before(e.v, e.h, bv, bh)) { bv = e.v; bh = e.h; bs = s; }
-    }
-    // bucket ids of distinct pairs are distinct, so the owner lane is unique
-    double wv = bv;
-    uint32_t wh = bh;
-    warp_best(wv, wh);
-    if (bs >= 0 && bh == wh) taken |= 1u << bs;
-    if (lane == 0) bucket_out[r] = wh;
-  }
-  __syncwarp();
+  __syncthreads();
+  block_sort_sd(pairs, NC);
+  for (int r = threadIdx.x; r < P; r += blockDim.x) bucket_out[r] = pairs[r].id;
+  __syncthreads();
 }
 
 constexpr int RECHECK_THREADS = 256;
 
+// dv [2D] doubles, two sorted signed lists of pow2(2D) entries, and the
+// candidate pairs (at most P (1 + ln P) <= 1024 for P <= 128 ... bounded by
+// pair_count(P, ...) <= SLOW_PAIRS)
 __host__ __device__ inline size_t recheck_smem_bytes(int D) {
-  return (size_t)8 * 2 * D + (size_t)2 * LIST_CAP * 16 + (size_t)16 * SLOW_PAIRS;
+  return (size_t)8 * 2 * D + (size_t)2 * pow2_ceil(2 * D) * sizeof(SD) +
+         (size_t)SLOW_PAIRS * sizeof(SD);
 }
 
 // One CTA per (query, table) item of the recheck list: its warps compute the
@@ -426,8 +417,9 @@ probe_recheck_kernel(ProbeArgs a) {
       }
     }
     __syncthreads();
-    if (wid == 0) probe_exact_select(dv, a.D, P, wsm, a.out + (q * a.nt + tl) * (int64_t)a.probes);
-    __syncthreads();
+    SD* lists = reinterpret_cast<SD*>(wsm);
+    probe_exact_select(dv, a.D, P, lists, lists + 2 * pow2_ceil(2 * a.D),
+                       a.out + (q * a.nt + tl) * (int64_t)a.probes);
   }
 }
 
@@ -543,29 +535,27 @@ __global__ void query_norms_kernel(const float* __restrict__ Q, int64_t m, int64
 
 // ============================================================== gather + score
 //
-// Candidate gather, de-duplication and scoring run as four kernels per query
-// batch, so that the latency-bound part (walking buckets, bitmap
-// test-and-set) and the bandwidth-bound part (streaming candidate rows) each
-// get a launch shaped for them:
+// Candidate gather, de-duplication and scoring run as separate kernels per
+// query batch, so that the latency-bound part (walking buckets, hash-set
+// inserts) and the bandwidth-bound part (streaming candidate rows) each get
+// a launch shaped for them:
 //  count_entries  warp per query: bucket entries E_q of its probed buckets;
 //                 an exclusive scan gives each query a region of E_q slots;
-//  dedup          warp per query: walks the kept ids of its buckets (all
-//                 buckets resolved together, entries spread over the lanes),
-//                 test-and-sets each id in the warp's bitmap (n bits in
-//                 global memory, one bitmap per resident warp, L2-resident),
-//                 writes the ids seen first to the front of its region,
-//                 cuts them into work items of <= ITEM ids, and clears the
-//                 bitmap words it touched;
+//  dedup          CTA per query with E_q <= 16,384: walks the kept ids of its
+//                 buckets, inserts them into a shared-memory hash set, writes
+//                 the ids seen first to the front of its region and appends
+//                 work items of <= ITEM ids; larger queries are copied
+//                 without de-duplication (flatten_kernel);
 //  score          flat over work items: every candidate row is read once
-//                 with coalesced float4 loads, 8 lanes per row and 16 rows in
-//                 flight per warp, and scored with the compensated dot
-//                 product, so scores are FP64-accurate;
+//                 with coalesced float4 loads, G lanes per row and 16 rows in
+//                 flight per warp (FP32 scores, error <= gamma_d);
 //  topk           warp per query: best k of its candidates by (score desc,
-//                 id asc).
+//                 id asc), with exact re-scoring of the boundary window.
 
-constexpr int DW = 8;                           // warps per bitmap-dedup CTA
-constexpr int HS = 4096;                        // hash slots per warp (power of two)
-constexpr int HMAX = HS / 2;                    // entries a query may have for the hash path
+constexpr int DW = 8;                           // warps per flatten CTA
+constexpr int HS_SMALL = 4096;                  // hash slots of the small-query CTAs
+constexpr int HS_BIG = 32768;                   // hash slots of the mid-size-query CTAs
+constexpr int HMAX_BIG = HS_BIG / 2;            // larger queries are not de-duplicated
 constexpr int HU = 8;                           // entry loads in flight per lane
 constexpr int PCHUNK = 128;                     // probed buckets resolved per pass
 constexpr int PPT = PCHUNK / 32;                // buckets per lane per pass
@@ -683,79 +673,74 @@ count_entries_kernel(DedupArgs a) {
   if (lane == 0) a.ecount[q] = s;
 }
 
+// Queries with more than HMAX_BIG bucket entries keep every entry (no
+// de-duplication): with that many probed buckets few ids repeat, and a
+// repeated id only costs one more row read; the top-k kernel drops repeated
+// (score, id) keys.  One warp per query copies its entries in bucket order.
 __global__ void __launch_bounds__(DW * 32, 4)
-dedup_kernel(DedupArgs a) {
+flatten_kernel(DedupArgs a) {
   __shared__ uint64_t s_pbase[DW][PCHUNK];
   __shared__ uint32_t s_pstart[DW][PCHUNK + 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int slot = blockIdx.x * DW + wid;
-  uint32_t* bm = a.bitmaps + (int64_t)slot * a.bitmap_words;
   const int64_t NB = 4ll * a.D * a.D;
-  unsigned long long ent = 0, uni = 0, prb = 0;
+  unsigned long long ent = 0, prb = 0;
   const int64_t nwarps = (int64_t)gridDim.x * DW;
   for (int64_t q = (int64_t)blockIdx.x * DW + wid; q < a.mq; q += nwarps) {
-    if (a.eoff[q + 1] - a.eoff[q] <= (uint64_t)HMAX) continue;   // the hash kernel's
+    const uint64_t E = a.eoff[q + 1] - a.eoff[q];
+    if (E <= (uint64_t)HMAX_BIG) continue;   // the hash kernels'
     const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
     WarpWalk w{&a, q, Pq, a.nt * Pq, NB, s_pbase[wid], s_pstart[wid]};
     uint32_t* out = a.cand + a.eoff[q];
-    struct Discover {
-      uint32_t* bm; uint32_t* out; uint32_t n;
+    struct Copy {
+      uint32_t* out; uint32_t n;
       __device__ void operator()(const uint32_t (&id)[EPT], const bool (&has)[EPT]) {
-        uint32_t old[EPT];
-#pragma unroll
-        for (int r = 0; r < EPT; ++r)   // all atomics in flight before any result is used
-          old[r] = has[r] ? atomicOr(bm + (id[r] >> 5), 1u << (id[r] & 31)) : 0xFFFFFFFFu;
-        const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+        // the valid entries of a round are a prefix of its 32 * EPT slots
+        const int lane = threadIdx.x & 31;
+        uint32_t valid = 0;
 #pragma unroll
         for (int r = 0; r < EPT; ++r) {
-          const bool fresh = !(old[r] & (1u << (id[r] & 31)));
-          const unsigned m = __ballot_sync(FULL, fresh);
-          if (fresh) out[n + __popc(m & lt)] = id[r];
-          n += __popc(m);
+          if (has[r]) out[n + r * 32 + lane] = id[r];
+          valid += __popc(__ballot_sync(FULL, has[r]));
         }
+        n += valid;
       }
-    } disc{bm, out, 0u};
-    warp_walk(w, disc);
-    const uint32_t U = disc.n;
-    if (lane == 0) {   // per-warp totals, summed over the warp below
-      ent += a.eoff[q + 1] - a.eoff[q];
-      uni += U;
+    } cp{out, 0u};
+    warp_walk(w, cp);
+    const uint32_t U = (uint32_t)E;
+    if (lane == 0) {
+      ent += E;
       prb += (unsigned long long)w.nprobe;
+      a.ucount[q] = U;
     }
-    if (lane == 0) a.ucount[q] = U;
     write_items(a, q, U);
-    __syncwarp();
-    // clear the bitmap words of the ids just written (this warp wrote them)
-    for (uint32_t k = lane; k < U; k += 32) bm[out[k] >> 5] = 0u;
     __syncwarp();
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     ent += __shfl_xor_sync(FULL, ent, o);
-    uni += __shfl_xor_sync(FULL, uni, o);
     prb += __shfl_xor_sync(FULL, prb, o);
   }
   if (lane == 0 && a.stats) {
     atomicAdd(a.stats + 0, ent);
-    atomicAdd(a.stats + 1, uni);
+    atomicAdd(a.stats + 1, ent);
     atomicAdd(a.stats + 3, prb);
   }
 }
 
-// De-duplication of the queries with at most HMAX bucket entries, one CTA
+// De-duplication of the queries with (ELO, HS / 2] bucket entries, one CTA
 // (HT threads) per query: an open-addressing hash set of HS ids in shared
 // memory (linear probing, insertion by compare-and-swap, so exactly one
 // thread sees an id as new), at most half full and reset after each query.
 // The probed buckets are resolved HT at a time; each thread then walks a
 // contiguous run of the entries, so the bucket of its next entry is found by
-// stepping instead of searching.  Larger queries are left to the bitmap
-// kernel.
+// stepping instead of searching.
 constexpr uint32_t HEMPTY = 0xFFFFFFFFu;
 constexpr int HT = 256;                         // threads per hash-dedup CTA
 
-__global__ void __launch_bounds__(HT, 4)
+template <int HS, int LOG2HS, int ELO>
+__global__ void __launch_bounds__(HT)
 dedup_hash_kernel(DedupArgs a) {
-  __shared__ __align__(16) uint32_t tab[HS];
+  extern __shared__ __align__(16) uint32_t tab[];
   __shared__ uint64_t pbase[HT];
   __shared__ uint32_t pstart[HT + 1];
   __shared__ uint32_t wsum[HT / 32];
@@ -769,7 +754,7 @@ dedup_hash_kernel(DedupArgs a) {
   unsigned long long ent = 0, uni = 0, prb = 0;
   for (int64_t q = blockIdx.x; q < a.mq; q += gridDim.x) {
     const uint64_t E = a.eoff[q + 1] - a.eoff[q];
-    if (E > (uint64_t)HMAX) continue;   // uniform over the CTA
+    if (E > (uint64_t)(HS / 2) || E <= (uint64_t)ELO) continue;   // uniform over the CTA
     const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
     const int nprobe = a.nt * Pq;
     uint32_t* out = a.cand + a.eoff[q];
@@ -841,7 +826,7 @@ dedup_hash_kernel(DedupArgs a) {
         for (int u = 0; u < HU; ++u) {
           bool fresh = false;
           if (has[u]) {
-            uint32_t h = (id[u] * 0x9E3779B1u) >> (32 - 12);   // log2(HS) = 12
+            uint32_t h = (id[u] * 0x9E3779B1u) >> (32 - LOG2HS);
             while (true) {
               const uint32_t old = atomicCAS(tab + h, HEMPTY, id[u]);
               if (old == HEMPTY) { fresh = true; break; }
@@ -1229,8 +1214,21 @@ topk_kernel(TopkArgs a) {
   for (int e = (int)nsl + lane; e < np2; e += 32) list[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
   __syncwarp();
   warp_sort_sd(list, np2);
+  // a candidate listed twice (lists that were not de-duplicated) now sits
+  // next to its copy: keep one of each
+  int nd = 0;
+  for (int i0 = 0; i0 < (int)nsl; i0 += 32) {
+    const int i = i0 + lane;
+    const SD v = i < (int)nsl ? list[i] : SD{-INFINITY, 0xFFFFFFFFu, 0};
+    const bool keep = i < (int)nsl && (i == 0 || list[i - 1].id != v.id);
+    const unsigned m = __ballot_sync(FULL, keep);
+    __syncwarp();
+    if (keep) list[nd + __popc(m & ((1u << lane) - 1u))] = v;
+    nd += __popc(m);
+    __syncwarp();
+  }
   for (int e = lane; e < a.kmax; e += 32) {
-    const bool ok = e < kq && e < (int)nsl;
+    const bool ok = e < kq && e < nd;
     a.out_ids[orow + e] = ok ? (int64_t)list[e].id : -1;
     a.out_scores[orow + e] = ok ? (float)list[e].s : -INFINITY;
   }
@@ -1481,7 +1479,6 @@ fpp_status launch_query_norms(const float* Q, int64_t m, int64_t ldq, int d, flo
   return FPP_OK;
 }
 
-int dedup_slots(int sm_count) { return sm_count * DW; }
 int score_item_len() { return ITEM; }
 int64_t score_item_slots(uint64_t cand_total, int64_t mq) {
   return (int64_t)(cand_total / ITEM) + mq + 1;
@@ -1494,24 +1491,37 @@ fpp_status launch_count_entries(const DedupArgs& a, cudaStream_t st) {
   return FPP_OK;
 }
 
-fpp_status launch_dedup(const DedupArgs& a, int slots, cudaStream_t st) {
-  if (a.mq <= 0) return FPP_OK;
-  // queries with at most HMAX entries: shared-memory hash sets, one CTA each
-  static std::atomic<int> hash_grid{0};
-  if (!hash_grid.load(std::memory_order_relaxed)) {
+template <int HS, int LOG2HS, int ELO>
+fpp_status launch_hash_tier(const DedupArgs& a, std::atomic<int>& grid_cache, cudaStream_t st) {
+  const size_t smem = (size_t)HS * 4;
+  int g = grid_cache.load(std::memory_order_relaxed);
+  if (!g) {
+    FPP_CUDA(cudaFuncSetAttribute(dedup_hash_kernel<HS, LOG2HS, ELO>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0, dev = 0, sms = 0;
-    FPP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dedup_hash_kernel, HT, 0));
+    FPP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dedup_hash_kernel<HS, LOG2HS, ELO>,
+                                                           HT, smem));
     FPP_CUDA(cudaGetDevice(&dev));
     FPP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    hash_grid.store(std::max(1, per_sm) * sms, std::memory_order_relaxed);
+    g = std::max(1, per_sm) * sms;
+    grid_cache.store(g, std::memory_order_relaxed);
   }
-  const int hgrid = (int)std::min<int64_t>(a.mq, hash_grid.load());
-  dedup_hash_kernel<<<hgrid, HT, 0, st>>>(a);
+  dedup_hash_kernel<HS, LOG2HS, ELO><<<(int)std::min<int64_t>(a.mq, g), HT, smem, st>>>(a);
   FPP_LAUNCHED();
-  // the rest: one global bitmap of n bits per warp slot
-  const int64_t ctas = ceil_div(a.mq, DW);
-  const int grid = (int)std::min<int64_t>(ctas, slots / DW);
-  dedup_kernel<<<grid, DW * 32, 0, st>>>(a);
+  return FPP_OK;
+}
+
+fpp_status launch_dedup(const DedupArgs& a, cudaStream_t st) {
+  if (a.mq <= 0) return FPP_OK;
+  // three tiers by entry count: a 4,096-slot table (<= 2,048 entries), a
+  // 32,768-slot table (<= 16,384), and no de-duplication above that
+  static std::atomic<int> g_small{0}, g_big{0};
+  FPP_TRY((launch_hash_tier<HS_SMALL, 12, 0>(a, g_small, st)));
+  FPP_TRY((launch_hash_tier<HS_BIG, 15, HS_SMALL / 2>(a, g_big, st)));
+  int sms = 0, dev = 0;
+  FPP_CUDA(cudaGetDevice(&dev));
+  FPP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  flatten_kernel<<<(int)std::min<int64_t>(ceil_div(a.mq, DW), (int64_t)sms * 4), DW * 32, 0, st>>>(a);
   FPP_LAUNCHED();
   return FPP_OK;
 }

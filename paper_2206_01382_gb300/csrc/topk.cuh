@@ -123,7 +123,20 @@ struct WarpTop {
     for (int i = cnt + lane; i < cap; i += 32) buf[i] = 0;
     __syncwarp();
     warp_sort_desc(buf, cap);
-    cnt = cnt < kp ? cnt : kp;
+    // a candidate offered twice (lists that were not de-duplicated) has the
+    // same key both times: keep one copy of each key
+    int n = 0;
+    for (int i0 = 0; i0 < cnt; i0 += 32) {
+      const int i = i0 + lane;
+      const uint64_t v = i < cnt ? buf[i] : 0ull;
+      const bool keep = i < cnt && (i == 0 || buf[i - 1] != v);
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      __syncwarp();
+      if (keep) buf[n + __popc(m & ((1u << lane) - 1u))] = v;
+      n += __popc(m);
+      __syncwarp();
+    }
+    cnt = n < kp ? n : kp;
     if (cnt == kp) thr = buf[kp - 1];
     __syncwarp();
   }

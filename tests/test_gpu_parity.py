@@ -234,7 +234,8 @@ def _oracle_point_probes(ix_o, t, ip):
     flag per point (hash ties or the ip-th / (ip+1)-th pair boundary)."""
     p1 = ix_o.X @ ix_o.R[t, 0].T
     p2 = ix_o.X @ ix_o.R[t, 1].T
-    b, _, margin = O._top_pairs(O._signed_lists(p1), O._signed_lists(p2), ip)
+    from oracle import falconn as OF
+    b, _, margin = OF._top_pairs(OF._signed_lists(p1), OF._signed_lists(p2), ip)
     _, _, f1 = O.cross_polytope_hash(p1)
     _, _, f2 = O.cross_polytope_hash(p2)
     return b, (margin < O.NEAR_TIE) | f1 | f2
@@ -266,3 +267,25 @@ def test_multiprobe_indexing_and_limit_scaling_parity(F, ip, kappa, D):
         c, s, fails = PT.compare_search(res, gi, gs, 10, list(range(L)), excl)
         assert not fails, fails[:3]
         assert c >= 0.7 * len(res), (c, s)
+
+
+@pytest.mark.parametrize("n,L,D,P", [(30000, 24, 4, 8), (12000, 6, 8, 12)])
+def test_large_candidate_lists_parity(F, n, L, D, P):
+    # queries with more than 16,384 bucket entries (first case: ~90,000 per
+    # query, most of them repeats) skip de-duplication; the mid-size table
+    # takes 2,049..16,384 entries (second case); results are unchanged
+    X, Q = W.small_mixture(n, 30, 16, 8, 0.3, 92 + D)
+    ix_o = O.build_index(X, L, D, 1.0, seed=44)
+    ix_g = F.Index(X, L, D, 1.0, seed=44)
+    excl = {t: PT.excluded_buckets(ix_o, t, F.fpp_debug_point_buckets(ix_g.handle, t))
+            for t in range(L)}
+    gi, gs = ix_g.search(Q, 20, P)
+    _, _, res = O.search_batch(ix_o, Q, 20, P)
+    c, s, fails = PT.compare_search(res, gi, gs, 20, list(range(L)), excl)
+    assert not fails, fails[:3]
+    assert c >= 0.7 * len(res), (c, s)
+    for i in range(len(Q)):   # no id twice in a result
+        row = gi[i][gi[i] >= 0]
+        assert len(set(row.tolist())) == len(row)
+    _, _, st = F.fpp_search_ex(ix_g.handle, Q, k=20, probes=P)
+    assert st["entries"] > 2048 * len(Q)
