@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="serving workload: seconds of arrivals per offered rate")
     ap.add_argument("--slots", type=int, default=3, help="serving workload: batches in flight")
+    ap.add_argument("--graph", action="store_true",
+                    help="time the steps as replays of the library's captured search graph")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -378,7 +380,8 @@ def main():
     stream = torch.cuda.Stream(device=dev)
 
     for _ in range(args.warmup):
-        F.fpp_search_ex(ix.handle, Qd, stream=stream, ids=ids, scores=sc, **search_kw)
+        F.fpp_search_ex(ix.handle, Qd, stream=stream, ids=ids, scores=sc, want_stats=False,
+                        graph=args.graph, **search_kw)
     barrier()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
@@ -393,7 +396,7 @@ def main():
     evs[0].record(stream)
     for s in range(args.steps):
         F.fpp_search_ex(ix.handle, Qd, stream=stream, ids=ids, scores=sc, want_stats=False,
-                        **search_kw)
+                        graph=args.graph, **search_kw)
         evs[s + 1].record(stream)
     barrier()
     launches = F.fpp_launch_count() - launches0
@@ -552,6 +555,7 @@ def main():
                        "recall_sample": mcal, "l2": "inputs larger than L2 (X is "
                        f"{w.n * w.d * 4 / 2**20:.0f} MiB), no flush",
                        "build_s": build_s, "index_kept_ids": info["kept_total"],
+                       "max_bucket_kept": info["max_bucket_kept"], "cuda_graph": args.graph,
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"batch_p50": sm[len(sm) // 2], "batch_p99": sm[min(len(sm) - 1, int(0.99 * len(sm)))]},
             "roofline": roof,

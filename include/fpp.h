@@ -94,16 +94,29 @@ typedef struct fpp_search_opts {
   int32_t k_max;              /* row stride of ids/scores; >= every k         */
   int32_t table_begin;        /* search tables [table_begin, table_end)     */
   int32_t table_end;          /* 0 or L = all tables                          */
-  int32_t reserved0;
+  int32_t flags;              /* FPP_SEARCH_* bits                            */
   void* stream;               /* cudaStream_t or NULL                         */
 } fpp_search_opts;
+
+/* FPP_SEARCH_GRAPH: run the call as one CUDA graph, captured on the first
+ * call and replayed by later calls with the same Q, ids, scores, per-query
+ * arrays, k, probes, k_max, table range and stream (the data they point to
+ * may change between calls).  Taken only when stream is non-NULL, Q, ids,
+ * scores and the per-query arrays are device memory and stats is NULL;
+ * otherwise (or when the candidate buffers would need a read-back) the call
+ * runs normally.  Results are complete once the stream reaches the call's
+ * point; error flags raised inside the graph are not reported. */
+#define FPP_SEARCH_GRAPH 1
 
 /* Counters of one search call (summed over queries). */
 typedef struct fpp_search_stats {
   uint64_t queries;
   uint64_t probes;            /* buckets probed                               */
   uint64_t entries;           /* bucket entries scanned, with duplicates      */
-  uint64_t unique;            /* distinct candidates scored                   */
+  uint64_t unique;            /* candidates scored: distinct ids, except for
+                                 queries with more than 16,384 bucket entries,
+                                 whose entries are scored without
+                                 de-duplication (repeats dropped at top-k)    */
   uint64_t probe_rechecks;    /* (query, table) probe sets re-decided in
                                  FP64-accurate arithmetic                     */
   uint64_t topk_rechecks;     /* queries whose top-k boundary was re-decided  */

@@ -21,6 +21,7 @@ from . import _build
 
 FPP_OK, FPP_EINVAL, FPP_ENOMEM, FPP_ECUDA, FPP_ETIMEOUT, FPP_EBUSY, FPP_EINTERNAL = range(7)
 FPP_FP32, FPP_BF16 = 0, 1
+FPP_SEARCH_GRAPH = 1
 STATUS_NAMES = {0: "FPP_OK", 1: "FPP_EINVAL", 2: "FPP_ENOMEM", 3: "FPP_ECUDA",
                 4: "FPP_ETIMEOUT", 5: "FPP_EBUSY", 6: "FPP_EINTERNAL"}
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
@@ -44,7 +45,7 @@ class fpp_search_opts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("probes", ctypes.c_int32),
                 ("k_per_query", ctypes.c_void_p), ("probes_per_query", ctypes.c_void_p),
                 ("k_max", ctypes.c_int32), ("table_begin", ctypes.c_int32),
-                ("table_end", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("table_end", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -242,7 +243,8 @@ def fpp_search(ix, Q, k: int, probes: int, ids=None, scores=None):
 
 def fpp_search_ex(ix, Q, k: int = 10, probes: int = 1, k_per_query=None, probes_per_query=None,
                   k_max: int | None = None, table_begin: int = 0, table_end: int = 0,
-                  stream=None, ids=None, scores=None, want_stats: bool = True):
+                  stream=None, ids=None, scores=None, want_stats: bool = True,
+                  graph: bool = False):
     """fpp_search with per-query k / probes, a table range, a stream and stats."""
     Q = _f32(Q)
     m = Q.shape[0]
@@ -256,6 +258,7 @@ def fpp_search_ex(ix, Q, k: int = 10, probes: int = 1, k_per_query=None, probes_
     o.k_per_query, o.probes_per_query = _ptr(kpq), _ptr(ppq)
     o.k_max, o.table_begin, o.table_end = k_max, table_begin, table_end
     o.stream = _stream_ptr(stream)
+    o.flags = FPP_SEARCH_GRAPH if graph else 0
     ids = _alloc_like(Q, (m, k_max), "i64") if ids is None else ids
     scores = _alloc_like(Q, (m, k_max), "f32") if scores is None else scores
     st = fpp_search_stats()

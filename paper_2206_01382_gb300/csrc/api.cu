@@ -1,5 +1,6 @@
 // C ABI of libfpp: index object, build and search orchestration.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -40,6 +41,10 @@ bool is_device_ptr(const void* p) {
 }
 
 // Grow-only device buffer.
+// Every (re)allocation of a workspace buffer bumps g_alloc_gen, so that a
+// captured search graph (which holds buffer addresses) is re-captured.
+std::atomic<uint64_t> g_alloc_gen{0};
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -49,6 +54,7 @@ struct DevBuf {
     p = nullptr;
     bytes = 0;
     const size_t sz = std::max<size_t>(need, 256);
+    g_alloc_gen.fetch_add(1);
     FPP_CUDA(cudaMalloc(&p, sz));
     bytes = sz;
     if (zero) FPP_CUDA(cudaMemsetAsync(p, 0, sz, st));
@@ -66,12 +72,29 @@ struct DevBuf {
 struct Workspace {
   DevBuf qpad, qsplit, proj, probes, qnorm, recheck, recheck2, kpq, ppq, out_ids, out_scores,
       ecount, eoff, scan, cand, cscores, items, tkslow, stats;
+  // completion of the last call that used this workspace: a call on another
+  // stream waits for it before touching the buffers
+  cudaEvent_t done = nullptr;
+  fpp_status order_after_last(cudaStream_t st) {
+    if (!done) {
+      FPP_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+      return FPP_OK;
+    }
+    FPP_CUDA(cudaStreamWaitEvent(st, done, 0));
+    return FPP_OK;
+  }
+  fpp_status mark_done(cudaStream_t st) {
+    FPP_CUDA(cudaEventRecord(done, st));
+    return FPP_OK;
+  }
   uint64_t cand_cap = 0;    // candidate slots in cand / cscores
   void release() {
     for (DevBuf* b : {&qpad, &qsplit, &proj, &probes, &qnorm, &recheck, &recheck2, &kpq, &ppq,
                       &out_ids, &out_scores, &ecount, &eoff, &scan, &cand, &cscores,
                       &items, &tkslow, &stats})
       b->release();
+    if (done) cudaEventDestroy(done);
+    done = nullptr;
   }
 };
 
@@ -92,6 +115,10 @@ struct fpp_index {
   int rerank_k = 0;            // FPP_BF16: shortlist re-ranked on the FP32 rows
   double score_gamma = 0.0;    // candidate score error factor
   uint64_t cand_budget_entries = 0;  // candidate slots a batch may provision without a read-back
+  // captured search graph (FPP_SEARCH_GRAPH) and the call it was captured for
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<uint64_t> graph_key;
+  uint64_t graph_kernels = 0;  // kernel nodes of the graph
   float* rmax = nullptr;       // [2L]
   float xmax = 0.f;
   uint32_t* offsets = nullptr; // [L][4D^2 + 1]
@@ -135,6 +162,8 @@ void free_index_memory(fpp_index* ix) {
   cudaFree(ix->offsets);
   cudaFree(ix->table_base);
   cudaFree(ix->ids);
+  if (ix->graph_exec) cudaGraphExecDestroy(ix->graph_exec);
+  ix->graph_exec = nullptr;
   ix->ws.release();
 }
 
@@ -703,6 +732,75 @@ fpp_status prepare_workspace(fpp_index* ix, Workspace& ws, const SearchPlan& pl,
   return FPP_OK;
 }
 
+// FPP_SEARCH_GRAPH: the whole call (every batch) as one CUDA graph, captured
+// on first use and replayed while the call's arguments and the workspace
+// stay the same.  Needs candidate buffers provisioned from the worst-case
+// bound (no read-back inside a graph); returns false (nothing done) when the
+// bound exceeds the sync-free budget, so the caller runs the call normally.
+bool search_graph(fpp_index* ix, const float* Q, int64_t m, const fpp_search_opts* o,
+                  const SearchPlan& pl, int64_t mc, int64_t* ids, float* scores, cudaStream_t st,
+                  fpp_status& out) {
+  Workspace& ws = ix->ws;
+  const int nt = pl.te - pl.tb;
+  const uint64_t bound = (uint64_t)mc * nt * pl.pmax * std::max<uint32_t>(ix->max_bucket_kept, 1);
+  if (bound > ws.cand_cap && bound > ix->cand_budget_entries) return false;
+  out = FPP_OK;
+  auto fail = [&](fpp_status s) { out = s; return true; };
+  if (bound > ws.cand_cap) {
+    ws.cand.release(); ws.cscores.release(); ws.items.release();
+    if ((out = ws.cand.ensure((size_t)bound * 4)) != FPP_OK) return true;
+    if ((out = ws.cscores.ensure((size_t)bound * 4)) != FPP_OK) return true;
+    ws.cand_cap = bound;
+  }
+  if ((out = ws.items.ensure((size_t)score_item_slots(ws.cand_cap, mc) * sizeof(ScoreItem))) != FPP_OK)
+    return true;
+  const std::vector<uint64_t> key = {
+      (uint64_t)(uintptr_t)Q, (uint64_t)m, (uint64_t)(uintptr_t)ids, (uint64_t)(uintptr_t)scores,
+      (uint64_t)(uintptr_t)pl.kpq, (uint64_t)(uintptr_t)pl.ppq, (uint64_t)pl.k,
+      (uint64_t)pl.probes, (uint64_t)pl.kmax, (uint64_t)pl.pmax, (uint64_t)pl.tb, (uint64_t)pl.te,
+      (uint64_t)(uintptr_t)st, g_alloc_gen.load()};
+  if (!ix->graph_exec || ix->graph_key != key) {
+    if (ix->graph_exec) cudaGraphExecDestroy(ix->graph_exec);
+    ix->graph_exec = nullptr;
+    ix->graph_key.clear();
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      set_error("search graph: stream capture could not start");
+      return fail(FPP_ECUDA);
+    }
+    fpp_status s = FPP_OK;
+    const uint64_t k0 = launch_counter().load();
+    if (cudaMemsetAsync(ws.stats.p, 0, 16 * 8, st) != cudaSuccess) s = FPP_ECUDA;
+    for (int64_t q0 = 0; q0 < m && s == FPP_OK; q0 += mc) {
+      const int64_t c = std::min<int64_t>(mc, m - q0);
+      s = search_chunk(ix, ws, Q, q0, c, pl, ids + q0 * pl.kmax, scores + q0 * pl.kmax, st, kFull,
+                       nullptr);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(st, &g);
+    if (s == FPP_OK && ce != cudaSuccess) {
+      set_error(std::string("search graph: capture failed: ") + cudaGetErrorString(ce));
+      s = FPP_ECUDA;
+    }
+    if (s == FPP_OK && cudaGraphInstantiate(&ix->graph_exec, g, 0) != cudaSuccess) {
+      set_error("search graph: instantiation failed");
+      ix->graph_exec = nullptr;
+      s = FPP_ECUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+    // the capture counted the kernels it recorded; they run at each replay
+    ix->graph_kernels = launch_counter().load() - k0;
+    launch_counter().fetch_sub(ix->graph_kernels);
+    if (s != FPP_OK) return fail(s);
+    ix->graph_key = key;
+  }
+  if (cudaGraphLaunch(ix->graph_exec, st) != cudaSuccess) {
+    set_error("search graph: launch failed");
+    return fail(FPP_ECUDA);
+  }
+  launch_counter().fetch_add(ix->graph_kernels, std::memory_order_relaxed);
+  return true;
+}
+
 fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fpp_search_opts* o,
                        int64_t* ids, float* scores, fpp_search_stats* stats) {
   SearchPlan pl{};
@@ -716,6 +814,15 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
   const int nt = pl.te - pl.tb;
   const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt, pl.pmax), m);
   FPP_TRY(prepare_workspace(ix, ix->ws, pl, mc, !dev_out, st));
+  FPP_TRY(ix->ws.order_after_last(st));
+  if ((o->flags & FPP_SEARCH_GRAPH) && st && dev_out && !stats && is_device_ptr(Q) &&
+      (!pl.kpq || pl.kpq_dev) && (!pl.ppq || pl.ppq_dev)) {
+    fpp_status gs = FPP_OK;
+    if (search_graph(ix, Q, m, o, pl, mc, ids, scores, st, gs)) {
+      if (gs == FPP_OK) gs = ix->ws.mark_done(st);
+      return gs;
+    }
+  }
   FPP_CUDA(cudaMemsetAsync(ix->ws.stats.p, 0, 16 * 8, st));
   cudaEvent_t ev[7] = {};
   bool timing = stats != nullptr;
@@ -745,6 +852,7 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
       for (int i = 0; i < 7; ++i) ms[i] += t[i];
     }
   }
+  FPP_TRY(ix->ws.mark_done(st));
   const bool need_sync = !dev_out || o->stream == nullptr || stats != nullptr;
   unsigned long long hs[8] = {0};
   if (need_sync) {
@@ -1237,6 +1345,7 @@ fpp_status fpp_debug_probes(const fpp_index* cix, const float* Q, int64_t m, int
   const int nt = pl.te - pl.tb;
   const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt, pl.pmax), m);
   FPP_TRY(prepare_workspace(ix, ix->ws, pl, mc, false, 0));
+  FPP_TRY(ix->ws.order_after_last(0));
   for (int64_t q0 = 0; q0 < m; q0 += mc) {
     const int64_t c = std::min<int64_t>(mc, m - q0);
     FPP_TRY(search_chunk(ix, ix->ws, Q, q0, c, pl, nullptr, nullptr, 0, kProbesOnly, nullptr));
@@ -1265,6 +1374,7 @@ fpp_status fpp_debug_candidates(const fpp_index* cix, const float* Q, int64_t m,
   const int nt = pl.te - pl.tb;
   const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt, pl.pmax), m);
   FPP_TRY(prepare_workspace(ix, ix->ws, pl, mc, false, 0));
+  FPP_TRY(ix->ws.order_after_last(0));
   std::vector<uint64_t> eoff;
   std::vector<uint32_t> ucount, buf;
   for (int64_t q0 = 0; q0 < m; q0 += mc) {
@@ -1313,6 +1423,7 @@ fpp_status fpp_debug_projections(const fpp_index* cix, const float* Q, int64_t m
   const int64_t ldp = round_up(N, 4);
   const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt, pl.pmax, false), m);
   FPP_TRY(prepare_workspace(ix, ix->ws, pl, mc, false, 0, false));
+  FPP_TRY(ix->ws.order_after_last(0));
   FPP_CUDA(cudaMemset(ix->ws.stats.p, 0, 16 * 8));
   for (int64_t q0 = 0; q0 < m; q0 += mc) {
     const int64_t c = std::min<int64_t>(mc, m - q0);
