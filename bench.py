@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="serving workload: seconds of arrivals per offered rate")
     ap.add_argument("--slots", type=int, default=3, help="serving workload: batches in flight")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--graph", action="store_true",
                     help="time the steps as replays of the library's captured search graph")
     ap.add_argument("--no-e2e", action="store_true")
@@ -375,6 +376,12 @@ def main():
                                             [args.probes] if args.probes else list(w.probes))
         kpq = ppq = None
         search_kw = dict(k=k, probes=P)
+    # the library's autotuner picks the scoring kernel's launch shape on the
+    # workload's first batch (results do not depend on it)
+    tune = None
+    if not args.no_autotune:
+        tune = F.fpp_autotune(ix.handle, Qd, k if not per_query else 10,
+                              P if not per_query else 8)
     ids = torch.empty((m, k), dtype=torch.int64, device=dev)
     sc = torch.empty((m, k), dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
@@ -556,6 +563,7 @@ def main():
                        f"{w.n * w.d * 4 / 2**20:.0f} MiB), no flush",
                        "build_s": build_s, "index_kept_ids": info["kept_total"],
                        "max_bucket_kept": info["max_bucket_kept"], "cuda_graph": args.graph,
+                       "autotune": tune,
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"batch_p50": sm[len(sm) // 2], "batch_p99": sm[min(len(sm) - 1, int(0.99 * len(sm)))]},
             "roofline": roof,

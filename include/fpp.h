@@ -270,6 +270,23 @@ fpp_status fpp_bruteforce_static(const float* X, int64_t n, int32_t d, const flo
                                  int64_t m, int32_t k, int64_t* ids, float* scores,
                                  void* stream);
 
+/* Autotuner: runs the search once on Q [m][d] (host or device) with k and
+ * probes, then times the candidate-scoring kernel on the candidates of that
+ * batch under each launch shape it supports (lanes per candidate row x CTAs
+ * per resident slot) and keeps the fastest for every later search on this
+ * index (and on servers over it).  The results of searches do not depend on
+ * the shape.  report may be NULL.  Errors as fpp_search_ex. */
+typedef struct fpp_tune_report {
+  int32_t score_lanes;        /* lanes per candidate row chosen               */
+  int32_t score_waves;        /* CTAs per resident slot chosen                */
+  float ms_default;           /* scoring time with the built-in choice        */
+  float ms_best;              /* scoring time with the chosen shape           */
+  int32_t shapes_tried;
+  int32_t reserved0;
+} fpp_tune_report;
+fpp_status fpp_autotune(fpp_index* ix, const float* Q, int64_t m, int32_t k, int32_t probes,
+                        fpp_tune_report* report);
+
 /* ------------------------------------------------------------ serving
  *
  * A server answers a stream of independent search requests on one index with

@@ -74,6 +74,12 @@ class fpp_server_stats(ctypes.Structure):
                                                "batches", "queries", "entries", "probes")]
 
 
+class fpp_tune_report(ctypes.Structure):
+    _fields_ = [("score_lanes", ctypes.c_int32), ("score_waves", ctypes.c_int32),
+                ("ms_default", ctypes.c_float), ("ms_best", ctypes.c_float),
+                ("shapes_tried", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+
+
 class fpp_index_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("L", ctypes.c_int32),
                 ("D", ctypes.c_int32), ("iprobes", ctypes.c_int32), ("kappa", ctypes.c_int32),
@@ -125,6 +131,7 @@ def load(path: str | None = None):
         "fpp_bruteforce_static": (ctypes.c_int, [f32p, i64, i32, f32p, i64, i32, vp, vp, vp]),
         "fpp_launch_count": (u64, []),
         "fpp_merge_topk": (ctypes.c_int, [vp, vp, i32, i64, i32, vp, vp]),
+        "fpp_autotune": (ctypes.c_int, [vp, f32p, i64, i32, i32, ctypes.POINTER(fpp_tune_report)]),
         "fpp_default_server_cfg": (None, [ctypes.POINTER(fpp_server_cfg)]),
         "fpp_server_create": (ctypes.c_int, [vp, ctypes.POINTER(fpp_server_cfg),
                                              ctypes.POINTER(ctypes.c_void_p)]),
@@ -389,6 +396,14 @@ class Index:
             self.close()
         except Exception:
             pass
+
+
+def fpp_autotune(ix, Q, k: int, probes: int) -> dict:
+    """Tunes the scoring kernel's launch shape on one batch of Q; returns the report."""
+    Q = _f32(Q)
+    r = fpp_tune_report()
+    _check(load().fpp_autotune(ix, _ptr(Q), Q.shape[0], k, probes, ctypes.byref(r)))
+    return {f: getattr(r, f) for f, _ in r._fields_}
 
 
 def fpp_merge_topk(ids, scores):

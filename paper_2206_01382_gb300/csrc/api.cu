@@ -119,6 +119,7 @@ struct fpp_index {
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<uint64_t> graph_key;
   uint64_t graph_kernels = 0;  // kernel nodes of the graph
+  int tune_score_g = 0, tune_score_waves = 0;   // fpp_autotune's choice (0: built-in)
   float* rmax = nullptr;       // [2L]
   float xmax = 0.f;
   uint32_t* offsets = nullptr; // [L][4D^2 + 1]
@@ -677,6 +678,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   sa.X = ix->X; sa.ldx = ix->dpad; sa.Q = ws.qpad.as<float>(); sa.ldq = ix->dpad;
   sa.Xb = ix->Xb; sa.ldxb = ix->ldxb;
   sa.scores = ws.cscores.as<float>();
+  sa.tune_g = ix->tune_score_g; sa.tune_waves = ix->tune_score_waves;
   FPP_TRY(launch_score(sa, ix->sm_count, st));
   if (ev) FPP_CUDA(cudaEventRecord(ev[6], st));
   TopkArgs ta{};
@@ -1509,6 +1511,83 @@ fpp_status fpp_bruteforce(const float* X, int64_t n, int32_t d, const float* Q, 
   return done(FPP_OK);
 }
 
+
+fpp_status fpp_autotune(fpp_index* ix, const float* Q, int64_t m, int32_t k, int32_t probes,
+                        fpp_tune_report* report) {
+  g_err.clear();
+  fpp_search_opts o;
+  fpp_default_search_opts(&o);
+  o.k = k;
+  o.probes = probes;
+  o.k_max = k;
+  SearchPlan pl{};
+  int64_t dummy_i = 0;
+  float dummy_s = 0;
+  FPP_TRY(validate_search(ix, Q, m, &o, &dummy_i, &dummy_s, pl));
+  if (m < 1) { set_error("fpp_autotune needs at least one query"); return FPP_EINVAL; }
+  std::lock_guard<std::mutex> lock(ix->mu);
+  const int nt = pl.te - pl.tb;
+  const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt, pl.pmax), m);
+  Workspace& ws = ix->ws;
+  FPP_TRY(prepare_workspace(ix, ws, pl, mc, true, 0));
+  FPP_TRY(ws.order_after_last(0));
+  // one batch through the whole path leaves its candidates in the workspace
+  FPP_CUDA(cudaMemsetAsync(ws.stats.p, 0, 16 * 8, 0));
+  FPP_TRY(search_chunk(ix, ws, Q, 0, mc, pl, ws.out_ids.as<int64_t>(), ws.out_scores.as<float>(), 0,
+                       kFull, nullptr));
+  FPP_CUDA(cudaDeviceSynchronize());
+  ScoreArgs sa{};
+  sa.items = ws.items.as<ScoreItem>();
+  sa.nitems = reinterpret_cast<unsigned*>(ws.stats.as<unsigned long long>() + 10);
+  sa.eoff = ws.eoff.as<uint64_t>(); sa.mq = mc;
+  sa.cand = ws.cand.as<uint32_t>();
+  sa.X = ix->X; sa.ldx = ix->dpad; sa.Q = ws.qpad.as<float>(); sa.ldq = ix->dpad;
+  sa.Xb = ix->Xb; sa.ldxb = ix->ldxb;
+  sa.scores = ws.cscores.as<float>();
+  cudaEvent_t e0, e1;
+  FPP_CUDA(cudaEventCreate(&e0));
+  FPP_CUDA(cudaEventCreate(&e1));
+  auto time_shape = [&](int g, int waves, float* ms) -> fpp_status {
+    sa.tune_g = g;
+    sa.tune_waves = waves;
+    float best = 1e30f;
+    for (int r = 0; r < 4; ++r) {   // the first run warms up, the best of the rest counts
+      FPP_CUDA(cudaEventRecord(e0, 0));
+      FPP_TRY(launch_score(sa, ix->sm_count, 0));
+      FPP_CUDA(cudaEventRecord(e1, 0));
+      FPP_CUDA(cudaEventSynchronize(e1));
+      float t = 0.f;
+      FPP_CUDA(cudaEventElapsedTime(&t, e0, e1));
+      if (r > 0) best = std::min(best, t);
+    }
+    *ms = best;
+    return FPP_OK;
+  };
+  fpp_tune_report rep{};
+  fpp_status st = time_shape(0, 0, &rep.ms_default);
+  int best_g = 0, best_w = 0;
+  float best_ms = rep.ms_default;
+  const int chunks = ix->precision == FPP_BF16 ? (int)(ix->ldxb / 8) : ix->dpad / 4;
+  for (int g = 1; g <= 32 && st == FPP_OK; g <<= 1) {
+    if (g * 8 < chunks || g > 2 * chunks) continue;   // shapes the kernels instantiate well
+    for (int w : {1, 2, 3, 4, 6, 8}) {
+      float ms = 0.f;
+      if ((st = time_shape(g, w, &ms)) != FPP_OK) break;
+      ++rep.shapes_tried;
+      if (ms < best_ms * 0.98f) { best_ms = ms; best_g = g; best_w = w; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != FPP_OK) return st;
+  ix->tune_score_g = best_g;
+  ix->tune_score_waves = best_w;
+  rep.score_lanes = best_g;
+  rep.score_waves = best_w;
+  rep.ms_best = best_ms;
+  if (report) *report = rep;
+  return FPP_OK;
+}
 
 fpp_status fpp_merge_topk(const int64_t* ids, const float* scores, int32_t parts, int64_t m,
                           int32_t k, int64_t* out_ids, float* out_scores) {

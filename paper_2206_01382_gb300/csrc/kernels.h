@@ -184,6 +184,8 @@ struct ScoreArgs {
   const void* Xb;            // BF16 rows [n][ldxb] (precision path) or NULL
   int64_t ldxb;
   float* scores;             // FP32 scores, parallel to cand
+  int tune_g;                // lanes per row (power of two) or 0: heuristic
+  int tune_waves;            // CTAs per resident slot or 0: default
 };
 
 struct TopkArgs {

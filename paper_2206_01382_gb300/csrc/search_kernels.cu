@@ -372,14 +372,73 @@ __device__ void probe_exact_select(const double* dv, int D, int P, SD* lists, SD
   __syncthreads();
 }
 
+// Small budgets (P <= 16): the same selection by one warp, E rounds of warp
+// maximum per list and P rounds over the pairs.
+__device__ void probe_exact_select_warp(const double* dv, int D, int P, unsigned char* wsm,
+                                        uint32_t* bucket_out) {
+  const int lane = threadIdx.x & 31;
+  DEntry* top = reinterpret_cast<DEntry*>(wsm);                              // 2 x LIST_CAP
+  DEntry* pairs = reinterpret_cast<DEntry*>(wsm + (size_t)2 * LIST_CAP * 16);  // SLOW_PAIRS
+  const int W2 = 2 * D;
+  const int E = P < W2 ? P : W2;
+  for (int j = 0; j < 2; ++j) {
+    uint64_t taken = 0ull;  // bit s: wedge lane + 32 s already selected
+    for (int r = 0; r < E; ++r) {
+      double bv = -INFINITY;
+      uint32_t bh = 0xFFFFFFFFu;
+      for (int s = 0; s * 32 + lane < W2; ++s) {
+        if (taken & (1ull << s)) continue;
+        const uint32_t h = s * 32 + lane;
+        const double v = h < (uint32_t)D ? dv[j * D + h] : -dv[j * D + h - D];
+        if (dentry_before(v, h, bv, bh)) { bv = v; bh = h; }
+      }
+      warp_best(bv, bh);
+      if ((int)(bh & 31) == lane) taken |= 1ull << (bh >> 5);
+      if (lane == 0) top[j * LIST_CAP + r] = DEntry{bv, bh, 0};
+    }
+  }
+  __syncwarp();
+  int C = 0;
+  for (int ai = 0; ai < E; ++ai) {
+    int nb = P / (ai + 1);
+    if (nb > E) nb = E;
+    if (nb <= 0) break;
+    for (int b = lane; b < nb; b += 32) {
+      const DEntry x = top[ai], y = top[LIST_CAP + b];
+      pairs[C + b] = DEntry{x.v + y.v, x.h * (uint32_t)W2 + y.h, 0};
+    }
+    C += nb;
+  }
+  __syncwarp();
+  unsigned taken = 0u;
+  for (int r = 0; r < P; ++r) {
+    double bv = -INFINITY;
+    uint32_t bh = 0xFFFFFFFFu;
+    int bs = -1;
+    for (int s = 0; s * 32 + lane < C; ++s) {
+      if (taken & (1u << s)) continue;
+      const DEntry e = pairs[s * 32 + lane];
+      if (dentry_before(e.v, e.h, bv, bh)) { bv = e.v; bh = e.h; bs = s; }
+    }
+    // bucket ids of distinct pairs are distinct, so the owner lane is unique
+    double wv = bv;
+    uint32_t wh = bh;
+    warp_best(wv, wh);
+    if (bs >= 0 && bh == wh) taken |= 1u << bs;
+    if (lane == 0) bucket_out[r] = wh;
+  }
+  __syncwarp();
+}
+
 constexpr int RECHECK_THREADS = 256;
 
 // dv [2D] doubles, two sorted signed lists of pow2(2D) entries, and the
 // candidate pairs (at most P (1 + ln P) <= 1024 for P <= 128 ... bounded by
 // pair_count(P, ...) <= SLOW_PAIRS)
 __host__ __device__ inline size_t recheck_smem_bytes(int D) {
-  return (size_t)8 * 2 * D + (size_t)2 * pow2_ceil(2 * D) * sizeof(SD) +
-         (size_t)SLOW_PAIRS * sizeof(SD);
+  const size_t lists = (size_t)2 * pow2_ceil(2 * D) * sizeof(SD);
+  const size_t wtop = (size_t)2 * LIST_CAP * sizeof(DEntry);   // the one-warp selection
+  return (size_t)8 * 2 * D + (lists > wtop ? lists : wtop) + (size_t)SLOW_PAIRS * sizeof(SD);
 }
 
 // One CTA per (query, table) item of the recheck list: its warps compute the
@@ -417,9 +476,14 @@ probe_recheck_kernel(ProbeArgs a) {
       }
     }
     __syncthreads();
-    SD* lists = reinterpret_cast<SD*>(wsm);
-    probe_exact_select(dv, a.D, P, lists, lists + 2 * pow2_ceil(2 * a.D),
-                       a.out + (q * a.nt + tl) * (int64_t)a.probes);
+    uint32_t* dst = a.out + (q * a.nt + tl) * (int64_t)a.probes;
+    if (P <= 16) {
+      if (wid == 0) probe_exact_select_warp(dv, a.D, P, wsm, dst);
+      __syncthreads();
+    } else {
+      SD* lists = reinterpret_cast<SD*>(wsm);
+      probe_exact_select(dv, a.D, P, lists, lists + 2 * pow2_ceil(2 * a.D), dst);
+    }
   }
 }
 
@@ -1387,7 +1451,7 @@ fpp_status launch_resident(Kernel* k, int sms, const ScoreArgs& a, std::atomic<i
     b = std::max(1, b);
     per_sm.store(b, std::memory_order_relaxed);
   }
-  k<<<b * sms * SCORE_WAVES, 256, 0, st>>>(a);
+  k<<<b * sms * (a.tune_waves > 0 ? a.tune_waves : SCORE_WAVES), 256, 0, st>>>(a);
   FPP_LAUNCHED();
   return FPP_OK;
 }
@@ -1550,6 +1614,7 @@ fpp_status launch_score(const ScoreArgs& a, int sm_count, cudaStream_t st) {
     int g = 1;
     const int nch = (int)(a.ldxb / 8);
     while (g < 32 && g * 2 < nch) g <<= 1;
+    if (a.tune_g) g = a.tune_g;
     switch (g) {
       case 1: return launch_score_bf<1>(a, grid, st);
       case 2: return launch_score_bf<2>(a, grid, st);
@@ -1559,7 +1624,7 @@ fpp_status launch_score(const ScoreArgs& a, int sm_count, cudaStream_t st) {
       default: return launch_score_bf<32>(a, grid, st);
     }
   }
-  switch (choose_g((int)(a.ldx / 4))) {
+  switch (a.tune_g ? a.tune_g : choose_g((int)(a.ldx / 4))) {
     case 1: return launch_score_g<1>(a, grid, st);
     case 2: return launch_score_g<2>(a, grid, st);
     case 4: return launch_score_g<4>(a, grid, st);

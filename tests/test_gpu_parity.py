@@ -311,3 +311,15 @@ def test_graph_replay_equals_plain_calls(F):
         assert np.array_equal(ids.cpu().numpy(), gi)
         assert np.array_equal(sc.cpu().numpy(), gs)
     assert F.fpp_launch_count() - n0 > 4 * 8   # graph kernels are counted at each replay
+
+
+def test_autotune_keeps_results(F):
+    X, Q = W.small_mixture(40000, 500, 96, 64, 0.25, 94)
+    for prec in (F.FPP_FP32, F.FPP_BF16):
+        ix = F.Index(X, 8, 64, 0.2, seed=8, precision=prec)
+        gi, gs = ix.search(Q, 10, 2)
+        rep = F.fpp_autotune(ix.handle, Q, 10, 2)
+        assert rep["shapes_tried"] >= 4
+        assert 0 < rep["ms_best"] <= rep["ms_default"] * 1.0001
+        ti, ts = ix.search(Q, 10, 2)
+        assert np.array_equal(gi, ti) and np.array_equal(gs, ts)
