@@ -70,7 +70,8 @@ struct DevBuf {
 };
 
 struct Workspace {
-  DevBuf qpad, qsplit, proj, probes, qnorm, recheck, recheck2, kpq, ppq, out_ids, out_scores,
+  DevBuf qpad, qsplit, proj, probes, qnorm, recheck, recheck2, recheck_s, kpq, ppq, out_ids,
+      out_scores,
       ecount, eoff, scan, cand, cscores, items, tkslow, stats;
   // completion of the last call that used this workspace: a call on another
   // stream waits for it before touching the buffers
@@ -89,7 +90,7 @@ struct Workspace {
   }
   uint64_t cand_cap = 0;    // candidate slots in cand / cscores
   void release() {
-    for (DevBuf* b : {&qpad, &qsplit, &proj, &probes, &qnorm, &recheck, &recheck2, &kpq, &ppq,
+    for (DevBuf* b : {&qpad, &qsplit, &proj, &probes, &qnorm, &recheck, &recheck2, &recheck_s, &kpq, &ppq,
                       &out_ids, &out_scores, &ecount, &eoff, &scan, &cand, &cscores,
                       &items, &tkslow, &stats})
       b->release();
@@ -628,6 +629,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   pa.recheck_count = reinterpret_cast<unsigned*>(ws.stats.as<unsigned long long>() + 8);
   pa.recheck2 = ws.recheck2.as<uint32_t>();
   pa.recheck2_count = reinterpret_cast<unsigned*>(ws.stats.as<unsigned long long>() + 8) + 1;
+  pa.recheck_s = EL ? nullptr : ws.recheck_s.as<float>();   // pair-window pass (stored projections)
   pa.rechecks = ws.stats.as<unsigned long long>() + 6;
   FPP_TRY(launch_probe(pa, st, ev ? ev[4] : nullptr));
   if (ev) FPP_CUDA(cudaEventRecord(ev[2], st));
@@ -720,6 +722,7 @@ fpp_status prepare_workspace(fpp_index* ix, Workspace& ws, const SearchPlan& pl,
   FPP_TRY(ws.qnorm.ensure((size_t)mc * 4, false, st));
   FPP_TRY(ws.recheck.ensure((size_t)mc * nt * 4, false, st));
   FPP_TRY(ws.recheck2.ensure((size_t)mc * nt * 4, false, st));
+  FPP_TRY(ws.recheck_s.ensure((size_t)mc * nt * 8, false, st));
   FPP_TRY(ws.kpq.ensure((size_t)mc * 4, false, st));
   FPP_TRY(ws.ppq.ensure((size_t)mc * 4, false, st));
   FPP_TRY(ws.stats.ensure(16 * 8, true, st));

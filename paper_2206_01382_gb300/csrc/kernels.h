@@ -140,6 +140,8 @@ struct ProbeArgs {
   unsigned* recheck_count;   // device counter of recheck items
   uint32_t* recheck2;        // [mq * nt] items the window pass could not settle
   unsigned* recheck2_count;
+  float* recheck_s;          // [mq * nt][2] the FP32 P-th and (P+1)-th pair scores of
+                             // each recheck item (stored projections), or NULL
   unsigned long long* rechecks;  // statistics counter or NULL
 };
 fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_begin = nullptr);

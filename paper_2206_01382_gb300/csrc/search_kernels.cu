@@ -217,6 +217,11 @@ probe_kernel(ProbeArgs a, int pmax) {
   } else if (lane == 0) {
     const unsigned slot = atomicAdd(a.recheck_count, 1u);
     a.recheck[slot] = (uint32_t)(q * a.nt + tl);
+    if (a.recheck_s) {   // the boundary the window pass re-decides (NaN: none)
+      const bool have = boundary && C >= Tsel;
+      a.recheck_s[2 * slot] = have ? key_score(pout[P - 1]) : __int_as_float(0x7fc00000);
+      a.recheck_s[2 * slot + 1] = have ? key_score(pout[P]) : __int_as_float(0x7fc00000);
+    }
     if (a.rechecks) atomicAdd(a.rechecks, 1ull);
   }
 }
@@ -450,8 +455,9 @@ probe_recheck_kernel(ProbeArgs a) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = RECHECK_THREADS / 32;
   double* dv = reinterpret_cast<double*>(smem);
   unsigned char* wsm = smem + (size_t)8 * 2 * a.D;
-  const unsigned cnt = a.lists ? *a.recheck2_count : *a.recheck_count;
-  const uint32_t* items = a.lists ? a.recheck2 : a.recheck;
+  const bool after_window = a.lists || a.recheck_s;
+  const unsigned cnt = after_window ? *a.recheck2_count : *a.recheck_count;
+  const uint32_t* items = after_window ? a.recheck2 : a.recheck;
   const int rows = 2 * a.D;
   const int nf4 = (int)(a.ldr / 4);
   for (unsigned it = blockIdx.x; it < cnt; it += gridDim.x) {
@@ -579,6 +585,166 @@ probe_window_kernel(ProbeArgs a) {
         dst[r] = pb[r];
       }
     }
+    __syncwarp();
+  }
+}
+
+// Pair-window pass (stored projections): a (query, table) whose FP32 probe
+// boundary sP (P-th pair score) / sP1 ((P+1)-th) was inside the error bound
+// is settled from exact values of only the pairs near the boundary.  With
+// every FP32 pair score within delta of the exact one, a pair scoring above
+// sP1 + 2 delta is in the exact top-P, a pair below sP - 2 delta is out, and
+// the top-P is those above plus the best of the window pairs in between by
+// exact score.  Every pair scoring at least tau = sP - 2 delta has both
+// entries at least tau minus the other list's maximum, so the candidate
+// entries of each list are found by a scan; their pairs are classified, and
+// the entries of window pairs get compensated (FP64-accurate) values.  An
+// item with more than 32 candidate entries in a list or 64 window pairs goes
+// to the full pass.
+constexpr int PW_CAND = 32;
+constexpr int PW_WIN = 64;
+
+struct PWinShared {
+  uint32_t ch[2][PW_CAND];
+  float cv[2][PW_CAND];
+  double ev[2][PW_CAND];
+  uint32_t need[2];            // bit c: candidate c is in a window pair
+  uint16_t wa[PW_WIN], wb[PW_WIN];
+  SD ws[PW_WIN];
+  unsigned nwin, nin;
+};
+
+__global__ void __launch_bounds__(256)
+probe_pwin_kernel(ProbeArgs a) {
+  __shared__ PWinShared shm[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  PWinShared& sh = shm[wid];
+  const unsigned cnt = *a.recheck_count;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int nf4 = (int)(a.ldr / 4);
+  for (unsigned it = blockIdx.x * (blockDim.x >> 5) + wid; it < cnt; it += nwarps) {
+    const uint32_t item = a.recheck[it];
+    const int64_t q = item / a.nt;
+    const int tl = (int)(item % a.nt);
+    const int t = a.tb + tl;
+    const int P = a.probes_pq ? a.probes_pq[q] : a.probes;
+    const int D = a.D;
+    const float sP = a.recheck_s[2 * it], sP1 = a.recheck_s[2 * it + 1];
+    auto give_up = [&]() {
+      if (lane == 0) a.recheck2[atomicAdd(a.recheck2_count, 1u)] = item;
+    };
+    if (isnan(sP) || isnan(sP1)) { give_up(); continue; }
+    const float* pr[2] = {a.P + q * a.ldp + (int64_t)(2 * tl) * D,
+                          a.P + q * a.ldp + (int64_t)(2 * tl + 1) * D};
+    float vmax[2];
+    for (int j = 0; j < 2; ++j) {
+      float m = 0.f;
+      for (int i = lane; i < D; i += 32) m = fmaxf(m, fabsf(pr[j][i]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, o));
+      vmax[j] = m;
+    }
+    // per-pair bound: the projections' error plus the rounding of the FP32
+    // sum (every pair score is at most vmax[0] + vmax[1] in magnitude)
+    const float eps = a.gammaf * a.qnorm[q] * (a.rmax[2 * t] + a.rmax[2 * t + 1]);
+    const float delta = (eps + 6.0e-8f * (vmax[0] + vmax[1] + fabsf(sP) + fabsf(sP1))) * 1.001f + 1e-30f;
+    const float tau = sP - 2.f * delta, hi = sP1 + 2.f * delta;
+    // candidate entries (signed wedges h in [0, 2D)) of each list
+    int nc[2] = {0, 0};
+    bool over = false;
+    for (int j = 0; j < 2 && !over; ++j) {
+      const float lim = (tau - vmax[1 - j]) - 1e-6f * (fabsf(tau) + vmax[1 - j]);
+      for (int h0 = 0; h0 < 2 * D; h0 += 32) {
+        const int h = h0 + lane;
+        float v = 0.f;
+        bool in = false;
+        if (h < 2 * D) {
+          const float p = pr[j][h < D ? h : h - D];
+          v = h < D ? p : -p;
+          in = v >= lim;
+        }
+        const unsigned m = __ballot_sync(FULL, in);
+        if (in) {
+          const int slot = nc[j] + __popc(m & ((1u << lane) - 1u));
+          if (slot < PW_CAND) { sh.ch[j][slot] = (uint32_t)h; sh.cv[j][slot] = v; }
+        }
+        nc[j] += __popc(m);
+      }
+      if (nc[j] > PW_CAND) over = true;
+    }
+    if (over) { give_up(); continue; }
+    if (lane == 0) { sh.nwin = 0; sh.nin = 0; sh.need[0] = sh.need[1] = 0u; }
+    __syncwarp();
+    // classify the pairs of candidates: lane x takes list-1 candidate x
+    if (lane < nc[0]) {
+      const float x = sh.cv[0][lane];
+      unsigned nin = 0;
+      for (int y = 0; y < nc[1]; ++y) {
+        const float s2 = x + sh.cv[1][y];   // the fast pass's FP32 pair score
+        if (s2 > hi) {
+          ++nin;
+        } else if (s2 >= tau) {
+          const unsigned w = atomicAdd(&sh.nwin, 1u);
+          if (w < PW_WIN) { sh.wa[w] = (uint16_t)lane; sh.wb[w] = (uint16_t)y; }
+          atomicOr(&sh.need[0], 1u << lane);
+          atomicOr(&sh.need[1], 1u << y);
+        }
+      }
+      atomicAdd(&sh.nin, nin);
+    }
+    __syncwarp();
+    const unsigned nwin = sh.nwin, nin = sh.nin;
+    if (nwin > (unsigned)PW_WIN || nin > (unsigned)P || nin + nwin < (unsigned)P) {
+      give_up();
+      continue;
+    }
+    // compensated values of the candidates in window pairs
+    const float* qv = a.Q + q * a.ldq;
+    for (int j = 0; j < 2; ++j) {
+      const unsigned need = sh.need[j];
+      for (int c0 = 0; c0 < nc[j]; c0 += 8) {
+        const float* rows[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int c = min(c0 + u, nc[j] - 1);
+          rows[u] = a.R + ((int64_t)(2 * t + j) * D + (sh.ch[j][c] % (uint32_t)D)) * a.ldr;
+        }
+        if (!(need >> c0 & 0xFFu)) continue;
+        double v[8];
+        warp_dot2_gather<8>(qv, rows, nf4, v);
+        if (lane == 0)
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (c0 + u < nc[j]) sh.ev[j][c0 + u] = sh.ch[j][c0 + u] < (uint32_t)D ? v[u] : -v[u];
+      }
+    }
+    __syncwarp();
+    // exact window pair scores, best first (score desc, bucket asc)
+    const int NW = 64;
+    for (int w = lane; w < NW; w += 32) {
+      if (w < (int)nwin) {
+        const int x = sh.wa[w], y = sh.wb[w];
+        sh.ws[w] = SD{sh.ev[0][x] + sh.ev[1][y], sh.ch[0][x] * (uint32_t)(2 * D) + sh.ch[1][y], 0};
+      } else {
+        sh.ws[w] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+      }
+    }
+    __syncwarp();
+    warp_sort_sd(sh.ws, NW);
+    // output: the certain pairs, then the best P - nin window pairs
+    uint32_t* dst = a.out + (q * a.nt + tl) * (int64_t)a.probes;
+    if (lane == 0) sh.nin = 0;
+    __syncwarp();
+    if (lane < nc[0]) {
+      const float x = sh.cv[0][lane];
+      for (int y = 0; y < nc[1]; ++y)
+        if (x + sh.cv[1][y] > hi) {
+          const unsigned o = atomicAdd(&sh.nin, 1u);
+          dst[o] = sh.ch[0][lane] * (uint32_t)(2 * D) + sh.ch[1][y];
+        }
+    }
+    __syncwarp();
+    for (int w = lane; w < P - (int)nin; w += 32) dst[nin + w] = sh.ws[w].id;
     __syncwarp();
   }
 }
@@ -1498,7 +1664,7 @@ fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_b
     return FPP_EINVAL;
   }
   FPP_CUDA(cudaMemsetAsync(a.recheck_count, 0, sizeof(unsigned), st));
-  if (a.lists) FPP_CUDA(cudaMemsetAsync(a.recheck2_count, 0, sizeof(unsigned), st));
+  if (a.lists || a.recheck_s) FPP_CUDA(cudaMemsetAsync(a.recheck2_count, 0, sizeof(unsigned), st));
   const int S = pow2_ceil((a.D + 31) / 32);
   fpp_status s;
   if (a.lists && a.probes + 1 <= a.EL && a.EL <= SMALL_E) {
@@ -1520,6 +1686,9 @@ fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_b
   cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, dev0);
   if (a.lists) {
     probe_window_kernel<<<sms0 * 2, 256, 0, st>>>(a);
+    FPP_LAUNCHED();
+  } else if (a.recheck_s) {
+    probe_pwin_kernel<<<sms0 * 2, 256, 0, st>>>(a);
     FPP_LAUNCHED();
   }
   // exact pass over the items the fast pass could not decide; the grid is
