@@ -26,6 +26,7 @@ from .falconn import (  # noqa: F401
     OracleIndex,
     brute_force,
     build_index,
+    center_points,
     cross_polytope_hash,
     keep_count,
     probe_buckets,

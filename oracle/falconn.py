@@ -225,17 +225,37 @@ def build_table(X64, Rt, alpha, iprobes=1, kappa=0):
     return offsets, ids, counts, point_bucket, hash_flag, filter_flag
 
 
+def center_points(X, c=None):
+    """Centering (Section 3.4, heuristic (1)): c = the mean of the points,
+    x -> x - c.  c is the FP64 mean rounded to FP32 (or the given vector);
+    each centered coordinate is the FP32 rounding of the exact difference.
+    Returns (c as FP32, centered points as FP32)."""
+    X32 = np.asarray(X, dtype=np.float32)
+    if c is None:
+        c = X32.astype(np.float64).mean(axis=0)
+    c32 = np.asarray(c, dtype=np.float32)
+    Xc = (X32.astype(np.float64) - c32.astype(np.float64)).astype(np.float32)
+    return c32, Xc
+
+
 def build_index(X, L: int, D: int, alpha: float, seed: int | None = None,
                 R: np.ndarray | None = None, iprobes: int = 1, kappa: int = 0,
-                tables=None) -> OracleIndex:
+                tables=None, center: bool = False, c=None) -> OracleIndex:
     """Build the index over ``X`` [n][d] (FP32 or FP64 input, promoted).
 
     R comes from ``seed`` through the rotation generator, or is given.
     ``tables`` restricts the build to a subset of table numbers (the other
     tables are left empty) so that full-size cases can be checked table by
-    table."""
+    table.  ``center``: the tables are built over the centered points
+    x - c (Section 3.4, heuristic (1); queries are not centered, and search
+    scores stay the inner products with the original points, whose order
+    the centering does not change)."""
     X64 = np.asarray(X, dtype=np.float64)
     n, d = X64.shape
+    Xh = X64
+    if center:
+        _, Xc = center_points(X, c)
+        Xh = Xc.astype(np.float64)
     if R is None:
         R = gaussian_rotations(seed, L, D, d)
     R64 = np.asarray(R, dtype=np.float64).reshape(L, 2, D, d)
@@ -247,8 +267,8 @@ def build_index(X, L: int, D: int, alpha: float, seed: int | None = None,
     hflag = np.zeros((L, n), dtype=bool)
     fflag = np.zeros((L, NB), dtype=bool)
     for t in (range(L) if tables is None else tables):
-        o, i, c, b, hf, ff = build_table(X64, R64[t], alpha, iprobes, kappa)
-        offsets[t], ids[t], counts[t], hflag[t], fflag[t] = o, i, c, hf, ff
+        o, i, cnt, b, hf, ff = build_table(Xh, R64[t], alpha, iprobes, kappa)
+        offsets[t], ids[t], counts[t], hflag[t], fflag[t] = o, i, cnt, hf, ff
         if pb is not None:
             pb[t] = b
     return OracleIndex(n, d, L, D, float(alpha), iprobes, kappa, R64, X64,

@@ -352,3 +352,50 @@ def test_ceos_projection_preserves_inner_product_order():
     # asymptotic value c * sqrt(2 ln D) = 2.13; the finite-D mean of the top
     # order statistic is a little smaller, so a band of +-20%
     assert 0.8 * c * math.sqrt(2 * math.log(D)) < mean < 1.2 * c * math.sqrt(2 * math.log(D))
+
+
+def test_centering_transform_pinned():
+    # Section 3.4, heuristic (1): c is the mean of the points and x -> x - c,
+    # here on values where every step is exact
+    X = np.array([[1.0, 2.0, -3.0], [3.0, 4.0, 5.0]], dtype=np.float32)
+    c, Xc = O.center_points(X)
+    assert c.tolist() == [2.0, 3.0, 1.0]
+    assert Xc.tolist() == [[-1.0, -1.0, -4.0], [1.0, 1.0, 4.0]]
+    # an explicit centre is used as given
+    c2, Xc2 = O.center_points(X, np.array([1.0, 1.0, 1.0]))
+    assert Xc2.tolist() == [[0.0, 1.0, -4.0], [2.0, 3.0, 4.0]]
+
+
+def test_centered_index_is_the_index_of_centered_points():
+    # the centered build hashes and filters the centered points, so its
+    # tables equal those of a plain build over x - c; the search still
+    # scores the original points
+    import workloads as W
+    X, Q = W.small_mixture(3000, 20, 24, 16, 0.3, 81)
+    X = X + np.float32(0.2)   # a common offset, then centering
+    ixc = O.build_index(X, 4, 8, 0.5, seed=5, center=True)
+    _, Xc = O.center_points(X)
+    ixp = O.build_index(Xc, 4, 8, 0.5, seed=5)
+    for t in range(4):
+        assert np.array_equal(ixc.offsets[t], ixp.offsets[t])
+        assert np.array_equal(ixc.ids[t], ixp.ids[t])
+    ids, sc, _ = O.search_batch(ixc, Q, 5, 2)
+    X64, Q64 = X.astype(np.float64), Q.astype(np.float64)
+    for i in range(len(Q)):
+        ok = ids[i] >= 0
+        assert np.allclose(sc[i][ok], X64[ids[i][ok]] @ Q64[i], rtol=0, atol=1e-12)
+
+
+def test_centering_spreads_skewed_data_over_buckets():
+    # the point of centering (Section 3.4): data crowded on one area of the
+    # sphere falls into few buckets; after centering it spreads out
+    rng = np.random.default_rng(12)
+    d = 32
+    base = np.zeros(d); base[0] = 1.0
+    X = base + 0.15 * rng.standard_normal((4000, d))
+    X = (X / np.linalg.norm(X, axis=1, keepdims=True)).astype(np.float32)
+    plain = O.build_index(X, 2, 8, 1.0, seed=3)
+    cent = O.build_index(X, 2, 8, 1.0, seed=3, center=True)
+    for t in range(2):
+        assert cent.counts[t].max() < 0.5 * plain.counts[t].max()
+        assert np.count_nonzero(cent.counts[t]) > np.count_nonzero(plain.counts[t])
