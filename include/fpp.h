@@ -83,6 +83,12 @@ typedef struct fpp_params {
   int32_t precision;   /* fpp_precision                                      */
   int32_t rerank_k;    /* FPP_BF16: shortlist length (default 100), 0..256  */
   void* stream;        /* cudaStream_t for the build, or NULL (legacy)       */
+  int32_t center;      /* 1: build the tables over the centered points x - c
+                          (Section 3.4, heuristic (1)); queries are not
+                          centered and scores stay x^T q (default 0)        */
+  int32_t reserved1;
+  const float* center_vec; /* optional c [d] (host or device); NULL = the
+                          FP64 column means of X rounded to FP32            */
 } fpp_params;
 
 /* Per-call search options.  Initialise with fpp_default_search_opts(). */
@@ -141,6 +147,7 @@ typedef struct fpp_index_info {
   uint64_t device_bytes;      /* device memory held by the index              */
   float build_ms;             /* wall time of fpp_build                        */
   int32_t rerank_k;           /* FPP_BF16 shortlist length (0 for FPP_FP32)    */
+  int32_t center;             /* 1: the tables hash the centered points        */
   double score_error_factor;  /* c: a candidate's first-pass score is within
                                  c ||q|| ||x|| of x^T q (FPP_FP32: the FP32
                                  bound gamma_d; FPP_BF16: the statistical

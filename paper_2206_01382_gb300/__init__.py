@@ -38,7 +38,9 @@ class fpp_params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("D", ctypes.c_int32), ("iprobes", ctypes.c_int32),
                 ("kappa", ctypes.c_int32), ("alpha", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("R", ctypes.c_void_p), ("precision", ctypes.c_int32),
-                ("rerank_k", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("rerank_k", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("center", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+                ("center_vec", ctypes.c_void_p)]
 
 
 class fpp_search_opts(ctypes.Structure):
@@ -86,7 +88,8 @@ class fpp_index_info(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("alpha", ctypes.c_double),
                 ("kept_total", ctypes.c_uint64), ("max_bucket_kept", ctypes.c_uint32),
                 ("device_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_float),
-                ("rerank_k", ctypes.c_int32), ("score_error_factor", ctypes.c_double)]
+                ("rerank_k", ctypes.c_int32), ("center", ctypes.c_int32),
+                ("score_error_factor", ctypes.c_double)]
 
 
 _lib = None
@@ -217,13 +220,16 @@ def fpp_default_params() -> fpp_params:
 
 def fpp_build(X, L: int, D: int, alpha: float, seed: int = 0, R=None, iprobes: int = 1,
               kappa: int = 0, precision: int = FPP_FP32, rerank_k: int = 100,
-              stream=None) -> ctypes.c_void_p:
+              center: bool = False, center_vec=None, stream=None) -> ctypes.c_void_p:
     """Builds an index over X [n][d]; returns the opaque handle."""
     lib = load()
     X = _f32(X)
     p = fpp_default_params()
     p.L, p.D, p.alpha, p.seed = L, D, float(alpha), int(seed)
     p.iprobes, p.kappa, p.precision, p.rerank_k = iprobes, kappa, precision, rerank_k
+    p.center = 1 if center else 0
+    cv = _f32(center_vec) if center_vec is not None else None
+    p.center_vec = _ptr(cv)
     Rc = _f32(R) if R is not None else None
     p.R = _ptr(Rc)
     p.stream = _stream_ptr(stream)

@@ -107,6 +107,9 @@ struct fpp_index {
   int d = 0, dpad = 0, L = 0, D = 0, iprobes = 1, kappa = 0, precision = 0;
   double alpha = 1.0;
   float* X = nullptr;          // [n][dpad]
+  float* Xc = nullptr;         // [n][dpad] centered points (center = 1), else NULL
+  float* c = nullptr;          // [dpad] the center (center = 1)
+  int center = 0;
   float* R = nullptr;          // [2 L D][dpad]
   void* Rs = nullptr;          // [2 L D][pieces Kp] BF16 pieces of R (tensor-core operand)
   int Kp = 0;
@@ -122,7 +125,8 @@ struct fpp_index {
   uint64_t graph_kernels = 0;  // kernel nodes of the graph
   int tune_score_g = 0, tune_score_waves = 0;   // fpp_autotune's choice (0: built-in)
   float* rmax = nullptr;       // [2L]
-  float xmax = 0.f;
+  float xmax = 0.f;            // largest point norm (inflated)
+  float xhmax = 0.f;           // largest norm of the hashed rows (the centered points when centering)
   uint32_t* offsets = nullptr; // [L][4D^2 + 1]
   uint64_t* table_base = nullptr;  // [L]
   uint32_t* ids = nullptr;
@@ -157,6 +161,8 @@ fpp_status to_device_padded(const float* src, int64_t rows, int d, int dpad, flo
 
 void free_index_memory(fpp_index* ix) {
   cudaFree(ix->X);
+  cudaFree(ix->Xc);
+  cudaFree(ix->c);
   cudaFree(ix->R);
   cudaFree(ix->Rs);
   cudaFree(ix->Xb);
@@ -191,6 +197,10 @@ int sig_bits(uint64_t v) {
   while (v) { ++b; v >>= 1; }
   return b;
 }
+
+// The rows the tables hash and filter: the centered points when the index
+// centers (Section 3.4, heuristic (1)), else the points.
+const float* hashed_rows(const fpp_index* ix) { return ix->Xc ? ix->Xc : ix->X; }
 
 // Builds tables [t0, t0 + nt) and appends their kept ids.
 struct BuildScratch {
@@ -258,13 +268,13 @@ fpp_status build_tables(fpp_index* ix, int t0, int nt, BuildScratch& B, cudaStre
 
   for (int64_t r0 = 0; r0 < n; r0 += rows) {
     const int64_t rc = std::min<int64_t>(rows, n - r0);
-    FPP_TRY(project_rows(ix, ix->X + r0 * ix->dpad, rc, B.xsplit, t0, nt, B.proj.as<float>(), ldp,
+    FPP_TRY(project_rows(ix, hashed_rows(ix) + r0 * ix->dpad, rc, B.xsplit, t0, nt, B.proj.as<float>(), ldp,
                          reinterpret_cast<int*>(B.rechecks.as<unsigned long long>() + 1), st,
                          EL ? B.proj.as<uint64_t>() : nullptr, EL));
     if (ip > 1) {
       // Algorithm 1 with iProbes > 1: each point goes into the iProbes
       // buckets it ranks highest, by the same exact ranking as a query
-      const float* xr = ix->X + r0 * ix->dpad;
+      const float* xr = hashed_rows(ix) + r0 * ix->dpad;
       FPP_TRY(launch_query_norms(xr, rc, ix->dpad, ix->d, B.norms.as<float>(), st));
       ProbeArgs pa{};
       pa.P = EL ? nullptr : B.proj.as<float>(); pa.ldp = ldp; pa.mq = rc;
@@ -283,7 +293,7 @@ fpp_status build_tables(fpp_index* ix, int t0, int nt, BuildScratch& B, cudaStre
       FPP_TRY(launch_probe(pa, st));
       PairArgs pr{};
       pr.probes = B.pout.as<uint32_t>(); pr.iprobes = ip; pr.rows = rc; pr.row0 = r0;
-      pr.t0 = t0; pr.nt = nt; pr.D = D; pr.X = ix->X; pr.ldx = ix->dpad;
+      pr.t0 = t0; pr.nt = nt; pr.D = D; pr.X = hashed_rows(ix); pr.ldx = ix->dpad;
       pr.R = ix->R; pr.ldr = ix->dpad; pr.n = n;
       pr.rec = B.recA.as<Rec>(); pr.counts = B.counts.as<uint32_t>();
       FPP_TRY(launch_pair_records(pr, st));
@@ -294,9 +304,9 @@ fpp_status build_tables(fpp_index* ix, int t0, int nt, BuildScratch& B, cudaStre
     h.lists = EL ? B.proj.as<uint64_t>() : nullptr; h.EL = EL;
     h.trunc = EL ? tc_list_trunc(D) : 0.f;
     h.t0 = t0; h.nt = nt; h.D = D;
-    h.X = ix->X; h.ldx = ix->dpad; h.R = ix->R; h.ldr = ix->dpad; h.d = ix->d;
-    h.rmax = ix->rmax; h.xmax = ix->xmax; h.gamma = ix->gamma; h.n = n;
-    h.eps_xf = (float)(ix->gamma * (double)ix->xmax * 1.0001);
+    h.X = hashed_rows(ix); h.ldx = ix->dpad; h.R = ix->R; h.ldr = ix->dpad; h.d = ix->d;
+    h.rmax = ix->rmax; h.xmax = ix->xhmax; h.gamma = ix->gamma; h.n = n;
+    h.eps_xf = (float)(ix->gamma * (double)ix->xhmax * 1.0001);
     h.rec = B.recA.as<Rec>(); h.counts = B.counts.as<uint32_t>(); h.point_bucket = nullptr;
     h.rechecks = B.rechecks.as<unsigned long long>();
     FPP_TRY(launch_build_hash(h, st));
@@ -418,6 +428,27 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
     hrmax[tj] = std::max(hrmax[tj], (float)(std::sqrt(s) * (1.0 + 1e-6)));
   }
   if ((s = to_device_padded(X, n, d, ix->dpad, &ix->X, st, &ix->device_bytes)) != FPP_OK) return fail(s);
+  if (p->center) {
+    // c: the given vector, or the FP64 column means rounded to FP32; the
+    // tables are built over fl(x - c)
+    ix->center = 1;
+    if (cudaMalloc(&ix->c, (size_t)ix->dpad * 4) != cudaSuccess ||
+        cudaMalloc(&ix->Xc, (size_t)n * ix->dpad * 4) != cudaSuccess) {
+      set_error("cudaMalloc (centering)");
+      return fail(FPP_ENOMEM);
+    }
+    ix->device_bytes += (uint64_t)n * ix->dpad * 4 + (uint64_t)ix->dpad * 4;
+    if (cudaMemsetAsync(ix->c, 0, (size_t)ix->dpad * 4, st) != cudaSuccess) return fail(FPP_ECUDA);
+    if (p->center_vec) {
+      if (cudaMemcpyAsync(ix->c, p->center_vec, (size_t)d * 4, cudaMemcpyDefault, st) != cudaSuccess) {
+        set_error("copying params->center_vec failed");
+        return fail(FPP_EINVAL);
+      }
+    } else if ((s = launch_column_means(ix->X, n, ix->dpad, d, ix->c, st)) != FPP_OK) {
+      return fail(s);
+    }
+    if ((s = launch_center_rows(ix->X, n, ix->dpad, ix->c, ix->Xc, st)) != FPP_OK) return fail(s);
+  }
   if ((s = to_device_padded(hR.data(), rrows, d, ix->dpad, &ix->R, st, &ix->device_bytes)) != FPP_OK)
     return fail(s);
   if (cudaMalloc(&ix->Rs, (size_t)rrows * ix->pieces * ix->Kp * 2) != cudaSuccess) {
@@ -441,13 +472,19 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
     return fail(FPP_ECUDA);
   }
   {
+    // largest norm of the points (score bounds) and of the hashed rows
+    // (projection bounds of the build); equal unless the index centers
     float* dxm = nullptr;
-    if (cudaMalloc(&dxm, 4) != cudaSuccess) { set_error("cudaMalloc"); return fail(FPP_ENOMEM); }
+    if (cudaMalloc(&dxm, 8) != cudaSuccess) { set_error("cudaMalloc"); return fail(FPP_ENOMEM); }
     s = launch_row_norm_max(ix->X, n, ix->dpad, d, dxm, st);
-    if (s == FPP_OK && cudaMemcpyAsync(&ix->xmax, dxm, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) s = FPP_ECUDA;
+    if (s == FPP_OK) s = launch_row_norm_max(hashed_rows(ix), n, ix->dpad, d, dxm + 1, st);
+    float hm[2] = {0.f, 0.f};
+    if (s == FPP_OK && cudaMemcpyAsync(hm, dxm, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) s = FPP_ECUDA;
     if (s == FPP_OK && cudaStreamSynchronize(st) != cudaSuccess) s = FPP_ECUDA;
     cudaFree(dxm);
     if (s != FPP_OK) return fail(s);
+    ix->xmax = hm[0];
+    ix->xhmax = hm[1];
   }
   const int64_t NB = nbuckets(D);
   if (cudaMalloc(&ix->offsets, (size_t)L * (NB + 1) * 4) != cudaSuccess) {
@@ -1253,6 +1290,7 @@ fpp_status fpp_index_get_info(const fpp_index* ix, fpp_index_info* info) {
   info->max_bucket_kept = ix->max_bucket_kept; info->device_bytes = ix->device_bytes;
   info->build_ms = ix->build_ms;
   info->rerank_k = ix->rerank_k;
+  info->center = ix->center;
   info->score_error_factor = ix->score_gamma;
   return FPP_OK;
 }
@@ -1282,12 +1320,12 @@ fpp_status fpp_debug_point_buckets(const fpp_index* cix, int32_t t, uint32_t* ou
     return done(s);
   for (int64_t r0 = 0; r0 < ix->n; r0 += rows) {
     const int64_t rc = std::min<int64_t>(rows, ix->n - r0);
-    if ((s = project_rows(ix, ix->X + r0 * ix->dpad, rc, split, t, 1, proj.as<float>(), ldp,
+    if ((s = project_rows(ix, hashed_rows(ix) + r0 * ix->dpad, rc, split, t, 1, proj.as<float>(), ldp,
                           err.as<int>(), st)) != FPP_OK)
       return done(s);
     if (ip > 1) {
       // the point's iProbes best buckets, ranked as for a query
-      const float* xr = ix->X + r0 * ix->dpad;
+      const float* xr = hashed_rows(ix) + r0 * ix->dpad;
       if ((s = launch_query_norms(xr, rc, ix->dpad, ix->d, norms.as<float>(), st)) != FPP_OK)
         return done(s);
       ProbeArgs pa{};
@@ -1303,9 +1341,9 @@ fpp_status fpp_debug_point_buckets(const fpp_index* cix, int32_t t, uint32_t* ou
     }
     HashArgs h{};
     h.P = proj.as<float>(); h.ldp = ldp; h.rows = rc; h.row0 = r0; h.t0 = t; h.nt = 1; h.D = ix->D;
-    h.X = ix->X; h.ldx = ix->dpad; h.R = ix->R; h.ldr = ix->dpad; h.d = ix->d;
-    h.rmax = ix->rmax; h.xmax = ix->xmax; h.gamma = ix->gamma; h.n = ix->n;
-    h.eps_xf = (float)(ix->gamma * (double)ix->xmax * 1.0001);
+    h.X = hashed_rows(ix); h.ldx = ix->dpad; h.R = ix->R; h.ldr = ix->dpad; h.d = ix->d;
+    h.rmax = ix->rmax; h.xmax = ix->xhmax; h.gamma = ix->gamma; h.n = ix->n;
+    h.eps_xf = (float)(ix->gamma * (double)ix->xhmax * 1.0001);
     h.point_bucket = pb.as<uint32_t>() + r0;
     if ((s = launch_build_hash(h, st)) != FPP_OK) return done(s);
   }

@@ -427,6 +427,63 @@ fpp_status launch_pair_records(const PairArgs& a, cudaStream_t st) {
   return FPP_OK;
 }
 
+// Centering (Section 3.4, heuristic (1)).  Column sums in FP64 over row
+// blocks of CM_ROWS (one thread per column, rows in order), then the block
+// partials summed in order and divided by n; the FP64 mean is rounded to
+// FP32.  The order is fixed, so c is the same on every run.
+constexpr int CM_ROWS = 4096;
+
+__global__ void column_partials_kernel(const float* __restrict__ X, int64_t n, int64_t ldx, int d,
+                                       double* __restrict__ part) {
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= d) return;
+  const int64_t r0 = (int64_t)blockIdx.x * CM_ROWS;
+  const int64_t r1 = n < r0 + CM_ROWS ? n : r0 + CM_ROWS;
+  double s = 0.0;
+  for (int64_t r = r0; r < r1; ++r) s += (double)X[r * ldx + c];
+  part[(int64_t)blockIdx.x * d + c] = s;
+}
+
+__global__ void column_means_kernel(const double* __restrict__ part, int nblk, int d, int64_t n,
+                                    float* __restrict__ c) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * d + j];
+  c[j] = __double2float_rn(s / (double)n);
+}
+
+// x -> fl(x - c), the padded columns stay zero (c is zero there)
+__global__ void center_rows_kernel(const float* __restrict__ X, int64_t total, int64_t ldx,
+                                   const float* __restrict__ c, float* __restrict__ Xc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  Xc[i] = __fsub_rn(X[i], c[i % ldx]);
+}
+
+fpp_status launch_column_means(const float* X, int64_t n, int64_t ldx, int d, float* c,
+                               cudaStream_t st) {
+  const int nblk = (int)ceil_div(n, CM_ROWS);
+  double* part = nullptr;
+  FPP_CUDA(cudaMalloc(&part, (size_t)nblk * d * 8));
+  column_partials_kernel<<<dim3(nblk, (unsigned)ceil_div(d, 128)), 128, 0, st>>>(X, n, ldx, d, part);
+  FPP_LAUNCHED();
+  column_means_kernel<<<(unsigned)ceil_div(d, 128), 128, 0, st>>>(part, nblk, d, n, c);
+  FPP_LAUNCHED();
+  FPP_CUDA(cudaStreamSynchronize(st));
+  cudaFree(part);
+  return FPP_OK;
+}
+
+fpp_status launch_center_rows(const float* X, int64_t n, int64_t ldx, const float* c, float* Xc,
+                              cudaStream_t st) {
+  const int64_t total = n * ldx;
+  if (total <= 0) return FPP_OK;
+  center_rows_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>(X, total, ldx, c, Xc);
+  FPP_LAUNCHED();
+  return FPP_OK;
+}
+
 fpp_status launch_build_hash(const HashArgs& a, cudaStream_t st) {
   const int64_t warps = a.rows * a.nt;
   if (warps <= 0) return FPP_OK;

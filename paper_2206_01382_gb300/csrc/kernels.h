@@ -89,6 +89,11 @@ fpp_status launch_pair_records(const PairArgs& a, cudaStream_t st);
 
 fpp_status launch_row_norm_max(const float* X, int64_t n, int64_t ldx, int d, float* out,
                                cudaStream_t st);
+// Centering: c [d] = FP32 rounding of the FP64 column means of X; Xc = fl(X - c).
+fpp_status launch_column_means(const float* X, int64_t n, int64_t ldx, int d, float* c,
+                               cudaStream_t st);
+fpp_status launch_center_rows(const float* X, int64_t n, int64_t ldx, const float* c, float* Xc,
+                              cudaStream_t st);
 
 // Exclusive scan of n values into out[0..n] (out[n] = total).  mode 0: the
 // values are in[i]; mode 1: the values are keep_count(in[i]).

@@ -323,3 +323,28 @@ def test_autotune_keeps_results(F):
         assert 0 < rep["ms_best"] <= rep["ms_default"] * 1.0001
         ti, ts = ix.search(Q, 10, 2)
         assert np.array_equal(gi, ti) and np.array_equal(gs, ts)
+
+
+@pytest.mark.parametrize("given_c", [False, True])
+def test_centering_parity(F, given_c):
+    # Section 3.4, heuristic (1): tables over x - c, queries and scores as usual
+    X, Q = W.small_mixture(8000, 100, 32, 64, 0.25, 95)
+    X = (X + np.float32(0.15)).astype(np.float32)
+    c, _ = O.center_points(X)
+    ix_o = O.build_index(X, 6, 16, 0.3, seed=12, center=True)
+    ix_g = F.Index(X, 6, 16, 0.3, seed=12, center=True, center_vec=c if given_c else None)
+    assert ix_g.info()["center"] == 1
+    excl = {}
+    for t in range(6):
+        gpb = F.fpp_debug_point_buckets(ix_g.handle, t)
+        nbad, unexplained = PT.compare_point_buckets(ix_o, t, gpb)
+        assert not unexplained, (t, unexplained[:5])
+        excl[t] = PT.excluded_buckets(ix_o, t, gpb)
+        off, ids = F.fpp_debug_table(ix_g.handle, t)
+        assert not PT.compare_table(ix_o, t, off, ids, excl[t]), t
+    for P in (1, 4):
+        gi, gs = ix_g.search(Q, 10, P)
+        _, _, res = O.search_batch(ix_o, Q, 10, P)
+        c_, s_, fails = PT.compare_search(res, gi, gs, 10, list(range(6)), excl)
+        assert not fails, fails[:3]
+        assert c_ >= 0.8 * len(res)
