@@ -30,6 +30,7 @@ from .falconn import (  # noqa: F401
     cross_polytope_hash,
     keep_count,
     probe_buckets,
+    probe_global,
     recall_at,
     search,
     search_batch,

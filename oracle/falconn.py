@@ -291,6 +291,27 @@ def probe_buckets(index: OracleIndex, q, P: int, tables=None):
     return b, s, margin < NEAR_TIE
 
 
+def probe_global(index: OracleIndex, q, Qp: int, tables=None):
+    """Global probe budget (qProbes, Sections 2.2 and 4): the Qp best
+    (table, bucket) pairs over all tables by the pair score v1(h1) + v2(h2);
+    ties go to the lower table, then the lower bucket.
+
+    Returns (buckets: one array per table of its selected buckets in rank
+    order, flag: near-tie between the Qp-th and (Qp+1)-th pair scores)."""
+    q64 = np.asarray(q, dtype=np.float64)
+    tsel = np.arange(index.L) if tables is None else np.asarray(tables)
+    p = index.R[tsel] @ q64                              # [L', 2, D]
+    T = min(Qp + 1, index.nbuckets)
+    b, s, _ = _top_pairs(_signed_lists(p[:, 0]), _signed_lists(p[:, 1]), T)
+    tt = np.repeat(np.arange(len(tsel)), b.shape[1])
+    bb, ss = b.reshape(-1), s.reshape(-1)
+    order = np.lexsort((bb, tt, -ss))
+    take = order[:Qp]
+    flag = bool(order.size > Qp and ss[order[Qp - 1]] - ss[order[Qp]] < NEAR_TIE)
+    per = [bb[take][tt[take] == ti] for ti in range(len(tsel))]
+    return per, flag
+
+
 def topk_exact(cand: np.ndarray, scores: np.ndarray, k: int):
     """Top-k of (cand, scores) by score desc then id asc, padded with
     (-1, -inf); also the near-tie flag at the k-th / (k+1)-th boundary."""
@@ -326,11 +347,17 @@ class QueryResult:
     entries: int             # bucket entries scanned (with duplicates)
 
 
-def search(index: OracleIndex, q, k: int, P: int, tables=None) -> QueryResult:
-    """One Falconn++ query: project, probe P buckets per table, union their
-    kept points, score them exactly and return the top-k."""
+def search(index: OracleIndex, q, k: int, P: int, tables=None,
+           global_probes: int = 0) -> QueryResult:
+    """One Falconn++ query: project, probe P buckets per table (or, with a
+    global budget, the global_probes best buckets over all tables), union
+    their kept points, score them exactly and return the top-k."""
     q64 = np.asarray(q, dtype=np.float64)
-    b, _, pflag = probe_buckets(index, q64, P, tables)
+    if global_probes:
+        b, gflag = probe_global(index, q64, global_probes, tables)
+        pflag = np.full(len(b), gflag)
+    else:
+        b, _, pflag = probe_buckets(index, q64, P, tables)
     tsel = np.arange(index.L) if tables is None else np.asarray(tables)
     entries = int(sum(index.offsets[t, bb + 1] - index.offsets[t, bb]
                       for ti, t in enumerate(tsel) for bb in b[ti]))
@@ -340,7 +367,7 @@ def search(index: OracleIndex, q, k: int, P: int, tables=None) -> QueryResult:
     return QueryResult(ids, sc, cand, b, pflag, tflag, entries)
 
 
-def search_batch(index: OracleIndex, Q, k, P, tables=None):
+def search_batch(index: OracleIndex, Q, k, P, tables=None, global_probes: int = 0):
     """``search`` over the rows of Q; k and P may be scalars or per-query
     arrays.  Returns ids [m][kmax], scores, and the per-query results."""
     Q = np.asarray(Q)
@@ -352,7 +379,7 @@ def search_batch(index: OracleIndex, Q, k, P, tables=None):
     sc = np.full((m, kmax), -np.inf)
     res = []
     for i in range(m):
-        r = search(index, Q[i], int(ks[i]), int(ps[i]), tables)
+        r = search(index, Q[i], int(ks[i]), int(ps[i]), tables, global_probes)
         ids[i, : ks[i]] = r.ids
         sc[i, : ks[i]] = r.scores
         res.append(r)

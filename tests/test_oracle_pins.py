@@ -399,3 +399,50 @@ def test_centering_spreads_skewed_data_over_buckets():
     for t in range(2):
         assert cent.counts[t].max() < 0.5 * plain.counts[t].max()
         assert np.count_nonzero(cent.counts[t]) > np.count_nonzero(plain.counts[t])
+
+
+def test_global_probes_equal_brute_force_enumeration():
+    # qProbes (Sections 2.2 and 4): the Qp best (table, bucket) pairs over
+    # all tables, checked against a plain enumeration of every pair
+    import workloads as W
+    X, Q = W.small_mixture(500, 6, 12, 8, 0.3, 83)
+    L, D = 3, 2
+    ix = O.build_index(X, L, D, 1.0, seed=7)
+    for q in Q:
+        q64 = q.astype(np.float64)
+        allp = []
+        for t in range(L):
+            p1 = ix.R[t, 0] @ q64
+            p2 = ix.R[t, 1] @ q64
+            v1 = np.concatenate([p1, -p1])
+            v2 = np.concatenate([p2, -p2])
+            for h1 in range(2 * D):
+                for h2 in range(2 * D):
+                    allp.append((-(v1[h1] + v2[h2]), t, h1 * 2 * D + h2))
+        allp.sort()
+        for Qp in (1, 5, 12, 4 * D * D * L):
+            per, flag = O.probe_global(ix, q, Qp)
+            want = allp[:Qp]
+            got = sorted((t, int(b)) for t in range(L) for b in per[t])
+            if not flag:
+                assert got == sorted((t, b) for _, t, b in want)
+            assert sum(len(x) for x in per) == Qp
+
+
+def test_global_probes_all_buckets_is_bruteforce_and_monotone():
+    import workloads as W
+    X, Q = W.small_mixture(1500, 8, 16, 8, 0.3, 84)
+    ix = O.build_index(X, 3, 3, 1.0, seed=8)
+    bi, _, bflag = O.brute_force(X, Q, 5)
+    _, _, res = O.search_batch(ix, Q, 5, 1, global_probes=3 * 36)
+    for i, r in enumerate(res):
+        if not bflag[i]:
+            assert np.array_equal(r.ids, bi[i])
+    prev = None
+    for Qp in (1, 3, 9, 27):
+        _, _, res = O.search_batch(ix, Q, 5, 1, global_probes=Qp)
+        if prev is not None:
+            for a, b in zip(prev, res):
+                if not (np.any(a.probe_flag) or np.any(b.probe_flag)):
+                    assert set(a.cand.tolist()) <= set(b.cand.tolist())
+        prev = res
