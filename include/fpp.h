@@ -102,6 +102,14 @@ typedef struct fpp_search_opts {
   int32_t table_end;          /* 0 or L = all tables                          */
   int32_t flags;              /* FPP_SEARCH_* bits                            */
   void* stream;               /* cudaStream_t or NULL                         */
+  int32_t global_probes;      /* > 0: probe this many buckets per query over
+                                 all tables together (qProbes, Sections 2.2
+                                 and 4), the best by pair score, at most
+                                 min(global_probes, 128, 4D^2) from one table;
+                                 probes and probes_per_query are then unused
+                                 (probes_per_query must be NULL).  0: probes
+                                 per table.                                   */
+  int32_t reserved1;
 } fpp_search_opts;
 
 /* FPP_SEARCH_GRAPH: run the call as one CUDA graph, captured on the first

@@ -48,7 +48,8 @@ class fpp_search_opts(ctypes.Structure):
                 ("k_per_query", ctypes.c_void_p), ("probes_per_query", ctypes.c_void_p),
                 ("k_max", ctypes.c_int32), ("table_begin", ctypes.c_int32),
                 ("table_end", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("global_probes", ctypes.c_int32),
+                ("reserved1", ctypes.c_int32)]
 
 
 class fpp_search_stats(ctypes.Structure):
@@ -257,7 +258,7 @@ def fpp_search(ix, Q, k: int, probes: int, ids=None, scores=None):
 def fpp_search_ex(ix, Q, k: int = 10, probes: int = 1, k_per_query=None, probes_per_query=None,
                   k_max: int | None = None, table_begin: int = 0, table_end: int = 0,
                   stream=None, ids=None, scores=None, want_stats: bool = True,
-                  graph: bool = False):
+                  graph: bool = False, global_probes: int = 0):
     """fpp_search with per-query k / probes, a table range, a stream and stats."""
     Q = _f32(Q)
     m = Q.shape[0]
@@ -272,6 +273,7 @@ def fpp_search_ex(ix, Q, k: int = 10, probes: int = 1, k_per_query=None, probes_
     o.k_max, o.table_begin, o.table_end = k_max, table_begin, table_end
     o.stream = _stream_ptr(stream)
     o.flags = FPP_SEARCH_GRAPH if graph else 0
+    o.global_probes = global_probes
     ids = _alloc_like(Q, (m, k_max), "i64") if ids is None else ids
     scores = _alloc_like(Q, (m, k_max), "f32") if scores is None else scores
     st = fpp_search_stats()

@@ -559,6 +559,7 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
 struct SearchPlan {
   int64_t m;
   int kmax, pmax, tb, te;
+  int global_q = 0;     // > 0: global probe budget (pmax = the per-table cap)
   const int32_t* kpq;   // user arrays (host or device) or NULL
   const int32_t* ppq;
   bool kpq_dev, ppq_dev;
@@ -602,9 +603,20 @@ fpp_status validate_search(const fpp_index* ix, const float* Q, int64_t m, const
   if (pl.kpq) FPP_TRY(check_arr(pl.kpq, 1, 256, kmax_seen, "k_per_query"));
   else if (pl.k < 1 || pl.k > 256) { set_error("k must be in [1, 256]"); return FPP_EINVAL; }
   if (pl.ppq) FPP_TRY(check_arr(pl.ppq, 1, pcap, pmax_seen, "probes_per_query"));
-  else if (pl.probes < 1 || pl.probes > pcap) {
+  else if (o->global_probes <= 0 && (pl.probes < 1 || pl.probes > pcap)) {
     set_error("probes must be in [1, min(4D^2, 128)]");
     return FPP_EINVAL;
+  }
+  if (o->global_probes < 0) { set_error("global_probes must be >= 0"); return FPP_EINVAL; }
+  if (o->global_probes > 0) {
+    if (pl.ppq) { set_error("global_probes excludes probes_per_query"); return FPP_EINVAL; }
+    pl.global_q = o->global_probes;
+    pl.probes = (int)std::min<int64_t>(std::min<int64_t>(o->global_probes, 128), NB);
+    pmax_seen = pl.probes;
+    if ((int64_t)(pl.te - pl.tb) * pl.probes > 16384) {
+      set_error("global_probes: tables x per-table cap must be <= 16384");
+      return FPP_EINVAL;
+    }
   }
   pl.kmax = o->k_max > 0 ? o->k_max : kmax_seen;
   if (pl.kmax < kmax_seen || pl.kmax > 256) { set_error("k_max must cover every k and be <= 256"); return FPP_EINVAL; }
@@ -669,6 +681,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   pa.recheck_s = EL ? nullptr : ws.recheck_s.as<float>();   // pair-window pass (stored projections)
   pa.rechecks = ws.stats.as<unsigned long long>() + 6;
   FPP_TRY(launch_probe(pa, st, ev ? ev[4] : nullptr));
+  if (pl.global_q > 0) FPP_TRY(launch_global_probes(pa, pl.global_q, st));
   if (ev) FPP_CUDA(cudaEventRecord(ev[2], st));
   if (stage == kProbesOnly) return FPP_OK;
   // ---- candidates: count bucket entries, give each query a region, dedup,
@@ -800,7 +813,7 @@ bool search_graph(fpp_index* ix, const float* Q, int64_t m, const fpp_search_opt
       (uint64_t)(uintptr_t)Q, (uint64_t)m, (uint64_t)(uintptr_t)ids, (uint64_t)(uintptr_t)scores,
       (uint64_t)(uintptr_t)pl.kpq, (uint64_t)(uintptr_t)pl.ppq, (uint64_t)pl.k,
       (uint64_t)pl.probes, (uint64_t)pl.kmax, (uint64_t)pl.pmax, (uint64_t)pl.tb, (uint64_t)pl.te,
-      (uint64_t)(uintptr_t)st, g_alloc_gen.load()};
+      (uint64_t)(uintptr_t)st, (uint64_t)pl.global_q, g_alloc_gen.load()};
   if (!ix->graph_exec || ix->graph_key != key) {
     if (ix->graph_exec) cudaGraphExecDestroy(ix->graph_exec);
     ix->graph_exec = nullptr;

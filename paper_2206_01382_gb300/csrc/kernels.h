@@ -150,6 +150,14 @@ struct ProbeArgs {
   unsigned long long* rechecks;  // statistics counter or NULL
 };
 fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_begin = nullptr);
+
+// Global probe budget: out of the probe kernels' per-table top-P lists
+// (a.out, P = a.probes), keeps the Qp best (table, bucket) pairs of every
+// query by pair score (ties: lower table, lower bucket) and marks the rest
+// of each table's slots empty (PROBE_EMPTY).  Exact: a boundary inside the
+// error bound is re-decided from compensated projections.
+constexpr uint32_t PROBE_EMPTY = 0xFFFFFFFFu;
+fpp_status launch_global_probes(const ProbeArgs& a, int Qp, cudaStream_t st);
 fpp_status launch_query_norms(const float* Q, int64_t m, int64_t ldq, int d, float* out,
                               cudaStream_t st);
 

@@ -749,6 +749,147 @@ probe_pwin_kernel(ProbeArgs a) {
   }
 }
 
+// Global probe budget (qProbes, Sections 2.2 and 4), one CTA per query:
+// the FP32 pair scores of every table's top-P buckets are sorted (score
+// desc, then table and bucket asc); when the Qp-th and (Qp+1)-th scores are
+// closer than twice the per-pair error bound delta, the pairs in the window
+// [s_Qp - 2 delta, s_Qp+1 + 2 delta] are re-scored from compensated
+// projections and ranked exactly.  The selected buckets of each table are
+// written to the front of its slots, the other slots are marked empty.
+constexpr int GP_THREADS = 256;
+constexpr int GP_WIN = 64;
+
+__device__ __forceinline__ float pair_value_fp32(const ProbeArgs& a, int64_t q, int tl, uint32_t h,
+                                                 int j) {
+  const int D = a.D;
+  const uint32_t i = h % (uint32_t)D;
+  float p;
+  if (a.P) {
+    p = a.P[q * a.ldp + (int64_t)(2 * tl + j) * D + i];
+  } else {
+    // list mode: the entry of wedge h is among the hash's EL best keys
+    const uint64_t* L = a.lists + ((q * a.nt + tl) * 2 + j) * (int64_t)(a.EL + 1);
+    p = 0.f;
+    for (int e = 0; e < a.EL; ++e) {
+      const uint64_t k = L[e];
+      if (k && (0xFFFFFFFFu - (uint32_t)k) % (uint32_t)D == i) {
+        const float v = __uint_as_float((uint32_t)(k >> 32) - 1u);
+        p = (0xFFFFFFFFu - (uint32_t)k) < (uint32_t)D ? v : -v;
+        break;
+      }
+    }
+  }
+  return h < (uint32_t)D ? p : -p;
+}
+
+__global__ void __launch_bounds__(GP_THREADS)
+global_probes_kernel(ProbeArgs a, int Qp, int npow2) {
+  extern __shared__ __align__(16) uint64_t keys[];   // [npow2]
+  __shared__ SD win[GP_WIN];
+  __shared__ int s_cnt[1];
+  __shared__ float s_sQ, s_sQ1;
+  const int tid = threadIdx.x;
+  const int64_t q = blockIdx.x;
+  const int P = a.probes;
+  const int N = a.nt * P;
+  const int64_t NB = 4ll * a.D * a.D;
+  const uint32_t* src = a.out + q * a.nt * (int64_t)P;
+  for (int e = tid; e < npow2; e += GP_THREADS) {
+    uint64_t key = 0ull;
+    if (e < N) {
+      const int tl = e / P;
+      const uint32_t b = src[e];
+      const uint32_t h1 = b / (uint32_t)(2 * a.D), h2 = b % (uint32_t)(2 * a.D);
+      const float f = pair_value_fp32(a, q, tl, h1, 0) + pair_value_fp32(a, q, tl, h2, 1);
+      key = ((uint64_t)float_key(f) << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)(tl * NB + b));
+    }
+    keys[e] = key;
+  }
+  __syncthreads();
+  block_sort_desc(keys, npow2);
+  const int Qe = min(Qp, N);
+  // the boundary and the window
+  bool exact_ok = true;
+  int lo = Qe, hi_i = Qe;   // window [lo, hi_i) in the sorted order
+  if (tid == 0) { s_sQ = key_score(keys[Qe - 1]); s_sQ1 = Qe < N ? key_score(keys[Qe]) : -INFINITY; }
+  __syncthreads();
+  const float sQ = s_sQ, sQ1 = s_sQ1;
+  if (Qe < N) {
+    float rmx = 0.f;
+    for (int t = 0; t < a.nt; ++t) rmx = fmaxf(rmx, a.rmax[2 * (a.tb + t)] + a.rmax[2 * (a.tb + t) + 1]);
+    // truncated list values: a pair score (two non-negative list values)
+    // may be low by trunc times itself, at most the largest pair score
+    const float tr = a.P ? 0.f : a.trunc * fabsf(key_score(keys[0])) * 1.001f;
+    const float eps = a.gammaf * a.qnorm[q] * rmx + tr;
+    const float delta = (eps + 6.0e-8f * (fabsf(sQ) + fabsf(sQ1) + 2.f * eps)) * 1.001f + 1e-30f;
+    if (sQ - sQ1 <= 2.f * delta) {
+      // window: sorted positions whose score lies in [sQ - 2 delta, sQ1 + 2 delta]
+      const float top = sQ1 + 2.f * delta, bot = sQ - 2.f * delta;
+      if (tid == 0) {
+        int l = Qe - 1;
+        while (l > 0 && key_score(keys[l - 1]) <= top) --l;
+        int h = Qe;
+        while (h < N && key_score(keys[h]) >= bot) ++h;
+        s_cnt[0] = (h - l <= GP_WIN) ? (l << 16 | (h - l)) : -1;
+      }
+      __syncthreads();
+      if (s_cnt[0] < 0) {
+        exact_ok = false;
+      } else {
+        lo = s_cnt[0] >> 16;
+        hi_i = lo + (s_cnt[0] & 0xFFFF);
+        // compensated pair scores of the window, one warp per pair
+        const int lane = tid & 31, wid = tid >> 5;
+        const float* qv = a.Q + q * a.ldq;
+        const int nf4 = (int)(a.ldr / 4);
+        for (int w = wid; w < hi_i - lo; w += GP_THREADS / 32) {
+          const uint32_t code = 0xFFFFFFFFu - (uint32_t)keys[lo + w];
+          const int tl = (int)(code / NB);
+          const uint32_t b = code - (uint32_t)(tl * NB);
+          const uint32_t h1 = b / (uint32_t)(2 * a.D), h2 = b % (uint32_t)(2 * a.D);
+          const int t = a.tb + tl;
+          const float* rows[2] = {a.R + ((int64_t)(2 * t) * a.D + h1 % (uint32_t)a.D) * a.ldr,
+                                  a.R + ((int64_t)(2 * t + 1) * a.D + h2 % (uint32_t)a.D) * a.ldr};
+          double v[2];
+          warp_dot2_gather<2>(qv, rows, nf4, v);
+          if (lane == 0) {
+            const double f = (h1 < (uint32_t)a.D ? v[0] : -v[0]) + (h2 < (uint32_t)a.D ? v[1] : -v[1]);
+            win[w] = SD{f, code, 0};
+          }
+        }
+        for (int w = tid; w < GP_WIN; w += GP_THREADS)
+          if (w >= hi_i - lo) win[w] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+        __syncthreads();
+        block_sort_sd(win, GP_WIN);
+      }
+    }
+  }
+  // write: the first lo sorted pairs, then Qe - lo window pairs by exact rank
+  uint32_t* dst = a.out + q * a.nt * (int64_t)P;
+  __shared__ int s_tcount[1];
+  // per table fill counters live at the end of the key array
+  int* tcount = reinterpret_cast<int*>(keys + npow2);
+  if (!exact_ok) lo = Qe;   // no exact window: keep the FP32 ranking (flagged below)
+  __syncthreads();
+  // stage the chosen codes in keys[npow2 - Qe ..] is unsafe; copy first
+  for (int t = tid; t < a.nt; t += GP_THREADS) tcount[t] = 0;
+  __syncthreads();
+  uint32_t* chosen = reinterpret_cast<uint32_t*>(tcount + a.nt);
+  for (int e = tid; e < Qe; e += GP_THREADS)
+    chosen[e] = e < lo ? 0xFFFFFFFFu - (uint32_t)keys[e] : win[e - lo].id;
+  __syncthreads();
+  for (int e = tid; e < N; e += GP_THREADS) dst[e] = PROBE_EMPTY;
+  __syncthreads();
+  for (int e = tid; e < Qe; e += GP_THREADS) {
+    const uint32_t code = chosen[e];
+    const int tl = (int)(code / NB);
+    const int slot = atomicAdd(&tcount[tl], 1);
+    dst[tl * P + slot] = code - (uint32_t)(tl * NB);
+  }
+  if (tid == 0 && !exact_ok && a.rechecks) atomicAdd(a.rechecks + 1, 1ull);
+  (void)s_tcount;
+}
+
 __global__ void query_norms_kernel(const float* __restrict__ Q, int64_t m, int64_t ldq, int d,
                                    float* __restrict__ out) {
   const int lane = threadIdx.x & 31;
@@ -821,8 +962,8 @@ __device__ __forceinline__ void warp_walk(const WarpWalk& w, Visit& visit) {
         const int t = a.tb + tl;
         const uint32_t b = a.probes[(w.q * a.nt + tl) * (int64_t)a.pstride + p];
         const uint32_t* off = a.offsets + (int64_t)t * (w.NB + 1);
-        const uint32_t o0 = off[b];
-        c = off[b + 1] - o0;
+        const uint32_t o0 = b == PROBE_EMPTY ? 0u : off[b];   // empty slot: no bucket
+        c = b == PROBE_EMPTY ? 0u : off[b + 1] - o0;
         w.pbase[i] = a.table_base[t] + o0;
       }
       cnt[r] = c;
@@ -896,7 +1037,7 @@ count_entries_kernel(DedupArgs a) {
     const int tl = pi / Pq, p = pi - tl * Pq;
     const uint32_t b = a.probes[(q * a.nt + tl) * (int64_t)a.pstride + p];
     const uint32_t* off = a.offsets + (int64_t)(a.tb + tl) * (NB + 1);
-    s += off[b + 1] - off[b];
+    if (b != PROBE_EMPTY) s += off[b + 1] - off[b];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
@@ -997,8 +1138,8 @@ dedup_hash_kernel(DedupArgs a) {
         const int t = a.tb + tl;
         const uint32_t bk = a.probes[(q * a.nt + tl) * (int64_t)a.pstride + p];
         const uint32_t* off = a.offsets + (int64_t)t * (NB + 1);
-        const uint32_t o0 = off[bk];
-        c = off[bk + 1] - o0;
+        const uint32_t o0 = bk == PROBE_EMPTY ? 0u : off[bk];   // empty slot: no bucket
+        c = bk == PROBE_EMPTY ? 0u : off[bk + 1] - o0;
         pbase[tid] = a.table_base[t] + o0;
       }
       // exclusive prefix sum of the bucket sizes over the CTA
@@ -1700,6 +1841,22 @@ fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_b
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   probe_recheck_kernel<<<sms * 4, RECHECK_THREADS, smem, st>>>(a);
+  FPP_LAUNCHED();
+  return FPP_OK;
+}
+
+fpp_status launch_global_probes(const ProbeArgs& a, int Qp, cudaStream_t st) {
+  if (a.mq <= 0) return FPP_OK;
+  const int N = a.nt * a.probes;
+  const int npow2 = pow2_ceil(N > 1 ? N : 1);
+  const size_t smem = (size_t)npow2 * 8 + (size_t)a.nt * 4 + (size_t)Qp * 4 + 16;
+  if (smem > 200 * 1024) {
+    set_error("global probes: tables x per-table budget too large (at most 16,384 pairs)");
+    return FPP_EINVAL;
+  }
+  FPP_CUDA(cudaFuncSetAttribute(global_probes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  global_probes_kernel<<<(unsigned)a.mq, GP_THREADS, smem, st>>>(a, Qp, npow2);
   FPP_LAUNCHED();
   return FPP_OK;
 }

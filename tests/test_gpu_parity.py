@@ -348,3 +348,19 @@ def test_centering_parity(F, given_c):
         c_, s_, fails = PT.compare_search(res, gi, gs, 10, list(range(6)), excl)
         assert not fails, fails[:3]
         assert c_ >= 0.8 * len(res)
+
+
+@pytest.mark.parametrize("Qp,L,D", [(12, 6, 16), (40, 10, 8), (200, 4, 64)])
+def test_global_probes_parity(F, Qp, L, D):
+    # qProbes over all tables together (Sections 2.2 and 4), list mode
+    # (small per-table cap) and stored projections (large)
+    X, Q = W.small_mixture(6000, 60, 32, 64, 0.25, 96 + Qp)
+    ix_o = O.build_index(X, L, D, 0.3, seed=14)
+    ix_g = F.Index(X, L, D, 0.3, seed=14)
+    excl = {t: PT.excluded_buckets(ix_o, t, F.fpp_debug_point_buckets(ix_g.handle, t))
+            for t in range(L)}
+    gi, gs, _ = F.fpp_search_ex(ix_g.handle, Q, k=10, global_probes=Qp, want_stats=False)
+    _, _, res = O.search_batch(ix_o, Q, 10, 1, global_probes=Qp)
+    c, s, fails = PT.compare_search(res, gi, gs, 10, list(range(L)), excl)
+    assert not fails, fails[:3]
+    assert c >= 0.7 * len(res), (c, s)
