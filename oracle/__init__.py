@@ -34,4 +34,7 @@ from .falconn import (  # noqa: F401
     recall_at,
     search,
     search_batch,
+    simhash_select,
+    simhash_signatures,
+    hamming,
 )

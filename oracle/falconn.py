@@ -317,6 +317,41 @@ def probe_global(index: OracleIndex, q, Qp: int, tables=None):
     return per, flag
 
 
+def simhash_signatures(index: OracleIndex, V, bits: int) -> np.ndarray:
+    """SimHash signatures (Charikar, STOC 2002) from the index's own random
+    vectors, as the paper suggests (Section 4: the projections are reused):
+    bit i of a vector v is [v^T r_i >= 0] for the i-th of the 2 L D vectors
+    in table-major order (r of table t, hash j, index i at (2t + j) D + i),
+    packed little-endian into uint32 words.  V: [m][d]; returns [m][bits/32]."""
+    if bits % 32 or not 0 < bits <= 2 * index.L * index.D:
+        raise ValueError("bits must be a multiple of 32 in (0, 2 L D]")
+    R = index.R.reshape(-1, index.d)[:bits]
+    P = np.atleast_2d(np.asarray(V, dtype=np.float64)) @ R.T          # [m][bits]
+    b = (P >= 0).astype(np.uint64)
+    w = np.zeros((b.shape[0], bits // 32), dtype=np.uint64)
+    for i in range(bits):
+        w[:, i // 32] |= b[:, i] << np.uint64(i % 32)
+    return w.astype(np.uint32)
+
+
+def hamming(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Bit differences between signature rows a [..., W] and b [W]."""
+    x = np.bitwise_xor(a, b)
+    return np.array([sum(bin(int(v)).count("1") for v in row) for row in np.atleast_2d(x)],
+                    dtype=np.int64)
+
+
+def simhash_select(sig_x: np.ndarray, sig_q: np.ndarray, cand: np.ndarray, keep: int):
+    """The ``keep`` candidates whose signatures differ from the query's in
+    the fewest bits (ties: lower id), sorted by id: SimHash pre-ranking of
+    the candidates before exact scoring (Section 4)."""
+    if cand.size <= keep:
+        return cand
+    h = hamming(sig_x[cand], sig_q)
+    order = np.lexsort((cand, h))
+    return np.sort(cand[order[:keep]])
+
+
 def topk_exact(cand: np.ndarray, scores: np.ndarray, k: int):
     """Top-k of (cand, scores) by score desc then id asc, padded with
     (-1, -inf); also the near-tie flag at the k-th / (k+1)-th boundary."""
@@ -353,7 +388,7 @@ class QueryResult:
 
 
 def search(index: OracleIndex, q, k: int, P: int, tables=None,
-           global_probes: int = 0) -> QueryResult:
+           global_probes: int = 0, simhash=None) -> QueryResult:
     """One Falconn++ query: project, probe P buckets per table (or, with a
     global budget, the global_probes best buckets over all tables), union
     their kept points, score them exactly and return the top-k."""
@@ -367,12 +402,19 @@ def search(index: OracleIndex, q, k: int, P: int, tables=None,
     entries = int(sum(index.offsets[t, bb + 1] - index.offsets[t, bb]
                       for ti, t in enumerate(tsel) for bb in b[ti]))
     cand = candidates(index, b, tables)
+    if simhash is not None:
+        # simhash = (signatures of X [n][W], bits, keep): only the keep
+        # candidates closest in Hamming distance are scored
+        sig_x, bits, keep = simhash
+        sig_q = simhash_signatures(index, q64[None, :], bits)[0]
+        cand = simhash_select(sig_x, sig_q, cand, keep)
     s = index.X[cand] @ q64
     ids, sc, tflag = topk_exact(cand, s, k)
     return QueryResult(ids, sc, cand, b, pflag, tflag, entries)
 
 
-def search_batch(index: OracleIndex, Q, k, P, tables=None, global_probes: int = 0):
+def search_batch(index: OracleIndex, Q, k, P, tables=None, global_probes: int = 0,
+                 simhash=None):
     """``search`` over the rows of Q; k and P may be scalars or per-query
     arrays.  Returns ids [m][kmax], scores, and the per-query results."""
     Q = np.asarray(Q)
@@ -384,7 +426,7 @@ def search_batch(index: OracleIndex, Q, k, P, tables=None, global_probes: int = 
     sc = np.full((m, kmax), -np.inf)
     res = []
     for i in range(m):
-        r = search(index, Q[i], int(ks[i]), int(ps[i]), tables, global_probes)
+        r = search(index, Q[i], int(ks[i]), int(ps[i]), tables, global_probes, simhash)
         ids[i, : ks[i]] = r.ids
         sc[i, : ks[i]] = r.scores
         res.append(r)

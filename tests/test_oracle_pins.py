@@ -446,3 +446,48 @@ def test_global_probes_all_buckets_is_bruteforce_and_monotone():
                 if not (np.any(a.probe_flag) or np.any(b.probe_flag)):
                     assert set(a.cand.tolist()) <= set(b.cand.tolist())
         prev = res
+
+
+def test_simhash_signature_bits_by_hand():
+    # bit i = [v^T r_i >= 0] over the index's vectors in table-major order
+    R = np.zeros((1, 2, 16, 3))   # 32 vectors; all but the first four are zero
+    R[0, 0, 0] = [1, 0, 0]
+    R[0, 0, 1] = [0, 1, 0]
+    R[0, 0, 2] = [0, 0, 1]
+    R[0, 0, 3] = [1, 1, 1]
+    X = np.array([[0.6, -0.8, 0.0]], dtype=np.float32)
+    ix = O.build_index(X, 1, 16, 1.0, R=R)
+    sig = O.simhash_signatures(ix, np.array([[0.6, -0.8, 0.0], [-1.0, 2.0, -3.0]]), 32)
+    # v1: +, -, 0 (>= 0 -> 1), -0.2 -> bits 1,0,1,0 ; v2: -, +, -, - -> 0,1,0,0;
+    # the zero vectors give 0 >= 0 -> 1 in bits 4..31
+    assert sig[0, 0] == 0xFFFFFFF5 and sig[1, 0] == 0xFFFFFFF2
+    assert O.hamming(sig, sig[0]).tolist() == [0, 3]
+
+
+def test_simhash_estimates_angle():
+    # Charikar: a random hyperplane separates two vectors with probability
+    # theta / pi
+    rng = np.random.default_rng(13)
+    d = 64
+    X = rng.standard_normal((2, d)).astype(np.float32)
+    ix = O.build_index(X, 8, 64, 1.0, seed=9)   # 1,024 vectors
+    q = rng.standard_normal(d)
+    for c in (0.9, 0.5, 0.0, -0.7):
+        z = rng.standard_normal(d); z -= z.dot(q) * q / q.dot(q)
+        v = c * q / np.linalg.norm(q) + math.sqrt(1 - c * c) * z / np.linalg.norm(z)
+        s = O.simhash_signatures(ix, np.stack([q, v]), 1024)
+        frac = O.hamming(s[1:], s[0])[0] / 1024.0
+        assert abs(frac - math.acos(c) / math.pi) < 0.05
+
+
+def test_simhash_keep_all_equals_plain_search(tiny_data, tiny_index):
+    w, X, Q = tiny_data
+    sig = O.simhash_signatures(tiny_index, X, 256)
+    a, sa, _ = O.search_batch(tiny_index, Q[:20], w.k, 4)
+    b, sb, _ = O.search_batch(tiny_index, Q[:20], w.k, 4, simhash=(sig, 256, 10 ** 6))
+    assert np.array_equal(a, b) and np.array_equal(sa, sb)
+    # a small keep scores fewer candidates; the result is within the kept ones
+    _, _, res = O.search_batch(tiny_index, Q[:20], w.k, 4, simhash=(sig, 256, 50))
+    for r in res:
+        assert r.cand.size <= 50
+        assert set(r.ids[r.ids >= 0].tolist()) <= set(r.cand.tolist())
