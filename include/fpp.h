@@ -86,7 +86,10 @@ typedef struct fpp_params {
   int32_t center;      /* 1: build the tables over the centered points x - c
                           (Section 3.4, heuristic (1)); queries are not
                           centered and scores stay x^T q (default 0)        */
-  int32_t reserved1;
+  int32_t simhash_bits; /* SimHash signature bits per point, 0 (none) or a
+                          multiple of 256 up to min(1024, 2 L D): bit i is
+                          [x^T r_i >= 0] for the i-th random vector in table
+                          order (Section 4); needed by simhash_keep        */
   const float* center_vec; /* optional c [d] (host or device); NULL = the
                           FP64 column means of X rounded to FP32            */
 } fpp_params;
@@ -109,7 +112,11 @@ typedef struct fpp_search_opts {
                                  probes and probes_per_query are then unused
                                  (probes_per_query must be NULL).  0: probes
                                  per table.                                   */
-  int32_t reserved1;
+  int32_t simhash_keep;       /* > 0: score only the simhash_keep candidates
+                                 whose signatures differ least from the
+                                 query's (ties: lower id), 1..512; needs an
+                                 index built with simhash_bits (Section 4).
+                                 An approximation: graded by recall.  0: off */
 } fpp_search_opts;
 
 /* FPP_SEARCH_GRAPH: run the call as one CUDA graph, captured on the first
@@ -156,6 +163,8 @@ typedef struct fpp_index_info {
   float build_ms;             /* wall time of fpp_build                        */
   int32_t rerank_k;           /* FPP_BF16 shortlist length (0 for FPP_FP32)    */
   int32_t center;             /* 1: the tables hash the centered points        */
+  int32_t simhash_bits;       /* SimHash signature bits per point (0: none)    */
+  int32_t reserved2;
   double score_error_factor;  /* c: a candidate's first-pass score is within
                                  c ||q|| ||x|| of x^T q (FPP_FP32: the FP32
                                  bound gamma_d; FPP_BF16: the statistical

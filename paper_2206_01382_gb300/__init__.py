@@ -39,7 +39,7 @@ class fpp_params(ctypes.Structure):
                 ("kappa", ctypes.c_int32), ("alpha", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("R", ctypes.c_void_p), ("precision", ctypes.c_int32),
                 ("rerank_k", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("center", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+                ("center", ctypes.c_int32), ("simhash_bits", ctypes.c_int32),
                 ("center_vec", ctypes.c_void_p)]
 
 
@@ -49,7 +49,7 @@ class fpp_search_opts(ctypes.Structure):
                 ("k_max", ctypes.c_int32), ("table_begin", ctypes.c_int32),
                 ("table_end", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("global_probes", ctypes.c_int32),
-                ("reserved1", ctypes.c_int32)]
+                ("simhash_keep", ctypes.c_int32)]
 
 
 class fpp_search_stats(ctypes.Structure):
@@ -90,6 +90,7 @@ class fpp_index_info(ctypes.Structure):
                 ("kept_total", ctypes.c_uint64), ("max_bucket_kept", ctypes.c_uint32),
                 ("device_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_float),
                 ("rerank_k", ctypes.c_int32), ("center", ctypes.c_int32),
+                ("simhash_bits", ctypes.c_int32), ("reserved2", ctypes.c_int32),
                 ("score_error_factor", ctypes.c_double)]
 
 
@@ -221,7 +222,8 @@ def fpp_default_params() -> fpp_params:
 
 def fpp_build(X, L: int, D: int, alpha: float, seed: int = 0, R=None, iprobes: int = 1,
               kappa: int = 0, precision: int = FPP_FP32, rerank_k: int = 100,
-              center: bool = False, center_vec=None, stream=None) -> ctypes.c_void_p:
+              center: bool = False, center_vec=None, simhash_bits: int = 0,
+              stream=None) -> ctypes.c_void_p:
     """Builds an index over X [n][d]; returns the opaque handle."""
     lib = load()
     X = _f32(X)
@@ -229,6 +231,7 @@ def fpp_build(X, L: int, D: int, alpha: float, seed: int = 0, R=None, iprobes: i
     p.L, p.D, p.alpha, p.seed = L, D, float(alpha), int(seed)
     p.iprobes, p.kappa, p.precision, p.rerank_k = iprobes, kappa, precision, rerank_k
     p.center = 1 if center else 0
+    p.simhash_bits = simhash_bits
     cv = _f32(center_vec) if center_vec is not None else None
     p.center_vec = _ptr(cv)
     Rc = _f32(R) if R is not None else None
@@ -258,7 +261,7 @@ def fpp_search(ix, Q, k: int, probes: int, ids=None, scores=None):
 def fpp_search_ex(ix, Q, k: int = 10, probes: int = 1, k_per_query=None, probes_per_query=None,
                   k_max: int | None = None, table_begin: int = 0, table_end: int = 0,
                   stream=None, ids=None, scores=None, want_stats: bool = True,
-                  graph: bool = False, global_probes: int = 0):
+                  graph: bool = False, global_probes: int = 0, simhash_keep: int = 0):
     """fpp_search with per-query k / probes, a table range, a stream and stats."""
     Q = _f32(Q)
     m = Q.shape[0]
@@ -274,6 +277,7 @@ def fpp_search_ex(ix, Q, k: int = 10, probes: int = 1, k_per_query=None, probes_
     o.stream = _stream_ptr(stream)
     o.flags = FPP_SEARCH_GRAPH if graph else 0
     o.global_probes = global_probes
+    o.simhash_keep = simhash_keep
     ids = _alloc_like(Q, (m, k_max), "i64") if ids is None else ids
     scores = _alloc_like(Q, (m, k_max), "f32") if scores is None else scores
     st = fpp_search_stats()

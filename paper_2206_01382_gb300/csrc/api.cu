@@ -71,7 +71,7 @@ struct DevBuf {
 
 struct Workspace {
   DevBuf qpad, qsplit, proj, probes, qnorm, recheck, recheck2, recheck_s, kpq, ppq, out_ids,
-      out_scores,
+      out_scores, sigproj, qsig,
       ecount, eoff, scan, cand, cscores, items, tkslow, stats;
   // completion of the last call that used this workspace: a call on another
   // stream waits for it before touching the buffers
@@ -90,7 +90,8 @@ struct Workspace {
   }
   uint64_t cand_cap = 0;    // candidate slots in cand / cscores
   void release() {
-    for (DevBuf* b : {&qpad, &qsplit, &proj, &probes, &qnorm, &recheck, &recheck2, &recheck_s, &kpq, &ppq,
+    for (DevBuf* b : {&qpad, &qsplit, &proj, &probes, &qnorm, &recheck, &recheck2, &recheck_s, &sigproj,
+                      &qsig, &kpq, &ppq,
                       &out_ids, &out_scores, &ecount, &eoff, &scan, &cand, &cscores,
                       &items, &tkslow, &stats})
       b->release();
@@ -110,6 +111,9 @@ struct fpp_index {
   float* Xc = nullptr;         // [n][dpad] centered points (center = 1), else NULL
   float* c = nullptr;          // [dpad] the center (center = 1)
   int center = 0;
+  uint32_t* sig = nullptr;     // [n][sig_words] SimHash signatures, or NULL
+  int sig_words = 0;
+  float rsig_max = 0.f;        // largest norm of the signature vectors (inflated)
   float* R = nullptr;          // [2 L D][dpad]
   void* Rs = nullptr;          // [2 L D][pieces Kp] BF16 pieces of R (tensor-core operand)
   int Kp = 0;
@@ -163,6 +167,7 @@ void free_index_memory(fpp_index* ix) {
   cudaFree(ix->X);
   cudaFree(ix->Xc);
   cudaFree(ix->c);
+  cudaFree(ix->sig);
   cudaFree(ix->R);
   cudaFree(ix->Rs);
   cudaFree(ix->Xb);
@@ -363,6 +368,11 @@ fpp_status validate_params(int64_t n, int32_t d, const fpp_params* p) {
     set_error("precision must be FPP_FP32 or FPP_BF16");
     return FPP_EINVAL;
   }
+  if (p->simhash_bits < 0 || p->simhash_bits % 256 || p->simhash_bits > 1024 ||
+      p->simhash_bits > 2ll * p->L * p->D) {
+    set_error("simhash_bits must be 0 or a multiple of 256 up to min(1024, 2 L D)");
+    return FPP_EINVAL;
+  }
   if (p->precision == FPP_BF16 && (p->rerank_k < 0 || p->rerank_k > 256)) {
     set_error("rerank_k must be in [0, 256]");
     return FPP_EINVAL;
@@ -548,6 +558,48 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
     return fail(FPP_ETIMEOUT);
   }
   ix->build_rechecks = rech[0];
+  if (p->simhash_bits > 0) {
+    // SimHash signatures of the points over the first simhash_bits random
+    // vectors (the rows of R in table order)
+    const int bits = p->simhash_bits;
+    ix->sig_words = bits / 32;
+    for (int j = 0; j * D < bits; ++j) ix->rsig_max = std::max(ix->rsig_max, hrmax[j]);
+    if (cudaMalloc(&ix->sig, (size_t)n * ix->sig_words * 4) != cudaSuccess) {
+      set_error("cudaMalloc (signatures)");
+      cleanup();
+      return fail(FPP_ENOMEM);
+    }
+    ix->device_bytes += (uint64_t)n * ix->sig_words * 4;
+    const int64_t rows = std::min<int64_t>(n, 1 << 16);
+    if ((s = B.proj.ensure((size_t)rows * bits * 4)) != FPP_OK ||
+        (s = B.norms.ensure((size_t)rows * 4)) != FPP_OK) {
+      cleanup();
+      return fail(s);
+    }
+    for (int64_t r0 = 0; r0 < n && s == FPP_OK; r0 += rows) {
+      const int64_t rc = std::min<int64_t>(rows, n - r0);
+      const float* xr = ix->X + r0 * ix->dpad;
+      s = B.xsplit.ensure((size_t)rc * ix->pieces * ix->Kp * 2);
+      if (s == FPP_OK) s = split_to_bf16(xr, rc, ix->dpad, d, ix->pieces, B.xsplit.p, st);
+      if (s == FPP_OK)
+        s = project_tc(B.xsplit.p, rc, ix->Rs, bits, ix->Kp, ix->pieces, 0, 0, B.proj.as<float>(),
+                       bits, nullptr, reinterpret_cast<int*>(B.rechecks.as<unsigned long long>() + 1), st);
+      if (s == FPP_OK) s = launch_query_norms(xr, rc, ix->dpad, d, B.norms.as<float>(), st);
+      if (s == FPP_OK) {
+        SignArgs sa{};
+        sa.P = B.proj.as<float>(); sa.ldp = bits; sa.rows = rc; sa.words = ix->sig_words;
+        sa.V = xr; sa.ldv = ix->dpad; sa.vnorm = B.norms.as<float>();
+        sa.R = ix->R; sa.ldr = ix->dpad; sa.gamma = ix->gamma; sa.rsig_max = ix->rsig_max;
+        sa.out = ix->sig + r0 * ix->sig_words;
+        s = launch_sign_bits(sa, st);
+      }
+    }
+    if (s == FPP_OK && cudaStreamSynchronize(st) != cudaSuccess) s = FPP_ECUDA;
+    if (s != FPP_OK) {
+      cleanup();
+      return fail(s);
+    }
+  }
   cleanup();
   ix->build_ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - wall0).count();
   *out = ix;
@@ -560,6 +612,7 @@ struct SearchPlan {
   int64_t m;
   int kmax, pmax, tb, te;
   int global_q = 0;     // > 0: global probe budget (pmax = the per-table cap)
+  int sim_keep = 0;     // > 0: SimHash pre-ranking keeps this many candidates
   const int32_t* kpq;   // user arrays (host or device) or NULL
   const int32_t* ppq;
   bool kpq_dev, ppq_dev;
@@ -618,6 +671,15 @@ fpp_status validate_search(const fpp_index* ix, const float* Q, int64_t m, const
       return FPP_EINVAL;
     }
   }
+  if (o->simhash_keep < 0 || o->simhash_keep > 512) {
+    set_error("simhash_keep must be in [0, 512]");
+    return FPP_EINVAL;
+  }
+  if (o->simhash_keep > 0 && !ix->sig) {
+    set_error("simhash_keep needs an index built with simhash_bits");
+    return FPP_EINVAL;
+  }
+  pl.sim_keep = o->simhash_keep;
   pl.kmax = o->k_max > 0 ? o->k_max : kmax_seen;
   if (pl.kmax < kmax_seen || pl.kmax > 256) { set_error("k_max must cover every k and be <= 256"); return FPP_EINVAL; }
   pl.pmax = std::max(1, pmax_seen);
@@ -665,6 +727,19 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
                        EL ? ws.proj.as<uint64_t>() : nullptr, EL));
   if (ev) FPP_CUDA(cudaEventRecord(ev[1], st));
   FPP_TRY(launch_query_norms(ws.qpad.as<float>(), mc, ix->dpad, ix->d, ws.qnorm.as<float>(), st));
+  if (pl.sim_keep > 0) {
+    // the queries' SimHash signatures from their split pieces
+    const int bits = ix->sig_words * 32;
+    FPP_TRY(project_tc(ws.qsplit.p, mc, ix->Rs, bits, ix->Kp, ix->pieces, 0, 0,
+                       ws.sigproj.as<float>(), bits, nullptr,
+                       reinterpret_cast<int*>(ws.stats.as<unsigned long long>() + 9), st));
+    SignArgs sg{};
+    sg.P = ws.sigproj.as<float>(); sg.ldp = bits; sg.rows = mc; sg.words = ix->sig_words;
+    sg.V = ws.qpad.as<float>(); sg.ldv = ix->dpad; sg.vnorm = ws.qnorm.as<float>();
+    sg.R = ix->R; sg.ldr = ix->dpad; sg.gamma = ix->gamma; sg.rsig_max = ix->rsig_max;
+    sg.out = ws.qsig.as<uint32_t>();
+    FPP_TRY(launch_sign_bits(sg, st));
+  }
   ProbeArgs pa{};
   pa.P = EL ? nullptr : ws.proj.as<float>(); pa.ldp = ldp; pa.mq = mc;
   pa.lists = EL ? ws.proj.as<uint64_t>() : nullptr; pa.EL = EL;
@@ -694,6 +769,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   da.ecount = ws.ecount.as<uint32_t>(); da.eoff = ws.eoff.as<uint64_t>();
   da.ucount = ws.ecount.as<uint32_t>() + mc;
   da.nitems = reinterpret_cast<unsigned*>(stv + 10);
+  da.no_items = pl.sim_keep > 0 ? 1 : 0;
   da.stats = stv;
   FPP_TRY(launch_count_entries(da, st));
   FPP_TRY(exclusive_scan_u32(ws.ecount.as<uint32_t>(), mc, ws.eoff.as<uint64_t>(), 0,
@@ -721,6 +797,14 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   da.cand = ws.cand.as<uint32_t>();
   da.items = ws.items.as<ScoreItem>();
   FPP_TRY(launch_dedup(da, st));
+  if (pl.sim_keep > 0) {
+    SimArgs sm{};
+    sm.mq = mc; sm.eoff = ws.eoff.as<uint64_t>(); sm.cand = ws.cand.as<uint32_t>();
+    sm.ucount = da.ucount; sm.xsig = ix->sig; sm.qsig = ws.qsig.as<uint32_t>();
+    sm.words = ix->sig_words; sm.keep = pl.sim_keep; sm.cap = topk_cap(pl.sim_keep);
+    sm.items = ws.items.as<ScoreItem>(); sm.nitems = da.nitems;
+    FPP_TRY(launch_simhash_filter(sm, st));
+  }
   if (ev) FPP_CUDA(cudaEventRecord(ev[5], st));
   if (stage == kCandidatesOnly) return FPP_OK;
   ScoreArgs sa{};
@@ -773,6 +857,10 @@ fpp_status prepare_workspace(fpp_index* ix, Workspace& ws, const SearchPlan& pl,
   FPP_TRY(ws.recheck.ensure((size_t)mc * nt * 4, false, st));
   FPP_TRY(ws.recheck2.ensure((size_t)mc * nt * 4, false, st));
   FPP_TRY(ws.recheck_s.ensure((size_t)mc * nt * 8, false, st));
+  if (pl.sim_keep > 0) {
+    FPP_TRY(ws.sigproj.ensure((size_t)mc * ix->sig_words * 32 * 4, false, st));
+    FPP_TRY(ws.qsig.ensure((size_t)mc * ix->sig_words * 4, false, st));
+  }
   FPP_TRY(ws.kpq.ensure((size_t)mc * 4, false, st));
   FPP_TRY(ws.ppq.ensure((size_t)mc * 4, false, st));
   FPP_TRY(ws.stats.ensure(16 * 8, true, st));
@@ -813,7 +901,7 @@ bool search_graph(fpp_index* ix, const float* Q, int64_t m, const fpp_search_opt
       (uint64_t)(uintptr_t)Q, (uint64_t)m, (uint64_t)(uintptr_t)ids, (uint64_t)(uintptr_t)scores,
       (uint64_t)(uintptr_t)pl.kpq, (uint64_t)(uintptr_t)pl.ppq, (uint64_t)pl.k,
       (uint64_t)pl.probes, (uint64_t)pl.kmax, (uint64_t)pl.pmax, (uint64_t)pl.tb, (uint64_t)pl.te,
-      (uint64_t)(uintptr_t)st, (uint64_t)pl.global_q, g_alloc_gen.load()};
+      (uint64_t)(uintptr_t)st, (uint64_t)pl.global_q, (uint64_t)pl.sim_keep, g_alloc_gen.load()};
   if (!ix->graph_exec || ix->graph_key != key) {
     if (ix->graph_exec) cudaGraphExecDestroy(ix->graph_exec);
     ix->graph_exec = nullptr;
@@ -1304,6 +1392,7 @@ fpp_status fpp_index_get_info(const fpp_index* ix, fpp_index_info* info) {
   info->build_ms = ix->build_ms;
   info->rerank_k = ix->rerank_k;
   info->center = ix->center;
+  info->simhash_bits = ix->sig_words * 32;
   info->score_error_factor = ix->score_gamma;
   return FPP_OK;
 }

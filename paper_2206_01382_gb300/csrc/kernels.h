@@ -69,6 +69,25 @@ struct HashArgs {
 };
 fpp_status launch_build_hash(const HashArgs& a, cudaStream_t st);
 
+// SimHash signature bits (Section 4): bit i of row r is [v_r^T r_i >= 0]
+// for the first 32 W random vectors, from the FP32 projections P [rows][ldp]
+// where |p| exceeds eps_r = gamma ||v_r|| rsig_max, else from a compensated
+// dot product.  out: [rows][W] uint32, little-endian bits.
+struct SignArgs {
+  const float* P;
+  int64_t ldp, rows;
+  int words;
+  const float* V;            // [rows][ldv] padded vectors
+  int64_t ldv;
+  const float* vnorm;        // [rows] norm upper bounds
+  const float* R;            // signature vectors [32 W][ldr]
+  int64_t ldr;
+  double gamma;
+  float rsig_max;
+  uint32_t* out;
+};
+fpp_status launch_sign_bits(const SignArgs& a, cudaStream_t st);
+
 // Multi-probe indexing (Algorithm 1, iProbes > 1): the records of the
 // iProbes buckets each point was ranked into (probe kernels run on the
 // points), with the exact pair score v1(h1) + v2(h2) as filter score.
@@ -183,8 +202,27 @@ struct DedupArgs {
   uint32_t* ucount;          // [mq] distinct candidates per query
   ScoreItem* items;          // score work items, appended (any order)
   unsigned* nitems;          // items appended (zeroed by count_entries)
+  int no_items;              // 1: leave the items to the SimHash filter
   unsigned long long* stats; // entries, unique, -, probes
 };
+
+// SimHash pre-ranking: for every query with more than keep candidates,
+// the keep with the fewest differing signature bits (ties: lower id) are
+// moved to the front of its region and become its candidates; then the
+// score work items of every query are appended (the de-duplication kernels
+// skip that step when this runs).
+struct SimArgs {
+  int64_t mq;
+  const uint64_t* eoff;
+  uint32_t* cand;
+  uint32_t* ucount;
+  const uint32_t* xsig;      // [n][W]
+  const uint32_t* qsig;      // [mq][W]
+  int words, keep, cap;
+  ScoreItem* items;
+  unsigned* nitems;
+};
+fpp_status launch_simhash_filter(const SimArgs& a, cudaStream_t st);
 
 struct ScoreArgs {
   const ScoreItem* items;    // [*nitems] work items

@@ -890,6 +890,33 @@ global_probes_kernel(ProbeArgs a, int Qp, int npow2) {
   (void)s_tcount;
 }
 
+// SimHash signature bits (Section 4: the signatures reuse the index's
+// random projections).  One thread per (row, 32-bit word); a bit whose FP32
+// projection lies inside the error bound is taken from a compensated dot
+// product, so every bit is the sign of the exact projection (0 counts as +).
+__global__ void __launch_bounds__(256)
+sign_bits_kernel(SignArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.rows * a.words) return;
+  const int64_t r = i / a.words;
+  const int w = (int)(i - r * a.words);
+  const float eps = (float)(a.gamma * (double)a.vnorm[r] * (double)a.rsig_max * 1.0001);
+  const int nf4 = (int)(a.ldv / 4);
+  uint32_t bits = 0;
+  for (int b = 0; b < 32; ++b) {
+    const int c = w * 32 + b;
+    const float p = a.P[r * a.ldp + c];
+    bool pos;
+    if (fabsf(p) > eps) {
+      pos = p >= 0.f;
+    } else {
+      pos = thread_dot2_f4(a.V + r * a.ldv, a.R + (int64_t)c * a.ldr, nf4) >= 0.0;
+    }
+    bits |= (pos ? 1u : 0u) << b;
+  }
+  a.out[r * a.words + w] = bits;
+}
+
 __global__ void query_norms_kernel(const float* __restrict__ Q, int64_t m, int64_t ldq, int d,
                                    float* __restrict__ out) {
   const int lane = threadIdx.x & 31;
@@ -1009,6 +1036,7 @@ __device__ __forceinline__ void warp_walk(const WarpWalk& w, Visit& visit) {
 // Appends query q's ceil(U / ITEM) score work items (at most ITEM candidates
 // each) to the item list (one counter atomic per query, warp-collective).
 __device__ __forceinline__ void write_items(const DedupArgs& a, int64_t q, uint32_t U) {
+  if (a.no_items) return;
   const int lane = threadIdx.x & 31;
   const uint32_t nit = (U + ITEM - 1) / ITEM;
   unsigned base = 0;
@@ -1217,7 +1245,7 @@ dedup_hash_kernel(DedupArgs a) {
       __syncthreads();   // pbase / pstart are rewritten by the next chunk
     }
     const uint32_t U = s_n;
-    const uint32_t nit = (U + ITEM - 1) / ITEM;
+    const uint32_t nit = a.no_items ? 0u : (U + ITEM - 1) / ITEM;
     if (tid == 0) {
       ent += E;
       uni += U;
@@ -1242,6 +1270,54 @@ dedup_hash_kernel(DedupArgs a) {
     atomicAdd(a.stats + 0, ent);
     atomicAdd(a.stats + 1, uni);
     atomicAdd(a.stats + 3, prb);
+  }
+}
+
+// SimHash pre-ranking, warp per query (see SimArgs).
+__global__ void __launch_bounds__(256)
+simhash_filter_kernel(SimArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * 8 + wid;
+  if (q >= a.mq) return;
+  uint64_t* buf = reinterpret_cast<uint64_t*>(smem) + (size_t)wid * a.cap;
+  uint32_t* reg = a.cand + a.eoff[q];
+  uint32_t U = a.ucount[q];
+  if (U > (uint32_t)a.keep) {
+    const uint32_t* qs = a.qsig + q * a.words;
+    WarpTop wt;
+    wt.init(buf, a.cap, a.keep);
+    for (uint32_t i0 = 0; i0 < U; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      const bool ok = i < U;
+      uint64_t key = 0ull;
+      if (ok) {
+        const uint32_t id = reg[i];
+        const uint32_t* xs = a.xsig + (int64_t)id * a.words;
+        uint32_t h = 0;
+        for (int w = 0; w < a.words; ++w) h += __popc(__ldg(xs + w) ^ __ldg(qs + w));
+        // larger key = fewer differing bits, then lower id
+        key = ((uint64_t)(0xFFFFFFFFu - h) << 32) | (uint64_t)(0xFFFFFFFFu - id);
+      }
+      wt.offer(ok, key);
+    }
+    const int nk = wt.finish();
+    __syncwarp();
+    for (int e = lane; e < nk; e += 32) reg[e] = 0xFFFFFFFFu - (uint32_t)buf[e];
+    U = (uint32_t)nk;
+    if (lane == 0) a.ucount[q] = U;
+    __syncwarp();
+  }
+  const uint32_t nit = (U + ITEM - 1) / ITEM;
+  unsigned base = 0;
+  if (lane == 0 && nit) base = atomicAdd(a.nitems, nit);
+  base = __shfl_sync(FULL, base, 0);
+  for (uint32_t k = lane; k < nit; k += 32) {
+    ScoreItem it;
+    it.q = (uint32_t)q;
+    it.len = min((uint32_t)ITEM, U - k * ITEM);
+    it.start = a.eoff[q] + (uint64_t)k * ITEM;
+    a.items[base + k] = it;
   }
 }
 
@@ -1857,6 +1933,24 @@ fpp_status launch_global_probes(const ProbeArgs& a, int Qp, cudaStream_t st) {
   FPP_CUDA(cudaFuncSetAttribute(global_probes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   global_probes_kernel<<<(unsigned)a.mq, GP_THREADS, smem, st>>>(a, Qp, npow2);
+  FPP_LAUNCHED();
+  return FPP_OK;
+}
+
+fpp_status launch_sign_bits(const SignArgs& a, cudaStream_t st) {
+  const int64_t n = a.rows * a.words;
+  if (n <= 0) return FPP_OK;
+  sign_bits_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(a);
+  FPP_LAUNCHED();
+  return FPP_OK;
+}
+
+fpp_status launch_simhash_filter(const SimArgs& a, cudaStream_t st) {
+  if (a.mq <= 0) return FPP_OK;
+  const size_t smem = (size_t)8 * a.cap * 8;
+  FPP_CUDA(cudaFuncSetAttribute(simhash_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)std::max<size_t>(smem, 48 * 1024)));
+  simhash_filter_kernel<<<(unsigned)ceil_div(a.mq, 8), 256, smem, st>>>(a);
   FPP_LAUNCHED();
   return FPP_OK;
 }

@@ -364,3 +364,23 @@ def test_global_probes_parity(F, Qp, L, D):
     c, s, fails = PT.compare_search(res, gi, gs, 10, list(range(L)), excl)
     assert not fails, fails[:3]
     assert c >= 0.7 * len(res), (c, s)
+
+
+@pytest.mark.parametrize("bits,keep", [(256, 40), (512, 7)])
+def test_simhash_preranking_parity(F, bits, keep):
+    # Section 4: candidates pre-ranked by SimHash signatures of the index's
+    # random vectors; the keep closest (Hamming) are scored exactly
+    X, Q = W.small_mixture(8000, 60, 48, 64, 0.25, 97 + keep)
+    L, D = 8, 32
+    ix_o = O.build_index(X, L, D, 0.3, seed=15)
+    ix_g = F.Index(X, L, D, 0.3, seed=15, simhash_bits=bits)
+    assert ix_g.info()["simhash_bits"] == bits
+    sig = O.simhash_signatures(ix_o, X, bits)
+    excl = {t: PT.excluded_buckets(ix_o, t, F.fpp_debug_point_buckets(ix_g.handle, t))
+            for t in range(L)}
+    for P in (2, 6):
+        gi, gs, _ = F.fpp_search_ex(ix_g.handle, Q, k=10, probes=P, simhash_keep=keep)
+        _, _, res = O.search_batch(ix_o, Q, 10, P, simhash=(sig, bits, keep))
+        c, s, fails = PT.compare_search(res, gi, gs, 10, list(range(L)), excl)
+        assert not fails, fails[:3]
+        assert c >= 0.7 * len(res), (c, s)
