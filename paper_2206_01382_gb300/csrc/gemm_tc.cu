@@ -45,17 +45,12 @@ constexpr uint32_t A_TILE = TC_BM * TC_BK * 2;         // 16 KB
 constexpr uint32_t B_TILE = TC_BN * TC_BK * 2;         // 32 KB
 constexpr uint32_t STAGE_BYTES = A_TILE + B_TILE;
 constexpr long long WAIT_CYCLES = 4000000000ll;        // ~2 s at 2 GHz
-// A-resident mode (exact split, Kp <= 128): the query tile's three pieces
-// stay in shared memory while the CTA walks the tiles of its row block, and
-// only B tiles stream through a TC_STAGES_B-deep ring
-constexpr int TC_STAGES_B = 3;
 
 struct __align__(8) TcShared {
   uint64_t full[TC_STAGES];
   uint64_t empty[TC_STAGES];
   uint64_t tfull[2];
   uint64_t tempty[2];
-  uint64_t afull, afree;      // A-resident mode: the row block's A tiles loaded / released
   uint32_t tmem_base;
   int abort;
   // list mode with D = 256: the second column half of every row hands its
@@ -231,35 +226,7 @@ __device__ __forceinline__ void chunk_pieces(int c, int nkb, int pieces, int& pa
 // FP32 projections.  EL > 0: for every (row, hash) it keeps the EL largest
 // keys of the hash's D columns (D divides 256) followed by a "cut" key whose
 // value is the largest |p| left out, and stores only those EL + 1 keys.
-// The products of the exact split grouped by their B piece (A-resident
-// mode): group g multiplies B piece group_b(g) with the group_n(g) A pieces
-// group_a(g, j); the five small products come first and hi.hi alone last,
-// as in the streaming order, so the error bound is the same.
-__device__ __forceinline__ int group_b(int g) { return g == 0 ? 2 : g == 1 ? 1 : 0; }
-__device__ __forceinline__ int group_n(int g) { return (g == 1 || g == 2) ? 2 : 1; }
-__device__ __forceinline__ int group_a(int g, int j) {
-  return g == 0 ? 0 : g == 1 ? j : g == 2 ? 1 + j : 0;
-}
-
-// Tiles of a CTA: contiguous ranges (row-block major) in A-resident mode,
-// so consecutive tiles share their A tile; strided otherwise.
-struct TileRange {
-  int t, end, step;
-  __device__ TileRange(bool contiguous, int ntiles) {
-    if (contiguous) {
-      const int64_t G = gridDim.x, b = blockIdx.x;
-      t = (int)(b * ntiles / G);
-      end = (int)((b + 1) * ntiles / G);
-      step = 1;
-    } else {
-      t = blockIdx.x;
-      end = ntiles;
-      step = gridDim.x;
-    }
-  }
-};
-
-template <int EL, bool ARES>
+template <int EL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                float* __restrict__ C, int64_t ldc, uint64_t* __restrict__ lists, int M, int N,
@@ -267,25 +234,19 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   extern __shared__ __align__(1024) unsigned char dsm[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
-  const int nkb = Kp / TC_BK;
-  constexpr int NSTAGE = ARES ? TC_STAGES_B : TC_STAGES;
-  constexpr uint32_t SBYTES = ARES ? B_TILE : STAGE_BYTES;
-  unsigned char* ares = base;                                   // A-resident tiles
-  unsigned char* stages = ARES ? base + (size_t)3 * nkb * A_TILE : base;
-  TcShared* sh = reinterpret_cast<TcShared*>(stages + NSTAGE * SBYTES);
+  TcShared* sh = reinterpret_cast<TcShared*>(base + TC_STAGES * STAGE_BYTES);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nchunks = ARES ? 4 * nkb : (pieces == 1 ? 1 : 6) * nkb;
+  const int nkb = Kp / TC_BK;
+  const int nchunks = (pieces == 1 ? 1 : 6) * nkb;
   const int ntn = (N + TC_BN - 1) / TC_BN, ntm = (M + TC_BM - 1) / TC_BM;
   const int ntiles = ntn * ntm;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NSTAGE; ++s) {
+    for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&sh->full[s], 1);
       mbar_init(&sh->empty[s], 1);
     }
-    mbar_init(&sh->afull, 1);
-    mbar_init(&sh->afree, 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sh->tfull[b], 1);
       mbar_init(&sh->tempty[b], EPI_WARPS);
@@ -309,41 +270,21 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
     uint32_t g = 0;
-    int cur_m = -1;
-    uint32_t aload = 0;
-    for (TileRange tr(ARES, ntiles); tr.t < tr.end; tr.t += tr.step) {
-      const int t = tr.t;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
       const int m0 = (t / ntn) * TC_BM, n0 = (t % ntn) * TC_BN;
       bool ok = true;
-      if (ARES && m0 != cur_m) {
-        // the previous row block's MMAs must be done with the A tiles
-        if (aload > 0 && !mbar_wait(&sh->afree, (aload - 1) & 1, sh, err, 5)) break;
-        mbar_expect_tx(&sh->afull, (uint32_t)(3 * nkb) * A_TILE);
-        for (int pa = 0; pa < 3; ++pa)
-          for (int kb = 0; kb < nkb; ++kb)
-            tma_load_2d(ares + (size_t)(pa * nkb + kb) * A_TILE, &mapA, pa * Kp + kb * TC_BK, m0,
-                        &sh->afull);
-        ++aload;
-        cur_m = m0;
-      }
       for (int c = 0; c < nchunks; ++c, ++g) {
-        const uint32_t s = g % NSTAGE;
-        if (g >= NSTAGE && !mbar_wait(&sh->empty[s], ((g / NSTAGE) - 1) & 1, sh, err, 1)) {
+        const uint32_t s = g % TC_STAGES;
+        if (g >= TC_STAGES && !mbar_wait(&sh->empty[s], ((g / TC_STAGES) - 1) & 1, sh, err, 1)) {
           ok = false;
           break;
         }
-        unsigned char* st = stages + s * SBYTES;
-        if (ARES) {
-          const int grp = c / nkb, kb = c - grp * nkb;
-          mbar_expect_tx(&sh->full[s], B_TILE);
-          tma_load_2d(st, &mapB, group_b(grp) * Kp + kb * TC_BK, n0, &sh->full[s]);
-        } else {
-          int pa, pb, kb;
-          chunk_pieces(c, nkb, pieces, pa, pb, kb);
-          mbar_expect_tx(&sh->full[s], STAGE_BYTES);
-          tma_load_2d(st, &mapA, pa * Kp + kb * TC_BK, m0, &sh->full[s]);
-          tma_load_2d(st + A_TILE, &mapB, pb * Kp + kb * TC_BK, n0, &sh->full[s]);
-        }
+        int pa, pb, kb;
+        chunk_pieces(c, nkb, pieces, pa, pb, kb);
+        unsigned char* st = base + s * STAGE_BYTES;
+        mbar_expect_tx(&sh->full[s], STAGE_BYTES);
+        tma_load_2d(st, &mapA, pa * Kp + kb * TC_BK, m0, &sh->full[s]);
+        tma_load_2d(st + A_TILE, &mapB, pb * Kp + kb * TC_BK, n0, &sh->full[s]);
       }
       if (!ok) break;
     }
@@ -351,49 +292,25 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     // ---------------- MMA issuer
     uint32_t g = 0;
     int i = 0;
-    int cur_m = -1;
-    uint32_t aload = 0;
-    for (TileRange tr(ARES, ntiles); tr.t < tr.end; tr.t += tr.step, ++i) {
-      const int t = tr.t;
-      const int m0 = (t / ntn) * TC_BM;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
       const int b = i & 1;
       if (i >= 2 && !mbar_wait(&sh->tempty[b], ((i >> 1) - 1) & 1, sh, err, 4)) break;
-      if (ARES && m0 != cur_m) {
-        if (!mbar_wait(&sh->afull, aload & 1, sh, err, 6)) break;
-        ++aload;
-        cur_m = m0;
-      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t d = tmem + (uint32_t)(b * TC_BN);
       bool ok = true;
       for (int c = 0; c < nchunks; ++c, ++g) {
-        const uint32_t s = g % NSTAGE;
-        if (!mbar_wait(&sh->full[s], (g / NSTAGE) & 1, sh, err, 2)) { ok = false; break; }
+        const uint32_t s = g % TC_STAGES;
+        if (!mbar_wait(&sh->full[s], (g / TC_STAGES) & 1, sh, err, 2)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ARES) {
-          const int grp = c / nkb, kb = c - grp * nkb;
-          const uint32_t b_addr = smem_u32(stages + s * SBYTES);
-          for (int j = 0; j < group_n(grp); ++j) {
-            const uint32_t a_addr = smem_u32(ares + (size_t)(group_a(grp, j) * nkb + kb) * A_TILE);
+        const uint32_t a_addr = smem_u32(base + s * STAGE_BYTES);
+        const uint32_t b_addr = a_addr + A_TILE;
 #pragma unroll
-            for (int kk = 0; kk < TC_BK / 16; ++kk)
-              mma_bf16(d, smem_desc_sw128(a_addr + kk * 32), smem_desc_sw128(b_addr + kk * 32),
-                       (c == 0 && j == 0 && kk == 0) ? 0u : 1u);
-          }
-        } else {
-          const uint32_t a_addr = smem_u32(stages + s * SBYTES);
-          const uint32_t b_addr = a_addr + A_TILE;
-#pragma unroll
-          for (int kk = 0; kk < TC_BK / 16; ++kk)
-            mma_bf16(d, smem_desc_sw128(a_addr + kk * 32), smem_desc_sw128(b_addr + kk * 32),
-                     (c == 0 && kk == 0) ? 0u : 1u);
-        }
+        for (int kk = 0; kk < TC_BK / 16; ++kk)
+          mma_bf16(d, smem_desc_sw128(a_addr + kk * 32), smem_desc_sw128(b_addr + kk * 32),
+                   (c == 0 && kk == 0) ? 0u : 1u);
         mma_commit(&sh->empty[s]);
       }
       mma_commit(&sh->tfull[b]);
-      // the row block's last tile: release the A tiles once its MMAs are done
-      if (ARES && (tr.t + tr.step >= tr.end || ((tr.t + tr.step) / ntn) * TC_BM != m0))
-        mma_commit(&sh->afree);
       if (!ok) break;
     }
   } else if (warp >= 2) {
@@ -404,8 +321,7 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     const int NH = N / D;   // hashes per row (list mode)
     const int LS = EL + 1;  // list stride: EL keys and the cut
     int i = 0;
-    for (TileRange tr(ARES, ntiles); tr.t < tr.end; tr.t += tr.step, ++i) {
-      const int t = tr.t;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
       const int b = i & 1;
       const int m0 = (t / ntn) * TC_BM, n0 = (t % ntn) * TC_BN;
       if (!mbar_wait(&sh->tfull[b], (i >> 1) & 1, sh, err, 3)) break;
@@ -629,18 +545,16 @@ fpp_status split_to_bf16(const float* src, int64_t rows, int64_t lds, int d, int
 
 namespace {
 
-template <int EL, bool ARES>
-fpp_status launch_proj_k(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int64_t ldc,
-                         uint64_t* lists, int64_t M, int64_t N, int Kp, int pieces, int D, int* err,
-                         cudaStream_t st) {
-  // shared memory: the ring (and, A-resident, up to 2 x 3 A tiles) and the barriers
-  const size_t smem = ARES ? 1024 + (size_t)6 * A_TILE + TC_STAGES_B * B_TILE + sizeof(TcShared)
-                           : 1024 + (size_t)TC_STAGES * STAGE_BYTES + sizeof(TcShared);
+template <int EL>
+fpp_status launch_proj(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int64_t ldc,
+                       uint64_t* lists, int64_t M, int64_t N, int Kp, int pieces, int D, int* err,
+                       cudaStream_t st) {
+  const size_t smem = 1024 + TC_STAGES * STAGE_BYTES + sizeof(TcShared);
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&]() {
-    attr_err = cudaFuncSetAttribute(tc_proj_kernel<EL, ARES>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_err = cudaFuncSetAttribute(tc_proj_kernel<EL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
   });
   FPP_CUDA(attr_err);
   int dev = 0, sms = 0;
@@ -648,21 +562,10 @@ fpp_status launch_proj_k(const CUtensorMap& ma, const CUtensorMap& mb, float* C,
   FPP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t ntiles = ceil_div(M, TC_BM) * ceil_div(N, TC_BN);
   const int grid = (int)std::min<int64_t>(ntiles, sms);
-  tc_proj_kernel<EL, ARES><<<grid, TC_THREADS, smem, st>>>(ma, mb, C, ldc, lists, (int)M, (int)N,
-                                                           Kp, pieces, D, err);
+  tc_proj_kernel<EL><<<grid, TC_THREADS, smem, st>>>(ma, mb, C, ldc, lists, (int)M, (int)N, Kp,
+                                                     pieces, D, err);
   FPP_LAUNCHED();
   return FPP_OK;
-}
-
-// The exact split with Kp <= 128 keeps A resident (three pieces of at most
-// 2 x 16 KB); otherwise A and B stream together.
-template <int EL>
-fpp_status launch_proj(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int64_t ldc,
-                       uint64_t* lists, int64_t M, int64_t N, int Kp, int pieces, int D, int* err,
-                       cudaStream_t st) {
-  if (pieces == 3 && Kp <= 2 * TC_BK)
-    return launch_proj_k<EL, true>(ma, mb, C, ldc, lists, M, N, Kp, pieces, D, err, st);
-  return launch_proj_k<EL, false>(ma, mb, C, ldc, lists, M, N, Kp, pieces, D, err, st);
 }
 
 }  // namespace
