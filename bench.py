@@ -47,9 +47,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="plain1m", choices=sorted(W.WORKLOADS))
     ap.add_argument("--probes", type=int, default=0, help="force a probe budget")
-    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32",
-                    help="fp32: exact decisions; bf16: BF16 projections and scores with an "
-                         "FP32 re-ranked shortlist")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="fp32",
+                    help="fp32: exact decisions; bf16 / fp8: candidate rows in BF16 / FP8 e4m3 "
+                         "with an exactly re-scored shortlist")
     ap.add_argument("--rerank-k", type=int, default=100)
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="serving workload: seconds of arrivals per offered rate")
@@ -235,7 +235,7 @@ def run_serve(args, w):
     X, Q = W.dataset(w)
     Xd = torch.from_numpy(X).cuda()
     Qd = torch.from_numpy(Q[:CALIB_QUERIES]).cuda()
-    prec = F.FPP_BF16 if args.precision == "bf16" else F.FPP_FP32
+    prec = {"fp32": F.FPP_FP32, "bf16": F.FPP_BF16, "fp8": F.FPP_FP8E4M3}[args.precision]
     tb = time.perf_counter()
     ix = F.Index(Xd, w.L, w.D, w.alpha, seed=w.rot_seed, precision=prec, rerank_k=args.rerank_k)
     torch.cuda.synchronize()
@@ -295,9 +295,10 @@ def run_serve(args, w):
         "metric": METRIC, "value": sat["qps"], "unit": "queries/s", "n_gpus": 1,
         "steps": len(W.SERVE_RATES) + 1, "warmup": 1, "ms_per_step": None,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if prec == F.FPP_BF16 else "f32", "data": "synthetic",
+        "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "fp8e4m3"}[args.precision],
+        "data": "synthetic",
         "config": {"workload": w.name, "note": w.note, "precision": args.precision,
-                   "rerank_k": args.rerank_k if prec == F.FPP_BF16 else None,
+                   "rerank_k": args.rerank_k if prec != F.FPP_FP32 else None,
                    "n": w.n, "d": w.d, "L": w.L, "D": w.D, "alpha": w.alpha, "probes": P,
                    "recall_at_10": recalls[P], "recall_sweep": recalls, "recall_sample": mcal,
                    "slots": args.slots, "max_batch": 4096, "build_s": build_s,
@@ -352,7 +353,7 @@ def main():
     Qd = torch.from_numpy(Q).to(dev)
     torch.cuda.synchronize()
     tb = time.perf_counter()
-    prec = F.FPP_BF16 if args.precision == "bf16" else F.FPP_FP32
+    prec = {"fp32": F.FPP_FP32, "bf16": F.FPP_BF16, "fp8": F.FPP_FP8E4M3}[args.precision]
     ix = F.Index(Xd, w.L, w.D, w.alpha, seed=w.rot_seed, precision=prec, rerank_k=args.rerank_k)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - tb
@@ -435,8 +436,9 @@ def main():
     per = chunks * K
     qpl = m / chunks
     d = w.d
-    bf16 = args.precision == "bf16"
-    row_bytes = 2 * (-(-d // 8) * 8) if bf16 else 4 * d
+    bf16 = args.precision != "fp32"
+    row_bytes = (2 * (-(-d // 8) * 8) + 0 if args.precision == "bf16"
+                 else (-(-d // 16) * 16 + 4) if args.precision == "fp8" else 4 * d)
     kprime = max(k + 16, args.rerank_k if bf16 else 0)
     probes_pl, entries_pl, unique_pl = (tot["probes"] / per, tot["entries"] / per,
                                         tot["unique"] / per)
@@ -479,7 +481,8 @@ def main():
         "dedup": hbm("dedup_hash_kernel", "search_kernels.cu", ms_of["ms_dedup"], dedup_b,
                      "count_entries + scan + dedup_hash + dedup (bitmap) kernels; "
                      "latency-bound bucket walk"),
-        "score": hbm("score_bf16_kernel" if bf16 else "score_kernel", "search_kernels.cu",
+        "score": hbm({"fp32": "score_kernel", "bf16": "score_bf16_kernel",
+                      "fp8": "score_fp8_kernel"}[args.precision], "search_kernels.cu",
                      ms_of["ms_score"], score_b, "candidate rows streamed once"),
         "topk": hbm("topk_kernel", "search_kernels.cu", ms_of["ms_topk"], topk_b,
                     "selection, exact re-scoring of the shortlist"),
@@ -551,7 +554,7 @@ def main():
             "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16" if bf16 else "f32",
+            "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "fp8e4m3"}[args.precision],
             "data": "synthetic",
             "config": {"workload": w.name, "note": w.note, "precision": args.precision,
                        "rerank_k": args.rerank_k if bf16 else None,

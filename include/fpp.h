@@ -58,7 +58,7 @@ typedef enum fpp_status {
 
 typedef enum fpp_precision {
   FPP_FP32 = 0,      /* FP32 storage and projections, FP64-exact decisions */
-  FPP_BF16 = 1       /* Candidate scores are read from a BF16 copy of X
+  FPP_BF16 = 1,      /* Candidate scores are read from a BF16 copy of X
                         (FP32 accumulation); the best max(rerank_k, k + 16)
                         of them form the shortlist, and every shortlisted
                         candidate within twice the BF16 error window
@@ -68,6 +68,13 @@ typedef enum fpp_precision {
                         Hashing and probing are as for FPP_FP32.  The index
                         holds X in both precisions (6 bytes per element).
                         Graded by recall and score error. */
+  FPP_FP8E4M3 = 2    /* As FPP_BF16 with candidate rows stored in FP8 e4m3
+                        (one byte per element) times a per-row FP32 scale
+                        (the row's largest magnitude / 448); the window is
+                        nine estimated standard deviations of the e4m3
+                        rounding error (unit roundoff 2^-4).  5 bytes per
+                        element with the FP32 rows.  Graded by recall and
+                        score error. */
 } fpp_precision;
 
 /* Index parameters.  Initialise with fpp_default_params(). */

@@ -20,7 +20,7 @@ import numpy as np
 from . import _build
 
 FPP_OK, FPP_EINVAL, FPP_ENOMEM, FPP_ECUDA, FPP_ETIMEOUT, FPP_EBUSY, FPP_EINTERNAL = range(7)
-FPP_FP32, FPP_BF16 = 0, 1
+FPP_FP32, FPP_BF16, FPP_FP8E4M3 = 0, 1, 2
 FPP_SEARCH_GRAPH = 1
 STATUS_NAMES = {0: "FPP_OK", 1: "FPP_EINVAL", 2: "FPP_ENOMEM", 3: "FPP_ECUDA",
                 4: "FPP_ETIMEOUT", 5: "FPP_EBUSY", 6: "FPP_EINTERNAL"}

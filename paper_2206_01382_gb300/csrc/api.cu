@@ -120,6 +120,9 @@ struct fpp_index {
   int pieces = 3;              // 3: exact split (FPP_FP32); 1: plain BF16 (FPP_BF16)
   void* Xb = nullptr;          // [n][ldxb] BF16 copy of X (FPP_BF16 only)
   int64_t ldxb = 0;
+  uint8_t* Xq = nullptr;       // [n][ldxq] FP8 e4m3 copy of X (FPP_FP8E4M3 only)
+  int64_t ldxq = 0;
+  float* xscale = nullptr;     // [n] scales of the FP8 rows
   int rerank_k = 0;            // FPP_BF16: shortlist re-ranked on the FP32 rows
   double score_gamma = 0.0;    // candidate score error factor
   uint64_t cand_budget_entries = 0;  // candidate slots a batch may provision without a read-back
@@ -171,6 +174,8 @@ void free_index_memory(fpp_index* ix) {
   cudaFree(ix->R);
   cudaFree(ix->Rs);
   cudaFree(ix->Xb);
+  cudaFree(ix->Xq);
+  cudaFree(ix->xscale);
   cudaFree(ix->rmax);
   cudaFree(ix->offsets);
   cudaFree(ix->table_base);
@@ -364,8 +369,8 @@ fpp_status validate_params(int64_t n, int32_t d, const fpp_params* p) {
     return FPP_EINVAL;
   }
   if (p->kappa < 0) { set_error("kappa must be >= 0"); return FPP_EINVAL; }
-  if (p->precision != FPP_FP32 && p->precision != FPP_BF16) {
-    set_error("precision must be FPP_FP32 or FPP_BF16");
+  if (p->precision != FPP_FP32 && p->precision != FPP_BF16 && p->precision != FPP_FP8E4M3) {
+    set_error("precision must be FPP_FP32, FPP_BF16 or FPP_FP8E4M3");
     return FPP_EINVAL;
   }
   if (p->simhash_bits < 0 || p->simhash_bits % 256 || p->simhash_bits > 1024 ||
@@ -373,7 +378,7 @@ fpp_status validate_params(int64_t n, int32_t d, const fpp_params* p) {
     set_error("simhash_bits must be 0 or a multiple of 256 up to min(1024, 2 L D)");
     return FPP_EINVAL;
   }
-  if (p->precision == FPP_BF16 && (p->rerank_k < 0 || p->rerank_k > 256)) {
+  if (p->precision != FPP_FP32 && (p->rerank_k < 0 || p->rerank_k > 256)) {
     set_error("rerank_k must be in [0, 256]");
     return FPP_EINVAL;
   }
@@ -409,6 +414,9 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
   if (p->precision == FPP_BF16) {
     ix->rerank_k = p->rerank_k;
     ix->score_gamma = bf16_window_factor(d);
+  } else if (p->precision == FPP_FP8E4M3) {
+    ix->rerank_k = p->rerank_k;
+    ix->score_gamma = fp8_window_factor(d);
   } else {
     ix->score_gamma = gamma_fp32(ix->dpad);
   }
@@ -475,6 +483,17 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
     }
     ix->device_bytes += (uint64_t)n * ix->ldxb * 2;
     if ((s = rows_to_bf16(ix->X, n, ix->dpad, d, ix->ldxb, ix->Xb, st)) != FPP_OK) return fail(s);
+  }
+  if (ix->precision == FPP_FP8E4M3) {
+    ix->ldxq = round_up(d, 16);
+    if (cudaMalloc(&ix->Xq, (size_t)n * ix->ldxq) != cudaSuccess ||
+        cudaMalloc(&ix->xscale, (size_t)n * 4) != cudaSuccess) {
+      set_error("cudaMalloc Xq");
+      return fail(FPP_ENOMEM);
+    }
+    ix->device_bytes += (uint64_t)n * ix->ldxq + (uint64_t)n * 4;
+    if ((s = rows_to_fp8(ix->X, n, ix->dpad, d, ix->ldxq, ix->Xq, ix->xscale, st)) != FPP_OK)
+      return fail(s);
   }
   if (cudaMalloc(&ix->rmax, 2 * L * 4) != cudaSuccess) { set_error("cudaMalloc rmax"); return fail(FPP_ENOMEM); }
   if (cudaMemcpyAsync(ix->rmax, hrmax.data(), 2 * L * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) {
@@ -689,7 +708,7 @@ fpp_status validate_search(const fpp_index* ix, const float* Q, int64_t m, const
 // Entries the top-k kernel re-scores exactly: k + 16, or the FP32 shortlist
 // of the BF16 path when that is longer.
 int topk_kprime(const fpp_index* ix, int kmax) {
-  return std::max(kmax + 16, ix->precision == FPP_BF16 ? ix->rerank_k : 0);
+  return std::max(kmax + 16, ix->precision != FPP_FP32 ? ix->rerank_k : 0);
 }
 
 // Runs projection + probe ranking (and, unless probes_only, gather/score) for
@@ -813,6 +832,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   sa.cand = ws.cand.as<uint32_t>();
   sa.X = ix->X; sa.ldx = ix->dpad; sa.Q = ws.qpad.as<float>(); sa.ldq = ix->dpad;
   sa.Xb = ix->Xb; sa.ldxb = ix->ldxb;
+  sa.Xq = ix->Xq; sa.ldxq = ix->ldxq; sa.xscale = ix->xscale;
   sa.scores = ws.cscores.as<float>();
   sa.tune_g = ix->tune_score_g; sa.tune_waves = ix->tune_score_waves;
   FPP_TRY(launch_score(sa, ix->sm_count, st));
@@ -823,7 +843,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   ta.X = ix->X; ta.ldx = ix->dpad; ta.Q = ws.qpad.as<float>(); ta.ldq = ix->dpad; ta.d = ix->d;
   ta.qnorm = ws.qnorm.as<float>(); ta.xmax = ix->xmax; ta.gamma = ix->score_gamma;
   ta.kprime = topk_kprime(ix, pl.kmax);
-  ta.approx = ix->precision == FPP_BF16;
+  ta.approx = ix->precision != FPP_FP32;
   ta.cap = topk_cap(ta.kprime); ta.rcap = topk_rcap(ta.kprime);
   ta.slow = ws.tkslow.p; ta.err = reinterpret_cast<int*>(stv + 5); ta.stats = stv;
   ta.out_ids = ids_dev; ta.out_scores = scores_dev;
@@ -1686,6 +1706,7 @@ fpp_status fpp_autotune(fpp_index* ix, const float* Q, int64_t m, int32_t k, int
   sa.cand = ws.cand.as<uint32_t>();
   sa.X = ix->X; sa.ldx = ix->dpad; sa.Q = ws.qpad.as<float>(); sa.ldq = ix->dpad;
   sa.Xb = ix->Xb; sa.ldxb = ix->ldxb;
+  sa.Xq = ix->Xq; sa.ldxq = ix->ldxq; sa.xscale = ix->xscale;
   sa.scores = ws.cscores.as<float>();
   cudaEvent_t e0, e1;
   FPP_CUDA(cudaEventCreate(&e0));
@@ -1710,7 +1731,9 @@ fpp_status fpp_autotune(fpp_index* ix, const float* Q, int64_t m, int32_t k, int
   fpp_status st = time_shape(0, 0, &rep.ms_default);
   int best_g = 0, best_w = 0;
   float best_ms = rep.ms_default;
-  const int chunks = ix->precision == FPP_BF16 ? (int)(ix->ldxb / 8) : ix->dpad / 4;
+  const int chunks = ix->precision == FPP_BF16      ? (int)(ix->ldxb / 8)
+                     : ix->precision == FPP_FP8E4M3 ? (int)(ix->ldxq / 16)
+                                                    : ix->dpad / 4;
   for (int g = 1; g <= 32 && st == FPP_OK; g <<= 1) {
     if (g * 8 < chunks || g > 2 * chunks) continue;   // shapes the kernels instantiate well
     for (int w : {1, 2, 3, 4, 6, 8}) {

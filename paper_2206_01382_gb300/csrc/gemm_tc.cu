@@ -25,6 +25,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <cmath>
 
@@ -510,6 +511,45 @@ double bf16_window_factor(int d) {
   // those plus the worst-case FP32 accumulation error: a statistical margin,
   // not a bound (the BF16 path is graded by recall and score error).
   return 9.0 * 3.90625e-3 / std::sqrt(3.0 * (double)d) + 2.0 * gamma_fp32(tc_kpad(d));
+}
+
+double fp8_window_factor(int d) {
+  // e4m3 keeps 3 fraction bits (unit roundoff 2^-4); rows are scaled so their
+  // largest magnitude is 448, which keeps every element above the subnormal
+  // range unless it is below 2^-6 / 448 of that magnitude.  Nine standard
+  // deviations of u ||a|| ||b|| / sqrt(3 d), plus the subnormal spacing
+  // (2^-9 of the scale unit) over d elements and the FP32 accumulation bound.
+  return 9.0 * 0.0625 / std::sqrt(3.0 * (double)d) + (double)d * std::ldexp(1.0, -9) / 448.0 +
+         2.0 * gamma_fp32(tc_kpad(d));
+}
+
+namespace {
+__global__ void rows_fp8_kernel(const float* __restrict__ src, int64_t rows, int64_t lds, int d,
+                                int64_t ldo, __nv_fp8_storage_t* __restrict__ dst,
+                                float* __restrict__ scale) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= rows) return;
+  const float* x = src + r * lds;
+  float m = 0.f;
+  for (int i = lane; i < d; i += 32) m = fmaxf(m, fabsf(x[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const float sc = m > 0.f ? m / 448.f : 1.f;
+  for (int i = lane; i < ldo; i += 32)
+    dst[r * ldo + i] = i < d ? __nv_cvt_float_to_fp8(x[i] / sc, __NV_SATFINITE, __NV_E4M3)
+                             : (__nv_fp8_storage_t)0;
+  if (lane == 0) scale[r] = sc;
+}
+}  // namespace
+
+fpp_status rows_to_fp8(const float* src, int64_t rows, int64_t lds, int d, int64_t ldo, void* dst,
+                       float* scale, cudaStream_t st) {
+  if (rows <= 0) return FPP_OK;
+  rows_fp8_kernel<<<(unsigned)ceil_div(rows, 8), 256, 0, st>>>(
+      src, rows, lds, d, ldo, reinterpret_cast<__nv_fp8_storage_t*>(dst), scale);
+  FPP_LAUNCHED();
+  return FPP_OK;
 }
 
 namespace {

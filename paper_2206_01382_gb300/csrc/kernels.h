@@ -27,6 +27,13 @@ int tc_kpad(int d);
 double tc_error_bound_factor(int Kp, int pieces);
 // Near-tie window (relative to ||a|| ||b||) of dot products with BF16 rows.
 double bf16_window_factor(int d);
+// Near-tie window (relative to ||a|| ||b||) of dot products with rows in FP8
+// e4m3 times a per-row scale.
+double fp8_window_factor(int d);
+// FP32 rows [rows][lds] (d used) -> e4m3 rows [rows][ldo] (zero padded) and
+// per-row scales (largest magnitude / 448, 1 for a zero row).
+fpp_status rows_to_fp8(const float* src, int64_t rows, int64_t lds, int d, int64_t ldo, void* dst,
+                       float* scale, cudaStream_t st);
 // FP32 rows [rows][lds] (d used) -> BF16 rows [rows][ldo], zero padded.
 fpp_status rows_to_bf16(const float* src, int64_t rows, int64_t lds, int d, int64_t ldo, void* dst,
                         cudaStream_t st);
@@ -236,6 +243,9 @@ struct ScoreArgs {
   int64_t ldq;
   const void* Xb;            // BF16 rows [n][ldxb] (precision path) or NULL
   int64_t ldxb;
+  const uint8_t* Xq;         // FP8 e4m3 rows [n][ldxq] or NULL
+  int64_t ldxq;
+  const float* xscale;       // [n] scales of the FP8 rows
   float* scores;             // FP32 scores, parallel to cand
   int tune_g;                // lanes per row (power of two) or 0: heuristic
   int tune_waves;            // CTAs per resident slot or 0: default

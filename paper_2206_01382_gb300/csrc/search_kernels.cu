@@ -6,6 +6,8 @@
 #include <climits>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -1476,6 +1478,94 @@ score_bf16_kernel(ScoreArgs a) {
   }
 }
 
+// FP8 e4m3 rows times a per-row scale: each 16-byte chunk holds 16 values,
+// decoded in pairs to half precision (exact) and accumulated in FP32
+// against the FP32 query; the row's scale multiplies the sum.
+template <int G, int CPL, bool EXACT>
+__global__ void __launch_bounds__(256)
+score_fp8_kernel(ScoreArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t nslots = (int64_t)*a.nitems;
+  constexpr int RPP = 32 / G;
+  constexpr int U = 4;
+  const int sub = lane % G, grp = lane / G;
+  const int nch = (int)(a.ldxq / 16);
+  const uint4* Xq = reinterpret_cast<const uint4*>(a.Xq);
+  int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  ScoreItem item = it < nslots ? a.items[it] : ScoreItem{0u, 0u, 0ull};
+  for (; it < nslots; it += nw) {
+    const ScoreItem nxt = it + nw < nslots ? a.items[it + nw] : ScoreItem{0u, 0u, 0ull};
+    if (item.len == 0) { item = nxt; continue; }
+    const uint32_t* ids = a.cand + item.start;
+    const float* qrow = a.Q + (int64_t)item.q * a.ldq;
+    float* out = a.scores + item.start;
+    for (int r0 = 0; r0 < (int)item.len; r0 += U * RPP) {
+      uint32_t id[U];
+      bool ok[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int r = r0 + u * RPP + grp;
+        ok[u] = (uint32_t)r < item.len;
+        id[u] = ok[u] ? __ldg(ids + r) : 0u;
+      }
+      float p[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) p[u] = 0.f;
+      for (int cb = 0; cb < nch; cb += CPL * G) {
+        uint4 x[U][CPL];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            const int ch = cb + sub + c * G;
+            x[u][c] = (ok[u] && (EXACT || ch < nch)) ? __ldg(Xq + (int64_t)id[u] * (a.ldxq / 16) + ch)
+                                                     : make_uint4(0u, 0u, 0u, 0u);
+          }
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          const int ch = cb + sub + c * G;
+          if (!(EXACT || ch < nch)) continue;
+          // the 16 query values of the chunk (the query row is padded to 4;
+          // values past it meet zero FP8 bytes)
+          float qv[16];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int col = ch * 16 + v * 4;
+            const float4 q4 = col < a.ldq ? __ldg(reinterpret_cast<const float4*>(qrow + col))
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+            qv[4 * v] = q4.x; qv[4 * v + 1] = q4.y; qv[4 * v + 2] = q4.z; qv[4 * v + 3] = q4.w;
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const uint32_t w[4] = {x[u][c].x, x[u][c].y, x[u][c].z, x[u][c].w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const __half2_raw h0 = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] & 0xFFFFu), __NV_E4M3);
+              const __half2_raw h1 = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] >> 16), __NV_E4M3);
+              const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&h0));
+              const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&h1));
+              p[u] = fmaf(f0.x, qv[4 * k], p[u]);
+              p[u] = fmaf(f0.y, qv[4 * k + 1], p[u]);
+              p[u] = fmaf(f1.x, qv[4 * k + 2], p[u]);
+              p[u] = fmaf(f1.y, qv[4 * k + 3], p[u]);
+            }
+          }
+        }
+        if (EXACT) break;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        float f = p[u];
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) f += __shfl_xor_sync(FULL, f, o);
+        if (ok[u] && sub == 0) out[r0 + u * RPP + grp] = f * __ldg(a.xscale + id[u]);
+      }
+    }
+    item = nxt;
+  }
+}
+
 // Best k candidates of each query by (score desc, id asc).  The first-pass
 // scores pre-select the best K' = max(k + 16, kprime); the entries among them
 // within twice the score error of the k-th are re-scored with the
@@ -2027,8 +2117,39 @@ fpp_status launch_score_bf(const ScoreArgs& a, int sms, cudaStream_t st) {
   return launch_score_bf_one<G, 4, false>(a, sms, st);
 }
 
+template <int G, int CPL, bool EXACT>
+fpp_status launch_score_f8_one(const ScoreArgs& a, int sms, cudaStream_t st) {
+  static std::atomic<int> per_sm{0};
+  return launch_resident(score_fp8_kernel<G, CPL, EXACT>, sms, a, per_sm, st);
+}
+
+template <int G>
+fpp_status launch_score_f8(const ScoreArgs& a, int sms, cudaStream_t st) {
+  const int nch = (int)(a.ldxq / 16);
+  const int cpl = (nch + G - 1) / G;
+  if (cpl == 1 && nch == G) return launch_score_f8_one<G, 1, true>(a, sms, st);
+  if (cpl == 2 && nch == 2 * G) return launch_score_f8_one<G, 2, true>(a, sms, st);
+  if (cpl <= 1) return launch_score_f8_one<G, 1, false>(a, sms, st);
+  return launch_score_f8_one<G, 2, false>(a, sms, st);
+}
+
 fpp_status launch_score(const ScoreArgs& a, int sm_count, cudaStream_t st) {
   const int grid = sm_count;
+  if (a.Xq) {
+    // 16-byte chunks of 16 e4m3 values, at most 2 per lane before G = 32
+    int g = 1;
+    const int nch = (int)(a.ldxq / 16);
+    while (g < 32 && g * 2 < nch) g <<= 1;
+    if (a.tune_g) g = a.tune_g;
+    switch (g) {
+      case 1: return launch_score_f8<1>(a, grid, st);
+      case 2: return launch_score_f8<2>(a, grid, st);
+      case 4: return launch_score_f8<4>(a, grid, st);
+      case 8: return launch_score_f8<8>(a, grid, st);
+      case 16: return launch_score_f8<16>(a, grid, st);
+      default: return launch_score_f8<32>(a, grid, st);
+    }
+  }
   if (a.Xb) {
     // 16-byte chunks of 8 BF16; at most 2 chunks per lane before G = 32
     int g = 1;

@@ -60,7 +60,7 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     for kw in (dict(L=0, D=4, alpha=0.1), dict(L=2, D=0, alpha=0.1),
                dict(L=2, D=2000, alpha=0.1), dict(L=2, D=4, alpha=0.0),
                dict(L=2, D=4, alpha=1.5), dict(L=2, D=4, alpha=0.1, kappa=-1),
-               dict(L=2, D=4, alpha=0.1, precision=2),
+               dict(L=2, D=4, alpha=0.1, precision=3),
                dict(L=2, D=4, alpha=0.1, precision=F.FPP_BF16, rerank_k=257),
                dict(L=2, D=4, alpha=0.1, precision=F.FPP_BF16, rerank_k=-1)):
         with pytest.raises(F.FppError) as e:

@@ -139,3 +139,21 @@ def test_bf16_ragged_dimension(F):
     assert float(np.abs(gs[fin] - ex[fin]).max()) <= 1e-5
     info = ix.info()
     assert info["precision"] == F.FPP_BF16
+
+
+@pytest.mark.parametrize("rerank_k", [0, 100])
+def test_fp8_rows_match_exact_path(F, rerank_k):
+    # FP8 e4m3 candidate rows with per-row scales: the same candidates as the
+    # exact path, results equal except where the statistical window misses
+    X, Q = W.small_mixture(40000, 300, 96, 128, 0.3 / np.sqrt(96), 314)
+    ix8 = F.Index(X, 16, 64, 0.1, seed=16, precision=F.FPP_FP8E4M3, rerank_k=rerank_k)
+    ix32 = F.Index(X, 16, 64, 0.1, seed=16)
+    assert ix8.info()["precision"] == F.FPP_FP8E4M3
+    for P in (1, 4):
+        i8, s8 = ix8.search(Q, 10, P)
+        i32, s32 = ix32.search(Q, 10, P)
+        same = np.mean([np.array_equal(a, b) for a, b in zip(i8, i32)])
+        assert same >= 0.98, (P, same)
+        ex = _exact_scores(X, Q, i8)
+        fin = i8 >= 0
+        assert float(np.abs(s8[fin] - ex[fin]).max()) <= 1e-5
