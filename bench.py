@@ -2,7 +2,7 @@
 """Throughput benchmark of the GB300 Falconn++ search path.
 
 One step = one batched search of the workload's whole query set through the
-hot path (projection GEMM, probe ranking, gather + bitmap dedup + exact
+hot path (projection GEMM, probe ranking, gather + hash-set dedup + exact
 scoring + top-k), with the index and the queries resident in HBM.  The probe
 budget is the smallest of the workload's sweep whose recall@10 against exact
 search reaches 0.90 (measured once, before timing, on a query sample with the
@@ -450,9 +450,10 @@ def main():
     score_b = (row_bytes + 8) * unique_pl + 4 * d * qpl
     topk_b = 8 * unique_pl + 4 * d * kprime * qpl + 12 * k * qpl
     # projection: BF16 tensor-core products over K padded to 64; the FP32
-    # contraction runs 6 of them (exact three-piece split)
+    # contraction runs 3 of them when the random vectors are on the BF16 grid
+    # (three query pieces times one vector piece), else 6 (both split)
     kpad = -(-d // 64) * 64
-    products = 6
+    products = 3 if info["r_pieces"] == 1 else 6
     proj_flops = 2.0 * qpl * kpad * 2 * w.L * w.D * products
     ms_of = {key: phase[key] / per for key in phase}
 
@@ -479,7 +480,7 @@ def main():
                         "ms_per_launch": ms_of["ms_probe_exact"], "launches_per_step": chunks,
                         "bound": "alu"},
         "dedup": hbm("dedup_hash_kernel", "search_kernels.cu", ms_of["ms_dedup"], dedup_b,
-                     "count_entries + scan + dedup_hash + dedup (bitmap) kernels; "
+                     "count_entries + scan + dedup_hash tiers + flatten kernels; "
                      "latency-bound bucket walk"),
         "score": hbm({"fp32": "score_kernel", "bf16": "score_bf16_kernel",
                       "fp8": "score_fp8_kernel"}[args.precision], "search_kernels.cu",

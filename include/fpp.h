@@ -171,7 +171,9 @@ typedef struct fpp_index_info {
   int32_t rerank_k;           /* FPP_BF16 shortlist length (0 for FPP_FP32)    */
   int32_t center;             /* 1: the tables hash the centered points        */
   int32_t simhash_bits;       /* SimHash signature bits per point (0: none)    */
-  int32_t reserved2;
+  int32_t r_pieces;           /* BF16 pieces of R in the projection: 1 when
+                                 every coordinate of R is a BF16 value (the
+                                 seeded generator's), else 3                  */
   double score_error_factor;  /* c: a candidate's first-pass score is within
                                  c ||q|| ||x|| of x^T q (FPP_FP32: the FP32
                                  bound gamma_d; FPP_BF16: the statistical
@@ -219,10 +221,13 @@ const char* fpp_last_error(void);
 
 /* Host-only: the canonical random vectors R[L][2][D][d] for a seed.  Stream
  * 2t+j (table t, hash j) is SplitMix64 (Steele, Lea, Flood 2014) started at
- * seed XOR 0x9E3779B97F4A7C15*(2t+j+1); coordinate (i, c) is the FP32-rounded
+ * seed XOR 0x9E3779B97F4A7C15*(2t+j+1); coordinate (i, c) is the
  * Box-Muller value sqrt(-2 ln u1) cos(2 pi u2) of the stream's outputs
- * 2(i d + c) and 2(i d + c)+1, u1 = (top53 + 1) / 2^53, u2 = top53 / 2^53.
- * The paper fixes only that each coordinate is N(0, 1) (Section 2.2).
+ * 2(i d + c) and 2(i d + c)+1, u1 = (top53 + 1) / 2^53, u2 = top53 / 2^53,
+ * rounded to FP32 and then to the nearest BF16 value (ties to even).  The
+ * paper fixes only that each coordinate is N(0, 1) (Section 2.2); with R on
+ * the BF16 grid the projections take three tensor-core products instead of
+ * six (any FP32 R passed in params->R still works, at the six-product cost).
  * R is host memory of L*2*D*d floats owned by the caller.  Needs no GPU. */
 fpp_status fpp_rotations(uint64_t seed, int32_t L, int32_t D, int32_t d, float* R);
 

@@ -17,8 +17,11 @@ Layout: R[t][j][i][c] for table t < L, hash j < 2, vector i < D, coordinate
 c < d.  Stream id = 2t + j with initial state seed XOR (golden * (id + 1)).
 Coordinate (i, c) uses the stream's outputs 2(i d + c) and 2(i d + c) + 1 as
 (u1, u2): u1 = (top 53 bits + 1) / 2^53 in (0, 1], u2 = top 53 bits / 2^53 in
-[0, 1).  The FP64 value is rounded to FP32; that FP32 array is the canonical
-R, promoted exactly to FP64 by the oracle.
+[0, 1).  The FP64 value is rounded to FP32 and that to the nearest BF16 value
+(ties to even); the resulting FP32 array (every element on the BF16 grid) is
+the canonical R, promoted exactly to FP64 by the oracle.  The paper fixes
+only the N(0, 1) distribution; 8 significant bits per coordinate keep the
+vectors as random for the hash.
 """
 from __future__ import annotations
 
@@ -64,15 +67,24 @@ def uniform_pair(raw: np.ndarray):
     return (top1 + 1.0) / 9007199254740992.0, top2 / 9007199254740992.0
 
 
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """Finite FP32 values rounded to the nearest BF16 value (ties to even),
+    returned as FP32: add 0x7FFF plus the lowest kept bit, clear 16 bits."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + np.uint64(0x7FFF) + ((u >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)) \
+        << np.uint64(16)
+    return u.astype(np.uint32).view(np.float32)
+
+
 def gaussian_stream(seed: int, stream_id: int, count: int) -> np.ndarray:
-    """``count`` FP32 standard normals of one stream."""
+    """``count`` standard normals of one stream, on the BF16 grid (FP32)."""
     raw = splitmix64(stream_state(seed, stream_id), 2 * count)
     u1, u2 = uniform_pair(raw)
-    return box_muller(u1, u2).astype(np.float32)
+    return round_bf16(box_muller(u1, u2).astype(np.float32))
 
 
 def gaussian_rotations(seed: int, L: int, D: int, d: int) -> np.ndarray:
-    """The canonical FP32 random vectors ``R[L][2][D][d]``."""
+    """The canonical random vectors ``R[L][2][D][d]`` (FP32 holding BF16 values)."""
     R = np.empty((L, 2, D, d), dtype=np.float32)
     for t in range(L):
         for j in range(2):

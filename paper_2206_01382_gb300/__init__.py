@@ -90,7 +90,7 @@ class fpp_index_info(ctypes.Structure):
                 ("kept_total", ctypes.c_uint64), ("max_bucket_kept", ctypes.c_uint32),
                 ("device_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_float),
                 ("rerank_k", ctypes.c_int32), ("center", ctypes.c_int32),
-                ("simhash_bits", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("simhash_bits", ctypes.c_int32), ("r_pieces", ctypes.c_int32),
                 ("score_error_factor", ctypes.c_double)]
 
 

@@ -118,6 +118,7 @@ struct fpp_index {
   void* Rs = nullptr;          // [2 L D][pieces Kp] BF16 pieces of R (tensor-core operand)
   int Kp = 0;
   int pieces = 3;              // 3: exact split (FPP_FP32); 1: plain BF16 (FPP_BF16)
+  int bpieces = 3;             // 1: every coordinate of R is a BF16 value (three products)
   void* Xb = nullptr;          // [n][ldxb] BF16 copy of X (FPP_BF16 only)
   int64_t ldxb = 0;
   uint8_t* Xq = nullptr;       // [n][ldxq] FP8 e4m3 copy of X (FPP_FP8E4M3 only)
@@ -227,8 +228,8 @@ fpp_status project_rows(const fpp_index* ix, const float* src, int64_t rc, DevBu
   FPP_TRY(split_to_bf16(src, rc, ix->dpad, ix->d, ix->pieces, split.p, st));
   const char* rb =
       static_cast<const char*>(ix->Rs) + (size_t)2 * t0 * ix->D * ix->pieces * ix->Kp * 2;
-  return project_tc(split.p, rc, rb, 2ll * nt * ix->D, ix->Kp, ix->pieces, ix->D, EL, out, ldp,
-                    lists, err, st);
+  return project_tc(split.p, rc, rb, 2ll * nt * ix->D, ix->Kp, ix->pieces, ix->bpieces, ix->D, EL,
+                    out, ldp, lists, err, st);
 }
 
 // List length of the fused projection epilogue for a probe budget, or 0
@@ -438,6 +439,13 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
   } else {
     generate_rotations(p->seed, L, D, d, hR.data());
   }
+  // R on the BF16 grid (the seeded generator's): three projection products
+  ix->bpieces = 1;
+  for (size_t e = 0; e < hR.size() && ix->bpieces == 1; ++e) {
+    uint32_t u;
+    std::memcpy(&u, &hR[e], 4);
+    if (u & 0xFFFFu) ix->bpieces = ix->pieces;
+  }
   std::vector<float> hrmax(2 * L, 0.f);
   for (int64_t r = 0; r < rrows; ++r) {
     double s = 0.0;
@@ -601,7 +609,7 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
       s = B.xsplit.ensure((size_t)rc * ix->pieces * ix->Kp * 2);
       if (s == FPP_OK) s = split_to_bf16(xr, rc, ix->dpad, d, ix->pieces, B.xsplit.p, st);
       if (s == FPP_OK)
-        s = project_tc(B.xsplit.p, rc, ix->Rs, bits, ix->Kp, ix->pieces, 0, 0, B.proj.as<float>(),
+        s = project_tc(B.xsplit.p, rc, ix->Rs, bits, ix->Kp, ix->pieces, ix->bpieces, 0, 0, B.proj.as<float>(),
                        bits, nullptr, reinterpret_cast<int*>(B.rechecks.as<unsigned long long>() + 1), st);
       if (s == FPP_OK) s = launch_query_norms(xr, rc, ix->dpad, d, B.norms.as<float>(), st);
       if (s == FPP_OK) {
@@ -749,7 +757,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   if (pl.sim_keep > 0) {
     // the queries' SimHash signatures from their split pieces
     const int bits = ix->sig_words * 32;
-    FPP_TRY(project_tc(ws.qsplit.p, mc, ix->Rs, bits, ix->Kp, ix->pieces, 0, 0,
+    FPP_TRY(project_tc(ws.qsplit.p, mc, ix->Rs, bits, ix->Kp, ix->pieces, ix->bpieces, 0, 0,
                        ws.sigproj.as<float>(), bits, nullptr,
                        reinterpret_cast<int*>(ws.stats.as<unsigned long long>() + 9), st));
     SignArgs sg{};
@@ -788,8 +796,11 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   da.ecount = ws.ecount.as<uint32_t>(); da.eoff = ws.eoff.as<uint64_t>();
   da.ucount = ws.ecount.as<uint32_t>() + mc;
   da.nitems = reinterpret_cast<unsigned*>(stv + 10);
+  da.tierq = ws.ecount.as<uint32_t>() + 2 * mc;
+  da.tiern = da.nitems + 1;
   da.no_items = pl.sim_keep > 0 ? 1 : 0;
   da.stats = stv;
+  FPP_CUDA(cudaMemsetAsync(da.nitems, 0, 3 * sizeof(unsigned), st));   // items, tier counts
   FPP_TRY(launch_count_entries(da, st));
   FPP_TRY(exclusive_scan_u32(ws.ecount.as<uint32_t>(), mc, ws.eoff.as<uint64_t>(), 0,
                              KeepRule{1.0, 1, 0}, ws.scan.as<uint64_t>(), st));
@@ -888,7 +899,7 @@ fpp_status prepare_workspace(fpp_index* ix, Workspace& ws, const SearchPlan& pl,
     FPP_TRY(ws.out_ids.ensure((size_t)mc * pl.kmax * 8, false, st));
     FPP_TRY(ws.out_scores.ensure((size_t)mc * pl.kmax * 4, false, st));
   }
-  FPP_TRY(ws.ecount.ensure((size_t)2 * mc * 4, false, st));
+  FPP_TRY(ws.ecount.ensure((size_t)3 * mc * 4, false, st));   // counts, distinct counts, tiers
   FPP_TRY(ws.eoff.ensure((size_t)(mc + 1) * 8, false, st));
   FPP_TRY(ws.scan.ensure((size_t)scan_scratch_elems(mc) * 8, false, st));
   FPP_TRY(ws.tkslow.ensure((size_t)(ceil_div(mc, 8) * 8) * topk_slow_cap() * 16, false, st));
@@ -1413,6 +1424,7 @@ fpp_status fpp_index_get_info(const fpp_index* ix, fpp_index_info* info) {
   info->rerank_k = ix->rerank_k;
   info->center = ix->center;
   info->simhash_bits = ix->sig_words * 32;
+  info->r_pieces = ix->bpieces;
   info->score_error_factor = ix->score_gamma;
   return FPP_OK;
 }

@@ -9,11 +9,16 @@
 // BF16 values x = hi + mid + lo (each residual x - hi, x - hi - mid is exact
 // in FP32 and the last one has at most 8 significant bits).  The product
 // a . b is then the sum of the nine piece products; the kernel accumulates
-// hi.hi in one TMEM accumulator and the five next-order products (hi.mid,
-// mid.hi, hi.lo, mid.mid, lo.hi) in a second one, and the epilogue adds the
-// two.  The dropped products are below 2^-23 |a||b|, the correction
-// accumulator is 2^-7 smaller than the main one, so the error bound stays
-// within a small factor of the FP32 one (see tc_error_bound).
+// the five next-order products (hi.mid, mid.hi, hi.lo, mid.mid, lo.hi) and
+// then hi.hi into one TMEM accumulator.  The dropped products are below
+// 2^-23 |a||b| and the partial sums of the small products stay 2^-7 below
+// the final value, so the error bound stays within a small factor of the
+// FP32 one (tc_error_bound_factor).
+//
+// When every element of B is itself a BF16 value (bpieces = 1), B's mid and
+// lo pieces are zero and the three products lo.hi, mid.hi, hi.hi (in that
+// order, into one accumulator) are the exact sum of all nine: half the
+// tensor-core work for the same error bound.
 //
 // Plain mode (pieces = 1): one BF16 product, for the BF16 precision path.
 //
@@ -198,11 +203,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 // accumulator: while the small products accumulate, the partial sums (and so
 // the rounding errors) stay 2^-7 smaller than the final value, which keeps
 // the error bound of the whole sum close to that of hi.hi alone.
-__device__ __forceinline__ void chunk_pieces(int c, int nkb, int pieces, int& pa, int& pb,
-                                             int& kb) {
+// With bpieces = 1 the chunks are lo.hi, mid.hi and hi.hi.
+__device__ __forceinline__ void chunk_pieces(int c, int nkb, int pieces, int bpieces, int& pa,
+                                             int& pb, int& kb) {
   const int pair = c / nkb;
   kb = c - pair * nkb;
   if (pieces == 1) { pa = pb = 0; return; }
+  if (bpieces == 1) { pa = 2 - pair; pb = 0; return; }
   switch (pair) {
     case 0: pa = 0; pb = 1; break;
     case 1: pa = 1; pb = 0; break;
@@ -227,11 +234,14 @@ __device__ __forceinline__ void chunk_pieces(int c, int nkb, int pieces, int& pa
 // FP32 projections.  EL > 0: for every (row, hash) it keeps the EL largest
 // keys of the hash's D columns (D divides 256) followed by a "cut" key whose
 // value is the largest |p| left out, and stores only those EL + 1 keys.
+// mfast = 1 hands out the tiles of one column block for consecutive row
+// blocks, so that CTAs running together share B's tiles in L2 (for B larger
+// than A); otherwise they share A's.
 template <int EL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                float* __restrict__ C, int64_t ldc, uint64_t* __restrict__ lists, int M, int N,
-               int Kp, int pieces, int D, int* err) {
+               int Kp, int pieces, int bpieces, int D, int mfast, int* err) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
@@ -239,7 +249,7 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nkb = Kp / TC_BK;
-  const int nchunks = (pieces == 1 ? 1 : 6) * nkb;
+  const int nchunks = (pieces == 1 ? 1 : bpieces == 1 ? 3 : 6) * nkb;
   const int ntn = (N + TC_BN - 1) / TC_BN, ntm = (M + TC_BM - 1) / TC_BM;
   const int ntiles = ntn * ntm;
 
@@ -272,7 +282,8 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     // ---------------- TMA producer
     uint32_t g = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      const int m0 = (t / ntn) * TC_BM, n0 = (t % ntn) * TC_BN;
+      const int m0 = (mfast ? t % ntm : t / ntn) * TC_BM;
+      const int n0 = (mfast ? t / ntm : t % ntn) * TC_BN;
       bool ok = true;
       for (int c = 0; c < nchunks; ++c, ++g) {
         const uint32_t s = g % TC_STAGES;
@@ -281,7 +292,7 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
           break;
         }
         int pa, pb, kb;
-        chunk_pieces(c, nkb, pieces, pa, pb, kb);
+        chunk_pieces(c, nkb, pieces, bpieces, pa, pb, kb);
         unsigned char* st = base + s * STAGE_BYTES;
         mbar_expect_tx(&sh->full[s], STAGE_BYTES);
         tma_load_2d(st, &mapA, pa * Kp + kb * TC_BK, m0, &sh->full[s]);
@@ -324,7 +335,8 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     int i = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
       const int b = i & 1;
-      const int m0 = (t / ntn) * TC_BM, n0 = (t % ntn) * TC_BN;
+      const int m0 = (mfast ? t % ntm : t / ntn) * TC_BM;
+      const int n0 = (mfast ? t / ntm : t % ntn) * TC_BN;
       if (!mbar_wait(&sh->tfull[b], (i >> 1) & 1, sh, err, 3)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int row = m0 + quarter * 32 + lane;
@@ -497,7 +509,10 @@ double tc_error_bound_factor(int Kp, int pieces) {
   // 2^-7 sum|a b|, the Kp main products below (1 + 2^-7) sum|a b|, so the
   // bound is gamma_Kp (1 + 5 2^-7 + 2^-7) doubled to allow truncating
   // accumulation, plus the dropped products (< 2^-23 |a||b|) and the BF16
-  // piece residuals.  Plain BF16: the input rounding 2 * 2^-8 dominates.
+  // piece residuals.  The three-product form (B on the BF16 grid) drops
+  // nothing and its two small products likewise keep the partial sums below
+  // 2^-7 sum|a b|, so the same bound holds.  Plain BF16: the input rounding
+  // 2 * 2^-8 dominates.
   if (pieces == 1) return 2.0 * 3.90625e-3 + 2.0 * gamma_fp32(Kp) + 1.6e-5;
   return 2.0 * gamma_fp32(Kp) * 1.05 + 2.0e-7;
 }
@@ -587,8 +602,8 @@ namespace {
 
 template <int EL>
 fpp_status launch_proj(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int64_t ldc,
-                       uint64_t* lists, int64_t M, int64_t N, int Kp, int pieces, int D, int* err,
-                       cudaStream_t st) {
+                       uint64_t* lists, int64_t M, int64_t N, int Kp, int pieces, int bpieces,
+                       int D, int* err, cudaStream_t st) {
   const size_t smem = 1024 + TC_STAGES * STAGE_BYTES + sizeof(TcShared);
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
@@ -602,8 +617,9 @@ fpp_status launch_proj(const CUtensorMap& ma, const CUtensorMap& mb, float* C, i
   FPP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t ntiles = ceil_div(M, TC_BM) * ceil_div(N, TC_BN);
   const int grid = (int)std::min<int64_t>(ntiles, sms);
+  const int mfast = N * bpieces > M * pieces ? 1 : 0;   // B's bytes read > A's
   tc_proj_kernel<EL><<<grid, TC_THREADS, smem, st>>>(ma, mb, C, ldc, lists, (int)M, (int)N, Kp,
-                                                     pieces, D, err);
+                                                     pieces, bpieces, D, mfast, err);
   FPP_LAUNCHED();
   return FPP_OK;
 }
@@ -628,13 +644,15 @@ int tc_list_len(int want) {
 
 fpp_status gemm_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, int pieces, float* C,
                    int64_t ldc, int* err, cudaStream_t st) {
-  return project_tc(A, M, B, N, Kp, pieces, 0, 0, C, ldc, nullptr, err, st);
+  return project_tc(A, M, B, N, Kp, pieces, pieces, 0, 0, C, ldc, nullptr, err, st);
 }
 
-fpp_status project_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, int pieces, int D,
-                      int EL, float* C, int64_t ldc, uint64_t* lists, int* err, cudaStream_t st) {
+fpp_status project_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, int pieces,
+                      int bpieces, int D, int EL, float* C, int64_t ldc, uint64_t* lists, int* err,
+                      cudaStream_t st) {
   if (M <= 0 || N <= 0) return FPP_OK;
-  if (Kp % TC_BK || (pieces != 1 && pieces != 3) || M >= (1ll << 31) || N >= (1ll << 31)) {
+  if (Kp % TC_BK || (pieces != 1 && pieces != 3) || (bpieces != 1 && bpieces != pieces) ||
+      M >= (1ll << 31) || N >= (1ll << 31)) {
     set_error("project_tc: bad shape");
     return FPP_EINTERNAL;
   }
@@ -650,10 +668,10 @@ fpp_status project_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp
   FPP_TRY(make_map(&ma, A, M, (int64_t)pieces * Kp, TC_BM));
   FPP_TRY(make_map(&mb, B, N, (int64_t)pieces * Kp, TC_BN));
   switch (EL) {
-    case 0: return launch_proj<0>(ma, mb, C, ldc, lists, M, N, Kp, pieces, D, err, st);
-    case 2: return launch_proj<2>(ma, mb, C, ldc, lists, M, N, Kp, pieces, D, err, st);
-    case 4: return launch_proj<4>(ma, mb, C, ldc, lists, M, N, Kp, pieces, D, err, st);
-    case 8: return launch_proj<8>(ma, mb, C, ldc, lists, M, N, Kp, pieces, D, err, st);
+    case 0: return launch_proj<0>(ma, mb, C, ldc, lists, M, N, Kp, pieces, bpieces, D, err, st);
+    case 2: return launch_proj<2>(ma, mb, C, ldc, lists, M, N, Kp, pieces, bpieces, D, err, st);
+    case 4: return launch_proj<4>(ma, mb, C, ldc, lists, M, N, Kp, pieces, bpieces, D, err, st);
+    case 8: return launch_proj<8>(ma, mb, C, ldc, lists, M, N, Kp, pieces, bpieces, D, err, st);
     default:
       set_error("project_tc: list length must be 0, 2, 4 or 8");
       return FPP_EINTERNAL;

@@ -46,8 +46,11 @@ fpp_status gemm_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, i
 int tc_list_len(int want);
 // Relative bound t of the list values' truncation: |p|' <= |p| < |p|' (1 + t).
 float tc_list_trunc(int D);
-fpp_status project_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, int pieces, int D,
-                      int EL, float* C, int64_t ldc, uint64_t* lists, int* err, cudaStream_t st);
+// bpieces = 1: every element of B is a BF16 value (its mid and lo pieces are
+// zero), three products per K block instead of six; else bpieces = pieces.
+fpp_status project_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, int pieces,
+                      int bpieces, int D, int EL, float* C, int64_t ldc, uint64_t* lists, int* err,
+                      cudaStream_t st);
 
 // Build (build_kernels.cu).
 struct HashArgs {
@@ -208,7 +211,10 @@ struct DedupArgs {
   uint32_t* cand;            // candidate ids, query q at eoff[q] ..
   uint32_t* ucount;          // [mq] distinct candidates per query
   ScoreItem* items;          // score work items, appended (any order)
-  unsigned* nitems;          // items appended (zeroed by count_entries)
+  unsigned* nitems;          // items appended (zeroed before count_entries)
+  uint32_t* tierq;           // [mq] queries of the 32,768-slot tier from the front and of
+                             // the no-de-duplication tier from the back (count_entries)
+  unsigned* tiern;           // [2] their counts (zeroed before count_entries)
   int no_items;              // 1: leave the items to the SimHash filter
   unsigned long long* stats; // entries, unique, -, probes
 };

@@ -230,9 +230,11 @@ probe_kernel(ProbeArgs a, int pmax) {
 
 // Thread-per-(query, table) variant of the fast pass for small budgets in
 // list mode (P + 1 <= EL <= 8): the same candidate pairs, selection and
-// margin test on at most 8 list entries per hash, held in registers.
+// margin test on the SE = EL list entries per hash, held in registers (the
+// loops are unrolled over SE, so a list of 2 costs 4 candidate pairs).
 constexpr int SMALL_E = 8;
 
+template <int SE>
 __global__ void __launch_bounds__(256)
 probe_small_kernel(ProbeArgs a) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -245,34 +247,34 @@ probe_small_kernel(ProbeArgs a) {
   const int T = P + 1;
   const int E = T < D ? T : D;
   const int64_t NB = 4ll * D * D;
-  float va[2][SMALL_E];
-  uint32_t ha[2][SMALL_E];
+  float va[2][SE];
+  uint32_t ha[2][SE];
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     const uint64_t* L = a.lists + (idx * 2 + j) * (int64_t)(a.EL + 1);
 #pragma unroll
-    for (int e = 0; e < SMALL_E; ++e) {
+    for (int e = 0; e < SE; ++e) {
       const uint64_t k = e < E ? L[e] : 0ull;
       va[j][e] = __uint_as_float((uint32_t)(k >> 32) - 1u);
       ha[j][e] = 0xFFFFFFFFu - (uint32_t)k;
     }
   }
   // the best T pairs among (a+1)(b+1) <= T, kept sorted in registers
-  uint64_t best[SMALL_E + 1];
+  uint64_t best[SE + 1];
 #pragma unroll
-  for (int e = 0; e <= SMALL_E; ++e) best[e] = 0ull;
+  for (int e = 0; e <= SE; ++e) best[e] = 0ull;
   int C = 0;
 #pragma unroll
-  for (int x = 0; x < SMALL_E; ++x) {
+  for (int x = 0; x < SE; ++x) {
 #pragma unroll
-    for (int y = 0; y < SMALL_E; ++y) {
+    for (int y = 0; y < SE; ++y) {
       if (x < E && y < E && (x + 1) * (y + 1) <= T) {
         const uint32_t bucket = ha[0][x] * (uint32_t)(2 * D) + ha[1][y];
         uint64_t key = ((uint64_t)float_key(va[0][x] + va[1][y]) << 32) |
                        (uint64_t)(0xFFFFFFFFu - bucket);
         ++C;
 #pragma unroll
-        for (int e = 0; e <= SMALL_E; ++e) {
+        for (int e = 0; e <= SE; ++e) {
           const bool sw = key > best[e];
           const uint64_t tv = best[e];
           best[e] = sw ? key : tv;
@@ -286,7 +288,7 @@ probe_small_kernel(ProbeArgs a) {
   if (certain && boundary) {
     uint64_t kP = 0, kP1 = 0;
 #pragma unroll
-    for (int e = 0; e <= SMALL_E; ++e) {
+    for (int e = 0; e <= SE; ++e) {
       if (e == P - 1) kP = best[e];
       if (e == P) kP1 = best[e];
     }
@@ -300,7 +302,7 @@ probe_small_kernel(ProbeArgs a) {
   if (certain) {
     uint32_t* dst = a.out + idx * (int64_t)a.probes;
 #pragma unroll
-    for (int e = 0; e < SMALL_E; ++e)
+    for (int e = 0; e < SE; ++e)
       if (e < P) dst[e] = 0xFFFFFFFFu - (uint32_t)best[e];
   } else {
     const unsigned slot = atomicAdd(a.recheck_count, 1u);
@@ -449,8 +451,8 @@ __host__ __device__ inline size_t recheck_smem_bytes(int D) {
 }
 
 // One CTA per (query, table) item of the recheck list: its warps compute the
-// 2D compensated projections (four rows in flight per warp, coalesced float4
-// loads), then warp 0 re-decides the probe set.
+// 2D compensated projections (eight rows in flight per warp, coalesced
+// float4 loads), then warp 0 re-decides the probe set.
 __global__ void __launch_bounds__(RECHECK_THREADS)
 probe_recheck_kernel(ProbeArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -470,11 +472,14 @@ probe_recheck_kernel(ProbeArgs a) {
     const int P = a.probes_pq ? a.probes_pq[q] : a.probes;
     const float* qv = a.Q + q * a.ldq;
     const float* Rt = a.R + (int64_t)2 * t * a.D * a.ldr;
-    for (int i0 = wid * 4; i0 < rows; i0 += nw * 4) {
-      if (i0 + 4 <= rows) {
-        double v[4];
-        warp_dot2_rows<4>(qv, Rt + (int64_t)i0 * a.ldr, a.ldr, nf4, v);
-        if (lane == 0) { dv[i0] = v[0]; dv[i0 + 1] = v[1]; dv[i0 + 2] = v[2]; dv[i0 + 3] = v[3]; }
+    for (int i0 = wid * 8; i0 < rows; i0 += nw * 8) {
+      if (i0 + 8 <= rows) {
+        double v[8];
+        warp_dot2_rows<8>(qv, Rt + (int64_t)i0 * a.ldr, a.ldr, nf4, v);
+        if (lane == 0) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) dv[i0 + k] = v[k];
+        }
       } else {
         for (int i = i0; i < rows; ++i) {
           double v[1];
@@ -506,12 +511,21 @@ probe_recheck_kernel(ProbeArgs a) {
 // the P best pairs exactly; otherwise the item goes to the full pass.
 constexpr int WIN_MAX = 8;
 
+struct WinShared {
+  double v[2][WIN_MAX];   // exact |q^T r| of each hash's candidates, best first
+  uint32_t w[2][WIN_MAX]; // their signed wedges
+};
+
 __global__ void __launch_bounds__(256)
 probe_window_kernel(ProbeArgs a) {
+  __shared__ WinShared shm[8];
   const int lane = threadIdx.x & 31;
+  WinShared& sh = shm[threadIdx.x >> 5];
   const unsigned cnt = *a.recheck_count;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int nf4 = (int)(a.ldr / 4);
+  // lane 16 j + e holds list entry e of hash j (e <= EL <= 8)
+  const int j = lane >> 4, e = lane & 15;
   for (unsigned it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < cnt; it += nwarps) {
     const uint32_t item = a.recheck[it];
     const int64_t q = item / a.nt;
@@ -519,74 +533,78 @@ probe_window_kernel(ProbeArgs a) {
     const int t = a.tb + tl;
     const int P = a.probes_pq ? a.probes_pq[q] : a.probes;
     const int D = a.D;
-    const double qn = (double)a.qnorm[q];
-    bool ok = P <= a.EL;
-    int ncand[2] = {0, 0};
-    uint32_t hh[2][WIN_MAX];
-    for (int j = 0; j < 2 && ok; ++j) {
-      const uint64_t* L = a.lists + ((q * a.nt + tl) * 2 + j) * (int64_t)(a.EL + 1);
-      auto val = [&](uint64_t k) { return k ? (double)__uint_as_float((uint32_t)(k >> 32) - 1u) : -1.0; };
-      // FP32 error, plus the truncation of the list values (at most trunc
-      // times the hash's largest value)
-      const double eps = a.gamma * qn * (double)a.rmax[2 * t + j] * (1.0 + 1e-6) +
-                         (double)a.trunc * fmax(val(L[0]), 0.0) * (1.0 + 1e-6);
-      const double lim = val(L[P - 1]) - 2.0 * eps;
-      if (!(val(L[a.EL]) < lim)) { ok = false; break; }   // L[EL]: largest |p| left out
-      for (int e = 0; e < a.EL && e < WIN_MAX; ++e)
-        if (L[e] && val(L[e]) >= lim) hh[j][ncand[j]++] = 0xFFFFFFFFu - (uint32_t)L[e];
-    }
-    if (!ok) {
+    if (P > a.EL || P > WIN_MAX) {
       if (lane == 0) a.recheck2[atomicAdd(a.recheck2_count, 1u)] = item;
       continue;
     }
-    // exact projections of the candidates
-    double ev[2][WIN_MAX];
+    const uint64_t key =
+        e <= a.EL ? a.lists[((q * a.nt + tl) * 2 + j) * (int64_t)(a.EL + 1) + e] : 0ull;
+    const double v = key ? (double)__uint_as_float((uint32_t)(key >> 32) - 1u) : -1.0;
+    const double v0 = __shfl_sync(FULL, v, 16 * j);
+    const double vP = __shfl_sync(FULL, v, 16 * j + P - 1);
+    const double vcut = __shfl_sync(FULL, v, 16 * j + a.EL);   // largest |p| left out
+    // FP32 error, plus the truncation of the list values (at most trunc
+    // times the hash's largest value)
+    const double eps = a.gamma * (double)a.qnorm[q] * (double)a.rmax[2 * t + j] * (1.0 + 1e-6) +
+                       (double)a.trunc * fmax(v0, 0.0) * (1.0 + 1e-6);
+    const double lim = vP - 2.0 * eps;
+    // every entry that can still be among the P best of its hash is in the list
+    if (!__all_sync(FULL, vcut < lim)) {
+      if (lane == 0) a.recheck2[atomicAdd(a.recheck2_count, 1u)] = item;
+      continue;
+    }
+    const bool in = e < a.EL && e < WIN_MAX && key != 0ull && v >= lim;
+    const unsigned mask = __ballot_sync(FULL, in);
+    const int nc = __popc(mask);
+    // exact projections of the candidates, four rows in flight per round
+    const uint32_t h = 0xFFFFFFFFu - (uint32_t)key;
+    double ev = 0.0;
     const float* qv = a.Q + q * a.ldq;
-    for (int j = 0; j < 2; ++j) {
-      const float* rows[WIN_MAX];
+    for (int g = 0; g < nc; g += 4) {
+      const float* rows[4];
+      int src[4];
 #pragma unroll
-      for (int e = 0; e < WIN_MAX; ++e) {
-        const uint32_t i = hh[j][e < ncand[j] ? e : 0] % (uint32_t)D;
-        rows[e] = a.R + ((int64_t)(2 * t + j) * D + i) * a.ldr;
+      for (int k = 0; k < 4; ++k) {
+        src[k] = __fns(mask, 0, 1 + min(g + k, nc - 1));   // lane of candidate g + k
+        const uint32_t hk = __shfl_sync(FULL, h, src[k]) % (uint32_t)D;
+        rows[k] = a.R + ((int64_t)(2 * t + (src[k] >> 4)) * D + hk) * a.ldr;
       }
-      warp_dot2_gather<WIN_MAX>(qv, rows, nf4, ev[j]);
+      double out[4];
+      warp_dot2_gather<4>(qv, rows, nf4, out);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (g + k < nc && lane == src[k]) ev = out[k];
     }
-    if (lane == 0) {
-      // exact lists: (|v|, wedge) of the candidates, best first
-      double av[2][WIN_MAX];
-      uint32_t wh[2][WIN_MAX];
-      for (int j = 0; j < 2; ++j) {
-        for (int e = 0; e < ncand[j]; ++e) {
-          const uint32_t i = hh[j][e] % (uint32_t)D;
-          av[j][e] = fabs(ev[j][e]);
-          wh[j][e] = i + (ev[j][e] < 0.0 ? (uint32_t)D : 0u);
-        }
-        for (int x = 1; x < ncand[j]; ++x)   // insertion sort (at most 8 entries)
-          for (int y = x; y > 0 && dentry_before(av[j][y], wh[j][y], av[j][y - 1], wh[j][y - 1]); --y) {
-            const double tv = av[j][y]; av[j][y] = av[j][y - 1]; av[j][y - 1] = tv;
-            const uint32_t tw = wh[j][y]; wh[j][y] = wh[j][y - 1]; wh[j][y - 1] = tw;
-          }
-      }
-      // the P best pairs: candidates (a+1)(b+1) <= P, P < 8
-      double ps[WIN_MAX * 4];
-      uint32_t pb[WIN_MAX * 4];
-      int C = 0;
-      for (int x = 0; x < P && x < ncand[0]; ++x)
-        for (int y = 0; (x + 1) * (y + 1) <= P && y < ncand[1]; ++y) {
-          ps[C] = av[0][x] + av[1][y];
-          pb[C] = wh[0][x] * (uint32_t)(2 * D) + wh[1][y];
-          ++C;
-        }
-      uint32_t* dst = a.out + (q * a.nt + tl) * (int64_t)a.probes;
-      for (int r = 0; r < P; ++r) {
-        int best = r;
-        for (int c = r + 1; c < C; ++c)
-          if (dentry_before(ps[c], pb[c], ps[best], pb[best])) best = c;
-        const double tv = ps[r]; ps[r] = ps[best]; ps[best] = tv;
-        const uint32_t tb = pb[r]; pb[r] = pb[best]; pb[best] = tb;
-        dst[r] = pb[r];
-      }
+    // rank of each candidate within its hash by (|v| desc, wedge asc)
+    const double av = fabs(ev);
+    const uint32_t wh = (h % (uint32_t)D) + (ev < 0.0 ? (uint32_t)D : 0u);
+    int rank = 0;
+    for (int o = 0; o < 16; ++o) {
+      const int l2 = 16 * j + o;
+      const double av2 = __shfl_sync(FULL, av, l2);
+      const uint32_t wh2 = __shfl_sync(FULL, wh, l2);
+      if (l2 != lane && ((mask >> l2) & 1u) && dentry_before(av2, wh2, av, wh)) ++rank;
     }
+    if (in) { sh.v[j][rank] = av; sh.w[j][rank] = wh; }
+    __syncwarp();
+    const int n0 = __popc(mask & 0xFFFFu), n1 = __popc(mask >> 16);
+    // the candidate pairs (x, y), (x + 1)(y + 1) <= P: lane l takes pair l
+    int x = 0, y = -1, base = 0;
+    for (int xx = 0; xx < P && xx < n0; ++xx) {
+      const int nb = min(P / (xx + 1), n1);
+      if (lane >= base && lane < base + nb) { x = xx; y = lane - base; }
+      base += nb;
+    }
+    const bool has = y >= 0;
+    const double ps = has ? sh.v[0][x] + sh.v[1][y] : -1.0;
+    const uint32_t pb = has ? sh.w[0][x] * (uint32_t)(2 * D) + sh.w[1][y] : 0xFFFFFFFFu;
+    int prank = 0;
+    for (int l2 = 0; l2 < base; ++l2) {
+      const double ps2 = __shfl_sync(FULL, ps, l2);
+      const uint32_t pb2 = __shfl_sync(FULL, pb, l2);
+      if (l2 != lane && dentry_before(ps2, pb2, ps, pb)) ++prank;
+    }
+    if (has && prank < P) a.out[(q * a.nt + tl) * (int64_t)a.probes + prank] = pb;
     __syncwarp();
   }
 }
@@ -1056,7 +1074,6 @@ __device__ __forceinline__ void write_items(const DedupArgs& a, int64_t q, uint3
 __global__ void __launch_bounds__(256)
 count_entries_kernel(DedupArgs a) {
   const int lane = threadIdx.x & 31;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *a.nitems = 0u;   // the dedup kernels append
   const int64_t q = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (q >= a.mq) return;
   const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
@@ -1071,7 +1088,12 @@ count_entries_kernel(DedupArgs a) {
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-  if (lane == 0) a.ecount[q] = s;
+  if (lane == 0) {
+    a.ecount[q] = s;
+    // the larger queries are listed for the kernels of their tier
+    if (s > (uint32_t)HMAX_BIG) a.tierq[a.mq - 1 - atomicAdd(a.tiern + 1, 1u)] = (uint32_t)q;
+    else if (s > (uint32_t)(HS_SMALL / 2)) a.tierq[atomicAdd(a.tiern, 1u)] = (uint32_t)q;
+  }
 }
 
 // Queries with more than HMAX_BIG bucket entries keep every entry (no
@@ -1086,9 +1108,10 @@ flatten_kernel(DedupArgs a) {
   const int64_t NB = 4ll * a.D * a.D;
   unsigned long long ent = 0, prb = 0;
   const int64_t nwarps = (int64_t)gridDim.x * DW;
-  for (int64_t q = (int64_t)blockIdx.x * DW + wid; q < a.mq; q += nwarps) {
+  const int64_t nq = a.tiern[1];   // listed by count_entries
+  for (int64_t i = (int64_t)blockIdx.x * DW + wid; i < nq; i += nwarps) {
+    const int64_t q = a.tierq[a.mq - 1 - i];
     const uint64_t E = a.eoff[q + 1] - a.eoff[q];
-    if (E <= (uint64_t)HMAX_BIG) continue;   // the hash kernels'
     const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
     WarpWalk w{&a, q, Pq, a.nt * Pq, NB, s_pbase[wid], s_pstart[wid]};
     uint32_t* out = a.cand + a.eoff[q];
@@ -1147,13 +1170,17 @@ dedup_hash_kernel(DedupArgs a) {
   __shared__ uint32_t wsum[HT / 32];
   __shared__ uint32_t s_n, s_base;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // the small tier scans every query; the larger one walks its list
+  const int64_t nq = ELO ? (int64_t)*a.tiern : a.mq;
+  if (nq == 0) return;   // uniform over the CTA
   for (int i = tid; i < HS / 4; i += HT)
     reinterpret_cast<uint4*>(tab)[i] = make_uint4(HEMPTY, HEMPTY, HEMPTY, HEMPTY);
   if (tid == 0) s_n = 0;
   __syncthreads();
   const int64_t NB = 4ll * a.D * a.D;
   unsigned long long ent = 0, uni = 0, prb = 0;
-  for (int64_t q = blockIdx.x; q < a.mq; q += gridDim.x) {
+  for (int64_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
+    const int64_t q = ELO ? (int64_t)a.tierq[qi] : qi;
     const uint64_t E = a.eoff[q + 1] - a.eoff[q];
     if (E > (uint64_t)(HS / 2) || E <= (uint64_t)ELO) continue;   // uniform over the CTA
     const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
@@ -1975,7 +2002,10 @@ fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_b
   const int S = pow2_ceil((a.D + 31) / 32);
   fpp_status s;
   if (a.lists && a.probes + 1 <= a.EL && a.EL <= SMALL_E) {
-    probe_small_kernel<<<(unsigned)ceil_div(warps, 256), 256, 0, st>>>(a);
+    const unsigned grid = (unsigned)ceil_div(warps, 256);
+    if (a.EL <= 2) probe_small_kernel<2><<<grid, 256, 0, st>>>(a);
+    else if (a.EL <= 4) probe_small_kernel<4><<<grid, 256, 0, st>>>(a);
+    else probe_small_kernel<SMALL_E><<<grid, 256, 0, st>>>(a);
     FPP_LAUNCHED();
     s = FPP_OK;
   } else switch (S) {
@@ -1992,7 +2022,8 @@ fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_b
   cudaGetDevice(&dev0);
   cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, dev0);
   if (a.lists) {
-    probe_window_kernel<<<sms0 * 2, 256, 0, st>>>(a);
+    // up to 64 resident warps per SM, one item each
+    probe_window_kernel<<<sms0 * 8, 256, 0, st>>>(a);
     FPP_LAUNCHED();
   } else if (a.recheck_s) {
     probe_pwin_kernel<<<sms0 * 2, 256, 0, st>>>(a);

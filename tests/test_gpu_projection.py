@@ -39,6 +39,24 @@ def test_projection_error_within_bound(F, d, D, L):
     assert float(err.max()) < 1e-4 * np.abs(exact).max()
 
 
+@pytest.mark.parametrize("d,D,L", [(128, 256, 2), (30, 5, 3)])
+def test_projection_error_within_bound_fp32_vectors(F, d, D, L):
+    # random vectors off the BF16 grid take the six-product split
+    X, Q = W.small_mixture(600, 300, d, 32, 0.25, 195 + d)
+    R = np.random.default_rng(7 + d).standard_normal((L, 2, D, d)).astype(np.float32)
+    ix = F.Index(X, L, D, 0.5, R=R)
+    assert ix.info()["r_pieces"] == 3
+    P = F.fpp_debug_projections(ix.handle, Q).astype(np.float64)
+    R64 = R.astype(np.float64).reshape(-1, d)
+    Q64 = Q.astype(np.float64)
+    exact = Q64 @ R64.T
+    c = F.fpp_projection_error_bound(ix.handle)
+    bound = c * np.linalg.norm(Q64, axis=1)[:, None] * np.linalg.norm(R64, axis=1)[None, :]
+    assert float((np.abs(P - exact) / bound).max()) < 0.25
+    # the seeded vectors are on the BF16 grid: three products
+    assert F.Index(X, L, D, 0.5, seed=1).info()["r_pieces"] == 1
+
+
 def test_projection_table_range(F):
     X, Q = W.small_mixture(500, 20, 64, 16, 0.25, 99)
     ix = F.Index(X, 6, 32, 0.5, seed=3)

@@ -57,6 +57,38 @@ def test_rotations_are_standard_normal():
     assert abs(np.corrcoef(a, b)[0, 1]) < 0.03
 
 
+def _nearest_bf16(x: float) -> float:
+    # the two BF16 neighbours of an FP32 value and the closer one, ties to
+    # the one with an even last kept bit
+    u = int(np.float32(x).view(np.uint32))
+    lo = u & 0xFFFF0000
+    hi = lo + 0x10000
+    flo = float(np.uint32(lo).view(np.float32))
+    fhi = float(np.uint32(hi).view(np.float32))
+    dlo, dhi = abs(x - flo), abs(fhi - x)
+    if dlo != dhi:
+        return flo if dlo < dhi else fhi
+    return flo if (lo >> 16) % 2 == 0 else fhi
+
+
+def test_rotations_on_bf16_grid():
+    # hand cases of the rounding: 1 + 2^-8 is a tie (to 1, even), 1 + 3 2^-9
+    # rounds up, -1.00390625 (tie) goes to -1
+    for x, want in ((1.0 + 2.0 ** -8, 1.0), (1.0 + 3 * 2.0 ** -9, 1.0 + 2.0 ** -7),
+                    (-(1.0 + 2.0 ** -8), -1.0), (1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -6)):
+        assert float(RG.round_bf16(np.array([x], np.float32))[0]) == want
+    # every coordinate is the BF16 value nearest to the FP32 Box-Muller value
+    raw = RG.splitmix64(RG.stream_state(5, 3), 2 * 300)
+    u1, u2 = RG.uniform_pair(raw)
+    z32 = RG.box_muller(u1, u2).astype(np.float32)
+    got = RG.gaussian_stream(5, 3, 300)
+    assert np.all(got.view(np.uint32) & 0xFFFF == 0)
+    for a, b in zip(z32, got):
+        assert _nearest_bf16(float(a)) == float(b)
+    R = O.gaussian_rotations(9, 2, 16, 24)
+    assert np.all(R.view(np.uint32) & 0xFFFF == 0)
+
+
 def test_uniforms_in_range():
     raw = RG.splitmix64(RG.stream_state(5, 3), 20000)
     u1, u2 = RG.uniform_pair(raw)
