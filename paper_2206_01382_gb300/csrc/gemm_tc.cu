@@ -358,6 +358,88 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             }
           }
         }
+      } else if (D >= 128) {
+        // D = 128 or 256: the thread's 128 columns belong to one hash.  Keys
+        // are ranked without the sign: (|p| bits with the low log2(2D)
+        // cleared) | 2^31 | (column offset o < 128 within the thread's half),
+        // one LOP3 per value with o an immediate; the signs are shifted into
+        // one mask per 32 columns and put into the kept keys at the end.
+        const int ldD = __ffs(D) - 1;
+        const uint32_t keep = 0x7FFFFFFFu & ~(2u * (uint32_t)D - 1u);
+        const uint32_t colbase = (uint32_t)cbeg & ((uint32_t)D - 1u);   // 0, or 128 when D = 256
+        uint32_t tk[EL > 0 ? EL + 1 : 1];
+#pragma unroll
+        for (int e = 0; e <= EL; ++e) tk[e] = 0u;
+        auto insert = [&](uint32_t x) {
+#pragma unroll
+          for (int e = 0; e < EL; ++e) {
+            const uint32_t hi = max(tk[e], x);
+            x = min(tk[e], x);
+            tk[e] = hi;
+          }
+          tk[EL] = max(tk[EL], x);
+        };
+        uint32_t sg[4];
+        uint32_t ra[32], rb[32];
+        tmem_ld32_async(taddr + (uint32_t)cbeg, ra);
+        tmem_wait(ra);
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          if (jj < 3) tmem_ld32_async(taddr + (uint32_t)(cbeg + 32 * (jj + 1)), rb);
+          uint32_t m = 0u;
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const uint32_t u = ra[k];
+            insert((u & keep) | (0x80000000u | (uint32_t)(32 * jj + k)));
+            m = __funnelshift_l(u, m, 1);   // m = (m << 1) | sign(u): bit 31 - k is column k's
+          }
+          sg[jj] = m;
+          if (jj < 3) {
+            tmem_wait(rb);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) ra[k] = rb[k];
+          }
+        }
+        // signed keys 2^31 | (|p| bits) | h, h = column + D for p < 0
+#pragma unroll
+        for (int e = 0; e <= EL; ++e) {
+          const uint32_t o = tk[e] & 127u, jj = o >> 5;
+          const uint32_t msk = jj == 0 ? sg[0] : jj == 1 ? sg[1] : jj == 2 ? sg[2] : sg[3];
+          const uint32_t neg = (msk >> (31u - (o & 31u))) & 1u;
+          tk[e] = tk[e] ? ((tk[e] & keep) | 0x80000000u | (neg << ldD) | (colbase + o)) : 0u;
+        }
+        // the cut only needs its value
+        const uint32_t cmask = 2u * (uint32_t)D - 1u;
+        auto emit = [&]() {
+          const int hg = n0 / D + half * (TC_BN / 2) / D;
+          if (row < M && hg < NH) {
+            uint64_t* dst = lists + ((int64_t)row * NH + hg) * LS;
+#pragma unroll
+            for (int e = 0; e < EL; ++e)
+              dst[e] = tk[e] ? (((uint64_t)((tk[e] & keep) + 1u) << 32) |
+                                (uint64_t)(0xFFFFFFFFu - (tk[e] & cmask)))
+                             : 0ull;
+            dst[EL] = tk[EL] ? ((uint64_t)((tk[EL] & keep) + 1u) << 32) : 0ull;
+          }
+        };
+        if (D == TC_BN) {
+          // the hash spans both column halves: merge the second half into the first
+          const int bA = 1 + quarter, bB = 5 + quarter;
+          if (half == 1) {
+#pragma unroll
+            for (int e = 0; e <= EL; ++e) sh->xk[quarter][lane][e] = tk[e];
+            asm volatile("bar.sync %0, 64;" ::"r"(bA) : "memory");
+            asm volatile("bar.sync %0, 64;" ::"r"(bB) : "memory");
+          } else {
+            asm volatile("bar.sync %0, 64;" ::"r"(bA) : "memory");
+#pragma unroll
+            for (int f = 0; f <= EL; ++f) insert(sh->xk[quarter][lane][f]);
+            asm volatile("bar.sync %0, 64;" ::"r"(bB) : "memory");
+            emit();
+          }
+        } else {
+          emit();
+        }
       } else {
         // running top-(EL + 1) packed keys of the current hash (descending;
         // 0 = none): entries 0..EL-1 form the list, entry EL is the cut

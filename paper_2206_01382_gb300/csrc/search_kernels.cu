@@ -1090,6 +1090,7 @@ count_entries_kernel(DedupArgs a) {
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
   if (lane == 0) {
     a.ecount[q] = s;
+    if (s == 0) a.ucount[q] = 0u;   // no tier kernel visits an empty query
     // the larger queries are listed for the kernels of their tier
     if (s > (uint32_t)HMAX_BIG) a.tierq[a.mq - 1 - atomicAdd(a.tiern + 1, 1u)] = (uint32_t)q;
     else if (s > (uint32_t)(HS_SMALL / 2)) a.tierq[atomicAdd(a.tiern, 1u)] = (uint32_t)q;

@@ -61,6 +61,28 @@ def test_tiny_workload_full_parity(F):
     _full_parity(F, X, Q, w.L, w.D, w.alpha, w.rot_seed, w.k, (1, 4, 16))
 
 
+@pytest.mark.parametrize("D", [128, 256])
+def test_list_epilogue_full_parity(F, D):
+    # D = 128 and 256 take the projection epilogue's wide path (sign masks,
+    # keys without the sign until the end); P = 1, 3, 7 give lists of 2, 4, 8
+    X, Q = W.small_mixture(30000, 60, 64, 64, 0.25, 90 + D)
+    _full_parity(F, X, Q, L=3, D=D, alpha=0.5, seed=7 + D, k=10, probes_list=(1, 3, 7))
+
+
+def test_queries_without_candidates_after_a_full_search(F):
+    # a query whose probed buckets are all empty returns only padding, also
+    # when the workspace still holds an earlier search's candidate counts
+    X, Q = W.small_mixture(50, 200, 16, 4, 0.3, 93)
+    ix = F.Index(X, 2, 64, 1.0, seed=3)
+    ix.search(X, 5, 1)
+    gi, gs = ix.search(Q, 5, 1)
+    _, _, res = O.search_batch(O.build_index(X, 2, 64, 1.0, seed=3), Q, 5, 1)
+    empty = [i for i, r in enumerate(res) if r.entries == 0 and not np.any(r.probe_flag)]
+    assert len(empty) > 20
+    for i in empty:
+        assert np.all(gi[i] == -1) and not np.any(np.isfinite(gs[i])), i
+
+
 def test_ragged_shapes_full_parity(F):
     # n, d, D, k, probes off every tile size; d not a multiple of 4
     X, Q = W.small_mixture(2999, 37, 30, 40, 0.2, 77)
