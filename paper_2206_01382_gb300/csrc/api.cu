@@ -899,7 +899,7 @@ fpp_status prepare_workspace(fpp_index* ix, Workspace& ws, const SearchPlan& pl,
     FPP_TRY(ws.out_ids.ensure((size_t)mc * pl.kmax * 8, false, st));
     FPP_TRY(ws.out_scores.ensure((size_t)mc * pl.kmax * 4, false, st));
   }
-  FPP_TRY(ws.ecount.ensure((size_t)3 * mc * 4, false, st));   // counts, distinct counts, tiers
+  FPP_TRY(ws.ecount.ensure((size_t)4 * mc * 4, false, st));   // counts, distinct counts, 2 tiers
   FPP_TRY(ws.eoff.ensure((size_t)(mc + 1) * 8, false, st));
   FPP_TRY(ws.scan.ensure((size_t)scan_scratch_elems(mc) * 8, false, st));
   FPP_TRY(ws.tkslow.ensure((size_t)(ceil_div(mc, 8) * 8) * topk_slow_cap() * 16, false, st));

@@ -504,10 +504,55 @@ fpp_status launch_row_norm_max(const float* X, int64_t n, int64_t ldx, int d, fl
 
 int64_t scan_scratch_elems(int64_t n) { return ceil_div(n, SCAN_BLK) + 1; }
 
+// Exclusive scan of at most SCAN1_MAX plain counts in one CTA: each thread
+// sums a contiguous run, the CTA scans the run totals, and each thread writes
+// its run's prefixes; out[n] is the total.
+constexpr int SCAN1_T = 1024;
+constexpr int64_t SCAN1_MAX = 65536;
+
+__global__ void __launch_bounds__(SCAN1_T)
+scan_single_kernel(const uint32_t* __restrict__ in, int64_t n, uint64_t* __restrict__ out) {
+  __shared__ uint64_t wsum[SCAN1_T / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int64_t per = (n + SCAN1_T - 1) / SCAN1_T;
+  const int64_t b = tid * per, e = b + per < n ? b + per : n;
+  uint64_t s = 0;
+  for (int64_t i = b; i < e; ++i) s += in[i];
+  uint64_t inc = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    uint64_t w = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  uint64_t run = (wid ? wsum[wid - 1] : 0ull) + inc - s;
+  for (int64_t i = b; i < e; ++i) {
+    out[i] = run;
+    run += in[i];
+  }
+  if (tid == SCAN1_T - 1) out[n] = wsum[SCAN1_T / 32 - 1];
+}
+
 fpp_status exclusive_scan_u32(const uint32_t* in, int64_t n, uint64_t* out, int mode,
                               KeepRule rule, uint64_t* scratch, cudaStream_t st) {
   if (n <= 0) {
     FPP_CUDA(cudaMemsetAsync(out, 0, sizeof(uint64_t), st));
+    return FPP_OK;
+  }
+  if (mode == 0 && n <= SCAN1_MAX) {
+    scan_single_kernel<<<1, SCAN1_T, 0, st>>>(in, n, out);
+    FPP_LAUNCHED();
     return FPP_OK;
   }
   const int64_t nb = ceil_div(n, SCAN_BLK);

@@ -104,6 +104,28 @@ __device__ __forceinline__ FF ff_add(FF x, FF y) {
 
 __device__ __forceinline__ double ff_value(FF x) { return (double)x.hi + (double)x.lo; }
 
+// hi + lo renormalised so that hi = fl(hi + lo) (an error-free TwoSum): such
+// pairs order like their exact sums by comparing hi, then lo, which keeps
+// exact comparisons off the (slow) FP64 pipe.
+__device__ __forceinline__ FF ff_norm(FF x) {
+  float s, e;
+  two_sum(x.hi, x.lo, s, e);
+  return FF{s, e};
+}
+
+// |x| of a normalised pair (hi carries the sign of the sum; hi = 0 means 0).
+__device__ __forceinline__ FF ff_abs(FF x) { return x.hi < 0.f ? FF{-x.hi, -x.lo} : x; }
+
+// a before b: larger value (normalised pairs), ties by lower id.
+__device__ __forceinline__ bool ff_before(FF a, uint32_t ia, FF b, uint32_t ib) {
+  if (a.hi != b.hi) return a.hi > b.hi;
+  if (a.lo != b.lo) return a.lo > b.lo;
+  return ia < ib;
+}
+
+// Normalised sum of two normalised pairs (relative error about 2^-46).
+__device__ __forceinline__ FF ff_sum(FF x, FF y) { return ff_norm(ff_add(x, y)); }
+
 // Warp-cooperative compensated dot product of two length-n FP32 vectors;
 // every lane returns the result.  Lanes take strided elements; the 32 partial
 // float-float sums are combined with error-free additions.
@@ -124,11 +146,11 @@ __device__ __forceinline__ double warp_dot2(const float* __restrict__ a,
 // Warp-cooperative compensated dot products of q with NR rows r_0..r_{NR-1}
 // (row stride ldr floats); q and the rows are 16-byte aligned with nf4 float4
 // per row.  Lanes read float4 chunks (coalesced); the NR rows are in flight
-// together.  Every lane returns all NR results.
+// together.  Every lane returns all NR results as normalised pairs.
 template <int NR>
-__device__ __forceinline__ void warp_dot2_rows(const float* __restrict__ q,
-                                               const float* __restrict__ r0, int64_t ldr,
-                                               int nf4, double* out) {
+__device__ __forceinline__ void warp_dot2_rows_ff(const float* __restrict__ q,
+                                                  const float* __restrict__ r0, int64_t ldr,
+                                                  int nf4, FF* out) {
   const int lane = threadIdx.x & 31;
   float p[NR], s[NR];
 #pragma unroll
@@ -155,14 +177,24 @@ __device__ __forceinline__ void warp_dot2_rows(const float* __restrict__ q,
       FF w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
       v = ff_add(v, w);
     }
-    out[k] = ff_value(v);
+    out[k] = ff_norm(v);
   }
+}
+
+template <int NR>
+__device__ __forceinline__ void warp_dot2_rows(const float* __restrict__ q,
+                                               const float* __restrict__ r0, int64_t ldr,
+                                               int nf4, double* out) {
+  FF v[NR];
+  warp_dot2_rows_ff<NR>(q, r0, ldr, nf4, v);
+#pragma unroll
+  for (int k = 0; k < NR; ++k) out[k] = ff_value(v[k]);
 }
 
 // Same, for NR rows at arbitrary addresses (16-byte aligned).
 template <int NR>
-__device__ __forceinline__ void warp_dot2_gather(const float* __restrict__ q,
-                                                 const float* const* rows, int nf4, double* out) {
+__device__ __forceinline__ void warp_dot2_gather_ff(const float* __restrict__ q,
+                                                    const float* const* rows, int nf4, FF* out) {
   const int lane = threadIdx.x & 31;
   float p[NR], s[NR];
 #pragma unroll
@@ -189,8 +221,17 @@ __device__ __forceinline__ void warp_dot2_gather(const float* __restrict__ q,
       FF w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
       v = ff_add(v, w);
     }
-    out[k] = ff_value(v);
+    out[k] = ff_norm(v);
   }
+}
+
+template <int NR>
+__device__ __forceinline__ void warp_dot2_gather(const float* __restrict__ q,
+                                                 const float* const* rows, int nf4, double* out) {
+  FF v[NR];
+  warp_dot2_gather_ff<NR>(q, rows, nf4, v);
+#pragma unroll
+  for (int k = 0; k < NR; ++k) out[k] = ff_value(v[k]);
 }
 
 // Single-thread compensated dot product of two 16-byte aligned rows of nf4

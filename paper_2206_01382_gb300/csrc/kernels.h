@@ -212,8 +212,8 @@ struct DedupArgs {
   uint32_t* ucount;          // [mq] distinct candidates per query
   ScoreItem* items;          // score work items, appended (any order)
   unsigned* nitems;          // items appended (zeroed before count_entries)
-  uint32_t* tierq;           // [mq] queries of the 32,768-slot tier from the front and of
-                             // the no-de-duplication tier from the back (count_entries)
+  uint32_t* tierq;           // [2][mq] queries listed by count_entries for the 32,768-slot
+                             // tier and for the no-de-duplication tier
   unsigned* tiern;           // [2] their counts (zeroed before count_entries)
   int no_items;              // 1: leave the items to the SimHash filter
   unsigned long long* stats; // entries, unique, -, probes

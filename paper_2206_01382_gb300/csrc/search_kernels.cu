@@ -334,14 +334,31 @@ __device__ __forceinline__ void warp_best(double& v, uint32_t& h) {
   }
 }
 
+// Entries with float-float values (normalised pairs; see ff_before).
+struct FEntry {
+  FF v;
+  uint32_t h;
+  uint32_t pad;
+};
+
+__device__ __forceinline__ void warp_best_ff(FF& v, uint32_t& h) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const FF v2{__shfl_xor_sync(FULL, v.hi, o), __shfl_xor_sync(FULL, v.lo, o)};
+    const uint32_t h2 = __shfl_xor_sync(FULL, h, o);
+    if (ff_before(v2, h2, v, h)) { v = v2; h = h2; }
+  }
+}
+
 
 // Re-decides the probe set of one (query, table) from compensated
-// projections dv[2D] (FP64-accurate), with the same ranking rule: the whole
+// projections dv[2D] (FP64-accurate float-float pairs), with the same ranking
+// rule: the whole
 // CTA sorts each hash's signed list (v desc, wedge asc), forms the pairs of
 // the best E = min(P, 2D) entries of each list with (a+1)(b+1) <= P, and
 // sorts them (score desc, bucket asc).  wsm holds 2 lists of pow2(2D) and
 // the pairs, pow2(pair_count) entries.
-__device__ void probe_exact_select(const double* dv, int D, int P, SD* lists, SD* pairs,
+__device__ void probe_exact_select(const FF* dv, int D, int P, SD* lists, SD* pairs,
                                    uint32_t* bucket_out) {
   const int W2 = 2 * D;
   const int NL = pow2_ceil(W2);
@@ -350,7 +367,7 @@ __device__ void probe_exact_select(const double* dv, int D, int P, SD* lists, SD
     SD* L = lists + j * NL;
     for (int h = threadIdx.x; h < NL; h += blockDim.x) {
       if (h < W2) {
-        const double v = h < D ? dv[j * D + h] : -dv[j * D + h - D];
+        const double v = h < D ? ff_value(dv[j * D + h]) : -ff_value(dv[j * D + h - D]);
         L[h] = SD{v, (uint32_t)h, 0};
       } else {
         L[h] = SD{-INFINITY, 0xFFFFFFFFu, 0};
@@ -382,28 +399,30 @@ __device__ void probe_exact_select(const double* dv, int D, int P, SD* lists, SD
 }
 
 // Small budgets (P <= 16): the same selection by one warp, E rounds of warp
-// maximum per list and P rounds over the pairs.
-__device__ void probe_exact_select_warp(const double* dv, int D, int P, unsigned char* wsm,
+// maximum per list and P rounds over the pairs, all in float-float.
+__device__ void probe_exact_select_warp(const FF* dv, int D, int P, unsigned char* wsm,
                                         uint32_t* bucket_out) {
   const int lane = threadIdx.x & 31;
-  DEntry* top = reinterpret_cast<DEntry*>(wsm);                              // 2 x LIST_CAP
-  DEntry* pairs = reinterpret_cast<DEntry*>(wsm + (size_t)2 * LIST_CAP * 16);  // SLOW_PAIRS
+  FEntry* top = reinterpret_cast<FEntry*>(wsm);                              // 2 x LIST_CAP
+  FEntry* pairs = reinterpret_cast<FEntry*>(wsm + (size_t)2 * LIST_CAP * 16);  // SLOW_PAIRS
   const int W2 = 2 * D;
   const int E = P < W2 ? P : W2;
+  const FF none{-INFINITY, 0.f};
   for (int j = 0; j < 2; ++j) {
     uint64_t taken = 0ull;  // bit s: wedge lane + 32 s already selected
     for (int r = 0; r < E; ++r) {
-      double bv = -INFINITY;
+      FF bv = none;
       uint32_t bh = 0xFFFFFFFFu;
       for (int s = 0; s * 32 + lane < W2; ++s) {
         if (taken & (1ull << s)) continue;
         const uint32_t h = s * 32 + lane;
-        const double v = h < (uint32_t)D ? dv[j * D + h] : -dv[j * D + h - D];
-        if (dentry_before(v, h, bv, bh)) { bv = v; bh = h; }
+        const FF x = dv[j * D + (h < (uint32_t)D ? h : h - D)];
+        const FF v = h < (uint32_t)D ? x : FF{-x.hi, -x.lo};
+        if (ff_before(v, h, bv, bh)) { bv = v; bh = h; }
       }
-      warp_best(bv, bh);
+      warp_best_ff(bv, bh);
       if ((int)(bh & 31) == lane) taken |= 1ull << (bh >> 5);
-      if (lane == 0) top[j * LIST_CAP + r] = DEntry{bv, bh, 0};
+      if (lane == 0) top[j * LIST_CAP + r] = FEntry{bv, bh, 0};
     }
   }
   __syncwarp();
@@ -413,26 +432,26 @@ __device__ void probe_exact_select_warp(const double* dv, int D, int P, unsigned
     if (nb > E) nb = E;
     if (nb <= 0) break;
     for (int b = lane; b < nb; b += 32) {
-      const DEntry x = top[ai], y = top[LIST_CAP + b];
-      pairs[C + b] = DEntry{x.v + y.v, x.h * (uint32_t)W2 + y.h, 0};
+      const FEntry x = top[ai], y = top[LIST_CAP + b];
+      pairs[C + b] = FEntry{ff_sum(x.v, y.v), x.h * (uint32_t)W2 + y.h, 0};
     }
     C += nb;
   }
   __syncwarp();
   unsigned taken = 0u;
   for (int r = 0; r < P; ++r) {
-    double bv = -INFINITY;
+    FF bv = none;
     uint32_t bh = 0xFFFFFFFFu;
     int bs = -1;
     for (int s = 0; s * 32 + lane < C; ++s) {
       if (taken & (1u << s)) continue;
-      const DEntry e = pairs[s * 32 + lane];
-      if (dentry_before(e.v, e.h, bv, bh)) { bv = e.v; bh = e.h; bs = s; }
+      const FEntry e = pairs[s * 32 + lane];
+      if (ff_before(e.v, e.h, bv, bh)) { bv = e.v; bh = e.h; bs = s; }
     }
     // bucket ids of distinct pairs are distinct, so the owner lane is unique
-    double wv = bv;
+    FF wv = bv;
     uint32_t wh = bh;
-    warp_best(wv, wh);
+    warp_best_ff(wv, wh);
     if (bs >= 0 && bh == wh) taken |= 1u << bs;
     if (lane == 0) bucket_out[r] = wh;
   }
@@ -457,7 +476,7 @@ __global__ void __launch_bounds__(RECHECK_THREADS)
 probe_recheck_kernel(ProbeArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = RECHECK_THREADS / 32;
-  double* dv = reinterpret_cast<double*>(smem);
+  FF* dv = reinterpret_cast<FF*>(smem);
   unsigned char* wsm = smem + (size_t)8 * 2 * a.D;
   const bool after_window = a.lists || a.recheck_s;
   const unsigned cnt = after_window ? *a.recheck2_count : *a.recheck_count;
@@ -474,16 +493,16 @@ probe_recheck_kernel(ProbeArgs a) {
     const float* Rt = a.R + (int64_t)2 * t * a.D * a.ldr;
     for (int i0 = wid * 8; i0 < rows; i0 += nw * 8) {
       if (i0 + 8 <= rows) {
-        double v[8];
-        warp_dot2_rows<8>(qv, Rt + (int64_t)i0 * a.ldr, a.ldr, nf4, v);
+        FF v[8];
+        warp_dot2_rows_ff<8>(qv, Rt + (int64_t)i0 * a.ldr, a.ldr, nf4, v);
         if (lane == 0) {
 #pragma unroll
           for (int k = 0; k < 8; ++k) dv[i0 + k] = v[k];
         }
       } else {
         for (int i = i0; i < rows; ++i) {
-          double v[1];
-          warp_dot2_rows<1>(qv, Rt + (int64_t)i * a.ldr, a.ldr, nf4, v);
+          FF v[1];
+          warp_dot2_rows_ff<1>(qv, Rt + (int64_t)i * a.ldr, a.ldr, nf4, v);
           if (lane == 0) dv[i] = v[0];
         }
       }
@@ -512,7 +531,7 @@ probe_recheck_kernel(ProbeArgs a) {
 constexpr int WIN_MAX = 8;
 
 struct WinShared {
-  double v[2][WIN_MAX];   // exact |q^T r| of each hash's candidates, best first
+  FF v[2][WIN_MAX];       // exact |q^T r| of each hash's candidates, best first
   uint32_t w[2][WIN_MAX]; // their signed wedges
 };
 
@@ -539,15 +558,16 @@ probe_window_kernel(ProbeArgs a) {
     }
     const uint64_t key =
         e <= a.EL ? a.lists[((q * a.nt + tl) * 2 + j) * (int64_t)(a.EL + 1) + e] : 0ull;
-    const double v = key ? (double)__uint_as_float((uint32_t)(key >> 32) - 1u) : -1.0;
-    const double v0 = __shfl_sync(FULL, v, 16 * j);
-    const double vP = __shfl_sync(FULL, v, 16 * j + P - 1);
-    const double vcut = __shfl_sync(FULL, v, 16 * j + a.EL);   // largest |p| left out
-    // FP32 error, plus the truncation of the list values (at most trunc
-    // times the hash's largest value)
-    const double eps = a.gamma * (double)a.qnorm[q] * (double)a.rmax[2 * t + j] * (1.0 + 1e-6) +
-                       (double)a.trunc * fmax(v0, 0.0) * (1.0 + 1e-6);
-    const double lim = vP - 2.0 * eps;
+    const float v = key ? __uint_as_float((uint32_t)(key >> 32) - 1u) : -1.f;
+    const float v0 = __shfl_sync(FULL, v, 16 * j);
+    const float vP = __shfl_sync(FULL, v, 16 * j + P - 1);
+    const float vcut = __shfl_sync(FULL, v, 16 * j + a.EL);   // largest |p| left out
+    // FP32 error, plus the truncation of the list values (at most trunc times
+    // the hash's largest value); the 1e-5 margins cover the roundings of
+    // these FP32 expressions, and lim is lowered by one more ulp of vP
+    const float eps = a.gammaf * a.qnorm[q] * a.rmax[2 * t + j] * 1.00001f +
+                      a.trunc * fmaxf(v0, 0.f) * 1.00001f;
+    const float lim = (vP - 2.f * eps) - 1.2e-7f * fabsf(vP) - 1e-30f;
     // every entry that can still be among the P best of its hash is in the list
     if (!__all_sync(FULL, vcut < lim)) {
       if (lane == 0) a.recheck2[atomicAdd(a.recheck2_count, 1u)] = item;
@@ -558,7 +578,7 @@ probe_window_kernel(ProbeArgs a) {
     const int nc = __popc(mask);
     // exact projections of the candidates, four rows in flight per round
     const uint32_t h = 0xFFFFFFFFu - (uint32_t)key;
-    double ev = 0.0;
+    FF ev{0.f, 0.f};
     const float* qv = a.Q + q * a.ldq;
     for (int g = 0; g < nc; g += 4) {
       const float* rows[4];
@@ -569,21 +589,21 @@ probe_window_kernel(ProbeArgs a) {
         const uint32_t hk = __shfl_sync(FULL, h, src[k]) % (uint32_t)D;
         rows[k] = a.R + ((int64_t)(2 * t + (src[k] >> 4)) * D + hk) * a.ldr;
       }
-      double out[4];
-      warp_dot2_gather<4>(qv, rows, nf4, out);
+      FF out[4];
+      warp_dot2_gather_ff<4>(qv, rows, nf4, out);
 #pragma unroll
       for (int k = 0; k < 4; ++k)
         if (g + k < nc && lane == src[k]) ev = out[k];
     }
     // rank of each candidate within its hash by (|v| desc, wedge asc)
-    const double av = fabs(ev);
-    const uint32_t wh = (h % (uint32_t)D) + (ev < 0.0 ? (uint32_t)D : 0u);
+    const FF av = ff_abs(ev);
+    const uint32_t wh = (h % (uint32_t)D) + (ev.hi < 0.f ? (uint32_t)D : 0u);
     int rank = 0;
     for (int o = 0; o < 16; ++o) {
       const int l2 = 16 * j + o;
-      const double av2 = __shfl_sync(FULL, av, l2);
+      const FF av2{__shfl_sync(FULL, av.hi, l2), __shfl_sync(FULL, av.lo, l2)};
       const uint32_t wh2 = __shfl_sync(FULL, wh, l2);
-      if (l2 != lane && ((mask >> l2) & 1u) && dentry_before(av2, wh2, av, wh)) ++rank;
+      if (l2 != lane && ((mask >> l2) & 1u) && ff_before(av2, wh2, av, wh)) ++rank;
     }
     if (in) { sh.v[j][rank] = av; sh.w[j][rank] = wh; }
     __syncwarp();
@@ -596,13 +616,13 @@ probe_window_kernel(ProbeArgs a) {
       base += nb;
     }
     const bool has = y >= 0;
-    const double ps = has ? sh.v[0][x] + sh.v[1][y] : -1.0;
+    const FF ps = has ? ff_sum(sh.v[0][x], sh.v[1][y]) : FF{-1.f, 0.f};
     const uint32_t pb = has ? sh.w[0][x] * (uint32_t)(2 * D) + sh.w[1][y] : 0xFFFFFFFFu;
     int prank = 0;
     for (int l2 = 0; l2 < base; ++l2) {
-      const double ps2 = __shfl_sync(FULL, ps, l2);
+      const FF ps2{__shfl_sync(FULL, ps.hi, l2), __shfl_sync(FULL, ps.lo, l2)};
       const uint32_t pb2 = __shfl_sync(FULL, pb, l2);
-      if (l2 != lane && dentry_before(ps2, pb2, ps, pb)) ++prank;
+      if (l2 != lane && ff_before(ps2, pb2, ps, pb)) ++prank;
     }
     if (has && prank < P) a.out[(q * a.nt + tl) * (int64_t)a.probes + prank] = pb;
     __syncwarp();
@@ -959,7 +979,7 @@ __global__ void query_norms_kernel(const float* __restrict__ Q, int64_t m, int64
 // a launch shaped for them:
 //  count_entries  warp per query: bucket entries E_q of its probed buckets;
 //                 an exclusive scan gives each query a region of E_q slots;
-//  dedup          CTA per query with E_q <= 16,384: walks the kept ids of its
+//  dedup          CTA per query with E_q <= 16,384 (three sizes): walks the kept ids of its
 //                 buckets, inserts them into a shared-memory hash set, writes
 //                 the ids seen first to the front of its region and appends
 //                 work items of <= ITEM ids; larger queries are copied
@@ -973,6 +993,8 @@ __global__ void query_norms_kernel(const float* __restrict__ Q, int64_t m, int64
 constexpr int DW = 8;                           // warps per flatten CTA
 constexpr int HS_SMALL = 4096;                  // hash slots of the small-query CTAs
 constexpr int HS_BIG = 32768;                   // hash slots of the mid-size-query CTAs
+constexpr int HMAX_SMALL = 3072;                // entries of the small-query tier (the distinct
+                                                // ids, about 40% of them, fill a fraction of it)
 constexpr int HMAX_BIG = HS_BIG / 2;            // larger queries are not de-duplicated
 constexpr int HU = 8;                           // entry loads in flight per lane
 constexpr int PCHUNK = 128;                     // probed buckets resolved per pass
@@ -1080,20 +1102,34 @@ count_entries_kernel(DedupArgs a) {
   const int64_t NB = 4ll * a.D * a.D;
   const int nprobe = a.nt * Pq;
   uint32_t s = 0;
-  for (int pi = lane; pi < nprobe; pi += 32) {
-    const int tl = pi / Pq, p = pi - tl * Pq;
-    const uint32_t b = a.probes[(q * a.nt + tl) * (int64_t)a.pstride + p];
-    const uint32_t* off = a.offsets + (int64_t)(a.tb + tl) * (NB + 1);
-    if (b != PROBE_EMPTY) s += off[b + 1] - off[b];
+  // four probes per lane per pass: their bucket ids, then their offsets,
+  // are loaded together
+  for (int pi0 = 0; pi0 < nprobe; pi0 += 128) {
+    uint32_t b[4];
+    const uint32_t* off[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int pi = pi0 + r * 32 + lane;
+      b[r] = PROBE_EMPTY;
+      off[r] = a.offsets;
+      if (pi < nprobe) {
+        const int tl = pi / Pq, p = pi - tl * Pq;
+        b[r] = a.probes[(q * a.nt + tl) * (int64_t)a.pstride + p];
+        off[r] = a.offsets + (int64_t)(a.tb + tl) * (NB + 1);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (b[r] != PROBE_EMPTY) s += off[r][b[r] + 1] - off[r][b[r]];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
   if (lane == 0) {
     a.ecount[q] = s;
     if (s == 0) a.ucount[q] = 0u;   // no tier kernel visits an empty query
-    // the larger queries are listed for the kernels of their tier
-    if (s > (uint32_t)HMAX_BIG) a.tierq[a.mq - 1 - atomicAdd(a.tiern + 1, 1u)] = (uint32_t)q;
-    else if (s > (uint32_t)(HS_SMALL / 2)) a.tierq[atomicAdd(a.tiern, 1u)] = (uint32_t)q;
+    // queries above the small tier are listed for the kernels of their tier
+    const int tier = s > (uint32_t)HMAX_BIG ? 1 : s > (uint32_t)HMAX_SMALL ? 0 : -1;
+    if (tier >= 0) a.tierq[tier * a.mq + atomicAdd(a.tiern + tier, 1u)] = (uint32_t)q;
   }
 }
 
@@ -1111,7 +1147,7 @@ flatten_kernel(DedupArgs a) {
   const int64_t nwarps = (int64_t)gridDim.x * DW;
   const int64_t nq = a.tiern[1];   // listed by count_entries
   for (int64_t i = (int64_t)blockIdx.x * DW + wid; i < nq; i += nwarps) {
-    const int64_t q = a.tierq[a.mq - 1 - i];
+    const int64_t q = a.tierq[a.mq + i];
     const uint64_t E = a.eoff[q + 1] - a.eoff[q];
     const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
     WarpWalk w{&a, q, Pq, a.nt * Pq, NB, s_pbase[wid], s_pstart[wid]};
@@ -1152,43 +1188,42 @@ flatten_kernel(DedupArgs a) {
   }
 }
 
-// De-duplication of the queries with (ELO, HS / 2] bucket entries, one CTA
-// (HT threads) per query: an open-addressing hash set of HS ids in shared
-// memory (linear probing, insertion by compare-and-swap, so exactly one
-// thread sees an id as new), at most half full and reset after each query.
-// The probed buckets are resolved HT at a time; each thread then walks a
+// De-duplication of the queries with (ELO, EHI] bucket entries, one CTA (NT
+// threads) per query: an open-addressing hash set of HS ids in shared memory
+// (linear probing, insertion by compare-and-swap, so exactly one thread sees
+// an id as new), at most EHI / HS full and reset after each query.  TIER < 0
+// visits every query; otherwise the queries count_entries listed for TIER.
+// The probed buckets are resolved NT at a time; each thread then walks a
 // contiguous run of the entries, so the bucket of its next entry is found by
 // stepping instead of searching.
 constexpr uint32_t HEMPTY = 0xFFFFFFFFu;
-constexpr int HT = 256;                         // threads per hash-dedup CTA
 
-template <int HS, int LOG2HS, int ELO>
-__global__ void __launch_bounds__(HT)
+template <int NT, int HS, int LOG2HS, int ELO, int EHI, int TIER>
+__global__ void __launch_bounds__(NT, 1280 / NT)
 dedup_hash_kernel(DedupArgs a) {
   extern __shared__ __align__(16) uint32_t tab[];
-  __shared__ uint64_t pbase[HT];
-  __shared__ uint32_t pstart[HT + 1];
-  __shared__ uint32_t wsum[HT / 32];
+  __shared__ uint64_t pbase[NT];
+  __shared__ uint32_t pstart[NT + 1];
+  __shared__ uint32_t wsum[NT / 32];
   __shared__ uint32_t s_n, s_base;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  // the small tier scans every query; the larger one walks its list
-  const int64_t nq = ELO ? (int64_t)*a.tiern : a.mq;
+  const int64_t nq = TIER < 0 ? a.mq : (int64_t)a.tiern[TIER];
   if (nq == 0) return;   // uniform over the CTA
-  for (int i = tid; i < HS / 4; i += HT)
+  for (int i = tid; i < HS / 4; i += NT)
     reinterpret_cast<uint4*>(tab)[i] = make_uint4(HEMPTY, HEMPTY, HEMPTY, HEMPTY);
   if (tid == 0) s_n = 0;
   __syncthreads();
   const int64_t NB = 4ll * a.D * a.D;
   unsigned long long ent = 0, uni = 0, prb = 0;
   for (int64_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
-    const int64_t q = ELO ? (int64_t)a.tierq[qi] : qi;
+    const int64_t q = TIER < 0 ? qi : (int64_t)a.tierq[TIER * a.mq + qi];
     const uint64_t E = a.eoff[q + 1] - a.eoff[q];
-    if (E > (uint64_t)(HS / 2) || E <= (uint64_t)ELO) continue;   // uniform over the CTA
+    if (E > (uint64_t)EHI || E <= (uint64_t)ELO) continue;   // uniform over the CTA
     const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
     const int nprobe = a.nt * Pq;
     uint32_t* out = a.cand + a.eoff[q];
-    for (int pc0 = 0; pc0 < nprobe; pc0 += HT) {
-      const int nc = min(HT, nprobe - pc0);
+    for (int pc0 = 0; pc0 < nprobe; pc0 += NT) {
+      const int nc = min(NT, nprobe - pc0);
       uint32_t c = 0;
       if (tid < nc) {
         const int pi = pc0 + tid;
@@ -1211,15 +1246,15 @@ dedup_hash_kernel(DedupArgs a) {
       __syncthreads();
       uint32_t woff = 0, total = 0;
 #pragma unroll
-      for (int w = 0; w < HT / 32; ++w) {
+      for (int w = 0; w < NT / 32; ++w) {
         const uint32_t v = wsum[w];
         woff += w < wid ? v : 0u;
         total += v;
       }
       if (tid < nc) pstart[tid] = woff + inc - c;
-      if (tid == 0) pstart[nc] = total;   // nc <= HT; entries past nc are never read
+      if (tid == 0) pstart[nc] = total;   // nc <= NT; entries past nc are never read
       __syncthreads();
-      const uint32_t per = (total + HT - 1) / HT;
+      const uint32_t per = (total + NT - 1) / NT;
       uint32_t e = tid * per;
       const uint32_t eend = min(e + per, total);
       int bk = 0;
@@ -1251,26 +1286,54 @@ dedup_hash_kernel(DedupArgs a) {
             ++e;
           }
         }
+        // insertion: every pending id tries its current slot each pass, all
+        // HU compare-and-swaps in flight together; at load <= 1/4 a second
+        // pass is rare
+        uint32_t hp[HU];
+        bool pend[HU], fresh[HU];
 #pragma unroll
         for (int u = 0; u < HU; ++u) {
-          bool fresh = false;
-          if (has[u]) {
-            uint32_t h = (id[u] * 0x9E3779B1u) >> (32 - LOG2HS);
-            while (true) {
-              const uint32_t old = atomicCAS(tab + h, HEMPTY, id[u]);
-              if (old == HEMPTY) { fresh = true; break; }
-              if (old == id[u]) break;
-              h = (h + 1) & (HS - 1);
+          pend[u] = has[u];
+          fresh[u] = false;
+          hp[u] = (id[u] * 0x9E3779B1u) >> (32 - LOG2HS);
+        }
+        bool again = true;
+        while (again) {
+          again = false;
+#pragma unroll
+          for (int u = 0; u < HU; ++u) {
+            if (pend[u]) {
+              const uint32_t old = atomicCAS(tab + hp[u], HEMPTY, id[u]);
+              if (old == HEMPTY) {
+                fresh[u] = true;
+                pend[u] = false;
+              } else if (old == id[u]) {
+                pend[u] = false;
+              } else {
+                hp[u] = (hp[u] + 1) & (HS - 1);
+                again = true;
+              }
             }
           }
-          const unsigned m = __ballot_sync(FULL, fresh);
-          if (m) {
-            uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(&s_n, (uint32_t)__popc(m));
-            base = __shfl_sync(FULL, base, 0);
-            if (fresh) out[base + __popc(m & ((1u << lane) - 1u))] = id[u];
-          }
         }
+        // the thread's new ids go to consecutive slots: one warp scan and one
+        // shared-memory atomic per warp
+        uint32_t nf = 0;
+#pragma unroll
+        for (int u = 0; u < HU; ++u) nf += fresh[u] ? 1u : 0u;
+        uint32_t inc = nf;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t2 = __shfl_up_sync(FULL, inc, o);
+          if (lane >= o) inc += t2;
+        }
+        uint32_t wbase = 0;
+        if (lane == 31 && inc) wbase = atomicAdd(&s_n, inc);
+        wbase = __shfl_sync(FULL, wbase, 31);
+        uint32_t pos = wbase + inc - nf;
+#pragma unroll
+        for (int u = 0; u < HU; ++u)
+          if (fresh[u]) out[pos++] = id[u];
       }
       __syncthreads();   // pbase / pstart are rewritten by the next chunk
     }
@@ -1284,14 +1347,14 @@ dedup_hash_kernel(DedupArgs a) {
       s_base = nit ? atomicAdd(a.nitems, nit) : 0u;
     }
     __syncthreads();
-    for (uint32_t k = tid; k < nit; k += HT) {
+    for (uint32_t k = tid; k < nit; k += NT) {
       ScoreItem itm;
       itm.q = (uint32_t)q;
       itm.len = min((uint32_t)ITEM, U - k * ITEM);
       itm.start = a.eoff[q] + (uint64_t)k * ITEM;
       a.items[s_base + k] = itm;
     }
-    for (int i = tid; i < HS / 4; i += HT)
+    for (int i = tid; i < HS / 4; i += NT)
       reinterpret_cast<uint4*>(tab)[i] = make_uint4(HEMPTY, HEMPTY, HEMPTY, HEMPTY);
     if (tid == 0) s_n = 0;
     __syncthreads();
@@ -2097,33 +2160,35 @@ fpp_status launch_count_entries(const DedupArgs& a, cudaStream_t st) {
   return FPP_OK;
 }
 
-template <int HS, int LOG2HS, int ELO>
+template <int NT, int HS, int LOG2HS, int ELO, int EHI, int TIER>
 fpp_status launch_hash_tier(const DedupArgs& a, std::atomic<int>& grid_cache, cudaStream_t st) {
   const size_t smem = (size_t)HS * 4;
   int g = grid_cache.load(std::memory_order_relaxed);
   if (!g) {
-    FPP_CUDA(cudaFuncSetAttribute(dedup_hash_kernel<HS, LOG2HS, ELO>,
+    FPP_CUDA(cudaFuncSetAttribute(dedup_hash_kernel<NT, HS, LOG2HS, ELO, EHI, TIER>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0, dev = 0, sms = 0;
-    FPP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dedup_hash_kernel<HS, LOG2HS, ELO>,
-                                                           HT, smem));
+    FPP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dedup_hash_kernel<NT, HS, LOG2HS, ELO, EHI, TIER>,
+                                                           NT, smem));
     FPP_CUDA(cudaGetDevice(&dev));
     FPP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     g = std::max(1, per_sm) * sms;
     grid_cache.store(g, std::memory_order_relaxed);
   }
-  dedup_hash_kernel<HS, LOG2HS, ELO><<<(int)std::min<int64_t>(a.mq, g), HT, smem, st>>>(a);
+  dedup_hash_kernel<NT, HS, LOG2HS, ELO, EHI, TIER><<<(int)std::min<int64_t>(a.mq, g), NT, smem, st>>>(a);
   FPP_LAUNCHED();
   return FPP_OK;
 }
 
 fpp_status launch_dedup(const DedupArgs& a, cudaStream_t st) {
   if (a.mq <= 0) return FPP_OK;
-  // three tiers by entry count: a 4,096-slot table (<= 2,048 entries), a
-  // 32,768-slot table (<= 16,384), and no de-duplication above that
+  // three tiers by entry count: 128 threads and 4,096 slots (<= 3,072
+  // entries), 256 threads and 32,768 slots (<= 16,384), and no
+  // de-duplication above that; a table never holds more distinct ids than
+  // three quarters of its slots (one half for the larger one)
   static std::atomic<int> g_small{0}, g_big{0};
-  FPP_TRY((launch_hash_tier<HS_SMALL, 12, 0>(a, g_small, st)));
-  FPP_TRY((launch_hash_tier<HS_BIG, 15, HS_SMALL / 2>(a, g_big, st)));
+  FPP_TRY((launch_hash_tier<128, HS_SMALL, 12, 0, HMAX_SMALL, -1>(a, g_small, st)));
+  FPP_TRY((launch_hash_tier<256, HS_BIG, 15, HMAX_SMALL, HMAX_BIG, 0>(a, g_big, st)));
   int sms = 0, dev = 0;
   FPP_CUDA(cudaGetDevice(&dev));
   FPP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
