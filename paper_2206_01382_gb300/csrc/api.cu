@@ -853,6 +853,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   ta.scores = ws.cscores.as<float>(); ta.k_pq = kpq; ta.k = pl.k; ta.kmax = pl.kmax;
   ta.X = ix->X; ta.ldx = ix->dpad; ta.Q = ws.qpad.as<float>(); ta.ldq = ix->dpad; ta.d = ix->d;
   ta.qnorm = ws.qnorm.as<float>(); ta.xmax = ix->xmax; ta.gamma = ix->score_gamma;
+  ta.gammaf = (float)(ix->score_gamma * 1.0001);
   ta.kprime = topk_kprime(ix, pl.kmax);
   ta.approx = ix->precision != FPP_FP32;
   ta.cap = topk_cap(ta.kprime); ta.rcap = topk_rcap(ta.kprime);

@@ -504,9 +504,9 @@ fpp_status launch_row_norm_max(const float* X, int64_t n, int64_t ldx, int d, fl
 
 int64_t scan_scratch_elems(int64_t n) { return ceil_div(n, SCAN_BLK) + 1; }
 
-// Exclusive scan of at most SCAN1_MAX plain counts in one CTA: each thread
-// sums a contiguous run, the CTA scans the run totals, and each thread writes
-// its run's prefixes; out[n] is the total.
+// Exclusive scan of at most SCAN1_MAX plain counts in one CTA, in tiles of
+// 4 x 1,024 counts: each thread scans four consecutive counts, the CTA scans
+// the thread totals, and a running carry joins the tiles; out[n] is the total.
 constexpr int SCAN1_T = 1024;
 constexpr int64_t SCAN1_MAX = 65536;
 
@@ -514,34 +514,41 @@ __global__ void __launch_bounds__(SCAN1_T)
 scan_single_kernel(const uint32_t* __restrict__ in, int64_t n, uint64_t* __restrict__ out) {
   __shared__ uint64_t wsum[SCAN1_T / 32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int64_t per = (n + SCAN1_T - 1) / SCAN1_T;
-  const int64_t b = tid * per, e = b + per < n ? b + per : n;
-  uint64_t s = 0;
-  for (int64_t i = b; i < e; ++i) s += in[i];
-  uint64_t inc = s;
+  uint64_t carry = 0;
+  for (int64_t t0 = 0; t0 < n; t0 += 4 * SCAN1_T) {
+    const int64_t b = t0 + 4 * tid;
+    uint32_t v[4];
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint64_t t = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += t;
-  }
-  if (lane == 31) wsum[wid] = inc;
-  __syncthreads();
-  if (wid == 0) {
-    uint64_t w = wsum[lane];
+    for (int r = 0; r < 4; ++r) v[r] = b + r < n ? in[b + r] : 0u;
+    const uint64_t s = (uint64_t)v[0] + v[1] + v[2] + v[3];
+    uint64_t inc = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint64_t t = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += t;
+      const uint64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
     }
-    wsum[lane] = w;
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+      uint64_t w = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t t = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += t;
+      }
+      wsum[lane] = w;
+    }
+    __syncthreads();
+    uint64_t run = carry + (wid ? wsum[wid - 1] : 0ull) + inc - s;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (b + r < n) out[b + r] = run;
+      run += v[r];
+    }
+    carry += wsum[SCAN1_T / 32 - 1];
+    __syncthreads();   // wsum is rewritten by the next tile
   }
-  __syncthreads();
-  uint64_t run = (wid ? wsum[wid - 1] : 0ull) + inc - s;
-  for (int64_t i = b; i < e; ++i) {
-    out[i] = run;
-    run += in[i];
-  }
-  if (tid == SCAN1_T - 1) out[n] = wsum[SCAN1_T / 32 - 1];
+  if (tid == 0) out[n] = carry;
 }
 
 fpp_status exclusive_scan_u32(const uint32_t* in, int64_t n, uint64_t* out, int mode,

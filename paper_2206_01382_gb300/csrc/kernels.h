@@ -271,6 +271,7 @@ struct TopkArgs {
   const float* qnorm;        // [mq]
   float xmax;
   double gamma;              // FP32 score error factor gamma_d
+  float gammaf;              // gamma rounded up to FP32 with margin
   const int32_t* k_pq;       // [mq] or NULL
   int k, kmax, cap, rcap;
   int kprime;                // shortlist re-scored exactly (>= k + 16)

@@ -351,6 +351,27 @@ __device__ __forceinline__ void warp_best_ff(FF& v, uint32_t& h) {
 }
 
 
+// Bitonic sort of N (a power of two) entries by ff_before, one warp.
+__device__ __forceinline__ void warp_sort_fe(FEntry* a, int N) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 2; k <= N; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < N; i += 32) {
+        const int l = i ^ j;
+        if (l > i) {
+          const FEntry x = a[i], y = a[l];
+          const bool first = (i & k) == 0;
+          if (first ? ff_before(y.v, y.h, x.v, x.h) : ff_before(x.v, x.h, y.v, y.h)) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // Re-decides the probe set of one (query, table) from compensated
 // projections dv[2D] (FP64-accurate float-float pairs), with the same ranking
 // rule: the whole
@@ -1146,6 +1167,7 @@ flatten_kernel(DedupArgs a) {
   unsigned long long ent = 0, prb = 0;
   const int64_t nwarps = (int64_t)gridDim.x * DW;
   const int64_t nq = a.tiern[1];   // listed by count_entries
+  if ((int64_t)blockIdx.x * DW >= nq) return;   // no listed query for this CTA
   for (int64_t i = (int64_t)blockIdx.x * DW + wid; i < nq; i += nwarps) {
     const int64_t q = a.tierq[a.mq + i];
     const uint64_t E = a.eoff[q + 1] - a.eoff[q];
@@ -1181,7 +1203,7 @@ flatten_kernel(DedupArgs a) {
     ent += __shfl_xor_sync(FULL, ent, o);
     prb += __shfl_xor_sync(FULL, prb, o);
   }
-  if (lane == 0 && a.stats) {
+  if (lane == 0 && a.stats && ent) {
     atomicAdd(a.stats + 0, ent);
     atomicAdd(a.stats + 1, ent);
     atomicAdd(a.stats + 3, prb);
@@ -1738,6 +1760,7 @@ topk_kernel(TopkArgs a) {
   const int64_t q = (int64_t)blockIdx.x * 8 + wid;
   uint64_t* buf = reinterpret_cast<uint64_t*>(smem) + (size_t)wid * a.cap;
   SD* resc = reinterpret_cast<SD*>(smem + (size_t)8 * a.cap * 8) + (size_t)wid * a.rcap;
+  FEntry* rf = reinterpret_cast<FEntry*>(resc);   // the same 16-byte slots
   if (q >= a.mq) return;
   const int kq = a.k_pq ? a.k_pq[q] : a.k;
   const int kp = max(kq + 16, a.kprime);   // the FP32 re-ranked shortlist
@@ -1765,16 +1788,21 @@ topk_kernel(TopkArgs a) {
   // is sorted, so those entries are a prefix S of it.  If the window reaches
   // the end of the pre-selection while more candidates exist, the slow path
   // re-scores every candidate in the window.
-  const double qn = (double)a.qnorm[q];
-  const double eps_s = a.gamma * qn * (double)a.xmax;
-  const double du = 5.9604644775390625e-08 * (a.d + 8);
-  const double delta = 4.0 * du * du * qn * (double)a.xmax + 1e-300;
+  // FP32 arithmetic (the FP64 pipe is slow): the 1e-5 factors cover the
+  // roundings of these products, and the threshold is lowered by one more
+  // ulp of the k-th score, so the window can only grow
+  const float qn = a.qnorm[q];
+  const float eps_s = a.gammaf * qn * a.xmax * 1.00001f;
+  const float du = 5.9604645e-08f * (float)(a.d + 8);
+  const float delta = 4.f * du * du * qn * a.xmax * 1.00001f + 1e-30f;
   const int kk = min(kq, nk);
-  const double thr64 = nk > 0 ? (double)key_score(buf[kk - 1]) - 2.0 * eps_s - 2.0 * delta : 0.0;
+  const float kth = nk > 0 ? key_score(buf[kk - 1]) : 0.f;
+  const float thr = nk > 0 ? (kth - 2.f * eps_s - 2.f * delta) - 1.2e-7f * fabsf(kth) - 1e-30f : 0.f;
+  const double thr64 = (double)thr;
   int ns = 0;   // |S|
   for (int e0 = 0; e0 < nk; e0 += 32) {
     const int e = e0 + lane;
-    ns += __popc(__ballot_sync(FULL, e < nk && (double)key_score(buf[e]) >= thr64));
+    ns += __popc(__ballot_sync(FULL, e < nk && key_score(buf[e]) >= thr));
   }
   const bool slow = U > (uint32_t)nk && ns == nk;
   const int64_t orow = q * a.kmax;
@@ -1802,16 +1830,17 @@ topk_kernel(TopkArgs a) {
         FF w{__shfl_xor_sync(FULL, v.hi, o), __shfl_xor_sync(FULL, v.lo, o)};
         v = ff_add(v, w);
       }
-      if (ok && sub == 0) resc[r] = SD{ff_value(v), id, 0};
+      if (ok && sub == 0) rf[r] = FEntry{ff_norm(v), id, 0};
     }
     const int np2 = pow2_ceil(ns > 1 ? ns : 1);
-    for (int e = ns + lane; e < np2; e += 32) resc[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+    for (int e = ns + lane; e < np2; e += 32) rf[e] = FEntry{FF{-INFINITY, 0.f}, 0xFFFFFFFFu, 0};
     __syncwarp();
-    warp_sort_sd(resc, np2);
+    warp_sort_fe(rf, np2);
+    // hi of a normalised pair is its sum rounded to FP32
     for (int e = lane; e < a.kmax; e += 32) {
       const bool ok = e < kq && e < ns;
-      a.out_ids[orow + e] = ok ? (int64_t)resc[e].id : -1;
-      a.out_scores[orow + e] = ok ? (float)resc[e].s : -INFINITY;
+      a.out_ids[orow + e] = ok ? (int64_t)rf[e].h : -1;
+      a.out_scores[orow + e] = ok ? rf[e].v.hi : -INFINITY;
     }
     return;
   }
