@@ -398,8 +398,8 @@ def main():
     launches0 = F.fpp_launch_count()
     phase = {"ms_project": 0.0, "ms_probe": 0.0, "ms_probe_exact": 0.0, "ms_gather_score": 0.0,
              "ms_dedup": 0.0, "ms_score": 0.0, "ms_topk": 0.0}
-    tot = {"entries": 0, "unique": 0, "probes": 0, "probe_rechecks": 0, "topk_rechecks": 0,
-           "batches": 0}
+    tot = {"entries": 0, "unique": 0, "probes": 0, "probe_rechecks": 0, "probe_full_rechecks": 0,
+           "topk_rechecks": 0, "batches": 0}
     # timed steps: asynchronous on one stream, no host round trip per step
     evs[0].record(stream)
     for s in range(args.steps):

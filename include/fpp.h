@@ -150,11 +150,14 @@ typedef struct fpp_search_stats {
   uint64_t topk_rechecks;     /* queries whose top-k boundary was re-decided  */
   uint64_t batches;           /* query batches the call was split into (each
                                  batch is one launch of every search kernel)  */
+  uint64_t probe_full_rechecks; /* of the probe_rechecks, those re-decided from
+                                 all 2D projections of the table (the window
+                                 passes could not settle them)                 */
   float ms_project;           /* device time per phase, milliseconds          */
   float ms_probe;             /* fast probe ranking                            */
   float ms_probe_exact;       /* exact re-decision of near-tie probe sets      */
   float ms_gather_score;      /* candidate gather, scoring and top-k, of which: */
-  float ms_dedup;             /*   bucket walk and bitmap de-duplication       */
+  float ms_dedup;             /*   bucket walk and hash-set de-duplication     */
   float ms_score;             /*   candidate scoring                            */
   float ms_topk;              /*   per-query top-k                              */
   float ms_total;

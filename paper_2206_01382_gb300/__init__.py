@@ -56,7 +56,8 @@ class fpp_search_stats(ctypes.Structure):
     _fields_ = [("queries", ctypes.c_uint64), ("probes", ctypes.c_uint64),
                 ("entries", ctypes.c_uint64), ("unique", ctypes.c_uint64),
                 ("probe_rechecks", ctypes.c_uint64), ("topk_rechecks", ctypes.c_uint64),
-                ("batches", ctypes.c_uint64), ("ms_project", ctypes.c_float), ("ms_probe", ctypes.c_float),
+                ("batches", ctypes.c_uint64), ("probe_full_rechecks", ctypes.c_uint64),
+                ("ms_project", ctypes.c_float), ("ms_probe", ctypes.c_float),
                 ("ms_probe_exact", ctypes.c_float), ("ms_gather_score", ctypes.c_float),
                 ("ms_dedup", ctypes.c_float), ("ms_score", ctypes.c_float),
                 ("ms_topk", ctypes.c_float), ("ms_total", ctypes.c_float)]

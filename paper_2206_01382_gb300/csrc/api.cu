@@ -782,6 +782,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   pa.recheck2_count = reinterpret_cast<unsigned*>(ws.stats.as<unsigned long long>() + 8) + 1;
   pa.recheck_s = EL ? nullptr : ws.recheck_s.as<float>();   // pair-window pass (stored projections)
   pa.rechecks = ws.stats.as<unsigned long long>() + 6;
+  pa.full_rechecks = ws.stats.as<unsigned long long>() + 7;
   FPP_TRY(launch_probe(pa, st, ev ? ev[4] : nullptr));
   if (pl.global_q > 0) FPP_TRY(launch_global_probes(pa, pl.global_q, st));
   if (ev) FPP_CUDA(cudaEventRecord(ev[2], st));
@@ -1055,6 +1056,7 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
     stats->topk_rechecks = hs[2];
     stats->probes = hs[3];
     stats->probe_rechecks = hs[6];
+    stats->probe_full_rechecks = hs[7];
     stats->batches = batches;
     stats->ms_project = ms[0];
     stats->ms_probe = ms[1];

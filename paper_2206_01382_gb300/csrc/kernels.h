@@ -177,6 +177,7 @@ struct ProbeArgs {
   float* recheck_s;          // [mq * nt][2] the FP32 P-th and (P+1)-th pair scores of
                              // each recheck item (stored projections), or NULL
   unsigned long long* rechecks;  // statistics counter or NULL
+  unsigned long long* full_rechecks;  // items of the full pass (statistics) or NULL
 };
 fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_begin = nullptr);
 

@@ -109,11 +109,142 @@ __device__ __forceinline__ ListEntry signed_entry(const uint64_t* keys, int a, i
   return ListEntry{-v, h};
 }
 
-// Best E entries of one list into out[0..E): register-resident sorted runs of
-// S keys per lane and E rounds of warp max.
+// Warp-wide bitonic sort, descending, of 32 S keys held S per lane; element
+// i = lane S + s is key[s], so the stages with distance below S stay inside a
+// lane and the others exchange whole registers between lanes.
+template <int S>
+__device__ __forceinline__ void warp_bitonic_desc(uint64_t (&key)[S]) {
+  const int lane = threadIdx.x & 31;
+  constexpr int N = 32 * S;
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= S) {
+        const int lj = j / S;   // the partner lane is lane ^ lj
+        const bool lower = (lane & lj) == 0;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const bool desc = ((lane * S + s) & k) == 0;
+          const uint64_t other = __shfl_xor_sync(FULL, key[s], lj);
+          // the lower index of a descending run keeps the larger key
+          key[s] = (lower == desc) ? (key[s] > other ? key[s] : other)
+                                   : (key[s] < other ? key[s] : other);
+        }
+      } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const int t = s ^ j;
+          if (t > s) {
+            const bool desc = ((lane * S + s) & k) == 0;
+            const uint64_t x = key[s], y = key[t];
+            const bool sw = desc ? (x < y) : (x > y);
+            key[s] = sw ? y : x;
+            key[t] = sw ? x : y;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Best E entries of one list into out[0..E) (out holds LIST_CAP >= 64
+// keys).  Lists of up to 128 entries: one warp-wide sort when E > 32, else
+// register-resident sorted runs of S keys per lane and E rounds of warp max.
+// Longer lists (S >= 16) keep only 32-bit magnitudes in registers: a binary
+// search finds a threshold that admits between E and E + 16 of them, those
+// are compacted and sorted; heavy ties at the threshold fall back to E rounds
+// of warp max over the untaken entries.
 template <int S>
 __device__ __forceinline__ void list_top(const float* __restrict__ pr, int D, int E, uint64_t* out) {
   const int lane = threadIdx.x & 31;
+  if (S >= 16) {
+    uint32_t v[S];   // bits(|p|) + 1; 0: no entry
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const int i = s * 32 + lane;
+      v[s] = i < D ? (__float_as_uint(pr[i]) & 0x7FFFFFFFu) + 1u : 0u;
+    }
+    uint32_t vmin = 0xFFFFFFFFu, vmax = 0u;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      if (v[s]) vmin = min(vmin, v[s]);
+      vmax = max(vmax, v[s]);
+    }
+    uint32_t lo = __reduce_min_sync(FULL, vmin), hi = __reduce_max_sync(FULL, vmax);
+    // count(v >= lo) >= E holds throughout (E <= D entries exist)
+    while (lo < hi) {
+      const uint32_t mid = lo + (hi - lo + 1u) / 2u;
+      unsigned c = 0;
+#pragma unroll
+      for (int s = 0; s < S; ++s) c += v[s] >= mid ? 1u : 0u;
+      c = __reduce_add_sync(FULL, c);
+      if (c >= (unsigned)E) {
+        lo = mid;
+        if (c <= (unsigned)E + 16u) break;
+      } else {
+        hi = mid - 1u;
+      }
+    }
+    unsigned c = 0;
+#pragma unroll
+    for (int s = 0; s < S; ++s) c += v[s] >= lo ? 1u : 0u;
+    const unsigned total = __reduce_add_sync(FULL, c);
+    if (total <= 64u) {
+      unsigned n = 0;
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const bool take = v[s] >= lo;
+        const unsigned m = __ballot_sync(FULL, take);
+        if (take) {
+          const int i = s * 32 + lane;
+          out[n + __popc(m & ((1u << lane) - 1u))] = list_key(pr[i], (uint32_t)i, (uint32_t)D);
+        }
+        n += __popc(m);
+      }
+      const int np2 = pow2_ceil(total > 1u ? (int)total : 1);
+      for (int e = (int)total + lane; e < np2; e += 32) out[e] = 0ull;
+      __syncwarp();
+      warp_sort_desc(out, np2);
+      return;
+    }
+    // heavy ties: E rounds, each taking the best untaken entry
+    uint32_t taken = 0u;
+    for (int r = 0; r < E; ++r) {
+      uint64_t best = 0ull;
+      int bs = -1;
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const int i = s * 32 + lane;
+        if (!((taken >> s) & 1u) && v[s]) {
+          const uint32_t h = (uint32_t)i + (pr[i] < 0.f ? (uint32_t)D : 0u);
+          const uint64_t key = ((uint64_t)v[s] << 32) | (uint64_t)(0xFFFFFFFFu - h);
+          if (key > best) { best = key; bs = s; }
+        }
+      }
+      const uint32_t bh = (uint32_t)(best >> 32), bl = (uint32_t)best;
+      const uint32_t mh = __reduce_max_sync(FULL, bh);
+      const uint32_t ml = __reduce_max_sync(FULL, bh == mh ? bl : 0u);
+      if (bs >= 0 && bh == mh && bl == ml) taken |= 1u << bs;
+      if (lane == 0) out[r] = ((uint64_t)mh << 32) | ml;
+    }
+    __syncwarp();
+    return;
+  }
+  if (S <= 4 && E > 32) {
+    uint64_t key[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const int i = lane * S + s;
+      key[s] = i < D ? list_key(pr[i], (uint32_t)i, (uint32_t)D) : 0ull;
+    }
+    warp_bitonic_desc<S>(key);
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      if (lane * S + s < E) out[lane * S + s] = key[s];
+    __syncwarp();
+    return;
+  }
   uint64_t key[S];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
@@ -315,25 +446,6 @@ probe_small_kernel(ProbeArgs a) {
 
 constexpr int SLOW_PAIRS = 1024;
 
-struct DEntry {
-  double v;
-  uint32_t h;
-  uint32_t pad;
-};
-
-__device__ __forceinline__ bool dentry_before(double v1, uint32_t h1, double v2, uint32_t h2) {
-  return v1 > v2 || (v1 == v2 && h1 < h2);
-}
-
-__device__ __forceinline__ void warp_best(double& v, uint32_t& h) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double v2 = __shfl_xor_sync(FULL, v, o);
-    const uint32_t h2 = __shfl_xor_sync(FULL, h, o);
-    if (dentry_before(v2, h2, v, h)) { v = v2; h = h2; }
-  }
-}
-
 // Entries with float-float values (normalised pairs; see ff_before).
 struct FEntry {
   FF v;
@@ -372,6 +484,26 @@ __device__ __forceinline__ void warp_sort_fe(FEntry* a, int N) {
   }
 }
 
+// Bitonic sort of N (a power of two) entries by ff_before, the whole CTA.
+__device__ __forceinline__ void block_sort_fe(FEntry* a, int N) {
+  for (int k = 2; k <= N; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const FEntry x = a[i], y = a[l];
+          const bool first = (i & k) == 0;
+          if (first ? ff_before(y.v, y.h, x.v, x.h) : ff_before(x.v, x.h, y.v, y.h)) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Re-decides the probe set of one (query, table) from compensated
 // projections dv[2D] (FP64-accurate float-float pairs), with the same ranking
 // rule: the whole
@@ -379,25 +511,26 @@ __device__ __forceinline__ void warp_sort_fe(FEntry* a, int N) {
 // the best E = min(P, 2D) entries of each list with (a+1)(b+1) <= P, and
 // sorts them (score desc, bucket asc).  wsm holds 2 lists of pow2(2D) and
 // the pairs, pow2(pair_count) entries.
-__device__ void probe_exact_select(const FF* dv, int D, int P, SD* lists, SD* pairs,
+__device__ void probe_exact_select(const FF* dv, int D, int P, FEntry* lists, FEntry* pairs,
                                    uint32_t* bucket_out) {
   const int W2 = 2 * D;
   const int NL = pow2_ceil(W2);
   const int E = P < W2 ? P : W2;
+  const FEntry none{FF{-INFINITY, 0.f}, 0xFFFFFFFFu, 0};
   for (int j = 0; j < 2; ++j) {
-    SD* L = lists + j * NL;
+    FEntry* L = lists + j * NL;
     for (int h = threadIdx.x; h < NL; h += blockDim.x) {
       if (h < W2) {
-        const double v = h < D ? ff_value(dv[j * D + h]) : -ff_value(dv[j * D + h - D]);
-        L[h] = SD{v, (uint32_t)h, 0};
+        const FF x = dv[j * D + (h < D ? h : h - D)];
+        L[h] = FEntry{h < D ? x : FF{-x.hi, -x.lo}, (uint32_t)h, 0};
       } else {
-        L[h] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+        L[h] = none;
       }
     }
   }
   __syncthreads();
-  block_sort_sd(lists, NL);
-  block_sort_sd(lists + NL, NL);
+  block_sort_fe(lists, NL);
+  block_sort_fe(lists + NL, NL);
   // pairs (a, b) with (a+1)(b+1) <= P: row a holds min(P / (a+1), E) of them
   int C = 0;
   for (int ai = 0; ai < E; ++ai) C += min(P / (ai + 1), E);
@@ -407,15 +540,15 @@ __device__ void probe_exact_select(const FF* dv, int D, int P, SD* lists, SD* pa
       int ai = 0, base = 0;
       while (base + min(P / (ai + 1), E) <= idx) { base += min(P / (ai + 1), E); ++ai; }
       const int bi = idx - base;
-      const SD x = lists[ai], y = lists[NL + bi];
-      pairs[idx] = SD{x.s + y.s, x.id * (uint32_t)W2 + y.id, 0};
+      const FEntry x = lists[ai], y = lists[NL + bi];
+      pairs[idx] = FEntry{ff_sum(x.v, y.v), x.h * (uint32_t)W2 + y.h, 0};
     } else {
-      pairs[idx] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+      pairs[idx] = none;
     }
   }
   __syncthreads();
-  block_sort_sd(pairs, NC);
-  for (int r = threadIdx.x; r < P; r += blockDim.x) bucket_out[r] = pairs[r].id;
+  block_sort_fe(pairs, NC);
+  for (int r = threadIdx.x; r < P; r += blockDim.x) bucket_out[r] = pairs[r].h;
   __syncthreads();
 }
 
@@ -479,15 +612,15 @@ __device__ void probe_exact_select_warp(const FF* dv, int D, int P, unsigned cha
   __syncwarp();
 }
 
-constexpr int RECHECK_THREADS = 256;
+constexpr int RECHECK_THREADS = 1024;   // 32 warps: eight rows each in flight, 256 rows per pass
 
-// dv [2D] doubles, two sorted signed lists of pow2(2D) entries, and the
+// dv [2D] float-float pairs, two sorted signed lists of pow2(2D) entries, and the
 // candidate pairs (at most P (1 + ln P) <= 1024 for P <= 128 ... bounded by
 // pair_count(P, ...) <= SLOW_PAIRS)
 __host__ __device__ inline size_t recheck_smem_bytes(int D) {
-  const size_t lists = (size_t)2 * pow2_ceil(2 * D) * sizeof(SD);
-  const size_t wtop = (size_t)2 * LIST_CAP * sizeof(DEntry);   // the one-warp selection
-  return (size_t)8 * 2 * D + (lists > wtop ? lists : wtop) + (size_t)SLOW_PAIRS * sizeof(SD);
+  const size_t lists = (size_t)2 * pow2_ceil(2 * D) * sizeof(FEntry);
+  const size_t wtop = (size_t)2 * LIST_CAP * sizeof(FEntry);   // the one-warp selection
+  return (size_t)8 * 2 * D + (lists > wtop ? lists : wtop) + (size_t)SLOW_PAIRS * sizeof(FEntry);
 }
 
 // One CTA per (query, table) item of the recheck list: its warps compute the
@@ -501,6 +634,8 @@ probe_recheck_kernel(ProbeArgs a) {
   unsigned char* wsm = smem + (size_t)8 * 2 * a.D;
   const bool after_window = a.lists || a.recheck_s;
   const unsigned cnt = after_window ? *a.recheck2_count : *a.recheck_count;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && a.full_rechecks && cnt)
+    atomicAdd(a.full_rechecks, (unsigned long long)cnt);
   const uint32_t* items = after_window ? a.recheck2 : a.recheck;
   const int rows = 2 * a.D;
   const int nf4 = (int)(a.ldr / 4);
@@ -534,7 +669,7 @@ probe_recheck_kernel(ProbeArgs a) {
       if (wid == 0) probe_exact_select_warp(dv, a.D, P, wsm, dst);
       __syncthreads();
     } else {
-      SD* lists = reinterpret_cast<SD*>(wsm);
+      FEntry* lists = reinterpret_cast<FEntry*>(wsm);
       probe_exact_select(dv, a.D, P, lists, lists + 2 * pow2_ceil(2 * a.D), dst);
     }
   }
@@ -668,10 +803,10 @@ constexpr int PW_WIN = 64;
 struct PWinShared {
   uint32_t ch[2][PW_CAND];
   float cv[2][PW_CAND];
-  double ev[2][PW_CAND];
+  FF ev[2][PW_CAND];           // signed exact values (normalised float-float)
   uint32_t need[2];            // bit c: candidate c is in a window pair
   uint16_t wa[PW_WIN], wb[PW_WIN];
-  SD ws[PW_WIN];
+  FEntry ws[PW_WIN];
   unsigned nwin, nin;
 };
 
@@ -771,12 +906,13 @@ probe_pwin_kernel(ProbeArgs a) {
           rows[u] = a.R + ((int64_t)(2 * t + j) * D + (sh.ch[j][c] % (uint32_t)D)) * a.ldr;
         }
         if (!(need >> c0 & 0xFFu)) continue;
-        double v[8];
-        warp_dot2_gather<8>(qv, rows, nf4, v);
+        FF v[8];
+        warp_dot2_gather_ff<8>(qv, rows, nf4, v);
         if (lane == 0)
 #pragma unroll
           for (int u = 0; u < 8; ++u)
-            if (c0 + u < nc[j]) sh.ev[j][c0 + u] = sh.ch[j][c0 + u] < (uint32_t)D ? v[u] : -v[u];
+            if (c0 + u < nc[j])
+              sh.ev[j][c0 + u] = sh.ch[j][c0 + u] < (uint32_t)D ? v[u] : FF{-v[u].hi, -v[u].lo};
       }
     }
     __syncwarp();
@@ -785,13 +921,14 @@ probe_pwin_kernel(ProbeArgs a) {
     for (int w = lane; w < NW; w += 32) {
       if (w < (int)nwin) {
         const int x = sh.wa[w], y = sh.wb[w];
-        sh.ws[w] = SD{sh.ev[0][x] + sh.ev[1][y], sh.ch[0][x] * (uint32_t)(2 * D) + sh.ch[1][y], 0};
+        sh.ws[w] = FEntry{ff_sum(sh.ev[0][x], sh.ev[1][y]),
+                          sh.ch[0][x] * (uint32_t)(2 * D) + sh.ch[1][y], 0};
       } else {
-        sh.ws[w] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+        sh.ws[w] = FEntry{FF{-INFINITY, 0.f}, 0xFFFFFFFFu, 0};
       }
     }
     __syncwarp();
-    warp_sort_sd(sh.ws, NW);
+    warp_sort_fe(sh.ws, NW);
     // output: the certain pairs, then the best P - nin window pairs
     uint32_t* dst = a.out + (q * a.nt + tl) * (int64_t)a.probes;
     if (lane == 0) sh.nin = 0;
@@ -805,7 +942,7 @@ probe_pwin_kernel(ProbeArgs a) {
         }
     }
     __syncwarp();
-    for (int w = lane; w < P - (int)nin; w += 32) dst[nin + w] = sh.ws[w].id;
+    for (int w = lane; w < P - (int)nin; w += 32) dst[nin + w] = sh.ws[w].h;
     __syncwarp();
   }
 }
@@ -2130,7 +2267,7 @@ fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_b
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  probe_recheck_kernel<<<sms * 4, RECHECK_THREADS, smem, st>>>(a);
+  probe_recheck_kernel<<<sms, RECHECK_THREADS, smem, st>>>(a);
   FPP_LAUNCHED();
   return FPP_OK;
 }
