@@ -773,6 +773,10 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   pa.trunc = EL ? tc_list_trunc(ix->D) : 0.f;
   pa.Q = ws.qpad.as<float>(); pa.ldq = ix->dpad; pa.qnorm = ws.qnorm.as<float>();
   pa.R = ix->R; pa.ldr = ix->dpad; pa.d = ix->d; pa.D = ix->D; pa.tb = pl.tb; pa.nt = nt;
+  if (ix->bpieces == 1) {   // R on the BF16 grid: its first BF16 piece is R itself
+    pa.Rb = static_cast<const uint16_t*>(ix->Rs);
+    pa.ldrb = (int64_t)ix->pieces * ix->Kp;
+  }
   pa.rmax = ix->rmax; pa.gamma = ix->gamma; pa.gammaf = (float)(ix->gamma * 1.0001);
   pa.probes_pq = ppq; pa.probes = pl.pmax;
   pa.out = ws.probes.as<uint32_t>();
@@ -889,7 +893,7 @@ fpp_status prepare_workspace(fpp_index* ix, Workspace& ws, const SearchPlan& pl,
   FPP_TRY(ws.qnorm.ensure((size_t)mc * 4, false, st));
   FPP_TRY(ws.recheck.ensure((size_t)mc * nt * 4, false, st));
   FPP_TRY(ws.recheck2.ensure((size_t)mc * nt * 4, false, st));
-  FPP_TRY(ws.recheck_s.ensure((size_t)mc * nt * 8, false, st));
+  FPP_TRY(ws.recheck_s.ensure((size_t)mc * nt * 16, false, st));   // sP, sP1, two list maxima
   if (pl.sim_keep > 0) {
     FPP_TRY(ws.sigproj.ensure((size_t)mc * ix->sig_words * 32 * 4, false, st));
     FPP_TRY(ws.qsig.ensure((size_t)mc * ix->sig_words * 4, false, st));

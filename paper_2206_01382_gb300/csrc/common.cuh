@@ -225,6 +225,60 @@ __device__ __forceinline__ void warp_dot2_gather_ff(const float* __restrict__ q,
   }
 }
 
+// Same, for rows stored as BF16 bit patterns (uint16, a BF16 value is exact
+// in FP32: its bits shifted up by 16).  q has dq floats (a multiple of 4);
+// each row holds at least round_up(dq, 8) values, zero past the vector, and
+// is 16-byte aligned.  Lanes read 8-value chunks; a last 4-value chunk is
+// taken by lane 0.
+__device__ __forceinline__ void dot2_bf2(float a0, float a1, uint32_t w, float& p, float& s) {
+  dot2_step(a0, __uint_as_float(w << 16), p, s);
+  dot2_step(a1, __uint_as_float(w & 0xFFFF0000u), p, s);
+}
+
+template <int NR>
+__device__ __forceinline__ void warp_dot2_gather_bf_ff(const float* __restrict__ q,
+                                                       const uint16_t* const* rows, int dq,
+                                                       FF* out) {
+  const int lane = threadIdx.x & 31;
+  float p[NR], s[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) { p[k] = 0.f; s[k] = 0.f; }
+  const float4* q4 = reinterpret_cast<const float4*>(q);
+  const int n8 = dq >> 3;
+  for (int c = lane; c < n8; c += 32) {
+    const float4 a0 = q4[2 * c], a1 = q4[2 * c + 1];
+    uint4 b[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) b[k] = __ldg(reinterpret_cast<const uint4*>(rows[k]) + c);
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      dot2_bf2(a0.x, a0.y, b[k].x, p[k], s[k]);
+      dot2_bf2(a0.z, a0.w, b[k].y, p[k], s[k]);
+      dot2_bf2(a1.x, a1.y, b[k].z, p[k], s[k]);
+      dot2_bf2(a1.z, a1.w, b[k].w, p[k], s[k]);
+    }
+  }
+  if ((dq & 4) && lane == 0) {
+    const float4 a0 = q4[2 * n8];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      const uint2 b = __ldg(reinterpret_cast<const uint2*>(rows[k] + 8 * n8));
+      dot2_bf2(a0.x, a0.y, b.x, p[k], s[k]);
+      dot2_bf2(a0.z, a0.w, b.y, p[k], s[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    FF v{p[k], s[k]};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      FF w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+      v = ff_add(v, w);
+    }
+    out[k] = ff_norm(v);
+  }
+}
+
 template <int NR>
 __device__ __forceinline__ void warp_dot2_gather(const float* __restrict__ q,
                                                  const float* const* rows, int nf4, double* out) {

@@ -163,6 +163,8 @@ struct ProbeArgs {
   const float* qnorm;        // [mq] upper bounds of the query norms
   const float* R;            // [2 L D][ldr]
   int64_t ldr;
+  const uint16_t* Rb;        // R as BF16 bits, row stride ldrb (R on the BF16 grid), or NULL
+  int64_t ldrb;
   int d, D, tb, nt;
   const float* rmax;         // [2L]
   double gamma;
@@ -174,8 +176,9 @@ struct ProbeArgs {
   unsigned* recheck_count;   // device counter of recheck items
   uint32_t* recheck2;        // [mq * nt] items the window pass could not settle
   unsigned* recheck2_count;
-  float* recheck_s;          // [mq * nt][2] the FP32 P-th and (P+1)-th pair scores of
-                             // each recheck item (stored projections), or NULL
+  float* recheck_s;          // [mq * nt][4] the FP32 P-th and (P+1)-th pair scores of each
+                             // recheck item and its two hashes' largest abs(p) (stored
+                             // projections; 16-byte aligned), or NULL
   unsigned long long* rechecks;  // statistics counter or NULL
   unsigned long long* full_rechecks;  // items of the full pass (statistics) or NULL
 };

@@ -352,8 +352,11 @@ probe_kernel(ProbeArgs a, int pmax) {
     a.recheck[slot] = (uint32_t)(q * a.nt + tl);
     if (a.recheck_s) {   // the boundary the window pass re-decides (NaN: none)
       const bool have = boundary && C >= Tsel;
-      a.recheck_s[2 * slot] = have ? key_score(pout[P - 1]) : __int_as_float(0x7fc00000);
-      a.recheck_s[2 * slot + 1] = have ? key_score(pout[P]) : __int_as_float(0x7fc00000);
+      a.recheck_s[4 * slot] = have ? key_score(pout[P - 1]) : __int_as_float(0x7fc00000);
+      a.recheck_s[4 * slot + 1] = have ? key_score(pout[P]) : __int_as_float(0x7fc00000);
+      // each hash's largest abs(p) (its first list entry)
+      a.recheck_s[4 * slot + 2] = signed_entry(lists, 0, D).v;
+      a.recheck_s[4 * slot + 3] = signed_entry(lists + LIST_CAP, 0, D).v;
     }
     if (a.rechecks) atomicAdd(a.rechecks, 1ull);
   }
@@ -612,7 +615,31 @@ __device__ void probe_exact_select_warp(const FF* dv, int D, int P, unsigned cha
   __syncwarp();
 }
 
-constexpr int RECHECK_THREADS = 1024;   // 32 warps: eight rows each in flight, 256 rows per pass
+// Compensated projections of query q on NR rows of R given by their global
+// row index (2t + j) D + i; from the BF16 copy when R is on the BF16 grid
+// (the same values in half the bytes).
+template <int NR, bool RB>
+__device__ __forceinline__ void proj_rows_ff(const ProbeArgs& a, const float* qv,
+                                             const int64_t (&row)[NR], FF* out) {
+  if (RB) {
+    const uint16_t* rp[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) rp[k] = a.Rb + row[k] * a.ldrb;
+    warp_dot2_gather_bf_ff<NR>(qv, rp, (int)a.ldq, out);
+  } else {
+    const float* rp[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) rp[k] = a.R + row[k] * a.ldr;
+    warp_dot2_gather_ff<NR>(qv, rp, (int)(a.ldr / 4), out);
+  }
+}
+
+// The full pass runs 1,024 threads per CTA (eight rows in flight per warp,
+// 256 rows per pass) when the budget is small (P <= 16: one warp selects, the
+// rows dominate an item's time); larger budgets spend most of an item in the
+// CTA-wide sorts, which use 256 threads better, with four CTAs per SM.
+constexpr int RECHECK_THREADS = 1024;
+constexpr int RECHECK_THREADS_LARGE_P = 256;
 
 // dv [2D] float-float pairs, two sorted signed lists of pow2(2D) entries, and the
 // candidate pairs (at most P (1 + ln P) <= 1024 for P <= 128 ... bounded by
@@ -626,10 +653,11 @@ __host__ __device__ inline size_t recheck_smem_bytes(int D) {
 // One CTA per (query, table) item of the recheck list: its warps compute the
 // 2D compensated projections (eight rows in flight per warp, coalesced
 // float4 loads), then warp 0 re-decides the probe set.
-__global__ void __launch_bounds__(RECHECK_THREADS)
+template <bool RB, int NT>
+__global__ void __launch_bounds__(NT)
 probe_recheck_kernel(ProbeArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = RECHECK_THREADS / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = NT / 32;
   FF* dv = reinterpret_cast<FF*>(smem);
   unsigned char* wsm = smem + (size_t)8 * 2 * a.D;
   const bool after_window = a.lists || a.recheck_s;
@@ -638,7 +666,6 @@ probe_recheck_kernel(ProbeArgs a) {
     atomicAdd(a.full_rechecks, (unsigned long long)cnt);
   const uint32_t* items = after_window ? a.recheck2 : a.recheck;
   const int rows = 2 * a.D;
-  const int nf4 = (int)(a.ldr / 4);
   for (unsigned it = blockIdx.x; it < cnt; it += gridDim.x) {
     const uint32_t item = items[it];
     const int64_t q = item / a.nt;
@@ -646,11 +673,14 @@ probe_recheck_kernel(ProbeArgs a) {
     const int t = a.tb + tl;
     const int P = a.probes_pq ? a.probes_pq[q] : a.probes;
     const float* qv = a.Q + q * a.ldq;
-    const float* Rt = a.R + (int64_t)2 * t * a.D * a.ldr;
+    const int64_t r0 = (int64_t)2 * t * a.D;   // first row of the table
     for (int i0 = wid * 8; i0 < rows; i0 += nw * 8) {
       if (i0 + 8 <= rows) {
         FF v[8];
-        warp_dot2_rows_ff<8>(qv, Rt + (int64_t)i0 * a.ldr, a.ldr, nf4, v);
+        int64_t row[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) row[k] = r0 + i0 + k;
+        proj_rows_ff<8, RB>(a, qv, row, v);
         if (lane == 0) {
 #pragma unroll
           for (int k = 0; k < 8; ++k) dv[i0 + k] = v[k];
@@ -658,7 +688,8 @@ probe_recheck_kernel(ProbeArgs a) {
       } else {
         for (int i = i0; i < rows; ++i) {
           FF v[1];
-          warp_dot2_rows_ff<1>(qv, Rt + (int64_t)i * a.ldr, a.ldr, nf4, v);
+          const int64_t row[1] = {r0 + i};
+          proj_rows_ff<1, RB>(a, qv, row, v);
           if (lane == 0) dv[i] = v[0];
         }
       }
@@ -691,6 +722,7 @@ struct WinShared {
   uint32_t w[2][WIN_MAX]; // their signed wedges
 };
 
+template <bool RB>
 __global__ void __launch_bounds__(256)
 probe_window_kernel(ProbeArgs a) {
   __shared__ WinShared shm[8];
@@ -698,7 +730,6 @@ probe_window_kernel(ProbeArgs a) {
   WinShared& sh = shm[threadIdx.x >> 5];
   const unsigned cnt = *a.recheck_count;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
-  const int nf4 = (int)(a.ldr / 4);
   // lane 16 j + e holds list entry e of hash j (e <= EL <= 8)
   const int j = lane >> 4, e = lane & 15;
   for (unsigned it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < cnt; it += nwarps) {
@@ -737,16 +768,16 @@ probe_window_kernel(ProbeArgs a) {
     FF ev{0.f, 0.f};
     const float* qv = a.Q + q * a.ldq;
     for (int g = 0; g < nc; g += 4) {
-      const float* rows[4];
+      int64_t rows[4];
       int src[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         src[k] = __fns(mask, 0, 1 + min(g + k, nc - 1));   // lane of candidate g + k
         const uint32_t hk = __shfl_sync(FULL, h, src[k]) % (uint32_t)D;
-        rows[k] = a.R + ((int64_t)(2 * t + (src[k] >> 4)) * D + hk) * a.ldr;
+        rows[k] = (int64_t)(2 * t + (src[k] >> 4)) * D + hk;
       }
       FF out[4];
-      warp_dot2_gather_ff<4>(qv, rows, nf4, out);
+      proj_rows_ff<4, RB>(a, qv, rows, out);
 #pragma unroll
       for (int k = 0; k < 4; ++k)
         if (g + k < nc && lane == src[k]) ev = out[k];
@@ -810,6 +841,7 @@ struct PWinShared {
   unsigned nwin, nin;
 };
 
+template <bool RB>
 __global__ void __launch_bounds__(256)
 probe_pwin_kernel(ProbeArgs a) {
   __shared__ PWinShared shm[8];
@@ -817,7 +849,6 @@ probe_pwin_kernel(ProbeArgs a) {
   PWinShared& sh = shm[wid];
   const unsigned cnt = *a.recheck_count;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
-  const int nf4 = (int)(a.ldr / 4);
   for (unsigned it = blockIdx.x * (blockDim.x >> 5) + wid; it < cnt; it += nwarps) {
     const uint32_t item = a.recheck[it];
     const int64_t q = item / a.nt;
@@ -825,46 +856,54 @@ probe_pwin_kernel(ProbeArgs a) {
     const int t = a.tb + tl;
     const int P = a.probes_pq ? a.probes_pq[q] : a.probes;
     const int D = a.D;
-    const float sP = a.recheck_s[2 * it], sP1 = a.recheck_s[2 * it + 1];
+    const float4 rs = reinterpret_cast<const float4*>(a.recheck_s)[it];
+    const float sP = rs.x, sP1 = rs.y;
     auto give_up = [&]() {
       if (lane == 0) a.recheck2[atomicAdd(a.recheck2_count, 1u)] = item;
     };
     if (isnan(sP) || isnan(sP1)) { give_up(); continue; }
     const float* pr[2] = {a.P + q * a.ldp + (int64_t)(2 * tl) * D,
                           a.P + q * a.ldp + (int64_t)(2 * tl + 1) * D};
-    float vmax[2];
-    for (int j = 0; j < 2; ++j) {
-      float m = 0.f;
-      for (int i = lane; i < D; i += 32) m = fmaxf(m, fabsf(pr[j][i]));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, o));
-      vmax[j] = m;
-    }
+    const float vmax[2] = {rs.z, rs.w};   // each hash's largest abs(p), from the fast pass
     // per-pair bound: the projections' error plus the rounding of the FP32
     // sum (every pair score is at most vmax[0] + vmax[1] in magnitude)
     const float eps = a.gammaf * a.qnorm[q] * (a.rmax[2 * t] + a.rmax[2 * t + 1]);
     const float delta = (eps + 6.0e-8f * (vmax[0] + vmax[1] + fabsf(sP) + fabsf(sP1))) * 1.001f + 1e-30f;
     const float tau = sP - 2.f * delta, hi = sP1 + 2.f * delta;
-    // candidate entries (signed wedges h in [0, 2D)) of each list
+    // candidate entries (signed wedges h in [0, 2D)) of each list: every
+    // value p_i gives the wedges i (value p_i) and i + D (value -p_i); the
+    // values are read eight per lane at a time
     int nc[2] = {0, 0};
     bool over = false;
+    const unsigned lt = (1u << lane) - 1u;
     for (int j = 0; j < 2 && !over; ++j) {
       const float lim = (tau - vmax[1 - j]) - 1e-6f * (fabsf(tau) + vmax[1 - j]);
-      for (int h0 = 0; h0 < 2 * D; h0 += 32) {
-        const int h = h0 + lane;
-        float v = 0.f;
-        bool in = false;
-        if (h < 2 * D) {
-          const float p = pr[j][h < D ? h : h - D];
-          v = h < D ? p : -p;
-          in = v >= lim;
+      for (int i0 = 0; i0 < D; i0 += 256) {
+        float pv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u * 32 + lane;
+          pv[u] = i < D ? pr[j][i] : 0.f;
         }
-        const unsigned m = __ballot_sync(FULL, in);
-        if (in) {
-          const int slot = nc[j] + __popc(m & ((1u << lane) - 1u));
-          if (slot < PW_CAND) { sh.ch[j][slot] = (uint32_t)h; sh.cv[j][slot] = v; }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u * 32 + lane;
+          const bool ok = i < D;
+#pragma unroll
+          for (int sg = 0; sg < 2; ++sg) {
+            const float v = sg ? -pv[u] : pv[u];
+            const bool in = ok && v >= lim;
+            const unsigned m = __ballot_sync(FULL, in);
+            if (in) {
+              const int slot = nc[j] + __popc(m & lt);
+              if (slot < PW_CAND) {
+                sh.ch[j][slot] = (uint32_t)(i + (sg ? D : 0));
+                sh.cv[j][slot] = v;
+              }
+            }
+            nc[j] += __popc(m);
+          }
         }
-        nc[j] += __popc(m);
       }
       if (nc[j] > PW_CAND) over = true;
     }
@@ -899,15 +938,15 @@ probe_pwin_kernel(ProbeArgs a) {
     for (int j = 0; j < 2; ++j) {
       const unsigned need = sh.need[j];
       for (int c0 = 0; c0 < nc[j]; c0 += 8) {
-        const float* rows[8];
+        int64_t rows[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int c = min(c0 + u, nc[j] - 1);
-          rows[u] = a.R + ((int64_t)(2 * t + j) * D + (sh.ch[j][c] % (uint32_t)D)) * a.ldr;
+          rows[u] = (int64_t)(2 * t + j) * D + (sh.ch[j][c] % (uint32_t)D);
         }
         if (!(need >> c0 & 0xFFu)) continue;
         FF v[8];
-        warp_dot2_gather_ff<8>(qv, rows, nf4, v);
+        proj_rows_ff<8, RB>(a, qv, rows, v);
         if (lane == 0)
 #pragma unroll
           for (int u = 0; u < 8; ++u)
@@ -2253,21 +2292,36 @@ fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_b
   cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, dev0);
   if (a.lists) {
     // up to 64 resident warps per SM, one item each
-    probe_window_kernel<<<sms0 * 8, 256, 0, st>>>(a);
+    if (a.Rb) probe_window_kernel<true><<<sms0 * 8, 256, 0, st>>>(a);
+    else probe_window_kernel<false><<<sms0 * 8, 256, 0, st>>>(a);
     FPP_LAUNCHED();
   } else if (a.recheck_s) {
-    probe_pwin_kernel<<<sms0 * 2, 256, 0, st>>>(a);
+    // 80 registers with BF16 rows: three CTAs per SM
+    if (a.Rb) probe_pwin_kernel<true><<<sms0 * 3, 256, 0, st>>>(a);
+    else probe_pwin_kernel<false><<<sms0 * 2, 256, 0, st>>>(a);
     FPP_LAUNCHED();
   }
   // exact pass over the items the fast pass could not decide; the grid is
   // fixed and the kernel reads the item count on the device
   const size_t smem = recheck_smem_bytes(a.D);
-  FPP_CUDA(cudaFuncSetAttribute(probe_recheck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  const bool small_p = a.probes <= 16;
+  const void* fn = small_p ? (a.Rb ? (const void*)probe_recheck_kernel<true, RECHECK_THREADS>
+                                   : (const void*)probe_recheck_kernel<false, RECHECK_THREADS>)
+                           : (a.Rb ? (const void*)probe_recheck_kernel<true, RECHECK_THREADS_LARGE_P>
+                                   : (const void*)probe_recheck_kernel<false, RECHECK_THREADS_LARGE_P>);
+  FPP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  probe_recheck_kernel<<<sms, RECHECK_THREADS, smem, st>>>(a);
+  if (small_p) {
+    if (a.Rb) probe_recheck_kernel<true, RECHECK_THREADS><<<sms, RECHECK_THREADS, smem, st>>>(a);
+    else probe_recheck_kernel<false, RECHECK_THREADS><<<sms, RECHECK_THREADS, smem, st>>>(a);
+  } else {
+    if (a.Rb)
+      probe_recheck_kernel<true, RECHECK_THREADS_LARGE_P><<<sms * 4, RECHECK_THREADS_LARGE_P, smem, st>>>(a);
+    else
+      probe_recheck_kernel<false, RECHECK_THREADS_LARGE_P><<<sms * 4, RECHECK_THREADS_LARGE_P, smem, st>>>(a);
+  }
   FPP_LAUNCHED();
   return FPP_OK;
 }

@@ -27,9 +27,9 @@ def F():
     return F
 
 
-def _full_parity(F, X, Q, L, D, alpha, seed, k, probes_list, min_compared=0.9):
-    ix_o = O.build_index(X, L, D, alpha, seed=seed)
-    ix_g = F.Index(X, L, D, alpha, seed=seed)
+def _full_parity(F, X, Q, L, D, alpha, seed, k, probes_list, min_compared=0.9, R=None):
+    ix_o = O.build_index(X, L, D, alpha, seed=seed, R=R)
+    ix_g = F.Index(X, L, D, alpha, seed=seed, R=R)
     excl = {}
     for t in range(L):
         gpb = F.fpp_debug_point_buckets(ix_g.handle, t)
@@ -67,6 +67,16 @@ def test_list_epilogue_full_parity(F, D):
     # keys without the sign until the end); P = 1, 3, 7 give lists of 2, 4, 8
     X, Q = W.small_mixture(30000, 60, 64, 64, 0.25, 90 + D)
     _full_parity(F, X, Q, L=3, D=D, alpha=0.5, seed=7 + D, k=10, probes_list=(1, 3, 7))
+
+
+def test_fp32_random_vectors_full_parity(F):
+    # random vectors off the BF16 grid: six-product projections, and the exact
+    # passes read the FP32 rows of R (the seeded vectors use their BF16 copy)
+    w = W.WORKLOADS["tiny"]
+    X, Q = W.dataset(w)
+    R = np.random.default_rng(17).standard_normal((w.L, 2, w.D, w.d)).astype(np.float32)
+    ix_o, ix_g = _full_parity(F, X, Q, w.L, w.D, w.alpha, 0, w.k, (1, 4, 16), R=R)
+    assert ix_g.info()["r_pieces"] == 3
 
 
 def test_queries_without_candidates_after_a_full_search(F):
