@@ -47,9 +47,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="plain1m", choices=sorted(W.WORKLOADS))
     ap.add_argument("--probes", type=int, default=0, help="force a probe budget")
-    ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="fp32",
+    ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default=None,
                     help="fp32: exact decisions; bf16 / fp8: candidate rows in BF16 / FP8 e4m3 "
-                         "with an exactly re-scored shortlist")
+                         "with an exactly re-scored shortlist (default: the workload's stored "
+                         "precision, bf16 for precision1m and serve2m)")
     ap.add_argument("--rerank-k", type=int, default=100)
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="serving workload: seconds of arrivals per offered rate")
@@ -245,7 +246,7 @@ def run_serve(args, w):
     srv = F.Server(ix, k_max=100, probes_max=P, slots=args.slots, max_batch=4096)
     m = Q.shape[0]
 
-    def drive(t, sizes, ks, paced):
+    def drive(t, sizes, ks, paced, srv=srv, P=P):
         rids = [None] * len(t)
         lat = np.zeros(len(t))
         start = time.perf_counter()
@@ -291,6 +292,24 @@ def run_serve(args, w):
     s1 = srv.stats()
     srv.close()
     batches = s1["batches"] - s0["batches"]
+    # the plain FP32 path under the same saturation request mix, at its own
+    # calibrated probe budget (recall@10 >= 0.90)
+    fp32_base = None
+    if prec != F.FPP_FP32:
+        ix.close()
+        Xd = torch.from_numpy(X).cuda()
+        ix32 = F.Index(Xd, w.L, w.D, w.alpha, seed=w.rot_seed)
+        P32, rec32, _ = calibrate_probes(F, ix32, Xd, Qd, w.k,
+                                         [args.probes] if args.probes else w.probes)
+        del Xd
+        srv32 = F.Server(ix32, k_max=100, probes_max=P32, slots=args.slots, max_batch=4096)
+        tw, szw, ksw = W.serve_arrivals(99, 100_000, 0.2)
+        drive(tw, szw, ksw, paced=False, srv=srv32, P=P32)
+        sat32 = drive(t, sizes, ks, paced=False, srv=srv32, P=P32)
+        srv32.close()
+        ix32.close()
+        fp32_base = {"precision": "fp32", "probes": P32, "recall_at_10": rec32[P32],
+                     "saturation": sat32, "bf16_over_fp32_qps": sat["qps"] / sat32["qps"]}
     line = {
         "metric": METRIC, "value": sat["qps"], "unit": "queries/s", "n_gpus": 1,
         "steps": len(W.SERVE_RATES) + 1, "warmup": 1, "ms_per_step": None,
@@ -305,7 +324,8 @@ def run_serve(args, w):
                    "l2": "inputs larger than L2 (X is "
                          f"{w.n * w.d * 4 / 2**20:.0f} MiB FP32), no flush"},
         "serving": {"offered": rates, "saturation": sat,
-                    "mean_batch_queries": (s1["queries"] - s0["queries"]) / max(batches, 1)},
+                    "mean_batch_queries": (s1["queries"] - s0["queries"]) / max(batches, 1),
+                    "fp32_same_mix": fp32_base},
         "latency_ms": {"p50": sat["p50_ms"], "p99": sat["p99_ms"]},
         "roofline": None,
         "e2e": {"value": sat["qps"], "unit": "queries/s",
@@ -319,6 +339,8 @@ def run_serve(args, w):
 def main():
     args = parse()
     w = W.WORKLOADS[args.workload]
+    if args.precision is None:   # the workload's stored precision
+        args.precision = "bf16" if w.storage == "bf16" else "fp32"
     if args.impl == "reference":
         run_reference(args, w)
         return

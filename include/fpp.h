@@ -32,10 +32,10 @@
  *    sets, top-k ids) equal those of an exact FP64 evaluation of the method
  *    except where an FP64 margin below 1e-6 makes two answers equally valid;
  *    returned scores are FP64-accurate inner products rounded to FP32.  With
- *    FPP_BF16 the same holds except with the (small) probability that a BF16
- *    rounding error exceeds the statistical window described at
- *    fpp_precision (the top-k ids may then differ); returned scores are
- *    still FP64-accurate.
+ *    FPP_BF16 the top-k ids may differ where a BF16 rounding error exceeds
+ *    the statistical window described at fpp_precision or a true top-k
+ *    candidate falls outside the shortlist; returned scores are still
+ *    FP64-accurate.
  */
 #ifndef FPP_H_
 #define FPP_H_
@@ -64,11 +64,15 @@ typedef enum fpp_precision {
                         candidate within twice the BF16 error window
                         (nine estimated standard deviations of the rounding
                         error, score_error_factor) of the k-th is re-scored
-                        exactly on the FP32 rows before the final top-k.
+                        exactly on the FP32 rows before the final top-k
+                        (when the window spans the whole shortlist, the
+                        shortlist is re-ranked and nothing beyond it).
                         Hashing and probing are as for FPP_FP32.  The index
                         holds X in both precisions (6 bytes per element).
                         Graded by recall and score error. */
-  FPP_FP8E4M3 = 2    /* As FPP_BF16 with candidate rows stored in FP8 e4m3
+  FPP_FP8E4M3 = 2    /* As FPP_BF16 (but a window reaching past the
+                        shortlist re-scores every candidate inside it) with
+                        candidate rows stored in FP8 e4m3
                         (one byte per element) times a per-row FP32 scale
                         (the row's largest magnitude / 448); the window is
                         nine estimated standard deviations of the e4m3

@@ -860,7 +860,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   ta.qnorm = ws.qnorm.as<float>(); ta.xmax = ix->xmax; ta.gamma = ix->score_gamma;
   ta.gammaf = (float)(ix->score_gamma * 1.0001);
   ta.kprime = topk_kprime(ix, pl.kmax);
-  ta.approx = ix->precision != FPP_FP32;
+  ta.approx = ix->precision == FPP_BF16 ? 1 : ix->precision == FPP_FP8E4M3 ? 2 : 0;
   ta.cap = topk_cap(ta.kprime); ta.rcap = topk_rcap(ta.kprime);
   ta.slow = ws.tkslow.p; ta.err = reinterpret_cast<int*>(stv + 5); ta.stats = stv;
   ta.out_ids = ids_dev; ta.out_scores = scores_dev;

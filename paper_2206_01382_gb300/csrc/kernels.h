@@ -279,7 +279,8 @@ struct TopkArgs {
   const int32_t* k_pq;       // [mq] or NULL
   int k, kmax, cap, rcap;
   int kprime;                // shortlist re-scored exactly (>= k + 16)
-  int approx;                // precision path: overflow of the slow list is not an error
+  int approx;                // 0 exact; 1 BF16 (the pre-selection is re-ranked, no slow
+                             // path); 2 FP8 (slow-list overflow is not an error)
   void* slow;                // [ceil(mq / 8) * 8][topk_slow_cap()] 16-byte entries
   int* err;
   unsigned long long* stats; // stats[2] counts slow-path queries

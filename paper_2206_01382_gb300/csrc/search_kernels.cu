@@ -1974,40 +1974,61 @@ topk_kernel(TopkArgs a) {
   const int kk = min(kq, nk);
   const float kth = nk > 0 ? key_score(buf[kk - 1]) : 0.f;
   const float thr = nk > 0 ? (kth - 2.f * eps_s - 2.f * delta) - 1.2e-7f * fabsf(kth) - 1e-30f : 0.f;
-  const double thr64 = (double)thr;
   int ns = 0;   // |S|
   for (int e0 = 0; e0 < nk; e0 += 32) {
     const int e = e0 + lane;
     ns += __popc(__ballot_sync(FULL, e < nk && key_score(buf[e]) >= thr));
   }
-  const bool slow = U > (uint32_t)nk && ns == nk;
+  // a window reaching the end of the pre-selection while more candidates
+  // exist sends the query to the slow path, except on the BF16 path, which
+  // re-ranks its pre-selection (the best K' first-pass scores) and stops
+  // there; the FP8 window is about sixteen times wider and keeps the slow path
+  const bool slow = U > (uint32_t)nk && ns == nk && a.approx != 1;
   const int64_t orow = q * a.kmax;
-  if (!slow) {
-    // exact re-scoring of S: G lanes per row (a power of two, 32 / G rows per round)
-    const int G = ns >= 32 ? 1 : 32 / pow2_ceil(ns > 1 ? ns : 1);
+  // exact (float-float) scores of n rows, G lanes per row (a power of two,
+  // 32 / G rows per round): eight lanes per row for longer lists, so that
+  // each row is read in 128-byte coalesced pieces
+  const float4* q4 = reinterpret_cast<const float4*>(qv);
+  auto rescore = [&](int n, auto id_of, auto put) {
+    const int G = n > 8 ? 8 : 32 / pow2_ceil(n > 1 ? n : 1);
     const int rows_per_round = 32 / G;
     const int sub = lane % G;
-    for (int r0 = 0; r0 < ns; r0 += rows_per_round) {
+    for (int r0 = 0; r0 < n; r0 += rows_per_round) {
       const int r = r0 + lane / G;
-      const bool ok = r < ns;
-      const uint32_t id = ok ? key_id(buf[r]) : key_id(buf[0]);
+      const bool ok = r < n;
+      const uint32_t id = id_of(ok ? r : 0);
       const float4* x4 = reinterpret_cast<const float4*>(a.X + (int64_t)id * a.ldx);
-      const float4* q4 = reinterpret_cast<const float4*>(qv);
       float p = 0.f, sacc = 0.f;
-      for (int c = sub; c < nf4; c += G) {
-        const float4 x = __ldg(x4 + c), y = __ldg(q4 + c);
-        dot2_step(x.x, y.x, p, sacc);
-        dot2_step(x.y, y.y, p, sacc);
-        dot2_step(x.z, y.z, p, sacc);
-        dot2_step(x.w, y.w, p, sacc);
+      // four chunks of the lane's part of the row loaded before any is used
+      // (zero chunks past the row add exact zeros)
+      for (int c0 = sub; c0 < nf4; c0 += 4 * G) {
+        float4 x[4], y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = c0 + u * G;
+          x[u] = c < nf4 ? __ldg(x4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+          y[u] = c < nf4 ? __ldg(q4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          dot2_step(x[u].x, y[u].x, p, sacc);
+          dot2_step(x[u].y, y[u].y, p, sacc);
+          dot2_step(x[u].z, y[u].z, p, sacc);
+          dot2_step(x[u].w, y[u].w, p, sacc);
+        }
       }
       FF v{p, sacc};
       for (int o = G / 2; o > 0; o >>= 1) {
         FF w{__shfl_xor_sync(FULL, v.hi, o), __shfl_xor_sync(FULL, v.lo, o)};
         v = ff_add(v, w);
       }
-      if (ok && sub == 0) rf[r] = FEntry{ff_norm(v), id, 0};
+      if (ok && sub == 0) put(r, ff_norm(v), id);
     }
+  };
+  if (!slow) {
+    // exact re-scoring of S
+    rescore(ns, [&](int r) { return key_id(buf[r]); },
+            [&](int r, FF v, uint32_t id) { rf[r] = FEntry{v, id, 0}; });
     const int np2 = pow2_ceil(ns > 1 ? ns : 1);
     for (int e = ns + lane; e < np2; e += 32) rf[e] = FEntry{FF{-INFINITY, 0.f}, 0xFFFFFFFFu, 0};
     __syncwarp();
@@ -2022,15 +2043,15 @@ topk_kernel(TopkArgs a) {
   }
   // slow path: every candidate whose FP32 score may still reach the top-k
   if (lane == 0 && a.stats) atomicAdd(a.stats + 2, 1ull);
-  SD* list = reinterpret_cast<SD*>(a.slow) + (int64_t)(blockIdx.x * 8 + wid) * TK_SLOW;
+  FEntry* list = reinterpret_cast<FEntry*>(a.slow) + (int64_t)(blockIdx.x * 8 + wid) * TK_SLOW;
   unsigned nsl = 0;
   for (uint32_t i0 = 0; i0 < U; i0 += 32) {
     const uint32_t i = i0 + lane;
-    const bool take = i < U && (double)sc[i] >= thr64;
+    const bool take = i < U && sc[i] >= thr;
     const unsigned m = __ballot_sync(FULL, take);
     if (take) {
       const unsigned slot = nsl + __popc(m & ((1u << lane) - 1u));
-      if (slot < (unsigned)TK_SLOW) list[slot].id = cid[i];
+      if (slot < (unsigned)TK_SLOW) list[slot].h = cid[i];
     }
     nsl += __popc(m);
   }
@@ -2041,19 +2062,19 @@ topk_kernel(TopkArgs a) {
     nsl = TK_SLOW;
   }
   __syncwarp();
-  for (unsigned e = lane; e < nsl; e += 32)
-    list[e].s = thread_dot2_f4(qv, a.X + (int64_t)list[e].id * a.ldx, nf4);
+  rescore((int)nsl, [&](int r) { return list[r].h; },
+          [&](int r, FF v, uint32_t) { list[r].v = v; });
   const int np2 = pow2_ceil(nsl > 1 ? (int)nsl : 1);
-  for (int e = (int)nsl + lane; e < np2; e += 32) list[e] = SD{-INFINITY, 0xFFFFFFFFu, 0};
+  for (int e = (int)nsl + lane; e < np2; e += 32) list[e] = FEntry{FF{-INFINITY, 0.f}, 0xFFFFFFFFu, 0};
   __syncwarp();
-  warp_sort_sd(list, np2);
+  warp_sort_fe(list, np2);
   // a candidate listed twice (lists that were not de-duplicated) now sits
   // next to its copy: keep one of each
   int nd = 0;
   for (int i0 = 0; i0 < (int)nsl; i0 += 32) {
     const int i = i0 + lane;
-    const SD v = i < (int)nsl ? list[i] : SD{-INFINITY, 0xFFFFFFFFu, 0};
-    const bool keep = i < (int)nsl && (i == 0 || list[i - 1].id != v.id);
+    const FEntry v = i < (int)nsl ? list[i] : FEntry{FF{-INFINITY, 0.f}, 0xFFFFFFFFu, 0};
+    const bool keep = i < (int)nsl && (i == 0 || list[i - 1].h != v.h);
     const unsigned m = __ballot_sync(FULL, keep);
     __syncwarp();
     if (keep) list[nd + __popc(m & ((1u << lane) - 1u))] = v;
@@ -2062,8 +2083,8 @@ topk_kernel(TopkArgs a) {
   }
   for (int e = lane; e < a.kmax; e += 32) {
     const bool ok = e < kq && e < nd;
-    a.out_ids[orow + e] = ok ? (int64_t)list[e].id : -1;
-    a.out_scores[orow + e] = ok ? (float)list[e].s : -INFINITY;
+    a.out_ids[orow + e] = ok ? (int64_t)list[e].h : -1;
+    a.out_scores[orow + e] = ok ? list[e].v.hi : -INFINITY;
   }
 }
 
@@ -2429,6 +2450,7 @@ fpp_status launch_score_bf(const ScoreArgs& a, int sms, cudaStream_t st) {
   const int cpl = (nch + G - 1) / G;
   if (cpl == 1 && nch == G) return launch_score_bf_one<G, 1, true>(a, sms, st);
   if (cpl == 2 && nch == 2 * G) return launch_score_bf_one<G, 2, true>(a, sms, st);
+  if (cpl == 4 && nch == 4 * G) return launch_score_bf_one<G, 4, true>(a, sms, st);
   if (cpl <= 1) return launch_score_bf_one<G, 1, false>(a, sms, st);
   if (cpl <= 2) return launch_score_bf_one<G, 2, false>(a, sms, st);
   return launch_score_bf_one<G, 4, false>(a, sms, st);
@@ -2468,10 +2490,11 @@ fpp_status launch_score(const ScoreArgs& a, int sm_count, cudaStream_t st) {
     }
   }
   if (a.Xb) {
-    // 16-byte chunks of 8 BF16; at most 2 chunks per lane before G = 32
+    // 16-byte chunks of 8 BF16; at most 4 chunks per lane before G = 32 (as
+    // for FP32 rows: more rows per warp in flight)
     int g = 1;
     const int nch = (int)(a.ldxb / 8);
-    while (g < 32 && g * 2 < nch) g <<= 1;
+    while (g < 32 && g * 4 < nch) g <<= 1;
     if (a.tune_g) g = a.tune_g;
     switch (g) {
       case 1: return launch_score_bf<1>(a, grid, st);
