@@ -72,7 +72,7 @@ struct DevBuf {
 struct Workspace {
   DevBuf qpad, qsplit, proj, probes, qnorm, recheck, recheck2, recheck_s, kpq, ppq, out_ids,
       out_scores, sigproj, qsig,
-      ecount, eoff, scan, cand, cscores, items, tkslow, stats;
+      ecount, eoff, cand, cscores, items, tkslow, stats;
   // completion of the last call that used this workspace: a call on another
   // stream waits for it before touching the buffers
   cudaEvent_t done = nullptr;
@@ -92,7 +92,7 @@ struct Workspace {
   void release() {
     for (DevBuf* b : {&qpad, &qsplit, &proj, &probes, &qnorm, &recheck, &recheck2, &recheck_s, &sigproj,
                       &qsig, &kpq, &ppq,
-                      &out_ids, &out_scores, &ecount, &eoff, &scan, &cand, &cscores,
+                      &out_ids, &out_scores, &ecount, &eoff, &cand, &cscores,
                       &items, &tkslow, &stats})
       b->release();
     if (done) cudaEventDestroy(done);
@@ -803,12 +803,12 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   da.nitems = reinterpret_cast<unsigned*>(stv + 10);
   da.tierq = ws.ecount.as<uint32_t>() + 2 * mc;
   da.tiern = da.nitems + 1;
+  da.region_total = stv + 12;
   da.no_items = pl.sim_keep > 0 ? 1 : 0;
   da.stats = stv;
-  FPP_CUDA(cudaMemsetAsync(da.nitems, 0, 3 * sizeof(unsigned), st));   // items, tier counts
+  // items, tier counts (slots 10 and 11) and the slots handed out (slot 12)
+  FPP_CUDA(cudaMemsetAsync(stv + 10, 0, 3 * sizeof(unsigned long long), st));
   FPP_TRY(launch_count_entries(da, st));
-  FPP_TRY(exclusive_scan_u32(ws.ecount.as<uint32_t>(), mc, ws.eoff.as<uint64_t>(), 0,
-                             KeepRule{1.0, 1, 0}, ws.scan.as<uint64_t>(), st));
   // candidate slots: the bound from the largest kept bucket when the
   // workspace holds it or can be grown to it within the sync-free budget
   // (no host round trip, so the batch can be captured in a graph);
@@ -817,7 +817,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   uint64_t need = bound;
   bool exact = false;
   if (bound > ws.cand_cap && bound > ix->cand_budget_entries) {
-    FPP_CUDA(cudaMemcpyAsync(&need, ws.eoff.as<uint64_t>() + mc, 8, cudaMemcpyDeviceToHost, st));
+    FPP_CUDA(cudaMemcpyAsync(&need, stv + 12, 8, cudaMemcpyDeviceToHost, st));
     FPP_CUDA(cudaStreamSynchronize(st));
     exact = true;
   }
@@ -906,8 +906,7 @@ fpp_status prepare_workspace(fpp_index* ix, Workspace& ws, const SearchPlan& pl,
     FPP_TRY(ws.out_scores.ensure((size_t)mc * pl.kmax * 4, false, st));
   }
   FPP_TRY(ws.ecount.ensure((size_t)4 * mc * 4, false, st));   // counts, distinct counts, 2 tiers
-  FPP_TRY(ws.eoff.ensure((size_t)(mc + 1) * 8, false, st));
-  FPP_TRY(ws.scan.ensure((size_t)scan_scratch_elems(mc) * 8, false, st));
+  FPP_TRY(ws.eoff.ensure((size_t)mc * 8, false, st));
   FPP_TRY(ws.tkslow.ensure((size_t)(ceil_div(mc, 8) * 8) * topk_slow_cap() * 16, false, st));
   return FPP_OK;
 }
@@ -1564,15 +1563,18 @@ fpp_status fpp_debug_candidates(const fpp_index* cix, const float* Q, int64_t m,
   for (int64_t q0 = 0; q0 < m; q0 += mc) {
     const int64_t c = std::min<int64_t>(mc, m - q0);
     FPP_TRY(search_chunk(ix, ix->ws, Q, q0, c, pl, nullptr, nullptr, 0, kCandidatesOnly, nullptr));
-    eoff.resize(c + 1);
+    eoff.resize(c);
     ucount.resize(c);
-    FPP_CUDA(cudaMemcpy(eoff.data(), ix->ws.eoff.p, (c + 1) * 8, cudaMemcpyDeviceToHost));
+    uint64_t total = 0;   // slots handed out to the batch's regions
+    FPP_CUDA(cudaMemcpy(eoff.data(), ix->ws.eoff.p, c * 8, cudaMemcpyDeviceToHost));
     FPP_CUDA(cudaMemcpy(ucount.data(), ix->ws.ecount.as<uint32_t>() + c, c * 4,
                         cudaMemcpyDeviceToHost));
+    FPP_CUDA(cudaMemcpy(&total, ix->ws.stats.as<unsigned long long>() + 12, 8,
+                        cudaMemcpyDeviceToHost));
     if (cand) {
-      buf.resize(eoff[c]);
-      if (eoff[c])
-        FPP_CUDA(cudaMemcpy(buf.data(), ix->ws.cand.p, eoff[c] * 4, cudaMemcpyDeviceToHost));
+      buf.resize(total);
+      if (total)
+        FPP_CUDA(cudaMemcpy(buf.data(), ix->ws.cand.p, total * 4, cudaMemcpyDeviceToHost));
     }
     for (int64_t i = 0; i < c; ++i) {
       const int64_t g = q0 + i;

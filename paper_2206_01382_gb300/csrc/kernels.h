@@ -210,8 +210,10 @@ struct DedupArgs {
   const uint32_t* offsets;   // [L][4D^2 + 1]
   const uint64_t* table_base;// [L]
   const uint32_t* ids;       // kept ids
-  uint32_t* ecount;          // [mq] bucket entries per query
-  const uint64_t* eoff;      // [mq + 1] exclusive scan of ecount
+  uint32_t* ecount;          // [mq] bucket entries per query (count_entries)
+  uint64_t* eoff;            // [mq] start of each query's region of ecount slots
+                             // (count_entries; regions are not in query order)
+  unsigned long long* region_total;  // slots handed out (zeroed before count_entries)
   uint32_t* cand;            // candidate ids, query q at eoff[q] ..
   uint32_t* ucount;          // [mq] distinct candidates per query
   ScoreItem* items;          // score work items, appended (any order)

@@ -1292,10 +1292,12 @@ __device__ __forceinline__ void write_items(const DedupArgs& a, int64_t q, uint3
 
 __global__ void __launch_bounds__(256)
 count_entries_kernel(DedupArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int64_t q = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (q >= a.mq) return;
-  const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
+  __shared__ uint32_t s_cnt[8];
+  __shared__ unsigned long long s_base;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * 8 + wid;
+  const bool live = q < a.mq;
+  const int Pq = !live ? 0 : a.probes_pq ? a.probes_pq[q] : a.pstride;
   const int64_t NB = 4ll * a.D * a.D;
   const int nprobe = a.nt * Pq;
   uint32_t s = 0;
@@ -1321,7 +1323,20 @@ count_entries_kernel(DedupArgs a) {
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-  if (lane == 0) {
+  // the CTA's eight regions, consecutive, at a base taken from one global
+  // counter (regions are not in query order; no scan over the batch)
+  if (lane == 0) s_cnt[wid] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tot = 0;
+    for (int w = 0; w < 8; ++w) tot += s_cnt[w];
+    s_base = tot ? atomicAdd(a.region_total, tot) : 0ull;
+  }
+  __syncthreads();
+  if (live && lane == 0) {
+    unsigned long long off = s_base;
+    for (int w = 0; w < wid; ++w) off += s_cnt[w];
+    a.eoff[q] = off;
     a.ecount[q] = s;
     if (s == 0) a.ucount[q] = 0u;   // no tier kernel visits an empty query
     // queries above the small tier are listed for the kernels of their tier
@@ -1346,7 +1361,7 @@ flatten_kernel(DedupArgs a) {
   if ((int64_t)blockIdx.x * DW >= nq) return;   // no listed query for this CTA
   for (int64_t i = (int64_t)blockIdx.x * DW + wid; i < nq; i += nwarps) {
     const int64_t q = a.tierq[a.mq + i];
-    const uint64_t E = a.eoff[q + 1] - a.eoff[q];
+    const uint64_t E = a.ecount[q];
     const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
     WarpWalk w{&a, q, Pq, a.nt * Pq, NB, s_pbase[wid], s_pstart[wid]};
     uint32_t* out = a.cand + a.eoff[q];
@@ -1415,7 +1430,7 @@ dedup_hash_kernel(DedupArgs a) {
   unsigned long long ent = 0, uni = 0, prb = 0;
   for (int64_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
     const int64_t q = TIER < 0 ? qi : (int64_t)a.tierq[TIER * a.mq + qi];
-    const uint64_t E = a.eoff[q + 1] - a.eoff[q];
+    const uint64_t E = a.ecount[q];
     if (E > (uint64_t)EHI || E <= (uint64_t)ELO) continue;   // uniform over the CTA
     const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
     const int nprobe = a.nt * Pq;
