@@ -128,6 +128,15 @@ typedef struct fpp_search_opts {
                                  query's (ties: lower id), 1..512; needs an
                                  index built with simhash_bits (Section 4).
                                  An approximation: graded by recall.  0: off */
+  int32_t score_range_rows;   /* candidate scoring groups each query's ids by
+                                 row range so that the rows of one range are
+                                 read by the whole GPU at once and stay in L2.
+                                 0: ranges of at most 64 MiB of candidate rows
+                                 (none when all rows fit one range); > 0: at
+                                 least this many rows per range (rounded up to
+                                 a power of two, at most 256 ranges).  Results
+                                 do not depend on it.                          */
+  int32_t reserved0;
 } fpp_search_opts;
 
 /* FPP_SEARCH_GRAPH: run the call as one CUDA graph, captured on the first

@@ -49,7 +49,8 @@ class fpp_search_opts(ctypes.Structure):
                 ("k_max", ctypes.c_int32), ("table_begin", ctypes.c_int32),
                 ("table_end", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("global_probes", ctypes.c_int32),
-                ("simhash_keep", ctypes.c_int32)]
+                ("simhash_keep", ctypes.c_int32), ("score_range_rows", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32)]
 
 
 class fpp_search_stats(ctypes.Structure):
@@ -262,7 +263,8 @@ def fpp_search(ix, Q, k: int, probes: int, ids=None, scores=None):
 def fpp_search_ex(ix, Q, k: int = 10, probes: int = 1, k_per_query=None, probes_per_query=None,
                   k_max: int | None = None, table_begin: int = 0, table_end: int = 0,
                   stream=None, ids=None, scores=None, want_stats: bool = True,
-                  graph: bool = False, global_probes: int = 0, simhash_keep: int = 0):
+                  graph: bool = False, global_probes: int = 0, simhash_keep: int = 0,
+                  score_range_rows: int = 0):
     """fpp_search with per-query k / probes, a table range, a stream and stats."""
     Q = _f32(Q)
     m = Q.shape[0]
@@ -279,6 +281,7 @@ def fpp_search_ex(ix, Q, k: int = 10, probes: int = 1, k_per_query=None, probes_
     o.flags = FPP_SEARCH_GRAPH if graph else 0
     o.global_probes = global_probes
     o.simhash_keep = simhash_keep
+    o.score_range_rows = score_range_rows
     ids = _alloc_like(Q, (m, k_max), "i64") if ids is None else ids
     scores = _alloc_like(Q, (m, k_max), "f32") if scores is None else scores
     st = fpp_search_stats()

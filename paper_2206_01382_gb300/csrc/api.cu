@@ -72,7 +72,8 @@ struct DevBuf {
 struct Workspace {
   DevBuf qpad, qsplit, proj, probes, qnorm, recheck, recheck2, recheck_s, kpq, ppq, out_ids,
       out_scores, sigproj, qsig,
-      ecount, eoff, cand, cscores, items, tkslow, stats;
+      ecount, eoff, cand, cscores, items, items2, rhist, tkslow, stats;
+  const ScoreItem* score_items = nullptr;   // the item list the last batch scored
   // completion of the last call that used this workspace: a call on another
   // stream waits for it before touching the buffers
   cudaEvent_t done = nullptr;
@@ -93,7 +94,7 @@ struct Workspace {
     for (DevBuf* b : {&qpad, &qsplit, &proj, &probes, &qnorm, &recheck, &recheck2, &recheck_s, &sigproj,
                       &qsig, &kpq, &ppq,
                       &out_ids, &out_scores, &ecount, &eoff, &cand, &cscores,
-                      &items, &tkslow, &stats})
+                      &items, &items2, &rhist, &tkslow, &stats})
       b->release();
     if (done) cudaEventDestroy(done);
     done = nullptr;
@@ -640,6 +641,8 @@ struct SearchPlan {
   int kmax, pmax, tb, te;
   int global_q = 0;     // > 0: global probe budget (pmax = the per-table cap)
   int sim_keep = 0;     // > 0: SimHash pre-ranking keeps this many candidates
+  int range_shift = 0;  // range_count > 1: candidates grouped by id >> range_shift
+  int range_count = 1;
   const int32_t* kpq;   // user arrays (host or device) or NULL
   const int32_t* ppq;
   bool kpq_dev, ppq_dev;
@@ -707,6 +710,22 @@ fpp_status validate_search(const fpp_index* ix, const float* Q, int64_t m, const
     return FPP_EINVAL;
   }
   pl.sim_keep = o->simhash_keep;
+  if (o->score_range_rows < 0) { set_error("score_range_rows must be >= 0"); return FPP_EINVAL; }
+  if (pl.sim_keep == 0) {
+    // rows per range: at most 64 MiB of candidate rows, or the caller's
+    // count, rounded to a power of two; at most SCORE_RANGE_MAX ranges
+    const uint64_t row_bytes = ix->precision == FPP_BF16 ? (uint64_t)ix->ldxb * 2
+                               : ix->precision == FPP_FP8E4M3 ? (uint64_t)ix->ldxq + 4
+                                                              : (uint64_t)ix->dpad * 4;
+    const uint64_t want = o->score_range_rows > 0 ? (uint64_t)o->score_range_rows
+                                                  : std::max<uint64_t>(1, (64ull << 20) / row_bytes);
+    int sh = 0;
+    while ((1ull << (sh + 1)) <= want) ++sh;
+    if (o->score_range_rows > 0 && (1ull << sh) < want) ++sh;
+    while ((uint64_t)((ix->n + (1ll << sh) - 1) >> sh) > (uint64_t)SCORE_RANGE_MAX) ++sh;
+    const int64_t R = (ix->n + (1ll << sh) - 1) >> sh;
+    if (R > 1) { pl.range_shift = sh; pl.range_count = (int)R; }
+  }
   pl.kmax = o->k_max > 0 ? o->k_max : kmax_seen;
   if (pl.kmax < kmax_seen || pl.kmax > 256) { set_error("k_max must cover every k and be <= 256"); return FPP_EINVAL; }
   pl.pmax = std::max(1, pmax_seen);
@@ -805,6 +824,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   da.tiern = da.nitems + 1;
   da.region_total = stv + 12;
   da.no_items = pl.sim_keep > 0 ? 1 : 0;
+  da.range_shift = pl.range_shift; da.range_count = pl.range_count;
   da.stats = stv;
   // items, tier counts (slots 10 and 11) and the slots handed out (slot 12)
   FPP_CUDA(cudaMemsetAsync(stv + 10, 0, 3 * sizeof(unsigned long long), st));
@@ -828,10 +848,24 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
     FPP_TRY(ws.cscores.ensure((size_t)cap * 4));
     ws.cand_cap = cap;
   }
-  FPP_TRY(ws.items.ensure((size_t)score_item_slots(ws.cand_cap, mc) * sizeof(ScoreItem)));
+  const size_t item_bytes =
+      (size_t)score_item_slots(ws.cand_cap, mc, pl.range_count) * sizeof(ScoreItem);
+  FPP_TRY(ws.items.ensure(item_bytes));
+  if (pl.range_count > 1) FPP_TRY(ws.items2.ensure(item_bytes));
   da.cand = ws.cand.as<uint32_t>();
   da.items = ws.items.as<ScoreItem>();
   FPP_TRY(launch_dedup(da, st));
+  // the work items in order of their row range (the scoring reads them so)
+  const ScoreItem* score_items = ws.items.as<ScoreItem>();
+  if (pl.range_count > 1) {
+    unsigned* rh = reinterpret_cast<unsigned*>(ws.rhist.p);
+    FPP_CUDA(cudaMemsetAsync(rh, 0, 2 * SCORE_RANGE_MAX * sizeof(unsigned), st));   // hist, cursors
+    FPP_TRY(launch_order_items(ws.items.as<ScoreItem>(), da.nitems, ws.cand.as<uint32_t>(),
+                               pl.range_shift, pl.range_count, rh, rh + SCORE_RANGE_MAX,
+                               ws.items2.as<ScoreItem>(), st));
+    score_items = ws.items2.as<ScoreItem>();
+  }
+  ws.score_items = score_items;
   if (pl.sim_keep > 0) {
     SimArgs sm{};
     sm.mq = mc; sm.eoff = ws.eoff.as<uint64_t>(); sm.cand = ws.cand.as<uint32_t>();
@@ -843,7 +877,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   if (ev) FPP_CUDA(cudaEventRecord(ev[5], st));
   if (stage == kCandidatesOnly) return FPP_OK;
   ScoreArgs sa{};
-  sa.items = ws.items.as<ScoreItem>(); sa.nitems = da.nitems;
+  sa.items = score_items; sa.nitems = da.nitems;
   sa.eoff = ws.eoff.as<uint64_t>(); sa.mq = mc;
   sa.cand = ws.cand.as<uint32_t>();
   sa.X = ix->X; sa.ldx = ix->dpad; sa.Q = ws.qpad.as<float>(); sa.ldq = ix->dpad;
@@ -901,6 +935,7 @@ fpp_status prepare_workspace(fpp_index* ix, Workspace& ws, const SearchPlan& pl,
   FPP_TRY(ws.kpq.ensure((size_t)mc * 4, false, st));
   FPP_TRY(ws.ppq.ensure((size_t)mc * 4, false, st));
   FPP_TRY(ws.stats.ensure(16 * 8, true, st));
+  FPP_TRY(ws.rhist.ensure(2 * SCORE_RANGE_MAX * sizeof(unsigned), false, st));
   if (host_out) {
     FPP_TRY(ws.out_ids.ensure((size_t)mc * pl.kmax * 8, false, st));
     FPP_TRY(ws.out_scores.ensure((size_t)mc * pl.kmax * 4, false, st));
@@ -931,13 +966,16 @@ bool search_graph(fpp_index* ix, const float* Q, int64_t m, const fpp_search_opt
     if ((out = ws.cscores.ensure((size_t)bound * 4)) != FPP_OK) return true;
     ws.cand_cap = bound;
   }
-  if ((out = ws.items.ensure((size_t)score_item_slots(ws.cand_cap, mc) * sizeof(ScoreItem))) != FPP_OK)
-    return true;
+  const size_t item_bytes =
+      (size_t)score_item_slots(ws.cand_cap, mc, pl.range_count) * sizeof(ScoreItem);
+  if ((out = ws.items.ensure(item_bytes)) != FPP_OK) return true;
+  if (pl.range_count > 1 && (out = ws.items2.ensure(item_bytes)) != FPP_OK) return true;
   const std::vector<uint64_t> key = {
       (uint64_t)(uintptr_t)Q, (uint64_t)m, (uint64_t)(uintptr_t)ids, (uint64_t)(uintptr_t)scores,
       (uint64_t)(uintptr_t)pl.kpq, (uint64_t)(uintptr_t)pl.ppq, (uint64_t)pl.k,
       (uint64_t)pl.probes, (uint64_t)pl.kmax, (uint64_t)pl.pmax, (uint64_t)pl.tb, (uint64_t)pl.te,
-      (uint64_t)(uintptr_t)st, (uint64_t)pl.global_q, (uint64_t)pl.sim_keep, g_alloc_gen.load()};
+      (uint64_t)(uintptr_t)st, (uint64_t)pl.global_q, (uint64_t)pl.sim_keep,
+      (uint64_t)pl.range_shift, (uint64_t)pl.range_count, g_alloc_gen.load()};
   if (!ix->graph_exec || ix->graph_key != key) {
     if (ix->graph_exec) cudaGraphExecDestroy(ix->graph_exec);
     ix->graph_exec = nullptr;
@@ -1721,7 +1759,7 @@ fpp_status fpp_autotune(fpp_index* ix, const float* Q, int64_t m, int32_t k, int
                        kFull, nullptr));
   FPP_CUDA(cudaDeviceSynchronize());
   ScoreArgs sa{};
-  sa.items = ws.items.as<ScoreItem>();
+  sa.items = ws.score_items;
   sa.nitems = reinterpret_cast<unsigned*>(ws.stats.as<unsigned long long>() + 10);
   sa.eoff = ws.eoff.as<uint64_t>(); sa.mq = mc;
   sa.cand = ws.cand.as<uint32_t>();

@@ -222,6 +222,8 @@ struct DedupArgs {
                              // tier and for the no-de-duplication tier
   unsigned* tiern;           // [2] their counts (zeroed before count_entries)
   int no_items;              // 1: leave the items to the SimHash filter
+  int range_shift;           // range_count > 1: each query's ids are grouped by row
+  int range_count;           // range (id >> range_shift), one or more items per range
   unsigned long long* stats; // entries, unique, -, probes
 };
 
@@ -291,11 +293,20 @@ struct TopkArgs {
 };
 
 int score_item_len();
-int64_t score_item_slots(uint64_t entries_total, int64_t mq);
+// Work-item slots for cand_total candidates of mq queries whose ids are
+// grouped into at most `ranges` row ranges.
+int64_t score_item_slots(uint64_t entries_total, int64_t mq, int ranges);
+constexpr int SCORE_RANGE_MAX = 256;   // row ranges of the grouped scoring
 int topk_cap(int kprime);
 int topk_rcap(int kprime);
 int topk_slow_cap();
 fpp_status launch_count_entries(const DedupArgs& a, cudaStream_t st);
+// Orders the score work items by the row range of their first candidate
+// (counting sort; hist and cursor are [range_count] zeroed counters), so that
+// the CTAs scoring at the same time read rows of one range, which stays in L2.
+fpp_status launch_order_items(const ScoreItem* in, const unsigned* nitems, const uint32_t* cand,
+                              int range_shift, int range_count, unsigned* hist, unsigned* cursor,
+                              ScoreItem* out, cudaStream_t st);
 fpp_status launch_dedup(const DedupArgs& a, cudaStream_t st);
 fpp_status launch_score(const ScoreArgs& a, int sm_count, cudaStream_t st);
 fpp_status launch_topk(const TopkArgs& a, cudaStream_t st);

@@ -1198,6 +1198,7 @@ constexpr int PCHUNK = 128;                     // probed buckets resolved per p
 constexpr int PPT = PCHUNK / 32;                // buckets per lane per pass
 constexpr int EPT = 8;                          // entries per lane per round
 constexpr int ITEM = 128;                       // candidates per score work item
+constexpr int RANGE_MAX = SCORE_RANGE_MAX;      // row ranges of the grouped scoring
 
 struct WarpWalk {
   const DedupArgs* a;
@@ -1365,6 +1366,8 @@ flatten_kernel(DedupArgs a) {
     const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
     WarpWalk w{&a, q, Pq, a.nt * Pq, NB, s_pbase[wid], s_pstart[wid]};
     uint32_t* out = a.cand + a.eoff[q];
+    const uint32_t U = (uint32_t)E;
+    // (not grouped by row range: its items are ordered by their first id)
     struct Copy {
       uint32_t* out; uint32_t n;
       __device__ void operator()(const uint32_t (&id)[EPT], const bool (&has)[EPT]) {
@@ -1380,7 +1383,6 @@ flatten_kernel(DedupArgs a) {
       }
     } cp{out, 0u};
     warp_walk(w, cp);
-    const uint32_t U = (uint32_t)E;
     if (lane == 0) {
       ent += E;
       prb += (unsigned long long)w.nprobe;
@@ -1419,6 +1421,7 @@ dedup_hash_kernel(DedupArgs a) {
   __shared__ uint32_t pstart[NT + 1];
   __shared__ uint32_t wsum[NT / 32];
   __shared__ uint32_t s_n, s_base;
+  const bool grouped = a.range_count > 1 && !a.no_items;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int64_t nq = TIER < 0 ? a.mq : (int64_t)a.tiern[TIER];
   if (nq == 0) return;   // uniform over the CTA
@@ -1551,21 +1554,86 @@ dedup_hash_kernel(DedupArgs a) {
       __syncthreads();   // pbase / pstart are rewritten by the next chunk
     }
     const uint32_t U = s_n;
-    const uint32_t nit = a.no_items ? 0u : (U + ITEM - 1) / ITEM;
-    if (tid == 0) {
-      ent += E;
-      uni += U;
-      prb += (unsigned long long)nprobe;
-      a.ucount[q] = U;
-      s_base = nit ? atomicAdd(a.nitems, nit) : 0u;
-    }
-    __syncthreads();
-    for (uint32_t k = tid; k < nit; k += NT) {
-      ScoreItem itm;
-      itm.q = (uint32_t)q;
-      itm.len = min((uint32_t)ITEM, U - k * ITEM);
-      itm.start = a.eoff[q] + (uint64_t)k * ITEM;
-      a.items[s_base + k] = itm;
+    if (grouped) {
+      // group the query's distinct ids by row range (id >> range_shift): the
+      // ids are staged in the table's slots [0, U), the per-range counts,
+      // offsets and cursors sit in its last 3 RANGE_MAX slots (U <= 3/4 HS)
+      if (tid == 0) {
+        ent += E;
+        uni += U;
+        prb += (unsigned long long)nprobe;
+        a.ucount[q] = U;
+      }
+      uint32_t* rc = tab + HS - 3 * RANGE_MAX;
+      uint32_t* out = a.cand + a.eoff[q];
+      const int R = a.range_count;
+      for (int r = tid; r < R; r += NT) rc[r] = 0u;
+      __syncthreads();
+      for (uint32_t i = tid; i < U; i += NT) {
+        const uint32_t id = out[i];
+        tab[i] = id;
+        atomicAdd(rc + (id >> a.range_shift), 1u);
+      }
+      __syncthreads();
+      if (wid == 0) {   // exclusive offsets of the ranges and of their items
+        uint32_t carry = 0, icarry = 0;
+        for (int r0 = 0; r0 < R; r0 += 32) {
+          const int r = r0 + lane;
+          const uint32_t c = r < R ? rc[r] : 0u;
+          const uint32_t ni = (c + ITEM - 1) / ITEM;
+          uint32_t inc = c, iinc = ni;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t2 = __shfl_up_sync(FULL, inc, o);
+            const uint32_t t3 = __shfl_up_sync(FULL, iinc, o);
+            if (lane >= o) { inc += t2; iinc += t3; }
+          }
+          if (r < R) {
+            rc[RANGE_MAX + r] = carry + inc - c;
+            rc[2 * RANGE_MAX + r] = icarry + iinc - ni;
+          }
+          carry += __shfl_sync(FULL, inc, 31);
+          icarry += __shfl_sync(FULL, iinc, 31);
+        }
+        if (lane == 0) s_base = icarry ? atomicAdd(a.nitems, icarry) : 0u;   // one reservation
+      }
+      __syncthreads();
+      for (int r = tid; r < R; r += NT) {
+        const uint32_t c = rc[r];
+        const uint32_t nit = (c + ITEM - 1) / ITEM;
+        for (uint32_t k = 0; k < nit; ++k) {
+          ScoreItem itm;
+          itm.q = (uint32_t)q;
+          itm.len = min((uint32_t)ITEM, c - k * ITEM);
+          itm.start = a.eoff[q] + rc[RANGE_MAX + r] + (uint64_t)k * ITEM;
+          a.items[s_base + rc[2 * RANGE_MAX + r] + k] = itm;
+        }
+      }
+      __syncthreads();
+      for (int r = tid; r < R; r += NT) rc[2 * RANGE_MAX + r] = rc[RANGE_MAX + r];   // cursors
+      __syncthreads();
+      for (uint32_t i = tid; i < U; i += NT) {
+        const uint32_t id = tab[i];
+        out[atomicAdd(rc + 2 * RANGE_MAX + (id >> a.range_shift), 1u)] = id;
+      }
+      __syncthreads();
+    } else {
+      const uint32_t nit = a.no_items ? 0u : (U + ITEM - 1) / ITEM;
+      if (tid == 0) {
+        ent += E;
+        uni += U;
+        prb += (unsigned long long)nprobe;
+        a.ucount[q] = U;
+        s_base = nit ? atomicAdd(a.nitems, nit) : 0u;
+      }
+      __syncthreads();
+      for (uint32_t k = tid; k < nit; k += NT) {
+        ScoreItem itm;
+        itm.q = (uint32_t)q;
+        itm.len = min((uint32_t)ITEM, U - k * ITEM);
+        itm.start = a.eoff[q] + (uint64_t)k * ITEM;
+        a.items[s_base + k] = itm;
+      }
     }
     for (int i = tid; i < HS / 4; i += NT)
       reinterpret_cast<uint4*>(tab)[i] = make_uint4(HEMPTY, HEMPTY, HEMPTY, HEMPTY);
@@ -2405,8 +2473,89 @@ fpp_status launch_query_norms(const float* Q, int64_t m, int64_t ldq, int d, flo
 }
 
 int score_item_len() { return ITEM; }
-int64_t score_item_slots(uint64_t cand_total, int64_t mq) {
-  return (int64_t)(cand_total / ITEM) + mq + 1;
+int64_t score_item_slots(uint64_t cand_total, int64_t mq, int ranges) {
+  return (int64_t)(cand_total / ITEM) + mq * (int64_t)(ranges > 1 ? ranges : 1) + 1;
+}
+
+// Counting sort of the score work items by the row range of their first
+// candidate.  Both kernels stride over the items with the same grid; each CTA
+// counts its items per range in shared memory and touches the global
+// counters once per range: the histogram kernel adds its counts to hist; the
+// scatter kernel takes the range bases from hist, reserves its slots in each
+// range with one atomic on cursor and places its items with shared-memory
+// atomics (the order inside a range is arbitrary).
+constexpr int ORDER_T = 256;
+
+__global__ void __launch_bounds__(ORDER_T)
+order_hist_kernel(const ScoreItem* __restrict__ in, const unsigned* nitems,
+                  const uint32_t* __restrict__ cand, int shift, int R, unsigned* hist) {
+  __shared__ unsigned cnt[RANGE_MAX];
+  for (int r = threadIdx.x; r < R; r += blockDim.x) cnt[r] = 0u;
+  __syncthreads();
+  const unsigned n = *nitems;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    atomicAdd(cnt + (cand[in[i].start] >> shift), 1u);
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += blockDim.x)
+    if (cnt[r]) atomicAdd(hist + r, cnt[r]);
+}
+
+__global__ void __launch_bounds__(ORDER_T)
+order_scatter_kernel(const ScoreItem* __restrict__ in, const unsigned* nitems,
+                     const uint32_t* __restrict__ cand, int shift, int R, const unsigned* hist,
+                     unsigned* cursor, ScoreItem* __restrict__ out) {
+  __shared__ unsigned base[RANGE_MAX], cnt[RANGE_MAX];
+  if (threadIdx.x < 32) {   // base[r]: the items of the ranges before r
+    const int lane = threadIdx.x;
+    unsigned carry = 0;
+    for (int r0 = 0; r0 < R; r0 += 32) {
+      const int r = r0 + lane;
+      const unsigned c = r < R ? hist[r] : 0u;
+      unsigned inc = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t2 = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += t2;
+      }
+      if (r < R) base[r] = carry + inc - c;
+      carry += __shfl_sync(FULL, inc, 31);
+    }
+  }
+  for (int r = threadIdx.x; r < R; r += blockDim.x) cnt[r] = 0u;
+  __syncthreads();
+  const unsigned n = *nitems;
+  const unsigned stride = gridDim.x * blockDim.x;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    atomicAdd(cnt + (cand[in[i].start] >> shift), 1u);
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    if (cnt[r]) base[r] += atomicAdd(cursor + r, cnt[r]);   // this CTA's slots of range r
+    cnt[r] = 0u;
+  }
+  __syncthreads();
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const ScoreItem it = in[i];
+    const int r = (int)(cand[it.start] >> shift);
+    out[base[r] + atomicAdd(cnt + r, 1u)] = it;
+  }
+}
+
+fpp_status launch_order_items(const ScoreItem* in, const unsigned* nitems, const uint32_t* cand,
+                              int range_shift, int range_count, unsigned* hist, unsigned* cursor,
+                              ScoreItem* out, cudaStream_t st) {
+  if (range_count > RANGE_MAX) {
+    set_error("launch_order_items: too many row ranges");
+    return FPP_EINTERNAL;
+  }
+  int dev = 0, sms = 0;
+  FPP_CUDA(cudaGetDevice(&dev));
+  FPP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  order_hist_kernel<<<sms * 4, ORDER_T, 0, st>>>(in, nitems, cand, range_shift, range_count, hist);
+  FPP_LAUNCHED();
+  order_scatter_kernel<<<sms * 4, ORDER_T, 0, st>>>(in, nitems, cand, range_shift, range_count,
+                                                    hist, cursor, out);
+  FPP_LAUNCHED();
+  return FPP_OK;
 }
 
 fpp_status launch_count_entries(const DedupArgs& a, cudaStream_t st) {

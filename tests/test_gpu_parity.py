@@ -79,6 +79,35 @@ def test_fp32_random_vectors_full_parity(F):
     assert ix_g.info()["r_pieces"] == 3
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_scoring_by_row_range_changes_nothing(F, prec):
+    # the candidates grouped by row range (forced here: 512 rows per range,
+    # 20 ranges) give the same ids and scores as one range
+    w = W.WORKLOADS["tiny"]
+    X, Q = W.dataset(w)
+    p = F.FPP_BF16 if prec == "bf16" else F.FPP_FP32
+    ix = F.Index(X, w.L, w.D, w.alpha, seed=w.rot_seed, precision=p)
+    rng = np.random.default_rng(5)
+    kq = rng.choice([1, 10, 50], size=len(Q)).astype(np.int32)
+    pq = rng.choice([1, 4, 16], size=len(Q)).astype(np.int32)
+    for kw in ({"k": 10, "probes": 4}, {"k_per_query": kq, "probes_per_query": pq}):
+        a_i, a_s, _ = F.fpp_search_ex(ix.handle, Q, **kw)
+        b_i, b_s, _ = F.fpp_search_ex(ix.handle, Q, score_range_rows=512, **kw)
+        assert np.array_equal(a_i, b_i) and np.array_equal(a_s, b_s)
+
+
+def test_scoring_by_row_range_large_lists(F):
+    # queries with more than 16,384 entries (not de-duplicated) and with
+    # 2,049..16,384 entries, grouped by row range: the same results
+    for n, L, D, P in ((30000, 24, 4, 8), (12000, 6, 8, 12)):
+        X, Q = W.small_mixture(n, 30, 16, 8, 0.3, 92 + D)
+        ix = F.Index(X, L, D, 1.0, seed=44)
+        a_i, a_s, st = F.fpp_search_ex(ix.handle, Q, k=20, probes=P)
+        b_i, b_s, _ = F.fpp_search_ex(ix.handle, Q, k=20, probes=P, score_range_rows=256)
+        assert np.array_equal(a_i, b_i) and np.array_equal(a_s, b_s)
+        assert st["entries"] > 2048 * len(Q)
+
+
 def test_queries_without_candidates_after_a_full_search(F):
     # a query whose probed buckets are all empty returns only padding, also
     # when the workspace still holds an earlier search's candidate counts
