@@ -502,11 +502,13 @@ def main():
                         "ms_per_launch": ms_of["ms_probe_exact"], "launches_per_step": chunks,
                         "bound": "alu"},
         "dedup": hbm("dedup_hash_kernel", "search_kernels.cu", ms_of["ms_dedup"], dedup_b,
-                     "count_entries + scan + dedup_hash tiers + flatten kernels; "
+                     "count_entries + dedup_hash tiers + flatten + item ordering kernels; "
                      "latency-bound bucket walk"),
         "score": hbm({"fp32": "score_kernel", "bf16": "score_bf16_kernel",
                       "fp8": "score_fp8_kernel"}[args.precision], "search_kernels.cu",
-                     ms_of["ms_score"], score_b, "candidate rows streamed once"),
+                     ms_of["ms_score"], score_b,
+                     "one row read per (query, candidate); candidates grouped by row range, so "
+                     "rows shared by the batch's queries come from L2 (frac can exceed 1)"),
         "topk": hbm("topk_kernel", "search_kernels.cu", ms_of["ms_topk"], topk_b,
                     "selection, exact re-scoring of the shortlist"),
     }
