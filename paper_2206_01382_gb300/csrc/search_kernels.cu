@@ -1948,17 +1948,18 @@ constexpr int TK_SLOW = 2048;
 constexpr int SEL_REGS = 16;   // candidates per lane of the register selection
 constexpr int SEL_SLACK = 16;  // extra keys the selection threshold may keep
 
-// Best kp of U <= 32 * SEL_REGS scored candidates by (score desc, id asc),
+// Best kp of U <= 32 * NREG scored candidates by (score desc, id asc),
 // sorted into buf[0..): the score keys sit in registers; a binary search over
 // the 32-bit key finds the largest t with at least kp keys >= t, the keys >= t
 // are compacted into buf and sorted.  Returns min(U, kp), or -1 when ties at
 // t leave more than cap entries (the caller then uses the running buffer).
+template <int NREG>
 __device__ __forceinline__ int select_small(const float* sc, const uint32_t* cid, uint32_t U,
                                             int kp, uint64_t* buf, int cap) {
   const int lane = threadIdx.x & 31;
-  uint32_t key[SEL_REGS];
+  uint32_t key[NREG];
 #pragma unroll
-  for (int j = 0; j < SEL_REGS; ++j) {
+  for (int j = 0; j < NREG; ++j) {
     const uint32_t i = (uint32_t)(j * 32 + lane);
     key[j] = i < U ? float_key(sc[i]) : 0u;   // 0: no entry (below every score key)
   }
@@ -1968,7 +1969,7 @@ __device__ __forceinline__ int select_small(const float* sc, const uint32_t* cid
     // keeps at most kp + SEL_SLACK keys (the sort below orders them anyway)
     uint32_t kmin = 0xFFFFFFFFu, kmax = 0u;
 #pragma unroll
-    for (int j = 0; j < SEL_REGS; ++j) {
+    for (int j = 0; j < NREG; ++j) {
       if (key[j]) kmin = min(kmin, key[j]);
       kmax = max(kmax, key[j]);
     }
@@ -1977,7 +1978,7 @@ __device__ __forceinline__ int select_small(const float* sc, const uint32_t* cid
       const uint32_t mid = lo + (hi - lo + 1u) / 2u;
       unsigned c = 0;
 #pragma unroll
-      for (int j = 0; j < SEL_REGS; ++j) c += key[j] >= mid ? 1u : 0u;
+      for (int j = 0; j < NREG; ++j) c += key[j] >= mid ? 1u : 0u;
       c = __reduce_add_sync(FULL, c);
       if (c >= (unsigned)kp) {
         lo = mid;
@@ -1990,13 +1991,13 @@ __device__ __forceinline__ int select_small(const float* sc, const uint32_t* cid
   }
   unsigned c = 0;
 #pragma unroll
-  for (int j = 0; j < SEL_REGS; ++j) c += key[j] >= t ? 1u : 0u;
+  for (int j = 0; j < NREG; ++j) c += key[j] >= t ? 1u : 0u;
   const unsigned total = __reduce_add_sync(FULL, c);
   if (total > (unsigned)cap) return -1;
   const unsigned lt = (1u << lane) - 1u;
   unsigned n = 0;
 #pragma unroll
-  for (int j = 0; j < SEL_REGS; ++j) {
+  for (int j = 0; j < NREG; ++j) {
     const bool take = key[j] >= t;
     const unsigned m = __ballot_sync(FULL, take);
     if (take) {
@@ -2030,7 +2031,11 @@ topk_kernel(TopkArgs a) {
   const float* qv = a.Q + q * a.ldq;
   const int nf4 = (int)(a.ldq / 4);
   int nk = -1;
-  if (U <= 32u * SEL_REGS) nk = select_small(sc, cid, U, kp, buf, a.cap);
+  // the register selection with as few registers per lane as U needs
+  if (U <= 128u) nk = select_small<4>(sc, cid, U, kp, buf, a.cap);
+  else if (U <= 256u) nk = select_small<8>(sc, cid, U, kp, buf, a.cap);
+  else if (U <= 384u) nk = select_small<12>(sc, cid, U, kp, buf, a.cap);
+  else if (U <= 32u * SEL_REGS) nk = select_small<SEL_REGS>(sc, cid, U, kp, buf, a.cap);
   if (nk < 0) {   // many candidates (or heavy ties): running buffer with compaction
     WarpTop wt;
     wt.init(buf, a.cap, kp);
