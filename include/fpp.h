@@ -23,9 +23,11 @@
  *    with cudaPointerGetAttributes and copies as needed.  Device pointers
  *    must be 4-byte aligned.
  *  - Results are complete when the call returns, except when the caller
- *    passes a non-NULL stream in fpp_search_opts AND both result pointers
- *    are device memory: then the results are complete once that stream has
- *    reached the call's point (the call itself does not synchronise).
+ *    passes a non-NULL stream in fpp_search_opts, no stats, and both result
+ *    pointers are device memory or page-locked (pinned) host memory: then
+ *    the results are complete once that stream has reached the call's point
+ *    (the call itself does not synchronise, and device-side error flags are
+ *    not reported).
  *  - An fpp_index is immutable after fpp_build.  Concurrent searches on one
  *    index from several host threads are serialised by a per-index lock.
  *  - With precision FPP_FP32, decisions (bucket ids, probe sets, candidate

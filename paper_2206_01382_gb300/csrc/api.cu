@@ -30,6 +30,17 @@ std::atomic<uint64_t>& launch_counter() { return g_launches; }
 
 namespace {
 
+// Page-locked (pinned) host memory: device copies to it are asynchronous.
+bool is_pinned_host(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes at;
@@ -1070,23 +1081,24 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
     }
   }
   FPP_TRY(ix->ws.mark_done(st));
-  const bool need_sync = !dev_out || o->stream == nullptr || stats != nullptr;
-  unsigned long long hs[8] = {0};
+  // with a stream and no stats the call returns without waiting when the
+  // outputs are device memory or page-locked host memory (the copies back
+  // are ordered on the stream); error flags are then not read
+  const bool out_async = dev_out || (is_pinned_host(ids) && is_pinned_host(scores));
+  const bool need_sync = !out_async || o->stream == nullptr || stats != nullptr;
+  unsigned long long hs[16] = {0};
   if (need_sync) {
-    FPP_CUDA(cudaMemcpyAsync(hs, ix->ws.stats.p, 8 * 8, cudaMemcpyDeviceToHost, st));
+    // counters, the top-k flag (slot 5) and the projection's wait flag (slot 9)
+    FPP_CUDA(cudaMemcpyAsync(hs, ix->ws.stats.p, 16 * 8, cudaMemcpyDeviceToHost, st));
     FPP_CUDA(cudaStreamSynchronize(st));
     if (hs[5]) {
       set_error("search: top-k re-check capacity exceeded");
       return FPP_EINTERNAL;
     }
-    FPP_CUDA(cudaMemcpyAsync(hs, ix->ws.stats.as<unsigned long long>() + 9, 8, cudaMemcpyDeviceToHost, st));
-    FPP_CUDA(cudaStreamSynchronize(st));
-    if (hs[0]) {
+    if (hs[9]) {
       set_error("search: a bounded wait in the projection kernel ran out");
       return FPP_ETIMEOUT;
     }
-    FPP_CUDA(cudaMemcpyAsync(hs, ix->ws.stats.p, 8 * 8, cudaMemcpyDeviceToHost, st));
-    FPP_CUDA(cudaStreamSynchronize(st));
   }
   if (timing)
     for (auto& e : ev) cudaEventDestroy(e);
