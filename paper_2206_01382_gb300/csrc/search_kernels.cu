@@ -1728,7 +1728,7 @@ score_kernel(ScoreArgs a) {
       for (int u = 0; u < U; ++u) {
         const int r = r0 + u * RPP + grp;
         ok[u] = (uint32_t)r < item.len;
-        id[u] = ok[u] ? __ldg(ids + r) : 0u;
+        id[u] = ok[u] ? __ldcs(ids + r) : 0u;   // streamed: keep L2 for the rows
       }
       float p[U];
 #pragma unroll
@@ -1766,7 +1766,7 @@ score_kernel(ScoreArgs a) {
         float f = p[u];
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) f += __shfl_xor_sync(FULL, f, o);
-        if (ok[u] && sub == 0) out[r0 + u * RPP + grp] = f;
+        if (ok[u] && sub == 0) __stcs(out + r0 + u * RPP + grp, f);
       }
     }
     item = nxt;
@@ -1801,7 +1801,7 @@ score_bf16_kernel(ScoreArgs a) {
       for (int u = 0; u < U; ++u) {
         const int r = r0 + u * RPP + grp;
         ok[u] = (uint32_t)r < item.len;
-        id[u] = ok[u] ? __ldg(ids + r) : 0u;
+        id[u] = ok[u] ? __ldcs(ids + r) : 0u;   // streamed: keep L2 for the rows
       }
       float p[U];
 #pragma unroll
@@ -1843,7 +1843,7 @@ score_bf16_kernel(ScoreArgs a) {
         float f = p[u];
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) f += __shfl_xor_sync(FULL, f, o);
-        if (ok[u] && sub == 0) out[r0 + u * RPP + grp] = f;
+        if (ok[u] && sub == 0) __stcs(out + r0 + u * RPP + grp, f);
       }
     }
     item = nxt;
