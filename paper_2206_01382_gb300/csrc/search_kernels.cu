@@ -1175,13 +1175,15 @@ __global__ void query_norms_kernel(const float* __restrict__ Q, int64_t m, int64
 // inserts) and the bandwidth-bound part (streaming candidate rows) each get
 // a launch shaped for them:
 //  count_entries  warp per query: bucket entries E_q of its probed buckets;
-//                 an exclusive scan gives each query a region of E_q slots;
-//  dedup          CTA per query with E_q <= 16,384 (three sizes): walks the kept ids of its
-//                 buckets, inserts them into a shared-memory hash set, writes
-//                 the ids seen first to the front of its region and appends
-//                 work items of <= ITEM ids; larger queries are copied
-//                 without de-duplication (flatten_kernel);
-//  score          flat over work items: every candidate row is read once
+//                 each CTA takes consecutive regions of E_q slots for its
+//                 queries from one global counter;
+//  dedup          CTA per query with E_q <= 16,384 (two sizes): walks the
+//                 kept ids of its buckets, inserts them into a shared-memory
+//                 hash set, writes the ids seen first to its region (grouped
+//                 by row range) and appends work items of <= ITEM ids; larger
+//                 queries are copied without de-duplication (flatten_kernel);
+//  order          the work items sorted by the row range of their ids;
+//  score          flat over work items: one row read per (query, candidate)
 //                 with coalesced float4 loads, G lanes per row and 16 rows in
 //                 flight per warp (FP32 scores, error <= gamma_d);
 //  topk           warp per query: best k of its candidates by (score desc,
@@ -1189,7 +1191,7 @@ __global__ void query_norms_kernel(const float* __restrict__ Q, int64_t m, int64
 
 constexpr int DW = 8;                           // warps per flatten CTA
 constexpr int HS_SMALL = 4096;                  // hash slots of the small-query CTAs
-constexpr int HS_BIG = 32768;                   // hash slots of the mid-size-query CTAs
+constexpr int HS_BIG = 32768;                   // hash slots of the larger-query CTAs
 constexpr int HMAX_SMALL = 3072;                // entries of the small-query tier (the distinct
                                                 // ids, about 40% of them, fill a fraction of it)
 constexpr int HMAX_BIG = HS_BIG / 2;            // larger queries are not de-duplicated
