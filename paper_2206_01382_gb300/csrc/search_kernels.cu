@@ -283,9 +283,13 @@ template <int S>
 __global__ void __launch_bounds__(PROBE_WARPS * 32)
 probe_kernel(ProbeArgs a, int pmax) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned s_cnt, s_base;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t w = (int64_t)blockIdx.x * PROBE_WARPS + wid;
-  if (w >= a.mq * a.nt) return;
+  if (threadIdx.x == 0) s_cnt = 0u;
+  __syncthreads();
+  const int64_t w0 = (int64_t)blockIdx.x * PROBE_WARPS + wid;
+  const bool live = w0 < a.mq * a.nt;
+  const int64_t w = live ? w0 : 0;   // a dead warp works on item 0 and stores nothing
   const int64_t q = w / a.nt;
   const int tl = (int)(w % a.nt);
   const int t = a.tb + tl;
@@ -344,11 +348,21 @@ probe_kernel(ProbeArgs a, int pmax) {
     const float need = (2.f * eps + 6.0e-8f * (fabsf(sP) + fabsf(sP1))) * 1.001f + 1e-30f;
     certain = (sP - sP1) > need;
   }
-  if (certain) {
+  if (live && certain) {
     uint32_t* dst = a.out + (q * a.nt + tl) * (int64_t)a.probes;
     for (int p = lane; p < P; p += 32) dst[p] = 0xFFFFFFFFu - (uint32_t)pout[p];
-  } else if (lane == 0) {
-    const unsigned slot = atomicAdd(a.recheck_count, 1u);
+  }
+  // recheck slots: counted in shared memory, one global reservation per CTA
+  const bool rc = live && !certain && lane == 0;
+  const unsigned my = rc ? atomicAdd(&s_cnt, 1u) : 0u;
+  __syncthreads();
+  if (threadIdx.x == 0 && s_cnt) {
+    s_base = atomicAdd(a.recheck_count, s_cnt);
+    if (a.rechecks) atomicAdd(a.rechecks, (unsigned long long)s_cnt);
+  }
+  __syncthreads();
+  if (rc) {
+    const unsigned slot = s_base + my;
     a.recheck[slot] = (uint32_t)(q * a.nt + tl);
     if (a.recheck_s) {   // the boundary the window pass re-decides (NaN: none)
       const bool have = boundary && C >= Tsel;
@@ -358,7 +372,6 @@ probe_kernel(ProbeArgs a, int pmax) {
       a.recheck_s[4 * slot + 2] = signed_entry(lists, 0, D).v;
       a.recheck_s[4 * slot + 3] = signed_entry(lists + LIST_CAP, 0, D).v;
     }
-    if (a.rechecks) atomicAdd(a.rechecks, 1ull);
   }
 }
 
@@ -371,8 +384,12 @@ constexpr int SMALL_E = 8;
 template <int SE>
 __global__ void __launch_bounds__(256)
 probe_small_kernel(ProbeArgs a) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= a.mq * a.nt) return;
+  __shared__ unsigned s_cnt, s_base;
+  if (threadIdx.x == 0) s_cnt = 0u;
+  __syncthreads();
+  const int64_t idx0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = idx0 < a.mq * a.nt;
+  const int64_t idx = live ? idx0 : 0;   // a dead thread works on item 0 and stores nothing
   const int64_t q = idx / a.nt;
   const int tl = (int)(idx % a.nt);
   const int t = a.tb + tl;
@@ -433,16 +450,22 @@ probe_small_kernel(ProbeArgs a) {
     const float need = (2.f * eps + 6.0e-8f * (fabsf(sP) + fabsf(sP1))) * 1.001f + 1e-30f;
     certain = (sP - sP1) > need;
   }
-  if (certain) {
+  if (live && certain) {
     uint32_t* dst = a.out + idx * (int64_t)a.probes;
 #pragma unroll
     for (int e = 0; e < SE; ++e)
       if (e < P) dst[e] = 0xFFFFFFFFu - (uint32_t)best[e];
-  } else {
-    const unsigned slot = atomicAdd(a.recheck_count, 1u);
-    a.recheck[slot] = (uint32_t)idx;
-    if (a.rechecks) atomicAdd(a.rechecks, 1ull);
   }
+  // recheck slots: counted in shared memory, one global reservation per CTA
+  const bool rc = live && !certain;
+  const unsigned my = rc ? atomicAdd(&s_cnt, 1u) : 0u;
+  __syncthreads();
+  if (threadIdx.x == 0 && s_cnt) {
+    s_base = atomicAdd(a.recheck_count, s_cnt);
+    if (a.rechecks) atomicAdd(a.rechecks, (unsigned long long)s_cnt);
+  }
+  __syncthreads();
+  if (rc) a.recheck[s_base + my] = (uint32_t)idx;
 }
 
 // ---------------------------------------------------------------- exact pass
