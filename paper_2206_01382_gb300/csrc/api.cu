@@ -246,7 +246,10 @@ fpp_status project_rows(const fpp_index* ix, const float* src, int64_t rc, DevBu
 
 // List length of the fused projection epilogue for a probe budget, or 0
 // when the projections must be stored (D must divide 256, and the P + 1
-// best entries of a list must lie on q's side of every hash).
+// best entries of a list must lie on q's side of every hash).  One probe
+// per table still takes two keys: the window pass re-scores both when the
+// first two are closer than the error bound (with one key and the cut,
+// every such item went to the full pass).
 int fused_list_len(const fpp_index* ix, int pmax) {
   if (256 % ix->D != 0 || pmax + 1 > ix->D) return 0;
   return tc_list_len(pmax + 1);

@@ -1027,16 +1027,25 @@ __device__ __forceinline__ float pair_value_fp32(const ProbeArgs& a, int64_t q, 
   if (a.P) {
     p = a.P[q * a.ldp + (int64_t)(2 * tl + j) * D + i];
   } else {
-    // list mode: the entry of wedge h is among the hash's EL best keys
+    // list mode: the entry of wedge h is normally among the hash's EL best
+    // keys; one the exact pass took from outside the list is projected here
+    // (a sequential FP32 dot product: error below gamma |q| |r|)
     const uint64_t* L = a.lists + ((q * a.nt + tl) * 2 + j) * (int64_t)(a.EL + 1);
+    bool found = false;
     p = 0.f;
     for (int e = 0; e < a.EL; ++e) {
       const uint64_t k = L[e];
       if (k && (0xFFFFFFFFu - (uint32_t)k) % (uint32_t)D == i) {
         const float v = __uint_as_float((uint32_t)(k >> 32) - 1u);
         p = (0xFFFFFFFFu - (uint32_t)k) < (uint32_t)D ? v : -v;
+        found = true;
         break;
       }
+    }
+    if (!found) {
+      const float* qv = a.Q + q * a.ldq;
+      const float* rv = a.R + ((int64_t)(2 * (a.tb + tl) + j) * D + i) * a.ldr;
+      for (int c = 0; c < a.d; ++c) p = fmaf(qv[c], rv[c], p);
     }
   }
   return h < (uint32_t)D ? p : -p;

@@ -411,10 +411,11 @@ def test_centering_parity(F, given_c):
         assert c_ >= 0.8 * len(res)
 
 
-@pytest.mark.parametrize("Qp,L,D", [(12, 6, 16), (40, 10, 8), (200, 4, 64)])
+@pytest.mark.parametrize("Qp,L,D", [(1, 8, 16), (12, 6, 16), (40, 10, 8), (200, 4, 64)])
 def test_global_probes_parity(F, Qp, L, D):
     # qProbes over all tables together (Sections 2.2 and 4), list mode
-    # (small per-table cap) and stored projections (large)
+    # (small per-table cap; Qp = 1 caps every table at one probe) and stored
+    # projections (large)
     X, Q = W.small_mixture(6000, 60, 32, 64, 0.25, 96 + Qp)
     ix_o = O.build_index(X, L, D, 0.3, seed=14)
     ix_g = F.Index(X, L, D, 0.3, seed=14)
