@@ -60,7 +60,11 @@ struct __align__(8) TcShared {
   uint32_t tmem_base;
   int abort;
   // list mode with D = 256: the second column half of every row hands its
-  // partial top list (up to 8 packed keys and the cut) to the first half
+  // partial top list (up to 8 packed keys and the cut) to the first half,
+  // per TMEM lane quarter; xfull completes when the second half has
+  // written, xempty when the first half has read
+  uint64_t xfull[4];
+  uint64_t xempty[4];
   uint32_t xk[4][32][9];
 };
 
@@ -180,6 +184,27 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
       : "memory");
 }
 
+// 16 consecutive columns of the warp's 32 TMEM lanes (one per thread).
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.wait::ld.sync.aligned;"
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+        "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+        "+r"(r[14]), "+r"(r[15])
+      :
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
   asm volatile(
@@ -262,6 +287,10 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       mbar_init(&sh->tfull[b], 1);
       mbar_init(&sh->tempty[b], EPI_WARPS);
     }
+    for (int qq = 0; qq < 4; ++qq) {
+      mbar_init(&sh->xfull[qq], 1);
+      mbar_init(&sh->xempty[qq], 1);
+    }
     sh->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -342,6 +371,17 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       const int row = m0 + quarter * 32 + lane;
       const uint32_t taddr = tmem + (uint32_t)(b * TC_BN) + ((uint32_t)(quarter * 32) << 16);
       const int cbeg = half * (TC_BN / 2), cend = cbeg + TC_BN / 2;
+      // the accumulator buffer goes back to the MMA warp once the warp's
+      // TMEM loads have completed (the wide list path does so before its
+      // last chunk, sign fix-up, merge and stores)
+      bool released = false;
+      auto release = [&]() {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh->tempty[b]);
+        released = true;
+      };
+      bool ok = true;
       if (EL == 0) {
         for (int c0 = cbeg; c0 < cend; c0 += 32) {
           float v[32];
@@ -379,26 +419,53 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
           }
           tk[EL] = max(tk[EL], x);
         };
-        uint32_t sg[4];
-        uint32_t ra[32], rb[32];
-        tmem_ld32_async(taddr + (uint32_t)cbeg, ra);
+        uint32_t sg[4] = {0u, 0u, 0u, 0u};
+        // the keys of 16 columns c0 .. c0 + 15 (c0 = 16 c): one LOP3 per
+        // value, the signs shifted into sg[c / 2]
+        auto chunk = [&](const uint32_t (&r)[16], const int c) {
+          uint32_t m = sg[c >> 1];
+          if (EL == 2) {
+            // two keys at a time into the running top three (t0 >= t1 >= t2):
+            // with hi >= lo the new second is max(t1, min(t0, hi), lo) and
+            // the new third max(t2, min(t1, hi), min(t0, lo))
+#pragma unroll
+            for (int k = 0; k < 16; k += 2) {
+              const uint32_t u0 = r[k], u1 = r[k + 1];
+              const uint32_t x = (u0 & keep) | (0x80000000u | (uint32_t)(16 * c + k));
+              const uint32_t y = (u1 & keep) | (0x80000000u | (uint32_t)(16 * c + k + 1));
+              m = __funnelshift_l(u0, m, 1);   // m = (m << 1) | sign(u): bit 31 - k is column k's
+              m = __funnelshift_l(u1, m, 1);
+              const uint32_t hi = max(x, y), lo = min(x, y);
+              const uint32_t t2 = __vimax3_u32(tk[2], min(tk[1], hi), min(tk[0], lo));
+              const uint32_t t1 = __vimax3_u32(tk[1], min(tk[0], hi), lo);
+              tk[0] = max(tk[0], hi);
+              tk[1] = t1;
+              tk[2] = t2;
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const uint32_t u = r[k];
+              insert((u & keep) | (0x80000000u | (uint32_t)(16 * c + k)));
+              m = __funnelshift_l(u, m, 1);
+            }
+          }
+          sg[c >> 1] = m;
+        };
+        // eight chunks through two register buffers, the next load in flight
+        // while a chunk is ranked
+        uint32_t ra[16], rb[16];
+        tmem_ld16_async(taddr + (uint32_t)cbeg, ra);
         tmem_wait(ra);
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          if (jj < 3) tmem_ld32_async(taddr + (uint32_t)(cbeg + 32 * (jj + 1)), rb);
-          uint32_t m = 0u;
-#pragma unroll
-          for (int k = 0; k < 32; ++k) {
-            const uint32_t u = ra[k];
-            insert((u & keep) | (0x80000000u | (uint32_t)(32 * jj + k)));
-            m = __funnelshift_l(u, m, 1);   // m = (m << 1) | sign(u): bit 31 - k is column k's
-          }
-          sg[jj] = m;
-          if (jj < 3) {
-            tmem_wait(rb);
-#pragma unroll
-            for (int k = 0; k < 32; ++k) ra[k] = rb[k];
-          }
+        for (int c = 0; c < 8; c += 2) {
+          tmem_ld16_async(taddr + (uint32_t)(cbeg + 16 * c + 16), rb);
+          chunk(ra, c);
+          tmem_wait(rb);
+          if (c < 6) tmem_ld16_async(taddr + (uint32_t)(cbeg + 16 * c + 32), ra);
+          else release();
+          chunk(rb, c + 1);
+          if (c < 6) tmem_wait(ra);
         }
         // signed keys 2^31 | (|p| bits) | h, h = column + D for p < 0
 #pragma unroll
@@ -423,18 +490,25 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
           }
         };
         if (D == TC_BN) {
-          // the hash spans both column halves: merge the second half into the first
-          const int bA = 1 + quarter, bB = 5 + quarter;
+          // the hash spans both column halves: the second half hands its
+          // list to the first (bounded waits: a wait that runs out ends the
+          // CTA's loop like the others)
           if (half == 1) {
+            if (i > 0 && !mbar_wait(&sh->xempty[quarter], (i - 1) & 1, sh, err, 5)) {
+              ok = false;
+            } else {
 #pragma unroll
-            for (int e = 0; e <= EL; ++e) sh->xk[quarter][lane][e] = tk[e];
-            asm volatile("bar.sync %0, 64;" ::"r"(bA) : "memory");
-            asm volatile("bar.sync %0, 64;" ::"r"(bB) : "memory");
+              for (int e = 0; e <= EL; ++e) sh->xk[quarter][lane][e] = tk[e];
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&sh->xfull[quarter]);
+            }
+          } else if (!mbar_wait(&sh->xfull[quarter], i & 1, sh, err, 5)) {
+            ok = false;
           } else {
-            asm volatile("bar.sync %0, 64;" ::"r"(bA) : "memory");
 #pragma unroll
             for (int f = 0; f <= EL; ++f) insert(sh->xk[quarter][lane][f]);
-            asm volatile("bar.sync %0, 64;" ::"r"(bB) : "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh->xempty[quarter]);
             emit();
           }
         } else {
@@ -497,26 +571,9 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             for (int k = 0; k < 32; ++k) ra[k] = rb[k];
           }
         }
-        if (D == TC_BN) {
-          // the hash spans both column halves: merge the second half into the first
-          const int bA = 1 + quarter, bB = 5 + quarter;
-          if (half == 1) {
-#pragma unroll
-            for (int e = 0; e <= EL; ++e) sh->xk[quarter][lane][e] = tk[e];
-            asm volatile("bar.sync %0, 64;" ::"r"(bA) : "memory");
-            asm volatile("bar.sync %0, 64;" ::"r"(bB) : "memory");
-          } else {
-            asm volatile("bar.sync %0, 64;" ::"r"(bA) : "memory");
-#pragma unroll
-            for (int f = 0; f <= EL; ++f) insert(sh->xk[quarter][lane][f]);
-            asm volatile("bar.sync %0, 64;" ::"r"(bB) : "memory");
-            emit(TC_BN - 1);
-          }
-        }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sh->tempty[b]);
+      if (!released) release();
+      if (!ok) break;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
