@@ -28,6 +28,13 @@
  *    the results are complete once that stream has reached the call's point
  *    (the call itself does not synchronise, and device-side error flags are
  *    not reported).
+ *  - Page-locked host queries Q with a non-NULL stream are uploaded on an
+ *    internal copy stream into one of two device query tiles used in turn,
+ *    so that a call's upload overlaps the previous call's search.  That
+ *    upload is not ordered after earlier work on the caller's stream: the
+ *    contents of Q must be final when the call is made and must not change
+ *    until the call's results are complete.  Other host inputs are copied on
+ *    the caller's stream.
  *  - An fpp_index is immutable after fpp_build.  Concurrent searches on one
  *    index from several host threads are serialised by a per-index lock.
  *  - With precision FPP_FP32, decisions (bucket ids, probe sets, candidate

@@ -81,10 +81,27 @@ struct DevBuf {
 };
 
 struct Workspace {
-  DevBuf qpad, qsplit, proj, probes, qnorm, recheck, recheck2, recheck_s, kpq, ppq, out_ids,
-      out_scores, sigproj, qsig,
+  DevBuf qpad, qpad_alt, qsplit, proj, probes, qnorm, recheck, recheck2, recheck_s, kpq, ppq,
+      out_ids, out_scores, sigproj, qsig,
       ecount, eoff, cand, cscores, items, items2, rhist, tkslow, stats;
   const ScoreItem* score_items = nullptr;   // the item list the last batch scored
+  // query tiles: qpad (slot 0) and qpad_alt (slot 1).  Asynchronous calls
+  // with page-locked host queries fill the two in turn on an internal copy
+  // stream, so that a batch's upload overlaps the previous batch's search;
+  // qfree[s] marks the end of the last search that read slot s
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t qready[2] = {nullptr, nullptr}, qfree[2] = {nullptr, nullptr};
+  bool qused[2] = {false, false};
+  int qslot = 0;
+  fpp_status ensure_copy_stream() {
+    if (cstream) return FPP_OK;
+    FPP_CUDA(cudaStreamCreateWithFlags(&cstream, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      FPP_CUDA(cudaEventCreateWithFlags(&qready[i], cudaEventDisableTiming));
+      FPP_CUDA(cudaEventCreateWithFlags(&qfree[i], cudaEventDisableTiming));
+    }
+    return FPP_OK;
+  }
   // completion of the last call that used this workspace: a call on another
   // stream waits for it before touching the buffers
   cudaEvent_t done = nullptr;
@@ -102,13 +119,24 @@ struct Workspace {
   }
   uint64_t cand_cap = 0;    // candidate slots in cand / cscores
   void release() {
-    for (DevBuf* b : {&qpad, &qsplit, &proj, &probes, &qnorm, &recheck, &recheck2, &recheck_s, &sigproj,
-                      &qsig, &kpq, &ppq,
+    for (DevBuf* b : {&qpad, &qpad_alt, &qsplit, &proj, &probes, &qnorm, &recheck, &recheck2,
+                      &recheck_s, &sigproj, &qsig, &kpq, &ppq,
                       &out_ids, &out_scores, &ecount, &eoff, &cand, &cscores,
                       &items, &items2, &rhist, &tkslow, &stats})
       b->release();
     if (done) cudaEventDestroy(done);
     done = nullptr;
+    if (cstream) {
+      cudaStreamSynchronize(cstream);
+      cudaStreamDestroy(cstream);
+      cstream = nullptr;
+    }
+    for (int i = 0; i < 2; ++i) {
+      if (qready[i]) cudaEventDestroy(qready[i]);
+      if (qfree[i]) cudaEventDestroy(qfree[i]);
+      qready[i] = qfree[i] = nullptr;
+      qused[i] = false;
+    }
   }
 };
 
@@ -758,12 +786,31 @@ enum Stage { kFull = 0, kProbesOnly = 1, kCandidatesOnly = 2 };
 
 fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0, int64_t mc,
                         const SearchPlan& pl, int64_t* ids_dev, float* scores_dev, cudaStream_t st,
-                        int stage, cudaEvent_t* ev) {
+                        int stage, cudaEvent_t* ev, bool ahead = false) {
   const int nt = pl.te - pl.tb;
   const int64_t ldp = round_up(2ll * nt * ix->D, 4);
-  // queries, padded
-  FPP_CUDA(cudaMemcpy2DAsync(ws.qpad.p, ix->dpad * 4, Q + q0 * ix->d, ix->d * 4, ix->d * 4, mc,
-                             cudaMemcpyDefault, st));
+  // queries, padded: on the call's stream, or (ahead) on the copy stream
+  // into the tile the search before last has finished reading
+  const int slot = ahead ? (ws.qslot ^= 1) : 0;
+  float* const qp = slot ? ws.qpad_alt.as<float>() : ws.qpad.as<float>();
+  if (ahead) {
+    if (ws.qused[slot]) FPP_CUDA(cudaStreamWaitEvent(ws.cstream, ws.qfree[slot], 0));
+    FPP_CUDA(cudaMemcpy2DAsync(qp, ix->dpad * 4, Q + q0 * ix->d, ix->d * 4, ix->d * 4, mc,
+                               cudaMemcpyHostToDevice, ws.cstream));
+    FPP_CUDA(cudaEventRecord(ws.qready[slot], ws.cstream));
+    FPP_CUDA(cudaStreamWaitEvent(st, ws.qready[slot], 0));
+  } else {
+    FPP_CUDA(cudaMemcpy2DAsync(qp, ix->dpad * 4, Q + q0 * ix->d, ix->d * 4, ix->d * 4, mc,
+                               cudaMemcpyDefault, st));
+  }
+  // the end of the reads of this tile (every return below)
+  auto tile_read = [&]() -> fpp_status {
+    if (ws.qfree[slot]) {
+      FPP_CUDA(cudaEventRecord(ws.qfree[slot], st));
+      ws.qused[slot] = true;
+    }
+    return FPP_OK;
+  };
   const int32_t* kpq = nullptr;
   const int32_t* ppq = nullptr;
   if (pl.kpq) {
@@ -782,11 +829,11 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   }
   if (ev) FPP_CUDA(cudaEventRecord(ev[0], st));
   const int EL = fused_list_len(ix, pl.pmax);
-  FPP_TRY(project_rows(ix, ws.qpad.as<float>(), mc, ws.qsplit, pl.tb, nt, ws.proj.as<float>(), ldp,
+  FPP_TRY(project_rows(ix, qp, mc, ws.qsplit, pl.tb, nt, ws.proj.as<float>(), ldp,
                        reinterpret_cast<int*>(ws.stats.as<unsigned long long>() + 9), st,
                        EL ? ws.proj.as<uint64_t>() : nullptr, EL));
   if (ev) FPP_CUDA(cudaEventRecord(ev[1], st));
-  FPP_TRY(launch_query_norms(ws.qpad.as<float>(), mc, ix->dpad, ix->d, ws.qnorm.as<float>(), st));
+  FPP_TRY(launch_query_norms(qp, mc, ix->dpad, ix->d, ws.qnorm.as<float>(), st));
   if (pl.sim_keep > 0) {
     // the queries' SimHash signatures from their split pieces
     const int bits = ix->sig_words * 32;
@@ -795,7 +842,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
                        reinterpret_cast<int*>(ws.stats.as<unsigned long long>() + 9), st));
     SignArgs sg{};
     sg.P = ws.sigproj.as<float>(); sg.ldp = bits; sg.rows = mc; sg.words = ix->sig_words;
-    sg.V = ws.qpad.as<float>(); sg.ldv = ix->dpad; sg.vnorm = ws.qnorm.as<float>();
+    sg.V = qp; sg.ldv = ix->dpad; sg.vnorm = ws.qnorm.as<float>();
     sg.R = ix->R; sg.ldr = ix->dpad; sg.gamma = ix->gamma; sg.rsig_max = ix->rsig_max;
     sg.out = ws.qsig.as<uint32_t>();
     FPP_TRY(launch_sign_bits(sg, st));
@@ -804,7 +851,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   pa.P = EL ? nullptr : ws.proj.as<float>(); pa.ldp = ldp; pa.mq = mc;
   pa.lists = EL ? ws.proj.as<uint64_t>() : nullptr; pa.EL = EL;
   pa.trunc = EL ? tc_list_trunc(ix->D) : 0.f;
-  pa.Q = ws.qpad.as<float>(); pa.ldq = ix->dpad; pa.qnorm = ws.qnorm.as<float>();
+  pa.Q = qp; pa.ldq = ix->dpad; pa.qnorm = ws.qnorm.as<float>();
   pa.R = ix->R; pa.ldr = ix->dpad; pa.d = ix->d; pa.D = ix->D; pa.tb = pl.tb; pa.nt = nt;
   if (ix->bpieces == 1) {   // R on the BF16 grid: its first BF16 piece is R itself
     pa.Rb = static_cast<const uint16_t*>(ix->Rs);
@@ -823,7 +870,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   FPP_TRY(launch_probe(pa, st, ev ? ev[4] : nullptr));
   if (pl.global_q > 0) FPP_TRY(launch_global_probes(pa, pl.global_q, st));
   if (ev) FPP_CUDA(cudaEventRecord(ev[2], st));
-  if (stage == kProbesOnly) return FPP_OK;
+  if (stage == kProbesOnly) return tile_read();
   // ---- candidates: count bucket entries, give each query a region, dedup,
   // score, top-k
   unsigned long long* stv = ws.stats.as<unsigned long long>();
@@ -889,12 +936,12 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
     FPP_TRY(launch_simhash_filter(sm, st));
   }
   if (ev) FPP_CUDA(cudaEventRecord(ev[5], st));
-  if (stage == kCandidatesOnly) return FPP_OK;
+  if (stage == kCandidatesOnly) return tile_read();
   ScoreArgs sa{};
   sa.items = score_items; sa.nitems = da.nitems;
   sa.eoff = ws.eoff.as<uint64_t>(); sa.mq = mc;
   sa.cand = ws.cand.as<uint32_t>();
-  sa.X = ix->X; sa.ldx = ix->dpad; sa.Q = ws.qpad.as<float>(); sa.ldq = ix->dpad;
+  sa.X = ix->X; sa.ldx = ix->dpad; sa.Q = qp; sa.ldq = ix->dpad;
   sa.Xb = ix->Xb; sa.ldxb = ix->ldxb;
   sa.Xq = ix->Xq; sa.ldxq = ix->ldxq; sa.xscale = ix->xscale;
   sa.scores = ws.cscores.as<float>();
@@ -904,7 +951,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   TopkArgs ta{};
   ta.mq = mc; ta.eoff = ws.eoff.as<uint64_t>(); ta.ucount = da.ucount; ta.cand = ws.cand.as<uint32_t>();
   ta.scores = ws.cscores.as<float>(); ta.k_pq = kpq; ta.k = pl.k; ta.kmax = pl.kmax;
-  ta.X = ix->X; ta.ldx = ix->dpad; ta.Q = ws.qpad.as<float>(); ta.ldq = ix->dpad; ta.d = ix->d;
+  ta.X = ix->X; ta.ldx = ix->dpad; ta.Q = qp; ta.ldq = ix->dpad; ta.d = ix->d;
   ta.qnorm = ws.qnorm.as<float>(); ta.xmax = ix->xmax; ta.gamma = ix->score_gamma;
   ta.gammaf = (float)(ix->score_gamma * 1.0001);
   ta.kprime = topk_kprime(ix, pl.kmax);
@@ -914,7 +961,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   ta.out_ids = ids_dev; ta.out_scores = scores_dev;
   FPP_TRY(launch_topk(ta, st));
   if (ev) FPP_CUDA(cudaEventRecord(ev[3], st));
-  return FPP_OK;
+  return tile_read();
 }
 
 // Queries per batch: bounded by the projection workspace (the FP32 tile, or
@@ -928,12 +975,29 @@ int64_t chunk_rows(const fpp_index* ix, int nt, int pmax, bool allow_fused = tru
 }
 
 fpp_status prepare_workspace(fpp_index* ix, Workspace& ws, const SearchPlan& pl, int64_t mc,
-                             bool host_out, cudaStream_t st, bool allow_fused = true) {
+                             bool host_out, cudaStream_t st, bool allow_fused = true,
+                             bool two_tiles = false) {
   const int nt = pl.te - pl.tb;
   const int64_t ldp = round_up(2ll * nt * ix->D, 4);
-  const bool qz = ws.qpad.bytes < (size_t)mc * ix->dpad * 4;
-  FPP_TRY(ws.qpad.ensure((size_t)mc * ix->dpad * 4, false, st));
-  if (qz && ix->dpad != ix->d) FPP_CUDA(cudaMemsetAsync(ws.qpad.p, 0, ws.qpad.bytes, st));
+  // query tiles; the pad columns stay zero (the uploads write d columns)
+  if (two_tiles) FPP_TRY(ws.ensure_copy_stream());
+  bool zeroed = false;
+  for (DevBuf* qb : {&ws.qpad, &ws.qpad_alt}) {
+    if (qb == &ws.qpad_alt && !two_tiles) break;
+    const bool qz = qb->bytes < (size_t)mc * ix->dpad * 4;
+    FPP_TRY(qb->ensure((size_t)mc * ix->dpad * 4, false, st));
+    if (qz && ix->dpad != ix->d) {
+      FPP_CUDA(cudaMemsetAsync(qb->p, 0, qb->bytes, st));
+      zeroed = true;
+    }
+  }
+  if (zeroed && ws.cstream) {
+    // uploads on the copy stream start after the zeroing
+    for (int i = 0; i < 2; ++i) {
+      FPP_CUDA(cudaEventRecord(ws.qfree[i], st));
+      ws.qused[i] = true;
+    }
+  }
   const int EL = allow_fused ? fused_list_len(ix, pl.pmax) : 0;
   const size_t tile = EL ? (size_t)mc * 2 * nt * (EL + 1) * 8 : (size_t)mc * ldp * 4;
   FPP_TRY(ws.proj.ensure(tile, false, st));
@@ -1044,7 +1108,10 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
   const bool dev_out = is_device_ptr(ids) && is_device_ptr(scores);
   const int nt = pl.te - pl.tb;
   const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt, pl.pmax), m);
-  FPP_TRY(prepare_workspace(ix, ix->ws, pl, mc, !dev_out, st));
+  // page-locked host queries on a caller's stream: the uploads run ahead on
+  // the workspace's copy stream, two query tiles in turn
+  const bool ahead = st != nullptr && !is_device_ptr(Q) && is_pinned_host(Q);
+  FPP_TRY(prepare_workspace(ix, ix->ws, pl, mc, !dev_out, st, true, ahead));
   FPP_TRY(ix->ws.order_after_last(st));
   if ((o->flags & FPP_SEARCH_GRAPH) && st && dev_out && !stats && is_device_ptr(Q) &&
       (!pl.kpq || pl.kpq_dev) && (!pl.ppq || pl.ppq_dev)) {
@@ -1065,7 +1132,8 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
     const int64_t c = std::min<int64_t>(mc, m - q0);
     int64_t* oid = dev_out ? ids + q0 * pl.kmax : ix->ws.out_ids.as<int64_t>();
     float* osc = dev_out ? scores + q0 * pl.kmax : ix->ws.out_scores.as<float>();
-    FPP_TRY(search_chunk(ix, ix->ws, Q, q0, c, pl, oid, osc, st, kFull, timing ? ev : nullptr));
+    FPP_TRY(search_chunk(ix, ix->ws, Q, q0, c, pl, oid, osc, st, kFull, timing ? ev : nullptr,
+                         ahead));
     if (!dev_out) {
       FPP_CUDA(cudaMemcpyAsync(ids + q0 * pl.kmax, oid, c * pl.kmax * 8, cudaMemcpyDeviceToHost, st));
       FPP_CUDA(cudaMemcpyAsync(scores + q0 * pl.kmax, osc, c * pl.kmax * 4, cudaMemcpyDeviceToHost, st));

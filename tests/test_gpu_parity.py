@@ -215,6 +215,40 @@ def test_device_pointers_and_stream(F):
     assert np.array_equal(gs.cpu().numpy(), hs)
 
 
+@pytest.mark.parametrize("d", [64, 37])
+def test_pinned_host_queries_upload_ahead(F, d):
+    # page-locked host queries on a stream: each call's upload runs ahead on
+    # the index's copy stream into one of two query tiles.  Back-to-back
+    # calls with different queries, one device-query call among them, give
+    # the synchronous results (d = 37: padded tiles, zeroed on first use)
+    X, Q = W.small_mixture(4000, 300, d, 32, 0.25, 330 + d)
+    ix = F.Index(X, 6, 16, 0.3, seed=22)
+    rng = np.random.default_rng(23)
+    batches = [Q[rng.permutation(len(Q))[: 200 + 20 * j]] for j in range(6)]
+    ref = [ix.search(b, 10, 4) for b in batches]
+    s = torch.cuda.Stream()
+    keep, outs = [], []
+    for j, b in enumerate(batches):
+        if j == 3:
+            Qd = torch.from_numpy(b).cuda()
+            gi, gs, _ = F.fpp_search_ex(ix.handle, Qd, k=10, probes=4, stream=s,
+                                        want_stats=False)
+            keep.append(Qd)
+            outs.append((gi, gs))
+            continue
+        qh = torch.from_numpy(b).pin_memory()
+        ih = torch.empty((len(b), 10), dtype=torch.int64).pin_memory()
+        sh = torch.empty((len(b), 10), dtype=torch.float32).pin_memory()
+        F.fpp_search_ex(ix.handle, qh, k=10, probes=4, stream=s, ids=ih, scores=sh,
+                        want_stats=False)
+        keep.append(qh)
+        outs.append((ih, sh))
+    s.synchronize()
+    for (gi, gs), (ri, rs) in zip(outs, ref):
+        assert np.array_equal(gi.cpu().numpy(), ri)
+        assert np.array_equal(gs.cpu().numpy(), rs)
+
+
 def test_empty_query_batch(F):
     w = W.WORKLOADS["tiny"]
     X, Q = W.dataset(w)
