@@ -22,11 +22,13 @@
 //
 // Plain mode (pieces = 1): one BF16 product, for the BF16 precision path.
 //
-// Roles (192 threads): warp 0 issues TMA loads, warp 1 allocates tensor
-// memory and issues the MMAs (one elected lane), warps 2..5 drain the
-// accumulators (warp w reads TMEM lanes 32 (w mod 4) .. +31, i.e. the rows it
-// owns) and store FP32 results.  Every mbarrier wait is bounded; a wait that
-// runs out records an error code and the CTA drains and exits.
+// Roles (320 threads): warp 0 issues TMA loads, warp 1 allocates tensor
+// memory and issues the MMAs (one elected lane), warps 2..9 drain the two
+// accumulator buffers (warp w reads TMEM lanes 32 (w mod 4) .. +31, i.e. the
+// rows it owns, in column half (w - 2) / 4) and store either FP32 results or
+// each hash's best keys (the fused list epilogue).  Every mbarrier wait is
+// bounded; a wait that runs out records an error code and the CTA drains and
+// exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
