@@ -1835,7 +1835,7 @@ score_bf16_kernel(ScoreArgs a) {
       for (int u = 0; u < U; ++u) {
         const int r = r0 + u * RPP + grp;
         ok[u] = (uint32_t)r < item.len;
-        id[u] = ok[u] ? __ldcs(ids + r) : 0u;   // streamed: keep L2 for the rows
+        id[u] = ok[u] ? __ldg(ids + r) : 0u;   // (a streaming hint here measured 30% slower)
       }
       float p[U];
 #pragma unroll
@@ -1877,7 +1877,7 @@ score_bf16_kernel(ScoreArgs a) {
         float f = p[u];
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) f += __shfl_xor_sync(FULL, f, o);
-        if (ok[u] && sub == 0) __stcs(out + r0 + u * RPP + grp, f);
+        if (ok[u] && sub == 0) out[r0 + u * RPP + grp] = f;
       }
     }
     item = nxt;
