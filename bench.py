@@ -121,9 +121,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# headers whose device code the kernels of a source file compile in
+KERNEL_HEADERS = {"search_kernels.cu": ("topk.cuh", "common.cuh"),
+                  "gemm_tc.cu": ("common.cuh",)}
+
+
 def kernel_source_hash(name: str) -> str:
-    p = os.path.join(ROOT, "paper_2206_01382_gb300", "csrc", name)
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    d = os.path.join(ROOT, "paper_2206_01382_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in (name,) + KERNEL_HEADERS.get(name, ()):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def committed_traffic(kernel: str, workload: str, src: str):

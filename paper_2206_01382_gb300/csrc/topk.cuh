@@ -30,6 +30,38 @@ __host__ __device__ constexpr int pow2_ceil(int x) {
 // Bitonic sort of a[0..N) (N a power of two), larger keys first, by one warp.
 __device__ __forceinline__ void warp_sort_desc(uint64_t* a, int N) {
   const int lane = threadIdx.x & 31;
+  if (N <= 64) {
+    // up to 64 keys sorted in registers, key i in e[i / 32] of lane i % 32:
+    // a compare-exchange of (i, i ^ j) keeps the larger key at the lower
+    // index where (i & k) == 0 and at the upper one otherwise; partners
+    // j < 32 sit in other lanes (shuffles), j = 32 in the same lane
+    __syncwarp();
+    uint64_t e0 = lane < N ? a[lane] : 0ull;
+    uint64_t e1 = lane + 32 < N ? a[lane + 32] : 0ull;
+    for (int k = 2; k <= N; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        if (j == 32) {   // k = 64: descending over the whole sequence
+          const uint64_t hi = e0 > e1 ? e0 : e1, lo = e0 > e1 ? e1 : e0;
+          e0 = hi;
+          e1 = lo;
+        } else {
+          const bool lower = (lane & j) == 0;
+          const uint64_t y0 = __shfl_xor_sync(0xffffffffu, e0, j);
+          const bool big0 = lower == ((lane & k) == 0);
+          e0 = big0 ? (e0 > y0 ? e0 : y0) : (e0 < y0 ? e0 : y0);
+          if (N > 32) {
+            const uint64_t y1 = __shfl_xor_sync(0xffffffffu, e1, j);
+            const bool big1 = lower == (((lane + 32) & k) == 0);
+            e1 = big1 ? (e1 > y1 ? e1 : y1) : (e1 < y1 ? e1 : y1);
+          }
+        }
+      }
+    }
+    if (lane < N) a[lane] = e0;
+    if (lane + 32 < N) a[lane + 32] = e1;
+    __syncwarp();
+    return;
+  }
   for (int k = 2; k <= N; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = lane; i < N; i += 32) {
