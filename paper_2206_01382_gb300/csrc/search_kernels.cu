@@ -2008,6 +2008,18 @@ __device__ __forceinline__ int select_small(const float* sc, const uint32_t* cid
       kmax = max(kmax, key[j]);
     }
     uint32_t lo = __reduce_min_sync(FULL, kmin), hi = __reduce_max_sync(FULL, kmax);
+    if (kp <= 32) {
+      // the 32 lane maxima are keys >= the smallest of them, so it keeps at
+      // least kp keys; often it is already a threshold to stop at
+      const uint32_t lm = __reduce_min_sync(FULL, kmax);
+      if (lm > lo) {
+        lo = lm;
+        unsigned c = 0;
+#pragma unroll
+        for (int j = 0; j < NREG; ++j) c += key[j] >= lo ? 1u : 0u;
+        if (__reduce_add_sync(FULL, c) <= (unsigned)(kp + SEL_SLACK)) hi = lo;
+      }
+    }
     while (lo < hi) {
       const uint32_t mid = lo + (hi - lo + 1u) / 2u;
       unsigned c = 0;
