@@ -8,7 +8,7 @@ random vectors r_i (Section 2.2), filter fraction alpha (Section 3.4),
 indexing probes iProbes and limit kappa (Algorithm 1 and Section 3.4),
 query probes P per table, k results.
 
-Readings of passages the paper leaves open (each also listed in the design doc):
+Readings of passages the paper leaves open:
 
 * Hash value encoding (Eq. 1).  A hash returns one of the 2D signed vectors
   +r_i or -r_i.  We number them h = i for +r_i and h = i + D for -r_i.  The
