@@ -364,6 +364,38 @@ def test_recall_monotone_in_probes(tiny_data, tiny_index):
     assert prev > 0.9
 
 
+def test_lemma1_collision_probability_band():
+    # Lemma 1 (Section 2.2, quoted from the Falconn analysis): two unit
+    # vectors at distance r collide under one cross-polytope hash with
+    # probability about D^(-1 / (4 / r^2 - 1)).  The form is asymptotic in D
+    # (lower-order factors), so it pins a loose band; orthogonal vectors
+    # (r = sqrt 2) hash independently over the 2D signed vectors, which pins
+    # 1 / (2D) tightly (a hash that dropped the sign would give 1 / D).
+    rng = np.random.default_rng(11)
+    d, T = 32, 20000
+    p = {}
+    for D in (8, 32):
+        for r in (0.5, 1.0, np.sqrt(2.0)):
+            q = rng.standard_normal((T, d))
+            q /= np.linalg.norm(q, axis=1)[:, None]
+            u = rng.standard_normal((T, d))
+            u -= (u * q).sum(1)[:, None] * q
+            u /= np.linalg.norm(u, axis=1)[:, None]
+            th = 2.0 * np.arcsin(r / 2.0)
+            x = np.cos(th) * q + np.sin(th) * u
+            R = rng.standard_normal((T, D, d))
+            hx = O.cross_polytope_hash(np.einsum("td,tkd->tk", x, R))[0]
+            hq = O.cross_polytope_hash(np.einsum("td,tkd->tk", q, R))[0]
+            p[D, r] = float((hx == hq).mean())
+        assert 0.8 < 2 * D * p[D, np.sqrt(2.0)] < 1.2, (D, p[D, np.sqrt(2.0)])
+        for r in (0.5, 1.0):
+            pred = D ** (-1.0 / (4.0 / r ** 2 - 1.0))
+            assert 0.25 < p[D, r] / pred <= 1.0, (D, r, p[D, r], pred)
+        assert p[D, 0.5] > p[D, 1.0] > p[D, np.sqrt(2.0)]
+    for r in (0.5, 1.0, np.sqrt(2.0)):
+        assert p[8, r] > p[32, r]
+
+
 def test_ceos_projection_preserves_inner_product_order():
     # Lemma 2 (CEOs): on the vector r_1 = argmax |q^T r_i|, x^T r_1 is
     # centred at sgn(q^T r_1) x^T q sqrt(2 ln D).  Loose statistical check
