@@ -151,6 +151,7 @@ class OracleIndex:
     point_buckets: np.ndarray     # int64 [L][n] (iProbes = 1 only, else None)
     hash_flag: np.ndarray         # bool [L][n]: near-tie bucket assignment
     filter_flag: np.ndarray       # bool [L][4D^2]: near-tie filter boundary
+    Xh: np.ndarray | None = None  # FP64 points the tables hash (centered), if not X
 
     @property
     def nbuckets(self) -> int:
@@ -272,7 +273,7 @@ def build_index(X, L: int, D: int, alpha: float, seed: int | None = None,
         if pb is not None:
             pb[t] = b
     return OracleIndex(n, d, L, D, float(alpha), iprobes, kappa, R64, X64,
-                       offsets, ids, counts, pb, hflag, fflag)
+                       offsets, ids, counts, pb, hflag, fflag, Xh if center else None)
 
 
 # ---------------------------------------------------------------------------
@@ -291,22 +292,20 @@ def probe_buckets(index: OracleIndex, q, P: int, tables=None):
     return b, s, margin < NEAR_TIE
 
 
-GLOBAL_PER_TABLE = 128   # at most this many of the global probes come from one table
-
-
 def probe_global(index: OracleIndex, q, Qp: int, tables=None):
     """Global probe budget (qProbes, Sections 2.2 and 4): the Qp best
-    (table, bucket) pairs over all tables by the pair score v1(h1) + v2(h2);
-    ties go to the lower table, then the lower bucket.  Reading: a table
-    offers its best min(Qp, 128, 4D^2) buckets (the per-table cap of the
-    probe ranking); the selection is over those.
+    (table, bucket) pairs over all 4D^2 buckets of every table, ranked by the
+    pair score v1(h1) + v2(h2); ties go to the lower table, then the lower
+    bucket.  A table can give at most Qp of them, so its best min(Qp, 4D^2)
+    pairs are the only ones that can be selected; one more per table is
+    ranked for the boundary flag.
 
     Returns (buckets: one array per table of its selected buckets in rank
     order, flag: near-tie between the Qp-th and (Qp+1)-th pair scores)."""
     q64 = np.asarray(q, dtype=np.float64)
     tsel = np.arange(index.L) if tables is None else np.asarray(tables)
     p = index.R[tsel] @ q64                              # [L', 2, D]
-    T = min(Qp, GLOBAL_PER_TABLE, index.nbuckets)
+    T = min(Qp + 1, index.nbuckets)
     b, s, _ = _top_pairs(_signed_lists(p[:, 0]), _signed_lists(p[:, 1]), T)
     tt = np.repeat(np.arange(len(tsel)), b.shape[1])
     bb, ss = b.reshape(-1), s.reshape(-1)

@@ -35,21 +35,53 @@ def compare_table(ix, t, gpu_off, gpu_ids, exclude):
     for b in np.nonzero((np.diff(off) != np.diff(g_off)) | (off[:-1] != g_off[:-1]))[0]:
         if int(b) not in exclude:
             bad.append(int(b))
-    # same kept counts: compare ids bucket by bucket (order inside a bucket is
-    # filter score desc, id asc on both sides)
+    # same kept counts: compare ids bucket by bucket.  The order inside a
+    # bucket is part of the CSR contract (filter score desc, id asc); two ids
+    # may change places only inside a run of FP64 filter scores whose
+    # neighbours are closer than the near-tie threshold.
     if not bad:
         diff = np.nonzero(ix.ids[t] != gpu_ids.astype(np.int64))[0]
         if diff.size:
             bk = np.searchsorted(off, diff, side="right") - 1
             for b in np.unique(bk):
-                if int(b) not in exclude:
-                    # order within a bucket may swap only on exactly tied scores;
-                    # the kept SET must agree
-                    a = set(ix.bucket_ids(t, int(b)).tolist())
-                    g = set(gpu_ids[off[b]: off[b + 1]].astype(np.int64).tolist())
-                    if a != g:
-                        bad.append(int(b))
+                if int(b) in exclude:
+                    continue
+                a = ix.bucket_ids(t, int(b))
+                g = gpu_ids[off[b]: off[b + 1]].astype(np.int64)
+                if not same_up_to_near_ties(a, g, bucket_filter_scores(ix, t, int(b), a)):
+                    bad.append(int(b))
     return bad
+
+
+def bucket_filter_scores(ix, t, b, ids):
+    """FP64 filter scores of points ``ids`` in bucket b of table t: the
+    bucket's pair score v1(h1) + v2(h2) of each point (Section 3.4 filter,
+    with the signed-wedge values of the probe ranking)."""
+    D = ix.D
+    h1, h2 = b // (2 * D), b % (2 * D)
+    x = (ix.X if ix.Xh is None else ix.Xh)[np.asarray(ids, dtype=np.int64)]
+
+    def v(j, h):
+        p = x @ ix.R[t, j, h % D]
+        return p if h < D else -p
+    return v(0, h1) + v(1, h2)
+
+
+def same_up_to_near_ties(want, got, scores):
+    """True if ``got`` lists the ids of ``want`` in the same order, except
+    that ids inside one run of consecutive ``scores`` (the FP64 keys of
+    ``want`` in its order) closer than NEAR_TIE may appear in any order."""
+    want = np.asarray(want)
+    got = np.asarray(got)
+    if want.shape != got.shape:
+        return False
+    lo = 0
+    for i in range(1, len(want) + 1):
+        if i == len(want) or scores[i - 1] - scores[i] >= O.NEAR_TIE:
+            if set(want[lo:i].tolist()) != set(got[lo:i].tolist()):
+                return False
+            lo = i
+    return True
 
 
 def compare_search(res, gpu_ids, gpu_scores, k, tables, excl_by_table):

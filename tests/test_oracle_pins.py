@@ -249,6 +249,53 @@ def test_multiprobe_indexing_counts():
             assert len(set(ids.tolist())) == len(ids)
 
 
+def _algorithm1_by_enumeration(X, R, alpha_num, alpha_den, iprobes, kappa):
+    """Multi-probe indexing (Algorithm 1) in plain Python loops for one table:
+    each point goes to its iProbes best buckets under the pair score
+    v1(h1) + v2(h2) over all (2D)^2 wedge pairs (ties: lower bucket), with
+    that score as its filter score there; a bucket of B entries keeps its
+    best min(B, max(kappa, ceil(alpha B / iProbes))) by (score desc, id asc).
+    alpha = alpha_num / alpha_den so that the ceil is taken in integers."""
+    D = len(R[0])
+    buckets = {}
+    for pid, x in enumerate(X):
+        x = [float(v) for v in x]
+        p1 = [sum(a * b for a, b in zip(x, r)) for r in R[0]]
+        p2 = [sum(a * b for a, b in zip(x, r)) for r in R[1]]
+        v1 = p1 + [-v for v in p1]
+        v2 = p2 + [-v for v in p2]
+        pairs = sorted((-(v1[a] + v2[b]), a * 2 * D + b)
+                       for a in range(2 * D) for b in range(2 * D))
+        for negs, b in pairs[:iprobes]:
+            buckets.setdefault(b, []).append((negs, pid))
+    kept = {}
+    for b, members in buckets.items():
+        members.sort()
+        B = len(members)
+        c = -((-alpha_num * B) // (alpha_den * iprobes))
+        c = min(B, max(kappa, c))
+        kept[b] = [pid for _, pid in members[:c]]
+    return kept
+
+
+@pytest.mark.parametrize("iprobes,kappa", [(3, 2), (2, 0), (4, 5)])
+def test_multiprobe_kept_set_matches_algorithm1_enumeration(iprobes, kappa):
+    X, _ = W.small_mixture(400, 1, 6, 4, 0.25, 7)
+    L, D = 2, 3
+    R = O.gaussian_rotations(21, L, D, 6).astype(np.float64)
+    ix = O.build_index(X, L, D, 0.5, R=R, iprobes=iprobes, kappa=kappa)
+    checked = 0
+    for t in range(L):
+        want = _algorithm1_by_enumeration(X, R[t], 1, 2, iprobes, kappa)
+        for b in range(ix.nbuckets):
+            got = ix.bucket_ids(t, b).tolist()
+            if ix.filter_flag[t, b] or any(ix.hash_flag[t, i] for i in got):
+                continue
+            assert got == want.get(b, []), (t, b)
+            checked += len(got)
+    assert checked > 0.9 * ix.offsets[:, -1].sum()
+
+
 # ---------------------------------------------------------------- probing
 
 def _pairs_by_enumeration(p1, p2, P):
@@ -418,6 +465,53 @@ def test_ceos_projection_preserves_inner_product_order():
     assert 0.8 * c * math.sqrt(2 * math.log(D)) < mean < 1.2 * c * math.sqrt(2 * math.log(D))
 
 
+def test_theorem1_keep_rates():
+    # Theorem 1 (Section 3.3): with r_1 the signed random vector the query
+    # hashes to, the threshold t = (1 - r^2 / 2) sqrt(2 ln D) keeps a point
+    # at distance r with probability about 1/2 and one at distance >= c r
+    # with probability at most q2 = exp(-g^2 / 2) / (g sqrt(2 pi)),
+    # g = c r (1 - 1/c^2) / sqrt(4 - c^2 r^2) sqrt(2 ln D).  The statement is
+    # asymptotic in D: at D = 256 the near rate sits a little below 1/2.
+    # The oracle's hash picks r_1 and its signed lists give x^T r_1, so a
+    # wrong sign or a wrong argmax in either sends the near rate to ~0.
+    rng = np.random.default_rng(5)
+    d, D, T = 64, 256, 4000
+    for r, c in ((1.0, 1.3), (0.8, 1.5)):
+        q = rng.standard_normal((T, d))
+        q /= np.linalg.norm(q, axis=1)[:, None]
+
+        def at(dist):
+            u = rng.standard_normal((T, d))
+            u -= (u * q).sum(1)[:, None] * q
+            u /= np.linalg.norm(u, axis=1)[:, None]
+            th = 2.0 * np.arcsin(dist / 2.0)
+            return np.cos(th) * q + np.sin(th) * u
+
+        x, y = at(r), at(c * r)
+        R = rng.standard_normal((T, D, d))
+        h, _, _ = O.cross_polytope_hash(np.einsum("td,tkd->tk", q, R))
+        vx = np.take_along_axis(F._signed_lists(np.einsum("td,tkd->tk", x, R)), h[:, None], 1)[:, 0]
+        vy = np.take_along_axis(F._signed_lists(np.einsum("td,tkd->tk", y, R)), h[:, None], 1)[:, 0]
+        t = (1.0 - r * r / 2.0) * math.sqrt(2.0 * math.log(D))
+        g = c * r * (1.0 - 1.0 / c ** 2) / math.sqrt(4.0 - (c * r) ** 2) * math.sqrt(2.0 * math.log(D))
+        q2 = math.exp(-g * g / 2.0) / (g * math.sqrt(2.0 * math.pi))
+        near, far = float((vx >= t).mean()), float((vy >= t).mean())
+        assert 0.33 < near < 0.6, (r, near)
+        assert far < q2, (r, c, far, q2)
+        assert far < 0.5 * near
+
+
+def test_recall_at_by_hand():
+    found = np.array([[1, 2, 3, -1], [5, 6, 7, 8]])
+    truth = np.array([[3, 2, 9, 10], [8, 7, 6, 5]])
+    # k = 4: query 0 finds {2, 3} of 4, query 1 all 4: 6 / 8
+    assert O.recall_at(found, truth, 4) == 0.75
+    # k = 2: {1, 2} vs {3, 2} is 1 hit, {5, 6} vs {8, 7} none: 1 / 4
+    assert O.recall_at(found, truth, 2) == 0.25
+    # padding ids (-1) never count, even against padded truth
+    assert O.recall_at(np.array([[-1, -1]]), np.array([[-1, -1]]), 2) == 0.0
+
+
 def test_centering_transform_pinned():
     # Section 3.4, heuristic (1): c is the mean of the points and x -> x - c,
     # here on values where every step is exact
@@ -493,6 +587,41 @@ def test_global_probes_equal_brute_force_enumeration():
             assert sum(len(x) for x in per) == Qp
 
 
+def test_global_probes_uncapped_past_128_per_table():
+    # qProbes ranks the buckets of all tables together with no per-table
+    # limit: with D = 8 a table has 256 buckets, and budgets above 128 must
+    # take more than 128 from one table when its pairs score highest
+    X, Q = W.small_mixture(300, 5, 10, 8, 0.3, 85)
+    L, D = 3, 8
+    ix = O.build_index(X, L, D, 1.0, seed=9)
+    over_128 = 0
+    for q in Q:
+        q64 = q.astype(np.float64)
+        allp = []
+        for t in range(L):
+            p1 = [float(v) for v in ix.R[t, 0] @ q64]
+            p2 = [float(v) for v in ix.R[t, 1] @ q64]
+            v1 = p1 + [-v for v in p1]
+            v2 = p2 + [-v for v in p2]
+            for h1 in range(2 * D):
+                for h2 in range(2 * D):
+                    allp.append((-(v1[h1] + v2[h2]), t, h1 * 2 * D + h2))
+        allp.sort()
+        for Qp in (129, 300, 700):
+            per, flag = O.probe_global(ix, q, Qp)
+            assert sum(len(x) for x in per) == Qp
+            if flag:
+                continue
+            got = sorted((t, int(b)) for t in range(L) for b in per[t])
+            assert got == sorted((t, b) for _, t, b in allp[:Qp])
+            # each table's buckets come in rank order
+            for t in range(L):
+                mine = [b for _, tt, b in allp[:Qp] if tt == t]
+                assert [int(b) for b in per[t]] == mine
+            over_128 += max(len(x) for x in per) > 128
+    assert over_128 > 0
+
+
 def test_global_probes_all_buckets_is_bruteforce_and_monotone():
     import workloads as W
     X, Q = W.small_mixture(1500, 8, 16, 8, 0.3, 84)
@@ -555,3 +684,29 @@ def test_simhash_keep_all_equals_plain_search(tiny_data, tiny_index):
     for r in res:
         assert r.cand.size <= 50
         assert set(r.ids[r.ids >= 0].tolist()) <= set(r.cand.tolist())
+
+
+def test_parallel_build_equals_serial_build():
+    # the process-pool build runs the same per-table function: identical index
+    from oracle.parallel import build_index_parallel
+    X, _ = W.small_mixture(3000, 1, 16, 8, 0.3, 86)
+    for kw in ({}, {"iprobes": 2, "kappa": 1}, {"center": True}):
+        a = O.build_index(X, 3, 4, 0.3, seed=5, **kw)
+        b = build_index_parallel(X, 3, 4, 0.3, seed=5, workers=2, **kw)
+        assert np.array_equal(a.offsets, b.offsets)
+        assert all(np.array_equal(x, y) for x, y in zip(a.ids, b.ids))
+        assert np.array_equal(a.counts, b.counts)
+        assert np.array_equal(a.hash_flag, b.hash_flag)
+        assert np.array_equal(a.filter_flag, b.filter_flag)
+        if a.point_buckets is not None:
+            assert np.array_equal(a.point_buckets, b.point_buckets)
+
+
+def test_in_bucket_order_comparison_allows_only_near_tie_swaps():
+    from tests import parity as PT
+    want = np.array([5, 3, 9, 1])
+    s = np.array([0.9, 0.5, 0.5 - 1e-8, 0.1])
+    assert PT.same_up_to_near_ties(want, want, s)
+    assert PT.same_up_to_near_ties(want, np.array([5, 9, 3, 1]), s)    # near-tied pair
+    assert not PT.same_up_to_near_ties(want, np.array([3, 5, 9, 1]), s)
+    assert not PT.same_up_to_near_ties(want, np.array([5, 3, 1, 9]), s)
