@@ -127,9 +127,17 @@ typedef struct fpp_search_opts {
   void* stream;               /* cudaStream_t or NULL                         */
   int32_t global_probes;      /* > 0: probe this many buckets per query over
                                  all tables together (qProbes, Sections 2.2
-                                 and 4), the best by pair score, at most
-                                 min(global_probes, 128, 4D^2) from one table;
-                                 probes and probes_per_query are then unused
+                                 and 4): the best (table, bucket) pairs by
+                                 pair score over all 4D^2 buckets of every
+                                 table (ties: lower table, lower bucket).
+                                 Each table offers its best
+                                 min(global_probes, 128, 4D^2) buckets; a
+                                 query that would take more than 128 from one
+                                 table makes the call return FPP_EINVAL (the
+                                 outputs are then not the uncapped selection).
+                                 Such a call always waits for its results and
+                                 never runs as a graph.  probes and
+                                 probes_per_query are then unused
                                  (probes_per_query must be NULL).  0: probes
                                  per table.                                   */
   int32_t simhash_keep;       /* > 0: score only the simhash_keep candidates
@@ -307,9 +315,8 @@ fpp_status fpp_bruteforce(const float* X, int64_t n, int32_t d, const float* Q,
 /* Exact search that allocates nothing.  The paper has no counterpart: this
  * is for callers that cannot allocate device memory when they search, for
  * example because their framework has already reserved the whole GPU for its
- * own allocator, because the implicit device synchronisation of cudaMalloc
- * and cudaFree is too costly on their path, or because they run where CUDA
- * forbids allocation calls (such as a host function enqueued on a stream).
+ * own allocator (so cudaMalloc fails), or because the implicit device
+ * synchronisation of cudaMalloc and cudaFree is too costly on their path.
  * It computes the same result as fpp_bruteforce with the same kernels, but
  * its scratch is a file-scope device array of FPP_STATIC_SCRATCH_BYTES that
  * every GPU which loads libfpp holds until the process exits.

@@ -867,6 +867,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   pa.recheck_s = EL ? nullptr : ws.recheck_s.as<float>();   // pair-window pass (stored projections)
   pa.rechecks = ws.stats.as<unsigned long long>() + 6;
   pa.full_rechecks = ws.stats.as<unsigned long long>() + 7;
+  pa.gcap_flag = ws.stats.as<unsigned long long>() + 13;
   FPP_TRY(launch_probe(pa, st, ev ? ev[4] : nullptr));
   if (pl.global_q > 0) FPP_TRY(launch_global_probes(pa, pl.global_q, st));
   if (ev) FPP_CUDA(cudaEventRecord(ev[2], st));
@@ -1113,7 +1114,7 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
   const bool ahead = st != nullptr && !is_device_ptr(Q) && is_pinned_host(Q);
   FPP_TRY(prepare_workspace(ix, ix->ws, pl, mc, !dev_out, st, true, ahead));
   FPP_TRY(ix->ws.order_after_last(st));
-  if ((o->flags & FPP_SEARCH_GRAPH) && st && dev_out && !stats && is_device_ptr(Q) &&
+  if ((o->flags & FPP_SEARCH_GRAPH) && st && dev_out && !stats && is_device_ptr(Q) && pl.global_q == 0 &&
       (!pl.kpq || pl.kpq_dev) && (!pl.ppq || pl.ppq_dev)) {
     fpp_status gs = FPP_OK;
     if (search_graph(ix, Q, m, o, pl, mc, ids, scores, st, gs)) {
@@ -1156,7 +1157,8 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
   // outputs are device memory or page-locked host memory (the copies back
   // are ordered on the stream); error flags are then not read
   const bool out_async = dev_out || (is_pinned_host(ids) && is_pinned_host(scores));
-  const bool need_sync = !out_async || o->stream == nullptr || stats != nullptr;
+  // a global probe budget always waits: its cap flag decides the status
+  const bool need_sync = !out_async || o->stream == nullptr || stats != nullptr || pl.global_q > 0;
   unsigned long long hs[16] = {0};
   if (need_sync) {
     // counters, the top-k flag (slot 5) and the projection's wait flag (slot 9)
@@ -1169,6 +1171,12 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
     if (hs[9]) {
       set_error("search: a bounded wait in the projection kernel ran out");
       return FPP_ETIMEOUT;
+    }
+    if (hs[13]) {
+      set_error("global_probes: " + std::to_string(hs[13]) +
+                " queries would take more than 128 buckets from one table; the results are not the "
+                "uncapped selection (use a smaller budget or per-table probes)");
+      return FPP_EINVAL;
     }
   }
   if (timing)

@@ -181,6 +181,8 @@ struct ProbeArgs {
                              // projections; 16-byte aligned), or NULL
   unsigned long long* rechecks;  // statistics counter or NULL
   unsigned long long* full_rechecks;  // items of the full pass (statistics) or NULL
+  unsigned long long* gcap_flag;  // global budget: queries whose per-table cap may have
+                                  // bound (some table gave all its `probes` slots), or NULL
 };
 fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_begin = nullptr);
 
@@ -188,7 +190,10 @@ fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_b
 // (a.out, P = a.probes), keeps the Qp best (table, bucket) pairs of every
 // query by pair score (ties: lower table, lower bucket) and marks the rest
 // of each table's slots empty (PROBE_EMPTY).  Exact: a boundary inside the
-// error bound is re-decided from compensated projections.
+// error bound is re-decided from compensated projections.  The selection
+// equals the uncapped one over all 4D^2 buckets of every table unless some
+// table had all of its P offered pairs selected while P < min(Qp, 4D^2);
+// such queries are counted in a.gcap_flag.
 constexpr uint32_t PROBE_EMPTY = 0xFFFFFFFFu;
 fpp_status launch_global_probes(const ProbeArgs& a, int Qp, cudaStream_t st);
 fpp_status launch_query_norms(const float* Q, int64_t m, int64_t ldq, int d, float* out,

@@ -1156,7 +1156,18 @@ global_probes_kernel(ProbeArgs a, int Qp, int npow2) {
     dst[tl * P + slot] = code - (uint32_t)(tl * NB);
   }
   if (tid == 0 && !exact_ok && a.rechecks) atomicAdd(a.rechecks + 1, 1ull);
-  (void)s_tcount;
+  // The per-table offer of P pairs can only change the selection when a
+  // table gave all of them: if the uncapped selection held a pair of table t
+  // ranked below t's P offered ones, fewer than Qp pairs precede it, so all P
+  // offered pairs of t are selected here too.  Such queries are reported.
+  if (a.gcap_flag && (int64_t)P < min((int64_t)Qp, NB)) {
+    if (tid == 0) s_tcount[0] = 0;
+    __syncthreads();
+    for (int t = tid; t < a.nt; t += GP_THREADS)
+      if (tcount[t] >= P) s_tcount[0] = 1;
+    __syncthreads();
+    if (tid == 0 && s_tcount[0]) atomicAdd(a.gcap_flag, 1ull);
+  }
 }
 
 // SimHash signature bits (Section 4: the signatures reuse the index's
@@ -2485,7 +2496,7 @@ fpp_status launch_global_probes(const ProbeArgs& a, int Qp, cudaStream_t st) {
   if (a.mq <= 0) return FPP_OK;
   const int N = a.nt * a.probes;
   const int npow2 = pow2_ceil(N > 1 ? N : 1);
-  const size_t smem = (size_t)npow2 * 8 + (size_t)a.nt * 4 + (size_t)Qp * 4 + 16;
+  const size_t smem = (size_t)npow2 * 8 + (size_t)a.nt * 4 + (size_t)std::min(Qp, N) * 4 + 16;
   if (smem > 200 * 1024) {
     set_error("global probes: tables x per-table budget too large (at most 16,384 pairs)");
     return FPP_EINVAL;

@@ -2,10 +2,9 @@
 //
 // Some callers cannot allocate device memory at the moment they search: a
 // framework that has already reserved the whole GPU for its own caching
-// allocator (so cudaMalloc fails), a latency-critical path that cannot afford
-// the implicit device synchronisation of cudaMalloc/cudaFree, or code that runs
-// where CUDA forbids allocation calls altogether (for instance inside a host
-// function enqueued on a stream).  fpp_bruteforce_static serves them: it runs
+// allocator (so cudaMalloc fails), or a latency-critical path that cannot
+// afford the implicit device synchronisation of cudaMalloc/cudaFree.
+// fpp_bruteforce_static serves them: it runs
 // the same projection GEMM and dense top-k kernels as fpp_bruteforce, but its
 // scratch (the score tile and a few counters) lives in the file-scope array
 // below, which every GPU that loads this library holds until the process exits.

@@ -1,10 +1,10 @@
 """fpp_bruteforce_static: exact search that allocates nothing inside libfpp.
 
 It serves callers that cannot allocate device memory when they search (their
-framework already holds the GPU's memory, cudaMalloc's implicit
-synchronisation is too costly for them, or CUDA forbids allocation where they
-run).  Its results must match those of fpp_bruteforce, which allocates its
-scratch, within the tolerance used by the other parity tests.  The file is
+framework already holds the GPU's memory, or cudaMalloc's implicit
+synchronisation is too costly for them).  Its results must match those of
+fpp_bruteforce, which allocates its scratch, within the tolerance used by the
+other parity tests, and the FP64 brute force of the CPU oracle.  The file is
 named so that pytest collects it last.
 """
 import numpy as np
@@ -48,6 +48,24 @@ def test_static_scratch_matches_allocating_path_on_consecutive_calls(F):
     # holds the first call's contents
     X2, Q2 = W.small_mixture(30001, 77, 32, 64, 0.3, 91)
     _same(F, torch.from_numpy(X2).cuda(), torch.from_numpy(Q2).cuda(), 17)
+
+
+def test_static_scratch_matches_oracle_brute_force(F):
+    import oracle as O
+    X, Q = W.small_mixture(20001, 50, 32, 96, 0.25, 94)
+    gi, gs = F.fpp_bruteforce_static(torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda(), 10)
+    torch.cuda.synchronize()
+    gi, gs = gi.cpu().numpy(), gs.cpu().numpy()
+    oi, osc, flags = O.brute_force(X, Q, 10)
+    compared = 0
+    for i in range(len(Q)):
+        if flags[i]:      # FP64 near-tie at the k-th place: either order is right
+            continue
+        assert np.array_equal(gi[i], oi[i]), i
+        assert np.allclose(gs[i], osc[i], rtol=RTOL, atol=1e-6), i
+        compared += 1
+    print(f"static brute force vs oracle: {compared} compared, {len(Q) - compared} near-tie skipped")
+    assert compared >= 0.9 * len(Q)
 
 
 def test_static_scratch_many_query_chunks(F):
