@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="serving workload: seconds of arrivals per offered rate")
     ap.add_argument("--slots", type=int, default=3, help="serving workload: batches in flight")
+    ap.add_argument("--serve-seconds-default", type=float, default=1.0,
+                    help="default run: seconds of arrivals per offered rate in its serving block")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="default run: skip the serving comparison block")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--graph", action="store_true",
                     help="time the steps as replays of the library's captured search graph")
@@ -149,69 +153,132 @@ def committed_traffic(kernel: str, workload: str, src: str):
     return d.get("bytes_per_launch")
 
 
-_POOL_IX = None
+class OracleSearchPool:
+    """The FP64 oracle's query path in spawned single-threaded processes over
+    one shared copy of a full-size oracle index (points, kept CSR and random
+    vectors in shared memory; each worker promotes the points to FP64 once).
+    The paper parallelises its search over queries (Section 4)."""
+
+    def __init__(self, ix, workers):
+        from multiprocessing import shared_memory
+        self.workers = workers
+        ids = np.concatenate([np.asarray(t, dtype=np.int64) for t in ix.ids])
+        starts = np.concatenate([[0], np.cumsum([len(t) for t in ix.ids])]).astype(np.int64)
+        X32 = ix.X.astype(np.float32)   # the points are FP32 inputs: exact round trip
+        self.blocks, meta = [], {}
+        for name, a in (("X", X32), ("offsets", ix.offsets), ("ids", ids), ("R", ix.R)):
+            shm = shared_memory.SharedMemory(create=True, size=max(a.nbytes, 1))
+            np.ndarray(a.shape, dtype=a.dtype, buffer=shm.buf)[...] = a
+            self.blocks.append(shm)
+            meta[name] = (shm.name, a.shape, a.dtype.str)
+        meta["starts"] = starts
+        meta["shape"] = (ix.n, ix.d, ix.L, ix.D, ix.alpha)
+        self.meta = meta
+        self.pool = None
+
+    def __enter__(self):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                                 "MKL_NUM_THREADS")}
+        for v in saved:
+            os.environ[v] = "1"   # inherited by the spawned workers
+        try:
+            self.pool = cf.ProcessPoolExecutor(self.workers, mp_context=mp.get_context("spawn"),
+                                               initializer=_oracle_worker_init,
+                                               initargs=(self.meta,))
+            # start every worker and load its index before any timing
+            list(self.pool.map(_oracle_worker_ready, range(self.workers)))
+        finally:
+            for v, old in saved.items():
+                if old is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = old
+        return self
+
+    def run(self, Q, ks, ps):
+        """Searches the rows of Q (query i with k = ks[i], P = ps[i]) spread
+        over the workers; returns the wall time in seconds."""
+        c = self.workers
+        jobs = [(Q[i::c], ks[i::c], ps[i::c]) for i in range(c) if len(Q[i::c])]
+        t0 = time.perf_counter()
+        list(self.pool.map(_oracle_worker_search, jobs))
+        return time.perf_counter() - t0
+
+    def __exit__(self, *exc):
+        if self.pool is not None:
+            self.pool.shutdown()
+        for shm in self.blocks:
+            shm.close()
+            shm.unlink()
 
 
-def _pool_init(blob):
-    global _POOL_IX
-    import pickle
-    _POOL_IX = pickle.loads(blob)
+_ORACLE_IX = {}
 
 
-def _pool_search(job):
-    """One worker's share of the oracle queries (single-threaded BLAS)."""
+def _oracle_worker_init(meta):
+    from multiprocessing import shared_memory
+    import oracle as O
+    arrs = {}
+    for name in ("X", "offsets", "ids", "R"):
+        shm_name, shape, dt = meta[name]
+        shm = shared_memory.SharedMemory(name=shm_name)
+        _ORACLE_IX.setdefault("shm", []).append(shm)
+        arrs[name] = np.ndarray(shape, dtype=np.dtype(dt), buffer=shm.buf)
+    n, d, L, D, alpha = meta["shape"]
+    st = meta["starts"]
+    ids = [arrs["ids"][st[t]:st[t + 1]] for t in range(L)]
+    _ORACLE_IX["ix"] = O.OracleIndex(n, d, L, D, alpha, 1, 0, arrs["R"],
+                                     arrs["X"].astype(np.float64), arrs["offsets"], ids,
+                                     None, None, None, None)
+
+
+def _oracle_worker_ready(_):
+    return os.getpid()
+
+
+def _oracle_worker_search(job):
     import oracle as O
     Qs, ks, ps = job
-    t0 = time.perf_counter()
     for q, k, p in zip(Qs, ks, ps):
-        O.search(_POOL_IX, q, int(k), int(p))
-    return len(Qs), time.perf_counter() - t0
+        O.search(_ORACLE_IX["ix"], q, int(k), int(p))
+    return len(Qs)
 
 
-def cpu_baseline(w, X, Q, P, k, n_sample=20000, max_q=100, budget_s=10.0):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload: one
-    query at a time in this process (its query path is single-threaded), then
-    the same queries spread over one spawned single-threaded process per core
-    (the paper parallelises over queries).  value = the all-core figure."""
-    import multiprocessing as mp
-    import pickle
-    import oracle as O
-    ix = O.build_index(X[:n_sample], w.L, w.D, w.alpha, seed=w.rot_seed)
-    kk = np.broadcast_to(np.asarray(k), (len(Q),))
-    pp = np.broadcast_to(np.asarray(P), (len(Q),))
+def oracle_index_full(w, X):
+    """The oracle's index over every point of the workload (its tables built
+    in one spawned process per host core); returns (index, build seconds)."""
+    from oracle.parallel import build_index_parallel
     t0 = time.perf_counter()
-    nq = 0
-    while nq < max_q and time.perf_counter() - t0 < budget_s:
-        O.search(ix, Q[nq], int(kk[nq]), int(pp[nq]))
-        nq += 1
-    qps1 = nq / (time.perf_counter() - t0)
+    ix = build_index_parallel(X, w.L, w.D, w.alpha, seed=w.rot_seed)
+    ix.point_buckets = ix.hash_flag = ix.filter_flag = ix.counts = None   # not used by search
+    return ix, time.perf_counter() - t0
+
+
+def cpu_baseline(w, X, Q, P, k, n1=500, budget_s=20.0):
+    """The FP64 oracle, as it stands, on the same full-size index: the query
+    path on one core (one single-threaded process, n1 queries) and on every
+    host core (one single-threaded process per core; about budget_s of work
+    in all).  value = the all-core figure."""
     cores = os.cpu_count() or 1
-    per = max(1, int(qps1 * budget_s / 2))   # queries per worker: ~half the budget
-    nall = min(len(Q), per * cores)
-    saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
-                                             "MKL_NUM_THREADS")}
-    for v in saved:
-        os.environ[v] = "1"   # inherited by the spawned workers
-    try:
-        jobs = [(Q[i:nall:cores], kk[i:nall:cores], pp[i:nall:cores]) for i in range(cores)]
-        with mp.get_context("spawn").Pool(cores, initializer=_pool_init,
-                                          initargs=(pickle.dumps(ix),)) as pool:
-            pool.map(_pool_search, [(Q[:1], kk[:1], pp[:1])] * cores)   # warm the workers
-            t1 = time.perf_counter()
-            res = pool.map(_pool_search, jobs)
-            wall = time.perf_counter() - t1
-    finally:
-        for v, old in saved.items():
-            if old is None:
-                os.environ.pop(v, None)
-            else:
-                os.environ[v] = old
-    done = sum(r[0] for r in res)
-    return {"value": done / wall, "unit": "queries/s", "cores": cores, "kind": "oracle",
-            "value_1core": qps1,
-            "sample": f"FP64 numpy oracle: index over the first {n_sample} points "
-                      f"(L={w.L}, D={w.D}, alpha={w.alpha}), {done} queries over {cores} "
-                      f"single-threaded processes ({nq} on one core for value_1core) at "
+    ix, build_s = oracle_index_full(w, X)
+    m = len(Q)
+    kk = np.broadcast_to(np.asarray(k), (m,))
+    pp = np.broadcast_to(np.asarray(P), (m,))
+    with OracleSearchPool(ix, 1) as one:
+        one.run(Q[:4], kk[:4], pp[:4])   # warm
+        t1 = one.run(Q[:n1], kk[:n1], pp[:n1])
+    qps1 = n1 / t1
+    nall = int(min(m, max(n1, qps1 * cores * budget_s / 2)))
+    with OracleSearchPool(ix, cores) as pool:
+        pool.run(Q[:cores], kk[:cores], pp[:cores])
+        tall = pool.run(Q[:nall], kk[:nall], pp[:nall])
+    return {"value": nall / tall, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "value_1core": qps1, "oracle_build_s": build_s,
+            "sample": f"FP64 numpy oracle over the full index (n={w.n}, L={w.L}, D={w.D}, "
+                      f"alpha={w.alpha}): the first {nall} queries over {cores} single-threaded "
+                      f"processes ({n1} on one process for value_1core) at "
                       f"{'per-query' if np.ndim(P) else P} probes/table, "
                       f"k={'per-query' if np.ndim(k) else k}"}
 
@@ -224,50 +291,34 @@ def run_reference(args, w):
     # the budget our arm's calibration picks: the smallest of the sweep that
     # reaches recall@10 >= 0.90 (plain1m: 1 probe per table, recall 0.964)
     P = args.probes or w.probes[0]
-    import multiprocessing as mp
-    import pickle
-    import oracle as O
-    n_sample = 20000
     cores = os.cpu_count() or 1
     per_step = 4 * cores   # queries per step, spread over one process per core
-    ix = O.build_index(X[:n_sample], w.L, w.D, w.alpha, seed=w.rot_seed)
-    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[v] = "1"   # single-threaded workers (inherited by the spawned processes)
+    ix, build_s = oracle_index_full(w, X)
     qi = 0
-
-    def step(pool):
-        nonlocal qi
-        idx = [(qi + i) % len(Q) for i in range(per_step)]
-        qi += per_step
-        Qs = Q[idx]
-        ks = np.full(per_step, w.k)
-        ps = np.full(per_step, P)
-        pool.map(_pool_search, [(Qs[c::cores], ks[c::cores], ps[c::cores]) for c in range(cores)])
-
-    with mp.get_context("spawn").Pool(cores, initializer=_pool_init,
-                                      initargs=(pickle.dumps(ix),)) as pool:
+    ks = np.full(per_step, w.k)
+    ps = np.full(per_step, P)
+    with OracleSearchPool(ix, cores) as pool:
+        def step():
+            nonlocal qi
+            idx = [(qi + i) % len(Q) for i in range(per_step)]
+            qi += per_step
+            return pool.run(Q[idx], ks, ps)
         for _ in range(args.warmup):
-            step(pool)
-        times = []
-        for _ in range(args.steps):
-            t0 = time.perf_counter()
-            step(pool)
-            times.append(time.perf_counter() - t0)
+            step()
+        times = [step() for _ in range(args.steps)]
     tot = sum(times)
     qps = per_step * args.steps / tot
+    sample = (f"FP64 numpy oracle over the full index (n={w.n}, L={w.L}, D={w.D}, "
+              f"alpha={w.alpha}, built in {build_s:.0f} s): {per_step} queries per step over "
+              f"{cores} single-threaded processes")
     line = {
         "impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "note": w.note, "probes": P, "k": w.k,
-                   "sample": f"index over the first {n_sample} points, {per_step} queries per "
-                             f"step over {cores} single-threaded processes"},
-        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores,
-                         "kind": "oracle",
-                         "sample": f"FP64 numpy oracle, index over the first {n_sample} points, "
-                                   f"{per_step} queries per step over {cores} single-threaded "
-                                   f"processes"},
+        "config": {"workload": w.name, "note": w.note, "probes": P, "k": w.k, "sample": sample},
+        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -292,14 +343,113 @@ def calibrate_probes(F, ix, Xd, Qd, k, sweep):
     return chosen, recalls, mcal
 
 
-def run_serve(args, w):
-    """Serving workload: requests arrive as a Poisson process at each offered
-    query rate (sizes log-uniform in 1..4096, k in {10, 100}), go through the
-    library's continuous-batching server and are timed from submit to
-    completion (host queries in, host results out).  Then a saturation run
-    submits the same request mix without pacing; its throughput is `value`."""
+def serve_drive(srv, Q, P, t, sizes, ks, paced):
+    """Submits the requests (arrival times t, sizes, k) to the server, paced
+    or not, and times each from submit to completion (host queries in, host
+    results out)."""
     import threading
+    m = Q.shape[0]
+    rids = [None] * len(t)
+    lat = np.zeros(len(t))
+    start = time.perf_counter()
 
+    def submitter():
+        qi = 0
+        for i in range(len(t)):
+            if paced:
+                wait = t[i] - (time.perf_counter() - start)
+                if wait > 0:
+                    time.sleep(wait)
+            nq = int(sizes[i])
+            if qi + nq > m:
+                qi = 0
+            rids[i] = srv.submit(Q[qi:qi + nq], int(ks[i]), P)
+            qi += nq
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    for i in range(len(t)):
+        while rids[i] is None:
+            time.sleep(5e-5)
+        lat[i] = srv.poll(rids[i])[2]
+    th.join()
+    wall = time.perf_counter() - start
+    return {"requests": int(len(t)), "queries": int(sizes.sum()),
+            "qps": float(sizes.sum() / wall),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_request": float(sizes.mean())}
+
+
+def serve_session(F, ix, Q, P, slots, seconds):
+    """Poisson arrivals at each offered query rate (sizes log-uniform in
+    1..4096, k in {10, 100}) through the continuous-batching server, then the
+    same kind of mix unpaced (saturation)."""
+    srv = F.Server(ix, k_max=100, probes_max=P, slots=slots, max_batch=4096)
+    try:
+        t, sizes, ks = W.serve_arrivals(99, 100_000, 0.2)
+        serve_drive(srv, Q, P, t, sizes, ks, paced=False)   # warm-up
+        s0 = srv.stats()
+        rates = {}
+        for ri, rate in enumerate(W.SERVE_RATES):
+            t, sizes, ks = W.serve_arrivals(ri, rate, seconds)
+            r = serve_drive(srv, Q, P, t, sizes, ks, paced=True)
+            r["offered_qps"] = rate
+            rates[str(rate)] = r
+        t, sizes, ks = W.serve_arrivals(len(W.SERVE_RATES), W.SERVE_RATES[-1], seconds)
+        sat = serve_drive(srv, Q, P, t, sizes, ks, paced=False)
+        s1 = srv.stats()
+    finally:
+        srv.close()
+    batches = s1["batches"] - s0["batches"]
+    return {"probes": P, "offered": rates, "saturation": sat,
+            "mean_batch_queries": (s1["queries"] - s0["queries"]) / max(batches, 1),
+            "h2d_bytes": int(sizes.sum() * Q.shape[1] * 4),
+            "d2h_bytes": int((np.asarray(sizes) * np.asarray(ks)).sum() * 12)}
+
+
+def serving_compare(F, w, precision, rerank_k, slots, seconds, probes=0):
+    """The serving workload with candidate rows in ``precision`` against the
+    plain FP32 path under the same request mix, each at its own calibrated
+    probe budget (the smallest of the sweep with recall@10 >= 0.90), with
+    the GPU clocks sampled over both serving windows."""
+    import torch
+    X, Q = W.dataset(w)
+    Xd = torch.from_numpy(X).cuda()
+    Qd = torch.from_numpy(Q[:CALIB_QUERIES]).cuda()
+    sweep = [probes] if probes else list(w.probes)
+    prec = {"fp32": F.FPP_FP32, "bf16": F.FPP_BF16, "fp8": F.FPP_FP8E4M3}[precision]
+    out = {"workload": w.name, "note": w.note, "seconds_per_rate": seconds, "slots": slots}
+    sampler = ClockSampler(torch.cuda.current_device())
+    arms = [(precision, prec)] + ([("fp32", F.FPP_FP32)] if prec != F.FPP_FP32 else [])
+    res = {}
+    for name, pc in arms:
+        tb = time.perf_counter()
+        ix = F.Index(Xd, w.L, w.D, w.alpha, seed=w.rot_seed, precision=pc, rerank_k=rerank_k)
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - tb
+        P, rec, mcal = calibrate_probes(F, ix, Xd, Qd, w.k, sweep)
+        if not res:
+            sampler.start()
+        r = serve_session(F, ix, Q, P, slots, seconds)
+        r.update(precision=name, recall_at_10=rec[P], recall_sweep=rec, recall_sample=mcal,
+                 build_s=build_s)
+        res[name] = r
+        ix.close()
+    out["clocks"] = sampler.stop()
+    out[precision] = res[precision]
+    if "fp32" in res and precision != "fp32":
+        out["fp32_same_mix"] = dict(res["fp32"])
+        out["fp32_same_mix"]["bf16_over_fp32_qps"] = (res[precision]["saturation"]["qps"]
+                                                     / res["fp32"]["saturation"]["qps"])
+    del Xd, Qd
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serve(args, w):
+    """Serving workload alone (``--workload serve2m``): the serving
+    comparison above, its saturation throughput as ``value``, and the gather
+    + score roofline of the served index on one 10,000-query batch."""
     import torch
     import paper_2206_01382_gb300 as F
     from paper_2206_01382_gb300 import _build
@@ -307,108 +457,10 @@ def run_serve(args, w):
     torch.cuda.set_device(0)
     _build.build()
     F.load()
-    X, Q = W.dataset(w)
-    Xd = torch.from_numpy(X).cuda()
-    Qd = torch.from_numpy(Q[:CALIB_QUERIES]).cuda()
-    prec = {"fp32": F.FPP_FP32, "bf16": F.FPP_BF16, "fp8": F.FPP_FP8E4M3}[args.precision]
-    tb = time.perf_counter()
-    ix = F.Index(Xd, w.L, w.D, w.alpha, seed=w.rot_seed, precision=prec, rerank_k=args.rerank_k)
-    torch.cuda.synchronize()
-    build_s = time.perf_counter() - tb
-    P, recalls, mcal = calibrate_probes(F, ix, Xd, Qd, w.k, [args.probes] if args.probes else w.probes)
-    del Xd
-    srv = F.Server(ix, k_max=100, probes_max=P, slots=args.slots, max_batch=4096)
-    m = Q.shape[0]
-
-    def drive(t, sizes, ks, paced, srv=srv, P=P):
-        rids = [None] * len(t)
-        lat = np.zeros(len(t))
-        start = time.perf_counter()
-
-        def submitter():
-            qi = 0
-            for i in range(len(t)):
-                if paced:
-                    wait = t[i] - (time.perf_counter() - start)
-                    if wait > 0:
-                        time.sleep(wait)
-                nq = int(sizes[i])
-                if qi + nq > m:
-                    qi = 0
-                rids[i] = srv.submit(Q[qi:qi + nq], int(ks[i]), P)
-                qi += nq
-
-        th = threading.Thread(target=submitter)
-        th.start()
-        for i in range(len(t)):
-            while rids[i] is None:
-                time.sleep(5e-5)
-            lat[i] = srv.poll(rids[i])[2]
-        th.join()
-        wall = time.perf_counter() - start
-        return {"requests": int(len(t)), "queries": int(sizes.sum()),
-                "qps": float(sizes.sum() / wall),
-                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_request": float(sizes.mean())}
-
-    # warm-up (allocations, first launches)
-    t, sizes, ks = W.serve_arrivals(99, 100_000, 0.2)
-    drive(t, sizes, ks, paced=False)
-    s0 = srv.stats()
-    rates = {}
-    for ri, rate in enumerate(W.SERVE_RATES):
-        t, sizes, ks = W.serve_arrivals(ri, rate, args.serve_seconds)
-        r = drive(t, sizes, ks, paced=True)
-        r["offered_qps"] = rate
-        rates[str(rate)] = r
-    t, sizes, ks = W.serve_arrivals(len(W.SERVE_RATES), W.SERVE_RATES[-1], args.serve_seconds)
-    sat = drive(t, sizes, ks, paced=False)
-    s1 = srv.stats()
-    srv.close()
-    batches = s1["batches"] - s0["batches"]
-    # gather + score roofline of the served index: one 10,000-query batch with
-    # the library's phase timers (k = 10 at the served probe budget)
-    hbm_peak, _, peak_src = peaks()
-    mq = min(10_000, m)
-    Qr = torch.from_numpy(Q[:mq]).cuda()
-    acc = {"ms_gather_score": 0.0, "probes": 0, "entries": 0, "unique": 0}
-    for r in range(4):
-        _, _, st = F.fpp_search_ex(ix.handle, Qr, k=10, probes=P)
-        if r:
-            for key in acc:
-                acc[key] += st[key] / 3
-    row_bytes = (2 * (-(-w.d // 8) * 8) if args.precision == "bf16"
-                 else (-(-w.d // 16) * 16 + 4) if args.precision == "fp8" else 4 * w.d)
-    kprime = max(10 + 16, args.rerank_k if prec != F.FPP_FP32 else 0)
-    gs_bytes = (8 * acc["probes"] + 4 * acc["entries"] + 4 * acc["unique"]
-                + (row_bytes + 8) * acc["unique"] + 4 * w.d * mq
-                + 8 * acc["unique"] + 4 * w.d * kprime * mq + 12 * 10 * mq)
-    gs_gbs = gs_bytes / (acc["ms_gather_score"] / 1e3) / 1e9
-    serve_roofline = {"kernel": "dedup + score + topk (10,000 queries, k = 10)", "bound": "hbm",
-                      "achieved": gs_gbs, "peak": hbm_peak, "unit": "GB/s",
-                      "frac": gs_gbs / hbm_peak, "traffic": None,
-                      "ms_per_launch": acc["ms_gather_score"],
-                      "algorithmic_bytes_per_launch": gs_bytes,
-                      "peak_source": peak_src + " (hbm_gbs, STREAM-style copy)"}
-    del Qr
-    # the plain FP32 path under the same saturation request mix, at its own
-    # calibrated probe budget (recall@10 >= 0.90)
-    fp32_base = None
-    if prec != F.FPP_FP32:
-        ix.close()
-        Xd = torch.from_numpy(X).cuda()
-        ix32 = F.Index(Xd, w.L, w.D, w.alpha, seed=w.rot_seed)
-        P32, rec32, _ = calibrate_probes(F, ix32, Xd, Qd, w.k,
-                                         [args.probes] if args.probes else w.probes)
-        del Xd
-        srv32 = F.Server(ix32, k_max=100, probes_max=P32, slots=args.slots, max_batch=4096)
-        tw, szw, ksw = W.serve_arrivals(99, 100_000, 0.2)
-        drive(tw, szw, ksw, paced=False, srv=srv32, P=P32)
-        sat32 = drive(t, sizes, ks, paced=False, srv=srv32, P=P32)
-        srv32.close()
-        ix32.close()
-        fp32_base = {"precision": "fp32", "probes": P32, "recall_at_10": rec32[P32],
-                     "saturation": sat32, "bf16_over_fp32_qps": sat["qps"] / sat32["qps"]}
+    srv = serving_compare(F, w, args.precision, args.rerank_k, args.slots, args.serve_seconds,
+                          args.probes)
+    main_arm = srv[args.precision]
+    sat = main_arm["saturation"]
     line = {
         "metric": METRIC, "value": sat["qps"], "unit": "queries/s", "n_gpus": 1,
         "steps": len(W.SERVE_RATES) + 1, "warmup": 1, "ms_per_step": None,
@@ -416,20 +468,19 @@ def run_serve(args, w):
         "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "fp8e4m3"}[args.precision],
         "data": "synthetic",
         "config": {"workload": w.name, "note": w.note, "precision": args.precision,
-                   "rerank_k": args.rerank_k if prec != F.FPP_FP32 else None,
-                   "n": w.n, "d": w.d, "L": w.L, "D": w.D, "alpha": w.alpha, "probes": P,
-                   "recall_at_10": recalls[P], "recall_sweep": recalls, "recall_sample": mcal,
-                   "slots": args.slots, "max_batch": 4096, "build_s": build_s,
+                   "rerank_k": args.rerank_k if args.precision != "fp32" else None,
+                   "n": w.n, "d": w.d, "L": w.L, "D": w.D, "alpha": w.alpha,
+                   "probes": main_arm["probes"], "recall_at_10": main_arm["recall_at_10"],
+                   "slots": args.slots, "max_batch": 4096,
                    "l2": "inputs larger than L2 (X is "
                          f"{w.n * w.d * 4 / 2**20:.0f} MiB FP32), no flush"},
-        "serving": {"offered": rates, "saturation": sat,
-                    "mean_batch_queries": (s1["queries"] - s0["queries"]) / max(batches, 1),
-                    "fp32_same_mix": fp32_base},
+        "serving": srv,
         "latency_ms": {"p50": sat["p50_ms"], "p99": sat["p99_ms"]},
-        "roofline": serve_roofline,
+        "clocks": srv["clocks"],
         "e2e": {"value": sat["qps"], "unit": "queries/s",
-                "h2d_bytes_per_step": int(sat["queries"] * w.d * 4),
-                "d2h_bytes_per_step": int((np.asarray(sizes) * np.asarray(ks)).sum() * 12)},
+                "h2d_bytes_per_step": main_arm["h2d_bytes"],
+                "d2h_bytes_per_step": main_arm["d2h_bytes"]},
+        "roofline": None,
         "cpu_baseline": None,
     }
     print(json.dumps(line), flush=True)
@@ -548,6 +599,15 @@ def main():
     ms_per_step = elapsed_ms / args.steps
     qps = world * m / (ms_per_step / 1e3)
 
+    # distinct candidate rows of the first query batch (the floor of the
+    # score kernel's DRAM reads), outside the timed region
+    distinct_rows = None
+    if not per_query:
+        nb = -(-m // max(1, tot["batches"] // PK))
+        cands = F.fpp_debug_candidates(ix.handle, Q[:nb], P)
+        distinct_rows = int(np.unique(np.concatenate(cands)).size) if cands else 0
+        del cands
+
     # per-kernel rooflines (device time measured with CUDA events on the
     # launching stream inside the library, summed over the timed steps;
     # "per launch" = one query batch)
@@ -558,24 +618,33 @@ def main():
     qpl = m / chunks
     d = w.d
     bf16 = args.precision != "fp32"
-    row_bytes = (2 * (-(-d // 8) * 8) + 0 if args.precision == "bf16"
-                 else (-(-d // 16) * 16 + 4) if args.precision == "fp8" else 4 * d)
+    row_bytes = (2 * d if args.precision == "bf16"
+                 else d + 4 if args.precision == "fp8" else 4 * d)
     kprime = max(k + 16, args.rerank_k if bf16 else 0)
     probes_pl, entries_pl, unique_pl = (tot["probes"] / per, tot["entries"] / per,
                                         tot["unique"] / per)
-    # algorithmic bytes per launch: offset pairs of the probed buckets and the
-    # kept ids scanned, written candidates (dedup); candidate rows, their ids,
-    # the scores and the query rows (score); scores and ids read, the exactly
-    # re-scored FP32 rows and the results (top-k)
-    dedup_b = 8 * probes_pl + 4 * entries_pl + 4 * unique_pl
-    score_b = (row_bytes + 8) * unique_pl + 4 * d * qpl
-    topk_b = 8 * unique_pl + 4 * d * kprime * qpl + 12 * k * qpl
-    # projection: BF16 tensor-core products over K padded to 64; the FP32
-    # contraction runs 3 of them when the random vectors are on the BF16 grid
-    # (three query pieces times one vector piece), else 6 (both split)
+    # Algorithmic bytes per launch, as the method defines the traffic of the
+    # gather and score steps (per query: 8 B per probed bucket for its offset
+    # pair, 4 B per kept id scanned, b d B per distinct candidate row with
+    # b = 4 FP32 / 2 BF16 / 1 FP8 plus a 4-byte scale, 12 B per result; the
+    # precision path adds the 4 d B FP32 rows of its re-ranked shortlist).
+    # The per-kernel splits below count the same terms where each kernel
+    # moves them; candidate writes and id/score round trips between kernels
+    # are implementation traffic and are not counted.
+    rerank_b = 4 * d * args.rerank_k * qpl if bf16 else 0.0
+    rows_b = row_bytes * unique_pl
+    algo_b = 8 * probes_pl + 4 * entries_pl + rows_b + 12 * k * qpl + rerank_b
+    dedup_b = 8 * probes_pl + 4 * entries_pl
+    score_b = rows_b
+    topk_b = 12 * k * qpl + rerank_b
+    # projection: the method's work is 2 d FLOPs per (query, random vector);
+    # the tensor cores execute it as BF16 products over K padded to 64, 3 of
+    # them per FP32 product when the random vectors are on the BF16 grid
+    # (three query pieces times one vector piece), else 6
     kpad = -(-d // 64) * 64
     products = 3 if info["r_pieces"] == 1 else 6
-    proj_flops = 2.0 * qpl * kpad * 2 * w.L * w.D * products
+    proj_flops = 2.0 * qpl * d * 2 * w.L * w.D
+    exec_flops = 2.0 * qpl * kpad * 2 * w.L * w.D * products
     ms_of = {key: phase[key] / per for key in phase}
 
     def hbm(name, src, ms, nbytes, note):
@@ -586,13 +655,18 @@ def main():
                 "peak_source": peak_src + " (hbm_gbs, STREAM-style copy)",
                 "traffic": committed_traffic(name, w.name, src)}
 
-    pj_tf = proj_flops / (ms_of["ms_project"] / 1e3) / 1e12
+    pj_s = ms_of["ms_project"] / 1e3
+    pj_tf = proj_flops / pj_s / 1e12
     kernels = {
         "project": {"kernel": "tc_proj_kernel", "ms_per_launch": ms_of["ms_project"],
                     "launches_per_step": chunks, "bound": "tensor", "achieved": pj_tf,
                     "peak": bf16_peak, "unit": "TFLOP/s", "frac": pj_tf / bf16_peak,
+                    "algorithmic_flops_per_launch": proj_flops,
+                    "note": "achieved = the method's 2 m d 2LD FLOPs per launch / time",
+                    "executed_bf16_flops_per_launch": exec_flops,
+                    "executed_tflops": exec_flops / pj_s / 1e12,
+                    "executed_frac": exec_flops / pj_s / 1e12 / bf16_peak,
                     "bf16_products_per_fp32_product": products,
-                    "fp32_equivalent_tflops": pj_tf / products * d / kpad,
                     "peak_source": peak_src + " (bf16_tflops, cuBLAS burst)",
                     "traffic": committed_traffic("tc_proj_kernel", w.name, "gemm_tc.cu")},
         "probe": {"kernel": "probe_small_kernel", "ms_per_launch": ms_of["ms_probe"],
@@ -601,26 +675,37 @@ def main():
                         "ms_per_launch": ms_of["ms_probe_exact"], "launches_per_step": chunks,
                         "bound": "alu"},
         "dedup": hbm("dedup_hash_kernel", "search_kernels.cu", ms_of["ms_dedup"], dedup_b,
-                     "count_entries + dedup_hash tiers + flatten + item ordering kernels; "
-                     "latency-bound bucket walk"),
+                     "count_entries + dedup_hash tiers + flatten + item ordering kernels: "
+                     "8 B per probed bucket + 4 B per kept id scanned"),
         "score": hbm({"fp32": "score_kernel", "bf16": "score_bf16_kernel",
                       "fp8": "score_fp8_kernel"}[args.precision], "search_kernels.cu",
                      ms_of["ms_score"], score_b,
-                     "one row read per (query, candidate); candidates grouped by row range, so "
-                     "rows shared by the batch's queries come from L2 (frac can exceed 1)"),
+                     "one row per (query, distinct candidate); rows shared by the batch's "
+                     "queries come from L2, so frac can exceed 1: see dram_vs_distinct_rows"),
         "topk": hbm("topk_kernel", "search_kernels.cu", ms_of["ms_topk"], topk_b,
-                    "selection, exact re-scoring of the shortlist"),
+                    "12 B per result (+ the re-ranked FP32 shortlist rows)"),
     }
+    if distinct_rows is not None:
+        sc = kernels["score"]
+        sc["distinct_rows_per_launch"] = distinct_rows
+        sc["distinct_row_bytes_per_launch"] = distinct_rows * row_bytes
+        if sc["traffic"]:
+            sc["dram_vs_distinct_rows"] = sc["traffic"] / (distinct_rows * row_bytes)
     gs_ms = ms_of["ms_gather_score"]
-    gs_gbs = (dedup_b + score_b + topk_b) / (gs_ms / 1e3) / 1e9
+    gs_gbs = algo_b / (gs_ms / 1e3) / 1e9
     kernels["gather_score"] = {"kernel": "dedup + score + topk", "ms_per_launch": gs_ms,
                                "bound": "hbm", "achieved": gs_gbs, "peak": hbm_peak,
                                "unit": "GB/s", "frac": gs_gbs / hbm_peak,
-                               "algorithmic_bytes_per_launch": dedup_b + score_b + topk_b}
+                               "algorithmic_bytes_per_launch": algo_b,
+                               "peak_source": peak_src + " (hbm_gbs, STREAM-style copy)",
+                               "note": "8 L P + 4 E + b d U + 12 k bytes per query "
+                                       "over the dedup + score + top-k time"}
     # the roofline line is the single kernel with the largest device time
     dom = max(("project", "dedup", "score", "topk"), key=lambda p: kernels[p]["ms_per_launch"])
     roof = {kk: kernels[dom][kk] for kk in ("kernel", "bound", "achieved", "peak", "unit", "frac",
                                             "traffic", "peak_source")}
+    if dom == "project":
+        roof["executed_frac"] = kernels[dom]["executed_frac"]
     phases = kernels
 
     # end to end: host (pinned) queries in, host results out, through the C ABI
@@ -673,6 +758,16 @@ def main():
     if per_query:
         recalls = {"per-query": recall_k}
 
+    # the serving comparison (BF16 rows against plain FP32 under one request
+    # mix, each at recall@10 >= 0.90) on the serving workload, one GPU only
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        ix.close()
+        del Xd, Qd, ids, sc
+        torch.cuda.empty_cache()
+        serving = serving_compare(F, W.WORKLOADS["serve2m"], "bf16", 100, args.slots,
+                                  args.serve_seconds_default)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, X, Q, ppq if per_query else P, kpq if per_query else k)
@@ -701,6 +796,7 @@ def main():
             "roofline": roof,
             "phases": phases,
             "search_stats_per_step": {kk: v / K for kk, v in tot.items()},
+            "serving": serving,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,

@@ -84,19 +84,68 @@ def same_up_to_near_ties(want, got, scores):
     return True
 
 
-def compare_search(res, gpu_ids, gpu_scores, k, tables, excl_by_table):
+def ambiguous_ids(ix, t, b, gpu_point_buckets=None):
+    """Points whose presence among the kept ids of bucket b of table t an
+    FP64 near-tie leaves open: the points whose hash is a near-tie and that
+    either side places in b, and the points around the filter cut, over the
+    range of kept counts those points can cause (plus any filter-score
+    near-tie at the cut)."""
+    pb = ix.point_buckets[t]
+    members = np.nonzero(pb == b)[0]
+    flagged = np.nonzero(ix.hash_flag[t])[0]
+    fl = flagged[pb[flagged] == b]
+    if gpu_point_buckets is not None:
+        fl = np.union1d(fl, flagged[np.asarray(gpu_point_buckets)[flagged] == b])
+    pool = np.union1d(members, fl)
+    if pool.size == 0:
+        return pool
+    sc = bucket_filter_scores(ix, t, b, pool)
+    order = np.lexsort((pool, -sc))
+    pool, sc = pool[order], sc[order]
+    fixed = np.setdiff1d(members, fl).size
+    kmin = int(O.keep_count(fixed, ix.alpha, ix.iprobes, ix.kappa))
+    kmax = int(O.keep_count(pool.size, ix.alpha, ix.iprobes, ix.kappa))
+    lo, hi = max(kmin - 1, 0), min(kmax + 1, pool.size)
+    # widen over filter-score near-ties at either end of the window
+    while lo > 0 and sc[lo - 1] - sc[lo] < O.NEAR_TIE:
+        lo -= 1
+    while hi < pool.size and sc[hi - 1] - sc[hi] < O.NEAR_TIE:
+        hi += 1
+    return np.union1d(fl, pool[lo:hi])
+
+
+def topk_determined(ix, q, cand, amb, k):
+    """True if every candidate set between cand minus amb and cand plus amb
+    has the same top-k (then it is the oracle's top-k of cand)."""
+    q64 = np.asarray(q, dtype=np.float64)
+    lo = np.setdiff1d(cand, amb)
+    hi = np.union1d(cand, amb)
+    a, _, fa = O.falconn.topk_exact(lo, ix.X[lo] @ q64, k)
+    b, _, fb = O.falconn.topk_exact(hi, ix.X[hi] @ q64, k)
+    return not fa and not fb and np.array_equal(a, b)
+
+
+def compare_search(res, gpu_ids, gpu_scores, k, tables, excl_by_table, ambiguous=None, Q=None,
+                   ix=None):
     """Per query: exact ids and scores within SCORE_RTOL unless a flag
     (probe boundary, top-k boundary, or a probed bucket that is excluded)
-    allows another answer.  Returns (n_compared, n_skipped, failures)."""
+    allows another answer.  With ``ambiguous`` ((t, b) -> ids, e.g.
+    ambiguous_ids), a query that probes excluded buckets is still compared
+    when its top-k is the same for every resolution of their ambiguous ids.
+    Returns (n_compared, n_skipped, failures)."""
     compared, skipped, fails = 0, 0, []
     for i, r in enumerate(res):
         flagged = bool(r.topk_flag) or bool(np.any(r.probe_flag))
         if not flagged:
-            for ti, t in enumerate(tables):
-                ex = excl_by_table[t]
-                if ex and any(int(b) in ex for b in r.buckets[ti]):
-                    flagged = True
-                    break
+            hit = [(t, int(b)) for ti, t in enumerate(tables) if excl_by_table[t]
+                   for b in r.buckets[ti] if int(b) in excl_by_table[t]]
+            if hit:
+                flagged = True
+                if ambiguous is not None:
+                    amb = np.unique(np.concatenate([ambiguous(t, b) for t, b in hit]
+                                                   + [np.zeros(0, dtype=np.int64)]))
+                    kk = len(r.ids)
+                    flagged = not topk_determined(ix, Q[i], r.cand, amb.astype(np.int64), kk)
         if flagged:
             skipped += 1
             continue
