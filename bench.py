@@ -686,11 +686,11 @@ def main():
                     "12 B per result (+ the re-ranked FP32 shortlist rows)"),
     }
     if distinct_rows is not None:
-        sc = kernels["score"]
-        sc["distinct_rows_per_launch"] = distinct_rows
-        sc["distinct_row_bytes_per_launch"] = distinct_rows * row_bytes
-        if sc["traffic"]:
-            sc["dram_vs_distinct_rows"] = sc["traffic"] / (distinct_rows * row_bytes)
+        sk = kernels["score"]
+        sk["distinct_rows_per_launch"] = distinct_rows
+        sk["distinct_row_bytes_per_launch"] = distinct_rows * row_bytes
+        if sk["traffic"]:
+            sk["dram_vs_distinct_rows"] = sk["traffic"] / (distinct_rows * row_bytes)
     gs_ms = ms_of["ms_gather_score"]
     gs_gbs = algo_b / (gs_ms / 1e3) / 1e9
     kernels["gather_score"] = {"kernel": "dedup + score + topk", "ms_per_launch": gs_ms,

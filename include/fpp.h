@@ -387,13 +387,25 @@ typedef struct fpp_server_stats {
   uint64_t queued;                        /* requests waiting now            */
   uint64_t batches, queries;              /* batches run, queries in them    */
   uint64_t entries, probes;               /* bucket entries scanned, buckets */
+  uint64_t splits;                        /* batches halved because their
+                                             candidates did not fit a slot  */
+  uint64_t serving_allocs;                /* device allocations made while
+                                             running batches (always 0)     */
 } fpp_server_stats;
 
 void fpp_default_server_cfg(fpp_server_cfg* cfg);
 
 /* Starts the worker threads and allocates every slot's workspace for
- * max_batch queries, probes_max probes and k_max results up front.
- * Errors: FPP_EINVAL for a field out of range; FPP_ENOMEM. */
+ * max_batch queries, probes_max probes and k_max results up front, with a
+ * candidate buffer of candidate_budget_bytes / 8 entries per slot; running
+ * batches allocates no device memory.  A free slot takes the oldest queued
+ * requests while the batch stays within max_batch queries and within the
+ * buffer by a running estimate of the entries per probed bucket; the exact
+ * entry count of the batch, taken after its probes are ranked, decides: a
+ * batch that does not fit is halved by queries (again if needed) and each
+ * part is searched in turn.  Errors: FPP_EINVAL for a field out of range or
+ * a buffer that cannot hold one query's worst case (8 L probes_max
+ * max_bucket_kept bytes); FPP_ENOMEM. */
 fpp_status fpp_server_create(const fpp_index* ix, const fpp_server_cfg* cfg,
                              fpp_server** out);
 
@@ -435,6 +447,8 @@ fpp_status fpp_merge_topk(const int64_t* ids, const float* scores, int32_t parts
 
 /* Number of kernels this process has launched through libfpp. */
 uint64_t fpp_launch_count(void);
+/* Number of device allocations (cudaMalloc) libfpp has made in this process. */
+uint64_t fpp_alloc_count(void);
 
 #ifdef __cplusplus
 }

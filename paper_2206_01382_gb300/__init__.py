@@ -76,7 +76,8 @@ class fpp_server_cfg(ctypes.Structure):
 
 class fpp_server_stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "completed", "failed", "queued",
-                                               "batches", "queries", "entries", "probes")]
+                                               "batches", "queries", "entries", "probes",
+                                               "splits", "serving_allocs")]
 
 
 class fpp_tune_report(ctypes.Structure):
@@ -137,6 +138,7 @@ def load(path: str | None = None):
         "fpp_projection_error_bound": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
         "fpp_bruteforce_static": (ctypes.c_int, [f32p, i64, i32, f32p, i64, i32, vp, vp, vp]),
         "fpp_launch_count": (u64, []),
+        "fpp_alloc_count": (u64, []),
         "fpp_merge_topk": (ctypes.c_int, [vp, vp, i32, i64, i32, vp, vp]),
         "fpp_autotune": (ctypes.c_int, [vp, f32p, i64, i32, i32, ctypes.POINTER(fpp_tune_report)]),
         "fpp_default_server_cfg": (None, [ctypes.POINTER(fpp_server_cfg)]),
@@ -386,6 +388,11 @@ def fpp_bruteforce_static(X, Q, k: int, ids=None, scores=None, stream=None):
 
 def fpp_launch_count() -> int:
     return int(load().fpp_launch_count())
+
+
+def fpp_alloc_count() -> int:
+    """Device allocations libfpp has made in this process."""
+    return int(load().fpp_alloc_count())
 
 
 class Index:

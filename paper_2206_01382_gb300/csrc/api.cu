@@ -27,6 +27,8 @@ std::atomic<uint64_t> g_launches{0};
 
 void set_error(const std::string& msg) { g_err = msg; }
 std::atomic<uint64_t>& launch_counter() { return g_launches; }
+std::atomic<uint64_t> g_dev_allocs{0};
+std::atomic<uint64_t>& alloc_counter() { return g_dev_allocs; }
 
 namespace {
 
@@ -66,7 +68,7 @@ struct DevBuf {
     bytes = 0;
     const size_t sz = std::max<size_t>(need, 256);
     g_alloc_gen.fetch_add(1);
-    FPP_CUDA(cudaMalloc(&p, sz));
+    FPP_CUDA(dev_malloc(&p, sz));
     bytes = sz;
     if (zero) FPP_CUDA(cudaMemsetAsync(p, 0, sz, st));
     return FPP_OK;
@@ -198,7 +200,7 @@ int64_t nbuckets(int D) { return 4ll * D * D; }
 
 fpp_status to_device_padded(const float* src, int64_t rows, int d, int dpad, float** dst,
                             cudaStream_t st, uint64_t* bytes) {
-  FPP_CUDA(cudaMalloc(dst, (size_t)std::max<int64_t>(rows, 1) * dpad * sizeof(float)));
+  FPP_CUDA(dev_malloc(dst, (size_t)std::max<int64_t>(rows, 1) * dpad * sizeof(float)));
   if (bytes) *bytes += (uint64_t)rows * dpad * sizeof(float);
   if (dpad != d) FPP_CUDA(cudaMemsetAsync(*dst, 0, (size_t)rows * dpad * sizeof(float), st));
   if (rows > 0)
@@ -391,7 +393,7 @@ fpp_status build_tables(fpp_index* ix, int t0, int nt, BuildScratch& B, cudaStre
   ix->max_bucket_kept = std::max(ix->max_bucket_kept, hmk);
   const uint64_t total = starts[nt];
   uint32_t* cids = nullptr;
-  FPP_CUDA(cudaMalloc(&cids, std::max<uint64_t>(total, 1) * 4));
+  FPP_CUDA(dev_malloc(&cids, std::max<uint64_t>(total, 1) * 4));
   chunks.emplace_back(cids, total);
   FPP_TRY(launch_compact(sorted, nrec, B.bstart.as<uint64_t>(), B.kstart.as<uint64_t>(),
                          B.counts.as<uint32_t>(), rule, cids, st));
@@ -501,8 +503,8 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
     // c: the given vector, or the FP64 column means rounded to FP32; the
     // tables are built over fl(x - c)
     ix->center = 1;
-    if (cudaMalloc(&ix->c, (size_t)ix->dpad * 4) != cudaSuccess ||
-        cudaMalloc(&ix->Xc, (size_t)n * ix->dpad * 4) != cudaSuccess) {
+    if (dev_malloc(&ix->c, (size_t)ix->dpad * 4) != cudaSuccess ||
+        dev_malloc(&ix->Xc, (size_t)n * ix->dpad * 4) != cudaSuccess) {
       set_error("cudaMalloc (centering)");
       return fail(FPP_ENOMEM);
     }
@@ -520,7 +522,7 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
   }
   if ((s = to_device_padded(hR.data(), rrows, d, ix->dpad, &ix->R, st, &ix->device_bytes)) != FPP_OK)
     return fail(s);
-  if (cudaMalloc(&ix->Rs, (size_t)rrows * ix->pieces * ix->Kp * 2) != cudaSuccess) {
+  if (dev_malloc(&ix->Rs, (size_t)rrows * ix->pieces * ix->Kp * 2) != cudaSuccess) {
     set_error("cudaMalloc Rs");
     return fail(FPP_ENOMEM);
   }
@@ -528,7 +530,7 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
   if ((s = split_to_bf16(ix->R, rrows, ix->dpad, d, ix->pieces, ix->Rs, st)) != FPP_OK) return fail(s);
   if (ix->precision == FPP_BF16) {
     ix->ldxb = round_up(d, 8);
-    if (cudaMalloc(&ix->Xb, (size_t)n * ix->ldxb * 2) != cudaSuccess) {
+    if (dev_malloc(&ix->Xb, (size_t)n * ix->ldxb * 2) != cudaSuccess) {
       set_error("cudaMalloc Xb");
       return fail(FPP_ENOMEM);
     }
@@ -537,8 +539,8 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
   }
   if (ix->precision == FPP_FP8E4M3) {
     ix->ldxq = round_up(d, 16);
-    if (cudaMalloc(&ix->Xq, (size_t)n * ix->ldxq) != cudaSuccess ||
-        cudaMalloc(&ix->xscale, (size_t)n * 4) != cudaSuccess) {
+    if (dev_malloc(&ix->Xq, (size_t)n * ix->ldxq) != cudaSuccess ||
+        dev_malloc(&ix->xscale, (size_t)n * 4) != cudaSuccess) {
       set_error("cudaMalloc Xq");
       return fail(FPP_ENOMEM);
     }
@@ -546,7 +548,7 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
     if ((s = rows_to_fp8(ix->X, n, ix->dpad, d, ix->ldxq, ix->Xq, ix->xscale, st)) != FPP_OK)
       return fail(s);
   }
-  if (cudaMalloc(&ix->rmax, 2 * L * 4) != cudaSuccess) { set_error("cudaMalloc rmax"); return fail(FPP_ENOMEM); }
+  if (dev_malloc(&ix->rmax, 2 * L * 4) != cudaSuccess) { set_error("cudaMalloc rmax"); return fail(FPP_ENOMEM); }
   if (cudaMemcpyAsync(ix->rmax, hrmax.data(), 2 * L * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) {
     set_error("copy rmax");
     return fail(FPP_ECUDA);
@@ -555,7 +557,7 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
     // largest norm of the points (score bounds) and of the hashed rows
     // (projection bounds of the build); equal unless the index centers
     float* dxm = nullptr;
-    if (cudaMalloc(&dxm, 8) != cudaSuccess) { set_error("cudaMalloc"); return fail(FPP_ENOMEM); }
+    if (dev_malloc(&dxm, 8) != cudaSuccess) { set_error("cudaMalloc"); return fail(FPP_ENOMEM); }
     s = launch_row_norm_max(ix->X, n, ix->dpad, d, dxm, st);
     if (s == FPP_OK) s = launch_row_norm_max(hashed_rows(ix), n, ix->dpad, d, dxm + 1, st);
     float hm[2] = {0.f, 0.f};
@@ -567,7 +569,7 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
     ix->xhmax = hm[1];
   }
   const int64_t NB = nbuckets(D);
-  if (cudaMalloc(&ix->offsets, (size_t)L * (NB + 1) * 4) != cudaSuccess) {
+  if (dev_malloc(&ix->offsets, (size_t)L * (NB + 1) * 4) != cudaSuccess) {
     set_error("cudaMalloc offsets");
     return fail(FPP_ENOMEM);
   }
@@ -594,7 +596,7 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
     if ((s = build_tables(ix, t0, nt, B, st, chunks, base)) != FPP_OK) { cleanup(); return fail(s); }
   }
   ix->kept_total = base;
-  if (cudaMalloc(&ix->ids, std::max<uint64_t>(base, 1) * 4) != cudaSuccess) {
+  if (dev_malloc(&ix->ids, std::max<uint64_t>(base, 1) * 4) != cudaSuccess) {
     set_error("cudaMalloc ids");
     cleanup();
     return fail(FPP_ENOMEM);
@@ -609,7 +611,7 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
     }
     at += c.second;
   }
-  if (cudaMalloc(&ix->table_base, L * 8) != cudaSuccess ||
+  if (dev_malloc(&ix->table_base, L * 8) != cudaSuccess ||
       cudaMemcpyAsync(ix->table_base, ix->h_table_base.data(), L * 8, cudaMemcpyHostToDevice, st) != cudaSuccess) {
     set_error("table_base");
     cleanup();
@@ -634,7 +636,7 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
     const int bits = p->simhash_bits;
     ix->sig_words = bits / 32;
     for (int j = 0; j * D < bits; ++j) ix->rsig_max = std::max(ix->rsig_max, hrmax[j]);
-    if (cudaMalloc(&ix->sig, (size_t)n * ix->sig_words * 4) != cudaSuccess) {
+    if (dev_malloc(&ix->sig, (size_t)n * ix->sig_words * 4) != cudaSuccess) {
       set_error("cudaMalloc (signatures)");
       cleanup();
       return fail(FPP_ENOMEM);
@@ -685,6 +687,8 @@ struct SearchPlan {
   int sim_keep = 0;     // > 0: SimHash pre-ranking keeps this many candidates
   int range_shift = 0;  // range_count > 1: candidates grouped by id >> range_shift
   int range_count = 1;
+  bool no_grow = false; // serving: never grow the candidate buffers; a batch
+                        // whose candidates do not fit returns FPP_EBUSY
   const int32_t* kpq;   // user arrays (host or device) or NULL
   const int32_t* ppq;
   bool kpq_dev, ppq_dev;
@@ -898,10 +902,14 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   const uint64_t bound = (uint64_t)mc * nt * pl.pmax * std::max<uint32_t>(ix->max_bucket_kept, 1);
   uint64_t need = bound;
   bool exact = false;
-  if (bound > ws.cand_cap && bound > ix->cand_budget_entries) {
+  if (bound > ws.cand_cap && (pl.no_grow || bound > ix->cand_budget_entries)) {
     FPP_CUDA(cudaMemcpyAsync(&need, stv + 12, 8, cudaMemcpyDeviceToHost, st));
     FPP_CUDA(cudaStreamSynchronize(st));
     exact = true;
+  }
+  if (need > ws.cand_cap && pl.no_grow) {
+    set_error("the batch's candidates exceed the candidate buffer");
+    return FPP_EBUSY;
   }
   if (need > ws.cand_cap) {
     ws.cand.release(); ws.cscores.release(); ws.items.release();
@@ -912,6 +920,10 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   }
   const size_t item_bytes =
       (size_t)score_item_slots(ws.cand_cap, mc, pl.range_count) * sizeof(ScoreItem);
+  if (pl.no_grow && (ws.items.bytes < item_bytes || (pl.range_count > 1 && ws.items2.bytes < item_bytes))) {
+    set_error("serving workspace: score items not provisioned");
+    return FPP_EINTERNAL;
+  }
   FPP_TRY(ws.items.ensure(item_bytes));
   if (pl.range_count > 1) FPP_TRY(ws.items2.ensure(item_bytes));
   da.cand = ws.cand.as<uint32_t>();
@@ -1260,19 +1272,29 @@ double request_entries(const fpp_server* s, const ServerRequest& r) {
   return (double)r.nq * s->ix->L * r.probes * s->entries_per_probe;
 }
 
-void server_run_batch(fpp_server* s, ServerSlot& sl, std::vector<ServerRequest*>& batch) {
+// A run of consecutive queries of one request.
+struct Seg {
+  ServerRequest* r;
+  int32_t q0, nq;
+};
+
+// One search over the segments' queries with the slot's pre-sized
+// workspace; results go straight into the requests.  FPP_EBUSY: the
+// candidates do not fit the slot's buffer (nothing was written).
+fpp_status server_search(fpp_server* s, ServerSlot& sl, const std::vector<Seg>& segs,
+                         unsigned long long* entries, unsigned long long* probes) {
   fpp_index* ix = s->ix;
   const int d = ix->d;
   int64_t m = 0;
   int pmax = 1;
-  for (ServerRequest* r : batch) {
-    std::memcpy(sl.hq + m * d, r->q.data(), (size_t)r->nq * d * 4);
-    for (int i = 0; i < r->nq; ++i) {
-      sl.hk[m + i] = r->k;
-      sl.hp[m + i] = r->probes;
+  for (const Seg& g : segs) {
+    std::memcpy(sl.hq + m * d, g.r->q.data() + (size_t)g.q0 * d, (size_t)g.nq * d * 4);
+    for (int i = 0; i < g.nq; ++i) {
+      sl.hk[m + i] = g.r->k;
+      sl.hp[m + i] = g.r->probes;
     }
-    pmax = std::max(pmax, r->probes);
-    m += r->nq;
+    pmax = std::max(pmax, g.r->probes);
+    m += g.nq;
   }
   SearchPlan pl{};
   pl.m = m;
@@ -1285,59 +1307,101 @@ void server_run_batch(fpp_server* s, ServerSlot& sl, std::vector<ServerRequest*>
   pl.kpq_dev = pl.ppq_dev = false;
   pl.k = s->cfg.k_max;
   pl.probes = pmax;
-  auto fail = [&](fpp_status st, const std::string& msg) {
-    std::lock_guard<std::mutex> lock(s->mu);
-    for (ServerRequest* r : batch) {
-      r->status = st;
-      r->error = msg;
-      r->state = 2;
-      r->t_done = std::chrono::steady_clock::now();
-    }
-    s->stats.failed += batch.size();
-    s->cv_done.notify_all();
-  };
-  fpp_status st = FPP_OK;
-  auto run = [&]() -> fpp_status {
-    FPP_TRY(prepare_workspace(ix, sl.ws, pl, m, true, sl.st));
-    FPP_CUDA(cudaMemsetAsync(sl.ws.stats.p, 0, 16 * 8, sl.st));
-    FPP_TRY(search_chunk(ix, sl.ws, sl.hq, 0, m, pl, sl.ws.out_ids.as<int64_t>(),
-                         sl.ws.out_scores.as<float>(), sl.st, kFull, nullptr));
-    FPP_CUDA(cudaMemcpyAsync(sl.hids, sl.ws.out_ids.p, (size_t)m * pl.kmax * 8,
-                             cudaMemcpyDeviceToHost, sl.st));
-    FPP_CUDA(cudaMemcpyAsync(sl.hsc, sl.ws.out_scores.p, (size_t)m * pl.kmax * 4,
-                             cudaMemcpyDeviceToHost, sl.st));
-    FPP_CUDA(cudaMemcpyAsync(sl.hstats, sl.ws.stats.p, 16 * 8, cudaMemcpyDeviceToHost, sl.st));
-    FPP_CUDA(cudaStreamSynchronize(sl.st));
-    if (sl.hstats[5]) { set_error("search: top-k re-check capacity exceeded"); return FPP_EINTERNAL; }
-    if (sl.hstats[9]) { set_error("search: a bounded wait in the projection kernel ran out"); return FPP_ETIMEOUT; }
-    return FPP_OK;
-  };
-  st = run();
-  if (st != FPP_OK) {
-    fail(st, g_err);
-    return;
-  }
-  const auto now = std::chrono::steady_clock::now();
+  pl.no_grow = true;
+  FPP_TRY(prepare_workspace(ix, sl.ws, pl, m, true, sl.st));
+  FPP_CUDA(cudaMemsetAsync(sl.ws.stats.p, 0, 16 * 8, sl.st));
+  FPP_TRY(search_chunk(ix, sl.ws, sl.hq, 0, m, pl, sl.ws.out_ids.as<int64_t>(),
+                       sl.ws.out_scores.as<float>(), sl.st, kFull, nullptr));
+  FPP_CUDA(cudaMemcpyAsync(sl.hids, sl.ws.out_ids.p, (size_t)m * pl.kmax * 8,
+                           cudaMemcpyDeviceToHost, sl.st));
+  FPP_CUDA(cudaMemcpyAsync(sl.hsc, sl.ws.out_scores.p, (size_t)m * pl.kmax * 4,
+                           cudaMemcpyDeviceToHost, sl.st));
+  FPP_CUDA(cudaMemcpyAsync(sl.hstats, sl.ws.stats.p, 16 * 8, cudaMemcpyDeviceToHost, sl.st));
+  FPP_CUDA(cudaStreamSynchronize(sl.st));
+  if (sl.hstats[5]) { set_error("search: top-k re-check capacity exceeded"); return FPP_EINTERNAL; }
+  if (sl.hstats[9]) { set_error("search: a bounded wait in the projection kernel ran out"); return FPP_ETIMEOUT; }
   int64_t row = 0;
-  for (ServerRequest* r : batch) {
-    for (int i = 0; i < r->nq; ++i) {
-      std::memcpy(r->ids.data() + (size_t)i * r->k, sl.hids + (row + i) * pl.kmax, (size_t)r->k * 8);
-      std::memcpy(r->scores.data() + (size_t)i * r->k, sl.hsc + (row + i) * pl.kmax, (size_t)r->k * 4);
+  for (const Seg& g : segs) {
+    ServerRequest* r = g.r;
+    for (int i = 0; i < g.nq; ++i) {
+      std::memcpy(r->ids.data() + (size_t)(g.q0 + i) * r->k, sl.hids + (row + i) * pl.kmax, (size_t)r->k * 8);
+      std::memcpy(r->scores.data() + (size_t)(g.q0 + i) * r->k, sl.hsc + (row + i) * pl.kmax, (size_t)r->k * 4);
     }
-    row += r->nq;
+    row += g.nq;
   }
+  *entries += sl.hstats[0];
+  *probes += sl.hstats[3];
+  return FPP_OK;
+}
+
+// Runs the segments, splitting them in half by queries (and again) while
+// their candidates do not fit the slot's buffer.  A single query always
+// fits: fpp_server_create checks its worst case against the buffer.
+fpp_status server_run_segs(fpp_server* s, ServerSlot& sl, const std::vector<Seg>& segs,
+                           unsigned long long* entries, unsigned long long* probes,
+                           uint64_t* splits) {
+  const fpp_status st = server_search(s, sl, segs, entries, probes);
+  if (st != FPP_EBUSY) return st;
+  int64_t m = 0;
+  for (const Seg& g : segs) m += g.nq;
+  if (m <= 1) {
+    set_error("server: one query's candidates exceed the slot's buffer");
+    return FPP_EINTERNAL;
+  }
+  ++*splits;
+  const int64_t half = m / 2;
+  std::vector<Seg> a, b;
+  int64_t at = 0;
+  for (const Seg& g : segs) {
+    if (at + g.nq <= half) a.push_back(g);
+    else if (at >= half) b.push_back(g);
+    else {
+      const int32_t na = (int32_t)(half - at);
+      a.push_back({g.r, g.q0, na});
+      b.push_back({g.r, g.q0 + na, g.nq - na});
+    }
+    at += g.nq;
+  }
+  FPP_TRY(server_run_segs(s, sl, a, entries, probes, splits));
+  return server_run_segs(s, sl, b, entries, probes, splits);
+}
+
+void server_run_batch(fpp_server* s, ServerSlot& sl, std::vector<ServerRequest*>& batch) {
+  std::vector<Seg> segs;
+  int64_t m = 0;
+  for (ServerRequest* r : batch) {
+    segs.push_back({r, 0, r->nq});
+    m += r->nq;
+  }
+  unsigned long long entries = 0, probes = 0;
+  uint64_t splits = 0;
+  const uint64_t allocs0 = alloc_counter().load();
+  const fpp_status st = server_run_segs(s, sl, segs, &entries, &probes, &splits);
+  const uint64_t allocs = alloc_counter().load() - allocs0;
+  const auto now = std::chrono::steady_clock::now();
   std::lock_guard<std::mutex> lock(s->mu);
+  s->stats.splits += splits;
+  s->stats.serving_allocs += allocs;
   for (ServerRequest* r : batch) {
     r->state = 2;
     r->t_done = now;
+    if (st != FPP_OK) {
+      r->status = st;
+      r->error = g_err;
+    }
+  }
+  if (st != FPP_OK) {
+    s->stats.failed += batch.size();
+    s->cv_done.notify_all();
+    return;
   }
   s->stats.completed += batch.size();
   s->stats.batches += 1;
   s->stats.queries += (uint64_t)m;
-  s->stats.entries += sl.hstats[0];
-  s->stats.probes += sl.hstats[3];
-  if (sl.hstats[3]) {
-    const double epp = (double)sl.hstats[0] / (double)sl.hstats[3];
+  s->stats.entries += entries;
+  s->stats.probes += probes;
+  if (probes) {
+    const double epp = (double)entries / (double)probes;
     s->entries_per_probe = 0.8 * s->entries_per_probe + 0.2 * epp * 1.25;
   }
   s->cv_done.notify_all();
@@ -1408,6 +1472,15 @@ fpp_status server_create_impl(const fpp_index* cix, const fpp_server_cfg* cfg, f
     set_error("candidate_budget_bytes must be >= 1 MiB");
     return FPP_EINVAL;
   }
+  // the worst case of one query (every probed bucket as large as the largest
+  // kept bucket) must fit a slot's buffer, so that splitting a batch always
+  // ends in batches that fit
+  const uint64_t one_query = (uint64_t)cix->L * cfg->probes_max * std::max<uint32_t>(cix->max_bucket_kept, 1);
+  if (one_query > cfg->candidate_budget_bytes / 8) {
+    set_error("candidate_budget_bytes must hold one query's worst case, 8 L probes_max max_bucket_kept = " +
+              std::to_string(one_query * 8) + " bytes");
+    return FPP_EINVAL;
+  }
   auto s = std::make_unique<fpp_server>();
   s->ix = const_cast<fpp_index*>(cix);
   s->cfg = *cfg;
@@ -1440,6 +1513,9 @@ fpp_status server_create_impl(const fpp_index* cix, const fpp_server_cfg* cfg, f
       if ((st = sl->ws.cand.ensure((size_t)cap * 4)) == FPP_OK &&
           (st = sl->ws.cscores.ensure((size_t)cap * 4)) == FPP_OK)
         sl->ws.cand_cap = cap;
+      // the score work items for a full buffer: serving allocates nothing
+      if (st == FPP_OK)
+        st = sl->ws.items.ensure((size_t)score_item_slots(cap, cfg->max_batch, 1) * sizeof(ScoreItem));
     }
     if (st == FPP_OK && cudaStreamSynchronize(sl->st) != cudaSuccess) st = FPP_ECUDA;
     s->slots.push_back(std::move(sl));
@@ -1486,6 +1562,7 @@ void fpp_default_search_opts(fpp_search_opts* o) {
 const char* fpp_last_error(void) { return g_err.c_str(); }
 
 uint64_t fpp_launch_count(void) { return g_launches.load(); }
+uint64_t fpp_alloc_count(void) { return alloc_counter().load(); }
 
 uint64_t fpp_keep_count(uint64_t B, double alpha, int32_t iprobes, int32_t kappa) {
   if (iprobes < 1) iprobes = 1;

@@ -465,7 +465,7 @@ fpp_status launch_column_means(const float* X, int64_t n, int64_t ldx, int d, fl
                                cudaStream_t st) {
   const int nblk = (int)ceil_div(n, CM_ROWS);
   double* part = nullptr;
-  FPP_CUDA(cudaMalloc(&part, (size_t)nblk * d * 8));
+  FPP_CUDA(dev_malloc(&part, (size_t)nblk * d * 8));
   column_partials_kernel<<<dim3(nblk, (unsigned)ceil_div(d, 128)), 128, 0, st>>>(X, n, ldx, d, part);
   FPP_LAUNCHED();
   column_means_kernel<<<(unsigned)ceil_div(d, 128), 128, 0, st>>>(part, nblk, d, n, c);

@@ -16,6 +16,14 @@ namespace fpp {
 
 void set_error(const std::string& msg);
 std::atomic<uint64_t>& launch_counter();
+// Device allocations made by the library (every cudaMalloc goes through
+// dev_malloc), for callers that check that a phase allocates nothing.
+std::atomic<uint64_t>& alloc_counter();
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  alloc_counter().fetch_add(1, std::memory_order_relaxed);
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
 
 struct Status {
   fpp_status code = FPP_OK;

@@ -183,24 +183,28 @@ def compare_probes(ix, Q, P, gpu_probes, tables):
     return compared, skipped, fails
 
 
-def compare_candidates(res, gpu_cands, tables, excl_by_table):
+def compare_candidates(res, gpu_cands, tables, excl_by_table, ambiguous=None):
     """Per query: the de-duplicated candidate set must equal the oracle's
-    unless a probe boundary or a probed bucket is flagged.  Returns
-    (n_compared, n_skipped, failures)."""
+    unless a probe boundary is flagged; where probed buckets are excluded,
+    the skip, or with ``ambiguous`` ((t, b) -> ids) the two sets must agree
+    outside the ids those buckets leave open.  Returns (n_compared,
+    n_skipped, failures)."""
     compared, skipped, fails = 0, 0, []
     for i, r in enumerate(res):
-        flagged = bool(np.any(r.probe_flag))
-        if not flagged:
-            for ti, t in enumerate(tables):
-                ex = excl_by_table[t]
-                if ex and any(int(b) in ex for b in r.buckets[ti]):
-                    flagged = True
-                    break
-        if flagged:
+        if bool(np.any(r.probe_flag)):
+            skipped += 1
+            continue
+        hit = [(t, int(b)) for ti, t in enumerate(tables) if excl_by_table[t]
+               for b in r.buckets[ti] if int(b) in excl_by_table[t]]
+        if hit and ambiguous is None:
             skipped += 1
             continue
         compared += 1
         g = np.asarray(gpu_cands[i]).astype(np.int64)
-        if not np.array_equal(g, r.cand):
+        want = r.cand
+        if hit:
+            amb = np.unique(np.concatenate([ambiguous(t, b) for t, b in hit])).astype(np.int64)
+            g, want = np.setdiff1d(g, amb), np.setdiff1d(want, amb)
+        if not np.array_equal(g, want):
             fails.append((i, len(r.cand), len(g)))
     return compared, skipped, fails

@@ -35,7 +35,7 @@ def test_struct_sizes_match_header(lib):
     assert ctypes.sizeof(F.fpp_search_opts) == 64
     assert ctypes.sizeof(F.fpp_search_stats) == 96
     assert ctypes.sizeof(F.fpp_server_cfg) == 32
-    assert ctypes.sizeof(F.fpp_server_stats) == 64
+    assert ctypes.sizeof(F.fpp_server_stats) == 80
 
 
 @pytest.mark.parametrize("seed,L,D,d", [(2000, 10, 64, 64), (7, 3, 5, 13), (2001, 4, 256, 128)])

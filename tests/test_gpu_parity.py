@@ -322,7 +322,8 @@ def test_plain1m_full_size_all_tables(F):
         print(f"plain1m P={P} top-10: {c} queries compared, {s} near-tie skipped")
         assert c >= 0.9 * len(Q), (c, s)
         gc = F.fpp_debug_candidates(ix.handle, Q, P)
-        c, s, fails = PT.compare_candidates(res, gc, tabs, excl)
+        c, s, fails = PT.compare_candidates(
+            res, gc, tabs, excl, ambiguous=lambda t, b: PT.ambiguous_ids(ix_o, t, b, gpbs[t]))
         assert not fails, fails[:3]
         print(f"plain1m P={P} candidates: {c} queries compared, {s} near-tie skipped")
         assert c >= 0.9 * len(Q), (c, s)

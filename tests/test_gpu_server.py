@@ -114,3 +114,44 @@ def test_server_device_queries_and_destroy_with_pending(F, data):
     for i in range(20):
         srv.submit(Q[i * 16:(i + 1) * 16], 10, 4)
     srv.close()   # drops what is still queued, joins the worker
+
+
+def test_server_splits_batches_that_do_not_fit_and_allocates_nothing(F, data):
+    # a 1 MiB candidate buffer per slot holds 131,072 entries; one request of
+    # 600 queries at 8 probes per table scans more, so the slot must halve the
+    # batch (the first request is always admitted whole) instead of growing
+    # its buffers: no device allocation while serving, the same results
+    X, Q, ix = data
+    gi, gs, st = F.fpp_search_ex(ix.handle, Q, k=10, probes=8)
+    assert st["entries"] > (1 << 20) // 8
+    srv = F.Server(ix, k_max=10, probes_max=8, slots=1, max_batch=4096,
+                   candidate_budget_bytes=1 << 20)
+    a0 = F.fpp_alloc_count()
+    ids, sc, _ = srv.poll(srv.submit(Q, 10, 8))
+    reqs = _requests(len(Q), 404)
+    rids = [srv.submit(Q[q0:q0 + nq], 10, 8) for q0, nq, _, _ in reqs]
+    outs = [srv.poll(r) for r in rids]
+    assert F.fpp_alloc_count() == a0
+    s = srv.stats()
+    srv.close()
+    assert s["serving_allocs"] == 0 and s["failed"] == 0
+    assert s["splits"] >= 1, s
+    assert np.array_equal(ids, gi) and np.array_equal(sc, gs)
+    for (q0, nq, _, _), o in zip(reqs, outs):
+        assert np.array_equal(o[0], gi[q0:q0 + nq]) and np.array_equal(o[1], gs[q0:q0 + nq])
+    print(f"\nserver: {s['batches']} batches, {s['splits']} halvings, 0 allocations")
+
+
+def test_server_refuses_a_buffer_below_one_querys_worst_case(F, data):
+    X, Q, _ = data
+    ix = F.Index(X, 16, 2, 1.0, seed=3)     # 16 buckets per table: very large buckets
+    worst = 16 * 8 * ix.info()["max_bucket_kept"] * 8
+    assert worst > 1 << 20
+    with pytest.raises(F.FppError) as e:
+        F.Server(ix, k_max=10, probes_max=8, candidate_budget_bytes=1 << 20)
+    assert e.value.status == F.FPP_EINVAL and "worst case" in str(e.value)
+    srv = F.Server(ix, k_max=10, probes_max=8, candidate_budget_bytes=worst)
+    gi, gs, _ = F.fpp_search_ex(ix.handle, Q[:50], k=10, probes=8, want_stats=False)
+    ids, sc, _ = srv.poll(srv.submit(Q[:50], 10, 8))
+    srv.close()
+    assert np.array_equal(ids, gi) and np.array_equal(sc, gs)
