@@ -121,9 +121,10 @@ def test_server_splits_batches_that_do_not_fit_and_allocates_nothing(F, data):
     # 600 queries at 8 probes per table scans more, so the slot must halve the
     # batch (the first request is always admitted whole) instead of growing
     # its buffers: no device allocation while serving, the same results
-    X, Q, ix = data
+    X, Q, _ = data
+    ix = F.Index(X, 16, 16, 0.5, seed=19)   # about 1,000 entries per query at 8 probes
     gi, gs, st = F.fpp_search_ex(ix.handle, Q, k=10, probes=8)
-    assert st["entries"] > (1 << 20) // 8
+    assert st["entries"] > 2 * ((1 << 20) // 8), st["entries"]
     srv = F.Server(ix, k_max=10, probes_max=8, slots=1, max_batch=4096,
                    candidate_budget_bytes=1 << 20)
     a0 = F.fpp_alloc_count()
