@@ -51,7 +51,15 @@ def parse():
                     help="fp32: exact decisions; bf16 / fp8: candidate rows in BF16 / FP8 e4m3 "
                          "with an exactly re-scored shortlist (default: the workload's stored "
                          "precision, bf16 for precision1m and serve2m)")
-    ap.add_argument("--rerank-k", type=int, default=100)
+    ap.add_argument("--rerank-k", type=int, default=None,
+                    help="bf16 / fp8 rows: FP32 re-ranked shortlist (default: 100 for the precision "
+                         "workload, which states it; 0 = the minimum k + 16 for serving)")
+    ap.add_argument("--hash", choices=["auto", "exact", "bf16"], default="auto",
+                    help="query projections of bf16 / fp8 rows: bf16 = one BF16 product (each "
+                         "hash's winner re-decided exactly, the other probes ranked by the BF16 "
+                         "values); exact = the three-piece split; auto = bf16 for the precision "
+                         "workload (whose projections are BF16), exact otherwise (measured faster "
+                         "for serving)")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="serving workload: seconds of arrivals per offered rate")
     ap.add_argument("--slots", type=int, default=3, help="serving workload: batches in flight")
@@ -59,6 +67,7 @@ def parse():
                     help="default run: seconds of arrivals per offered rate in its serving block")
     ap.add_argument("--no-serve", action="store_true",
                     help="default run: skip the serving comparison block")
+    ap.add_argument("--max-batch", type=int, default=4096, help="serving: queries per batch")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--graph", action="store_true",
                     help="time the steps as replays of the library's captured search graph")
@@ -355,11 +364,24 @@ def serve_drive(srv, Q, P, t, sizes, ks, paced):
 
     def submitter():
         qi = 0
+        if not paced:
+            # unpaced: the requests go in 16 at a time (one library call), so
+            # that the client's per-call overhead does not set the pace
+            # (16 x 4,096 rows fit the query pool)
+            for i0 in range(0, len(t), 16):
+                sz = np.asarray(sizes[i0:i0 + 16], dtype=np.int64)
+                tot = int(sz.sum())
+                if qi + tot > m:
+                    qi = 0
+                ids = srv.submit_many(Q[qi:qi + tot], sz, ks[i0:i0 + 16], P)
+                for j, rid in enumerate(ids):
+                    rids[i0 + j] = rid
+                qi += tot
+            return
         for i in range(len(t)):
-            if paced:
-                wait = t[i] - (time.perf_counter() - start)
-                if wait > 0:
-                    time.sleep(wait)
+            wait = t[i] - (time.perf_counter() - start)
+            if wait > 0:
+                time.sleep(wait)
             nq = int(sizes[i])
             if qi + nq > m:
                 qi = 0
@@ -380,11 +402,11 @@ def serve_drive(srv, Q, P, t, sizes, ks, paced):
             "mean_request": float(sizes.mean())}
 
 
-def serve_session(F, ix, Q, P, slots, seconds):
+def serve_session(F, ix, Q, P, slots, seconds, max_batch=4096):
     """Poisson arrivals at each offered query rate (sizes log-uniform in
     1..4096, k in {10, 100}) through the continuous-batching server, then the
     same kind of mix unpaced (saturation)."""
-    srv = F.Server(ix, k_max=100, probes_max=P, slots=slots, max_batch=4096)
+    srv = F.Server(ix, k_max=100, probes_max=P, slots=slots, max_batch=max_batch)
     try:
         t, sizes, ks = W.serve_arrivals(99, 100_000, 0.2)
         serve_drive(srv, Q, P, t, sizes, ks, paced=False)   # warm-up
@@ -396,8 +418,11 @@ def serve_session(F, ix, Q, P, slots, seconds):
             r["offered_qps"] = rate
             rates[str(rate)] = r
         t, sizes, ks = W.serve_arrivals(len(W.SERVE_RATES), W.SERVE_RATES[-1], seconds)
+        s_sat = srv.stats()
         sat = serve_drive(srv, Q, P, t, sizes, ks, paced=False)
         s1 = srv.stats()
+        sat["mean_batch_queries"] = (s1["queries"] - s_sat["queries"]) / max(
+            s1["batches"] - s_sat["batches"], 1)
     finally:
         srv.close()
     batches = s1["batches"] - s0["batches"]
@@ -407,7 +432,8 @@ def serve_session(F, ix, Q, P, slots, seconds):
             "d2h_bytes": int((np.asarray(sizes) * np.asarray(ks)).sum() * 12)}
 
 
-def serving_compare(F, w, precision, rerank_k, slots, seconds, probes=0):
+def serving_compare(F, w, precision, rerank_k, slots, seconds, probes=0, hash_bf16=False,
+                    max_batch=4096):
     """The serving workload with candidate rows in ``precision`` against the
     plain FP32 path under the same request mix, each at its own calibrated
     probe budget (the smallest of the sweep with recall@10 >= 0.90), with
@@ -418,21 +444,35 @@ def serving_compare(F, w, precision, rerank_k, slots, seconds, probes=0):
     Qd = torch.from_numpy(Q[:CALIB_QUERIES]).cuda()
     sweep = [probes] if probes else list(w.probes)
     prec = {"fp32": F.FPP_FP32, "bf16": F.FPP_BF16, "fp8": F.FPP_FP8E4M3}[precision]
-    out = {"workload": w.name, "note": w.note, "seconds_per_rate": seconds, "slots": slots}
+    out = {"workload": w.name, "note": w.note, "seconds_per_rate": seconds, "slots": slots,
+           "rerank_k": rerank_k}
     sampler = ClockSampler(torch.cuda.current_device())
     arms = [(precision, prec)] + ([("fp32", F.FPP_FP32)] if prec != F.FPP_FP32 else [])
     res = {}
     for name, pc in arms:
         tb = time.perf_counter()
-        ix = F.Index(Xd, w.L, w.D, w.alpha, seed=w.rot_seed, precision=pc, rerank_k=rerank_k)
+        hp = F.FPP_BF16 if (hash_bf16 and pc != F.FPP_FP32) else F.FPP_FP32
+        ix = F.Index(Xd, w.L, w.D, w.alpha, seed=w.rot_seed, precision=pc, rerank_k=rerank_k,
+                     hash_precision=hp)
         torch.cuda.synchronize()
         build_s = time.perf_counter() - tb
         P, rec, mcal = calibrate_probes(F, ix, Xd, Qd, w.k, sweep)
+        # the device time of each phase on one 10,000-query batch (k = 10)
+        Qb = torch.from_numpy(Q[:10_000]).cuda()
+        ph = {}
+        for rep in range(3):
+            _, _, st = F.fpp_search_ex(ix.handle, Qb, k=10, probes=P)
+            if rep:
+                for key in ("ms_project", "ms_probe", "ms_probe_exact", "ms_dedup", "ms_score",
+                            "ms_topk", "probe_rechecks", "topk_rechecks"):
+                    ph[key] = ph.get(key, 0.0) + st[key] / 2
+        del Qb
         if not res:
             sampler.start()
-        r = serve_session(F, ix, Q, P, slots, seconds)
+        r = serve_session(F, ix, Q, P, slots, seconds, max_batch)
         r.update(precision=name, recall_at_10=rec[P], recall_sweep=rec, recall_sample=mcal,
-                 build_s=build_s)
+                 build_s=build_s, batch_phases_10k=ph,
+                 query_projection="bf16 one product" if hp == F.FPP_BF16 else "exact split")
         res[name] = r
         ix.close()
     out["clocks"] = sampler.stop()
@@ -458,7 +498,7 @@ def run_serve(args, w):
     _build.build()
     F.load()
     srv = serving_compare(F, w, args.precision, args.rerank_k, args.slots, args.serve_seconds,
-                          args.probes)
+                          args.probes, args.hash_bf16, args.max_batch)
     main_arm = srv[args.precision]
     sat = main_arm["saturation"]
     line = {
@@ -471,7 +511,7 @@ def run_serve(args, w):
                    "rerank_k": args.rerank_k if args.precision != "fp32" else None,
                    "n": w.n, "d": w.d, "L": w.L, "D": w.D, "alpha": w.alpha,
                    "probes": main_arm["probes"], "recall_at_10": main_arm["recall_at_10"],
-                   "slots": args.slots, "max_batch": 4096,
+                   "slots": args.slots, "max_batch": args.max_batch,
                    "l2": "inputs larger than L2 (X is "
                          f"{w.n * w.d * 4 / 2**20:.0f} MiB FP32), no flush"},
         "serving": srv,
@@ -491,6 +531,9 @@ def main():
     w = W.WORKLOADS[args.workload]
     if args.precision is None:   # the workload's stored precision
         args.precision = "bf16" if w.storage == "bf16" else "fp32"
+    if args.rerank_k is None:
+        args.rerank_k = 0 if w.name == "serve2m" else 100
+    args.hash_bf16 = args.hash == "bf16" or (args.hash == "auto" and w.name == "precision1m")
     if args.impl == "reference":
         run_reference(args, w)
         return
@@ -526,7 +569,9 @@ def main():
     torch.cuda.synchronize()
     tb = time.perf_counter()
     prec = {"fp32": F.FPP_FP32, "bf16": F.FPP_BF16, "fp8": F.FPP_FP8E4M3}[args.precision]
-    ix = F.Index(Xd, w.L, w.D, w.alpha, seed=w.rot_seed, precision=prec, rerank_k=args.rerank_k)
+    hp = F.FPP_BF16 if (args.hash_bf16 and prec != F.FPP_FP32) else F.FPP_FP32
+    ix = F.Index(Xd, w.L, w.D, w.alpha, seed=w.rot_seed, precision=prec, rerank_k=args.rerank_k,
+                 hash_precision=hp)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - tb
     info = ix.info()
@@ -642,7 +687,7 @@ def main():
     # them per FP32 product when the random vectors are on the BF16 grid
     # (three query pieces times one vector piece), else 6
     kpad = -(-d // 64) * 64
-    products = 3 if info["r_pieces"] == 1 else 6
+    products = 1 if info["q_pieces"] == 1 else 3 if info["r_pieces"] == 1 else 6
     proj_flops = 2.0 * qpl * d * 2 * w.L * w.D
     exec_flops = 2.0 * qpl * kpad * 2 * w.L * w.D * products
     ms_of = {key: phase[key] / per for key in phase}
@@ -756,7 +801,16 @@ def main():
         ex[i, okm[i]] = X[sel].astype(np.float64) @ Q[i].astype(np.float64)
     max_score_err = float(np.abs(gs[okm] - ex[okm]).max()) if okm.any() else 0.0
     if per_query:
-        recalls = {"per-query": recall_k}
+        # recall@k of each (k, probes) group of the uneven workload
+        groups = {}
+        pq = ppq[:mcal]
+        for i in range(mcal):
+            key = f"k={int(kq[i])},P={int(pq[i])}"
+            h = len(set(gi[i, :kq[i]].tolist()) & set(truth[i, :kq[i]].tolist())) / kq[i]
+            groups.setdefault(key, []).append(h)
+        recalls = {"per-query": recall_k,
+                   "by_group": {g: {"recall": float(np.mean(v)), "queries": len(v)}
+                                for g, v in sorted(groups.items())}}
 
     # the serving comparison (BF16 rows against plain FP32 under one request
     # mix, each at recall@10 >= 0.90) on the serving workload, one GPU only
@@ -765,8 +819,9 @@ def main():
         ix.close()
         del Xd, Qd, ids, sc
         torch.cuda.empty_cache()
-        serving = serving_compare(F, W.WORKLOADS["serve2m"], "bf16", 100, args.slots,
-                                  args.serve_seconds_default)
+        serving = serving_compare(F, W.WORKLOADS["serve2m"], "bf16", 0, args.slots,
+                                  args.serve_seconds_default, hash_bf16=args.hash == "bf16",
+                                  max_batch=args.max_batch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -782,6 +837,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": w.name, "note": w.note, "precision": args.precision,
                        "rerank_k": args.rerank_k if bf16 else None,
+                       "query_projection": "bf16 one product" if info["q_pieces"] == 1
+                                           else "exact split",
                        "n": w.n, "d": w.d, "m": m, "L": w.L,
                        "D": w.D, "alpha": w.alpha, "k": k, "probes": P,
                        "recall_at_10": recalls[P], "recall_sweep": recalls,

@@ -112,6 +112,19 @@ typedef struct fpp_params {
                           order (Section 4); needed by simhash_keep        */
   const float* center_vec; /* optional c [d] (host or device); NULL = the
                           FP64 column means of X rounded to FP32            */
+  int32_t hash_precision; /* query projections of the search: FPP_FP32
+                          (default) = the exact three-piece split, decisions
+                          exact; FPP_BF16 = one BF16 product per projection
+                          (queries rounded to BF16, FP32 accumulation), only
+                          with precision FPP_BF16 or FPP_FP8E4M3 and without
+                          simhash_bits.  Then each hash's argmax (the query's
+                          own bucket) is re-decided exactly whenever its BF16
+                          lead is inside a window of nine estimated standard
+                          deviations of the rounding error (the factor
+                          bf16_window of Section 2.2's projections, see
+                          fpp_precision), and the other probes are ranked by
+                          the BF16 values: graded by recall.  The index's
+                          own hashing stays exact.                         */
 } fpp_params;
 
 /* Per-call search options.  Initialise with fpp_default_search_opts(). */
@@ -211,6 +224,10 @@ typedef struct fpp_index_info {
                                  c ||q|| ||x|| of x^T q (FPP_FP32: the FP32
                                  bound gamma_d; FPP_BF16: the statistical
                                  window of BF16 rows) before exact re-scoring */
+  int32_t q_pieces;           /* BF16 pieces of the search's query
+                                 projections: 3 (exact split) or 1
+                                 (hash_precision FPP_BF16)                    */
+  int32_t reserved1;
 } fpp_index_info;
 
 typedef struct fpp_index fpp_index;
@@ -300,9 +317,24 @@ fpp_status fpp_debug_candidates(const fpp_index* ix, const float* Q, int64_t m,
  *   the search computes them (tensor cores, exact three-piece BF16 split).
  * fpp_projection_error_bound: the factor c such that every such projection
  *   is within c ||q|| ||r_i|| of the exact inner product; the search's
- *   decisions rely on it (Section 2.2's projections, evaluated in pieces). */
+ *   decisions rely on it (Section 2.2's projections, evaluated in pieces).
+ *   With hash_precision FPP_BF16 the projections are one BF16 product and c
+ *   is the statistical window of their argmax decisions (not a bound). */
 fpp_status fpp_debug_projections(const fpp_index* ix, const float* Q, int64_t m,
                                  int32_t table_begin, int32_t table_end, float* out);
+
+/* Test hook of the bounded device waits (the paper has no counterpart).
+ * Every wait inside the projection kernel gives up after a limit (about 2 s
+ * by default): the CTA raises an error code, lets the copies and tensor-core
+ * operations it issued complete, frees its tensor memory and exits, and the
+ * call returns FPP_ETIMEOUT with the context still usable.  This setting
+ * applies to later fpp_debug_projections calls only (never to builds or
+ * searches): wait_cycles > 0 replaces the limit (in SM clock cycles; 0 = the
+ * default) and withhold = 1 makes the first CTA skip the loads of its first
+ * K chunk, so that its tensor-core warp's wait for them runs out.  Reset
+ * with (0, 0).  Errors: FPP_EINVAL for withhold not 0 or 1, or a negative
+ * wait_cycles. */
+fpp_status fpp_debug_wait_test(int32_t withhold, int64_t wait_cycles);
 fpp_status fpp_projection_error_bound(const fpp_index* ix, double* factor);
 
 /* Exact search: top-k of every query over all of X by inner product
@@ -416,6 +448,16 @@ fpp_status fpp_server_create(const fpp_index* ix, const fpp_server_cfg* cfg,
  * FPP_EBUSY when max_queue requests are already waiting. */
 fpp_status fpp_server_submit(fpp_server* s, const float* q, int32_t nq, int32_t k,
                              int32_t probes, uint64_t* req_id);
+
+/* Queues nreq requests in one call, as nreq fpp_server_submit calls would:
+ * request r has nq[r] consecutive query rows of q (host or device memory;
+ * the rows of the requests follow each other), k[r] results and probes[r]
+ * probes per table; req_ids [nreq] receives their ids.  On an error the
+ * requests before the failing one stay queued, the failing one and the rest
+ * get id 0, and the status is that of fpp_server_submit. */
+fpp_status fpp_server_submit_many(fpp_server* s, const float* q, int32_t nreq,
+                                  const int32_t* nq, const int32_t* k, const int32_t* probes,
+                                  uint64_t* req_ids);
 
 /* Waits up to timeout_us microseconds (< 0: without limit, 0: no wait) for
  * request req_id.  When it is complete, writes ids [nq][k] and scores

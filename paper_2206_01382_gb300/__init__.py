@@ -40,7 +40,7 @@ class fpp_params(ctypes.Structure):
                 ("R", ctypes.c_void_p), ("precision", ctypes.c_int32),
                 ("rerank_k", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("center", ctypes.c_int32), ("simhash_bits", ctypes.c_int32),
-                ("center_vec", ctypes.c_void_p)]
+                ("center_vec", ctypes.c_void_p), ("hash_precision", ctypes.c_int32)]
 
 
 class fpp_search_opts(ctypes.Structure):
@@ -94,7 +94,8 @@ class fpp_index_info(ctypes.Structure):
                 ("device_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_float),
                 ("rerank_k", ctypes.c_int32), ("center", ctypes.c_int32),
                 ("simhash_bits", ctypes.c_int32), ("r_pieces", ctypes.c_int32),
-                ("score_error_factor", ctypes.c_double)]
+                ("score_error_factor", ctypes.c_double), ("q_pieces", ctypes.c_int32),
+                ("reserved1", ctypes.c_int32)]
 
 
 _lib = None
@@ -137,6 +138,7 @@ def load(path: str | None = None):
         "fpp_debug_projections": (ctypes.c_int, [vp, f32p, i64, i32, i32, vp]),
         "fpp_projection_error_bound": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
         "fpp_bruteforce_static": (ctypes.c_int, [f32p, i64, i32, f32p, i64, i32, vp, vp, vp]),
+        "fpp_debug_wait_test": (ctypes.c_int, [i32, i64]),
         "fpp_launch_count": (u64, []),
         "fpp_alloc_count": (u64, []),
         "fpp_merge_topk": (ctypes.c_int, [vp, vp, i32, i64, i32, vp, vp]),
@@ -147,6 +149,7 @@ def load(path: str | None = None):
         "fpp_server_submit": (ctypes.c_int, [vp, f32p, i32, i32, i32,
                                              ctypes.POINTER(ctypes.c_uint64)]),
         "fpp_server_poll": (ctypes.c_int, [vp, u64, vp, vp, i32, ctypes.POINTER(ctypes.c_float)]),
+        "fpp_server_submit_many": (ctypes.c_int, [vp, f32p, i32, vp, vp, vp, vp]),
         "fpp_server_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(fpp_server_stats)]),
         "fpp_server_destroy": (None, [vp]),
     }
@@ -227,7 +230,7 @@ def fpp_default_params() -> fpp_params:
 def fpp_build(X, L: int, D: int, alpha: float, seed: int = 0, R=None, iprobes: int = 1,
               kappa: int = 0, precision: int = FPP_FP32, rerank_k: int = 100,
               center: bool = False, center_vec=None, simhash_bits: int = 0,
-              stream=None) -> ctypes.c_void_p:
+              stream=None, hash_precision: int = FPP_FP32) -> ctypes.c_void_p:
     """Builds an index over X [n][d]; returns the opaque handle."""
     lib = load()
     X = _f32(X)
@@ -236,6 +239,7 @@ def fpp_build(X, L: int, D: int, alpha: float, seed: int = 0, R=None, iprobes: i
     p.iprobes, p.kappa, p.precision, p.rerank_k = iprobes, kappa, precision, rerank_k
     p.center = 1 if center else 0
     p.simhash_bits = simhash_bits
+    p.hash_precision = hash_precision
     cv = _f32(center_vec) if center_vec is not None else None
     p.center_vec = _ptr(cv)
     Rc = _f32(R) if R is not None else None
@@ -358,6 +362,11 @@ def fpp_debug_projections(ix, Q, table_begin: int = 0, table_end: int = 0) -> np
     return out
 
 
+def fpp_debug_wait_test(withhold: int, wait_cycles: int) -> None:
+    """Test hook of the projection kernel's bounded waits (see include/fpp.h)."""
+    _check(load().fpp_debug_wait_test(int(withhold), int(wait_cycles)))
+
+
 def fpp_projection_error_bound(ix) -> float:
     f = ctypes.c_double()
     _check(load().fpp_projection_error_bound(ix, ctypes.byref(f)))
@@ -471,6 +480,19 @@ class Server:
         _check(load().fpp_server_submit(self.handle, _ptr(q), nq, k, probes, ctypes.byref(rid)))
         self._shape[rid.value] = (nq, k)
         return rid.value
+
+    def submit_many(self, q, sizes, ks, probes) -> list:
+        """Queues len(sizes) requests whose query rows follow each other in q."""
+        q = _f32(np.atleast_2d(np.asarray(q, dtype=np.float32)) if not _is_torch(q) else q)
+        sz = np.ascontiguousarray(sizes, dtype=np.int32)
+        kk = np.ascontiguousarray(ks, dtype=np.int32)
+        pp = np.ascontiguousarray(np.broadcast_to(np.asarray(probes, dtype=np.int32), sz.shape))
+        ids = np.zeros(sz.size, dtype=np.uint64)
+        _check(load().fpp_server_submit_many(self.handle, _ptr(q), int(sz.size), sz.ctypes.data,
+                                             kk.ctypes.data, pp.ctypes.data, ids.ctypes.data))
+        for rid, n, k in zip(ids.tolist(), sz.tolist(), kk.tolist()):
+            self._shape[rid] = (n, k)
+        return ids.tolist()
 
     def poll(self, rid: int, timeout_us: int = -1):
         nq, k = self._shape[rid]

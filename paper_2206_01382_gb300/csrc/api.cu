@@ -159,8 +159,12 @@ struct fpp_index {
   float* R = nullptr;          // [2 L D][dpad]
   void* Rs = nullptr;          // [2 L D][pieces Kp] BF16 pieces of R (tensor-core operand)
   int Kp = 0;
-  int pieces = 3;              // 3: exact split (FPP_FP32); 1: plain BF16 (FPP_BF16)
+  int pieces = 3;              // BF16 pieces of a projected row: 3 (exact split)
   int bpieces = 3;             // 1: every coordinate of R is a BF16 value (three products)
+  int qpieces = 3;             // pieces of the search's query projections: 3, or 1 with
+                               // hash_precision FPP_BF16 (one BF16 product)
+  double qgamma = 0.0;         // error factor of the query projections the probe
+                               // decisions use (a bound for 3 pieces, a window for 1)
   void* Xb = nullptr;          // [n][ldxb] BF16 copy of X (FPP_BF16 only)
   int64_t ldxb = 0;
   uint8_t* Xq = nullptr;       // [n][ldxq] FP8 e4m3 copy of X (FPP_FP8E4M3 only)
@@ -265,14 +269,23 @@ struct BuildScratch {
 // vectors of tables [t0, t0 + nt): split into BF16 pieces, tensor-core GEMM.
 fpp_status project_rows(const fpp_index* ix, const float* src, int64_t rc, DevBuf& split, int t0,
                         int nt, float* out, int64_t ldp, int* err, cudaStream_t st,
-                        uint64_t* lists = nullptr, int EL = 0) {
-  FPP_TRY(split.ensure((size_t)rc * ix->pieces * ix->Kp * 2));
-  FPP_TRY(split_to_bf16(src, rc, ix->dpad, ix->d, ix->pieces, split.p, st));
+                        uint64_t* lists = nullptr, int EL = 0, long long wait_cycles = 0,
+                        int withhold = 0, int pieces = 0) {
+  // pieces: the rows' BF16 pieces (0: the index's exact split); R keeps its
+  // pieces layout and only its first piece is read for one-piece rows
+  if (!pieces) pieces = ix->pieces;
+  FPP_TRY(split.ensure((size_t)rc * pieces * ix->Kp * 2));
+  FPP_TRY(split_to_bf16(src, rc, ix->dpad, ix->d, pieces, split.p, st));
   const char* rb =
       static_cast<const char*>(ix->Rs) + (size_t)2 * t0 * ix->D * ix->pieces * ix->Kp * 2;
-  return project_tc(split.p, rc, rb, 2ll * nt * ix->D, ix->Kp, ix->pieces, ix->bpieces, ix->D, EL,
-                    out, ldp, lists, err, st);
+  return project_tc(split.p, rc, rb, 2ll * nt * ix->D, ix->Kp, pieces,
+                    pieces == 1 ? 1 : ix->bpieces, ix->D, EL, out, ldp, lists, err, st,
+                    wait_cycles, withhold, ix->pieces);
 }
+
+// Test hook of fpp_debug_projections (fpp_debug_wait_test).
+std::atomic<int> g_wait_test_withhold{0};
+std::atomic<long long> g_wait_test_cycles{0};
 
 // List length of the fused projection epilogue for a probe budget, or 0
 // when the projections must be stored (D must divide 256, and the P + 1
@@ -419,6 +432,14 @@ fpp_status validate_params(int64_t n, int32_t d, const fpp_params* p) {
     set_error("precision must be FPP_FP32, FPP_BF16 or FPP_FP8E4M3");
     return FPP_EINVAL;
   }
+  if (p->hash_precision != FPP_FP32 && p->hash_precision != FPP_BF16) {
+    set_error("hash_precision must be FPP_FP32 or FPP_BF16");
+    return FPP_EINVAL;
+  }
+  if (p->hash_precision == FPP_BF16 && (p->precision == FPP_FP32 || p->simhash_bits)) {
+    set_error("hash_precision FPP_BF16 needs precision FPP_BF16 or FPP_FP8E4M3 and no simhash_bits");
+    return FPP_EINVAL;
+  }
   if (p->simhash_bits < 0 || p->simhash_bits % 256 || p->simhash_bits > 1024 ||
       p->simhash_bits > 2ll * p->L * p->D) {
     set_error("simhash_bits must be 0 or a multiple of 256 up to min(1024, 2 L D)");
@@ -457,6 +478,8 @@ fpp_status build_impl(const float* X, int64_t n, int32_t d, const fpp_params* p,
   // rounding error would send far more probe decisions to the exact pass.
   ix->pieces = 3;
   ix->gamma = tc_error_bound_factor(ix->Kp, 3);
+  ix->qpieces = p->hash_precision == FPP_BF16 ? 1 : 3;
+  ix->qgamma = ix->qpieces == 1 ? bf16_window_factor(d) : ix->gamma;
   if (p->precision == FPP_BF16) {
     ix->rerank_k = p->rerank_k;
     ix->score_gamma = bf16_window_factor(d);
@@ -835,7 +858,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   const int EL = fused_list_len(ix, pl.pmax);
   FPP_TRY(project_rows(ix, qp, mc, ws.qsplit, pl.tb, nt, ws.proj.as<float>(), ldp,
                        reinterpret_cast<int*>(ws.stats.as<unsigned long long>() + 9), st,
-                       EL ? ws.proj.as<uint64_t>() : nullptr, EL));
+                       EL ? ws.proj.as<uint64_t>() : nullptr, EL, 0, 0, ix->qpieces));
   if (ev) FPP_CUDA(cudaEventRecord(ev[1], st));
   FPP_TRY(launch_query_norms(qp, mc, ix->dpad, ix->d, ws.qnorm.as<float>(), st));
   if (pl.sim_keep > 0) {
@@ -861,7 +884,12 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
     pa.Rb = static_cast<const uint16_t*>(ix->Rs);
     pa.ldrb = (int64_t)ix->pieces * ix->Kp;
   }
-  pa.rmax = ix->rmax; pa.gamma = ix->gamma; pa.gammaf = (float)(ix->gamma * 1.0001);
+  pa.rmax = ix->rmax; pa.gamma = ix->qgamma; pa.gammaf = (float)(ix->qgamma * 1.0001);
+  pa.argmax_only = ix->qpieces == 1 ? 1 : 0;
+  // the argmax pass's pair list (list mode) reuses the pair-window buffer,
+  // which list mode does not use: 4 words per item hold 2 pairs
+  pa.amax_pairs = ws.recheck_s.as<uint32_t>();
+  pa.amax_count = reinterpret_cast<unsigned*>(ws.stats.as<unsigned long long>() + 14);
   pa.probes_pq = ppq; pa.probes = pl.pmax;
   pa.out = ws.probes.as<uint32_t>();
   pa.recheck = ws.recheck.as<uint32_t>();
@@ -901,11 +929,10 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   // otherwise the exact total, read back
   const uint64_t bound = (uint64_t)mc * nt * pl.pmax * std::max<uint32_t>(ix->max_bucket_kept, 1);
   uint64_t need = bound;
-  bool exact = false;
-  if (bound > ws.cand_cap && (pl.no_grow || bound > ix->cand_budget_entries)) {
+  const bool exact = bound > ws.cand_cap && (pl.no_grow || bound > ix->cand_budget_entries);
+  if (exact) {
     FPP_CUDA(cudaMemcpyAsync(&need, stv + 12, 8, cudaMemcpyDeviceToHost, st));
     FPP_CUDA(cudaStreamSynchronize(st));
-    exact = true;
   }
   if (need > ws.cand_cap && pl.no_grow) {
     set_error("the batch's candidates exceed the candidate buffer");
@@ -1014,6 +1041,7 @@ fpp_status prepare_workspace(fpp_index* ix, Workspace& ws, const SearchPlan& pl,
   const int EL = allow_fused ? fused_list_len(ix, pl.pmax) : 0;
   const size_t tile = EL ? (size_t)mc * 2 * nt * (EL + 1) * 8 : (size_t)mc * ldp * 4;
   FPP_TRY(ws.proj.ensure(tile, false, st));
+  FPP_TRY(ws.qsplit.ensure((size_t)mc * ix->pieces * ix->Kp * 2));   // the queries' BF16 pieces
   FPP_TRY(ws.probes.ensure((size_t)mc * nt * pl.pmax * 4, false, st));
   FPP_TRY(ws.qnorm.ensure((size_t)mc * 4, false, st));
   FPP_TRY(ws.recheck.ensure((size_t)mc * nt * 4, false, st));
@@ -1638,6 +1666,7 @@ fpp_status fpp_index_get_info(const fpp_index* ix, fpp_index_info* info) {
   info->simhash_bits = ix->sig_words * 32;
   info->r_pieces = ix->bpieces;
   info->score_error_factor = ix->score_gamma;
+  info->q_pieces = ix->qpieces;
   return FPP_OK;
 }
 
@@ -1823,16 +1852,35 @@ fpp_status fpp_debug_projections(const fpp_index* cix, const float* Q, int64_t m
                           cudaMemcpyDefault));
     FPP_TRY(project_rows(ix, ix->ws.qpad.as<float>(), c, ix->ws.qsplit, pl.tb, nt,
                          ix->ws.proj.as<float>(), ldp,
-                         reinterpret_cast<int*>(ix->ws.stats.as<unsigned long long>() + 9), 0));
+                         reinterpret_cast<int*>(ix->ws.stats.as<unsigned long long>() + 9), 0,
+                         nullptr, 0, g_wait_test_cycles.load(), g_wait_test_withhold.load(),
+                         ix->qpieces));
     FPP_CUDA(cudaMemcpy2D(out + q0 * N, N * 4, ix->ws.proj.p, ldp * 4, N * 4, c, cudaMemcpyDefault));
   }
+  unsigned long long flag = 0;
+  FPP_CUDA(cudaMemcpy(&flag, ix->ws.stats.as<unsigned long long>() + 9, 8, cudaMemcpyDeviceToHost));
+  if (flag) {
+    set_error("projection: a bounded wait ran out (code " + std::to_string(flag & 0xFFFFFFFFull) + ")");
+    return FPP_ETIMEOUT;
+  }
+  return FPP_OK;
+}
+
+fpp_status fpp_debug_wait_test(int32_t withhold, int64_t wait_cycles) {
+  g_err.clear();
+  if (withhold < 0 || withhold > 1 || wait_cycles < 0) {
+    set_error("withhold must be 0 or 1 and wait_cycles >= 0");
+    return FPP_EINVAL;
+  }
+  g_wait_test_withhold.store(withhold);
+  g_wait_test_cycles.store(wait_cycles);
   return FPP_OK;
 }
 
 fpp_status fpp_projection_error_bound(const fpp_index* ix, double* factor) {
   g_err.clear();
   if (!ix || !factor) { set_error("NULL argument"); return FPP_EINVAL; }
-  *factor = ix->gamma;
+  *factor = ix->qgamma;
   return FPP_OK;
 }
 
@@ -2038,6 +2086,81 @@ fpp_status fpp_server_create(const fpp_index* ix, const fpp_server_cfg* cfg, fpp
     set_error(std::string("fpp_server_create: ") + e.what());
     return FPP_EINTERNAL;
   }
+}
+
+fpp_status fpp_server_submit_many(fpp_server* s, const float* q, int32_t nreq, const int32_t* nq,
+                                  const int32_t* k, const int32_t* probes, uint64_t* req_ids) {
+  g_err.clear();
+  if (!s || !q || !nq || !k || !probes || !req_ids || nreq < 0) {
+    set_error("NULL argument or nreq < 0");
+    return FPP_EINVAL;
+  }
+  // copy every request first, then queue them under one lock with one
+  // wake-up, so that a free slot sees the whole group at once
+  std::vector<std::unique_ptr<ServerRequest>> rs;
+  fpp_status st = FPP_OK;
+  int32_t bad = nreq;
+  try {
+    int64_t row = 0;
+    const bool dev = is_device_ptr(q);
+    for (int32_t r = 0; r < nreq; ++r) {
+      if (nq[r] < 1 || nq[r] > s->cfg.max_batch || k[r] < 1 || k[r] > s->cfg.k_max ||
+          probes[r] < 1 || probes[r] > s->cfg.probes_max) {
+        set_error("request " + std::to_string(r) + ": nq, k or probes out of range");
+        st = FPP_EINVAL;
+        bad = r;
+        break;
+      }
+      auto x = std::make_unique<ServerRequest>();
+      x->nq = nq[r];
+      x->k = k[r];
+      x->probes = probes[r];
+      const size_t nel = (size_t)nq[r] * s->ix->d;
+      x->q.resize(nel);
+      const float* src = q + row * s->ix->d;
+      if (dev) {
+        if (cudaMemcpy(x->q.data(), src, nel * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+          set_error("copying the queries failed");
+          st = FPP_ECUDA;
+          bad = r;
+          break;
+        }
+      } else {
+        std::memcpy(x->q.data(), src, nel * 4);
+      }
+      x->ids.resize((size_t)nq[r] * k[r]);
+      x->scores.resize((size_t)nq[r] * k[r]);
+      rs.push_back(std::move(x));
+      row += nq[r];
+    }
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    st = FPP_ENOMEM;
+    bad = (int32_t)rs.size();
+  }
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    const auto now = std::chrono::steady_clock::now();
+    for (size_t r = 0; r < rs.size(); ++r) {
+      if (s->stop || (int64_t)s->queue.size() >= s->cfg.max_queue) {
+        set_error(s->stop ? "server is shutting down" : "queue full");
+        st = FPP_EBUSY;
+        bad = (int32_t)r;
+        break;
+      }
+      ServerRequest* x = rs[r].get();
+      x->t_submit = now;
+      x->id = s->next_id++;
+      req_ids[r] = x->id;
+      s->queue.push_back(x);
+      s->reqs.emplace(x->id, std::move(rs[r]));
+      s->stats.submitted += 1;
+    }
+    s->stats.queued = s->queue.size();
+  }
+  for (int32_t x = bad; x < nreq; ++x) req_ids[x] = 0;
+  s->cv_work.notify_all();
+  return st;
 }
 
 fpp_status fpp_server_submit(fpp_server* s, const float* q, int32_t nq, int32_t k, int32_t probes,

@@ -59,6 +59,8 @@ struct __align__(8) TcShared {
   uint64_t empty[TC_STAGES];
   uint64_t tfull[2];
   uint64_t tempty[2];
+  uint64_t drain;       // the MMA warp's last commit when the CTA aborts
+  long long limit;      // cycles a wait may take before the CTA aborts
   uint32_t tmem_base;
   int abort;
   // list mode with D = 256: the second column half of every row hands its
@@ -103,12 +105,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, TcShared
   const long long t0 = clock64();
   while (!mbar_try_wait(b, parity)) {
     if (*(volatile int*)&sh->abort) return false;
-    if (clock64() - t0 > WAIT_CYCLES) {
+    if (clock64() - t0 > sh->limit) {
       atomicExch(&sh->abort, 1);
       if (err) atomicExch(err, code);
       return false;
     }
   }
+  return true;
+}
+
+// Bounded wait used while an aborting CTA drains its own copies and MMAs
+// (the abort flag is already raised, so it is not consulted).
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* b, uint32_t parity, long long limit) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(b, parity))
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 
@@ -268,7 +279,8 @@ template <int EL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                float* __restrict__ C, int64_t ldc, uint64_t* __restrict__ lists, int M, int N,
-               int Kp, int pieces, int bpieces, int D, int mfast, int* err) {
+               int Kp, int pieces, int bpieces, int D, int mfast, int* err,
+               long long wait_cycles, int withhold) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
@@ -293,7 +305,9 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       mbar_init(&sh->xfull[qq], 1);
       mbar_init(&sh->xempty[qq], 1);
     }
+    mbar_init(&sh->drain, 1);
     sh->abort = 0;
+    sh->limit = wait_cycles > 0 ? wait_cycles : WAIT_CYCLES;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -309,6 +323,9 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = sh->tmem_base;
 
+  // the stages whose copies the producer issued, and the last chunk of each
+  uint32_t issued = 0;
+  uint32_t last_g[TC_STAGES];
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
     uint32_t g = 0;
@@ -325,9 +342,14 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         int pa, pb, kb;
         chunk_pieces(c, nkb, pieces, bpieces, pa, pb, kb);
         unsigned char* st = base + s * STAGE_BYTES;
+        // test hook (withhold = 1): CTA 0 never loads its first chunk, so the
+        // MMA warp's wait for it runs out
+        if (withhold && blockIdx.x == 0 && g == 0) continue;
         mbar_expect_tx(&sh->full[s], STAGE_BYTES);
         tma_load_2d(st, &mapA, pa * Kp + kb * TC_BK, m0, &sh->full[s]);
         tma_load_2d(st + A_TILE, &mapB, pb * Kp + kb * TC_BK, n0, &sh->full[s]);
+        issued |= 1u << s;
+        last_g[s] = g;
       }
       if (!ok) break;
     }
@@ -578,6 +600,20 @@ tc_proj_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       if (!ok) break;
     }
   }
+  // An aborted CTA drains before it frees TMEM and exits: the copies it
+  // issued land (each stage's last issued chunk completes its full barrier;
+  // a stage is refilled only after that) and its MMAs complete (one commit
+  // tracks every MMA the issuing thread started).
+  __syncthreads();
+  if (*(volatile int*)&sh->abort) {
+    if (warp == 0 && lane == 0) {
+      for (int s = 0; s < TC_STAGES; ++s)
+        if ((issued >> s) & 1u) mbar_wait_drain(&sh->full[s], (last_g[s] / TC_STAGES) & 1, sh->limit);
+    } else if (warp == 1 && lane == 0) {
+      mma_commit(&sh->drain);
+      mbar_wait_drain(&sh->drain, 0, sh->limit);
+    }
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
@@ -744,7 +780,7 @@ namespace {
 template <int EL>
 fpp_status launch_proj(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int64_t ldc,
                        uint64_t* lists, int64_t M, int64_t N, int Kp, int pieces, int bpieces,
-                       int D, int* err, cudaStream_t st) {
+                       int D, int* err, cudaStream_t st, long long wait_cycles, int withhold) {
   const size_t smem = 1024 + TC_STAGES * STAGE_BYTES + sizeof(TcShared);
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
@@ -760,7 +796,8 @@ fpp_status launch_proj(const CUtensorMap& ma, const CUtensorMap& mb, float* C, i
   const int grid = (int)std::min<int64_t>(ntiles, sms);
   const int mfast = N * bpieces > M * pieces ? 1 : 0;   // B's bytes read > A's
   tc_proj_kernel<EL><<<grid, TC_THREADS, smem, st>>>(ma, mb, C, ldc, lists, (int)M, (int)N, Kp,
-                                                     pieces, bpieces, D, mfast, err);
+                                                     pieces, bpieces, D, mfast, err, wait_cycles,
+                                                     withhold);
   FPP_LAUNCHED();
   return FPP_OK;
 }
@@ -790,8 +827,13 @@ fpp_status gemm_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, i
 
 fpp_status project_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, int pieces,
                       int bpieces, int D, int EL, float* C, int64_t ldc, uint64_t* lists, int* err,
-                      cudaStream_t st) {
+                      cudaStream_t st, long long wait_cycles, int withhold, int b_row_pieces) {
   if (M <= 0 || N <= 0) return FPP_OK;
+  if (!b_row_pieces) b_row_pieces = pieces;
+  if (b_row_pieces < pieces) {
+    set_error("project_tc: B rows hold fewer pieces than A's");
+    return FPP_EINTERNAL;
+  }
   if (Kp % TC_BK || (pieces != 1 && pieces != 3) || (bpieces != 1 && bpieces != pieces) ||
       M >= (1ll << 31) || N >= (1ll << 31)) {
     set_error("project_tc: bad shape");
@@ -807,12 +849,16 @@ fpp_status project_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp
   }
   CUtensorMap ma, mb;
   FPP_TRY(make_map(&ma, A, M, (int64_t)pieces * Kp, TC_BM));
-  FPP_TRY(make_map(&mb, B, N, (int64_t)pieces * Kp, TC_BN));
+  FPP_TRY(make_map(&mb, B, N, (int64_t)b_row_pieces * Kp, TC_BN));
   switch (EL) {
-    case 0: return launch_proj<0>(ma, mb, C, ldc, lists, M, N, Kp, pieces, bpieces, D, err, st);
-    case 2: return launch_proj<2>(ma, mb, C, ldc, lists, M, N, Kp, pieces, bpieces, D, err, st);
-    case 4: return launch_proj<4>(ma, mb, C, ldc, lists, M, N, Kp, pieces, bpieces, D, err, st);
-    case 8: return launch_proj<8>(ma, mb, C, ldc, lists, M, N, Kp, pieces, bpieces, D, err, st);
+    case 0: return launch_proj<0>(ma, mb, C, ldc, lists, M, N, Kp, pieces, bpieces, D, err, st,
+                                    wait_cycles, withhold);
+    case 2: return launch_proj<2>(ma, mb, C, ldc, lists, M, N, Kp, pieces, bpieces, D, err, st,
+                                    wait_cycles, withhold);
+    case 4: return launch_proj<4>(ma, mb, C, ldc, lists, M, N, Kp, pieces, bpieces, D, err, st,
+                                    wait_cycles, withhold);
+    case 8: return launch_proj<8>(ma, mb, C, ldc, lists, M, N, Kp, pieces, bpieces, D, err, st,
+                                    wait_cycles, withhold);
     default:
       set_error("project_tc: list length must be 0, 2, 4 or 8");
       return FPP_EINTERNAL;

@@ -48,9 +48,13 @@ int tc_list_len(int want);
 float tc_list_trunc(int D);
 // bpieces = 1: every element of B is a BF16 value (its mid and lo pieces are
 // zero), three products per K block instead of six; else bpieces = pieces.
+// wait_cycles > 0 replaces the default limit (about 2 s) of every bounded
+// wait; withhold = 1 makes CTA 0 skip its first chunk's loads (a test of the
+// bounded waits: the launch then reports a run-out wait in *err).
 fpp_status project_tc(const void* A, int64_t M, const void* B, int64_t N, int Kp, int pieces,
                       int bpieces, int D, int EL, float* C, int64_t ldc, uint64_t* lists, int* err,
-                      cudaStream_t st);
+                      cudaStream_t st, long long wait_cycles = 0, int withhold = 0,
+                      int b_row_pieces = 0);
 
 // Build (build_kernels.cu).
 struct HashArgs {
@@ -181,6 +185,11 @@ struct ProbeArgs {
                              // projections; 16-byte aligned), or NULL
   unsigned long long* rechecks;  // statistics counter or NULL
   unsigned long long* full_rechecks;  // items of the full pass (statistics) or NULL
+  uint32_t* amax_pairs;      // argmax pass, list mode: the uncertain (item, hash) pairs
+  unsigned* amax_count;      //   [2 mq nt] and their device counter
+  int argmax_only;            // 1 (one-piece BF16 query projections): only each hash's
+                             // argmax must be certain; the other probes take the FP32
+                             // ranking of the BF16 values
   unsigned long long* gcap_flag;  // global budget: queries whose per-table cap may have
                                   // bound (some table gave all its `probes` slots), or NULL
 };

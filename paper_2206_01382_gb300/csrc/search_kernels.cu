@@ -335,7 +335,11 @@ probe_kernel(ProbeArgs a, int pmax) {
   warp_select(col, Sc, Tsel, pout);
 
   bool certain = C >= Tsel;
-  if (certain && boundary) {
+  if (a.argmax_only) {
+    // the argmax pass has made each hash's winner exact; the other probes
+    // take the ranking of the BF16 values as it stands
+    certain = C >= P;
+  } else if (certain && boundary) {
     // FP32 arithmetic (the FP64 pipe is slow); every factor is positive and
     // the 1.001 margin covers the few roundings of this expression.  Pair
     // scores from truncated list values may be low by trunc times the two
@@ -375,11 +379,195 @@ probe_kernel(ProbeArgs a, int pmax) {
   }
 }
 
+// Argmax pass of the one-piece BF16 query projections (argmax_only): each
+// hash's winner (the query's own bucket) is made exact, the rest of the
+// ranking keeps the BF16 values.  A winner is certain when its BF16 lead
+// over the runner-up exceeds twice the window eps = gammaf |q| max|r| (plus
+// the list truncation) and its value exceeds eps (its sign); otherwise every
+// entry whose BF16 value lies within that margin of the top is re-computed
+// exactly (compensated dot products on the FP32 rows) and written back in
+// place.  Entries left out have BF16 values below the top's by more than
+// 2 eps, so exact values below the top entry's: the largest exact value is
+// the winner.  List mode re-sorts the corrected list; a window that reaches
+// past the list (its cut) re-computes all D entries and rebuilds the list.
+constexpr int SMALL_E = 8;   // longest per-hash list of the projection epilogue
+
+__device__ __forceinline__ float list_val(uint64_t k) {
+  return k ? __uint_as_float((uint32_t)(k >> 32) - 1u) : 0.f;
+}
+
+__device__ __forceinline__ uint64_t exact_key(float v, uint32_t i, int D) {
+  const uint32_t h = i + (v < 0.f ? (uint32_t)D : 0u);
+  return ((uint64_t)(__float_as_uint(fabsf(v)) + 1u) << 32) | (uint64_t)(0xFFFFFFFFu - h);
+}
+
+// the warp's exact projection of query row qv onto random vector row (2t + j) D + i
+__device__ __forceinline__ float exact_proj(const ProbeArgs& a, const float* qv, int t, int j,
+                                            uint32_t i) {
+  const float* rows[1] = {a.R + ((int64_t)(2 * t + j) * a.D + i) * a.ldr};
+  FF v[1];
+  warp_dot2_gather_ff<1>(qv, rows, (int)(a.ldr / 4), v);
+  return v[0].hi;   // the exact value rounded to FP32
+}
+
+// List mode, first kernel, thread per (query, table): the certainty test of
+// both hashes; an uncertain hash is listed as a pair (item, hash) for the
+// second kernel, and an item whose window reaches past a list (its cut) is
+// listed for the exact passes, which re-decide its whole probe set from all
+// 2D projections.
+__global__ void __launch_bounds__(256)
+probe_argmax_test_kernel(ProbeArgs a) {
+  const int D = a.D, EL = a.EL, LS = EL + 1;
+  const int64_t nitems = a.mq * a.nt;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nitems;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = idx / a.nt;
+    const int t = a.tb + (int)(idx % a.nt);
+    uint32_t bad = 0;
+    bool past = false;
+    for (int j = 0; j < 2; ++j) {
+      const uint64_t* L = a.lists + (idx * 2 + j) * (int64_t)LS;
+      const float v0 = list_val(L[0]), v1 = D > 1 ? list_val(L[1]) : 0.f;
+      const float eps = a.gammaf * a.qnorm[q] * a.rmax[2 * t + j] + a.trunc * v0;
+      const float need = (2.f * eps + 6.0e-8f * (v0 + v1)) * 1.001f + 1e-30f;
+      if (v0 - v1 > need && v0 > eps * 1.001f) continue;
+      bad |= 1u << j;
+      if (list_val(L[EL]) >= v0 - need) past = true;
+    }
+    if (past) {
+      a.recheck[atomicAdd(a.recheck_count, 1u)] = (uint32_t)idx;
+      if (a.rechecks) atomicAdd(a.rechecks, 1ull);
+    } else {
+      for (int j = 0; j < 2; ++j)
+        if ((bad >> j) & 1u) a.amax_pairs[atomicAdd(a.amax_count, 1u)] = (uint32_t)(idx * 2 + j);
+    }
+  }
+}
+
+// List mode, second kernel: four listed hashes per warp, eight lanes each.
+// The window entries (a prefix of the sorted list) are re-computed exactly
+// by the lane group (compensated dot products on the FP32 rows, float-float
+// sums combined across the group) and the list is re-sorted.
+__global__ void __launch_bounds__(256)
+probe_argmax_fix_kernel(ProbeArgs a) {
+  const int lane = threadIdx.x & 31, g = lane >> 3, gl = lane & 7;
+  const unsigned gmask = 0xFFu << (g * 8);
+  const int D = a.D, EL = a.EL, LS = EL + 1;
+  const unsigned n = *a.amax_count;
+  const int nf4 = (int)(a.ldr / 4);
+  for (unsigned base = ((unsigned)blockIdx.x * 8 + (threadIdx.x >> 5)) * 4; base < n;
+       base += (unsigned)gridDim.x * 32) {
+    const unsigned pi = base + (unsigned)g;
+    if (pi >= n) continue;   // the whole 8-lane group
+    const uint32_t pair = a.amax_pairs[pi];
+    const int64_t idx = pair >> 1;
+    const int j = (int)(pair & 1u);
+    const int64_t q = idx / a.nt;
+    const int t = a.tb + (int)(idx % a.nt);
+    uint64_t* L = const_cast<uint64_t*>(a.lists) + (idx * 2 + j) * (int64_t)LS;
+    const float v0 = list_val(L[0]), v1 = D > 1 ? list_val(L[1]) : 0.f;
+    const float eps = a.gammaf * a.qnorm[q] * a.rmax[2 * t + j] + a.trunc * v0;
+    const float need = (2.f * eps + 6.0e-8f * (v0 + v1)) * 1.001f + 1e-30f;
+    const float thr = v0 - need;
+    const float4* q4 = reinterpret_cast<const float4*>(a.Q + q * a.ldq);
+    uint64_t keys[SMALL_E];
+#pragma unroll
+    for (int e = 0; e < SMALL_E; ++e) {
+      keys[e] = e < EL ? L[e] : 0ull;
+      if (e < EL && keys[e] && list_val(keys[e]) >= thr) {   // uniform over the group
+        const uint32_t i = (0xFFFFFFFFu - (uint32_t)keys[e]) % (uint32_t)D;
+        const float4* r4 = reinterpret_cast<const float4*>(
+            a.R + ((int64_t)(2 * t + j) * D + i) * a.ldr);
+        float p = 0.f, sc = 0.f;
+        for (int c = gl; c < nf4; c += 8) {
+          const float4 x = q4[c], y = __ldg(r4 + c);
+          dot2_step(x.x, y.x, p, sc);
+          dot2_step(x.y, y.y, p, sc);
+          dot2_step(x.z, y.z, p, sc);
+          dot2_step(x.w, y.w, p, sc);
+        }
+        FF v{p, sc};
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+          FF w{__shfl_xor_sync(gmask, v.hi, o), __shfl_xor_sync(gmask, v.lo, o)};
+          v = ff_add(v, w);
+        }
+        keys[e] = exact_key(ff_norm(v).hi, i, D);
+      }
+    }
+    if (gl == 0) {
+      // insertion sort, descending (EL <= 8)
+#pragma unroll
+      for (int e = 1; e < SMALL_E; ++e) {
+#pragma unroll
+        for (int f = SMALL_E - 1; f >= 1; --f) {
+          if (f <= e && keys[f] > keys[f - 1]) {
+            const uint64_t tv = keys[f];
+            keys[f] = keys[f - 1];
+            keys[f - 1] = tv;
+          }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < SMALL_E; ++e)
+        if (e < EL) L[e] = keys[e];
+    }
+  }
+}
+
+// Stored projections (D > 256 or long lists): warp per (query, table); the
+// corrected values overwrite the projections the probe kernel then ranks.
+__global__ void __launch_bounds__(256)
+probe_argmax_rows_kernel(ProbeArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int D = a.D;
+  const int64_t nitems = a.mq * a.nt;
+  const int64_t stride = (int64_t)gridDim.x * 8;
+  for (int64_t it = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); it < nitems; it += stride) {
+    const int64_t q = it / a.nt;
+    const int tl = (int)(it % a.nt);
+    const int t = a.tb + tl;
+    const float* qv = a.Q + q * a.ldq;
+    for (int j = 0; j < 2; ++j) {
+      float* row = const_cast<float*>(a.P) + q * a.ldp + (int64_t)(2 * tl + j) * D;
+      // the two largest |p| of the row (ties: either; values only)
+      float b0 = -1.f, b1 = -1.f;
+      for (int i = lane; i < D; i += 32) {
+        const float v = fabsf(row[i]);
+        if (v > b0) { b1 = b0; b0 = v; } else if (v > b1) b1 = v;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float c0 = __shfl_xor_sync(FULL, b0, o), c1 = __shfl_xor_sync(FULL, b1, o);
+        const float n0 = fmaxf(b0, c0);
+        b1 = fmaxf(fminf(b0, c0), fmaxf(b1, c1));
+        b0 = n0;
+      }
+      const float v0 = b0, v1 = D > 1 ? fmaxf(b1, 0.f) : 0.f;
+      const float eps = a.gammaf * a.qnorm[q] * a.rmax[2 * t + j];
+      const float need = (2.f * eps + 6.0e-8f * (v0 + v1)) * 1.001f + 1e-30f;
+      if (v0 - v1 > need && v0 > eps * 1.001f) continue;   // uniform over the warp
+      const float thr = v0 - need;
+      for (int i0 = 0; i0 < D; i0 += 32) {
+        const int i = i0 + lane;
+        const bool cand = i < D && fabsf(row[i]) >= thr;
+        unsigned cm = __ballot_sync(FULL, cand);
+        while (cm) {
+          const int src = __ffs(cm) - 1;
+          cm &= cm - 1;
+          const float v = exact_proj(a, qv, t, j, (uint32_t)(i0 + src));
+          if (lane == src) row[i] = v;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // Thread-per-(query, table) variant of the fast pass for small budgets in
 // list mode (P + 1 <= EL <= 8): the same candidate pairs, selection and
 // margin test on the SE = EL list entries per hash, held in registers (the
 // loops are unrolled over SE, so a list of 2 costs 4 candidate pairs).
-constexpr int SMALL_E = 8;
 
 template <int SE>
 __global__ void __launch_bounds__(256)
@@ -436,7 +624,9 @@ probe_small_kernel(ProbeArgs a) {
   }
   const bool boundary = (int64_t)P < NB;
   bool certain = C >= (boundary ? P + 1 : P);
-  if (certain && boundary) {
+  if (a.argmax_only) {
+    certain = C >= P;   // each hash's winner made exact by the argmax pass
+  } else if (certain && boundary) {
     uint64_t kP = 0, kP1 = 0;
 #pragma unroll
     for (int e = 0; e <= SE; ++e) {
@@ -2436,6 +2626,27 @@ fpp_status launch_probe(const ProbeArgs& a, cudaStream_t st, cudaEvent_t exact_b
   if (a.lists || a.recheck_s) FPP_CUDA(cudaMemsetAsync(a.recheck2_count, 0, sizeof(unsigned), st));
   const int S = pow2_ceil((a.D + 31) / 32);
   fpp_status s;
+  if (a.argmax_only) {
+    // one-piece BF16 projections: make every hash's winner exact first
+    int dv = 0, nsm = 0;
+    FPP_CUDA(cudaGetDevice(&dv));
+    FPP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dv));
+    if (a.lists) {
+      if (a.EL > SMALL_E) {
+        set_error("argmax pass: lists longer than 8 entries");
+        return FPP_EINTERNAL;
+      }
+      FPP_CUDA(cudaMemsetAsync(a.amax_count, 0, sizeof(unsigned), st));
+      const int64_t need = ceil_div(warps, (int64_t)256);
+      probe_argmax_test_kernel<<<(unsigned)std::min<int64_t>(need, (int64_t)nsm * 16), 256, 0, st>>>(a);
+      FPP_LAUNCHED();
+      probe_argmax_fix_kernel<<<(unsigned)nsm * 8, 256, 0, st>>>(a);
+    } else {
+      const int64_t need = ceil_div(warps, (int64_t)8);
+      probe_argmax_rows_kernel<<<(unsigned)std::min<int64_t>(need, (int64_t)nsm * 8), 256, 0, st>>>(a);
+    }
+    FPP_LAUNCHED();
+  }
   if (a.lists && a.probes + 1 <= a.EL && a.EL <= SMALL_E) {
     const unsigned grid = (unsigned)ceil_div(warps, 256);
     if (a.EL <= 2) probe_small_kernel<2><<<grid, 256, 0, st>>>(a);

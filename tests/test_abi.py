@@ -31,7 +31,7 @@ def test_struct_sizes_match_header(lib):
     o = F.fpp_search_opts()
     lib.fpp_default_search_opts(ctypes.byref(o))
     assert (o.k, o.probes, o.k_max, o.table_begin, o.table_end) == (10, 1, 0, 0, 0)
-    assert ctypes.sizeof(F.fpp_params) == 72
+    assert ctypes.sizeof(F.fpp_params) == 80
     assert ctypes.sizeof(F.fpp_search_opts) == 64
     assert ctypes.sizeof(F.fpp_search_stats) == 96
     assert ctypes.sizeof(F.fpp_server_cfg) == 32

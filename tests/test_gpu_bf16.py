@@ -157,3 +157,50 @@ def test_fp8_rows_match_exact_path(F, rerank_k):
         ex = _exact_scores(X, Q, i8)
         fin = i8 >= 0
         assert float(np.abs(s8[fin] - ex[fin]).max()) <= 1e-5
+
+
+@pytest.mark.parametrize("d,D,L,P,K", [(256, 256, 6, 2, 512),     # lists of 4, thread per item
+                                       (128, 256, 4, 4, 256),     # lists of 8
+                                       (960, 1024, 2, 4, 256)])   # stored projections
+def test_one_piece_bf16_hashing_keeps_every_winner_exact(F, d, D, L, P, K):
+    # hash_precision FPP_BF16: the queries are projected with one BF16
+    # product; every hash's winner (the query's own bucket, the first probe)
+    # is re-decided exactly when its BF16 lead is inside the window, so the
+    # single-probe buckets equal the oracle's; the other probes are ranked by
+    # the BF16 values (graded by recall); scores stay exact
+    X, Q = W.small_mixture(20000, 300, d, K, 0.3 / np.sqrt(d), 600 + D + d)
+    ix = F.Index(X, L, D, 0.3, seed=60 + d, precision=F.FPP_BF16, hash_precision=F.FPP_BF16)
+    assert ix.info()["q_pieces"] == 1
+    ix_o = O.build_index(X, L, D, 0.3, seed=60 + d)
+    gp = F.fpp_debug_probes(ix.handle, Q, 1)
+    c, s, fails = PT.compare_probes(ix_o, Q, 1, gp, list(range(L)))
+    assert not fails, fails[:5]
+    assert c >= 0.95 * len(Q) * L
+    # every probe set contains the query's own bucket and P distinct buckets
+    gpP = F.fpp_debug_probes(ix.handle, Q, P)
+    for i in range(len(Q)):
+        for t in range(L):
+            row = gpP[i, t].astype(np.int64)
+            assert len(set(row.tolist())) == P and gp[i, t] in row
+    # recall against exact search stays with the exact-split BF16 path's
+    ix3 = F.Index(X, L, D, 0.3, seed=60 + d, precision=F.FPP_BF16)
+    ti, _ = F.fpp_bruteforce(X, Q, 10)
+    got, _ = ix.search(Q, 10, P)
+    ref, _ = ix3.search(Q, 10, P)
+    rec = O.recall_at(got, ti, 10)
+    rec3 = O.recall_at(ref, ti, 10)
+    print(f"\none-piece BF16 hashing d={d} D={D} P={P}: recall@10 {rec:.4f} (exact split {rec3:.4f}), "
+          f"{c} single-probe sets equal to the oracle's, {s} near-tie skipped")
+    assert rec >= rec3 - 0.01
+    gi, gs = ix.search(Q, 10, P)
+    ex = _exact_scores(X, Q, gi)
+    ok = gi >= 0
+    assert np.allclose(gs[ok], ex[ok], rtol=1e-5, atol=1e-6)
+
+
+def test_one_piece_bf16_hashing_is_refused_where_it_does_not_apply(F):
+    X, _ = W.small_mixture(1000, 1, 32, 8, 0.3, 610)
+    for kw in (dict(precision=F.FPP_FP32), dict(precision=F.FPP_BF16, simhash_bits=256)):
+        with pytest.raises(F.FppError) as e:
+            F.Index(X, 4, 32, 0.5, seed=1, hash_precision=F.FPP_BF16, **kw)
+        assert e.value.status == F.FPP_EINVAL

@@ -63,3 +63,28 @@ def test_projection_table_range(F):
     full = F.fpp_debug_projections(ix.handle, Q)
     part = F.fpp_debug_projections(ix.handle, Q, 2, 5)
     assert np.array_equal(part, full[:, 2 * 2 * 32: 5 * 2 * 32])
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable(F):
+    # 2 L D = 128 projections of 100 queries: one 128 x 256 tile, one CTA.
+    # With the host's test hook that CTA never loads its first K chunk, so
+    # the tensor-core warp's wait runs out after about 10 ms; the CTA drains
+    # what it issued, frees its tensor memory and the call reports
+    # FPP_ETIMEOUT.  The next calls run normally on the same context.
+    X, Q = W.small_mixture(2000, 100, 64, 16, 0.25, 501)
+    ix = F.Index(X, 1, 64, 0.5, seed=5)
+    ref = F.fpp_debug_projections(ix.handle, Q)
+    gi, gs = ix.search(Q, 10, 2)
+    F.fpp_debug_wait_test(1, 20_000_000)
+    try:
+        with pytest.raises(F.FppError) as e:
+            F.fpp_debug_projections(ix.handle, Q)
+        assert e.value.status == F.FPP_ETIMEOUT and "bounded wait" in str(e.value)
+    finally:
+        F.fpp_debug_wait_test(0, 0)
+    assert np.array_equal(F.fpp_debug_projections(ix.handle, Q), ref)
+    gi2, gs2 = ix.search(Q, 10, 2)
+    assert np.array_equal(gi2, gi) and np.array_equal(gs2, gs)
+    with pytest.raises(F.FppError) as e:
+        F.fpp_debug_wait_test(2, 0)
+    assert e.value.status == F.FPP_EINVAL

@@ -156,3 +156,23 @@ def test_server_refuses_a_buffer_below_one_querys_worst_case(F, data):
     ids, sc, _ = srv.poll(srv.submit(Q[:50], 10, 8))
     srv.close()
     assert np.array_equal(ids, gi) and np.array_equal(sc, gs)
+
+
+def test_server_bulk_submit_equals_single_submits(F, data):
+    X, Q, ix = data
+    reqs = _requests(300, 405)
+    ref = _alone(F, ix, Q, reqs)
+    srv = F.Server(ix, k_max=20, probes_max=8, slots=2, max_batch=512)
+    rows = np.concatenate([Q[q0:q0 + nq] for q0, nq, _, _ in reqs])
+    rids = []
+    for p in sorted({r[3] for r in reqs}):   # one probe budget per call
+        sel = [i for i, r in enumerate(reqs) if r[3] == p]
+        part = np.concatenate([Q[reqs[i][0]:reqs[i][0] + reqs[i][1]] for i in sel])
+        got = srv.submit_many(part, [reqs[i][1] for i in sel], [reqs[i][2] for i in sel], p)
+        rids += list(zip(sel, got))
+    for i, rid in rids:
+        ids, sc, _ = srv.poll(rid)
+        assert np.array_equal(ids, ref[i][0]) and np.array_equal(sc, ref[i][1])
+    with pytest.raises(F.FppError):   # a bad request stops the call there
+        srv.submit_many(rows[:10], [5, 0, 5], [5, 5, 5], 2)
+    srv.close()
