@@ -249,16 +249,29 @@ void fpp_default_search_opts(fpp_search_opts* o);
 fpp_status fpp_build(const float* X, int64_t n, int32_t d, const fpp_params* p,
                      fpp_index** out);
 
-/* Searches m queries Q [m][d]: writes ids [m][k] (int64, -1 padding) and
- * scores [m][k] (FP32, -inf padding), best first (score desc, id asc).
- * probes = buckets probed per table, 1..min(4D^2, 128); k = 1..256.
- * m = 0 is a no-op. */
+/* Searches m queries Q [m][d] (the Falconn++ query, Section 3.4): projects
+ * each query onto every table's random vectors (Section 2.2), takes the
+ * cross-polytope hash of each of its two hashes (Eq. 1), probes the `probes`
+ * buckets of every table with the highest pair score v1(h1) + v2(h2)
+ * (Section 3.4, multi-probing: the first is the query's own bucket), takes
+ * the union of their kept points, scores it by exact inner product and
+ * returns the top-k (the problem of Section 1: top-k by x^T q).
+ * Writes ids [m][k] (int64, -1 padding) and scores [m][k] (FP32, -inf
+ * padding), best first (score desc, id asc).  Q, ids and scores are
+ * caller-owned, host or device memory.  probes = buckets probed per table,
+ * 1..min(4D^2, 128); k = 1..256.  m = 0 is a no-op.  Errors: FPP_EINVAL
+ * for a NULL pointer or an argument out of range, FPP_ENOMEM, FPP_ECUDA,
+ * FPP_ETIMEOUT (a bounded device wait ran out), FPP_EINTERNAL. */
 fpp_status fpp_search(const fpp_index* ix, const float* Q, int64_t m, int32_t k,
                       int32_t probes, int64_t* ids, float* scores);
 
-/* fpp_search with per-query k and probe budgets, a table range, a stream and
- * counters.  ids/scores have row stride opts->k_max; entries past a query's
- * own k are set to -1 / -inf.  stats may be NULL. */
+/* fpp_search (Section 3.4's query) with per-query k and probe budgets, a
+ * table range (the slice a table-sharded rank searches), the global probe
+ * budget qProbes over all tables (Sections 2.2 and 4), SimHash pre-ranking
+ * of the candidates (Section 4), a stream and counters.  ids/scores have row
+ * stride opts->k_max; entries past a query's own k are set to -1 / -inf.
+ * stats may be NULL.  Same errors as fpp_search, plus FPP_EINVAL for a
+ * global budget that a table's 128 offered buckets cannot serve. */
 fpp_status fpp_search_ex(const fpp_index* ix, const float* Q, int64_t m,
                          const fpp_search_opts* opts, int64_t* ids,
                          float* scores, fpp_search_stats* stats);
