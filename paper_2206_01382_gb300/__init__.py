@@ -106,11 +106,13 @@ def lib_path() -> str:
 
 
 def load(path: str | None = None):
-    """Loads libfpp.so (raises if it has not been built)."""
+    """Loads libfpp.so (raises if it has not been built).  The environment
+    variable FPP_LIBRARY may name another build of it, such as the
+    FPP_DEBUG_BOUNDS one (``_build.LIB_DEBUG``)."""
     global _lib
     if _lib is not None:
         return _lib
-    p = path or _build.LIB
+    p = path or os.environ.get("FPP_LIBRARY") or _build.LIB
     if not os.path.exists(p):
         raise RuntimeError(f"libfpp.so not found at {p}; build it with "
                            "paper_2206_01382_gb300._build.build()")

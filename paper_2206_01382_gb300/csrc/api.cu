@@ -920,6 +920,9 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   da.no_items = pl.sim_keep > 0 ? 1 : 0;
   da.range_shift = pl.range_shift; da.range_count = pl.range_count;
   da.stats = stv;
+  // the FPP_DEBUG_BOUNDS build's limits (slot 15 takes the first violation)
+  da.bd.flag = stv + 15; da.bd.n = ix->n; da.bd.kept = ix->kept_total;
+  da.bd.cap = ws.cand_cap; da.bd.nb = nbuckets(ix->D);
   // items, tier counts (slots 10 and 11) and the slots handed out (slot 12)
   FPP_CUDA(cudaMemsetAsync(stv + 10, 0, 3 * sizeof(unsigned long long), st));
   FPP_TRY(launch_count_entries(da, st));
@@ -955,6 +958,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   if (pl.range_count > 1) FPP_TRY(ws.items2.ensure(item_bytes));
   da.cand = ws.cand.as<uint32_t>();
   da.items = ws.items.as<ScoreItem>();
+  da.bd.cap = ws.cand_cap;
   FPP_TRY(launch_dedup(da, st));
   // the work items in order of their row range (the scoring reads them so)
   const ScoreItem* score_items = ws.items.as<ScoreItem>();
@@ -986,6 +990,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   sa.Xq = ix->Xq; sa.ldxq = ix->ldxq; sa.xscale = ix->xscale;
   sa.scores = ws.cscores.as<float>();
   sa.tune_g = ix->tune_score_g; sa.tune_waves = ix->tune_score_waves;
+  sa.bd = da.bd;
   FPP_TRY(launch_score(sa, ix->sm_count, st));
   if (ev) FPP_CUDA(cudaEventRecord(ev[6], st));
   TopkArgs ta{};
@@ -999,6 +1004,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   ta.cap = topk_cap(ta.kprime); ta.rcap = topk_rcap(ta.kprime);
   ta.slow = ws.tkslow.p; ta.err = reinterpret_cast<int*>(stv + 5); ta.stats = stv;
   ta.out_ids = ids_dev; ta.out_scores = scores_dev;
+  ta.bd = da.bd;
   FPP_TRY(launch_topk(ta, st));
   if (ev) FPP_CUDA(cudaEventRecord(ev[3], st));
   return tile_read();
@@ -1212,6 +1218,11 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
       set_error("search: a bounded wait in the projection kernel ran out");
       return FPP_ETIMEOUT;
     }
+    if (hs[15]) {
+      set_error("bounds check failed at site " + std::to_string(hs[15] >> 48) + ", index " +
+                std::to_string(hs[15] & 0xFFFFFFFFFFFFull));
+      return FPP_EINTERNAL;
+    }
     if (hs[13]) {
       set_error("global_probes: " + std::to_string(hs[13]) +
                 " queries would take more than 128 buckets from one table; the results are not the "
@@ -1348,6 +1359,7 @@ fpp_status server_search(fpp_server* s, ServerSlot& sl, const std::vector<Seg>& 
   FPP_CUDA(cudaStreamSynchronize(sl.st));
   if (sl.hstats[5]) { set_error("search: top-k re-check capacity exceeded"); return FPP_EINTERNAL; }
   if (sl.hstats[9]) { set_error("search: a bounded wait in the projection kernel ran out"); return FPP_ETIMEOUT; }
+  if (sl.hstats[15]) { set_error("search: a bounds check failed"); return FPP_EINTERNAL; }
   int64_t row = 0;
   for (const Seg& g : segs) {
     ServerRequest* r = g.r;

@@ -342,4 +342,23 @@ __device__ __forceinline__ uint32_t float_key(float f) {
 
 #endif  // __CUDACC__
 
+// Device checks of the FPP_DEBUG_BOUNDS build (a second library built from
+// the same sources, in place of a memory checker): FPP_IN_BOUNDS(bd, cond,
+// site, index) records the first failed condition in *bd.flag and returns
+// false, so that the guarded access is skipped; in the product build it is
+// the constant true and the condition is not evaluated.
+#ifdef FPP_DEBUG_BOUNDS
+template <class B>
+__device__ __forceinline__ bool fpp_bounds_ok(const B& bd, bool cond, unsigned site,
+                                              unsigned long long index) {
+  if (cond) return true;
+  if (bd.flag) atomicCAS(bd.flag, 0ull, ((unsigned long long)site << 48) | (index & 0xFFFFFFFFFFFFull));
+  return false;
+}
+#define FPP_IN_BOUNDS(bd, cond, site, index) \
+  ::fpp::fpp_bounds_ok((bd), (cond), (site), (unsigned long long)(index))
+#else
+#define FPP_IN_BOUNDS(bd, cond, site, index) true
+#endif
+
 }  // namespace fpp

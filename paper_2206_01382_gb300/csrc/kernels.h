@@ -209,6 +209,17 @@ fpp_status launch_query_norms(const float* Q, int64_t m, int64_t ldq, int d, flo
                               cudaStream_t st);
 
 // Candidate gather / de-duplication / scoring / top-k (search_kernels.cu).
+// Bounds of the FPP_DEBUG_BOUNDS build's device checks (kernels.h users
+// fill it in both builds; only that build reads it): *flag receives the
+// first violation as (site << 48) | index, and the access is skipped.
+struct Bounds {
+  unsigned long long* flag = nullptr;
+  int64_t n = 0;             // points: every candidate id is below n
+  uint64_t kept = 0;         // kept ids of all tables (the ids array)
+  uint64_t cap = 0;          // candidate slots of the workspace
+  int64_t nb = 0;            // buckets per table
+};
+
 struct ScoreItem {
   uint32_t q;        // query in the batch
   uint32_t len;      // candidates in this item
@@ -239,6 +250,7 @@ struct DedupArgs {
   int range_shift;           // range_count > 1: each query's ids are grouped by row
   int range_count;           // range (id >> range_shift), one or more items per range
   unsigned long long* stats; // entries, unique, -, probes
+  Bounds bd;
 };
 
 // SimHash pre-ranking: for every query with more than keep candidates,
@@ -277,6 +289,7 @@ struct ScoreArgs {
   float* scores;             // FP32 scores, parallel to cand
   int tune_g;                // lanes per row (power of two) or 0: heuristic
   int tune_waves;            // CTAs per resident slot or 0: default
+  Bounds bd;
 };
 
 struct TopkArgs {
@@ -304,6 +317,7 @@ struct TopkArgs {
   unsigned long long* stats; // stats[2] counts slow-path queries
   int64_t* out_ids;          // [mq][kmax]
   float* out_scores;
+  Bounds bd;
 };
 
 int score_item_len();

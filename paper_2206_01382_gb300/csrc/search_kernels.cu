@@ -1464,8 +1464,10 @@ __device__ __forceinline__ void warp_walk(const WarpWalk& w, Visit& visit) {
         const int t = a.tb + tl;
         const uint32_t b = a.probes[(w.q * a.nt + tl) * (int64_t)a.pstride + p];
         const uint32_t* off = a.offsets + (int64_t)t * (w.NB + 1);
-        const uint32_t o0 = b == PROBE_EMPTY ? 0u : off[b];   // empty slot: no bucket
-        c = b == PROBE_EMPTY ? 0u : off[b + 1] - o0;
+        // empty slot: no bucket
+        const bool live_b = b != PROBE_EMPTY && FPP_IN_BOUNDS(a.bd, b < (uint32_t)w.NB, 3, b);
+        const uint32_t o0 = live_b ? off[b] : 0u;
+        c = live_b ? off[b + 1] - o0 : 0u;
         w.pbase[i] = a.table_base[t] + o0;
       }
       cnt[r] = c;
@@ -1499,7 +1501,8 @@ __device__ __forceinline__ void warp_walk(const WarpWalk& w, Visit& visit) {
             const int mid = (lo + hi) >> 1;
             if (w.pstart[mid] <= e) lo = mid; else hi = mid;
           }
-          id[r] = __ldg(a.ids + w.pbase[lo] + (e - w.pstart[lo]));
+          const uint64_t gi = w.pbase[lo] + (e - w.pstart[lo]);
+          id[r] = FPP_IN_BOUNDS(a.bd, gi < a.bd.kept, 8, gi) ? __ldg(a.ids + gi) : 0u;
         }
       }
       visit(id, has);
@@ -1555,7 +1558,10 @@ count_entries_kernel(DedupArgs a) {
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r)
-      if (b[r] != PROBE_EMPTY) s += off[r][b[r] + 1] - off[r][b[r]];
+      if (b[r] != PROBE_EMPTY && FPP_IN_BOUNDS(a.bd, b[r] < (uint32_t)NB, 1, b[r])) {
+        const uint32_t o0 = off[r][b[r]], o1 = off[r][b[r] + 1];
+        if (FPP_IN_BOUNDS(a.bd, o1 >= o0, 2, b[r])) s += o1 - o0;
+      }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
@@ -1682,8 +1688,10 @@ dedup_hash_kernel(DedupArgs a) {
         const int t = a.tb + tl;
         const uint32_t bk = a.probes[(q * a.nt + tl) * (int64_t)a.pstride + p];
         const uint32_t* off = a.offsets + (int64_t)t * (NB + 1);
-        const uint32_t o0 = bk == PROBE_EMPTY ? 0u : off[bk];   // empty slot: no bucket
-        c = bk == PROBE_EMPTY ? 0u : off[bk + 1] - o0;
+        // empty slot: no bucket
+        const bool live_b = bk != PROBE_EMPTY && FPP_IN_BOUNDS(a.bd, bk < (uint32_t)NB, 3, bk);
+        const uint32_t o0 = live_b ? off[bk] : 0u;
+        c = live_b ? off[bk + 1] - o0 : 0u;
         pbase[tid] = a.table_base[t] + o0;
       }
       // exclusive prefix sum of the bucket sizes over the CTA
@@ -1733,7 +1741,10 @@ dedup_hash_kernel(DedupArgs a) {
               bnext = pstart[bk + 1];
               bbase = pbase[bk];
             }
-            id[u] = __ldg(a.ids + bbase + (e - bstart));
+            const uint64_t gi = bbase + (e - bstart);
+            if (FPP_IN_BOUNDS(a.bd, gi < a.bd.kept, 4, gi)) id[u] = __ldg(a.ids + gi);
+            else has[u] = false;
+            if (!FPP_IN_BOUNDS(a.bd, id[u] < (uint64_t)a.bd.n, 5, id[u])) has[u] = false;
             ++e;
           }
         }
@@ -1784,7 +1795,10 @@ dedup_hash_kernel(DedupArgs a) {
         uint32_t pos = wbase + inc - nf;
 #pragma unroll
         for (int u = 0; u < HU; ++u)
-          if (fresh[u]) out[pos++] = id[u];
+          if (fresh[u]) {
+            if (FPP_IN_BOUNDS(a.bd, pos < E && a.eoff[q] + pos < a.bd.cap, 6, pos)) out[pos] = id[u];
+            ++pos;
+          }
       }
       __syncthreads();   // pbase / pstart are rewritten by the next chunk
     }
@@ -1952,7 +1966,11 @@ score_kernel(ScoreArgs a) {
   ScoreItem item = it < nslots ? a.items[it] : ScoreItem{0u, 0u, 0ull};
   for (; it < nslots; it += nw) {
     const ScoreItem nxt = it + nw < nslots ? a.items[it + nw] : ScoreItem{0u, 0u, 0ull};
-    if (item.len == 0) { item = nxt; continue; }
+    if (item.len == 0 ||
+        !FPP_IN_BOUNDS(a.bd, item.start + item.len <= a.bd.cap, 9, item.start)) {
+      item = nxt;
+      continue;
+    }
     const uint32_t* ids = a.cand + item.start;
     const float4* q4 = reinterpret_cast<const float4*>(a.Q + (int64_t)item.q * a.ldq);
     float* out = a.scores + item.start;
@@ -1964,6 +1982,7 @@ score_kernel(ScoreArgs a) {
         const int r = r0 + u * RPP + grp;
         ok[u] = (uint32_t)r < item.len;
         id[u] = ok[u] ? __ldcs(ids + r) : 0u;   // streamed: keep L2 for the rows
+        ok[u] = ok[u] && FPP_IN_BOUNDS(a.bd, id[u] < (uint64_t)a.bd.n, 10, id[u]);
       }
       float p[U];
 #pragma unroll
@@ -2025,7 +2044,11 @@ score_bf16_kernel(ScoreArgs a) {
   ScoreItem item = it < nslots ? a.items[it] : ScoreItem{0u, 0u, 0ull};
   for (; it < nslots; it += nw) {
     const ScoreItem nxt = it + nw < nslots ? a.items[it + nw] : ScoreItem{0u, 0u, 0ull};
-    if (item.len == 0) { item = nxt; continue; }
+    if (item.len == 0 ||
+        !FPP_IN_BOUNDS(a.bd, item.start + item.len <= a.bd.cap, 9, item.start)) {
+      item = nxt;
+      continue;
+    }
     const uint32_t* ids = a.cand + item.start;
     const float4* q4 = reinterpret_cast<const float4*>(a.Q + (int64_t)item.q * a.ldq);
     float* out = a.scores + item.start;
@@ -2037,6 +2060,7 @@ score_bf16_kernel(ScoreArgs a) {
         const int r = r0 + u * RPP + grp;
         ok[u] = (uint32_t)r < item.len;
         id[u] = ok[u] ? __ldg(ids + r) : 0u;   // (a streaming hint here measured 30% slower)
+        ok[u] = ok[u] && FPP_IN_BOUNDS(a.bd, id[u] < (uint64_t)a.bd.n, 10, id[u]);
       }
       float p[U];
 #pragma unroll
@@ -2103,7 +2127,11 @@ score_fp8_kernel(ScoreArgs a) {
   ScoreItem item = it < nslots ? a.items[it] : ScoreItem{0u, 0u, 0ull};
   for (; it < nslots; it += nw) {
     const ScoreItem nxt = it + nw < nslots ? a.items[it + nw] : ScoreItem{0u, 0u, 0ull};
-    if (item.len == 0) { item = nxt; continue; }
+    if (item.len == 0 ||
+        !FPP_IN_BOUNDS(a.bd, item.start + item.len <= a.bd.cap, 9, item.start)) {
+      item = nxt;
+      continue;
+    }
     const uint32_t* ids = a.cand + item.start;
     const float* qrow = a.Q + (int64_t)item.q * a.ldq;
     float* out = a.scores + item.start;
@@ -2272,7 +2300,7 @@ topk_kernel(TopkArgs a) {
   const int kq = a.k_pq ? a.k_pq[q] : a.k;
   const int kp = max(kq + 16, a.kprime);   // the FP32 re-ranked shortlist
   const uint64_t start = a.eoff[q];
-  const uint32_t U = a.ucount[q];
+  const uint32_t U = FPP_IN_BOUNDS(a.bd, start + a.ucount[q] <= a.bd.cap, 11, q) ? a.ucount[q] : 0u;
   const float* sc = a.scores + start;
   const uint32_t* cid = a.cand + start;
   const float* qv = a.Q + q * a.ldq;
