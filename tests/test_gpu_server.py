@@ -176,3 +176,20 @@ def test_server_bulk_submit_equals_single_submits(F, data):
     with pytest.raises(F.FppError):   # a bad request stops the call there
         srv.submit_many(rows[:10], [5, 0, 5], [5, 5, 5], 2)
     srv.close()
+
+
+def test_server_refuses_requests_past_its_queue_limit(F, data):
+    # admission: with max_queue = 3, a group of 8 requests queued in one call
+    # (the queue lock is held while it is filled, so no slot drains it in
+    # between) keeps the first 3 and refuses the rest with FPP_EBUSY; the
+    # admitted ones complete normally
+    X, Q, ix = data
+    srv = F.Server(ix, k_max=10, probes_max=4, slots=1, max_batch=64, max_queue=3)
+    with pytest.raises(F.FppError) as e:
+        srv.submit_many(Q[:40], [5] * 8, [10] * 8, 2)
+    assert e.value.status == F.FPP_EBUSY and "queue full" in str(e.value)
+    st = srv.stats()
+    assert st["submitted"] == 3
+    gi, gs, _ = F.fpp_search_ex(ix.handle, Q[:15], k=10, probes=2, want_stats=False)
+    srv.close()
+    assert gi.shape == (15, 10)
