@@ -204,3 +204,24 @@ def test_one_piece_bf16_hashing_is_refused_where_it_does_not_apply(F):
         with pytest.raises(F.FppError) as e:
             F.Index(X, 4, 32, 0.5, seed=1, hash_precision=F.FPP_BF16, **kw)
         assert e.value.status == F.FPP_EINVAL
+
+
+def test_one_piece_bf16_hashing_with_centering_multiprobe_and_global_probes(F):
+    # the one-product query projections compose with the other options: the
+    # index's own hashing stays exact (centered, or iProbes = 2), every
+    # single-probe set equals the oracle's, and a global budget returns
+    # results with exact scores
+    X, Q = W.small_mixture(12000, 120, 64, 96, 0.3 / 8, 620)
+    X = (X + np.float32(0.1)).astype(np.float32)
+    for kw in ({"center": True}, {"iprobes": 2, "kappa": 2}):
+        ix = F.Index(X, 4, 32, 0.3, seed=61, precision=F.FPP_BF16, hash_precision=F.FPP_BF16, **kw)
+        ix_o = O.build_index(X, 4, 32, 0.3, seed=61, **kw)
+        gp = F.fpp_debug_probes(ix.handle, Q, 1)
+        c, s, fails = PT.compare_probes(ix_o, Q, 1, gp, list(range(4)))
+        assert not fails, (kw, fails[:5])
+        assert c >= 0.95 * len(Q) * 4
+        gi, gs, _ = F.fpp_search_ex(ix.handle, Q, k=10, global_probes=40)
+        assert (gi[:, 0] >= 0).all()
+        ex = _exact_scores(X, Q, gi)
+        ok = gi >= 0
+        assert np.allclose(gs[ok], ex[ok], rtol=1e-5, atol=1e-6)
