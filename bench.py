@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--graph", action="store_true",
                     help="time the steps as replays of the library's captured search graph")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-pipeline", action="store_true",
+                    help="run the steps one after another (no FPP_SEARCH_PIPELINE)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -607,14 +609,20 @@ def main():
     sc = torch.empty((m, k), dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
 
+    # consecutive steps are pipelined (FPP_SEARCH_PIPELINE: the index
+    # alternates two workspaces on two internal streams, so one step's
+    # projections overlap the previous step's gather and scoring); a flush
+    # orders every step's results before the timed region ends
+    pipe = not args.graph and not args.no_pipeline
     for _ in range(args.warmup):
         F.fpp_search_ex(ix.handle, Qd, stream=stream, ids=ids, scores=sc, want_stats=False,
-                        graph=args.graph, **search_kw)
+                        graph=args.graph, pipeline=pipe, **search_kw)
+    F.fpp_search_flush(ix.handle, stream)
     barrier()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 2)]
     launches0 = F.fpp_launch_count()
     phase = {"ms_project": 0.0, "ms_probe": 0.0, "ms_probe_exact": 0.0, "ms_gather_score": 0.0,
              "ms_dedup": 0.0, "ms_score": 0.0, "ms_topk": 0.0}
@@ -624,8 +632,10 @@ def main():
     evs[0].record(stream)
     for s in range(args.steps):
         F.fpp_search_ex(ix.handle, Qd, stream=stream, ids=ids, scores=sc, want_stats=False,
-                        graph=args.graph, **search_kw)
+                        graph=args.graph, pipeline=pipe, **search_kw)
         evs[s + 1].record(stream)
+    F.fpp_search_flush(ix.handle, stream)
+    evs[-1].record(stream)
     barrier()
     launches = F.fpp_launch_count() - launches0
     clocks = sampler.stop()
@@ -638,7 +648,7 @@ def main():
             phase[key] += st[key]
         for key in tot:
             tot[key] += st[key]
-    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]   # (pipelined: call points)
     elapsed_ms = evs[0].elapsed_time(evs[-1])
     if dist is not None:
         t = torch.tensor([elapsed_ms], device=dev)
@@ -767,15 +777,17 @@ def main():
             host_kw.update(k_per_query=torch.from_numpy(kpq).pin_memory(),
                            probes_per_query=torch.from_numpy(ppq).pin_memory())
         F.fpp_search_ex(ix.handle, Qh, ids=ih, scores=sh, want_stats=False, stream=stream,
-                        **host_kw)
+                        pipeline=pipe, **host_kw)
+        F.fpp_search_flush(ix.handle, stream)
         barrier()
         # each step copies its queries in and its results out (pinned host
-        # memory, ordered on the stream); the calls do not wait, one
-        # synchronisation ends the timed region
+        # memory, ordered on the stream); the calls do not wait, one flush
+        # and one synchronisation end the timed region
         t0 = time.perf_counter()
         for _ in range(args.steps):
             F.fpp_search_ex(ix.handle, Qh, ids=ih, scores=sh, want_stats=False, stream=stream,
-                            **host_kw)
+                            pipeline=pipe, **host_kw)
+        F.fpp_search_flush(ix.handle, stream)
         barrier()
         e2e_s = (time.perf_counter() - t0) / args.steps
         if dist is not None:
@@ -850,6 +862,7 @@ def main():
                        f"{w.n * w.d * 4 / 2**20:.0f} MiB), no flush",
                        "build_s": build_s, "index_kept_ids": info["kept_total"],
                        "max_bucket_kept": info["max_bucket_kept"], "cuda_graph": args.graph,
+                       "pipelined_steps": pipe,
                        "autotune": tune,
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"batch_p50": sm[len(sm) // 2], "batch_p99": sm[min(len(sm) - 1, int(0.99 * len(sm)))]},

@@ -179,6 +179,19 @@ typedef struct fpp_search_opts {
  * point; error flags raised inside the graph are not reported. */
 #define FPP_SEARCH_GRAPH 1
 
+/* FPP_SEARCH_PIPELINE: consecutive calls on one index overlap on the
+ * device.  The index alternates two workspaces on two internal streams: a
+ * call starts once the caller's stream reaches it (its inputs must be final
+ * there) and the call before last has ended, so one call's projections run
+ * while the previous call gathers and scores.  Taken only with a non-NULL
+ * stream, NULL stats, no global_probes, device or page-locked host Q and
+ * outputs, and device per-query arrays; otherwise the call runs normally.
+ * A pipelined call's results are complete once the caller's stream reaches
+ * the next pipelined call on the index, or after fpp_search_flush(ix,
+ * stream); device-side error flags are not reported.  The index holds a
+ * second workspace while pipelining. */
+#define FPP_SEARCH_PIPELINE 2
+
 /* Counters of one search call (summed over queries). */
 typedef struct fpp_search_stats {
   uint64_t queries;
@@ -275,6 +288,12 @@ fpp_status fpp_search(const fpp_index* ix, const float* Q, int64_t m, int32_t k,
 fpp_status fpp_search_ex(const fpp_index* ix, const float* Q, int64_t m,
                          const fpp_search_opts* opts, int64_t* ids,
                          float* scores, fpp_search_stats* stats);
+
+/* Makes `stream` wait for every pipelined call of the index (see
+ * FPP_SEARCH_PIPELINE): their results are complete once the stream reaches
+ * this point.  A no-op when none is pending.  Errors: FPP_EINVAL for a NULL
+ * index, FPP_ECUDA. */
+fpp_status fpp_search_flush(const fpp_index* ix, void* stream);
 
 /* Releases the index and its device memory.  NULL is allowed. */
 void fpp_free(fpp_index* ix);

@@ -22,6 +22,7 @@ from . import _build
 FPP_OK, FPP_EINVAL, FPP_ENOMEM, FPP_ECUDA, FPP_ETIMEOUT, FPP_EBUSY, FPP_EINTERNAL = range(7)
 FPP_FP32, FPP_BF16, FPP_FP8E4M3 = 0, 1, 2
 FPP_SEARCH_GRAPH = 1
+FPP_SEARCH_PIPELINE = 2
 STATUS_NAMES = {0: "FPP_OK", 1: "FPP_EINVAL", 2: "FPP_ENOMEM", 3: "FPP_ECUDA",
                 4: "FPP_ETIMEOUT", 5: "FPP_EBUSY", 6: "FPP_EINTERNAL"}
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
@@ -141,6 +142,7 @@ def load(path: str | None = None):
         "fpp_projection_error_bound": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
         "fpp_bruteforce_static": (ctypes.c_int, [f32p, i64, i32, f32p, i64, i32, vp, vp, vp]),
         "fpp_debug_wait_test": (ctypes.c_int, [i32, i64]),
+        "fpp_search_flush": (ctypes.c_int, [vp, vp]),
         "fpp_launch_count": (u64, []),
         "fpp_alloc_count": (u64, []),
         "fpp_merge_topk": (ctypes.c_int, [vp, vp, i32, i64, i32, vp, vp]),
@@ -272,7 +274,7 @@ def fpp_search_ex(ix, Q, k: int = 10, probes: int = 1, k_per_query=None, probes_
                   k_max: int | None = None, table_begin: int = 0, table_end: int = 0,
                   stream=None, ids=None, scores=None, want_stats: bool = True,
                   graph: bool = False, global_probes: int = 0, simhash_keep: int = 0,
-                  score_range_rows: int = 0):
+                  score_range_rows: int = 0, pipeline: bool = False):
     """fpp_search with per-query k / probes, a table range, a stream and stats."""
     Q = _f32(Q)
     m = Q.shape[0]
@@ -286,7 +288,7 @@ def fpp_search_ex(ix, Q, k: int = 10, probes: int = 1, k_per_query=None, probes_
     o.k_per_query, o.probes_per_query = _ptr(kpq), _ptr(ppq)
     o.k_max, o.table_begin, o.table_end = k_max, table_begin, table_end
     o.stream = _stream_ptr(stream)
-    o.flags = FPP_SEARCH_GRAPH if graph else 0
+    o.flags = (FPP_SEARCH_GRAPH if graph else 0) | (FPP_SEARCH_PIPELINE if pipeline else 0)
     o.global_probes = global_probes
     o.simhash_keep = simhash_keep
     o.score_range_rows = score_range_rows
@@ -296,6 +298,11 @@ def fpp_search_ex(ix, Q, k: int = 10, probes: int = 1, k_per_query=None, probes_
     _check(load().fpp_search_ex(ix, _ptr(Q), m, ctypes.byref(o), _ptr(ids), _ptr(scores),
                                 ctypes.byref(st) if want_stats else None))
     return ids, scores, (st.as_dict() if want_stats else None)
+
+
+def fpp_search_flush(ix, stream=None) -> None:
+    """Makes the stream wait for every pipelined call of the index."""
+    _check(load().fpp_search_flush(ix, _stream_ptr(stream)))
 
 
 def fpp_rotations(seed: int, L: int, D: int, d: int) -> np.ndarray:

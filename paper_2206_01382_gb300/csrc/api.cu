@@ -194,6 +194,15 @@ struct fpp_index {
   uint64_t build_rechecks = 0;
   std::mutex mu;
   fpp::Workspace ws;
+  // FPP_SEARCH_PIPELINE: two workspaces used in turn on two internal
+  // streams, so that a call's projection overlaps the previous call's
+  // gather and scoring; pdone[c] marks the end of the last call on slot c
+  fpp::Workspace ws_pipe;
+  cudaStream_t pstream[2] = {nullptr, nullptr};
+  cudaEvent_t pdone[2] = {nullptr, nullptr};
+  cudaEvent_t pin = nullptr;
+  bool ppending[2] = {false, false};
+  int pnext = 0;
 };
 
 using namespace fpp;
@@ -229,7 +238,19 @@ void free_index_memory(fpp_index* ix) {
   cudaFree(ix->ids);
   if (ix->graph_exec) cudaGraphExecDestroy(ix->graph_exec);
   ix->graph_exec = nullptr;
+  for (int c = 0; c < 2; ++c) {
+    if (ix->pstream[c]) {
+      cudaStreamSynchronize(ix->pstream[c]);
+      cudaStreamDestroy(ix->pstream[c]);
+    }
+    if (ix->pdone[c]) cudaEventDestroy(ix->pdone[c]);
+    ix->pstream[c] = nullptr;
+    ix->pdone[c] = nullptr;
+  }
+  if (ix->pin) cudaEventDestroy(ix->pin);
+  ix->pin = nullptr;
   ix->ws.release();
+  ix->ws_pipe.release();
 }
 
 __global__ void gather_u64_kernel(const uint64_t* src, int64_t stride, int cnt, uint64_t* dst) {
@@ -1143,6 +1164,50 @@ bool search_graph(fpp_index* ix, const float* Q, int64_t m, const fpp_search_opt
   return true;
 }
 
+// FPP_SEARCH_PIPELINE: call c of the index runs on internal stream c % 2
+// with workspace c % 2.  It starts once the caller's stream reaches the call
+// (its inputs are then final) and the previous call on the same slot has
+// ended; the caller's stream then waits for the previous call of the other
+// slot, so at most two calls are in flight and each call's results are
+// complete when the caller's stream reaches the next pipelined call (or
+// fpp_search_flush).  Device-side error flags are not read.
+fpp_status search_pipelined(fpp_index* ix, const float* Q, int64_t m, const SearchPlan& pl,
+                            int64_t mc, int64_t* ids, float* scores, cudaStream_t st,
+                            bool dev_out) {
+  const int c = ix->pnext;
+  ix->pnext ^= 1;
+  if (!ix->pin) FPP_CUDA(cudaEventCreateWithFlags(&ix->pin, cudaEventDisableTiming));
+  if (!ix->pstream[c]) {
+    FPP_CUDA(cudaStreamCreateWithFlags(&ix->pstream[c], cudaStreamNonBlocking));
+    FPP_CUDA(cudaEventCreateWithFlags(&ix->pdone[c], cudaEventDisableTiming));
+  }
+  cudaStream_t ps = ix->pstream[c];
+  Workspace& W = c ? ix->ws_pipe : ix->ws;
+  FPP_CUDA(cudaEventRecord(ix->pin, st));
+  FPP_CUDA(cudaStreamWaitEvent(ps, ix->pin, 0));
+  FPP_TRY(prepare_workspace(ix, W, pl, mc, !dev_out, ps, true, false));
+  FPP_TRY(W.order_after_last(ps));
+  FPP_CUDA(cudaMemsetAsync(W.stats.p, 0, 16 * 8, ps));
+  for (int64_t q0 = 0; q0 < m; q0 += mc) {
+    const int64_t cq = std::min<int64_t>(mc, m - q0);
+    int64_t* oid = dev_out ? ids + q0 * pl.kmax : W.out_ids.as<int64_t>();
+    float* osc = dev_out ? scores + q0 * pl.kmax : W.out_scores.as<float>();
+    FPP_TRY(search_chunk(ix, W, Q, q0, cq, pl, oid, osc, ps, kFull, nullptr, false));
+    if (!dev_out) {
+      FPP_CUDA(cudaMemcpyAsync(ids + q0 * pl.kmax, oid, cq * pl.kmax * 8, cudaMemcpyDeviceToHost, ps));
+      FPP_CUDA(cudaMemcpyAsync(scores + q0 * pl.kmax, osc, cq * pl.kmax * 4, cudaMemcpyDeviceToHost, ps));
+    }
+  }
+  FPP_TRY(W.mark_done(ps));
+  FPP_CUDA(cudaEventRecord(ix->pdone[c], ps));
+  ix->ppending[c] = true;
+  if (ix->ppending[c ^ 1]) {
+    FPP_CUDA(cudaStreamWaitEvent(st, ix->pdone[c ^ 1], 0));
+    ix->ppending[c ^ 1] = false;
+  }
+  return FPP_OK;
+}
+
 fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fpp_search_opts* o,
                        int64_t* ids, float* scores, fpp_search_stats* stats) {
   SearchPlan pl{};
@@ -1155,6 +1220,11 @@ fpp_status search_impl(const fpp_index* cix, const float* Q, int64_t m, const fp
   const bool dev_out = is_device_ptr(ids) && is_device_ptr(scores);
   const int nt = pl.te - pl.tb;
   const int64_t mc = std::min<int64_t>(chunk_rows(ix, nt, pl.pmax), m);
+  const bool out_pinned = is_pinned_host(ids) && is_pinned_host(scores);
+  if ((o->flags & FPP_SEARCH_PIPELINE) && st && !stats && pl.global_q == 0 &&
+      (dev_out || out_pinned) && (is_device_ptr(Q) || is_pinned_host(Q)) &&
+      (!pl.kpq || pl.kpq_dev) && (!pl.ppq || pl.ppq_dev))
+    return search_pipelined(ix, Q, m, pl, mc, ids, scores, st, dev_out);
   // page-locked host queries on a caller's stream: the uploads run ahead on
   // the workspace's copy stream, two query tiles in turn
   const bool ahead = st != nullptr && !is_device_ptr(Q) && is_pinned_host(Q);
@@ -1600,6 +1670,19 @@ void fpp_default_search_opts(fpp_search_opts* o) {
 }
 
 const char* fpp_last_error(void) { return g_err.c_str(); }
+
+fpp_status fpp_search_flush(const fpp_index* cix, void* stream) {
+  g_err.clear();
+  if (!cix) { set_error("index is NULL"); return FPP_EINVAL; }
+  fpp_index* ix = const_cast<fpp_index*>(cix);
+  std::lock_guard<std::mutex> lock(ix->mu);
+  for (int c = 0; c < 2; ++c) {
+    if (!ix->ppending[c]) continue;
+    FPP_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, ix->pdone[c], 0));
+    ix->ppending[c] = false;
+  }
+  return FPP_OK;
+}
 
 uint64_t fpp_launch_count(void) { return g_launches.load(); }
 uint64_t fpp_alloc_count(void) { return alloc_counter().load(); }

@@ -533,3 +533,40 @@ def test_global_probes_past_the_per_table_cap_are_refused(F):
     ix_o = O.build_index(X, 2, 8, 0.5, seed=16)
     per, _ = O.probe_global(ix_o, Q[0], 300)
     assert max(len(b) for b in per) > 128
+
+
+def test_pipelined_calls_equal_plain_calls(F):
+    # FPP_SEARCH_PIPELINE: consecutive calls alternate two workspaces on two
+    # internal streams; after a flush every call's results equal the plain
+    # call's, with device or page-locked host buffers, a change of budget
+    # between calls and a plain call among them
+    X, Q = W.small_mixture(30000, 2400, 64, 64, 0.25, 97)
+    ix = F.Index(X, 8, 32, 0.2, seed=5)
+    parts = [(i * 400, (i + 1) * 400, 1 + (i % 3)) for i in range(6)]
+    ref = [ix.search(Q[lo:hi], 10, P) for lo, hi, P in parts]
+    st = torch.cuda.Stream()
+    Qd = torch.from_numpy(Q).cuda()
+    Qh = torch.from_numpy(Q).pin_memory()
+    outs = []
+    for j, (lo, hi, P) in enumerate(parts):
+        if j == 3:   # a plain call among the pipelined ones
+            gi, gs = ix.search(Q[lo:hi], 10, P)
+            outs.append((gi, gs))
+            continue
+        if j % 2:
+            ids = torch.empty((hi - lo, 10), dtype=torch.int64).pin_memory()
+            sc = torch.empty((hi - lo, 10), dtype=torch.float32).pin_memory()
+            q = Qh[lo:hi]
+        else:
+            ids = torch.empty((hi - lo, 10), dtype=torch.int64, device="cuda")
+            sc = torch.empty((hi - lo, 10), dtype=torch.float32, device="cuda")
+            q = Qd[lo:hi]
+        F.fpp_search_ex(ix.handle, q, k=10, probes=P, stream=st, ids=ids, scores=sc,
+                        want_stats=False, pipeline=True)
+        outs.append((ids, sc))
+    F.fpp_search_flush(ix.handle, st)
+    st.synchronize()
+    for (gi, gs), (ri, rs) in zip(outs, ref):
+        gi = gi.cpu().numpy() if hasattr(gi, "cpu") else gi
+        gs = gs.cpu().numpy() if hasattr(gs, "cpu") else gs
+        assert np.array_equal(gi, ri) and np.array_equal(gs, rs)
