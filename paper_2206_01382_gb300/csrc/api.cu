@@ -16,6 +16,10 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#ifndef FPP_PIPE_SLOTS
+#define FPP_PIPE_SLOTS 2
+#endif
+
 namespace fpp {
 
 void generate_rotations(uint64_t seed, int L, int D, int d, float* R);
@@ -194,14 +198,16 @@ struct fpp_index {
   uint64_t build_rechecks = 0;
   std::mutex mu;
   fpp::Workspace ws;
-  // FPP_SEARCH_PIPELINE: two workspaces used in turn on two internal
-  // streams, so that a call's projection overlaps the previous call's
-  // gather and scoring; pdone[c] marks the end of the last call on slot c
-  fpp::Workspace ws_pipe;
-  cudaStream_t pstream[2] = {nullptr, nullptr};
-  cudaEvent_t pdone[2] = {nullptr, nullptr};
+  // FPP_SEARCH_PIPELINE: PIPE_SLOTS workspaces used in turn on as many
+  // internal streams, so that a call's projection overlaps the previous
+  // calls' gather and scoring; pdone[c] marks the end of the last call on
+  // slot c (slot 0 uses ws, slot c > 0 ws_pipe[c - 1])
+  static constexpr int PIPE_SLOTS = FPP_PIPE_SLOTS;
+  fpp::Workspace ws_pipe[PIPE_SLOTS - 1];
+  cudaStream_t pstream[PIPE_SLOTS] = {};
+  cudaEvent_t pdone[PIPE_SLOTS] = {};
   cudaEvent_t pin = nullptr;
-  bool ppending[2] = {false, false};
+  bool ppending[PIPE_SLOTS] = {};
   int pnext = 0;
 };
 
@@ -238,7 +244,7 @@ void free_index_memory(fpp_index* ix) {
   cudaFree(ix->ids);
   if (ix->graph_exec) cudaGraphExecDestroy(ix->graph_exec);
   ix->graph_exec = nullptr;
-  for (int c = 0; c < 2; ++c) {
+  for (int c = 0; c < fpp_index::PIPE_SLOTS; ++c) {
     if (ix->pstream[c]) {
       cudaStreamSynchronize(ix->pstream[c]);
       cudaStreamDestroy(ix->pstream[c]);
@@ -250,7 +256,7 @@ void free_index_memory(fpp_index* ix) {
   if (ix->pin) cudaEventDestroy(ix->pin);
   ix->pin = nullptr;
   ix->ws.release();
-  ix->ws_pipe.release();
+  for (auto& w : ix->ws_pipe) w.release();
 }
 
 __global__ void gather_u64_kernel(const uint64_t* src, int64_t stride, int cnt, uint64_t* dst) {
@@ -1174,15 +1180,16 @@ bool search_graph(fpp_index* ix, const float* Q, int64_t m, const fpp_search_opt
 fpp_status search_pipelined(fpp_index* ix, const float* Q, int64_t m, const SearchPlan& pl,
                             int64_t mc, int64_t* ids, float* scores, cudaStream_t st,
                             bool dev_out) {
+  constexpr int NS = fpp_index::PIPE_SLOTS;
   const int c = ix->pnext;
-  ix->pnext ^= 1;
+  ix->pnext = (c + 1) % NS;
   if (!ix->pin) FPP_CUDA(cudaEventCreateWithFlags(&ix->pin, cudaEventDisableTiming));
   if (!ix->pstream[c]) {
     FPP_CUDA(cudaStreamCreateWithFlags(&ix->pstream[c], cudaStreamNonBlocking));
     FPP_CUDA(cudaEventCreateWithFlags(&ix->pdone[c], cudaEventDisableTiming));
   }
   cudaStream_t ps = ix->pstream[c];
-  Workspace& W = c ? ix->ws_pipe : ix->ws;
+  Workspace& W = c ? ix->ws_pipe[c - 1] : ix->ws;
   FPP_CUDA(cudaEventRecord(ix->pin, st));
   FPP_CUDA(cudaStreamWaitEvent(ps, ix->pin, 0));
   FPP_TRY(prepare_workspace(ix, W, pl, mc, !dev_out, ps, true, false));
@@ -1201,9 +1208,12 @@ fpp_status search_pipelined(fpp_index* ix, const float* Q, int64_t m, const Sear
   FPP_TRY(W.mark_done(ps));
   FPP_CUDA(cudaEventRecord(ix->pdone[c], ps));
   ix->ppending[c] = true;
-  if (ix->ppending[c ^ 1]) {
-    FPP_CUDA(cudaStreamWaitEvent(st, ix->pdone[c ^ 1], 0));
-    ix->ppending[c ^ 1] = false;
+  // the caller's stream waits for the oldest call still in flight, so that
+  // NS calls overlap and the call NS - 1 back is complete at this point
+  const int old = (c + 1) % NS;
+  if (ix->ppending[old]) {
+    FPP_CUDA(cudaStreamWaitEvent(st, ix->pdone[old], 0));
+    ix->ppending[old] = false;
   }
   return FPP_OK;
 }
@@ -1676,7 +1686,7 @@ fpp_status fpp_search_flush(const fpp_index* cix, void* stream) {
   if (!cix) { set_error("index is NULL"); return FPP_EINVAL; }
   fpp_index* ix = const_cast<fpp_index*>(cix);
   std::lock_guard<std::mutex> lock(ix->mu);
-  for (int c = 0; c < 2; ++c) {
+  for (int c = 0; c < fpp_index::PIPE_SLOTS; ++c) {
     if (!ix->ppending[c]) continue;
     FPP_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, ix->pdone[c], 0));
     ix->ppending[c] = false;
