@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--graph", action="store_true",
                     help="time the steps as replays of the library's captured search graph")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--score-range-rows", type=int, default=0,
+                    help="rows per candidate row range of the scoring (0: the library's choice)")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="run the steps one after another (no FPP_SEARCH_PIPELINE)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -599,6 +601,8 @@ def main():
                                             [args.probes] if args.probes else list(w.probes))
         kpq = ppq = None
         search_kw = dict(k=k, probes=P)
+    if args.score_range_rows:
+        search_kw["score_range_rows"] = args.score_range_rows
     # the library's autotuner picks the scoring kernel's launch shape on the
     # workload's first batch (results do not depend on it)
     tune = None

@@ -161,8 +161,9 @@ typedef struct fpp_search_opts {
   int32_t score_range_rows;   /* candidate scoring groups each query's ids by
                                  row range so that the rows of one range are
                                  read by the whole GPU at once and stay in L2.
-                                 0: ranges of at most 64 MiB of candidate rows
-                                 (none when all rows fit one range); > 0: at
+                                 0: ranges of 32,768 rows, more when 256
+                                 ranges do not cover the index (none when all
+                                 rows fit one range); > 0: at
                                  least this many rows per range (rounded up to
                                  a power of two, at most 256 ranges).  Results
                                  do not depend on it.                          */
