@@ -737,8 +737,9 @@ def main():
                         "ms_per_launch": ms_of["ms_probe_exact"], "launches_per_step": chunks,
                         "bound": "alu"},
         "dedup": hbm("dedup_hash_kernel", "search_kernels.cu", ms_of["ms_dedup"], dedup_b,
-                     "count_entries + dedup_hash tiers + flatten + item ordering kernels: "
-                     "8 B per probed bucket + 4 B per kept id scanned"),
+                     "dedup_hash tiers (the small one counts each query's entries itself; "
+                     "count_entries runs only when a batch needs its exact total) + flatten + "
+                     "item ordering kernels: 8 B per probed bucket + 4 B per kept id scanned"),
         "score": hbm({"fp32": "score_kernel", "bf16": "score_bf16_kernel",
                       "fp8": "score_fp8_kernel"}[args.precision], "search_kernels.cu",
                      ms_of["ms_score"], score_b,

@@ -949,15 +949,17 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   da.bd.cap = ws.cand_cap; da.bd.nb = nbuckets(ix->D);
   // items, tier counts (slots 10 and 11) and the slots handed out (slot 12)
   FPP_CUDA(cudaMemsetAsync(stv + 10, 0, 3 * sizeof(unsigned long long), st));
-  FPP_TRY(launch_count_entries(da, st));
   // candidate slots: the bound from the largest kept bucket when the
   // workspace holds it or can be grown to it within the sync-free budget
-  // (no host round trip, so the batch can be captured in a graph);
-  // otherwise the exact total, read back
+  // (no host round trip, so the batch can be captured in a graph; the
+  // de-duplication tiers then count the entries and reserve the regions
+  // themselves); otherwise count_entries' exact total, read back
   const uint64_t bound = (uint64_t)mc * nt * pl.pmax * std::max<uint32_t>(ix->max_bucket_kept, 1);
   uint64_t need = bound;
   const bool exact = bound > ws.cand_cap && (pl.no_grow || bound > ix->cand_budget_entries);
+  da.fused = exact ? 0 : 1;
   if (exact) {
+    FPP_TRY(launch_count_entries(da, st));
     FPP_CUDA(cudaMemcpyAsync(&need, stv + 12, 8, cudaMemcpyDeviceToHost, st));
     FPP_CUDA(cudaStreamSynchronize(st));
   }

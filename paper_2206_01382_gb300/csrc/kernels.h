@@ -235,9 +235,10 @@ struct DedupArgs {
   const uint32_t* offsets;   // [L][4D^2 + 1]
   const uint64_t* table_base;// [L]
   const uint32_t* ids;       // kept ids
-  uint32_t* ecount;          // [mq] bucket entries per query (count_entries)
-  uint64_t* eoff;            // [mq] start of each query's region of ecount slots
-                             // (count_entries; regions are not in query order)
+  uint32_t* ecount;          // [mq] bucket entries per query (count_entries, or the
+                             // fused small tier)
+  uint64_t* eoff;            // [mq] start of each query's region (regions are not in
+                             // query order)
   unsigned long long* region_total;  // slots handed out (zeroed before count_entries)
   uint32_t* cand;            // candidate ids, query q at eoff[q] ..
   uint32_t* ucount;          // [mq] distinct candidates per query
@@ -247,6 +248,9 @@ struct DedupArgs {
                              // tier and for the no-de-duplication tier
   unsigned* tiern;           // [2] their counts (zeroed before count_entries)
   int no_items;              // 1: leave the items to the SimHash filter
+  int fused;                 // 1: no count_entries pass; the small tier counts each
+                             // query's entries, lists the larger ones in tierq, and
+                             // every tier reserves its queries' regions itself
   int range_shift;           // range_count > 1: each query's ids are grouped by row
   int range_count;           // range (id >> range_shift), one or more items per range
   unsigned long long* stats; // entries, unique, -, probes

@@ -1513,7 +1513,7 @@ __device__ __forceinline__ void warp_walk(const WarpWalk& w, Visit& visit) {
 
 // Appends query q's ceil(U / ITEM) score work items (at most ITEM candidates
 // each) to the item list (one counter atomic per query, warp-collective).
-__device__ __forceinline__ void write_items(const DedupArgs& a, int64_t q, uint32_t U) {
+__device__ __forceinline__ void write_items(const DedupArgs& a, int64_t q, uint64_t eo, uint32_t U) {
   if (a.no_items) return;
   const int lane = threadIdx.x & 31;
   const uint32_t nit = (U + ITEM - 1) / ITEM;
@@ -1524,7 +1524,7 @@ __device__ __forceinline__ void write_items(const DedupArgs& a, int64_t q, uint3
     ScoreItem it;
     it.q = (uint32_t)q;
     it.len = min((uint32_t)ITEM, U - k * ITEM);
-    it.start = a.eoff[q] + (uint64_t)k * ITEM;
+    it.start = eo + (uint64_t)k * ITEM;
     a.items[base + k] = it;
   }
 }
@@ -1606,7 +1606,17 @@ flatten_kernel(DedupArgs a) {
     const uint64_t E = a.ecount[q];
     const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
     WarpWalk w{&a, q, Pq, a.nt * Pq, NB, s_pbase[wid], s_pstart[wid]};
-    uint32_t* out = a.cand + a.eoff[q];
+    unsigned long long eo = 0;   // under a.fused the warp reserves its region of E slots
+    if (a.fused) {
+      if (lane == 0) {
+        eo = atomicAdd(a.region_total, (unsigned long long)E);
+        a.eoff[q] = eo;
+      }
+      eo = __shfl_sync(FULL, eo, 0);
+    } else {
+      eo = a.eoff[q];
+    }
+    uint32_t* out = a.cand + eo;
     const uint32_t U = (uint32_t)E;
     // (not grouped by row range: its items are ordered by their first id)
     struct Copy {
@@ -1629,7 +1639,7 @@ flatten_kernel(DedupArgs a) {
       prb += (unsigned long long)w.nprobe;
       a.ucount[q] = U;
     }
-    write_items(a, q, U);
+    write_items(a, q, eo, U);
     __syncwarp();
   }
 #pragma unroll
@@ -1644,17 +1654,50 @@ flatten_kernel(DedupArgs a) {
   }
 }
 
+// A query that the fused small tier does not de-duplicate itself: its entry
+// count is recorded, an empty query gets no candidates, and the others are
+// listed for the tier their count needs (the same rule as count_entries).
+__device__ __forceinline__ void hand_off(const DedupArgs& a, int64_t q, uint32_t E) {
+  a.ecount[q] = E;
+  if (E == 0) {
+    a.ucount[q] = 0u;
+    a.eoff[q] = 0ull;
+    return;
+  }
+  const int tier = E > (uint32_t)HMAX_BIG ? 1 : 0;
+  a.tierq[tier * a.mq + atomicAdd(a.tiern + tier, 1u)] = (uint32_t)q;
+}
+
+// Entries of probed bucket pi of query q (0 for an empty probe slot).
+__device__ __forceinline__ uint32_t probe_entries(const DedupArgs& a, int64_t q, int pi, int Pq,
+                                                  int64_t NB) {
+  const int tl = pi / Pq, p = pi - tl * Pq;
+  const uint32_t bk = a.probes[(q * a.nt + tl) * (int64_t)a.pstride + p];
+  if (bk == PROBE_EMPTY || !FPP_IN_BOUNDS(a.bd, bk < (uint32_t)NB, 1, bk)) return 0u;
+  const uint32_t* off = a.offsets + (int64_t)(a.tb + tl) * (NB + 1);
+  const uint32_t o0 = off[bk], o1 = off[bk + 1];
+  return FPP_IN_BOUNDS(a.bd, o1 >= o0, 2, bk) ? o1 - o0 : 0u;
+}
+
 // De-duplication of the queries with (ELO, EHI] bucket entries, one CTA (NT
 // threads) per query: an open-addressing hash set of HS ids in shared memory
 // (linear probing, insertion by compare-and-swap, so exactly one thread sees
 // an id as new), at most EHI / HS full and reset after each query.  TIER < 0
-// visits every query; otherwise the queries count_entries listed for TIER.
-// The probed buckets are resolved NT at a time; each thread then walks a
-// contiguous run of the entries, so the bucket of its next entry is found by
-// stepping instead of searching.
+// visits every query; otherwise the queries listed for TIER.  The probed
+// buckets are resolved NT at a time; each thread then walks a contiguous run
+// of the entries, so the bucket of its next entry is found by stepping
+// instead of searching.
+//
+// Regions: without a.fused, count_entries gave each query its region of E
+// slots.  With a.fused there is no count_entries pass: the small tier
+// (FUSE = 1) takes each query's entry count from its own resolution of the
+// probed buckets (a first pass over them when they do not fit one chunk),
+// hands the larger queries to the other tiers, and reserves each of its
+// queries' regions of E slots with one atomic; the other tiers reserve
+// theirs the same way.
 constexpr uint32_t HEMPTY = 0xFFFFFFFFu;
 
-template <int NT, int HS, int LOG2HS, int ELO, int EHI, int TIER>
+template <int NT, int HS, int LOG2HS, int ELO, int EHI, int TIER, int FUSE>
 __global__ void __launch_bounds__(NT, 1280 / NT)
 dedup_hash_kernel(DedupArgs a) {
   extern __shared__ __align__(16) uint32_t tab[];
@@ -1662,6 +1705,7 @@ dedup_hash_kernel(DedupArgs a) {
   __shared__ uint32_t pstart[NT + 1];
   __shared__ uint32_t wsum[NT / 32];
   __shared__ uint32_t s_n, s_base;
+  __shared__ unsigned long long s_eb;
   const bool grouped = a.range_count > 1 && !a.no_items;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int64_t nq = TIER < 0 ? a.mq : (int64_t)a.tiern[TIER];
@@ -1674,11 +1718,50 @@ dedup_hash_kernel(DedupArgs a) {
   unsigned long long ent = 0, uni = 0, prb = 0;
   for (int64_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
     const int64_t q = TIER < 0 ? qi : (int64_t)a.tierq[TIER * a.mq + qi];
-    const uint64_t E = a.ecount[q];
-    if (E > (uint64_t)EHI || E <= (uint64_t)ELO) continue;   // uniform over the CTA
     const int Pq = a.probes_pq ? a.probes_pq[q] : a.pstride;
     const int nprobe = a.nt * Pq;
-    uint32_t* out = a.cand + a.eoff[q];
+    uint64_t E = 0;
+    uint64_t eo = 0;      // start of the query's region
+    if (FUSE) {
+      if (nprobe > NT) {
+        // the entries of every probed bucket first (the walk resolves them again)
+        uint32_t s = 0;
+        for (int pi = tid; pi < nprobe; pi += NT) s += probe_entries(a, q, pi, Pq, NB);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+        if (lane == 0) wsum[wid] = s;
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) E += wsum[w];
+        const bool mine = E > (uint64_t)ELO && E <= (uint64_t)EHI;
+        if (tid == 0) {
+          if (mine) {
+            s_eb = atomicAdd(a.region_total, (unsigned long long)E);
+            a.eoff[q] = s_eb;
+          } else {
+            hand_off(a, q, (uint32_t)E);
+          }
+        }
+        __syncthreads();   // wsum is rewritten below; s_eb is read
+        if (!mine) continue;   // uniform
+        eo = s_eb;
+      }
+    } else {
+      E = a.ecount[q];
+      if (E > (uint64_t)EHI || E <= (uint64_t)ELO) continue;   // uniform over the CTA
+      if (a.fused) {   // a larger tier under a.fused: its own region of E slots
+        if (tid == 0) {
+          s_eb = atomicAdd(a.region_total, (unsigned long long)E);
+          a.eoff[q] = s_eb;
+        }
+        __syncthreads();
+        eo = s_eb;
+      } else {
+        eo = a.eoff[q];
+      }
+    }
+    uint32_t* out = a.cand + eo;   // (a fused query of one chunk: set below)
+    bool skip = false;
     for (int pc0 = 0; pc0 < nprobe; pc0 += NT) {
       const int nc = min(NT, nprobe - pc0);
       uint32_t c = 0;
@@ -1710,9 +1793,27 @@ dedup_hash_kernel(DedupArgs a) {
         woff += w < wid ? v : 0u;
         total += v;
       }
+      if (FUSE && nprobe <= NT) {
+        // one pass: the query's entry count is this chunk's
+        E = total;
+        if (E <= (uint64_t)ELO || E > (uint64_t)EHI) {   // uniform
+          if (tid == 0) hand_off(a, q, (uint32_t)E);
+          __syncthreads();   // wsum is rewritten by the next query
+          skip = true;
+          break;
+        }
+        if (tid == 0) {
+          s_eb = atomicAdd(a.region_total, (unsigned long long)E);
+          a.eoff[q] = s_eb;
+        }
+      }
       if (tid < nc) pstart[tid] = woff + inc - c;
       if (tid == 0) pstart[nc] = total;   // nc <= NT; entries past nc are never read
       __syncthreads();
+      if (FUSE && nprobe <= NT) {
+        eo = s_eb;
+        out = a.cand + eo;
+      }
       const uint32_t per = (total + NT - 1) / NT;
       uint32_t e = tid * per;
       const uint32_t eend = min(e + per, total);
@@ -1727,9 +1828,8 @@ dedup_hash_kernel(DedupArgs a) {
       }
       uint32_t bstart = pstart[bk], bnext = pstart[bk + 1];
       uint64_t bbase = pbase[bk];
-      for (uint32_t it = 0; it < per; it += HU) {
-        uint32_t id[HU];
-        bool has[HU];
+      // the thread's next HU entries (has: the entry exists)
+      auto walk = [&](uint32_t (&id)[HU], bool (&has)[HU]) {
 #pragma unroll
         for (int u = 0; u < HU; ++u) {
           has[u] = e < eend;
@@ -1748,11 +1848,13 @@ dedup_hash_kernel(DedupArgs a) {
             ++e;
           }
         }
-        // insertion: every pending id tries its current slot each pass, all
-        // HU compare-and-swaps in flight together; at load <= 1/4 a second
-        // pass is rare
+      };
+      // insertion: every pending id tries its current slot each pass, all
+      // HU compare-and-swaps in flight together; at load <= 1/4 a second
+      // pass is rare (fresh: the id was not in the set)
+      auto insert = [&](const uint32_t (&id)[HU], const bool (&has)[HU], bool (&fresh)[HU]) {
         uint32_t hp[HU];
-        bool pend[HU], fresh[HU];
+        bool pend[HU];
 #pragma unroll
         for (int u = 0; u < HU; ++u) {
           pend[u] = has[u];
@@ -1778,8 +1880,14 @@ dedup_hash_kernel(DedupArgs a) {
             }
           }
         }
-        // the thread's new ids go to consecutive slots: one warp scan and one
-        // shared-memory atomic per warp
+      };
+      for (uint32_t it = 0; it < per; it += HU) {
+        uint32_t id[HU];
+        bool has[HU], fresh[HU];
+        walk(id, has);
+        insert(id, has, fresh);
+        // the thread's new ids go to consecutive slots: one warp scan and
+        // one shared-memory atomic per warp
         uint32_t nf = 0;
 #pragma unroll
         for (int u = 0; u < HU; ++u) nf += fresh[u] ? 1u : 0u;
@@ -1796,12 +1904,13 @@ dedup_hash_kernel(DedupArgs a) {
 #pragma unroll
         for (int u = 0; u < HU; ++u)
           if (fresh[u]) {
-            if (FPP_IN_BOUNDS(a.bd, pos < E && a.eoff[q] + pos < a.bd.cap, 6, pos)) out[pos] = id[u];
+            if (FPP_IN_BOUNDS(a.bd, pos < E && eo + pos < a.bd.cap, 6, pos)) out[pos] = id[u];
             ++pos;
           }
       }
       __syncthreads();   // pbase / pstart are rewritten by the next chunk
     }
+    if (skip) continue;   // uniform
     const uint32_t U = s_n;
     if (grouped) {
       // group the query's distinct ids by row range (id >> range_shift): the
@@ -1812,9 +1921,9 @@ dedup_hash_kernel(DedupArgs a) {
         uni += U;
         prb += (unsigned long long)nprobe;
         a.ucount[q] = U;
+        if (FUSE) a.ecount[q] = (uint32_t)E;
       }
       uint32_t* rc = tab + HS - 3 * RANGE_MAX;
-      uint32_t* out = a.cand + a.eoff[q];
       const int R = a.range_count;
       for (int r = tid; r < R; r += NT) rc[r] = 0u;
       __syncthreads();
@@ -1854,7 +1963,7 @@ dedup_hash_kernel(DedupArgs a) {
           ScoreItem itm;
           itm.q = (uint32_t)q;
           itm.len = min((uint32_t)ITEM, c - k * ITEM);
-          itm.start = a.eoff[q] + rc[RANGE_MAX + r] + (uint64_t)k * ITEM;
+          itm.start = eo + rc[RANGE_MAX + r] + (uint64_t)k * ITEM;
           a.items[s_base + rc[2 * RANGE_MAX + r] + k] = itm;
         }
       }
@@ -1873,6 +1982,7 @@ dedup_hash_kernel(DedupArgs a) {
         uni += U;
         prb += (unsigned long long)nprobe;
         a.ucount[q] = U;
+        if (FUSE) a.ecount[q] = (uint32_t)E;
         s_base = nit ? atomicAdd(a.nitems, nit) : 0u;
       }
       __syncthreads();
@@ -1880,7 +1990,7 @@ dedup_hash_kernel(DedupArgs a) {
         ScoreItem itm;
         itm.q = (uint32_t)q;
         itm.len = min((uint32_t)ITEM, U - k * ITEM);
-        itm.start = a.eoff[q] + (uint64_t)k * ITEM;
+        itm.start = eo + (uint64_t)k * ITEM;
         a.items[s_base + k] = itm;
       }
     }
@@ -2866,22 +2976,22 @@ fpp_status launch_count_entries(const DedupArgs& a, cudaStream_t st) {
   return FPP_OK;
 }
 
-template <int NT, int HS, int LOG2HS, int ELO, int EHI, int TIER>
+template <int NT, int HS, int LOG2HS, int ELO, int EHI, int TIER, int FUSE>
 fpp_status launch_hash_tier(const DedupArgs& a, std::atomic<int>& grid_cache, cudaStream_t st) {
   const size_t smem = (size_t)HS * 4;
   int g = grid_cache.load(std::memory_order_relaxed);
   if (!g) {
-    FPP_CUDA(cudaFuncSetAttribute(dedup_hash_kernel<NT, HS, LOG2HS, ELO, EHI, TIER>,
+    FPP_CUDA(cudaFuncSetAttribute(dedup_hash_kernel<NT, HS, LOG2HS, ELO, EHI, TIER, FUSE>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0, dev = 0, sms = 0;
-    FPP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dedup_hash_kernel<NT, HS, LOG2HS, ELO, EHI, TIER>,
+    FPP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dedup_hash_kernel<NT, HS, LOG2HS, ELO, EHI, TIER, FUSE>,
                                                            NT, smem));
     FPP_CUDA(cudaGetDevice(&dev));
     FPP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     g = std::max(1, per_sm) * sms;
     grid_cache.store(g, std::memory_order_relaxed);
   }
-  dedup_hash_kernel<NT, HS, LOG2HS, ELO, EHI, TIER><<<(int)std::min<int64_t>(a.mq, g), NT, smem, st>>>(a);
+  dedup_hash_kernel<NT, HS, LOG2HS, ELO, EHI, TIER, FUSE><<<(int)std::min<int64_t>(a.mq, g), NT, smem, st>>>(a);
   FPP_LAUNCHED();
   return FPP_OK;
 }
@@ -2892,9 +3002,12 @@ fpp_status launch_dedup(const DedupArgs& a, cudaStream_t st) {
   // entries), 256 threads and 32,768 slots (<= 16,384), and no
   // de-duplication above that; a table never holds more distinct ids than
   // three quarters of its slots (one half for the larger one)
-  static std::atomic<int> g_small{0}, g_big{0};
-  FPP_TRY((launch_hash_tier<128, HS_SMALL, 12, 0, HMAX_SMALL, -1>(a, g_small, st)));
-  FPP_TRY((launch_hash_tier<256, HS_BIG, 15, HMAX_SMALL, HMAX_BIG, 0>(a, g_big, st)));
+  static std::atomic<int> g_small{0}, g_fused{0}, g_big{0};
+  if (a.fused)
+    FPP_TRY((launch_hash_tier<128, HS_SMALL, 12, 0, HMAX_SMALL, -1, 1>(a, g_fused, st)));
+  else
+    FPP_TRY((launch_hash_tier<128, HS_SMALL, 12, 0, HMAX_SMALL, -1, 0>(a, g_small, st)));
+  FPP_TRY((launch_hash_tier<256, HS_BIG, 15, HMAX_SMALL, HMAX_BIG, 0, 0>(a, g_big, st)));
   int sms = 0, dev = 0;
   FPP_CUDA(cudaGetDevice(&dev));
   FPP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
