@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--graph", action="store_true",
                     help="time the steps as replays of the library's captured search graph")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="batch10m: steps as plain (pipelined) calls instead of graph replays")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--score-range-rows", type=int, default=0,
                     help="rows per candidate row range of the scoring (0: the library's choice)")
@@ -541,6 +543,8 @@ def main():
     if args.rerank_k is None:
         args.rerank_k = 0 if w.name == "serve2m" else 100
     args.hash_bf16 = args.hash == "bf16" or (args.hash == "auto" and w.name == "precision1m")
+    if w.name == "batch10m" and not args.no_graph:
+        args.graph = True   # the batching workload runs each call as one captured graph
     if args.impl == "reference":
         run_reference(args, w)
         return

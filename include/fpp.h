@@ -175,9 +175,16 @@ typedef struct fpp_search_opts {
  * arrays, k, probes, k_max, table range and stream (the data they point to
  * may change between calls).  Taken only when stream is non-NULL, Q, ids,
  * scores and the per-query arrays are device memory and stats is NULL;
- * otherwise (or when the candidate buffers would need a read-back) the call
- * runs normally.  Results are complete once the stream reaches the call's
- * point; error flags raised inside the graph are not reported. */
+ * otherwise the call runs normally.  When the candidate buffers can hold the
+ * batch's worst case (L x probes x the largest kept bucket per query) within
+ * the candidate budget (fpp_set_candidate_budget), the call returns without
+ * waiting: results are complete once the stream reaches the call's point.
+ * Otherwise the graph is optimistic: the buffers are provisioned up to the
+ * budget, every query's candidate region is checked against them on the
+ * device, and the call waits for the check; if some region did not fit, the
+ * call is repeated without the graph (sized from the exact totals) and
+ * fpp_index_info.graph_fallbacks counts it.  Error flags raised inside the
+ * graph are not reported. */
 #define FPP_SEARCH_GRAPH 1
 
 /* FPP_SEARCH_PIPELINE: consecutive calls on one index overlap on the
@@ -241,7 +248,9 @@ typedef struct fpp_index_info {
   int32_t q_pieces;           /* BF16 pieces of the search's query
                                  projections: 3 (exact split) or 1
                                  (hash_precision FPP_BF16)                    */
-  int32_t reserved1;
+  uint32_t graph_fallbacks;   /* FPP_SEARCH_GRAPH calls whose optimistic
+                                 graph found a candidate region past the
+                                 buffer and were repeated without the graph  */
 } fpp_index_info;
 
 typedef struct fpp_index fpp_index;
@@ -519,6 +528,13 @@ void fpp_server_destroy(fpp_server* s);
  * pointers, parts < 1, m < 0, k < 1. */
 fpp_status fpp_merge_topk(const int64_t* ids, const float* scores, int32_t parts, int64_t m,
                           int32_t k, int64_t* out_ids, float* out_scores);
+
+/* Candidate buffer a search call may provision from the worst-case bound
+ * without reading the exact entry count back (and the size of an optimistic
+ * graph's buffers), in bytes: 8 per candidate slot.  Default min(8 GiB,
+ * device memory / 16).  Errors: FPP_EINVAL for a NULL index or bytes below
+ * 4,096. */
+fpp_status fpp_set_candidate_budget(fpp_index* ix, uint64_t bytes);
 
 /* Number of kernels this process has launched through libfpp. */
 uint64_t fpp_launch_count(void);

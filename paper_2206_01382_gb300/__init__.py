@@ -96,7 +96,7 @@ class fpp_index_info(ctypes.Structure):
                 ("rerank_k", ctypes.c_int32), ("center", ctypes.c_int32),
                 ("simhash_bits", ctypes.c_int32), ("r_pieces", ctypes.c_int32),
                 ("score_error_factor", ctypes.c_double), ("q_pieces", ctypes.c_int32),
-                ("reserved1", ctypes.c_int32)]
+                ("graph_fallbacks", ctypes.c_uint32)]
 
 
 _lib = None
@@ -145,6 +145,7 @@ def load(path: str | None = None):
         "fpp_search_flush": (ctypes.c_int, [vp, vp]),
         "fpp_launch_count": (u64, []),
         "fpp_alloc_count": (u64, []),
+        "fpp_set_candidate_budget": (ctypes.c_int, [vp, u64]),
         "fpp_merge_topk": (ctypes.c_int, [vp, vp, i32, i64, i32, vp, vp]),
         "fpp_autotune": (ctypes.c_int, [vp, f32p, i64, i32, i32, ctypes.POINTER(fpp_tune_report)]),
         "fpp_default_server_cfg": (None, [ctypes.POINTER(fpp_server_cfg)]),
@@ -411,6 +412,11 @@ def fpp_launch_count() -> int:
 def fpp_alloc_count() -> int:
     """Device allocations libfpp has made in this process."""
     return int(load().fpp_alloc_count())
+
+
+def fpp_set_candidate_budget(ix, nbytes: int) -> None:
+    """Candidate buffer bytes a call may provision without a read-back."""
+    _check(load().fpp_set_candidate_budget(ix, int(nbytes)))
 
 
 class Index:

@@ -181,6 +181,7 @@ struct fpp_index {
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<uint64_t> graph_key;
   uint64_t graph_kernels = 0;  // kernel nodes of the graph
+  uint64_t graph_overflows = 0;  // optimistic replays repeated without the graph
   int tune_score_g = 0, tune_score_waves = 0;   // fpp_autotune's choice (0: built-in)
   float* rmax = nullptr;       // [2L]
   float xmax = 0.f;            // largest point norm (inflated)
@@ -739,6 +740,9 @@ struct SearchPlan {
   int range_count = 1;
   bool no_grow = false; // serving: never grow the candidate buffers; a batch
                         // whose candidates do not fit returns FPP_EBUSY
+  bool optimistic = false;  // captured graph whose worst case exceeds the buffer:
+                            // no read-back, the tiers check each region against
+                            // the buffer and raise the overflow flag (slot 4)
   const int32_t* kpq;   // user arrays (host or device) or NULL
   const int32_t* ppq;
   bool kpq_dev, ppq_dev;
@@ -956,8 +960,10 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   // themselves); otherwise count_entries' exact total, read back
   const uint64_t bound = (uint64_t)mc * nt * pl.pmax * std::max<uint32_t>(ix->max_bucket_kept, 1);
   uint64_t need = bound;
-  const bool exact = bound > ws.cand_cap && (pl.no_grow || bound > ix->cand_budget_entries);
+  const bool exact = !pl.optimistic && bound > ws.cand_cap &&
+                     (pl.no_grow || bound > ix->cand_budget_entries);
   da.fused = exact ? 0 : 1;
+  da.overflow = stv + 4;
   if (exact) {
     FPP_TRY(launch_count_entries(da, st));
     FPP_CUDA(cudaMemcpyAsync(&need, stv + 12, 8, cudaMemcpyDeviceToHost, st));
@@ -967,7 +973,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
     set_error("the batch's candidates exceed the candidate buffer");
     return FPP_EBUSY;
   }
-  if (need > ws.cand_cap) {
+  if (need > ws.cand_cap && !pl.optimistic) {
     ws.cand.release(); ws.cscores.release(); ws.items.release();
     const uint64_t cap = exact ? need + need / 4 + 1024 : need;
     FPP_TRY(ws.cand.ensure((size_t)cap * 4));
@@ -985,6 +991,7 @@ fpp_status search_chunk(fpp_index* ix, Workspace& ws, const float* Q, int64_t q0
   da.cand = ws.cand.as<uint32_t>();
   da.items = ws.items.as<ScoreItem>();
   da.bd.cap = ws.cand_cap;
+  da.cap = ws.cand_cap;
   FPP_TRY(launch_dedup(da, st));
   // the work items in order of their row range (the scoring reads them so)
   const ScoreItem* score_items = ws.items.as<ScoreItem>();
@@ -1099,23 +1106,31 @@ fpp_status prepare_workspace(fpp_index* ix, Workspace& ws, const SearchPlan& pl,
 
 // FPP_SEARCH_GRAPH: the whole call (every batch) as one CUDA graph, captured
 // on first use and replayed while the call's arguments and the workspace
-// stay the same.  Needs candidate buffers provisioned from the worst-case
-// bound (no read-back inside a graph); returns false (nothing done) when the
-// bound exceeds the sync-free budget, so the caller runs the call normally.
+// stay the same.  There is no read-back inside a graph.  When the
+// candidate buffers can be provisioned from the worst-case bound, the graph
+// runs without waiting.  Otherwise (a bound past the sync-free budget) the
+// buffers are provisioned up to that budget and the graph is optimistic:
+// the de-duplication tiers check every region against the buffer, a query
+// whose region would not fit gets no candidates and raises the overflow flag,
+// and the call waits for the flag; if it is set, search_graph returns false
+// and the caller repeats the call without the graph, sized from the exact
+// totals.  Returns false (nothing done) as well when the graph cannot be used.
 bool search_graph(fpp_index* ix, const float* Q, int64_t m, const fpp_search_opts* o,
-                  const SearchPlan& pl, int64_t mc, int64_t* ids, float* scores, cudaStream_t st,
+                  const SearchPlan& pl0, int64_t mc, int64_t* ids, float* scores, cudaStream_t st,
                   fpp_status& out) {
   Workspace& ws = ix->ws;
-  const int nt = pl.te - pl.tb;
-  const uint64_t bound = (uint64_t)mc * nt * pl.pmax * std::max<uint32_t>(ix->max_bucket_kept, 1);
-  if (bound > ws.cand_cap && bound > ix->cand_budget_entries) return false;
+  const int nt = pl0.te - pl0.tb;
+  const uint64_t bound = (uint64_t)mc * nt * pl0.pmax * std::max<uint32_t>(ix->max_bucket_kept, 1);
+  SearchPlan pl = pl0;
+  pl.optimistic = bound > ws.cand_cap && bound > ix->cand_budget_entries;
+  const uint64_t want = pl.optimistic ? std::max<uint64_t>(ws.cand_cap, ix->cand_budget_entries) : bound;
   out = FPP_OK;
   auto fail = [&](fpp_status s) { out = s; return true; };
-  if (bound > ws.cand_cap) {
+  if (want > ws.cand_cap) {
     ws.cand.release(); ws.cscores.release(); ws.items.release();
-    if ((out = ws.cand.ensure((size_t)bound * 4)) != FPP_OK) return true;
-    if ((out = ws.cscores.ensure((size_t)bound * 4)) != FPP_OK) return true;
-    ws.cand_cap = bound;
+    if ((out = ws.cand.ensure((size_t)want * 4)) != FPP_OK) return true;
+    if ((out = ws.cscores.ensure((size_t)want * 4)) != FPP_OK) return true;
+    ws.cand_cap = want;
   }
   const size_t item_bytes =
       (size_t)score_item_slots(ws.cand_cap, mc, pl.range_count) * sizeof(ScoreItem);
@@ -1126,7 +1141,7 @@ bool search_graph(fpp_index* ix, const float* Q, int64_t m, const fpp_search_opt
       (uint64_t)(uintptr_t)pl.kpq, (uint64_t)(uintptr_t)pl.ppq, (uint64_t)pl.k,
       (uint64_t)pl.probes, (uint64_t)pl.kmax, (uint64_t)pl.pmax, (uint64_t)pl.tb, (uint64_t)pl.te,
       (uint64_t)(uintptr_t)st, (uint64_t)pl.global_q, (uint64_t)pl.sim_keep,
-      (uint64_t)pl.range_shift, (uint64_t)pl.range_count, g_alloc_gen.load()};
+      (uint64_t)pl.range_shift, (uint64_t)pl.range_count, (uint64_t)pl.optimistic, g_alloc_gen.load()};
   if (!ix->graph_exec || ix->graph_key != key) {
     if (ix->graph_exec) cudaGraphExecDestroy(ix->graph_exec);
     ix->graph_exec = nullptr;
@@ -1166,6 +1181,19 @@ bool search_graph(fpp_index* ix, const float* Q, int64_t m, const fpp_search_opt
     return fail(FPP_ECUDA);
   }
   launch_counter().fetch_add(ix->graph_kernels, std::memory_order_relaxed);
+  if (pl.optimistic) {
+    unsigned long long ov = 0;
+    if (cudaMemcpyAsync(&ov, ws.stats.as<unsigned long long>() + 4, 8, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      set_error("search graph: reading the overflow flag failed");
+      return fail(FPP_ECUDA);
+    }
+    if (ov) {   // some region did not fit: the call is repeated without the graph
+      ix->graph_overflows += 1;
+      return false;
+    }
+  }
   return true;
 }
 
@@ -1771,6 +1799,16 @@ fpp_status fpp_index_get_info(const fpp_index* ix, fpp_index_info* info) {
   info->r_pieces = ix->bpieces;
   info->score_error_factor = ix->score_gamma;
   info->q_pieces = ix->qpieces;
+  info->graph_fallbacks = (uint32_t)ix->graph_overflows;
+  return FPP_OK;
+}
+
+fpp_status fpp_set_candidate_budget(fpp_index* ix, uint64_t bytes) {
+  g_err.clear();
+  if (!ix) { set_error("index is NULL"); return FPP_EINVAL; }
+  if (bytes < 4096) { set_error("the candidate budget must be at least 4,096 bytes"); return FPP_EINVAL; }
+  std::lock_guard<std::mutex> lock(ix->mu);
+  ix->cand_budget_entries = bytes / 8;
   return FPP_OK;
 }
 

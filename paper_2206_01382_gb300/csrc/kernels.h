@@ -251,6 +251,10 @@ struct DedupArgs {
   int fused;                 // 1: no count_entries pass; the small tier counts each
                              // query's entries, lists the larger ones in tierq, and
                              // every tier reserves its queries' regions itself
+  uint64_t cap;              // candidate slots: under fused, a query whose reserved
+                             // region would end past cap gets no candidates and
+                             // sets *overflow (the caller then repeats the call)
+  unsigned long long* overflow;
   int range_shift;           // range_count > 1: each query's ids are grouped by row
   int range_count;           // range (id >> range_shift), one or more items per range
   unsigned long long* stats; // entries, unique, -, probes

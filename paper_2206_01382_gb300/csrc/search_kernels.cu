@@ -1587,6 +1587,22 @@ count_entries_kernel(DedupArgs a) {
   }
 }
 
+// Under a.fused: whether a region reserved at eo for E slots ends within the
+// candidate buffer.  If not, the query gets no candidates (its region is not
+// written) and the overflow flag is raised; the caller repeats the call with
+// a buffer sized from the exact total.  Sets eoff[q] either way.
+__device__ __forceinline__ int region_fits(const DedupArgs& a, int64_t q, uint64_t eo, uint32_t E) {
+  if (eo + E <= a.cap) {
+    a.eoff[q] = eo;
+    return 1;
+  }
+  a.eoff[q] = 0ull;
+  a.ecount[q] = E;
+  a.ucount[q] = 0u;
+  atomicExch(a.overflow, 1ull);
+  return 0;
+}
+
 // Queries with more than HMAX_BIG bucket entries keep every entry (no
 // de-duplication): with that many probed buckets few ids repeat, and a
 // repeated id only costs one more row read; the top-k kernel drops repeated
@@ -1608,11 +1624,13 @@ flatten_kernel(DedupArgs a) {
     WarpWalk w{&a, q, Pq, a.nt * Pq, NB, s_pbase[wid], s_pstart[wid]};
     unsigned long long eo = 0;   // under a.fused the warp reserves its region of E slots
     if (a.fused) {
+      int fits = 1;
       if (lane == 0) {
         eo = atomicAdd(a.region_total, (unsigned long long)E);
-        a.eoff[q] = eo;
+        fits = region_fits(a, q, eo, (uint32_t)E);
       }
       eo = __shfl_sync(FULL, eo, 0);
+      if (!__shfl_sync(FULL, fits, 0)) continue;   // uniform over the warp
     } else {
       eo = a.eoff[q];
     }
@@ -1706,6 +1724,7 @@ dedup_hash_kernel(DedupArgs a) {
   __shared__ uint32_t wsum[NT / 32];
   __shared__ uint32_t s_n, s_base;
   __shared__ unsigned long long s_eb;
+  __shared__ int s_fit;
   const bool grouped = a.range_count > 1 && !a.no_items;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int64_t nq = TIER < 0 ? a.mq : (int64_t)a.tiern[TIER];
@@ -1737,13 +1756,13 @@ dedup_hash_kernel(DedupArgs a) {
         if (tid == 0) {
           if (mine) {
             s_eb = atomicAdd(a.region_total, (unsigned long long)E);
-            a.eoff[q] = s_eb;
+            s_fit = region_fits(a, q, s_eb, (uint32_t)E);
           } else {
             hand_off(a, q, (uint32_t)E);
           }
         }
-        __syncthreads();   // wsum is rewritten below; s_eb is read
-        if (!mine) continue;   // uniform
+        __syncthreads();   // wsum is rewritten below; s_eb and s_fit are read
+        if (!mine || !s_fit) continue;   // uniform
         eo = s_eb;
       }
     } else {
@@ -1752,9 +1771,13 @@ dedup_hash_kernel(DedupArgs a) {
       if (a.fused) {   // a larger tier under a.fused: its own region of E slots
         if (tid == 0) {
           s_eb = atomicAdd(a.region_total, (unsigned long long)E);
-          a.eoff[q] = s_eb;
+          s_fit = region_fits(a, q, s_eb, (uint32_t)E);
         }
         __syncthreads();
+        if (!s_fit) {   // uniform; s_fit is rewritten for the next query only after this barrier
+          __syncthreads();
+          continue;
+        }
         eo = s_eb;
       } else {
         eo = a.eoff[q];
@@ -1804,13 +1827,17 @@ dedup_hash_kernel(DedupArgs a) {
         }
         if (tid == 0) {
           s_eb = atomicAdd(a.region_total, (unsigned long long)E);
-          a.eoff[q] = s_eb;
+          s_fit = region_fits(a, q, s_eb, (uint32_t)E);
         }
       }
       if (tid < nc) pstart[tid] = woff + inc - c;
       if (tid == 0) pstart[nc] = total;   // nc <= NT; entries past nc are never read
       __syncthreads();
       if (FUSE && nprobe <= NT) {
+        if (!s_fit) {   // uniform: no region, no candidates
+          skip = true;
+          break;
+        }
         eo = s_eb;
         out = a.cand + eo;
       }

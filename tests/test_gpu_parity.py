@@ -445,6 +445,41 @@ def test_graph_replay_equals_plain_calls(F):
     assert F.fpp_launch_count() - n0 > 4 * 8   # graph kernels are counted at each replay
 
 
+def test_optimistic_graph_checks_regions_and_falls_back(F):
+    # a worst-case bound past the candidate budget makes the graph
+    # optimistic: every candidate region is checked against the buffer on the
+    # device; a call whose entries fit runs as the graph, one whose entries do
+    # not is repeated without it (and its buffers grow), so a second such
+    # call fits
+    X, Q = W.small_mixture(30000, 700, 64, 64, 0.25, 95)
+    ref = F.Index(X, 8, 32, 0.2, seed=5)
+    m = 300
+    _, _, s1 = F.fpp_search_ex(ref.handle, Q[:m], k=10, probes=1)
+    _, _, s8 = F.fpp_search_ex(ref.handle, Q[:m], k=10, probes=8)
+    e1, e8 = int(s1["entries"]), int(s8["entries"])
+    assert e8 > 2 * e1
+    budget = (e1 + e8) // 2   # candidate slots: P = 1 fits, P = 8 does not
+    ix = F.Index(X, 8, 32, 0.2, seed=5)
+    assert m * 8 * 1 * ix.info()["max_bucket_kept"] > budget   # optimistic even at P = 1
+    F.fpp_set_candidate_budget(ix.handle, budget * 8)
+    st = torch.cuda.Stream()
+    Qd = torch.from_numpy(Q[:m]).cuda()
+    ids = torch.empty((m, 10), dtype=torch.int64, device="cuda")
+    sc = torch.empty((m, 10), dtype=torch.float32, device="cuda")
+    for P, fallbacks in ((1, 0), (8, 1), (8, 1), (1, 1)):
+        ids.fill_(-7)
+        torch.cuda.synchronize()
+        F.fpp_search_ex(ix.handle, Qd, k=10, probes=P, stream=st, ids=ids, scores=sc,
+                        want_stats=False, graph=True)
+        st.synchronize()
+        gi, gs = ref.search(Q[:m], 10, P)
+        assert np.array_equal(ids.cpu().numpy(), gi), P
+        assert np.array_equal(sc.cpu().numpy(), gs), P
+        assert ix.info()["graph_fallbacks"] == fallbacks, (P, fallbacks)
+    with pytest.raises(F.FppError):
+        F.fpp_set_candidate_budget(ix.handle, 1024)
+
+
 def test_autotune_keeps_results(F):
     X, Q = W.small_mixture(40000, 500, 96, 64, 0.25, 94)
     for prec in (F.FPP_FP32, F.FPP_BF16):
