@@ -1727,12 +1727,14 @@ dedup_hash_kernel(DedupArgs a) {
   __shared__ uint32_t s_n, s_base;
   __shared__ unsigned long long s_eb;
   __shared__ int s_fit;
+  __shared__ uint32_t s_cnt[RANGE_MAX];   // a grouped query's per-range counts, then cursors
   const bool grouped = a.range_count > 1 && !a.no_items;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int64_t nq = TIER < 0 ? a.mq : (int64_t)a.tiern[TIER];
   if (nq == 0) return;   // uniform over the CTA
   for (int i = tid; i < HS / 4; i += NT)
     reinterpret_cast<uint4*>(tab)[i] = make_uint4(HEMPTY, HEMPTY, HEMPTY, HEMPTY);
+  for (int r = tid; r < RANGE_MAX; r += NT) s_cnt[r] = 0u;
   if (tid == 0) s_n = 0;
   __syncthreads();
   const int64_t NB = 4ll * a.D * a.D;
@@ -1943,8 +1945,10 @@ dedup_hash_kernel(DedupArgs a) {
     const uint32_t U = s_n;
     if (grouped) {
       // group the query's distinct ids by row range (id >> range_shift): the
-      // ids are staged in the table's slots [0, U), the per-range counts,
-      // offsets and cursors sit in its last 3 RANGE_MAX slots (U <= 3/4 HS)
+      // ids are staged in the table's slots [0, U), counted per range in
+      // s_cnt (zero between queries); the ranges' offsets (R + 1 of them) and
+      // their items' offsets sit in the table's last 3 RANGE_MAX slots (U <=
+      // 3/4 HS), and s_cnt then holds the cursors
       if (tid == 0) {
         ent += E;
         uni += U;
@@ -1952,21 +1956,20 @@ dedup_hash_kernel(DedupArgs a) {
         a.ucount[q] = U;
         if (FUSE) a.ecount[q] = (uint32_t)E;
       }
-      uint32_t* rc = tab + HS - 3 * RANGE_MAX;
+      uint32_t* ro = tab + HS - 3 * RANGE_MAX;
+      uint32_t* io = ro + RANGE_MAX + 1;
       const int R = a.range_count;
-      for (int r = tid; r < R; r += NT) rc[r] = 0u;
-      __syncthreads();
       for (uint32_t i = tid; i < U; i += NT) {
         const uint32_t id = out[i];
         tab[i] = id;
-        atomicAdd(rc + (id >> a.range_shift), 1u);
+        atomicAdd(s_cnt + (id >> a.range_shift), 1u);
       }
       __syncthreads();
       if (wid == 0) {   // exclusive offsets of the ranges and of their items
         uint32_t carry = 0, icarry = 0;
         for (int r0 = 0; r0 < R; r0 += 32) {
           const int r = r0 + lane;
-          const uint32_t c = r < R ? rc[r] : 0u;
+          const uint32_t c = r < R ? s_cnt[r] : 0u;
           const uint32_t ni = (c + ITEM - 1) / ITEM;
           uint32_t inc = c, iinc = ni;
 #pragma unroll
@@ -1976,34 +1979,36 @@ dedup_hash_kernel(DedupArgs a) {
             if (lane >= o) { inc += t2; iinc += t3; }
           }
           if (r < R) {
-            rc[RANGE_MAX + r] = carry + inc - c;
-            rc[2 * RANGE_MAX + r] = icarry + iinc - ni;
+            ro[r] = carry + inc - c;
+            io[r] = icarry + iinc - ni;
+            s_cnt[r] = carry + inc - c;   // cursor
           }
           carry += __shfl_sync(FULL, inc, 31);
           icarry += __shfl_sync(FULL, iinc, 31);
         }
-        if (lane == 0) s_base = icarry ? atomicAdd(a.nitems, icarry) : 0u;   // one reservation
+        if (lane == 0) {
+          ro[R] = carry;
+          s_base = icarry ? atomicAdd(a.nitems, icarry) : 0u;   // one reservation
+        }
       }
       __syncthreads();
       for (int r = tid; r < R; r += NT) {
-        const uint32_t c = rc[r];
+        const uint32_t c = ro[r + 1] - ro[r];
         const uint32_t nit = (c + ITEM - 1) / ITEM;
         for (uint32_t k = 0; k < nit; ++k) {
           ScoreItem itm;
           itm.q = (uint32_t)q;
           itm.len = min((uint32_t)ITEM, c - k * ITEM);
-          itm.start = eo + rc[RANGE_MAX + r] + (uint64_t)k * ITEM;
-          a.items[s_base + rc[2 * RANGE_MAX + r] + k] = itm;
+          itm.start = eo + ro[r] + (uint64_t)k * ITEM;
+          a.items[s_base + io[r] + k] = itm;
         }
       }
-      __syncthreads();
-      for (int r = tid; r < R; r += NT) rc[2 * RANGE_MAX + r] = rc[RANGE_MAX + r];   // cursors
-      __syncthreads();
       for (uint32_t i = tid; i < U; i += NT) {
         const uint32_t id = tab[i];
-        out[atomicAdd(rc + 2 * RANGE_MAX + (id >> a.range_shift), 1u)] = id;
+        out[atomicAdd(s_cnt + (id >> a.range_shift), 1u)] = id;
       }
       __syncthreads();
+      for (int r = tid; r < R; r += NT) s_cnt[r] = 0u;   // for the next query
     } else {
       const uint32_t nit = a.no_items ? 0u : (U + ITEM - 1) / ITEM;
       if (tid == 0) {
