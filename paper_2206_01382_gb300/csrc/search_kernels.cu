@@ -1433,6 +1433,10 @@ constexpr int PCHUNK = 128;                     // probed buckets resolved per p
 constexpr int PPT = PCHUNK / 32;                // buckets per lane per pass
 constexpr int EPT = 8;                          // entries per lane per round
 constexpr int ITEM = 128;                       // candidates per score work item
+// threads per score CTA: 128 threads (about 9k registers) still fit beside a
+// projection CTA (320 x 168 registers) on its SM, so a pipelined call's
+// scoring can run on SMs where the other call projects; 256 could not
+constexpr int SCORE_T = 128;
 constexpr int RANGE_MAX = SCORE_RANGE_MAX;      // row ranges of the grouped scoring
 
 struct WarpWalk {
@@ -2097,7 +2101,7 @@ simhash_filter_kernel(SimArgs a) {
 // inner product.  EXACT: G * CPL float4 chunks cover a row exactly.
 
 template <int G, int CPL, bool EXACT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(SCORE_T)
 score_kernel(ScoreArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -2174,7 +2178,7 @@ score_kernel(ScoreArgs a) {
 // BF16 rows (precision path): the same structure, each chunk 8 BF16 values
 // (16 bytes) against 8 FP32 query values, FP32 accumulation.
 template <int G, int CPL, bool EXACT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(SCORE_T)
 score_bf16_kernel(ScoreArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -2257,7 +2261,7 @@ score_bf16_kernel(ScoreArgs a) {
 // decoded in pairs to half precision (exact) and accumulated in FP32
 // against the FP32 query; the row's scale multiplies the sum.
 template <int G, int CPL, bool EXACT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(SCORE_T)
 score_fp8_kernel(ScoreArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -2744,11 +2748,11 @@ fpp_status launch_resident(Kernel* k, int sms, const ScoreArgs& a, std::atomic<i
                            cudaStream_t st) {
   int b = per_sm.load(std::memory_order_relaxed);
   if (!b) {
-    FPP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, 256, 0));
+    FPP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, SCORE_T, 0));
     b = std::max(1, b);
     per_sm.store(b, std::memory_order_relaxed);
   }
-  k<<<b * sms * (a.tune_waves > 0 ? a.tune_waves : SCORE_WAVES), 256, 0, st>>>(a);
+  k<<<b * sms * (a.tune_waves > 0 ? a.tune_waves : SCORE_WAVES), SCORE_T, 0, st>>>(a);
   FPP_LAUNCHED();
   return FPP_OK;
 }
