@@ -73,6 +73,8 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     assert st == F.FPP_EINVAL
     assert b"NULL" in lib.fpp_last_error()
     lib.fpp_free(None)   # NULL-safe
+    assert lib.fpp_set_candidate_budget(None, 1 << 20) == F.FPP_EINVAL
+    assert b"NULL" in lib.fpp_last_error()
 
 
 def test_launch_count_starts_at_zero_without_work(lib):
